@@ -1,0 +1,1049 @@
+/*
+ * sx_oracle.c -- plain FP64 CPU oracle for the energy-based time-integrator
+ * hot path of "SymX: Energy-based Simulation from Symbolic Expressions".
+ *
+ * TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library. The
+ * product path (the CUDA library) never calls it, and the two share no
+ * code: this file includes no header of the product and reimplements every
+ * step from the paper in the most direct form, in double precision.
+ *
+ * What it computes (paper passages in brackets):
+ *   - Stable Neo-Hookean tet4 energy, gradient, Hessian: element strain
+ *     energy V_e psi(F_e) [§3.1, Eq. 7] with the Stable Neo-Hookean density
+ *     [App. B, "Eq. 14 from Smith et al."]; derivatives by the chain rule
+ *     through P = dpsi/dF and d2psi/dF2 and the constant 9x12 map vec(F) =
+ *     B xhat built from Dm^-1 [App. A, tet4 shape functions].
+ *   - Quadratic hinge bending E = k_b/2 x^T Q x [§6.3, Eq. 13].
+ *   - IPC log barrier E = -k (d - dhat)^2 ln(d/dhat) on the unsigned
+ *     point-triangle distance [§6.4, Eq. 15], active only for d < dhat
+ *     [§5.2 "Conditional evaluations", Eq. 9].
+ *   - Per-element projection to positive semi-definiteness [§5.2
+ *     "Projection to positive semi-definiteness", Algorithm 1 ProjectToPD]
+ *     by cyclic Jacobi eigen-decomposition and eigenvalue clamping.
+ *   - 3x3 block CRS pattern, element slot maps and ordered assembly of the
+ *     global gradient and Hessian [§5.3, Eq. 11, Algorithm 1].
+ *   - Inertia term of the backward-Euler incremental potential [§3, Eq. 2].
+ *   - 3x3 block-Jacobi preconditioned CG [§7.2, linear solver paragraph].
+ *   - Backward-Euler step by Newton's method with backtracking line search
+ *     [§3, Eqs. 2-3; §5.1 three evaluation levels].
+ *
+ * Parity status: every function here is pinned by tests in tests/ against
+ * closed forms, invariants, finite differences, library routines or brute
+ * force (see the test files); none is "parity unpinned".
+ *
+ * Readings where the paper is silent or ambiguous are marked READING.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_EDEGENERATE (-7)
+#define ORC_ENOTCONV (-5)
+#define ORC_ELINESEARCH (-9)
+#define ORC_EINVALID_STATE (-6)
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* small dense helpers (row-major)                                      */
+/* ------------------------------------------------------------------ */
+
+/* Levi-Civita symbol for indices in {0,1,2}. */
+static int levi(int i, int j, int k) { return (i - j) * (j - k) * (k - i) / 2; }
+
+static double det3(const double A[9])
+{
+    double d = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) {
+                int e = levi(i, j, k);
+                if (e) d += e * A[0 * 3 + i] * A[1 * 3 + j] * A[2 * 3 + k];
+            }
+    return d;
+}
+
+/* cof(F)_ij = 1/2 eps_imn eps_jpq F_mp F_nq  (= d det F / d F_ij). */
+static void cofactor3(const double F[9], double C[9])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int m = 0; m < 3; ++m)
+                for (int n = 0; n < 3; ++n)
+                    for (int p = 0; p < 3; ++p)
+                        for (int q = 0; q < 3; ++q) {
+                            int e = levi(i, m, n) * levi(j, p, q);
+                            if (e) s += e * F[m * 3 + p] * F[n * 3 + q];
+                        }
+            C[i * 3 + j] = 0.5 * s;
+        }
+}
+
+/* inverse via cofactors: A^-1 = cof(A)^T / det A */
+static void inv3(const double A[9], double Ai[9], double* detA)
+{
+    double C[9];
+    cofactor3(A, C);
+    double d = det3(A);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Ai[i * 3 + j] = C[j * 3 + i] / d;
+    if (detA) *detA = d;
+}
+
+/* ------------------------------------------------------------------ */
+/* Stable Neo-Hookean material                                          */
+/* ------------------------------------------------------------------ */
+
+/* Lame parameters from Young's modulus and Poisson ratio (textbook
+ * isotropic relations; the paper gives only E and nu, §6.1), then the
+ * Stable Neo-Hookean re-parameterization of App. B. READING: the listing's
+ * "4/3*mu" and "lambda + 5/6*lambda" are read as mu' = 4 mu / 3 and
+ * lambda' = lambda + 5 mu / 6 (the form whose small-strain limit is linear
+ * elasticity with mu, lambda; pinned by a test). literal != 0 keeps
+ * mu' = mu, lambda' = lambda. */
+void orc_snh_lame(int n, const double* E, const double* nu, int literal,
+                  double* mu_s, double* lam_s)
+{
+    for (int e = 0; e < n; ++e) {
+        double mu = E[e] / (2.0 * (1.0 + nu[e]));
+        double lam = E[e] * nu[e] / ((1.0 + nu[e]) * (1.0 - 2.0 * nu[e]));
+        if (literal) {
+            mu_s[e] = mu;
+            lam_s[e] = lam;
+        } else {
+            mu_s[e] = 4.0 * mu / 3.0;
+            lam_s[e] = lam + 5.0 * mu / 6.0;
+        }
+    }
+}
+
+/* alpha of App. B: 1 + mu'/lambda' - mu'/(4 lambda'). READING: for
+ * lambda' = 0 the volume term vanishes and alpha is taken as 1. */
+static double snh_alpha(double mu, double lam)
+{
+    if (lam == 0.0) return 1.0;
+    return 1.0 + mu / lam - mu / (4.0 * lam);
+}
+
+/* psi(F), P = dpsi/dF and d2psi/dF2 (9x9, vec index 3i+j) of the Stable
+ * Neo-Hookean density psi = mu'/2 (Ic-3) + lambda'/2 (J-alpha)^2
+ * - mu'/2 ln(Ic+1) [App. B]. READING: the energy is stored relative to
+ * psi(I) so that the rest energy is zero; the constant changes no
+ * derivative. */
+static void snh_density(const double F[9], double mu, double lam,
+                        double* psi, double P[9], double A[81])
+{
+    double alpha = snh_alpha(mu, lam);
+    double Ic = 0.0;
+    for (int k = 0; k < 9; ++k) Ic += F[k] * F[k];
+    double J = det3(F);
+    double C[9];
+    cofactor3(F, C);
+    double psi0 = 0.5 * lam * (1.0 - alpha) * (1.0 - alpha) - 0.5 * mu * log(4.0);
+    *psi = 0.5 * mu * (Ic - 3.0) + 0.5 * lam * (J - alpha) * (J - alpha)
+         - 0.5 * mu * log(Ic + 1.0) - psi0;
+    if (P) {
+        double a = mu * (1.0 - 1.0 / (Ic + 1.0));
+        for (int k = 0; k < 9; ++k) P[k] = a * F[k] + lam * (J - alpha) * C[k];
+    }
+    if (A) {
+        double a = mu * (1.0 - 1.0 / (Ic + 1.0));
+        double b = 2.0 * mu / ((Ic + 1.0) * (Ic + 1.0));
+        for (int r = 0; r < 9; ++r)
+            for (int c = 0; c < 9; ++c)
+                A[r * 9 + c] = (r == c ? a : 0.0) + b * F[r] * F[c] + lam * C[r] * C[c];
+        /* lambda'(J-alpha) d cof(F)_ij / d F_kl = eps_ikn eps_jlq F_nq */
+        double s = lam * (J - alpha);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) {
+                        double d = 0.0;
+                        for (int n = 0; n < 3; ++n)
+                            for (int q = 0; q < 3; ++q) {
+                                int e = levi(i, k, n) * levi(j, l, q);
+                                if (e) d += e * F[n * 3 + q];
+                            }
+                        A[(i * 3 + j) * 9 + (k * 3 + l)] += s * d;
+                    }
+    }
+}
+
+/* Rest quantities of a tet (App. A, linear tet4): Dm = [X1-X0, X2-X0,
+ * X3-X0] (columns), its inverse, and V = det(Dm)/6. READING: the volume
+ * must be positive; a non-positive det is reported as degenerate. */
+int orc_tet_rest(int T, const double* X, const int* tets, double* Dminv, double* V)
+{
+    int bad = 0;
+    for (int e = 0; e < T; ++e) {
+        double Dm[9];
+        const int* t = tets + 4 * e;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                Dm[i * 3 + j] = X[3 * t[j + 1] + i] - X[3 * t[0] + i];
+        double d;
+        inv3(Dm, Dminv + 9 * e, &d);
+        V[e] = d / 6.0;
+        if (!(d > 0.0)) bad++;
+    }
+    return bad;
+}
+
+/* Lumped mass, READING: rho V_e / 4 to each vertex of every tet. */
+void orc_lumped_mass(int N, int T, const int* tets, const double* V,
+                     const double* rho, double* m)
+{
+    for (int n = 0; n < N; ++n) m[n] = 0.0;
+    for (int e = 0; e < T; ++e)
+        for (int a = 0; a < 4; ++a) m[tets[4 * e + a]] += rho[e] * V[e] / 4.0;
+}
+
+/* Gradient of the tet4 shape functions in rest coordinates: G (4x3) with
+ * F_ij = sum_a x_{a,i} G_{a,j}; rows 1..3 are rows of Dm^-1 and row 0 is
+ * minus their sum. The 9x12 map B has B[(3i+j),(3a+k)] = delta_ik G_aj. */
+static void tet_B(const double Dminv[9], double B[9 * 12])
+{
+    double G[12];
+    for (int j = 0; j < 3; ++j) {
+        G[0 * 3 + j] = -(Dminv[0 * 3 + j] + Dminv[1 * 3 + j] + Dminv[2 * 3 + j]);
+        for (int a = 1; a < 4; ++a) G[a * 3 + j] = Dminv[(a - 1) * 3 + j];
+    }
+    for (int r = 0; r < 9 * 12; ++r) B[r] = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int a = 0; a < 4; ++a)
+                B[(i * 3 + j) * 12 + (a * 3 + i)] = G[a * 3 + j];
+}
+
+/* One SNH tet: E = V psi(F), g = V B^T vec(P), H = V B^T (d2psi/dF2) B.
+ * xe = 4 vertices x 3 coordinates. g or H may be NULL. */
+void orc_snh_element(const double* xe, const double* Dminv, double V,
+                     double mu, double lam, double* E, double* g, double* H)
+{
+    double B[9 * 12];
+    tet_B(Dminv, B);
+    double F[9];
+    for (int r = 0; r < 9; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < 12; ++c) s += B[r * 12 + c] * xe[c];
+        F[r] = s;
+    }
+    double psi, P[9], A[81];
+    snh_density(F, mu, lam, &psi, (g || H) ? P : NULL, H ? A : NULL);
+    *E = V * psi;
+    if (g)
+        for (int c = 0; c < 12; ++c) {
+            double s = 0.0;
+            for (int r = 0; r < 9; ++r) s += B[r * 12 + c] * P[r];
+            g[c] = V * s;
+        }
+    if (H) {
+        double AB[9 * 12];
+        for (int r = 0; r < 9; ++r)
+            for (int c = 0; c < 12; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 9; ++k) s += A[r * 9 + k] * B[k * 12 + c];
+                AB[r * 12 + c] = s;
+            }
+        for (int r = 0; r < 12; ++r)
+            for (int c = 0; c < 12; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 9; ++k) s += B[k * 12 + r] * AB[k * 12 + c];
+                H[r * 12 + c] = V * s;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Quadratic hinge bending (§6.3, Eq. 13)                               */
+/* ------------------------------------------------------------------ */
+
+/* READING: Q_e = c (q q^T kron I3) with q the cotangent weights of the flat
+ * rest hinge and c = 3/(A0+A1) (Bergou et al., the cited construction);
+ * the library takes q and c as per-stencil inputs. The oracle forms the
+ * 12x12 Q and applies E = k/2 x^T Q x, g = k Q x, H = k Q literally. */
+void orc_hinge_element(const double* xe, const double* q, double c, double kb,
+                       double* E, double* g, double* H)
+{
+    double Q[144];
+    for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < 3; ++i)
+            for (int b = 0; b < 4; ++b)
+                for (int j = 0; j < 3; ++j)
+                    Q[(a * 3 + i) * 12 + (b * 3 + j)] = (i == j) ? c * q[a] * q[b] : 0.0;
+    double Qx[12];
+    for (int r = 0; r < 12; ++r) {
+        double s = 0.0;
+        for (int k = 0; k < 12; ++k) s += Q[r * 12 + k] * xe[k];
+        Qx[r] = s;
+    }
+    double xQx = 0.0;
+    for (int r = 0; r < 12; ++r) xQx += xe[r] * Qx[r];
+    *E = 0.5 * kb * xQx;
+    if (g) for (int r = 0; r < 12; ++r) g[r] = kb * Qx[r];
+    if (H) for (int r = 0; r < 144; ++r) H[r] = kb * Q[r];
+}
+
+/* ------------------------------------------------------------------ */
+/* Point-triangle barrier (§6.4, Eq. 15)                                */
+/* ------------------------------------------------------------------ */
+
+/* second-order forward-mode scalar: value, gradient and Hessian with
+ * respect to the 12 stencil coordinates (p, t0, t1, t2). */
+typedef struct { double v; double g[12]; double H[144]; } q2;
+
+static void q2_const(q2* r, double v) { memset(r, 0, sizeof(*r)); r->v = v; }
+static void q2_coord(q2* r, const double* xe, int node, int comp)
+{
+    q2_const(r, xe[3 * node + comp]);
+    r->g[3 * node + comp] = 1.0;
+}
+static void q2_add(q2* r, const q2* a, const q2* b, double sb)
+{
+    q2 t;
+    t.v = a->v + sb * b->v;
+    for (int i = 0; i < 12; ++i) t.g[i] = a->g[i] + sb * b->g[i];
+    for (int i = 0; i < 144; ++i) t.H[i] = a->H[i] + sb * b->H[i];
+    *r = t;
+}
+/* product rule */
+static void q2_mul(q2* r, const q2* a, const q2* b)
+{
+    q2 t;
+    t.v = a->v * b->v;
+    for (int i = 0; i < 12; ++i) t.g[i] = a->g[i] * b->v + a->v * b->g[i];
+    for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j)
+            t.H[i * 12 + j] = a->H[i * 12 + j] * b->v + a->v * b->H[i * 12 + j]
+                            + a->g[i] * b->g[j] + b->g[i] * a->g[j];
+    *r = t;
+}
+/* chain rule for a scalar function f with derivatives f0, f1, f2 */
+static void q2_apply(q2* r, const q2* a, double f0, double f1, double f2)
+{
+    q2 t;
+    t.v = f0;
+    for (int i = 0; i < 12; ++i) t.g[i] = f1 * a->g[i];
+    for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j)
+            t.H[i * 12 + j] = f1 * a->H[i * 12 + j] + f2 * a->g[i] * a->g[j];
+    *r = t;
+}
+static void q2_vec_sub(q2 r[3], const double* xe, int na, int nb)
+{
+    for (int k = 0; k < 3; ++k) {
+        q2 a, b;
+        q2_coord(&a, xe, na, k);
+        q2_coord(&b, xe, nb, k);
+        q2_add(&r[k], &a, &b, -1.0);
+    }
+}
+static void q2_cross(q2 r[3], const q2 u[3], const q2 v[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        q2 s; q2_const(&s, 0.0);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                int e = levi(k, i, j);
+                if (!e) continue;
+                q2 t; q2_mul(&t, &u[i], &v[j]);
+                q2_add(&s, &s, &t, (double)e);
+            }
+        r[k] = s;
+    }
+}
+static void q2_dot(q2* r, const q2 u[3], const q2 v[3])
+{
+    q2 s; q2_const(&s, 0.0);
+    for (int k = 0; k < 3; ++k) {
+        q2 t; q2_mul(&t, &u[k], &v[k]);
+        q2_add(&s, &s, &t, 1.0);
+    }
+    *r = s;
+}
+
+/* Closest-feature classification of point p against triangle (a,b,c) by
+ * the textbook Voronoi-region tests (vertex regions first, then edges,
+ * then the face), so that ties on a region boundary go to the
+ * lower-dimensional feature. Returns 0,1,2 = vertex a,b,c; 3 = edge ab,
+ * 4 = edge bc, 5 = edge ca; 6 = face. READING: the paper names the IPC
+ * distance kernels without a formula (§6.4). */
+int orc_pt_region(const double* xe)
+{
+    const double *p = xe, *a = xe + 3, *b = xe + 6, *c = xe + 9;
+    double ab[3], ac[3], ap[3], bp[3], cp[3];
+    for (int k = 0; k < 3; ++k) {
+        ab[k] = b[k] - a[k]; ac[k] = c[k] - a[k];
+        ap[k] = p[k] - a[k]; bp[k] = p[k] - b[k]; cp[k] = p[k] - c[k];
+    }
+#define DOT(u, v) ((u)[0] * (v)[0] + (u)[1] * (v)[1] + (u)[2] * (v)[2])
+    double d1 = DOT(ab, ap), d2 = DOT(ac, ap);
+    if (d1 <= 0.0 && d2 <= 0.0) return 0;
+    double d3 = DOT(ab, bp), d4 = DOT(ac, bp);
+    if (d3 >= 0.0 && d4 <= d3) return 1;
+    double vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) return 3;
+    double d5 = DOT(ab, cp), d6 = DOT(ac, cp);
+    if (d6 >= 0.0 && d5 <= d6) return 2;
+    double vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) return 5;
+    double va = d3 * d6 - d5 * d4;
+    if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) return 4;
+    return 6;
+#undef DOT
+}
+
+/* Squared distance s = |r|^2 / w of the active feature, with gradient and
+ * Hessian, through the quotient s w = sum r_k^2 differentiated twice:
+ * vertex v: r = p - v, w = 1; edge (u,v): r = (p-u) x (v-u), w = |v-u|^2;
+ * face: r = (p-a).((b-a)x(c-a)), w = |(b-a)x(c-a)|^2. */
+static void pt_sqdist(const double* xe, int region, q2* s)
+{
+    q2 num, w;
+    if (region <= 2) {
+        q2 r[3];
+        q2_vec_sub(r, xe, 0, 1 + region);
+        q2_dot(&num, r, r);
+        q2_const(&w, 1.0);
+    } else if (region <= 5) {
+        int u = (region == 3) ? 1 : (region == 4 ? 2 : 3);
+        int v = (region == 3) ? 2 : (region == 4 ? 3 : 1);
+        q2 e[3], d[3], r[3];
+        q2_vec_sub(e, xe, 0, u);
+        q2_vec_sub(d, xe, v, u);
+        q2_cross(r, e, d);
+        q2_dot(&num, r, r);
+        q2_dot(&w, d, d);
+    } else {
+        q2 e[3], e1[3], e2[3], N[3], u;
+        q2_vec_sub(e, xe, 0, 1);
+        q2_vec_sub(e1, xe, 2, 1);
+        q2_vec_sub(e2, xe, 3, 1);
+        q2_cross(N, e1, e2);
+        q2_dot(&u, e, N);
+        q2_mul(&num, &u, &u);
+        q2_dot(&w, N, N);
+    }
+    /* s = num / w: s w = num  =>  grad s = (grad num - s grad w)/w,
+     * hess s = (hess num - grad s grad w^T - grad w grad s^T - s hess w)/w */
+    q2 t;
+    t.v = num.v / w.v;
+    for (int i = 0; i < 12; ++i) t.g[i] = (num.g[i] - t.v * w.g[i]) / w.v;
+    for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j)
+            t.H[i * 12 + j] = (num.H[i * 12 + j] - t.g[i] * w.g[j] - w.g[i] * t.g[j]
+                               - t.v * w.H[i * 12 + j]) / w.v;
+    *s = t;
+}
+
+/* Unsigned point-triangle distance. */
+double orc_pt_distance(const double* xe)
+{
+    q2 s;
+    pt_sqdist(xe, orc_pt_region(xe), &s);
+    return sqrt(s.v);
+}
+
+/* b(d) = -kappa (d-dhat)^2 ln(d/dhat) and its first two derivatives. */
+void orc_barrier_1d(double d, double dhat, double kappa, double* b, double* b1, double* b2)
+{
+    double r = d - dhat, L = log(d / dhat);
+    *b = -kappa * r * r * L;
+    *b1 = -kappa * (2.0 * r * L + r * r / d);
+    *b2 = -kappa * (2.0 * L + 4.0 * r / d - r * r / (d * d));
+}
+
+/* Barrier element: returns 1 when active (0 < d < dhat), 0 when inactive
+ * (E, g, H zero: the element contributes nothing, Eq. 9), -1 for d <= 0
+ * (an intersecting state the barrier does not admit). */
+int orc_barrier_element(const double* xe, double dhat, double kappa,
+                        double* E, double* g, double* H)
+{
+    q2 s;
+    int region = orc_pt_region(xe);
+    pt_sqdist(xe, region, &s);
+    *E = 0.0;
+    if (g) memset(g, 0, 12 * sizeof(double));
+    if (H) memset(H, 0, 144 * sizeof(double));
+    if (!(s.v > 0.0)) return -1;
+    double d0 = sqrt(s.v);
+    if (!(d0 < dhat)) return 0;
+    /* d = sqrt(s) */
+    q2 d;
+    q2_apply(&d, &s, d0, 0.5 / d0, -0.25 / (s.v * d0));
+    double b, b1, b2;
+    orc_barrier_1d(d0, dhat, kappa, &b, &b1, &b2);
+    q2 e;
+    q2_apply(&e, &d, b, b1, b2);
+    *E = e.v;
+    if (g) memcpy(g, e.g, sizeof(e.g));
+    if (H) memcpy(H, e.H, sizeof(e.H));
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Projection to PSD (§5.2; Algorithm 1 ProjectToPD)                    */
+/* ------------------------------------------------------------------ */
+
+/* Cyclic Jacobi (textbook symmetric Schur rotations) until the
+ * off-diagonal norm is <= 1e-15 ||A||_F (at most 50 sweeps), then
+ * A <- sum_i max(lambda_i, 0) v_i v_i^T. READING: the paper says
+ * "positive semi-definiteness" (§5.2) and "ProjectToPD" (Algorithm 1);
+ * clamping at 0 is taken. Returns the sweeps used or -1 if the sweep limit
+ * was reached. n <= 12. */
+int orc_clamp_psd(int n, double* A)
+{
+    double V[144], W[144];
+    double fro = 0.0;
+    for (int i = 0; i < n * n; ++i) fro += A[i] * A[i];
+    fro = sqrt(fro);
+    if (fro == 0.0) return 0;
+    for (int i = 0; i < n * n; ++i) W[i] = A[i];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+    int sweep, ok = 0;
+    for (sweep = 0; sweep < 50; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                if (i != j) off += W[i * n + j] * W[i * n + j];
+        if (sqrt(off) <= 1e-15 * fro) { ok = 1; break; }
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = W[p * n + q];
+                if (apq == 0.0) continue;
+                double tau = (W[q * n + q] - W[p * n + p]) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = W[k * n + p], akq = W[k * n + q];
+                    W[k * n + p] = c * akp - s * akq;
+                    W[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = W[p * n + k], aqk = W[q * n + k];
+                    W[p * n + k] = c * apk - s * aqk;
+                    W[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) {
+                double lk = W[k * n + k];
+                if (lk > 0.0) s += lk * V[i * n + k] * V[j * n + k];
+            }
+            A[i * n + j] = s;
+        }
+    return ok ? sweep : -1;
+}
+
+/* eigenvalues (ascending order not guaranteed) by the same Jacobi
+ * iteration, for tests */
+int orc_sym_eigvals(int n, const double* A, double* lam)
+{
+    double W[144], fro = 0.0;
+    for (int i = 0; i < n * n; ++i) { W[i] = A[i]; fro += A[i] * A[i]; }
+    fro = sqrt(fro);
+    int sweep;
+    for (sweep = 0; sweep < 50 && fro > 0.0; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                if (i != j) off += W[i * n + j] * W[i * n + j];
+        if (sqrt(off) <= 1e-15 * fro) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = W[p * n + q];
+                if (apq == 0.0) continue;
+                double tau = (W[q * n + q] - W[p * n + p]) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = W[k * n + p], akq = W[k * n + q];
+                    W[k * n + p] = c * akp - s * akq;
+                    W[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = W[p * n + k], aqk = W[q * n + k];
+                    W[p * n + k] = c * apk - s * aqk;
+                    W[q * n + k] = s * apk + c * aqk;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i) lam[i] = W[i * n + i];
+    return sweep;
+}
+
+/* ------------------------------------------------------------------ */
+/* Batched element evaluation (the parallel element loop of Alg. 1)     */
+/* ------------------------------------------------------------------ */
+
+static void gather4(const double* x, const int* t, double xe[12])
+{
+    for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < 3; ++i) xe[3 * a + i] = x[3 * t[a] + i];
+}
+
+/* level: 0 = E, 1 = E+g, 2 = E+g+H. H_e is 144 per element (row-major). */
+void orc_snh_batch(int T, const double* x, const int* tets, const double* Dminv,
+                   const double* V, const double* mu, const double* lam,
+                   int level, int project, double* E_e, double* g_e, double* H_e)
+{
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < T; ++e) {
+        double xe[12];
+        gather4(x, tets + 4 * e, xe);
+        orc_snh_element(xe, Dminv + 9 * e, V[e], mu[e], lam[e], E_e + e,
+                        level >= 1 ? g_e + 12 * (size_t)e : NULL,
+                        level >= 2 ? H_e + 144 * (size_t)e : NULL);
+        if (level >= 2 && project) orc_clamp_psd(12, H_e + 144 * (size_t)e);
+    }
+}
+
+void orc_hinge_batch(int S, const double* x, const int* st, const double* q,
+                     const double* c, double kb, int level,
+                     double* E_e, double* g_e, double* H_e)
+{
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < S; ++e) {
+        double xe[12];
+        gather4(x, st + 4 * e, xe);
+        orc_hinge_element(xe, q + 4 * e, c[e], kb, E_e + e,
+                          level >= 1 ? g_e + 12 * (size_t)e : NULL,
+                          level >= 2 ? H_e + 144 * (size_t)e : NULL);
+    }
+}
+
+/* returns the number of pairs with d <= 0 (invalid state) */
+int orc_barrier_batch(int P, const double* x, const int* pairs, double dhat,
+                      double kappa, int level, int project,
+                      double* E_e, double* g_e, double* H_e, int* active)
+{
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int e = 0; e < P; ++e) {
+        double xe[12], gl[12], Hl[144];
+        gather4(x, pairs + 4 * e, xe);
+        int st = orc_barrier_element(xe, dhat, kappa, E_e + e, gl, Hl);
+        if (st < 0) bad++;
+        if (active) active[e] = st;
+        if (level >= 1) memcpy(g_e + 12 * (size_t)e, gl, sizeof(gl));
+        if (level >= 2) {
+            if (project && st == 1) orc_clamp_psd(12, Hl);
+            memcpy(H_e + 144 * (size_t)e, Hl, sizeof(Hl));
+        }
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* 3x3 block CRS pattern and slot maps (§5.3)                           */
+/* ------------------------------------------------------------------ */
+
+static int cmp_int(const void* a, const void* b)
+{
+    int x = *(const int*)a, y = *(const int*)b;
+    return (x > y) - (x < y);
+}
+
+/* Pattern = union over all stencils of their node pairs, plus the
+ * diagonal of every node; full storage, columns ascending in each row.
+ * Call with col == NULL to get row_ptr and the block count, then again
+ * with col sized to that count. READING: full (both triangles) storage,
+ * int32 indices. */
+long long orc_bsr_pattern(int N, int nst, const int* conn, int* row_ptr, int* col)
+{
+    int* cnt = (int*)calloc((size_t)N, sizeof(int));
+    for (int e = 0; e < nst; ++e)
+        for (int a = 0; a < 4; ++a) cnt[conn[4 * e + a]] += 4;
+    size_t* off = (size_t*)malloc(((size_t)N + 1) * sizeof(size_t));
+    off[0] = 0;
+    for (int n = 0; n < N; ++n) off[n + 1] = off[n] + (size_t)cnt[n] + 1;
+    int* buf = (int*)malloc(off[N] * sizeof(int));
+    int* fill = (int*)calloc((size_t)N, sizeof(int));
+    for (int n = 0; n < N; ++n) buf[off[n] + fill[n]++] = n;
+    for (int e = 0; e < nst; ++e)
+        for (int a = 0; a < 4; ++a) {
+            int r = conn[4 * e + a];
+            for (int b = 0; b < 4; ++b) buf[off[r] + fill[r]++] = conn[4 * e + b];
+        }
+    long long nnz = 0;
+    row_ptr[0] = 0;
+    for (int n = 0; n < N; ++n) {
+        int* row = buf + off[n];
+        int len = fill[n];
+        qsort(row, (size_t)len, sizeof(int), cmp_int);
+        int u = 0;
+        for (int k = 0; k < len; ++k)
+            if (k == 0 || row[k] != row[k - 1]) {
+                if (col) col[nnz + u] = row[k];
+                u++;
+            }
+        nnz += u;
+        row_ptr[n + 1] = (int)nnz;
+    }
+    free(cnt); free(off); free(buf); free(fill);
+    return nnz;
+}
+
+static int find_slot(const int* row_ptr, const int* col, int r, int c)
+{
+    int lo = row_ptr[r], hi = row_ptr[r + 1] - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        if (col[mid] == c) return mid;
+        if (col[mid] < c) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* slots[16 e + 4 a + b] = block index of (node a, node b) of stencil e;
+ * diag_slot[n] = block index of (n, n). */
+void orc_bsr_slots(int N, const int* row_ptr, const int* col, int nst,
+                   const int* conn, int* slots, int* diag_slot)
+{
+    for (int e = 0; e < nst; ++e)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+                slots[16 * (size_t)e + 4 * a + b] =
+                    find_slot(row_ptr, col, conn[4 * e + a], conn[4 * e + b]);
+    for (int n = 0; n < N; ++n) diag_slot[n] = find_slot(row_ptr, col, n, n);
+}
+
+/* ------------------------------------------------------------------ */
+/* Assembly (Algorithm 1; gradient sum R_e^T g_e)                       */
+/* ------------------------------------------------------------------ */
+
+/* Adds element blocks in stencil order (vals and grad must be zeroed by
+ * the caller or hold earlier contributions). H_e may be NULL. */
+void orc_assemble_elements(int nst, const int* conn, const int* slots,
+                           const double* g_e, const double* H_e,
+                           double* grad, double* vals)
+{
+    for (int e = 0; e < nst; ++e)
+        for (int a = 0; a < 4; ++a) {
+            int na = conn[4 * e + a];
+            if (grad)
+                for (int i = 0; i < 3; ++i) grad[3 * na + i] += g_e[12 * (size_t)e + 3 * a + i];
+            if (H_e && vals)
+                for (int b = 0; b < 4; ++b) {
+                    double* blk = vals + 9 * (size_t)slots[16 * (size_t)e + 4 * a + b];
+                    const double* He = H_e + 144 * (size_t)e;
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j)
+                            blk[3 * i + j] += He[(3 * a + i) * 12 + (3 * b + j)];
+                }
+        }
+}
+
+/* Inertia of the incremental potential (Eq. 2): per node
+ * m/(2 dt^2) |x - xt|^2, gradient m/dt^2 (x - xt), diagonal m/dt^2 I. */
+double orc_inertia(int N, const double* m, double dt, const double* x,
+                   const double* xt, const int* diag_slot, double* grad, double* vals)
+{
+    double E = 0.0, inv = 1.0 / (dt * dt);
+    for (int n = 0; n < N; ++n) {
+        double r2 = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            double r = x[3 * n + i] - xt[3 * n + i];
+            r2 += r * r;
+            if (grad) grad[3 * n + i] += m[n] * inv * r;
+        }
+        E += 0.5 * m[n] * inv * r2;
+        if (vals && diag_slot)
+            for (int i = 0; i < 3; ++i) vals[9 * (size_t)diag_slot[n] + 4 * i] += m[n] * inv;
+    }
+    return E;
+}
+
+/* ------------------------------------------------------------------ */
+/* Block-Jacobi PCG (§7.2)                                              */
+/* ------------------------------------------------------------------ */
+
+/* y = A x with pinned rows/columns eliminated: pinned DOFs map to
+ * themselves (identity), free rows only see free columns. READING: the
+ * paper leaves Dirichlet handling open; DOF elimination by mask is used. */
+static void spmv_masked(int N, const int* rp, const int* col, const double* vals,
+                        const unsigned char* pinned, const double* x, double* y)
+{
+    for (int r = 0; r < N; ++r) {
+        if (pinned && pinned[r]) {
+            for (int i = 0; i < 3; ++i) y[3 * r + i] = x[3 * r + i];
+            continue;
+        }
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int k = rp[r]; k < rp[r + 1]; ++k) {
+            int c = col[k];
+            if (pinned && pinned[c]) continue;
+            const double* B = vals + 9 * (size_t)k;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) acc[i] += B[3 * i + j] * x[3 * c + j];
+        }
+        for (int i = 0; i < 3; ++i) y[3 * r + i] = acc[i];
+    }
+}
+
+static double dotv(size_t n, const double* a, const double* b)
+{
+    double s = 0.0;
+    for (size_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Preconditioned CG on the masked system, x0 = 0, stop when
+ * ||r||_2 <= tol ||b||_2. READING: a fixed tolerance instead of the
+ * paper's forcing sequence. Returns 0, or ORC_ENOTCONV after maxit. */
+int orc_pcg(int N, const int* rp, const int* col, const double* vals,
+            const int* diag_slot, const unsigned char* pinned, const double* b,
+            double tol, int maxit, double* x, int* iters, double* relres)
+{
+    size_t n3 = 3 * (size_t)N;
+    double* Minv = (double*)malloc(9 * (size_t)N * sizeof(double));
+    double *r = (double*)malloc(n3 * sizeof(double)), *z = (double*)malloc(n3 * sizeof(double));
+    double *p = (double*)malloc(n3 * sizeof(double)), *q = (double*)malloc(n3 * sizeof(double));
+    for (int n = 0; n < N; ++n) {
+        if (pinned && pinned[n]) {
+            for (int k = 0; k < 9; ++k) Minv[9 * n + k] = (k % 4 == 0) ? 1.0 : 0.0;
+        } else {
+            inv3(vals + 9 * (size_t)diag_slot[n], Minv + 9 * (size_t)n, NULL);
+        }
+    }
+    for (size_t i = 0; i < n3; ++i) { x[i] = 0.0; r[i] = b[i]; }
+    double bn = sqrt(dotv(n3, b, b));
+    int it = 0, status = 0;
+    double rn = bn;
+    if (bn == 0.0) goto done;
+#define APPLY_M(dst, src) \
+    for (int nn = 0; nn < N; ++nn) \
+        for (int i = 0; i < 3; ++i) { \
+            double s_ = 0.0; \
+            for (int j = 0; j < 3; ++j) s_ += Minv[9 * (size_t)nn + 3 * i + j] * (src)[3 * nn + j]; \
+            (dst)[3 * nn + i] = s_; \
+        }
+    APPLY_M(z, r);
+    for (size_t i = 0; i < n3; ++i) p[i] = z[i];
+    double rz = dotv(n3, r, z);
+    status = ORC_ENOTCONV;
+    for (it = 0; it < maxit;) {
+        spmv_masked(N, rp, col, vals, pinned, p, q);
+        double alpha = rz / dotv(n3, p, q);
+        for (size_t i = 0; i < n3; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        ++it;
+        rn = sqrt(dotv(n3, r, r));
+        if (rn <= tol * bn) { status = 0; break; }
+        APPLY_M(z, r);
+        double rz2 = dotv(n3, r, z);
+        double beta = rz2 / rz;
+        rz = rz2;
+        for (size_t i = 0; i < n3; ++i) p[i] = z[i] + beta * p[i];
+    }
+#undef APPLY_M
+done:
+    if (iters) *iters = it;
+    if (relres) *relres = (bn > 0.0) ? rn / bn : 0.0;
+    free(Minv); free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Scene evaluation and the backward-Euler Newton step (Eqs. 2-3)       */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int N;
+    const double* mass;
+    int n_snh;
+    const int* snh_tets;
+    const double* snh_Dminv;
+    const double* snh_V;
+    const double* snh_mu;
+    const double* snh_lam;
+    int n_hinge;
+    const int* hinge;
+    const double* hinge_q;
+    const double* hinge_c;
+    double kb;
+    int n_pt;
+    const int* pt;
+    double dhat;
+    double kappa;
+    const unsigned char* pinned;
+    /* pattern over the concatenated stencils (snh, hinge, pt) */
+    const int* row_ptr;
+    const int* col;
+    const int* slots;
+    const int* diag_slot;
+    long long nnzb;
+} orc_scene;
+
+/* Full evaluation of E_BE = inertia + sum of element energies at x
+ * (Eq. 2 with Eq. 5). level as above. Returns the number of barrier pairs
+ * in an invalid (d <= 0) state. grad/vals are overwritten. */
+int orc_scene_eval(const orc_scene* s, const double* x, const double* xt, double dt,
+                   int level, int project, double* E_out, double* grad, double* vals)
+{
+    int bad = 0;
+    size_t n3 = 3 * (size_t)s->N;
+    if (level >= 1) memset(grad, 0, n3 * sizeof(double));
+    if (level >= 2) memset(vals, 0, 9 * (size_t)s->nnzb * sizeof(double));
+    double E = 0.0;
+    size_t base = 0;
+    int counts[3] = {s->n_snh, s->n_hinge, s->n_pt};
+    for (int kind = 0; kind < 3; ++kind) {
+        int n = counts[kind];
+        if (n == 0) continue;
+        double* Ee = (double*)malloc((size_t)n * sizeof(double));
+        double* ge = level >= 1 ? (double*)malloc(12 * (size_t)n * sizeof(double)) : NULL;
+        double* He = level >= 2 ? (double*)malloc(144 * (size_t)n * sizeof(double)) : NULL;
+        const int* conn;
+        if (kind == 0) {
+            conn = s->snh_tets;
+            orc_snh_batch(n, x, conn, s->snh_Dminv, s->snh_V, s->snh_mu, s->snh_lam,
+                          level, project, Ee, ge, He);
+        } else if (kind == 1) {
+            conn = s->hinge;
+            orc_hinge_batch(n, x, conn, s->hinge_q, s->hinge_c, s->kb, level, Ee, ge, He);
+        } else {
+            conn = s->pt;
+            bad += orc_barrier_batch(n, x, conn, s->dhat, s->kappa, level, project,
+                                     Ee, ge, He, NULL);
+        }
+        for (int e = 0; e < n; ++e) E += Ee[e];
+        if (level >= 1)
+            orc_assemble_elements(n, conn, s->slots + 16 * base, ge, He, grad,
+                                  level >= 2 ? vals : NULL);
+        free(Ee); free(ge); free(He);
+        base += (size_t)n;
+    }
+    if (xt && s->mass)
+        E += orc_inertia(s->N, s->mass, dt, x, xt, s->diag_slot,
+                         level >= 1 ? grad : NULL, level >= 2 ? vals : NULL);
+    *E_out = E;
+    return bad;
+}
+
+typedef struct {
+    double newton_tol;
+    double pcg_tol;
+    int max_newton;
+    int max_pcg;
+    int max_halvings;
+    double armijo_c;
+    int project;
+} orc_newton_opts;
+
+typedef struct {
+    int status;
+    int newton_iters;
+    int pcg_iters_total;
+    double g0_norm;
+    double g_norm;
+    double E_final;
+} orc_newton_report;
+
+static double free_norm(int N, const unsigned char* pinned, const double* g)
+{
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) {
+        if (pinned && pinned[n]) continue;
+        for (int i = 0; i < 3; ++i) s += g[3 * n + i] * g[3 * n + i];
+    }
+    return sqrt(s);
+}
+
+/* One backward-Euler step (Eqs. 2-3): xt = x + dt v + dt^2 g_ext;
+ * Newton from x0 = x_t (READING) with PCG directions and backtracking
+ * Armijo line search; stop when ||g_free|| <= tol max(||g_free(x0)||,
+ * 1e-30) (READING); then v = (x - x_t)/dt. x and v are updated in place. */
+int orc_newton_step(const orc_scene* s, double dt, const double gravity[3],
+                    const orc_newton_opts* o, double* x, double* v,
+                    orc_newton_report* rep)
+{
+    int N = s->N;
+    size_t n3 = 3 * (size_t)N;
+    double *xt = (double*)malloc(n3 * sizeof(double)), *x0 = (double*)malloc(n3 * sizeof(double));
+    double *g = (double*)malloc(n3 * sizeof(double)), *gtr = (double*)malloc(n3 * sizeof(double));
+    double *dx = (double*)malloc(n3 * sizeof(double)), *b = (double*)malloc(n3 * sizeof(double));
+    double *xtr = (double*)malloc(n3 * sizeof(double));
+    double* vals = (double*)malloc(9 * (size_t)s->nnzb * sizeof(double));
+    for (int n = 0; n < N; ++n)
+        for (int i = 0; i < 3; ++i) {
+            x0[3 * n + i] = x[3 * n + i];
+            xt[3 * n + i] = x[3 * n + i] + dt * v[3 * n + i] + dt * dt * gravity[i];
+        }
+    int status = ORC_ENOTCONV, it = 0, pcg_total = 0;
+    double E, gn0 = 0.0, gn = 0.0;
+    for (it = 0; it <= o->max_newton; ++it) {
+        orc_scene_eval(s, x, xt, dt, 2, o->project, &E, g, vals);
+        gn = free_norm(N, s->pinned, g);
+        if (it == 0) gn0 = gn;
+        double ref = gn0 > 1e-30 ? gn0 : 1e-30;
+        if (gn <= o->newton_tol * ref) { status = 0; break; }
+        if (it == o->max_newton) break;
+        for (int n = 0; n < N; ++n)
+            for (int i = 0; i < 3; ++i)
+                b[3 * n + i] = (s->pinned && s->pinned[n]) ? 0.0 : -g[3 * n + i];
+        int pit = 0;
+        int pst = orc_pcg(N, s->row_ptr, s->col, vals, s->diag_slot, s->pinned, b,
+                          o->pcg_tol, o->max_pcg, dx, &pit, NULL);
+        pcg_total += pit;
+        if (pst != 0) { status = ORC_ENOTCONV; break; }
+        double gdx = dotv(n3, g, dx);
+        double alpha = 1.0;
+        int accepted = 0;
+        for (int h = 0; h <= o->max_halvings; ++h) {
+            for (size_t k = 0; k < n3; ++k) xtr[k] = x[k] + alpha * dx[k];
+            double Et;
+            int bad = orc_scene_eval(s, xtr, xt, dt, 0, 0, &Et, NULL, NULL);
+            if (bad == 0 && isfinite(Et) && Et <= E + o->armijo_c * alpha * gdx) {
+                accepted = 1;
+                break;
+            }
+            alpha *= 0.5;
+        }
+        if (!accepted) { status = ORC_ELINESEARCH; break; }
+        memcpy(x, xtr, n3 * sizeof(double));
+    }
+    for (size_t k = 0; k < n3; ++k) v[k] = (x[k] - x0[k]) / dt;
+    if (rep) {
+        rep->status = status;
+        rep->newton_iters = it;
+        rep->pcg_iters_total = pcg_total;
+        rep->g0_norm = gn0;
+        rep->g_norm = gn;
+        rep->E_final = E;
+    }
+    free(xt); free(x0); free(g); free(gtr); free(dx); free(b); free(xtr); free(vals);
+    return status;
+}
