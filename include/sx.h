@@ -1,0 +1,273 @@
+/*
+ * sx.h -- C ABI of libsx, a GB300 (sm_103a) implementation of the hot path
+ * of the energy-based optimization time integrator of "SymX:
+ * Energy-based Simulation from Symbolic Expressions" (arXiv 2303.02156).
+ *
+ * The calls follow the paper's statement of the problem: register degrees
+ * of freedom (§5.1, Fig. 2 "add_dof_array"), add energies over element
+ * lists with per-element parameters (§3 Eq. 5; §5.1 "add_energy"),
+ * evaluate the global energy, gradient and Hessian at three levels
+ * (§5.2 "Data-Symbol Mapping": E for the line search, E+grad for the
+ * convergence test, E+grad+Hessian for the Newton system), with optional
+ * per-element projection to positive semi-definiteness (§5.2, Algorithm 1),
+ * assembled into a 3x3 block CRS matrix (§5.3, Eq. 11), and take a
+ * backward-Euler step by Newton's method (§3, Eqs. 2-3) with a 3x3
+ * block-Jacobi PCG linear solve (§7.2).
+ *
+ * Conventions (all calls):
+ *  - Every call returns an int status: SX_OK (0) or a negative SX_E* code;
+ *    sx_last_error(ctx) gives a one-line description of the last failure.
+ *    No C++ exception crosses this boundary.
+ *  - Input arrays may be host or device pointers (any address CUDA's
+ *    unified addressing resolves, pinned or pageable host memory included);
+ *    outputs of sx_eval_elements and the sx_get_* views are device memory.
+ *  - Inputs are copied into library-owned device memory; the library never
+ *    keeps a caller pointer past the call.
+ *  - Pointers returned by sx_get_* are views into library memory, valid
+ *    until the next call that mutates that scene.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that
+ *    return a host-side value (energy, report, footprint) synchronize that
+ *    stream; the others are asynchronous unless stated.
+ *  - Node arrays are AoS: node n's coordinates at [3n, 3n+2]. Stencils are
+ *    int32[n][4]. Per-element parameters are one value per element.
+ *  - A context is not thread-safe; use one context per host thread.
+ *  - All scenes of a context live on the device that was current at
+ *    sx_create.
+ */
+#ifndef SX_H
+#define SX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SX_OK 0
+#define SX_EINVAL (-1)        /* bad argument */
+#define SX_ENOMEM (-2)        /* device allocation failed */
+#define SX_ECUDA (-3)         /* a CUDA runtime call failed */
+#define SX_ENAN (-4)          /* non-finite energy, gradient or Hessian */
+#define SX_ENOTCONV (-5)      /* PCG or Newton iteration limit reached */
+#define SX_ESTATE (-6)        /* state outside the energy's domain (barrier d <= 0) */
+#define SX_EDEGENERATE (-7)   /* a rest element has non-positive volume */
+#define SX_EBUDGET (-8)       /* request can never fit the server's memory budget */
+#define SX_ELINESEARCH (-9)   /* line search found no decrease */
+#define SX_EORDER (-10)       /* call out of order (e.g. eval before finalize) */
+
+/* ---- evaluation levels (§5.2: three global evaluation functions) ------ */
+#define SX_E 0      /* energy */
+#define SX_EG 1     /* energy + gradient */
+#define SX_EGH 2    /* energy + gradient + Hessian */
+
+/* ---- element-math precision ------------------------------------------ */
+#define SX_FP64 0   /* all arithmetic in double */
+#define SX_FP32 1   /* element E/g/H and SpMV in float; the PSD projection,
+                       gradient assembly, energy sums, residual norms and PCG
+                       dot products stay in double */
+
+/* ---- energy kinds ----------------------------------------------------- */
+#define SX_KIND_SNH_TET4 0
+#define SX_KIND_HINGE4 1
+#define SX_KIND_PT_BARRIER 2
+
+typedef struct sx_ctx sx_ctx;
+typedef struct sx_scene sx_scene;
+typedef struct sx_server sx_server;
+
+typedef struct {
+    int device;          /* CUDA device ordinal; -1 = the current device */
+    int reserved[7];
+} sx_options;
+
+/* Create / destroy a context. */
+int sx_create(sx_ctx** ctx, const sx_options* opt);
+int sx_destroy(sx_ctx* ctx);
+const char* sx_last_error(sx_ctx* ctx);
+/* Library build string (arch, version); never NULL. */
+const char* sx_version(void);
+
+/* ---- scenes and DOF registration (§5.1 Fig. 2 "add_dof_array";
+ *      §5.3 concatenated DOF sets, Eq. 11) ---------------------------------
+ * A scene holds one global DOF vector of n_nodes 3D nodes; several DOF
+ * sets (a tet mesh, a shell, free points) are registered by stacking them
+ * into one node range, as §5.3 concatenates DOF sets. X_rest: rest
+ * positions, n_nodes x 3 doubles, node stride `stride` doubles (>= 3);
+ * host or device. The deformed state starts at X_rest with zero velocity. */
+int sx_scene_create(sx_ctx* ctx, int64_t n_nodes, const double* X_rest,
+                    int64_t stride, void* stream, sx_scene** scene);
+int sx_scene_destroy(sx_scene* scene);
+
+/* Stable Neo-Hookean linear tets (§3.1 Eq. 7; App. B density). tets: n x 4
+ * node ids; young, poisson: per-element Young's modulus (Pa) and Poisson
+ * ratio. Rest precompute on the device: Dm = [X1-X0,
+ * X2-X0, X3-X0], Dm^-1, V = det(Dm)/6 > 0 (else SX_EDEGENERATE and the
+ * block is not added), lumped mass rho V / 4 per vertex, and the density's
+ * parameters mu' = 4 mu / 3, lambda' = lambda + 5 mu / 6 from the
+ * isotropic Lame pair (literal_params != 0: mu' = mu, lambda' = lambda).
+ * Synchronous. energy_id (may be NULL) receives the block's id. */
+int sx_add_snh_tet4(sx_scene* scene, const int32_t* tets, int64_t n,
+                    const double* young, const double* poisson, double density,
+                    int literal_params, void* stream, int* energy_id);
+
+/* Quadratic hinge bending E = k_b/2 x^T Q x (§6.3, Eq. 13) over 4-node
+ * stencils (e0, e1, o0, o1): shared edge then the two opposite vertices.
+ * Q = c (q q^T kron I3) with q (n x 4) the per-stencil weights and c (n)
+ * the per-stencil scale (for Bergou et al.'s form, cotangent
+ * weights and 3/(A0+A1)). Q is constant and PSD, so it is never projected.
+ * Synchronous. */
+int sx_add_hinge4(sx_scene* scene, const int32_t* stencils, int64_t n,
+                  const double* q, const double* c, double k_b, void* stream,
+                  int* energy_id);
+
+/* Point-triangle IPC barrier E = -kappa (d - dhat)^2 ln(d / dhat) of the
+ * unsigned distance d between point p and triangle (t0, t1, t2) (§6.4,
+ * Eq. 15); active only for 0 < d < dhat (conditional evaluation, §5.2
+ * Eq. 9), inactive pairs contribute zero and keep their (zero) blocks in
+ * the fixed pattern. pairs: n x 4 = (p, t0, t1, t2). A state with
+ * d <= 0 makes sx_eval return SX_ESTATE. Synchronous. */
+int sx_add_pt_barrier(sx_scene* scene, const int32_t* pairs, int64_t n,
+                      double dhat, double kappa, void* stream, int* energy_id);
+
+/* Add per-node mass (n_nodes doubles) to the lumped mass, e.g. for shell
+ * vertices or free points that belong to no tet. Synchronous. */
+int sx_add_node_mass(sx_scene* scene, const double* mass, void* stream);
+
+/* Pinned (Dirichlet) nodes: their DOFs are eliminated from the Newton
+ * system (identity rows) and never move. nodes: n node ids; replaces any
+ * earlier set. Synchronous. */
+int sx_set_pinned(sx_scene* scene, const int32_t* nodes, int64_t n, void* stream);
+
+/* Constant external acceleration (M^-1 f_ext of Eq. 2), host double[3]. */
+int sx_set_gravity(sx_scene* scene, const double g[3]);
+
+/* Build the fixed 3x3-block CRS pattern (union of all stencils' node pairs
+ * plus every diagonal; columns ascending; full storage), the per-stencil
+ * slot maps and the assembly lists (§5.3). Must follow the last add_* call
+ * and precede any evaluation. Synchronous. */
+int sx_finalize(sx_scene* scene, void* stream);
+
+/* ---- state ------------------------------------------------------------ */
+/* x, v: n_nodes x 3 doubles (either may be NULL). */
+int sx_set_state(sx_scene* scene, const double* x, const double* v, void* stream);
+int sx_get_state(sx_scene* scene, double* x, double* v, void* stream);
+
+/* Enable the inertia term of the incremental potential (Eq. 2):
+ * m/(2 dt^2) |x - x_tilde|^2 per node. x_tilde: n_nodes x 3; NULL
+ * disables the term. */
+int sx_set_inertia(sx_scene* scene, double dt, const double* x_tilde, void* stream);
+
+/* ---- evaluation (§5.2; Algorithm 1) -----------------------------------
+ * level: SX_E, SX_EG or SX_EGH. project != 0 projects every non-convex
+ * element Hessian (SNH, barrier) to PSD by clamping its eigenvalues at 0
+ * (FP64 always). precision: SX_FP64 or SX_FP32. E_out (host, may be NULL)
+ * receives the total energy; the assembled gradient (FP64) and BSR values
+ * stay on the device (sx_get_grad, sx_get_bsr). Synchronous when E_out is
+ * given. */
+int sx_eval(sx_scene* scene, int level, int project, int precision,
+            double* E_out, void* stream);
+
+/* The same for several scenes of one context in one fused launch sequence
+ * (persistent element kernel over a tile queue of all their stencils).
+ * E_out: host array of n (may be NULL). */
+int sx_eval_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, int level,
+                  int project, int precision, double* E_out, void* stream);
+
+/* Views of the assembled system after an SX_EG / SX_EGH evaluation.
+ * dtype: SX_FP64 (double vals) or SX_FP32 (float vals), the precision of
+ * the last SX_EGH evaluation. vals: nnzb blocks x 9, row-major 3x3. */
+int sx_get_bsr(sx_scene* scene, const int32_t** row_ptr, const int32_t** col,
+               const void** vals, int64_t* nnzb, int* dtype);
+int sx_get_grad(sx_scene* scene, const double** grad);
+/* Diagonal block index of every node (n_nodes int32). */
+int sx_get_diag_slots(sx_scene* scene, const int32_t** diag_slot);
+
+/* Copies of the same data into caller buffers (host or device): row_ptr
+ * (n_nodes+1), col (nnzb), vals (nnzb x 9 of the last SX_EGH precision;
+ * dtype receives it); grad (n_nodes x 3). Any pointer may be NULL.
+ * Asynchronous on `stream` for device or pinned destinations. */
+int sx_copy_bsr(sx_scene* scene, int32_t* row_ptr, int32_t* col, void* vals, int* dtype,
+                void* stream);
+int sx_copy_grad(sx_scene* scene, double* grad, void* stream);
+
+/* Scene shape: node count, BSR block count (0 before sx_finalize), total
+ * stencils and energy blocks. Any pointer may be NULL. */
+int sx_scene_info(sx_scene* scene, int64_t* n_nodes, int64_t* nnzb, int64_t* n_stencils,
+                  int* n_blocks);
+/* Kind (SX_KIND_*) and element count of energy block `energy_id`. */
+int sx_block_info(sx_scene* scene, int energy_id, int* kind, int64_t* n);
+/* Counters of the last evaluation: elements whose Hessian was projected
+ * (SX_EGH with project), barrier pairs with d <= 0, non-finite flag.
+ * Synchronizes `stream`. */
+int sx_eval_stats(sx_scene* scene, int* clamped, int* bad_state, int* nonfinite,
+                  void* stream);
+
+/* ---- element-level outputs with global indices (§5.3 last paragraph;
+ *      §5.2 low-level API) ---------------------------------------------
+ * For energy block `energy_id`, write per element E (n doubles), g
+ * (n x 12 doubles), H (n x 144 doubles, row-major 12x12, projected when
+ * project != 0) to device buffers, and the block's slot map (n x 16 int32:
+ * BSR block index of local node pair (a, b) at 4a + b). Any of E, g, H,
+ * slots may be NULL. */
+int sx_eval_elements(sx_scene* scene, int energy_id, int project, int precision,
+                     double* E, double* g, double* H, int32_t* slots, void* stream);
+
+/* ---- backward-Euler Newton step (§3 Eqs. 2-3; §7.2 solver) ------------ */
+typedef struct {
+    double newton_tol;   /* stop when ||g_free|| <= tol * ||g_free(x0)|| */
+    double pcg_tol;      /* stop when ||r|| <= tol * ||b|| */
+    int max_newton;      /* Newton iteration cap */
+    int max_pcg;         /* PCG iteration cap per solve */
+    int max_halvings;    /* line-search halvings cap */
+    int project;         /* project element Hessians to PSD */
+    int precision;       /* SX_FP64 or SX_FP32 */
+    double armijo_c;     /* sufficient-decrease constant */
+} sx_newton_opts;
+
+/* Defaults: 1e-8, 1e-10, 100, 10000, 30, 1, SX_FP64, 1e-4. */
+void sx_newton_opts_default(sx_newton_opts* o);
+
+typedef struct {
+    int status;          /* SX_OK or the failing code */
+    int newton_iters;
+    int pcg_iters;       /* total over the step */
+    int ls_halvings;     /* total over the step */
+    double g0_norm;      /* ||g_free(x0)|| */
+    double g_norm;       /* final ||g_free|| */
+    double energy;       /* final E_BE */
+    double ms;           /* wall time of the step */
+} sx_step_report;
+
+/* One step: x_tilde = x + dt v + dt^2 g_ext; x0 = x; Newton with PCG and
+ * Armijo backtracking; v = (x - x_t)/dt. Synchronous. */
+int sx_newton_step(sx_scene* scene, double dt, const sx_newton_opts* opts,
+                   sx_step_report* report, void* stream);
+
+/* One step for each of n scenes, batched: every kernel of the Newton and
+ * PCG loops covers all still-active scenes in one launch, with per-scene
+ * scalars (step sizes, convergence) kept on the device. reports: host
+ * array of n. */
+int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
+                         const sx_newton_opts* opts, sx_step_report* reports,
+                         void* stream);
+
+/* ---- footprint (for admission by memory) ------------------------------ */
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_tets;
+    int64_t n_hinges;
+    int64_t n_pairs;
+    int64_t nnzb_hint;   /* 0: estimate from the counts */
+} sx_scene_desc;
+
+/* Device bytes a finalized scene of this shape holds (upper estimate). */
+int sx_scene_footprint(const sx_scene_desc* desc, int64_t* bytes);
+/* Device bytes this scene holds now. */
+int sx_scene_bytes(sx_scene* scene, int64_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SX_H */

@@ -153,19 +153,33 @@ static double snh_alpha(double mu, double lam)
  * Neo-Hookean density psi = mu'/2 (Ic-3) + lambda'/2 (J-alpha)^2
  * - mu'/2 ln(Ic+1) [App. B]. READING: the energy is stored relative to
  * psi(I) so that the rest energy is zero; the constant changes no
- * derivative. */
+ * derivative. psi(F) - psi(I) is written with the exact identities
+ *   (J-alpha)^2 - (1-alpha)^2 = (J-1)(J+1-2 alpha),
+ *   ln(Ic+1) - ln 4 = ln(1 + (Ic-3)/4),
+ * and, with D = F - I, Ic - 3 = |D|^2 + 2 tr D and
+ * J - 1 = det(I + D) - 1 = tr D + (sum of principal 2x2 minors of D) + det D,
+ * so that no O(1) quantity is subtracted from another (otherwise the
+ * energy carries an O(lambda' eps) absolute error per unit volume, far
+ * above the last Newton decreases). */
 static void snh_density(const double F[9], double mu, double lam,
                         double* psi, double P[9], double A[81])
 {
     double alpha = snh_alpha(mu, lam);
-    double Ic = 0.0;
-    for (int k = 0; k < 9; ++k) Ic += F[k] * F[k];
-    double J = det3(F);
+    double D[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) D[i * 3 + j] = F[i * 3 + j] - (i == j ? 1.0 : 0.0);
+    double trD = D[0] + D[4] + D[8];
+    double Ic3 = 2.0 * trD;
+    for (int k = 0; k < 9; ++k) Ic3 += D[k] * D[k];
+    double minors = (D[0] * D[4] - D[1] * D[3]) + (D[0] * D[8] - D[2] * D[6]) +
+                    (D[4] * D[8] - D[5] * D[7]);
+    double Jm1 = trD + minors + det3(D);
+    double Ic = 3.0 + Ic3;
+    double J = 1.0 + Jm1;
     double C[9];
     cofactor3(F, C);
-    double psi0 = 0.5 * lam * (1.0 - alpha) * (1.0 - alpha) - 0.5 * mu * log(4.0);
-    *psi = 0.5 * mu * (Ic - 3.0) + 0.5 * lam * (J - alpha) * (J - alpha)
-         - 0.5 * mu * log(Ic + 1.0) - psi0;
+    *psi = 0.5 * mu * Ic3 + 0.5 * lam * Jm1 * (J + 1.0 - 2.0 * alpha)
+         - 0.5 * mu * log1p(0.25 * Ic3);
     if (P) {
         double a = mu * (1.0 - 1.0 / (Ic + 1.0));
         for (int k = 0; k < 9; ++k) P[k] = a * F[k] + lam * (J - alpha) * C[k];
@@ -768,15 +782,21 @@ void orc_assemble_elements(int nst, const int* conn, const int* slots,
 }
 
 /* Inertia of the incremental potential (Eq. 2): per node
- * m/(2 dt^2) |x - xt|^2, gradient m/dt^2 (x - xt), diagonal m/dt^2 I. */
-double orc_inertia(int N, const double* m, double dt, const double* x,
-                   const double* xt, const int* diag_slot, double* grad, double* vals)
+ * m/(2 dt^2) |x - xt|^2, gradient m/dt^2 (x - xt), diagonal m/dt^2 I.
+ * With x0 != NULL, `xt` holds the increment xt - x0 (= dt v + dt^2 g) and
+ * the residual is formed as (x - x0) - (xt - x0): the first difference is
+ * exact for nearby x and x0, which keeps E_BE free of the O(|x| eps)
+ * rounding that would otherwise swamp the last Newton decreases. */
+static double inertia_impl(int N, const double* m, double dt, const double* x,
+                           const double* x0, const double* xt, const int* diag_slot,
+                           double* grad, double* vals)
 {
     double E = 0.0, inv = 1.0 / (dt * dt);
     for (int n = 0; n < N; ++n) {
         double r2 = 0.0;
         for (int i = 0; i < 3; ++i) {
-            double r = x[3 * n + i] - xt[3 * n + i];
+            double r = x0 ? (x[3 * n + i] - x0[3 * n + i]) - xt[3 * n + i]
+                          : x[3 * n + i] - xt[3 * n + i];
             r2 += r * r;
             if (grad) grad[3 * n + i] += m[n] * inv * r;
         }
@@ -785,6 +805,12 @@ double orc_inertia(int N, const double* m, double dt, const double* x,
             for (int i = 0; i < 3; ++i) vals[9 * (size_t)diag_slot[n] + 4 * i] += m[n] * inv;
     }
     return E;
+}
+
+double orc_inertia(int N, const double* m, double dt, const double* x,
+                   const double* xt, const int* diag_slot, double* grad, double* vals)
+{
+    return inertia_impl(N, m, dt, x, NULL, xt, diag_slot, grad, vals);
 }
 
 /* ------------------------------------------------------------------ */
@@ -910,8 +936,9 @@ typedef struct {
 /* Full evaluation of E_BE = inertia + sum of element energies at x
  * (Eq. 2 with Eq. 5). level as above. Returns the number of barrier pairs
  * in an invalid (d <= 0) state. grad/vals are overwritten. */
-int orc_scene_eval(const orc_scene* s, const double* x, const double* xt, double dt,
-                   int level, int project, double* E_out, double* grad, double* vals)
+static int scene_eval_impl(const orc_scene* s, const double* x, const double* x0,
+                           const double* xt, double dt, int level, int project,
+                           double* E_out, double* grad, double* vals)
 {
     int bad = 0;
     size_t n3 = 3 * (size_t)s->N;
@@ -947,10 +974,16 @@ int orc_scene_eval(const orc_scene* s, const double* x, const double* xt, double
         base += (size_t)n;
     }
     if (xt && s->mass)
-        E += orc_inertia(s->N, s->mass, dt, x, xt, s->diag_slot,
-                         level >= 1 ? grad : NULL, level >= 2 ? vals : NULL);
+        E += inertia_impl(s->N, s->mass, dt, x, x0, xt, s->diag_slot,
+                          level >= 1 ? grad : NULL, level >= 2 ? vals : NULL);
     *E_out = E;
     return bad;
+}
+
+int orc_scene_eval(const orc_scene* s, const double* x, const double* xt, double dt,
+                   int level, int project, double* E_out, double* grad, double* vals)
+{
+    return scene_eval_impl(s, x, NULL, xt, dt, level, project, E_out, grad, vals);
 }
 
 typedef struct {
@@ -1000,12 +1033,13 @@ int orc_newton_step(const orc_scene* s, double dt, const double gravity[3],
     for (int n = 0; n < N; ++n)
         for (int i = 0; i < 3; ++i) {
             x0[3 * n + i] = x[3 * n + i];
-            xt[3 * n + i] = x[3 * n + i] + dt * v[3 * n + i] + dt * dt * gravity[i];
+            /* increment xt - x0 = dt v + dt^2 g (Eq. 2) */
+            xt[3 * n + i] = dt * v[3 * n + i] + dt * dt * gravity[i];
         }
     int status = ORC_ENOTCONV, it = 0, pcg_total = 0;
     double E, gn0 = 0.0, gn = 0.0;
     for (it = 0; it <= o->max_newton; ++it) {
-        orc_scene_eval(s, x, xt, dt, 2, o->project, &E, g, vals);
+        scene_eval_impl(s, x, x0, xt, dt, 2, o->project, &E, g, vals);
         gn = free_norm(N, s->pinned, g);
         if (it == 0) gn0 = gn;
         double ref = gn0 > 1e-30 ? gn0 : 1e-30;
@@ -1025,7 +1059,7 @@ int orc_newton_step(const orc_scene* s, double dt, const double gravity[3],
         for (int h = 0; h <= o->max_halvings; ++h) {
             for (size_t k = 0; k < n3; ++k) xtr[k] = x[k] + alpha * dx[k];
             double Et;
-            int bad = orc_scene_eval(s, xtr, xt, dt, 0, 0, &Et, NULL, NULL);
+            int bad = scene_eval_impl(s, xtr, x0, xt, dt, 0, 0, &Et, NULL, NULL);
             if (bad == 0 && isfinite(Et) && Et <= E + o->armijo_c * alpha * gdx) {
                 accepted = 1;
                 break;

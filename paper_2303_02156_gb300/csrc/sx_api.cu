@@ -1,0 +1,1211 @@
+// sx_api.cu -- the C ABI of include/sx.h: contexts, scenes, registration,
+// evaluation, element-level outputs and the batched backward-Euler Newton
+// step. Host code only orchestrates; every step of the numerical path runs
+// in the kernels of sx_elements.cu, sx_graph.cu, sx_assemble.cu and
+// sx_solve.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "sx_internal.cuh"
+
+using namespace sx;
+
+// ------------------------------------------------------------------ helpers
+namespace {
+
+struct BlockHost {
+    int kind = 0;
+    int64_t n = 0;
+    int64_t base = 0;
+    int4* conn = nullptr;
+    double* Dminv = nullptr;
+    double* V = nullptr;
+    double* mu = nullptr;
+    double* lam = nullptr;
+    double rho = 0.0;
+    double* q = nullptr;
+    double* c = nullptr;
+    double kb = 0.0;
+    double dhat = 0.0, kappa = 0.0;
+};
+
+constexpr int kNodeTile = 256;
+constexpr int kSlotTile = 256;
+
+}  // namespace
+
+struct Batch;
+
+struct sx_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int elem_blocks_per_sm[2] = {1, 1};
+    std::string err;
+    int* queue = nullptr;
+    std::vector<std::unique_ptr<Batch>> batch_cache;
+};
+
+struct sx_scene {
+    sx_ctx* ctx = nullptr;
+    int64_t N = 0;
+    double* X = nullptr;
+    double* x = nullptr;
+    double* v = nullptr;
+    double* x_start = nullptr;
+    double* x_tilde = nullptr;
+    double* x_trial = nullptr;
+    double* dx = nullptr;
+    double* mass = nullptr;
+    double* extra_mass = nullptr;
+    uint8_t* pinned = nullptr;
+    double gravity[3] = {0.0, 0.0, 0.0};
+    std::vector<BlockHost> blocks;
+    bool finalized = false;
+    PatternOut pat{};
+    double* Ee = nullptr;
+    double* ge = nullptr;
+    double* He = nullptr;   // 90 doubles per stencil; float staging reuses it
+    double* vals64 = nullptr;
+    float* vals32 = nullptr;
+    double* grad = nullptr;
+    double *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+    double* Minv = nullptr;
+    SceneScal* sc = nullptr;
+    int last_precision = SX_FP64;
+    int last_level = -1;
+    bool inertia_on = false;
+    int inertia_mode = 0;
+    double dt = 1.0;
+    int64_t nst = 0;
+    int64_t bytes = 0;
+    uint64_t version = 1;   // bumps whenever the device descriptor changes
+    std::vector<void*> allocs;
+};
+
+// ---------------------------------------------------------------- batches
+struct Batch {
+    std::vector<sx_scene*> scenes;
+    std::vector<uint64_t> versions;
+    SceneDev* d_desc = nullptr;
+    SceneDev* d_desc_trial = nullptr;
+    std::vector<Tile> elem_tiles, node_tiles, slot_tiles;
+    Tile* d_elem = nullptr;
+    Tile* d_node = nullptr;
+    Tile* d_slot = nullptr;
+    int* d_elem_beg = nullptr;
+    int* d_elem_end = nullptr;
+    int* d_node_beg = nullptr;
+    int* d_node_end = nullptr;
+    double* d_part_elem = nullptr;   // 1 per elem tile
+    double* d_part_node = nullptr;   // 2 per node tile
+    int* d_bad = nullptr;
+    int* d_nonfin = nullptr;
+    int* d_clamped = nullptr;
+    SceneScal* d_scal = nullptr;     // gathered scalars
+    SceneScal* h_scal = nullptr;     // pinned host mirror
+    int* d_ctl_i = nullptr;
+    double* d_ctl_d = nullptr;
+    int* h_ctl_i = nullptr;
+    double* h_ctl_d = nullptr;
+    ~Batch()
+    {
+        cudaFree(d_desc); cudaFree(d_desc_trial); cudaFree(d_elem); cudaFree(d_node);
+        cudaFree(d_slot); cudaFree(d_elem_beg); cudaFree(d_elem_end); cudaFree(d_node_beg);
+        cudaFree(d_node_end); cudaFree(d_part_elem); cudaFree(d_part_node); cudaFree(d_bad);
+        cudaFree(d_nonfin); cudaFree(d_clamped); cudaFree(d_scal); cudaFreeHost(h_scal);
+        cudaFree(d_ctl_i); cudaFree(d_ctl_d); cudaFreeHost(h_ctl_i); cudaFreeHost(h_ctl_d);
+    }
+};
+
+namespace {
+
+int fail(sx_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(sx_ctx* c, cudaError_t e, const char* where)
+{
+    return fail(c, SX_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                         \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);         \
+    } while (0)
+
+template <typename T>
+int dalloc(sx_scene* s, T** p, size_t count)
+{
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return SX_ENOMEM;
+    }
+    s->allocs.push_back((void*)*p);
+    s->bytes += (int64_t)bytes;
+    return SX_OK;
+}
+
+SceneDev make_desc(const sx_scene* s, bool trial)
+{
+    SceneDev d{};
+    d.N = s->N;
+    d.nst = s->nst;
+    d.nnzb = s->pat.nnzb;
+    d.nblocks = (int)s->blocks.size();
+    d.inertia_on = s->inertia_on ? 1 : 0;
+    d.inertia_mode = s->inertia_mode;
+    d.dt = s->dt;
+    d.inv_dt2 = 1.0 / (s->dt * s->dt);
+    for (size_t b = 0; b < s->blocks.size(); ++b) {
+        const BlockHost& h = s->blocks[b];
+        ElemBlock& e = d.blk[b];
+        e.kind = h.kind;
+        e.n = h.n;
+        e.base = h.base;
+        e.conn = h.conn;
+        e.Dminv = h.Dminv;
+        e.V = h.V;
+        e.mu = h.mu;
+        e.lam = h.lam;
+        e.q = h.q;
+        e.c = h.c;
+        e.kb = h.kb;
+        e.dhat = h.dhat;
+        e.kappa = h.kappa;
+    }
+    d.x = trial ? s->x_trial : s->x;
+    d.v = s->v;
+    d.x_start = s->x_start;
+    d.x_tilde = s->x_tilde;
+    d.x_trial = s->x_trial;
+    d.dx = s->dx;
+    d.mass = s->mass;
+    d.pinned = s->pinned;
+    d.grad = s->grad;
+    d.Ee = s->Ee;
+    d.ge = s->ge;
+    d.He = s->He;
+    d.row_ptr = s->pat.row_ptr;
+    d.col = s->pat.col;
+    d.diag_slot = s->pat.diag_slot;
+    d.slots = s->pat.slots;
+    d.slot_ptr = s->pat.slot_ptr;
+    d.slot_src = s->pat.slot_src;
+    d.node_ptr = s->pat.node_ptr;
+    d.node_src = s->pat.node_src;
+    d.vals64 = s->vals64;
+    d.vals32 = s->vals32;
+    d.r = s->r;
+    d.z = s->z;
+    d.p0 = s->p0;
+    d.p1 = s->p1;
+    d.q = s->q;
+    d.Minv = s->Minv;
+    d.sc = s->sc;
+    return d;
+}
+
+template <typename T>
+int upload(sx_ctx* ctx, T** dptr, const std::vector<T>& v, cudaStream_t st)
+{
+    cudaFree(*dptr);
+    *dptr = nullptr;
+    CK(cudaMalloc((void**)dptr, std::max<size_t>(v.size(), 1) * sizeof(T)));
+    if (!v.empty()) CK(cudaMemcpyAsync(*dptr, v.data(), v.size() * sizeof(T),
+                                       cudaMemcpyHostToDevice, st));
+    return SX_OK;
+}
+
+// builds (or refreshes the descriptors of) a batch for `scenes`
+int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
+{
+    const int n = (int)B->scenes.size();
+    std::vector<SceneDev> desc(n), desc_t(n);
+    for (int i = 0; i < n; ++i) {
+        desc[i] = make_desc(B->scenes[i], false);
+        desc_t[i] = make_desc(B->scenes[i], true);
+    }
+    if (B->d_desc == nullptr) {
+        std::vector<int> eb(n), ee(n), nb(n), ne(n);
+        for (int i = 0; i < n; ++i) {
+            sx_scene* s = B->scenes[i];
+            eb[i] = (int)B->elem_tiles.size();
+            const int et = sx::elements_block_threads();
+            for (size_t b = 0; b < s->blocks.size(); ++b)
+                for (int64_t k = 0; k < s->blocks[b].n; k += et)
+                    B->elem_tiles.push_back(
+                        Tile{i, (int)b, k, (int)std::min<int64_t>(et, s->blocks[b].n - k), 0});
+            ee[i] = (int)B->elem_tiles.size();
+            nb[i] = (int)B->node_tiles.size();
+            for (int64_t k = 0; k < s->N; k += kNodeTile)
+                B->node_tiles.push_back(
+                    Tile{i, 0, k, (int)std::min<int64_t>(kNodeTile, s->N - k), 0});
+            ne[i] = (int)B->node_tiles.size();
+            for (int64_t k = 0; k < s->pat.nnzb; k += kSlotTile)
+                B->slot_tiles.push_back(
+                    Tile{i, 0, k, (int)std::min<int64_t>(kSlotTile, s->pat.nnzb - k), 0});
+        }
+        int rc;
+        if ((rc = upload(ctx, &B->d_elem, B->elem_tiles, st)) != SX_OK) return rc;
+        if ((rc = upload(ctx, &B->d_node, B->node_tiles, st)) != SX_OK) return rc;
+        if ((rc = upload(ctx, &B->d_slot, B->slot_tiles, st)) != SX_OK) return rc;
+        if ((rc = upload(ctx, &B->d_elem_beg, eb, st)) != SX_OK) return rc;
+        if ((rc = upload(ctx, &B->d_elem_end, ee, st)) != SX_OK) return rc;
+        if ((rc = upload(ctx, &B->d_node_beg, nb, st)) != SX_OK) return rc;
+        if ((rc = upload(ctx, &B->d_node_end, ne, st)) != SX_OK) return rc;
+        const size_t net = std::max<size_t>(B->elem_tiles.size(), 1);
+        const size_t nnt = std::max<size_t>(B->node_tiles.size(), 1);
+        CK(cudaMalloc((void**)&B->d_part_elem, net * sizeof(double)));
+        CK(cudaMalloc((void**)&B->d_part_node, 2 * nnt * sizeof(double)));
+        CK(cudaMalloc((void**)&B->d_bad, net * sizeof(int)));
+        CK(cudaMalloc((void**)&B->d_nonfin, net * sizeof(int)));
+        CK(cudaMalloc((void**)&B->d_clamped, net * sizeof(int)));
+        CK(cudaMalloc((void**)&B->d_scal, n * sizeof(SceneScal)));
+        CK(cudaMallocHost((void**)&B->h_scal, n * sizeof(SceneScal)));
+        CK(cudaMalloc((void**)&B->d_ctl_i, n * sizeof(int)));
+        CK(cudaMalloc((void**)&B->d_ctl_d, n * sizeof(double)));
+        CK(cudaMallocHost((void**)&B->h_ctl_i, n * sizeof(int)));
+        CK(cudaMallocHost((void**)&B->h_ctl_d, n * sizeof(double)));
+        CK(cudaMalloc((void**)&B->d_desc, n * sizeof(SceneDev)));
+        CK(cudaMalloc((void**)&B->d_desc_trial, n * sizeof(SceneDev)));
+        B->versions.assign(n, 0);
+    }
+    bool dirty = false;
+    for (int i = 0; i < n; ++i) dirty |= B->versions[i] != B->scenes[i]->version;
+    if (dirty) {
+        CK(cudaMemcpyAsync(B->d_desc, desc.data(), n * sizeof(SceneDev), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(B->d_desc_trial, desc_t.data(), n * sizeof(SceneDev),
+                           cudaMemcpyHostToDevice, st));
+        // the pageable source vectors must stay valid until the copies ran
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < n; ++i) B->versions[i] = B->scenes[i]->version;
+    }
+    return SX_OK;
+}
+
+Batch* get_batch(sx_ctx* ctx, sx_scene* const* scenes, int n)
+{
+    for (auto& b : ctx->batch_cache) {
+        if ((int)b->scenes.size() != n) continue;
+        bool same = true;
+        for (int i = 0; i < n && same; ++i) same = b->scenes[i] == scenes[i];
+        if (same) return b.get();
+    }
+    if (ctx->batch_cache.size() >= 16) ctx->batch_cache.erase(ctx->batch_cache.begin());
+    auto B = std::make_unique<Batch>();
+    B->scenes.assign(scenes, scenes + n);
+    ctx->batch_cache.push_back(std::move(B));
+    return ctx->batch_cache.back().get();
+}
+
+void drop_batches_with(sx_ctx* ctx, sx_scene* s)
+{
+    auto& v = ctx->batch_cache;
+    v.erase(std::remove_if(v.begin(), v.end(),
+                           [s](const std::unique_ptr<Batch>& b) {
+                               return std::find(b->scenes.begin(), b->scenes.end(), s) !=
+                                      b->scenes.end();
+                           }),
+            v.end());
+}
+
+int set_active(sx_ctx* ctx, Batch* B, const std::vector<int>& act, cudaStream_t st)
+{
+    const int n = (int)B->scenes.size();
+    for (int i = 0; i < n; ++i) B->h_ctl_i[i] = act[i];
+    CK(cudaMemcpyAsync(B->d_ctl_i, B->h_ctl_i, n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(launch_set_scal(B->d_desc, n, B->d_ctl_i, nullptr, st));
+    return SX_OK;
+}
+
+int set_alpha(sx_ctx* ctx, Batch* B, const std::vector<double>& a, cudaStream_t st)
+{
+    const int n = (int)B->scenes.size();
+    for (int i = 0; i < n; ++i) B->h_ctl_d[i] = a[i];
+    CK(cudaMemcpyAsync(B->d_ctl_d, B->h_ctl_d, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(launch_set_scal(B->d_desc, n, nullptr, B->d_ctl_d, st));
+    return SX_OK;
+}
+
+int read_scal(sx_ctx* ctx, Batch* B, cudaStream_t st)
+{
+    const int n = (int)B->scenes.size();
+    CK(launch_gather_scal(B->d_desc, n, B->d_scal, st));
+    CK(cudaMemcpyAsync(B->h_scal, B->d_scal, n * sizeof(SceneScal), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SX_OK;
+}
+
+int ensure_vals32(sx_ctx* ctx, sx_scene* s)
+{
+    if (s->vals32) return SX_OK;
+    if (dalloc(s, &s->vals32, 9 * (size_t)s->pat.nnzb) != SX_OK)
+        return fail(ctx, SX_ENOMEM, "eval: device allocation failed (FP32 values)");
+    s->version++;
+    return SX_OK;
+}
+
+// E / E+g / E+g+H over every active scene of the batch
+int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool trial,
+             cudaStream_t st)
+{
+    const int n = (int)B->scenes.size();
+    const SceneDev* desc = trial ? B->d_desc_trial : B->d_desc;
+    ElemLaunch L{};
+    L.scenes = desc;
+    L.tiles = B->d_elem;
+    L.ntiles = (int)B->elem_tiles.size();
+    L.level = level;
+    L.project = project;
+    L.precision = precision;
+    L.tile_E = B->d_part_elem;
+    L.tile_bad = B->d_bad;
+    L.tile_nonfinite = B->d_nonfin;
+    L.tile_clamped = B->d_clamped;
+    L.queue = ctx->queue;
+    const int pidx = precision == SX_FP32 ? 1 : 0;
+    int grid = std::min<int>(L.ntiles, ctx->sm_count * ctx->elem_blocks_per_sm[pidx]);
+    grid = std::max(grid, 1);
+    CK(launch_elements(L, grid, st));
+    CK(launch_scene_reduce(B->d_part_elem, 1, 0, B->d_elem_beg, B->d_elem_end, n, desc, F_E, 0,
+                           st));
+    CK(launch_scene_reduce_flags(B->d_bad, B->d_nonfin, B->d_clamped, B->d_elem_beg,
+                                 B->d_elem_end, n, desc, st));
+    const int nnt = (int)B->node_tiles.size();
+    if (level >= 1)
+        CK(launch_assemble_grad(desc, B->d_node, nnt, B->d_part_node, st));
+    else
+        CK(launch_inertia_energy(desc, B->d_node, nnt, nullptr, B->d_part_node, 0, st));
+    CK(launch_scene_reduce(B->d_part_node, 2, 0, B->d_node_beg, B->d_node_end, n, desc, F_E, 1,
+                           st));
+    if (level >= 1)
+        CK(launch_scene_reduce(B->d_part_node, 2, 1, B->d_node_beg, B->d_node_end, n, desc,
+                               F_GNORM2, 0, st));
+    if (level >= 2) {
+        AsmLaunch A{desc, B->d_slot, (int)B->slot_tiles.size(), precision};
+        CK(launch_assemble_vals(A, st));
+        CK(launch_inertia_diag(desc, B->d_node, nnt, precision, st));
+        for (sx_scene* s : B->scenes) s->last_precision = precision;
+    }
+    for (sx_scene* s : B->scenes) s->last_level = std::max(s->last_level, level);
+    return SX_OK;
+}
+
+int check_scene_ready(sx_scene* s)
+{
+    if (!s) return SX_EINVAL;
+    if (!s->finalized) return fail(s->ctx, SX_EORDER, "scene is not finalized");
+    return SX_OK;
+}
+
+__global__ void k_set_pinned(const int32_t* nodes, int64_t n, int64_t N, uint8_t* pinned,
+                             int* bad)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int v = nodes[i];
+    if (v < 0 || v >= N) {
+        atomicAdd(bad, 1);
+        return;
+    }
+    pinned[v] = 1;
+}
+
+__global__ void k_add_vec(double* dst, const double* src, int64_t n)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] += src[i];
+}
+
+__global__ void k_copy_conn(const int32_t* src, int64_t n, int4* dst)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = make_int4(src[4 * i], src[4 * i + 1], src[4 * i + 2], src[4 * i + 3]);
+}
+
+__global__ void k_soa4(const double* src, int64_t n, double* dst)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n)
+        for (int a = 0; a < 4; ++a) dst[(int64_t)a * n + i] = src[4 * i + a];
+}
+
+// full 12x12 from staged upper blocks is done in the element kernel; this
+// kernel copies a block's slot map
+int copy_conn(sx_ctx* ctx, sx_scene* s, const int32_t* src, int64_t n, int4** out,
+              cudaStream_t st)
+{
+    if (dalloc(s, out, (size_t)n) != SX_OK) return fail(ctx, SX_ENOMEM, "add: allocation failed");
+    int32_t* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, std::max<int64_t>(n, 1) * 4 * sizeof(int32_t), st));
+    if (n) CK(cudaMemcpyAsync(tmp, src, n * 4 * sizeof(int32_t), cudaMemcpyDefault, st));
+    if (n) k_copy_conn<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tmp, n, *out);
+    CK(cudaGetLastError());
+    CK(cudaFreeAsync(tmp, st));
+    return SX_OK;
+}
+
+int add_block_common(sx_scene* s, const char* what)
+{
+    if (!s) return SX_EINVAL;
+    if ((int)s->blocks.size() >= SX_MAX_BLOCKS)
+        return fail(s->ctx, SX_EINVAL, std::string(what) + ": too many energy blocks");
+    return SX_OK;
+}
+
+void register_block(sx_scene* s, BlockHost&& b, int* energy_id)
+{
+    b.base = s->nst;
+    s->nst += b.n;
+    s->blocks.push_back(b);
+    s->finalized = false;
+    s->version++;
+    if (energy_id) *energy_id = (int)s->blocks.size() - 1;
+}
+
+}  // namespace
+
+// ==================================================================== ABI
+extern "C" {
+
+const char* sx_version(void) { return "libsx 1.0 (sm_103a)"; }
+
+int sx_create(sx_ctx** out, const sx_options* opt)
+{
+    if (!out) return SX_EINVAL;
+    *out = nullptr;
+    auto* ctx = new sx_ctx();
+    if (opt && opt->device >= 0) {
+        cudaError_t e = cudaSetDevice(opt->device);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return SX_ECUDA;
+        }
+    }
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device) !=
+            cudaSuccess) {
+        delete ctx;
+        return SX_ECUDA;
+    }
+    for (int p = 0; p < 2; ++p) {
+        int nb = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elements_kernel(p),
+                                                      elements_block_threads(), 0);
+        ctx->elem_blocks_per_sm[p] = std::max(nb, 1);
+    }
+    if (cudaMalloc((void**)&ctx->queue, sizeof(int)) != cudaSuccess) {
+        delete ctx;
+        return SX_ENOMEM;
+    }
+    *out = ctx;
+    return SX_OK;
+}
+
+int sx_destroy(sx_ctx* ctx)
+{
+    if (!ctx) return SX_EINVAL;
+    ctx->batch_cache.clear();
+    cudaFree(ctx->queue);
+    delete ctx;
+    return SX_OK;
+}
+
+const char* sx_last_error(sx_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int sx_scene_create(sx_ctx* ctx, int64_t n_nodes, const double* X_rest, int64_t stride,
+                    void* stream, sx_scene** out)
+{
+    if (!ctx || !out) return SX_EINVAL;
+    *out = nullptr;
+    if (n_nodes <= 0 || !X_rest || stride < 3)
+        return fail(ctx, SX_EINVAL, "scene_create: need n_nodes > 0, X_rest, stride >= 3");
+    if (n_nodes >= (int64_t)INT32_MAX / 4)
+        return fail(ctx, SX_EINVAL, "scene_create: n_nodes too large for int32 node ids");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto* s = new sx_scene();
+    s->ctx = ctx;
+    s->N = n_nodes;
+    const size_t n3 = 3 * (size_t)n_nodes;
+    int rc = SX_OK;
+    rc |= dalloc(s, &s->X, n3);
+    rc |= dalloc(s, &s->x, n3);
+    rc |= dalloc(s, &s->v, n3);
+    rc |= dalloc(s, &s->x_start, n3);
+    rc |= dalloc(s, &s->x_tilde, n3);
+    rc |= dalloc(s, &s->x_trial, n3);
+    rc |= dalloc(s, &s->dx, n3);
+    rc |= dalloc(s, &s->mass, (size_t)n_nodes);
+    rc |= dalloc(s, &s->extra_mass, (size_t)n_nodes);
+    rc |= dalloc(s, &s->pinned, (size_t)n_nodes);
+    rc |= dalloc(s, &s->sc, 1);
+    if (rc != SX_OK) {
+        sx_scene_destroy(s);
+        return fail(ctx, SX_ENOMEM, "scene_create: device allocation failed");
+    }
+    cudaError_t e = cudaMemcpy2DAsync(s->X, 3 * sizeof(double), X_rest, stride * sizeof(double),
+                                      3 * sizeof(double), (size_t)n_nodes, cudaMemcpyDefault, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->x, s->X, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->v, 0, n3 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->extra_mass, 0, n_nodes * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->pinned, 0, (size_t)n_nodes, st);
+    if (e == cudaSuccess) {
+        SceneScal init{};
+        init.active = 1;
+        e = cudaMemcpyAsync(s->sc, &init, sizeof(init), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) {
+        sx_scene_destroy(s);
+        return cuda_fail(ctx, e, "scene_create");
+    }
+    *out = s;
+    return SX_OK;
+}
+
+int sx_scene_destroy(sx_scene* s)
+{
+    if (!s) return SX_EINVAL;
+    if (s->ctx) drop_batches_with(s->ctx, s);
+    cudaDeviceSynchronize();
+    for (void* p : s->allocs) cudaFree(p);
+    delete s;
+    return SX_OK;
+}
+
+int sx_add_snh_tet4(sx_scene* s, const int32_t* tets, int64_t n, const double* young,
+                    const double* poisson, double density, int literal_params, void* stream,
+                    int* energy_id)
+{
+    int rc = add_block_common(s, "add_snh_tet4");
+    if (rc != SX_OK) return rc;
+    sx_ctx* ctx = s->ctx;
+    if (n < 0 || (n > 0 && (!tets || !young || !poisson)) || !(density >= 0.0))
+        return fail(ctx, SX_EINVAL, "add_snh_tet4: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    BlockHost b;
+    b.kind = SX_KIND_SNH_TET4;
+    b.n = n;
+    b.rho = density;
+    if ((rc = copy_conn(ctx, s, tets, n, &b.conn, st)) != SX_OK) return rc;
+    if (dalloc(s, &b.Dminv, 9 * (size_t)n) || dalloc(s, &b.V, (size_t)n) ||
+        dalloc(s, &b.mu, (size_t)n) || dalloc(s, &b.lam, (size_t)n))
+        return fail(ctx, SX_ENOMEM, "add_snh_tet4: allocation failed");
+    double *dy = nullptr, *dp = nullptr;
+    int* bad = nullptr;
+    CK(cudaMallocAsync((void**)&dy, std::max<int64_t>(n, 1) * sizeof(double), st));
+    CK(cudaMallocAsync((void**)&dp, std::max<int64_t>(n, 1) * sizeof(double), st));
+    CK(cudaMallocAsync((void**)&bad, 2 * sizeof(int), st));
+    CK(cudaMemsetAsync(bad, 0, 2 * sizeof(int), st));
+    if (n) {
+        CK(cudaMemcpyAsync(dy, young, n * sizeof(double), cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(dp, poisson, n * sizeof(double), cudaMemcpyDefault, st));
+    }
+    CK(launch_snh_rest(s->X, s->N, b.conn, n, dy, dp, density, literal_params, b.Dminv, b.V,
+                       b.mu, b.lam, bad, st));
+    int h_bad2[2] = {0, 0};
+    CK(cudaMemcpyAsync(h_bad2, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(dy, st));
+    CK(cudaFreeAsync(dp, st));
+    CK(cudaFreeAsync(bad, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_bad2[1])
+        return fail(ctx, SX_EINVAL, "add_snh_tet4: node id out of range");
+    if (h_bad2[0])
+        return fail(ctx, SX_EDEGENERATE,
+                    "add_snh_tet4: " + std::to_string(h_bad2[0]) + " tets with det(Dm) <= 0");
+    register_block(s, std::move(b), energy_id);
+    return SX_OK;
+}
+
+int sx_add_hinge4(sx_scene* s, const int32_t* stencils, int64_t n, const double* q,
+                  const double* c, double k_b, void* stream, int* energy_id)
+{
+    int rc = add_block_common(s, "add_hinge4");
+    if (rc != SX_OK) return rc;
+    sx_ctx* ctx = s->ctx;
+    if (n < 0 || (n > 0 && (!stencils || !q || !c)))
+        return fail(ctx, SX_EINVAL, "add_hinge4: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    BlockHost b;
+    b.kind = SX_KIND_HINGE4;
+    b.n = n;
+    b.kb = k_b;
+    if ((rc = copy_conn(ctx, s, stencils, n, &b.conn, st)) != SX_OK) return rc;
+    if (dalloc(s, &b.q, 4 * (size_t)n) || dalloc(s, &b.c, (size_t)n))
+        return fail(ctx, SX_ENOMEM, "add_hinge4: allocation failed");
+    double* tq = nullptr;
+    CK(cudaMallocAsync((void**)&tq, std::max<int64_t>(n, 1) * 4 * sizeof(double), st));
+    if (n) {
+        CK(cudaMemcpyAsync(tq, q, n * 4 * sizeof(double), cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(b.c, c, n * sizeof(double), cudaMemcpyDefault, st));
+        k_soa4<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tq, n, b.q);
+        CK(cudaGetLastError());
+    }
+    CK(cudaFreeAsync(tq, st));
+    CK(cudaStreamSynchronize(st));
+    register_block(s, std::move(b), energy_id);
+    return SX_OK;
+}
+
+int sx_add_pt_barrier(sx_scene* s, const int32_t* pairs, int64_t n, double dhat, double kappa,
+                      void* stream, int* energy_id)
+{
+    int rc = add_block_common(s, "add_pt_barrier");
+    if (rc != SX_OK) return rc;
+    sx_ctx* ctx = s->ctx;
+    if (n < 0 || (n > 0 && !pairs) || !(dhat > 0.0) || !(kappa >= 0.0))
+        return fail(ctx, SX_EINVAL, "add_pt_barrier: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    BlockHost b;
+    b.kind = SX_KIND_PT_BARRIER;
+    b.n = n;
+    b.dhat = dhat;
+    b.kappa = kappa;
+    if ((rc = copy_conn(ctx, s, pairs, n, &b.conn, st)) != SX_OK) return rc;
+    CK(cudaStreamSynchronize(st));
+    register_block(s, std::move(b), energy_id);
+    return SX_OK;
+}
+
+int sx_add_node_mass(sx_scene* s, const double* mass, void* stream)
+{
+    if (!s || !mass) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, s->N * sizeof(double), st));
+    CK(cudaMemcpyAsync(tmp, mass, s->N * sizeof(double), cudaMemcpyDefault, st));
+    k_add_vec<<<(unsigned)((s->N + 255) / 256), 256, 0, st>>>(s->extra_mass, tmp, s->N);
+    if (s->finalized)
+        k_add_vec<<<(unsigned)((s->N + 255) / 256), 256, 0, st>>>(s->mass, tmp, s->N);
+    CK(cudaGetLastError());
+    CK(cudaFreeAsync(tmp, st));
+    CK(cudaStreamSynchronize(st));
+    return SX_OK;
+}
+
+int sx_set_pinned(sx_scene* s, const int32_t* nodes, int64_t n, void* stream)
+{
+    if (!s || n < 0 || (n > 0 && !nodes)) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* bad = nullptr;
+    int32_t* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&bad, sizeof(int), st));
+    CK(cudaMallocAsync((void**)&tmp, std::max<int64_t>(n, 1) * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(s->pinned, 0, (size_t)s->N, st));
+    if (n) {
+        CK(cudaMemcpyAsync(tmp, nodes, n * sizeof(int32_t), cudaMemcpyDefault, st));
+        k_set_pinned<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tmp, n, s->N, s->pinned, bad);
+        CK(cudaGetLastError());
+    }
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(bad, st));
+    CK(cudaFreeAsync(tmp, st));
+    CK(cudaStreamSynchronize(st));
+    if (h) return fail(ctx, SX_EINVAL, "set_pinned: node id out of range");
+    return SX_OK;
+}
+
+int sx_set_gravity(sx_scene* s, const double g[3])
+{
+    if (!s || !g) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    for (int i = 0; i < 3; ++i) s->gravity[i] = g[i];
+    CK(cudaMemcpy((char*)s->sc + offsetof(SceneScal, grav), s->gravity, 3 * sizeof(double),
+                  cudaMemcpyHostToDevice));
+    return SX_OK;
+}
+
+int sx_finalize(sx_scene* s, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->finalized) return SX_OK;
+    if (s->pat.row_ptr) return fail(ctx, SX_EORDER, "finalize: scene already finalized once");
+    // concatenated stencils in registration order
+    int4* conn = nullptr;
+    CK(cudaMalloc((void**)&conn, std::max<int64_t>(s->nst, 1) * sizeof(int4)));
+    for (auto& b : s->blocks)
+        if (b.n) CK(cudaMemcpyAsync(conn + b.base, b.conn, b.n * sizeof(int4),
+                                    cudaMemcpyDeviceToDevice, st));
+    std::string err;
+    int rc = build_pattern(conn, s->nst, s->N, &s->pat, &err, st);
+    cudaFree(conn);
+    if (rc != SX_OK) return fail(ctx, rc, err);
+    for (void* p : {(void*)s->pat.row_ptr, (void*)s->pat.col, (void*)s->pat.diag_slot,
+                    (void*)s->pat.slots, (void*)s->pat.slot_ptr, (void*)s->pat.slot_src,
+                    (void*)s->pat.node_ptr, (void*)s->pat.node_src})
+        s->allocs.push_back(p);
+    s->bytes += (int64_t)(s->N + 1) * 8 + s->pat.nnzb * 8 + s->N * 4 + s->nst * 16 * 4 * 2 +
+                s->nst * 4 * 4;
+    // lumped mass: extra + rho V / 4 of every SNH tet, in element order
+    CK(cudaMemcpyAsync(s->mass, s->extra_mass, s->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (auto& b : s->blocks)
+        if (b.kind == SX_KIND_SNH_TET4)
+            CK(launch_block_mass(s->pat.node_ptr, s->pat.node_src, s->N, b.base, b.n, b.V, b.rho,
+                                 s->mass, st));
+    const size_t n3 = 3 * (size_t)s->N;
+    if (dalloc(s, &s->Ee, (size_t)s->nst) || dalloc(s, &s->ge, 12 * (size_t)s->nst) ||
+        dalloc(s, &s->He, 90 * (size_t)s->nst) || dalloc(s, &s->vals64, 9 * (size_t)s->pat.nnzb) ||
+        dalloc(s, &s->grad, n3) || dalloc(s, &s->r, n3) || dalloc(s, &s->z, n3) ||
+        dalloc(s, &s->p0, n3) || dalloc(s, &s->p1, n3) || dalloc(s, &s->q, n3) ||
+        dalloc(s, &s->Minv, 9 * (size_t)s->N))
+        return fail(ctx, SX_ENOMEM, "finalize: device allocation failed");
+    CK(cudaMemsetAsync(s->grad, 0, n3 * sizeof(double), st));
+    CK(cudaMemsetAsync(s->vals64, 0, 9 * (size_t)s->pat.nnzb * sizeof(double), st));
+    CK(cudaStreamSynchronize(st));
+    s->finalized = true;
+    s->version++;
+    drop_batches_with(ctx, s);
+    return SX_OK;
+}
+
+int sx_set_state(sx_scene* s, const double* x, const double* v, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t b = 3 * (size_t)s->N * sizeof(double);
+    if (x) CK(cudaMemcpyAsync(s->x, x, b, cudaMemcpyDefault, st));
+    if (v) CK(cudaMemcpyAsync(s->v, v, b, cudaMemcpyDefault, st));
+    return SX_OK;
+}
+
+int sx_get_state(sx_scene* s, double* x, double* v, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t b = 3 * (size_t)s->N * sizeof(double);
+    if (x) CK(cudaMemcpyAsync(x, s->x, b, cudaMemcpyDefault, st));
+    if (v) CK(cudaMemcpyAsync(v, s->v, b, cudaMemcpyDefault, st));
+    return SX_OK;
+}
+
+int sx_set_inertia(sx_scene* s, double dt, const double* x_tilde, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!x_tilde) {
+        if (s->inertia_on) s->version++;
+        s->inertia_on = false;
+        return SX_OK;
+    }
+    if (!(dt > 0.0)) return fail(ctx, SX_EINVAL, "set_inertia: dt must be > 0");
+    CK(cudaMemcpyAsync(s->x_tilde, x_tilde, 3 * (size_t)s->N * sizeof(double), cudaMemcpyDefault,
+                       st));
+    if (!s->inertia_on || s->dt != dt || s->inertia_mode != 0) s->version++;
+    s->inertia_on = true;
+    s->inertia_mode = 0;
+    s->dt = dt;
+    return SX_OK;
+}
+
+static int status_from_scal(sx_ctx* ctx, const SceneScal& sc)
+{
+    if (sc.nonfinite) return fail(ctx, SX_ENAN, "eval: non-finite energy, gradient or Hessian");
+    if (sc.bad_state)
+        return fail(ctx, SX_ESTATE, "eval: " + std::to_string(sc.bad_state) +
+                                        " barrier pairs at distance <= 0");
+    return SX_OK;
+}
+
+int sx_eval_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, int level, int project,
+                  int precision, double* E_out, void* stream)
+{
+    if (!ctx || !scenes || n <= 0) return SX_EINVAL;
+    if (level < SX_E || level > SX_EGH || (precision != SX_FP64 && precision != SX_FP32))
+        return fail(ctx, SX_EINVAL, "eval: bad level or precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n; ++i) {
+        int rc = check_scene_ready(scenes[i]);
+        if (rc != SX_OK) return rc;
+        if (scenes[i]->ctx != ctx) return fail(ctx, SX_EINVAL, "eval: scene of another context");
+        if (level >= 2 && precision == SX_FP32 && (rc = ensure_vals32(ctx, scenes[i])) != SX_OK)
+            return rc;
+    }
+    Batch* B = get_batch(ctx, scenes, n);
+    int rc = prepare_batch(ctx, B, st);
+    if (rc != SX_OK) return rc;
+    std::vector<int> act(n, 1);
+    if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
+    if ((rc = run_eval(ctx, B, level, project, precision, false, st)) != SX_OK) return rc;
+    if (E_out) {
+        if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
+        int worst = SX_OK;
+        for (int i = 0; i < n; ++i) {
+            E_out[i] = B->h_scal[i].E;
+            int r2 = status_from_scal(ctx, B->h_scal[i]);
+            if (r2 != SX_OK) worst = r2;
+        }
+        return worst;
+    }
+    return SX_OK;
+}
+
+int sx_eval(sx_scene* s, int level, int project, int precision, double* E_out, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_scene* arr[1] = {s};
+    return sx_eval_batch(s->ctx, arr, 1, level, project, precision, E_out, stream);
+}
+
+int sx_get_bsr(sx_scene* s, const int32_t** row_ptr, const int32_t** col, const void** vals,
+               int64_t* nnzb, int* dtype)
+{
+    int rc = check_scene_ready(s);
+    if (rc != SX_OK) return rc;
+    if (row_ptr) *row_ptr = s->pat.row_ptr;
+    if (col) *col = s->pat.col;
+    if (nnzb) *nnzb = s->pat.nnzb;
+    if (dtype) *dtype = s->last_precision;
+    if (vals) *vals = s->last_precision == SX_FP32 ? (const void*)s->vals32 : (const void*)s->vals64;
+    return SX_OK;
+}
+
+int sx_get_grad(sx_scene* s, const double** grad)
+{
+    int rc = check_scene_ready(s);
+    if (rc != SX_OK) return rc;
+    if (grad) *grad = s->grad;
+    return SX_OK;
+}
+
+int sx_get_diag_slots(sx_scene* s, const int32_t** diag)
+{
+    int rc = check_scene_ready(s);
+    if (rc != SX_OK) return rc;
+    if (diag) *diag = s->pat.diag_slot;
+    return SX_OK;
+}
+
+int sx_copy_bsr(sx_scene* s, int32_t* row_ptr, int32_t* col, void* vals, int* dtype,
+                void* stream)
+{
+    int rc = check_scene_ready(s);
+    if (rc != SX_OK) return rc;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (row_ptr)
+        CK(cudaMemcpyAsync(row_ptr, s->pat.row_ptr, (s->N + 1) * sizeof(int32_t),
+                           cudaMemcpyDefault, st));
+    if (col)
+        CK(cudaMemcpyAsync(col, s->pat.col, s->pat.nnzb * sizeof(int32_t), cudaMemcpyDefault, st));
+    if (dtype) *dtype = s->last_precision;
+    if (vals) {
+        if (s->last_precision == SX_FP32)
+            CK(cudaMemcpyAsync(vals, s->vals32, 9 * s->pat.nnzb * sizeof(float), cudaMemcpyDefault,
+                               st));
+        else
+            CK(cudaMemcpyAsync(vals, s->vals64, 9 * s->pat.nnzb * sizeof(double),
+                               cudaMemcpyDefault, st));
+    }
+    return SX_OK;
+}
+
+int sx_copy_grad(sx_scene* s, double* grad, void* stream)
+{
+    int rc = check_scene_ready(s);
+    if (rc != SX_OK) return rc;
+    sx_ctx* ctx = s->ctx;
+    if (grad)
+        CK(cudaMemcpyAsync(grad, s->grad, 3 * s->N * sizeof(double), cudaMemcpyDefault,
+                           (cudaStream_t)stream));
+    return SX_OK;
+}
+
+int sx_scene_info(sx_scene* s, int64_t* n_nodes, int64_t* nnzb, int64_t* n_stencils,
+                  int* n_blocks)
+{
+    if (!s) return SX_EINVAL;
+    if (n_nodes) *n_nodes = s->N;
+    if (nnzb) *nnzb = s->finalized ? s->pat.nnzb : 0;
+    if (n_stencils) *n_stencils = s->nst;
+    if (n_blocks) *n_blocks = (int)s->blocks.size();
+    return SX_OK;
+}
+
+int sx_block_info(sx_scene* s, int energy_id, int* kind, int64_t* n)
+{
+    if (!s || energy_id < 0 || energy_id >= (int)s->blocks.size()) return SX_EINVAL;
+    if (kind) *kind = s->blocks[energy_id].kind;
+    if (n) *n = s->blocks[energy_id].n;
+    return SX_OK;
+}
+
+int sx_eval_stats(sx_scene* s, int* clamped, int* bad_state, int* nonfinite, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    SceneScal h{};
+    CK(cudaMemcpyAsync(&h, s->sc, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (clamped) *clamped = h.clamped;
+    if (bad_state) *bad_state = h.bad_state;
+    if (nonfinite) *nonfinite = h.nonfinite;
+    return SX_OK;
+}
+
+int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, double* E,
+                     double* g, double* H, int32_t* slots, void* stream)
+{
+    int rc = check_scene_ready(s);
+    if (rc != SX_OK) return rc;
+    sx_ctx* ctx = s->ctx;
+    if (energy_id < 0 || energy_id >= (int)s->blocks.size())
+        return fail(ctx, SX_EINVAL, "eval_elements: bad energy id");
+    if (precision != SX_FP64 && precision != SX_FP32)
+        return fail(ctx, SX_EINVAL, "eval_elements: bad precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    const BlockHost& b = s->blocks[energy_id];
+    if (slots && b.n)
+        CK(cudaMemcpyAsync(slots, s->pat.slots + 16 * b.base, b.n * 16 * sizeof(int32_t),
+                           cudaMemcpyDeviceToDevice, st));
+    if (!E && !g && !H) return SX_OK;
+    sx_scene* arr[1] = {s};
+    Batch* B = get_batch(ctx, arr, 1);
+    if ((rc = prepare_batch(ctx, B, st)) != SX_OK) return rc;
+    std::vector<int> act(1, 1);
+    if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
+    std::vector<Tile> tiles;
+    const int et = elements_block_threads();
+    for (int64_t k = 0; k < b.n; k += et)
+        tiles.push_back(Tile{0, energy_id, k, (int)std::min<int64_t>(et, b.n - k), 0});
+    Tile* d_tiles = nullptr;
+    if ((rc = upload(ctx, &d_tiles, tiles, st)) != SX_OK) return rc;
+    double* tmpE = nullptr;
+    if (!E) CK(cudaMallocAsync((void**)&tmpE, std::max<int64_t>(b.n, 1) * sizeof(double), st));
+    ElemLaunch L{};
+    L.scenes = B->d_desc;
+    L.tiles = d_tiles;
+    L.ntiles = (int)tiles.size();
+    L.level = H ? 2 : (g ? 1 : 0);
+    L.project = project;
+    L.precision = precision;
+    L.queue = ctx->queue;
+    L.out_E = E ? E : tmpE;
+    double* scratch_g = nullptr;
+    if (!g && H) CK(cudaMallocAsync((void**)&scratch_g, std::max<int64_t>(b.n, 1) * 12 * sizeof(double), st));
+    L.out_g = g ? g : scratch_g;
+    L.out_H = H;
+    int grid = std::min<int>(L.ntiles, ctx->sm_count * ctx->elem_blocks_per_sm[precision == SX_FP32]);
+    CK(launch_elements(L, std::max(grid, 1), st));
+    CK(cudaStreamSynchronize(st));
+    cudaFree(d_tiles);
+    if (tmpE) cudaFree(tmpE);
+    if (scratch_g) cudaFree(scratch_g);
+    return SX_OK;
+}
+
+void sx_newton_opts_default(sx_newton_opts* o)
+{
+    if (!o) return;
+    o->newton_tol = 1e-8;
+    o->pcg_tol = 1e-10;
+    o->max_newton = 100;
+    o->max_pcg = 10000;
+    o->max_halvings = 30;
+    o->project = 1;
+    o->precision = SX_FP64;
+    o->armijo_c = 1e-4;
+}
+
+int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
+                         const sx_newton_opts* opts_in, sx_step_report* reports, void* stream)
+{
+    if (!ctx || !scenes || n <= 0 || !(dt > 0.0)) return SX_EINVAL;
+    sx_newton_opts o;
+    if (opts_in) o = *opts_in;
+    else sx_newton_opts_default(&o);
+    cudaStream_t st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < n; ++i) {
+        int rc = check_scene_ready(scenes[i]);
+        if (rc != SX_OK) return rc;
+        if (o.precision == SX_FP32 && (rc = ensure_vals32(ctx, scenes[i])) != SX_OK) return rc;
+        sx_scene* s = scenes[i];
+        if (!s->inertia_on || s->dt != dt || s->inertia_mode != 1) s->version++;
+        s->inertia_on = true;
+        s->inertia_mode = 1;
+        s->dt = dt;
+    }
+    Batch* B = get_batch(ctx, scenes, n);
+    int rc = prepare_batch(ctx, B, st);
+    if (rc != SX_OK) return rc;
+    const int nnt = (int)B->node_tiles.size();
+    std::vector<int> done(n, 0), status(n, SX_OK), iters(n, 0), pcg_it(n, 0), halv(n, 0);
+    std::vector<double> g0(n, 0.0), gl(n, 0.0), E(n, 0.0);
+    std::vector<int> act(n, 1);
+    if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
+    CK(launch_predict(B->d_desc, B->d_node, nnt, st));
+    for (int it = 0; it <= o.max_newton; ++it) {
+        for (int i = 0; i < n; ++i) act[i] = !done[i];
+        if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
+        if ((rc = run_eval(ctx, B, SX_EGH, o.project, o.precision, false, st)) != SX_OK) return rc;
+        if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
+        int live = 0;
+        for (int i = 0; i < n; ++i) {
+            if (done[i]) continue;
+            const SceneScal& sc = B->h_scal[i];
+            E[i] = sc.E;
+            if (sc.nonfinite || !std::isfinite(sc.E)) { status[i] = SX_ENAN; done[i] = 1; continue; }
+            if (sc.bad_state) { status[i] = SX_ESTATE; done[i] = 1; continue; }
+            double gn = std::sqrt(sc.gnorm2);
+            gl[i] = gn;
+            if (it == 0) g0[i] = gn;
+            if (gn <= o.newton_tol * std::max(g0[i], 1e-30)) { done[i] = 1; continue; }
+            if (it == o.max_newton) { status[i] = SX_ENOTCONV; done[i] = 1; continue; }
+            iters[i] = it + 1;
+            ++live;
+        }
+        if (!live) break;
+        for (int i = 0; i < n; ++i) act[i] = !done[i];
+        if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
+        // ---- PCG on H dx = -g
+        CK(launch_pcg_setup_p(B->d_desc, B->d_node, nnt, o.precision, B->d_part_node, st));
+        CK(launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg, B->d_node_end, n, B->d_desc, 0,
+                             o.pcg_tol, o.max_pcg, st));
+        int par = 0;
+        for (int k = 0;; k += 8) {
+            for (int j = 0; j < 8; ++j) {
+                CK(launch_spmv_pq(B->d_desc, B->d_node, nnt, o.precision, par, B->d_part_node, st));
+                CK(launch_pcg_reduce(B->d_part_node, 1, B->d_node_beg, B->d_node_end, n,
+                                     B->d_desc, 1, o.pcg_tol, o.max_pcg, st));
+                CK(launch_pcg_update(B->d_desc, B->d_node, nnt, par, B->d_part_node, st));
+                CK(launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg, B->d_node_end, n,
+                                     B->d_desc, 2, o.pcg_tol, o.max_pcg, st));
+                par ^= 1;
+            }
+            if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
+            bool all = true;
+            for (int i = 0; i < n; ++i)
+                if (act[i] && !B->h_scal[i].pcg_done) all = false;
+            if (all) break;
+        }
+        for (int i = 0; i < n; ++i) {
+            if (!act[i]) continue;
+            pcg_it[i] += B->h_scal[i].pcg_iters;
+            if (B->h_scal[i].pcg_status != 0) {
+                status[i] = SX_ENOTCONV;
+                done[i] = 1;
+                act[i] = 0;
+            }
+        }
+        if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
+        // ---- Armijo backtracking on E_BE
+        CK(launch_gdx(B->d_desc, B->d_node, nnt, B->d_part_node, st));
+        CK(launch_scene_reduce(B->d_part_node, 1, 0, B->d_node_beg, B->d_node_end, n, B->d_desc,
+                               F_GDX, 0, st));
+        if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
+        std::vector<double> gdx(n), alpha(n, 1.0);
+        for (int i = 0; i < n; ++i) gdx[i] = B->h_scal[i].gdx;
+        std::vector<int> search = act;
+        for (int h = 0; h <= o.max_halvings; ++h) {
+            bool any = false;
+            for (int i = 0; i < n; ++i) any |= search[i] != 0;
+            if (!any) break;
+            if ((rc = set_active(ctx, B, search, st)) != SX_OK) return rc;
+            if ((rc = set_alpha(ctx, B, alpha, st)) != SX_OK) return rc;
+            CK(launch_trial(B->d_desc, B->d_node, nnt, st));
+            if ((rc = run_eval(ctx, B, SX_E, 0, o.precision, true, st)) != SX_OK) return rc;
+            if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
+            std::vector<int> acc(n, 0);
+            for (int i = 0; i < n; ++i) {
+                if (!search[i]) continue;
+                const SceneScal& sc = B->h_scal[i];
+                bool ok = sc.bad_state == 0 && sc.nonfinite == 0 && std::isfinite(sc.E) &&
+                          sc.E <= E[i] + o.armijo_c * alpha[i] * gdx[i];
+                if (ok) {
+                    acc[i] = 1;
+                    search[i] = 0;
+                } else {
+                    alpha[i] *= 0.5;
+                    halv[i] += 1;
+                }
+            }
+            if ((rc = set_active(ctx, B, acc, st)) != SX_OK) return rc;
+            CK(launch_accept(B->d_desc, B->d_node, nnt, st));
+        }
+        for (int i = 0; i < n; ++i)
+            if (search[i]) {
+                status[i] = SX_ELINESEARCH;
+                done[i] = 1;
+            }
+    }
+    std::vector<int> all(n, 1);
+    if ((rc = set_active(ctx, B, all, st)) != SX_OK) return rc;
+    CK(launch_velocity(B->d_desc, B->d_node, nnt, st));
+    CK(cudaStreamSynchronize(st));
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    int worst = SX_OK;
+    for (int i = 0; i < n; ++i) {
+        if (reports) {
+            sx_step_report& r = reports[i];
+            r.status = status[i];
+            r.newton_iters = iters[i];
+            r.pcg_iters = pcg_it[i];
+            r.ls_halvings = halv[i];
+            r.g0_norm = g0[i];
+            r.g_norm = gl[i];
+            r.energy = E[i];
+            r.ms = ms;
+        }
+        if (status[i] != SX_OK) worst = status[i];
+    }
+    if (worst != SX_OK) fail(ctx, worst, "newton_step: at least one scene did not converge");
+    return worst;
+}
+
+int sx_newton_step(sx_scene* s, double dt, const sx_newton_opts* opts, sx_step_report* report,
+                   void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_scene* arr[1] = {s};
+    return sx_newton_step_batch(s->ctx, arr, 1, dt, opts, report, stream);
+}
+
+int sx_scene_footprint(const sx_scene_desc* d, int64_t* bytes)
+{
+    if (!d || !bytes) return SX_EINVAL;
+    const int64_t N = d->n_nodes, nst = d->n_tets + d->n_hinges + d->n_pairs;
+    int64_t nnzb = d->nnzb_hint > 0 ? d->nnzb_hint : N + 16 * nst;
+    int64_t b = 0;
+    b += N * (3 * 8 * 13 + 8 * 2 + 1 + 9 * 8 + 8 * 2);    // node vectors, mass, pins, Minv, ptrs
+    b += d->n_tets * (16 + 12 * 8);                         // conn + rest params
+    b += d->n_hinges * (16 + 5 * 8);
+    b += d->n_pairs * 16;
+    b += nst * (8 + 12 * 8 + 90 * 8 + 16 * 4 * 2 + 4 * 4); // staging, slots, lists
+    b += nnzb * (4 + 4 + 9 * 8);                            // col, slot_ptr, values
+    b += 1 << 20;
+    *bytes = b;
+    return SX_OK;
+}
+
+int sx_scene_bytes(sx_scene* s, int64_t* bytes)
+{
+    if (!s || !bytes) return SX_EINVAL;
+    *bytes = s->bytes;
+    return SX_OK;
+}
+
+}  // extern "C"

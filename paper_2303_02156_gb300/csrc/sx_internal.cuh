@@ -1,0 +1,229 @@
+// sx_internal.cuh -- internal types shared by the libsx translation units.
+//
+// Data model (device, per scene; AoS xyz per node, SoA per-element params):
+//   x, v, x_start, x_tilde, x_trial, dx, grad, r, z, p0, p1, q : double[3N]
+//   mass : double[N];  pinned : uint8[N];  Minv : double[9N]
+//   energy blocks: conn int4[n]; SNH Dm^-1 double[9][n], V, mu', lambda'
+//                  double[n]; hinge q double[4][n], c double[n]
+//   staged element outputs: E_e double[nst]; g_e double[nst][12];
+//                           H_e (double|float)[nst][90] = 10 upper 3x3 blocks
+//   pattern: row_ptr int[N+1], col int[nnzb], diag_slot int[N],
+//            slots int[nst][16]
+//   assembly lists (element-id ordered): slot_ptr int[nnzb+1],
+//            slot_src int[nst*16] (code 16*stencil + 4a + b),
+//            node_ptr int[N+1], node_src int[nst*4] (code 4*stencil + a)
+//   BSR values: double[nnzb][9] (FP64) and float[nnzb][9] (FP32 form)
+//
+// Kernels are written over "tiles" (scene, block, start, count) so that a
+// single scene, a batch of scenes and the server's mixes all run through
+// the same launches; per-tile partial sums are reduced per scene in a fixed
+// order, so every result is deterministic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sx.h"
+
+#define SX_MAX_BLOCKS 8
+
+namespace sx {
+
+// upper 3x3 blocks of a 4-node stencil Hessian, in staging order
+__host__ __device__ constexpr int up_index(int a, int b)
+{
+    // (0,0)=0 (0,1)=1 (0,2)=2 (0,3)=3 (1,1)=4 (1,2)=5 (1,3)=6 (2,2)=7 (2,3)=8 (3,3)=9
+    return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
+}
+
+struct ElemBlock {
+    int kind;            // SX_KIND_*
+    int64_t n;           // stencils in this block
+    int64_t base;        // first scene-global stencil id of this block
+    const int4* conn;
+    // SNH tet4
+    const double* Dminv;  // [9][n] row-major Dm^-1 entries
+    const double* V;
+    const double* mu;
+    const double* lam;
+    // hinge
+    const double* q;      // [4][n]
+    const double* c;
+    double kb;
+    // barrier
+    double dhat, kappa;
+};
+
+// per-scene scalars the device loops read and write
+struct SceneScal {
+    double E;          // energy of the last evaluation
+    double gnorm2;     // ||g_free||^2 of the last EG/EGH evaluation
+    double bnorm2;     // PCG: ||b||^2
+    double rz;         // PCG: r.z
+    double rz_new;
+    double pq;         // PCG: p.Aq
+    double rr;         // PCG: ||r||^2
+    double gdx;        // Newton: g.dx
+    double pcg_alpha;
+    double pcg_beta;
+    double ls_alpha;   // line-search step
+    double grav[3];    // external acceleration (M^-1 f_ext)
+    int pcg_done;      // 1 once converged or stopped (kernels skip the scene)
+    int pcg_iters;
+    int pcg_status;    // 0 ok, 1 breakdown (p.Ap <= 0), 2 iteration cap
+    int active;        // scene takes part in the current batched phase
+    int bad_state;     // barrier pairs with d <= 0 in the last evaluation
+    int nonfinite;     // non-finite values seen in the last evaluation
+    int clamped;       // elements projected in the last EGH evaluation
+    int pad;
+};
+
+struct SceneDev {
+    int64_t N;
+    int64_t nst;
+    int64_t nnzb;
+    int nblocks;
+    int inertia_on;
+    int inertia_mode;   // 0: residual x - x_tilde; 1: (x - x_start) - (dt v + dt^2 g)
+    int pad0;
+    double dt;
+    double inv_dt2;
+    ElemBlock blk[SX_MAX_BLOCKS];
+    double* x;
+    double* v;
+    double* x_start;
+    double* x_tilde;
+    double* x_trial;
+    double* dx;
+    double* mass;
+    const uint8_t* pinned;
+    double* grad;
+    double* Ee;
+    double* ge;
+    void* He;
+    const int* row_ptr;
+    const int* col;
+    const int* diag_slot;
+    const int* slots;
+    const int* slot_ptr;
+    const int* slot_src;
+    const int* node_ptr;
+    const int* node_src;
+    double* vals64;
+    float* vals32;
+    double* r;
+    double* z;
+    double* p0;
+    double* p1;
+    double* q;
+    double* Minv;
+    SceneScal* sc;
+};
+
+struct Tile {
+    int scene;   // index into the batch's SceneDev array
+    int blk;     // energy block (element tiles) or unused
+    int64_t start;
+    int count;
+    int pad;
+};
+
+// ---------------------------------------------------------------- kernels
+// element evaluation (sx_elements.cu)
+struct ElemLaunch {
+    const SceneDev* scenes;
+    const Tile* tiles;
+    int ntiles;
+    int level;
+    int project;
+    int precision;
+    double* tile_E;       // per tile energy partial
+    int* tile_bad;        // per tile barrier d<=0 count
+    int* tile_nonfinite;
+    int* tile_clamped;    // per tile number of projected elements
+    int* queue;           // work counter for the persistent launch
+    // element-level output mode (sx_eval_elements): when non-null the
+    // kernel writes E, g (12) and the full 12x12 H per element of the
+    // block (indexed by the element's position in its block) instead of
+    // the staged assembly buffers
+    double* out_E;
+    double* out_g;
+    double* out_H;
+};
+cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s);
+int elements_block_threads();
+const void* elements_kernel(int precision);
+
+// registration and pattern (sx_graph.cu)
+cudaError_t launch_snh_rest(const double* X, int64_t N, const int4* tets, int64_t n,
+                            const double* young, const double* poisson, double rho,
+                            int literal, double* Dminv, double* V, double* mu,
+                            double* lam, int* bad, cudaStream_t s);
+cudaError_t launch_block_mass(const int* node_ptr, const int* node_src, int64_t N,
+                              int64_t base, int64_t cnt, const double* V, double rho,
+                              double* mass, cudaStream_t s);
+struct PatternOut {
+    int* row_ptr;
+    int* col;
+    int64_t nnzb;
+    int* diag_slot;
+    int* slots;
+    int* slot_ptr;
+    int* slot_src;
+    int* node_ptr;
+    int* node_src;
+};
+int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
+                  std::string* err, cudaStream_t s);
+
+// assembly and reductions (sx_assemble.cu)
+struct AsmLaunch {
+    const SceneDev* scenes;
+    const Tile* tiles;
+    int ntiles;
+    int precision;
+};
+cudaError_t launch_assemble_vals(const AsmLaunch& L, cudaStream_t s);
+cudaError_t launch_inertia_diag(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                                int precision, cudaStream_t s);
+cudaError_t launch_assemble_grad(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                                 double* tile_part, cudaStream_t s);
+cudaError_t launch_inertia_energy(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                                  const double* unused, double* tile_part, int use_trial,
+                                  cudaStream_t s);
+enum ScalField { F_E = 0, F_GNORM2 = 1, F_GDX = 2 };
+cudaError_t launch_scene_reduce(const double* part, int stride, int off, const int* tbeg,
+                                const int* tend, int nscenes, const SceneDev* scenes,
+                                int field, int accumulate, cudaStream_t s);
+cudaError_t launch_scene_reduce_flags(const int* bad, const int* nonfin, const int* clamped,
+                                      const int* tbeg, const int* tend, int nscenes,
+                                      const SceneDev* scenes, cudaStream_t s);
+cudaError_t launch_gather_scal(const SceneDev* scenes, int n, SceneScal* out, cudaStream_t s);
+cudaError_t launch_set_scal(const SceneDev* scenes, int n, const int* active,
+                            const double* ls_alpha, cudaStream_t s);
+
+// solver (sx_solve.cu)
+cudaError_t launch_predict(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                           cudaStream_t s);
+cudaError_t launch_pcg_setup_p(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                               int precision, double* part, cudaStream_t s);
+cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int ntiles,
+                           int precision, int parity, double* part, cudaStream_t s);
+cudaError_t launch_pcg_update(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                              int parity, double* part, cudaStream_t s);
+cudaError_t launch_pcg_reduce(const double* part, int nv, const int* tbeg, const int* tend,
+                              int nscenes, const SceneDev* scenes, int stage, double tol,
+                              int max_iter, cudaStream_t s);
+cudaError_t launch_gdx(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                       double* part, cudaStream_t s);
+cudaError_t launch_trial(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                         cudaStream_t s);
+cudaError_t launch_accept(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                          cudaStream_t s);
+cudaError_t launch_velocity(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                            cudaStream_t s);
+
+}  // namespace sx

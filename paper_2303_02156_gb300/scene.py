@@ -1,0 +1,213 @@
+"""Thin object wrapper over the C ABI (include/sx.h) for Python callers.
+
+Marshalling only: numpy inputs are passed as host pointers (the library
+copies them to the device), element-level outputs land in torch CUDA
+tensors, and every computation happens inside libsx.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import sx
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        opt = sx.sx_options()
+        opt.device = device
+        h = C.c_void_p()
+        rc = sx.sx_create(C.byref(h), C.byref(opt))
+        if rc != sx.SX_OK:
+            raise sx.SxError(rc, "sx_create failed (no CUDA device?)")
+        self.h = h
+
+    def check(self, rc):
+        return sx.check(self.h, rc)
+
+    def close(self):
+        if self.h:
+            sx.sx_destroy(self.h)
+            self.h = None
+
+    def eval_batch(self, scenes, level=sx.SX_EGH, project=True, precision=sx.SX_FP64,
+                   stream=0, want_energy=True):
+        arr = (C.c_void_p * len(scenes))(*[s.h.value for s in scenes])
+        E = (C.c_double * len(scenes))()
+        rc = sx.sx_eval_batch(self.h, arr, len(scenes), level, int(project), precision,
+                              E if want_energy else None, stream)
+        self.check(rc)
+        return np.array(E[:]) if want_energy else None
+
+    def newton_step_batch(self, scenes, dt, stream=0, raise_on_error=True, **opts):
+        arr = (C.c_void_p * len(scenes))(*[s.h.value for s in scenes])
+        reps = (sx.sx_step_report * len(scenes))()
+        o = sx.newton_opts(**opts)
+        rc = sx.sx_newton_step_batch(self.h, arr, len(scenes), float(dt), C.byref(o), reps,
+                                     stream)
+        if raise_on_error:
+            self.check(rc)
+        return rc, [_rep(r) for r in reps]
+
+
+def _rep(r):
+    return {k: getattr(r, k) for k, _ in sx.sx_step_report._fields_}
+
+
+class Scene:
+    """One scene: a DOF set of n nodes with energy blocks."""
+
+    def __init__(self, ctx: Context, X, stream=0):
+        X = _f64(X).reshape(-1, 3)
+        self.ctx = ctx
+        self.N = X.shape[0]
+        self.stream = stream
+        h = C.c_void_p()
+        ctx.check(sx.sx_scene_create(ctx.h, self.N, X.ctypes.data, 3, stream, C.byref(h)))
+        self.h = h
+        self.blocks = []
+
+    def close(self):
+        if self.h:
+            sx.sx_scene_destroy(self.h)
+            self.h = None
+
+    def _id(self, rc, eid, kind, n):
+        self.ctx.check(rc)
+        self.blocks.append((kind, n))
+        return eid.value
+
+    def add_snh(self, tets, young, poisson, density=1000.0, literal=False):
+        tets = _i32(tets); n = tets.shape[0]
+        E = _f64(np.broadcast_to(young, (n,))); nu = _f64(np.broadcast_to(poisson, (n,)))
+        eid = C.c_int()
+        rc = sx.sx_add_snh_tet4(self.h, tets.ctypes.data, n, E.ctypes.data, nu.ctypes.data,
+                                float(density), int(literal), self.stream, C.byref(eid))
+        return self._id(rc, eid, sx.SX_KIND_SNH_TET4, n)
+
+    def add_hinge(self, stencils, q, c, kb):
+        st = _i32(stencils); n = st.shape[0]
+        q = _f64(q); c = _f64(c)
+        eid = C.c_int()
+        rc = sx.sx_add_hinge4(self.h, st.ctypes.data, n, q.ctypes.data, c.ctypes.data,
+                              float(kb), self.stream, C.byref(eid))
+        return self._id(rc, eid, sx.SX_KIND_HINGE4, n)
+
+    def add_barrier(self, pairs, dhat, kappa):
+        pr = _i32(pairs); n = pr.shape[0]
+        eid = C.c_int()
+        rc = sx.sx_add_pt_barrier(self.h, pr.ctypes.data, n, float(dhat), float(kappa),
+                                  self.stream, C.byref(eid))
+        return self._id(rc, eid, sx.SX_KIND_PT_BARRIER, n)
+
+    def add_node_mass(self, m):
+        m = _f64(m)
+        self.ctx.check(sx.sx_add_node_mass(self.h, m.ctypes.data, self.stream))
+
+    def set_pinned(self, nodes):
+        nd = _i32(nodes)
+        self.ctx.check(sx.sx_set_pinned(self.h, nd.ctypes.data if nd.size else None, nd.size,
+                                        self.stream))
+
+    def set_gravity(self, g):
+        arr = (C.c_double * 3)(*[float(v) for v in g])
+        self.ctx.check(sx.sx_set_gravity(self.h, arr))
+
+    def finalize(self):
+        self.ctx.check(sx.sx_finalize(self.h, self.stream))
+
+    def set_state(self, x=None, v=None):
+        x = None if x is None else _f64(x)
+        v = None if v is None else _f64(v)
+        self.ctx.check(sx.sx_set_state(self.h, sx.ptr(x), sx.ptr(v), self.stream))
+
+    def get_state(self):
+        x = np.empty((self.N, 3)); v = np.empty((self.N, 3))
+        self.ctx.check(sx.sx_get_state(self.h, x.ctypes.data, v.ctypes.data, self.stream))
+        return x, v
+
+    def set_inertia(self, dt, x_tilde):
+        xt = None if x_tilde is None else _f64(x_tilde)
+        self.ctx.check(sx.sx_set_inertia(self.h, float(dt), sx.ptr(xt), self.stream))
+
+    def eval(self, level=sx.SX_EGH, project=True, precision=sx.SX_FP64, check=True):
+        E = C.c_double()
+        rc = sx.sx_eval(self.h, level, int(project), precision, C.byref(E), self.stream)
+        if check:
+            self.ctx.check(rc)
+            return E.value
+        return rc, E.value
+
+    def stats(self):
+        c, b, nf = C.c_int(), C.c_int(), C.c_int()
+        self.ctx.check(sx.sx_eval_stats(self.h, C.byref(c), C.byref(b), C.byref(nf),
+                                        self.stream))
+        return {"clamped": c.value, "bad_state": b.value, "nonfinite": nf.value}
+
+    def info(self):
+        n, nnz, nst, nb = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int()
+        self.ctx.check(sx.sx_scene_info(self.h, C.byref(n), C.byref(nnz), C.byref(nst),
+                                        C.byref(nb)))
+        return {"n_nodes": n.value, "nnzb": nnz.value, "n_stencils": nst.value,
+                "n_blocks": nb.value}
+
+    def bsr(self):
+        inf = self.info()
+        rp = np.empty(self.N + 1, dtype=np.int32)
+        col = np.empty(inf["nnzb"], dtype=np.int32)
+        dt = C.c_int()
+        self.ctx.check(sx.sx_copy_bsr(self.h, rp.ctypes.data, col.ctypes.data, None,
+                                      C.byref(dt), self.stream))
+        vals = np.empty((inf["nnzb"], 3, 3),
+                        dtype=np.float32 if dt.value == sx.SX_FP32 else np.float64)
+        self.ctx.check(sx.sx_copy_bsr(self.h, None, None, vals.ctypes.data, None,
+                                      self.stream))
+        return rp, col, vals
+
+    def grad(self):
+        g = np.empty(3 * self.N)
+        self.ctx.check(sx.sx_copy_grad(self.h, g.ctypes.data, self.stream))
+        return g
+
+    def eval_elements(self, energy_id, project=True, precision=sx.SX_FP64, want_H=True,
+                      want_g=True):
+        import torch
+        kind, n = self.blocks[energy_id]
+        dev = torch.device("cuda")
+        E = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+        g = torch.empty((max(n, 1), 12), dtype=torch.float64, device=dev) if want_g else None
+        H = torch.empty((max(n, 1), 12, 12), dtype=torch.float64, device=dev) if want_H else None
+        sl = torch.empty((max(n, 1), 16), dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        self.ctx.check(sx.sx_eval_elements(self.h, energy_id, int(project), precision,
+                                           sx.ptr(E), sx.ptr(g), sx.ptr(H), sx.ptr(sl),
+                                           self.stream))
+        torch.cuda.synchronize()
+        out = {"E": E[:n].cpu().numpy(), "slots": sl[:n].cpu().numpy()}
+        if want_g:
+            out["g"] = g[:n].cpu().numpy()
+        if want_H:
+            out["H"] = H[:n].cpu().numpy()
+        return out
+
+    def newton_step(self, dt, raise_on_error=True, **opts):
+        o = sx.newton_opts(**opts)
+        r = sx.sx_step_report()
+        rc = sx.sx_newton_step(self.h, float(dt), C.byref(o), C.byref(r), self.stream)
+        if raise_on_error:
+            self.ctx.check(rc)
+        return rc, _rep(r)
+
+    def nbytes(self):
+        b = C.c_int64()
+        self.ctx.check(sx.sx_scene_bytes(self.h, C.byref(b)))
+        return b.value

@@ -1,0 +1,166 @@
+"""ctypes binding of libsx (include/sx.h).
+
+Argument marshalling only: every function below forwards to the C entry
+point of the same name, and every step of the numerical path runs in the
+library's CUDA kernels. Device memory comes from torch tensors
+(``tensor.data_ptr()``). Importing works without a GPU; any call that
+needs the library raises ``RuntimeError`` when ``libsx.so`` is missing,
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsx.so")
+
+SX_OK, SX_EINVAL, SX_ENOMEM, SX_ECUDA, SX_ENAN = 0, -1, -2, -3, -4
+SX_ENOTCONV, SX_ESTATE, SX_EDEGENERATE, SX_EBUDGET, SX_ELINESEARCH, SX_EORDER = (
+    -5, -6, -7, -8, -9, -10)
+SX_E, SX_EG, SX_EGH = 0, 1, 2
+SX_FP64, SX_FP32 = 0, 1
+SX_KIND_SNH_TET4, SX_KIND_HINGE4, SX_KIND_PT_BARRIER = 0, 1, 2
+
+STATUS_NAMES = {0: "SX_OK", -1: "SX_EINVAL", -2: "SX_ENOMEM", -3: "SX_ECUDA", -4: "SX_ENAN",
+                -5: "SX_ENOTCONV", -6: "SX_ESTATE", -7: "SX_EDEGENERATE", -8: "SX_EBUDGET",
+                -9: "SX_ELINESEARCH", -10: "SX_EORDER"}
+
+# every symbol include/sx.h declares
+EXPORTS = [
+    "sx_create", "sx_destroy", "sx_last_error", "sx_version", "sx_scene_create",
+    "sx_scene_destroy", "sx_add_snh_tet4", "sx_add_hinge4", "sx_add_pt_barrier",
+    "sx_add_node_mass", "sx_set_pinned", "sx_set_gravity", "sx_finalize", "sx_set_state",
+    "sx_get_state", "sx_set_inertia", "sx_eval", "sx_eval_batch", "sx_get_bsr",
+    "sx_get_grad", "sx_get_diag_slots", "sx_eval_elements", "sx_newton_opts_default",
+    "sx_newton_step", "sx_newton_step_batch", "sx_scene_footprint", "sx_scene_bytes",
+    "sx_copy_bsr", "sx_copy_grad", "sx_scene_info", "sx_block_info", "sx_eval_stats",
+]
+
+
+class sx_options(C.Structure):
+    _fields_ = [("device", C.c_int), ("reserved", C.c_int * 7)]
+
+
+class sx_newton_opts(C.Structure):
+    _fields_ = [("newton_tol", C.c_double), ("pcg_tol", C.c_double),
+                ("max_newton", C.c_int), ("max_pcg", C.c_int), ("max_halvings", C.c_int),
+                ("project", C.c_int), ("precision", C.c_int), ("armijo_c", C.c_double)]
+
+
+class sx_step_report(C.Structure):
+    _fields_ = [("status", C.c_int), ("newton_iters", C.c_int), ("pcg_iters", C.c_int),
+                ("ls_halvings", C.c_int), ("g0_norm", C.c_double), ("g_norm", C.c_double),
+                ("energy", C.c_double), ("ms", C.c_double)]
+
+
+class sx_scene_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_hinges", C.c_int64),
+                ("n_pairs", C.c_int64), ("nnzb_hint", C.c_int64)]
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_D = C.c_double
+_I = C.c_int
+_PP = C.POINTER(C.c_void_p)
+
+_SIGS = {
+    "sx_create": (_I, [_PP, _P]),
+    "sx_destroy": (_I, [_P]),
+    "sx_last_error": (C.c_char_p, [_P]),
+    "sx_version": (C.c_char_p, []),
+    "sx_scene_create": (_I, [_P, _I64, _P, _I64, _P, _PP]),
+    "sx_scene_destroy": (_I, [_P]),
+    "sx_add_snh_tet4": (_I, [_P, _P, _I64, _P, _P, _D, _I, _P, C.POINTER(_I)]),
+    "sx_add_hinge4": (_I, [_P, _P, _I64, _P, _P, _D, _P, C.POINTER(_I)]),
+    "sx_add_pt_barrier": (_I, [_P, _P, _I64, _D, _D, _P, C.POINTER(_I)]),
+    "sx_add_node_mass": (_I, [_P, _P, _P]),
+    "sx_set_pinned": (_I, [_P, _P, _I64, _P]),
+    "sx_set_gravity": (_I, [_P, C.POINTER(_D)]),
+    "sx_finalize": (_I, [_P, _P]),
+    "sx_set_state": (_I, [_P, _P, _P, _P]),
+    "sx_get_state": (_I, [_P, _P, _P, _P]),
+    "sx_set_inertia": (_I, [_P, _D, _P, _P]),
+    "sx_eval": (_I, [_P, _I, _I, _I, C.POINTER(_D), _P]),
+    "sx_eval_batch": (_I, [_P, C.POINTER(_P), _I, _I, _I, _I, C.POINTER(_D), _P]),
+    "sx_get_bsr": (_I, [_P, _PP, _PP, _PP, C.POINTER(_I64), C.POINTER(_I)]),
+    "sx_get_grad": (_I, [_P, _PP]),
+    "sx_get_diag_slots": (_I, [_P, _PP]),
+    "sx_eval_elements": (_I, [_P, _I, _I, _I, _P, _P, _P, _P, _P]),
+    "sx_newton_opts_default": (None, [C.POINTER(sx_newton_opts)]),
+    "sx_newton_step": (_I, [_P, _D, C.POINTER(sx_newton_opts), C.POINTER(sx_step_report), _P]),
+    "sx_newton_step_batch": (_I, [_P, C.POINTER(_P), _I, _D, C.POINTER(sx_newton_opts),
+                                  C.POINTER(sx_step_report), _P]),
+    "sx_scene_footprint": (_I, [C.POINTER(sx_scene_desc), C.POINTER(_I64)]),
+    "sx_scene_bytes": (_I, [_P, C.POINTER(_I64)]),
+    "sx_copy_bsr": (_I, [_P, _P, _P, _P, C.POINTER(_I), _P]),
+    "sx_copy_grad": (_I, [_P, _P, _P]),
+    "sx_scene_info": (_I, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I)]),
+    "sx_block_info": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I64)]),
+    "sx_eval_stats": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), _P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsx.so and declare every signature. Raises RuntimeError if
+    the library was not built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "libsx.so not found at %s: build it with __graft_entry__.build() "
+            "(or python -m paper_2303_02156_gb300.build); there is no CPU fallback" % path)
+    L = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+class SxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+def check(ctx, rc):
+    if rc != SX_OK:
+        msg = load().sx_last_error(ctx).decode() if ctx else ""
+        raise SxError(rc, msg)
+    return rc
+
+
+def _def(name):
+    def f(*args):
+        return getattr(load(), name)(*args)
+    f.__name__ = name
+    f.__doc__ = "Forwards to the C entry point %s (include/sx.h)." % name
+    return f
+
+
+for _n in _SIGS:
+    globals()[_n] = _def(_n)
+
+
+# ---------------------------------------------------------------- helpers
+def ptr(t):
+    """Device (or host) address of a torch tensor / numpy array, or None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def newton_opts(**kw):
+    o = sx_newton_opts()
+    load().sx_newton_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
