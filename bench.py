@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path on one (or N) GB300.
+
+Metric: elements/s for E + grad + SPD-projected Hessian + BSR assembly
+(one ``sx_eval(SX_EGH, project=1)``: every SNH tet evaluated, its 12x12
+Hessian projected to PSD where it is indefinite, and all blocks gathered
+into the fixed-pattern 3x3 BSR matrix and the gradient).
+
+Workload: the 64^3 Kuhn cube (6 tets per cube: 1,572,864 Stable
+Neo-Hookean tets, 274,625 nodes, 4,018,753 BSR blocks), rest vertices
+jittered by U(+-0.1 h), per-element E log-uniform in [1e4, 1e6] Pa and nu
+uniform in [0.2, 0.45] (seed 2), evaluated at a deformed state (every node
+jittered by U(+-0.02 h), seed 5). FP64. Synthetic data.
+
+One step = one full pass over the mesh. Between timed steps L2 is flushed
+(a 256 MB device write); each step is timed with CUDA events on the
+library's stream. Also reported: ``e2e`` (the same pass through the C ABI
+with the state uploaded from and the energy + gradient read back to pinned
+host memory inside the timed region), a backward-Euler Newton step on the
+same cube from rest under gravity (dt = 0.005), the FP32 element-math form,
+the roofline of the dominant kernel, and the CPU oracle on a bounded sample.
+
+``--impl reference`` times the CPU oracle (oracle/) as it stands on the
+host cores, each step a bounded sample of the same workload.
+
+Under torchrun with N ranks every rank evaluates its own replica of the
+cube on its own GPU (independent scenes: no data exchange; "scaling":
+"weak"); rank 0 prints the line with value = N * tets * steps / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "elements/s for E+grad+SPD Hessian+BSR assembly; served Newton-step p50/p99 ms"
+UNIT = "elements/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x 2 flop x max clock
+CLAMP_FLOPS_PER_ELEMENT = 1.5e4                   # survey estimate of the 12x12 clamp
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--size", type=int, default=64)
+    p.add_argument("--no-newton", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=6.0)
+    return p.parse_args()
+
+
+def build_workload(n):
+    from paper_2303_02156_gb300 import scenes
+    m = scenes.kuhn_box(n, n, n, h=1.0 / n, seed=2)
+    T = m["tets"].shape[0]
+    E, nu = scenes.material_random(T, seed=2)
+    x = scenes.jitter_state(m["X"], 0.02 / n, seed=5)
+    return m, E, nu, x
+
+
+def workload_config(n, m, nnzb):
+    return {"workload": "snh_tet4_kuhn_cube_%d^3" % n, "tets": int(m["tets"].shape[0]),
+            "nodes": int(m["X"].shape[0]), "nnzb": int(nnzb), "material": "E~logU[1e4,1e6] Pa, nu~U[0.2,0.45]",
+            "state": "rest jitter 0.1h (seed 2) + deformation jitter 0.02h (seed 5)",
+            "precision": "fp64", "project": True, "l2": "flushed (256 MB write) between timed steps",
+            "seed": 2}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(m, E, nu, x, n_tets):
+    """Bounded sample of the workload for the CPU oracle: the first n_tets
+    tets (whole bottom layers of the cube) with their nodes."""
+    import numpy as np
+    from oracle import oracle as orc
+    tets = m["tets"][:n_tets]
+    used = np.unique(tets)
+    remap = -np.ones(m["X"].shape[0], dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    t2 = remap[tets].astype(np.int32)
+    X2 = m["X"][used]; x2 = x[used]
+    snh, mass, _ = orc.snh_scene_inputs(X2, t2, E[:n_tets], nu[:n_tets], 1000.0)
+    sc = orc.Scene(used.size, mass=mass, snh=snh)
+    return sc, x2
+
+
+def time_oracle(sc, x2, n_tets, seconds, min_reps=1):
+    from oracle import oracle as orc
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        sc.eval(x2, level=2, project=True)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if reps >= min_reps and dt >= seconds:
+            break
+    return n_tets * reps / dt, reps, dt, orc.num_threads()
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index=0):
+        self.samples, self.proc, self.index = [], None, index
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if len(s) >= 9 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) >= 9 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            if len(s) >= 9:
+                for k, nm in enumerate(names):
+                    if s[5 + k].lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ roofline traffic
+def clamp_traffic_per_element():
+    """DRAM bytes per projected stencil of the clamp kernel from the
+    committed ncu summary, if it was taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "k_clamp_snh_cube.md")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in ["sx_elements.cu", "sx_clamp.cuh"]:
+        h.update(open(os.path.join(ROOT, "paper_2303_02156_gb300", "csrc", f), "rb").read())
+    want = h.hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256_16") != want:
+        return None
+    try:
+        return float(vals["dram_bytes_per_projected_stencil"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    m, E, nu, x = build_workload(args.size)
+    n_tets = min(6 * args.size * args.size * 2, m["tets"].shape[0])   # two bottom layers
+    sc, x2 = oracle_sample(m, E, nu, x, n_tets)
+    for _ in range(args.warmup):
+        sc.eval(x2, level=2, project=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sc.eval(x2, level=2, project=True)
+    dt = time.perf_counter() - t0
+    from oracle import oracle as orc
+    value = n_tets * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.size, m, 0),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+                         "sample": "first %d tets (two bottom layers) of the cube, E+g+H+12x12 "
+                                   "Jacobi clamp+BSR assembly per step; host %s"
+                                   % (n_tets, cpu_model())},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_2303_02156_gb300 import sx
+    from paper_2303_02156_gb300.scene import Context, Scene
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    m, E, nu, x = build_workload(args.size)
+    T = m["tets"].shape[0]
+    N = m["X"].shape[0]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx = Context(local)
+    s = Scene(ctx, m["X"], stream=sh)
+    s.add_snh(m["tets"], E, nu, 1000.0)
+    s.set_pinned(m["pinned"])
+    s.set_gravity((0.0, 0.0, -9.81))
+    s.finalize()
+    s.set_state(x=x)
+    info = s.info()
+
+    def eval_async(prec=sx.SX_FP64):
+        rc = sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh)
+        if rc != sx.SX_OK:
+            ctx.check(rc)
+
+    for _ in range(args.warmup):
+        eval_async()
+    torch.cuda.synchronize()
+    st = s.stats()
+    clamped = st["clamped"]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sx.sx_profile(ctx.h, 1)
+    sx.sx_profile_read(ctx.h, None, None, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        eval_async()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_arr = (C.c_double * 9)()
+    ln_arr = (C.c_int64 * 9)()
+    sx.sx_profile_read(ctx.h, ms_arr, ln_arr, 1)
+    sx.sx_profile(ctx.h, 0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    phases = {sx.PHASES[i]: ms_arr[i] / args.steps for i in range(9)}
+    launches = int(sum(ln_arr))
+    value = world * T * args.steps / (total_ms / 1e3)
+
+    # ---- e2e through the C ABI with pinned host buffers
+    xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    gh = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+    Eh = C.c_double()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sx.sx_set_state(s.h, xh.data_ptr(), None, sh)
+        rc = sx.sx_eval(s.h, sx.SX_EGH, 1, sx.SX_FP64, C.byref(Eh), sh)
+        ctx.check(rc)
+        sx.sx_copy_grad(s.h, gh.data_ptr(), sh)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * T * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(gh.numel() * 8 + 8)}
+
+    # ---- FP32 element-math form and its deviation from the FP64 form
+    s.set_state(x=x)
+    s.eval(sx.SX_EGH, True, sx.SX_FP64)
+    rp, col, v64 = s.bsr()
+    g64 = s.grad()
+    for _ in range(3):
+        eval_async(sx.SX_FP32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f32_ms = 0.0
+    for _ in range(5):
+        flush.zero_()
+        e0.record(stream)
+        eval_async(sx.SX_FP32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f32_ms += e0.elapsed_time(e1)
+    f32_ms /= 5
+    _, _, v32 = s.bsr()
+    g32 = s.grad()
+    fp32 = {"elements_per_s": T / (f32_ms / 1e3), "ms_per_step": f32_ms,
+            "bsr_rel_err_vs_fp64": float(np.linalg.norm(v32.astype(np.float64) - v64) / np.linalg.norm(v64)),
+            "grad_rel_err_vs_fp64": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64))}
+
+    # ---- roofline of the dominant kernel (the FP64 eigen-clamp)
+    t_clamp = phases["clamp"] / 1e3
+    achieved = CLAMP_FLOPS_PER_ELEMENT * clamped / t_clamp / 1e12 if t_clamp > 0 else None
+    tpe = clamp_traffic_per_element()
+    roofline = {"bound": "alu", "kernel": "k_clamp (FP64 9x9 eigen-clamp)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "traffic": (tpe * clamped) if tpe else None,
+                "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s); "
+                               "probe-measured 1.198 TFLOP/s",
+                "units_per_launch": clamped, "flops_per_unit": CLAMP_FLOPS_PER_ELEMENT,
+                "avg_launch_ms": phases["clamp"]}
+
+    # ---- backward-Euler Newton step from rest under gravity
+    newton = None
+    if not args.no_newton:
+        s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+        sx.sx_profile(ctx.h, 1)
+        sx.sx_profile_read(ctx.h, None, None, 1)
+        rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-8, pcg_tol=1e-10)
+        sx.sx_profile_read(ctx.h, ms_arr, ln_arr, 1)
+        sx.sx_profile(ctx.h, 0)
+        newton = {"status": sx.STATUS_NAMES.get(rc, rc), "ms": rep["ms"],
+                  "newton_iters": rep["newton_iters"], "pcg_iters": rep["pcg_iters"],
+                  "phase_ms": {sx.PHASES[i]: round(ms_arr[i], 3) for i in range(9)},
+                  "dt": 0.005, "newton_tol": 1e-8, "pcg_tol": 1e-10}
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu and world == 1 and rank == 0:
+        n_tets = min(6 * args.size * args.size * 2, T)
+        sc, x2 = oracle_sample(m, E, nu, x, n_tets)
+        v, reps, dt, cores = time_oracle(sc, x2, n_tets, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "first %d tets (two bottom layers) of the cube, %d passes in %.1f s: "
+                         "E+g+H, 12x12 cyclic-Jacobi clamp, ordered BSR assembly; host %s"
+                         % (n_tets, reps, dt, cpu_model())}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(workload_config(args.size, m, info["nnzb"]),
+                                                parallelism="replicas" if world > 1 else "single"),
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "phase_ms_per_step": {k: round(v, 4) for k, v in phases.items()},
+            "projected_fraction": clamped / T, "fp32": fp32, "newton_step": newton,
+            "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
+                        "max": max(step_ms)},
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

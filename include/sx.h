@@ -253,6 +253,28 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
                          const sx_newton_opts* opts, sx_step_report* reports,
                          void* stream);
 
+/* ---- tracing: per-phase device time and launch counts ------------------
+ * Phases of the path, each timed with CUDA events recorded on the stream
+ * the phase's kernels are launched on. */
+#define SX_PH_ELEMENTS 0   /* element E/g/H kernel (+ PSD test)            */
+#define SX_PH_CLAMP 1      /* eigen-decomposition of queued stencils       */
+#define SX_PH_ASSEMBLE 2   /* BSR value gather + inertia diagonal          */
+#define SX_PH_GRAD 3       /* gradient gather, inertia energy, norms       */
+#define SX_PH_REDUCE 4     /* per-scene deterministic reductions           */
+#define SX_PH_SPMV 5       /* PCG: q = A p                                 */
+#define SX_PH_PCG 6        /* PCG: setup, vector updates, scalar steps     */
+#define SX_PH_NEWTON 7     /* predictor, line-search vectors, velocity     */
+#define SX_PH_OTHER 8      /* control writes and copies                    */
+#define SX_PH_COUNT 9
+
+/* enable != 0 starts recording (and clears the accumulators); 0 stops. */
+int sx_profile(sx_ctx* ctx, int enable);
+/* Synchronizes the recorded streams and returns, per phase, the summed
+ * device milliseconds (ms[SX_PH_COUNT], may be NULL) and the kernel
+ * launches since the last reset (launches[SX_PH_COUNT], may be NULL; counted
+ * whether or not timing is enabled). reset != 0 clears both. */
+int sx_profile_read(sx_ctx* ctx, double* ms, int64_t* launches, int reset);
+
 /* ---- footprint (for admission by memory) ------------------------------ */
 typedef struct {
     int64_t n_nodes;

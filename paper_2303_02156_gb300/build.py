@@ -19,6 +19,8 @@ SOURCES = ["sx_elements.cu", "sx_graph.cu", "sx_assemble.cu", "sx_solve.cu", "sx
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# extra nvcc flags (e.g. -DSX_F64_SWEEPS=1) for parameter studies
+EXTRA = os.environ.get("SX_NVCC_FLAGS", "").split()
 
 
 def _deps():
@@ -46,7 +48,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

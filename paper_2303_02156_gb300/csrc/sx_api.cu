@@ -44,9 +44,19 @@ constexpr int kSlotTile = 256;
 
 struct Batch;
 
+struct ProfRec {
+    int phase;
+    cudaEvent_t a, b;
+};
+
 struct sx_ctx {
     int device = 0;
     int sm_count = 0;
+    bool prof_on = false;
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[SX_PH_COUNT] = {0};
+    int64_t prof_launches[SX_PH_COUNT] = {0};
     int elem_blocks_per_sm[2] = {1, 1};
     std::string err;
     int* queue = nullptr;
@@ -115,8 +125,13 @@ struct Batch {
     double* d_ctl_d = nullptr;
     int* h_ctl_i = nullptr;
     double* h_ctl_d = nullptr;
+    double* d_clampM = nullptr;      // projection queue (45 doubles per entry)
+    ClampRef* d_clampRef = nullptr;
+    int* d_clampCount = nullptr;     // [0] count, [1] failures
+    int clamp_cap = 0;
     ~Batch()
     {
+        cudaFree(d_clampM); cudaFree(d_clampRef); cudaFree(d_clampCount);
         cudaFree(d_desc); cudaFree(d_desc_trial); cudaFree(d_elem); cudaFree(d_node);
         cudaFree(d_slot); cudaFree(d_elem_beg); cudaFree(d_elem_end); cudaFree(d_node_beg);
         cudaFree(d_node_end); cudaFree(d_part_elem); cudaFree(d_part_node); cudaFree(d_bad);
@@ -142,6 +157,49 @@ int cuda_fail(sx_ctx* c, cudaError_t e, const char* where)
     do {                                                                 \
         cudaError_t e_ = (call);                                         \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);         \
+    } while (0)
+
+cudaEvent_t prof_event(sx_ctx* ctx)
+{
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_drain(sx_ctx* ctx)
+{
+    for (auto& r : ctx->prof_pending) {
+        float ms = 0.0f;
+        cudaEventSynchronize(r.b);
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->prof_ms[r.phase] += ms;
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+}
+
+// profiled launch: counts `nl` kernel launches in `phase`, and when tracing
+// is on brackets the call with events on its stream
+#define PL(phase, nl, call)                                                   \
+    do {                                                                      \
+        cudaEvent_t a_ = nullptr;                                             \
+        if (ctx->prof_on) {                                                   \
+            a_ = prof_event(ctx);                                             \
+            cudaEventRecord(a_, st);                                          \
+        }                                                                     \
+        CK(call);                                                             \
+        ctx->prof_launches[phase] += (nl);                                    \
+        if (ctx->prof_on) {                                                   \
+            cudaEvent_t b_ = prof_event(ctx);                                 \
+            cudaEventRecord(b_, st);                                          \
+            ctx->prof_pending.push_back(ProfRec{phase, a_, b_});              \
+            if (ctx->prof_pending.size() > 4096) prof_drain(ctx);             \
+        }                                                                     \
     } while (0)
 
 template <typename T>
@@ -279,6 +337,15 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         CK(cudaMalloc((void**)&B->d_ctl_d, n * sizeof(double)));
         CK(cudaMallocHost((void**)&B->h_ctl_i, n * sizeof(int)));
         CK(cudaMallocHost((void**)&B->h_ctl_d, n * sizeof(double)));
+        int64_t cap = 0;
+        for (sx_scene* s : B->scenes)
+            for (auto& b : s->blocks)
+                if (b.kind != SX_KIND_HINGE4) cap += b.n;
+        B->clamp_cap = (int)std::min<int64_t>(std::max<int64_t>(cap, 1), INT32_MAX);
+        CK(cudaMalloc((void**)&B->d_clampM, (size_t)B->clamp_cap * 45 * sizeof(double)));
+        CK(cudaMalloc((void**)&B->d_clampRef, (size_t)B->clamp_cap * sizeof(ClampRef)));
+        CK(cudaMalloc((void**)&B->d_clampCount, 2 * sizeof(int)));
+        CK(cudaMemset(B->d_clampCount, 0, 2 * sizeof(int)));
         CK(cudaMalloc((void**)&B->d_desc, n * sizeof(SceneDev)));
         CK(cudaMalloc((void**)&B->d_desc_trial, n * sizeof(SceneDev)));
         B->versions.assign(n, 0);
@@ -327,7 +394,7 @@ int set_active(sx_ctx* ctx, Batch* B, const std::vector<int>& act, cudaStream_t 
     const int n = (int)B->scenes.size();
     for (int i = 0; i < n; ++i) B->h_ctl_i[i] = act[i];
     CK(cudaMemcpyAsync(B->d_ctl_i, B->h_ctl_i, n * sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(launch_set_scal(B->d_desc, n, B->d_ctl_i, nullptr, st));
+    PL(SX_PH_OTHER, 1, launch_set_scal(B->d_desc, n, B->d_ctl_i, nullptr, st));
     return SX_OK;
 }
 
@@ -336,14 +403,14 @@ int set_alpha(sx_ctx* ctx, Batch* B, const std::vector<double>& a, cudaStream_t 
     const int n = (int)B->scenes.size();
     for (int i = 0; i < n; ++i) B->h_ctl_d[i] = a[i];
     CK(cudaMemcpyAsync(B->d_ctl_d, B->h_ctl_d, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(launch_set_scal(B->d_desc, n, nullptr, B->d_ctl_d, st));
+    PL(SX_PH_OTHER, 1, launch_set_scal(B->d_desc, n, nullptr, B->d_ctl_d, st));
     return SX_OK;
 }
 
 int read_scal(sx_ctx* ctx, Batch* B, cudaStream_t st)
 {
     const int n = (int)B->scenes.size();
-    CK(launch_gather_scal(B->d_desc, n, B->d_scal, st));
+    PL(SX_PH_OTHER, 1, launch_gather_scal(B->d_desc, n, B->d_scal, st));
     CK(cudaMemcpyAsync(B->h_scal, B->d_scal, n * sizeof(SceneScal), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return SX_OK;
@@ -376,28 +443,35 @@ int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool 
     L.tile_nonfinite = B->d_nonfin;
     L.tile_clamped = B->d_clamped;
     L.queue = ctx->queue;
+    L.clamp_M = B->d_clampM;
+    L.clamp_ref = B->d_clampRef;
+    L.clamp_count = B->d_clampCount;
+    L.clamp_failed = B->d_clampCount + 1;
+    L.clamp_cap = B->clamp_cap;
+    L.clamp_grid = ctx->sm_count * 8;
     const int pidx = precision == SX_FP32 ? 1 : 0;
     int grid = std::min<int>(L.ntiles, ctx->sm_count * ctx->elem_blocks_per_sm[pidx]);
     grid = std::max(grid, 1);
-    CK(launch_elements(L, grid, st));
-    CK(launch_scene_reduce(B->d_part_elem, 1, 0, B->d_elem_beg, B->d_elem_end, n, desc, F_E, 0,
-                           st));
-    CK(launch_scene_reduce_flags(B->d_bad, B->d_nonfin, B->d_clamped, B->d_elem_beg,
-                                 B->d_elem_end, n, desc, st));
+    PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
+    if (level >= 2 && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
+    PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_elem, 1, 0, B->d_elem_beg, B->d_elem_end,
+                                            n, desc, F_E, 0, st));
+    PL(SX_PH_REDUCE, 1, launch_scene_reduce_flags(B->d_bad, B->d_nonfin, B->d_clamped,
+                                                  B->d_elem_beg, B->d_elem_end, n, desc, st));
     const int nnt = (int)B->node_tiles.size();
     if (level >= 1)
-        CK(launch_assemble_grad(desc, B->d_node, nnt, B->d_part_node, st));
+        PL(SX_PH_GRAD, 1, launch_assemble_grad(desc, B->d_node, nnt, B->d_part_node, st));
     else
-        CK(launch_inertia_energy(desc, B->d_node, nnt, nullptr, B->d_part_node, 0, st));
-    CK(launch_scene_reduce(B->d_part_node, 2, 0, B->d_node_beg, B->d_node_end, n, desc, F_E, 1,
-                           st));
+        PL(SX_PH_GRAD, 1, launch_inertia_energy(desc, B->d_node, nnt, nullptr, B->d_part_node, 0, st));
+    PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_node, 2, 0, B->d_node_beg, B->d_node_end,
+                                            n, desc, F_E, 1, st));
     if (level >= 1)
-        CK(launch_scene_reduce(B->d_part_node, 2, 1, B->d_node_beg, B->d_node_end, n, desc,
-                               F_GNORM2, 0, st));
+        PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_node, 2, 1, B->d_node_beg,
+                                                B->d_node_end, n, desc, F_GNORM2, 0, st));
     if (level >= 2) {
         AsmLaunch A{desc, B->d_slot, (int)B->slot_tiles.size(), precision};
-        CK(launch_assemble_vals(A, st));
-        CK(launch_inertia_diag(desc, B->d_node, nnt, precision, st));
+        PL(SX_PH_ASSEMBLE, 1, launch_assemble_vals(A, st));
+        PL(SX_PH_ASSEMBLE, 1, launch_inertia_diag(desc, B->d_node, nnt, precision, st));
         for (sx_scene* s : B->scenes) s->last_precision = precision;
     }
     for (sx_scene* s : B->scenes) s->last_level = std::max(s->last_level, level);
@@ -518,6 +592,8 @@ int sx_create(sx_ctx** out, const sx_options* opt)
 int sx_destroy(sx_ctx* ctx)
 {
     if (!ctx) return SX_EINVAL;
+    prof_drain(ctx);
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     ctx->batch_cache.clear();
     cudaFree(ctx->queue);
     delete ctx;
@@ -1008,12 +1084,56 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     if (!g && H) CK(cudaMallocAsync((void**)&scratch_g, std::max<int64_t>(b.n, 1) * 12 * sizeof(double), st));
     L.out_g = g ? g : scratch_g;
     L.out_H = H;
+    double* qM = nullptr;
+    ClampRef* qR = nullptr;
+    int* qC = nullptr;
+    if (H && project) {
+        CK(cudaMallocAsync((void**)&qM, std::max<int64_t>(b.n, 1) * 45 * sizeof(double), st));
+        CK(cudaMallocAsync((void**)&qR, std::max<int64_t>(b.n, 1) * sizeof(ClampRef), st));
+        CK(cudaMallocAsync((void**)&qC, 2 * sizeof(int), st));
+        CK(cudaMemsetAsync(qC, 0, 2 * sizeof(int), st));
+    }
+    L.clamp_M = qM;
+    L.clamp_ref = qR;
+    L.clamp_count = qC;
+    L.clamp_failed = qC ? qC + 1 : nullptr;
+    L.clamp_cap = (int)std::max<int64_t>(b.n, 1);
+    L.clamp_grid = ctx->sm_count * 8;
     int grid = std::min<int>(L.ntiles, ctx->sm_count * ctx->elem_blocks_per_sm[precision == SX_FP32]);
-    CK(launch_elements(L, std::max(grid, 1), st));
+    PL(SX_PH_ELEMENTS, 1, launch_elements(L, std::max(grid, 1), st));
+    if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
+    int qfail[2] = {0, 0};
+    if (qC) CK(cudaMemcpyAsync(qfail, qC, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (qM) { cudaFree(qM); cudaFree(qR); cudaFree(qC); }
     cudaFree(d_tiles);
+    if (qfail[1]) return fail(ctx, SX_ENAN, "eval_elements: projection did not converge");
     if (tmpE) cudaFree(tmpE);
     if (scratch_g) cudaFree(scratch_g);
+    return SX_OK;
+}
+
+int sx_profile(sx_ctx* ctx, int enable)
+{
+    if (!ctx) return SX_EINVAL;
+    prof_drain(ctx);
+    for (int i = 0; i < SX_PH_COUNT; ++i) ctx->prof_ms[i] = 0.0;
+    ctx->prof_on = enable != 0;
+    return SX_OK;
+}
+
+int sx_profile_read(sx_ctx* ctx, double* ms, int64_t* launches, int reset)
+{
+    if (!ctx) return SX_EINVAL;
+    prof_drain(ctx);
+    for (int i = 0; i < SX_PH_COUNT; ++i) {
+        if (ms) ms[i] = ctx->prof_ms[i];
+        if (launches) launches[i] = ctx->prof_launches[i];
+        if (reset) {
+            ctx->prof_ms[i] = 0.0;
+            ctx->prof_launches[i] = 0;
+        }
+    }
     return SX_OK;
 }
 
@@ -1057,7 +1177,7 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
     std::vector<double> g0(n, 0.0), gl(n, 0.0), E(n, 0.0);
     std::vector<int> act(n, 1);
     if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
-    CK(launch_predict(B->d_desc, B->d_node, nnt, st));
+    PL(SX_PH_NEWTON, 1, launch_predict(B->d_desc, B->d_node, nnt, st));
     for (int it = 0; it <= o.max_newton; ++it) {
         for (int i = 0; i < n; ++i) act[i] = !done[i];
         if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
@@ -1082,18 +1202,23 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
         for (int i = 0; i < n; ++i) act[i] = !done[i];
         if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
         // ---- PCG on H dx = -g
-        CK(launch_pcg_setup_p(B->d_desc, B->d_node, nnt, o.precision, B->d_part_node, st));
-        CK(launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg, B->d_node_end, n, B->d_desc, 0,
-                             o.pcg_tol, o.max_pcg, st));
+        PL(SX_PH_PCG, 1, launch_pcg_setup_p(B->d_desc, B->d_node, nnt, o.precision,
+                                            B->d_part_node, st));
+        PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg, B->d_node_end, n,
+                                           B->d_desc, 0, o.pcg_tol, o.max_pcg, st));
         int par = 0;
         for (int k = 0;; k += 8) {
             for (int j = 0; j < 8; ++j) {
-                CK(launch_spmv_pq(B->d_desc, B->d_node, nnt, o.precision, par, B->d_part_node, st));
-                CK(launch_pcg_reduce(B->d_part_node, 1, B->d_node_beg, B->d_node_end, n,
-                                     B->d_desc, 1, o.pcg_tol, o.max_pcg, st));
-                CK(launch_pcg_update(B->d_desc, B->d_node, nnt, par, B->d_part_node, st));
-                CK(launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg, B->d_node_end, n,
-                                     B->d_desc, 2, o.pcg_tol, o.max_pcg, st));
+                PL(SX_PH_SPMV, 1, launch_spmv_pq(B->d_desc, B->d_node, nnt, o.precision, par,
+                                                 B->d_part_node, st));
+                PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 1, B->d_node_beg,
+                                                   B->d_node_end, n, B->d_desc, 1, o.pcg_tol,
+                                                   o.max_pcg, st));
+                PL(SX_PH_PCG, 1, launch_pcg_update(B->d_desc, B->d_node, nnt, par,
+                                                   B->d_part_node, st));
+                PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg,
+                                                   B->d_node_end, n, B->d_desc, 2, o.pcg_tol,
+                                                   o.max_pcg, st));
                 par ^= 1;
             }
             if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
@@ -1113,9 +1238,9 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
         }
         if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
         // ---- Armijo backtracking on E_BE
-        CK(launch_gdx(B->d_desc, B->d_node, nnt, B->d_part_node, st));
-        CK(launch_scene_reduce(B->d_part_node, 1, 0, B->d_node_beg, B->d_node_end, n, B->d_desc,
-                               F_GDX, 0, st));
+        PL(SX_PH_NEWTON, 1, launch_gdx(B->d_desc, B->d_node, nnt, B->d_part_node, st));
+        PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_node, 1, 0, B->d_node_beg,
+                                                B->d_node_end, n, B->d_desc, F_GDX, 0, st));
         if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
         std::vector<double> gdx(n), alpha(n, 1.0);
         for (int i = 0; i < n; ++i) gdx[i] = B->h_scal[i].gdx;
@@ -1126,7 +1251,7 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             if (!any) break;
             if ((rc = set_active(ctx, B, search, st)) != SX_OK) return rc;
             if ((rc = set_alpha(ctx, B, alpha, st)) != SX_OK) return rc;
-            CK(launch_trial(B->d_desc, B->d_node, nnt, st));
+            PL(SX_PH_NEWTON, 1, launch_trial(B->d_desc, B->d_node, nnt, st));
             if ((rc = run_eval(ctx, B, SX_E, 0, o.precision, true, st)) != SX_OK) return rc;
             if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
             std::vector<int> acc(n, 0);
@@ -1144,7 +1269,7 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
                 }
             }
             if ((rc = set_active(ctx, B, acc, st)) != SX_OK) return rc;
-            CK(launch_accept(B->d_desc, B->d_node, nnt, st));
+            PL(SX_PH_NEWTON, 1, launch_accept(B->d_desc, B->d_node, nnt, st));
         }
         for (int i = 0; i < n; ++i)
             if (search[i]) {
@@ -1154,7 +1279,7 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
     }
     std::vector<int> all(n, 1);
     if ((rc = set_active(ctx, B, all, st)) != SX_OK) return rc;
-    CK(launch_velocity(B->d_desc, B->d_node, nnt, st));
+    PL(SX_PH_NEWTON, 1, launch_velocity(B->d_desc, B->d_node, nnt, st));
     CK(cudaStreamSynchronize(st));
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     int worst = SX_OK;

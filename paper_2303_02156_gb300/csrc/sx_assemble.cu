@@ -255,7 +255,8 @@ __global__ void k_scene_reduce_int(const int* bad, const int* nonfin, const int*
     }
     if (threadIdx.x == 0 && sc->active) {
         sc->bad_state = sh[0][0];
-        sc->nonfinite = sh[1][0];
+        sc->nonfinite = sh[1][0] + sc->clamp_fail;
+        sc->clamp_fail = 0;
         sc->clamped = sh[2][0];
     }
 }

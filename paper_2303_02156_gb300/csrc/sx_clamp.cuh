@@ -9,23 +9,38 @@
 // Clamping the eigenvalues of H at zero is therefore the same as clamping
 // those of M: proj(H) = H - sum_{lambda_i < 0} lambda_i u_i u_i^T with
 // u_i = (Hd kron I3)(0, v_i) and (lambda_i, v_i) the negative eigenpairs
-// of M. The 9x9 problem is solved in double precision:
-//   1. shifted LDL^T of M + tau I (tau = 1e-13 ||M||_F): if it succeeds
-//      the stencil is left as is (the change is at most tau);
-//   2. otherwise Householder reduction to tridiagonal T = Q^T M Q,
-//      eigenvalues of T by implicit QL with Wilkinson shifts, and for each
-//      eigenvalue below -tau an eigenvector by inverse iteration on T
-//      (partial-pivoting LU, three sweeps, Gram-Schmidt inside clusters),
-//      mapped back through the reflectors.
-// All steps are textbook dense symmetric eigen-methods (Golub & Van Loan,
-// ch. 8); the result, a spectral function of H, is unique even where
-// eigenvectors are not.
+// of M. The 9x9 problem is solved in double precision in two phases:
+//   1. (element kernel) shifted LDL^T of M + tau I, tau = 1e-13 ||M||_F:
+//      if it succeeds the stencil is left as is (the change is at most
+//      tau); otherwise M is queued for phase 2;
+//   2. (clamp kernel, one thread per queued M) a full eigen-decomposition
+//      with no data-dependent control flow, so the 32 stencils of a warp run
+//      in lockstep: cyclic Jacobi in float from the identity (float is ~60x
+//      faster than double on this part), modified Gram-Schmidt of the float
+//      eigenvectors in double, At = X^T M X in double (now nearly diagonal)
+//      and two double Jacobi sweeps on At accumulated into X; eigenvalues
+//      below -tau are clamped.
+// Matrices are kept packed (lower triangle, 45 entries) and every loop is
+// unrolled so they live in registers; the eigenvector matrix lives in
+// shared memory. Jacobi is the textbook symmetric Schur method (Golub &
+// Van Loan, ch. 8); the result, a spectral function of H, is unique even
+// where eigenvectors are not.
 #pragma once
 
 #include <float.h>
 #include <math.h>
 
 namespace sx {
+
+#ifndef SX_F64_SWEEPS
+#define SX_F64_SWEEPS 2
+#endif
+
+// packed lower-triangle index of (i, j), any order
+__host__ __device__ constexpr int pk(int i, int j)
+{
+    return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i;
+}
 
 // 1/2 Hadamard columns c = 1..3 applied to node quantities (a = 0..3)
 // y_c = sum_a Hd[a][c] x_a
@@ -48,236 +63,195 @@ __device__ __forceinline__ void had_inv(const T y1, const T y2, const T y3, T& x
     x3 = T(0.5) * (y3 - y1 - y2);
 }
 
-// Eigenvalues of the symmetric tridiagonal (d, e), e[0..n-2] the
-// subdiagonal, by implicit QL with Wilkinson shifts. d is overwritten by
-// the eigenvalues (unordered). Returns false if an eigenvalue needed more
-// than 60 sweeps.
-__device__ inline bool ql_eigvals9(double* d, double* e, double abs_floor)
+__device__ __forceinline__ double fro9(const double (&A)[45])
 {
-    const int n = 9;
-    e[n - 1] = 0.0;
-    for (int l = 0; l < n; ++l) {
-        int iter = 0;
-        for (;;) {
-            int m = l;
-            for (; m < n - 1; ++m) {
-                double dd = fabs(d[m]) + fabs(d[m + 1]);
-                if (fabs(e[m]) <= DBL_EPSILON * dd || fabs(e[m]) <= abs_floor) break;
-            }
-            if (m == l) break;
-            if (++iter > 60) return false;
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
-            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
-            double s = 1.0, c = 1.0, p = 0.0;
-            bool restart = false;
-            for (int i = m - 1; i >= l; --i) {
-                double f = s * e[i], b = c * e[i];
-                r = hypot(f, g);
-                e[i + 1] = r;
-                if (r == 0.0) {
-                    d[i + 1] -= p;
-                    e[m] = 0.0;
-                    restart = true;
-                    break;
-                }
-                s = f / r;
-                c = g / r;
-                g = d[i + 1] - p;
-                r = (d[i] - g) * s + 2.0 * c * b;
-                p = s * r;
-                d[i + 1] = g + p;
-                g = c * r - b;
-            }
-            if (restart) continue;
-            d[l] -= p;
-            e[l] = g;
-            e[m] = 0.0;
-        }
-    }
-    return true;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) s = fma((i == j ? 1.0 : 2.0) * A[pk(i, j)], A[pk(i, j)], s);
+    return sqrt(s);
 }
 
-// Negative eigenpairs of the symmetric 9x9 A (row-major, both triangles;
-// destroyed). Writes up to 9 pairs (lam[k] < -tau ascending, V[k][0..8]
-// orthonormal) and returns their number; returns -1 if QL failed (the
-// caller reports it). `fro_out` receives ||A||_F.
-__device__ inline int neg_eigs9(double* A, double* lam, double* V, double* fro_out)
+// Phase 1: true when M + tau I is positive definite (LDL^T without
+// pivoting succeeds), tau = 1e-13 ||M||_F. M is not modified.
+__device__ __forceinline__ bool psd_by_ldlt(const double (&M)[45])
 {
-    const int n = 9;
-    double fro2 = 0.0;
-#pragma unroll
-    for (int i = 0; i < 81; ++i) fro2 = fma(A[i], A[i], fro2);
-    double fro = sqrt(fro2);
-    *fro_out = fro;
-    if (fro == 0.0) return 0;
+    const double fro = fro9(M);
+    if (fro == 0.0) return true;
     const double tau = 1e-13 * fro;
+    double L[45];
+    double dg[9];
+    bool pd = true;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        double s = M[pk(j, j)] + tau;
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= L[pk(j, k)] * L[pk(j, k)] * dg[k];
+        pd = pd && (s > 0.0);
+        dg[j] = s;
+        const double inv = 1.0 / s;
+#pragma unroll
+        for (int i = j + 1; i < 9; ++i) {
+            double t = M[pk(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= L[pk(i, k)] * L[pk(j, k)] * dg[k];
+            L[pk(i, j)] = t * inv;
+        }
+    }
+    return pd;
+}
 
-    // 1. shifted LDL^T test (no pivoting: succeeds iff A + tau I is PD)
+// ---------------------------------------------------------------- phase 2
+// Cyclic Jacobi (symmetric Schur rotations, Golub & Van Loan 8.5) on the
+// packed 9x9 A with the rotations accumulated into X (row-major, column c =
+// eigenvector c). One sweep visits the 36 pairs (p, q) in a fixed order;
+// every loop is unrolled and there is no data-dependent control flow, so a
+// warp runs its 32 stencils in lockstep.
+
+// float sweep: exact float angle, a_pq set to zero
+__device__ __forceinline__ void jacobi_sweep_f32(float (&A)[45], float (&X)[81])
+{
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = p + 1; q < 9; ++q) {
+            const float apq = A[pk(p, q)], app = A[pk(p, p)], aqq = A[pk(q, q)];
+            const bool nz = apq != 0.0f;
+            const float tau = (aqq - app) / (nz ? 2.0f * apq : 1.0f);
+            const float tt = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+            const float t = nz ? tt : 0.0f;
+            const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
+            A[pk(p, p)] = app - t * apq;
+            A[pk(q, q)] = aqq + t * apq;
+            A[pk(p, q)] = 0.0f;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                if (r == p || r == q) continue;
+                const float arp = A[pk(r, p)], arq = A[pk(r, q)];
+                A[pk(r, p)] = c * arp - s * arq;
+                A[pk(r, q)] = s * arp + c * arq;
+            }
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                const float xp = X[r * 9 + p], xq = X[r * 9 + q];
+                X[r * 9 + p] = c * xp - s * xq;
+                X[r * 9 + q] = s * xp + c * xq;
+            }
+        }
+}
+
+// Accessor for a per-thread 9x9 double matrix in shared memory laid out
+// [81][threads] so that a warp's accesses to the same entry are contiguous.
+struct SmemMat {
+    double* base;
+    int stride;
+    __device__ __forceinline__ double& operator()(int r, int c) const
     {
-        double L[81];
-        double dg[9];
-        bool pd = true;
-        for (int j = 0; j < n && pd; ++j) {
-            double s = A[j * 9 + j] + tau;
-            for (int k = 0; k < j; ++k) s -= L[j * 9 + k] * L[j * 9 + k] * dg[k];
-            if (!(s > 0.0)) {
-                pd = false;
-                break;
-            }
-            dg[j] = s;
-            double inv = 1.0 / s;
-            for (int i = j + 1; i < n; ++i) {
-                double t = A[i * 9 + j];
-                for (int k = 0; k < j; ++k) t -= L[i * 9 + k] * L[j * 9 + k] * dg[k];
-                L[i * 9 + j] = t * inv;
-            }
-        }
-        if (pd) return 0;
+        return base[(r * 9 + c) * stride];
     }
+};
 
-    // 2. Householder tridiagonalization on the lower triangle; reflector k
-    //    (acting on rows k+1..8) is kept in column k below the diagonal.
-    double d[9], e[9], beta[9];
-    for (int k = 0; k < n - 2; ++k) {
-        double a2 = 0.0;
-        for (int i = k + 1; i < n; ++i) a2 = fma(A[i * 9 + k], A[i * 9 + k], a2);
-        double xn = sqrt(a2);
-        double x0 = A[(k + 1) * 9 + k];
-        if (xn <= 1e-300) {
-            beta[k] = 0.0;
-            e[k] = x0;
-            continue;
-        }
-        double alpha = (x0 > 0.0) ? -xn : xn;
-        double v0 = x0 - alpha;
-        double b = 1.0 / (xn * (xn + fabs(x0)));   // 2 / v^T v
-        A[(k + 1) * 9 + k] = v0;
-        beta[k] = b;
-        e[k] = alpha;
-        // p = b * A' v on the trailing block, lower storage
-        double p[9];
-        double K = 0.0;
-        for (int i = k + 1; i < n; ++i) {
-            double s = 0.0;
-            for (int j = k + 1; j <= i; ++j) s = fma(A[i * 9 + j], A[j * 9 + k], s);
-            for (int j = i + 1; j < n; ++j) s = fma(A[j * 9 + i], A[j * 9 + k], s);
-            p[i] = b * s;
-            K = fma(A[i * 9 + k], p[i], K);
-        }
-        K *= 0.5 * b;
-        for (int i = k + 1; i < n; ++i) p[i] = fma(-K, A[i * 9 + k], p[i]);   // w
-        for (int i = k + 1; i < n; ++i) {
-            double vi = A[i * 9 + k], wi = p[i];
-            for (int j = k + 1; j <= i; ++j)
-                A[i * 9 + j] -= fma(vi, p[j], wi * A[j * 9 + k]);
-        }
-    }
-    for (int i = 0; i < n; ++i) d[i] = A[i * 9 + i];
-    e[n - 2] = A[(n - 1) * 9 + (n - 2)];
-
-    // 3. eigenvalues of T
-    double ev[9], ee[9];
-    for (int i = 0; i < n; ++i) { ev[i] = d[i]; ee[i] = e[i]; }
-    if (!ql_eigvals9(ev, ee, 1e-18 * fro)) return -1;
-
-    // 4. the ones below -tau, ascending
-    int k = 0;
-    for (int i = 0; i < n; ++i)
-        if (ev[i] < -tau) {
-            double v = ev[i];
-            int j = k++;
-            while (j > 0 && lam[j - 1] > v) { lam[j] = lam[j - 1]; --j; }
-            lam[j] = v;
-        }
-    if (k == 0) return 0;
-
-    // 5. inverse iteration on T for each, then back through the reflectors
-    const double tiny = DBL_EPSILON * fro;
-    for (int t = 0; t < k; ++t) {
-        const double sig = lam[t];
-        // LU with partial pivoting of T - sig I
-        double a[9], bsup[9], u2[9], m[9], rinv[9];
-        unsigned piv = 0u;
-        for (int i = 0; i < n; ++i) {
-            a[i] = d[i] - sig;
-            bsup[i] = (i < n - 1) ? e[i] : 0.0;
-            u2[i] = 0.0;
-        }
-        for (int i = 0; i < n - 1; ++i) {
-            double c = e[i];   // subdiagonal of row i+1
-            if (fabs(a[i]) >= fabs(c)) {
-                if (fabs(a[i]) < tiny) a[i] = copysign(tiny, a[i] == 0.0 ? 1.0 : a[i]);
-                m[i] = c / a[i];
-                a[i + 1] -= m[i] * bsup[i];
-            } else {
-                piv |= 1u << i;
-                double mi = a[i] / c;
-                m[i] = mi;
-                double na_i = c, nb_i = a[i + 1];
-                double nu2 = (i + 1 < n - 1) ? bsup[i + 1] : 0.0;
-                double na_i1 = bsup[i] - mi * a[i + 1];
-                double nb_i1 = (i + 1 < n - 1) ? -mi * bsup[i + 1] : 0.0;
-                a[i] = na_i;
-                bsup[i] = nb_i;
-                u2[i] = nu2;
-                a[i + 1] = na_i1;
-                if (i + 1 < n - 1) bsup[i + 1] = nb_i1;
+// double sweep: the angle comes from float arithmetic (it only decides how
+// much a_pq shrinks), the rotation (c, s = t c with c = 1/sqrt(1+t^2)) and
+// the 2x2 update are exact in double, so A stays similar to M to working
+// precision
+__device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat& X)
+{
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = p + 1; q < 9; ++q) {
+            const double apq = A[pk(p, q)], app = A[pk(p, p)], aqq = A[pk(q, q)];
+            const float fpq = (float)apq;
+            const bool nz = fpq != 0.0f;
+            const float tau = (float)(aqq - app) / (nz ? 2.0f * fpq : 1.0f);
+            const float tt = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+            const double t = nz ? (double)tt : 0.0;
+            const double c = rsqrt(fma(t, t, 1.0)), s = t * c;
+            const double cc = c * c, ss = s * s, cs = c * s;
+            A[pk(p, p)] = fma(cc, app, fma(-2.0 * cs, apq, ss * aqq));
+            A[pk(q, q)] = fma(ss, app, fma(2.0 * cs, apq, cc * aqq));
+            A[pk(p, q)] = fma(cc - ss, apq, cs * (app - aqq));
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                if (r == p || r == q) continue;
+                const double arp = A[pk(r, p)], arq = A[pk(r, q)];
+                A[pk(r, p)] = fma(c, arp, -s * arq);
+                A[pk(r, q)] = fma(s, arp, c * arq);
+            }
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                const double xp = X(r, p), xq = X(r, q);
+                X(r, p) = fma(c, xp, -s * xq);
+                X(r, q) = fma(s, xp, c * xq);
             }
         }
-        if (fabs(a[n - 1]) < tiny) a[n - 1] = copysign(tiny, a[n - 1] == 0.0 ? 1.0 : a[n - 1]);
-        for (int i = 0; i < n; ++i) rinv[i] = 1.0 / a[i];
+}
 
+// Phase 2 driver. Mg: packed 9x9 (double, global memory; read twice so that
+// it is not held in registers across the float phase). On return X holds an
+// orthonormal eigenbasis of M to working precision and lam the eigenvalues.
+__device__ __forceinline__ void eig9(const double* __restrict__ Mg, const SmemMat& X,
+                                     double (&lam)[9])
+{
+    // 1. float Jacobi from the identity
+    {
+        float A[45], Xf[81];
+#pragma unroll
+        for (int k = 0; k < 45; ++k) A[k] = (float)Mg[k];
+#pragma unroll
+        for (int k = 0; k < 81; ++k) Xf[k] = (k % 10 == 0) ? 1.0f : 0.0f;
+#pragma unroll 1
+        for (int sw = 0; sw < 5; ++sw) jacobi_sweep_f32(A, Xf);
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) X(r, c) = (double)Xf[r * 9 + c];
+    }
+    // 2. re-orthonormalize in double (modified Gram-Schmidt; X is already
+    //    orthogonal to float precision, so one pass suffices)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+#pragma unroll
+        for (int i = 0; i < j; ++i) {
+            double d = 0.0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) d = fma(X(r, i), X(r, j), d);
+#pragma unroll
+            for (int r = 0; r < 9; ++r) X(r, j) = fma(-d, X(r, i), X(r, j));
+        }
+        double nn = 0.0;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) nn = fma(X(r, j), X(r, j), nn);
+        const double inv = rsqrt(nn);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) X(r, j) *= inv;
+    }
+    // 3. At = X^T M X (nearly diagonal), then double Jacobi sweeps
+    double At[45];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
         double y[9];
-        for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.618033988749895 * (double)((i * 7 + t * 3) % 9);
-        for (int sweep = 0; sweep < 3; ++sweep) {
-            // orthogonalize against earlier vectors of the same cluster
-            for (int s = 0; s < t; ++s) {
-                if (fabs(lam[s] - sig) > 1e-3 * fro) continue;
-                double dt_ = 0.0;
-                for (int i = 0; i < n; ++i) dt_ = fma(V[s * 9 + i], y[i], dt_);
-                for (int i = 0; i < n; ++i) y[i] = fma(-dt_, V[s * 9 + i], y[i]);
-            }
-            // forward elimination on the rhs
-            for (int i = 0; i < n - 1; ++i) {
-                if (piv & (1u << i)) { double tmp = y[i]; y[i] = y[i + 1]; y[i + 1] = tmp; }
-                y[i + 1] -= m[i] * y[i];
-            }
-            // back substitution
-            y[n - 1] *= rinv[n - 1];
-            y[n - 2] = (y[n - 2] - bsup[n - 2] * y[n - 1]) * rinv[n - 2];
-            for (int i = n - 3; i >= 0; --i)
-                y[i] = (y[i] - bsup[i] * y[i + 1] - u2[i] * y[i + 2]) * rinv[i];
-            double nn = 0.0;
-            for (int i = 0; i < n; ++i) nn = fma(y[i], y[i], nn);
-            double inv = 1.0 / sqrt(nn);
-            for (int i = 0; i < n; ++i) y[i] *= inv;
-        }
-        // final orthogonalization inside the cluster
-        for (int s = 0; s < t; ++s) {
-            if (fabs(lam[s] - sig) > 1e-3 * fro) continue;
-            double dt_ = 0.0;
-            for (int i = 0; i < n; ++i) dt_ = fma(V[s * 9 + i], y[i], dt_);
-            for (int i = 0; i < n; ++i) y[i] = fma(-dt_, V[s * 9 + i], y[i]);
-            double nn = 0.0;
-            for (int i = 0; i < n; ++i) nn = fma(y[i], y[i], nn);
-            double inv = 1.0 / sqrt(nn);
-            for (int i = 0; i < n; ++i) y[i] *= inv;
-        }
-        for (int i = 0; i < n; ++i) V[t * 9 + i] = y[i];
-    }
-    // back-transform all vectors: v = H_0 H_1 ... H_6 w
-    for (int t = 0; t < k; ++t) {
-        double* w = V + t * 9;
-        for (int kk = n - 3; kk >= 0; --kk) {
-            if (beta[kk] == 0.0) continue;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
             double s = 0.0;
-            for (int i = kk + 1; i < n; ++i) s = fma(A[i * 9 + kk], w[i], s);
-            s *= beta[kk];
-            for (int i = kk + 1; i < n; ++i) w[i] = fma(-s, A[i * 9 + kk], w[i]);
+#pragma unroll
+            for (int c = 0; c < 9; ++c) s = fma(__ldg(Mg + pk(r, c)), X(c, j), s);
+            y[r] = s;
+        }
+#pragma unroll
+        for (int i = j; i < 9; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) s = fma(X(r, i), y[r], s);
+            At[pk(i, j)] = s;
         }
     }
-    return k;
+#pragma unroll 1
+    for (int sw = 0; sw < SX_F64_SWEEPS; ++sw) jacobi_sweep_f64(At, X);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) lam[i] = At[pk(i, i)];
 }
 
 }  // namespace sx

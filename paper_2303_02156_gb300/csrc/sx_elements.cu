@@ -34,6 +34,7 @@
 namespace sx {
 
 static constexpr int kElemThreads = 128;
+static constexpr int kClampThreads = 64;
 
 int elements_block_threads() { return kElemThreads; }
 
@@ -184,9 +185,9 @@ __device__ __forceinline__ void matvec3(const R* M, const R* v, R* o)
     for (int i = 0; i < 3; ++i) o[i] = M[i * 3 + 0] * v[0] + M[i * 3 + 1] * v[1] + M[i * 3 + 2] * v[2];
 }
 
-// 9x9 translation-free Hessian M (double, both triangles) of an SNH tet.
+// 9x9 translation-free Hessian M (double, packed lower) of an SNH tet.
 template <typename R>
-__device__ __forceinline__ void snh_M(const SnhCore<R>& S, double* M)
+__device__ __forceinline__ void snh_M(const SnhCore<R>& S, double (&M)[45])
 {
     R K[3][3];   // K_c, c = 1..3 stored at [c-1]
 #pragma unroll
@@ -207,19 +208,17 @@ __device__ __forceinline__ void snh_M(const SnhCore<R>& S, double* M)
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    M[(3 * c + i) * 9 + (3 * d + k)] = (double)blk[i * 3 + k];
-                    M[(3 * d + k) * 9 + (3 * c + i)] = (double)blk[i * 3 + k];
-                }
+                for (int k = 0; k < 3; ++k)
+                    if (3 * d + k <= 3 * c + i || c != d)
+                        M[pk(3 * d + k, 3 * c + i)] = (double)blk[i * 3 + k];
         }
 }
 
 // ------------------------------------------------------------------ output
-// Writes the 10 upper blocks of H - sum_t lam_t u_t u_t^T, with the blocks
-// produced by `blockfn(a, b, out9)` in the element precision.
+// Writes the 10 upper blocks produced by `blockfn(a, b, out9)` (element
+// precision) to the staged buffer, or the full 12x12 to `full`.
 template <typename R, typename HT, typename BlockFn>
-__device__ __forceinline__ void write_blocks(BlockFn blockfn, int nneg, const double* lamv,
-                                             const double* U, HT* staged, double* full,
+__device__ __forceinline__ void write_blocks(BlockFn blockfn, HT* staged, double* full,
                                              int* nonfinite)
 {
 #pragma unroll
@@ -228,57 +227,39 @@ __device__ __forceinline__ void write_blocks(BlockFn blockfn, int nneg, const do
         for (int b = a; b < 4; ++b) {
             R blk[9];
             blockfn(a, b, blk);
-            double o[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) o[k] = (double)blk[k];
-            for (int t = 0; t < nneg; ++t) {
-                const double* u = U + 12 * t;
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int k = 0; k < 3; ++k)
-                        o[i * 3 + k] = fma(-lamv[t] * u[3 * a + i], u[3 * b + k], o[i * 3 + k]);
-            }
             bool bad = false;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) bad |= !isfinite(o[k]);
+            for (int k = 0; k < 9; ++k) bad |= !isfinite((double)blk[k]);
             if (bad) *nonfinite = 1;
             if (staged) {
                 HT* dst = staged + 9 * up_index(a, b);
 #pragma unroll
-                for (int k = 0; k < 9; ++k) dst[k] = (HT)o[k];
+                for (int k = 0; k < 9; ++k) dst[k] = (HT)blk[k];
             }
             if (full) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        full[(3 * a + i) * 12 + (3 * b + k)] = o[i * 3 + k];
-                        full[(3 * b + k) * 12 + (3 * a + i)] = o[i * 3 + k];
+                        full[(3 * a + i) * 12 + (3 * b + k)] = (double)blk[i * 3 + k];
+                        full[(3 * b + k) * 12 + (3 * a + i)] = (double)blk[i * 3 + k];
                     }
             }
         }
 }
 
-// negative eigenpairs of M mapped to 12-vectors u = (Hd kron I3)(0, v)
-__device__ __forceinline__ int project_negatives(double* M, double* lamv, double* U,
-                                                 int* failed)
+// phase 1 of the projection: queue M unless M + tau I is PD
+__device__ __forceinline__ bool queue_if_indefinite(const ElemLaunch& L, int scene, int blk,
+                                                    int64_t e, const double (&M)[45])
 {
-    double V9[81];
-    double fro;
-    int k = neg_eigs9(M, lamv, V9, &fro);
-    if (k < 0) {
-        *failed = 1;
-        return 0;
-    }
-    for (int t = 0; t < k; ++t) {
-        const double* v = V9 + 9 * t;
-        double* u = U + 12 * t;
+    if (psd_by_ldlt(M)) return false;
+    const int slot = atomicAdd(L.clamp_count, 1);
+    if (slot >= L.clamp_cap) return false;   // cannot happen: capacity = stencils
+    double* dst = L.clamp_M + 45 * (int64_t)slot;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            had_inv(v[i], v[3 + i], v[6 + i], u[i], u[3 + i], u[6 + i], u[9 + i]);
-    }
-    return k;
+    for (int k = 0; k < 45; ++k) dst[k] = M[k];
+    L.clamp_ref[slot] = ClampRef{scene, blk, e};
+    return true;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -286,12 +267,12 @@ struct ThreadOut {
     double E;
     int bad;        // barrier d <= 0
     int nonfinite;
-    int clamped;
+    int clamped;    // queued for the projection
 };
 
 template <typename R, typename HT>
-__device__ void eval_snh(const ElemLaunch& L, const SceneDev& S, const ElemBlock& B,
-                         int64_t e, ThreadOut& o)
+__device__ void eval_snh(const ElemLaunch& L, int scene, int blk, const SceneDev& S,
+                         const ElemBlock& B, int64_t e, ThreadOut& o)
 {
     const int4 t = B.conn[e];
     double xg[12];
@@ -320,29 +301,25 @@ __device__ void eval_snh(const ElemLaunch& L, const SceneDev& S, const ElemBlock
         }
     }
     if (L.level >= 2) {
-        double lamv[9];
-        double U[12 * 9];
-        int nneg = 0;
-        if (L.project) {
-            double M[81];
-            snh_M<R>(C, M);
-            int failed = 0;
-            nneg = project_negatives(M, lamv, U, &failed);
-            if (failed) o.nonfinite = 1;
-            o.clamped = nneg > 0;
-        }
-        R u[4][3], v[4][3];
+        {
+            R u[4][3], v[4][3];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            matvec3(C.F, C.G[a], u[a]);
-            matvec3(C.C, C.G[a], v[a]);
+            for (int a = 0; a < 4; ++a) {
+                matvec3(C.F, C.G[a], u[a]);
+                matvec3(C.C, C.G[a], v[a]);
+            }
+            auto blockfn = [&](int a, int b, R* out) {
+                snh_block(C, C.G[a], C.G[b], u[a], u[b], v[a], v[b], a == b, out);
+            };
+            HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
+            double* full = L.out_H ? L.out_H + 144 * e : nullptr;
+            write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
         }
-        auto blockfn = [&](int a, int b, R* out) {
-            snh_block(C, C.G[a], C.G[b], u[a], u[b], v[a], v[b], a == b, out);
-        };
-        HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
-        double* full = L.out_H ? L.out_H + 144 * e : nullptr;
-        write_blocks<R, HT>(blockfn, nneg, lamv, U, staged, full, &o.nonfinite);
+        if (L.project) {
+            double M[45];
+            snh_M<R>(C, M);
+            o.clamped = queue_if_indefinite(L, scene, blk, e, M);
+        }
     }
 }
 
@@ -352,13 +329,8 @@ __device__ void eval_hinge(const ElemLaunch& L, const SceneDev& S, const ElemBlo
 {
     const int4 t = B.conn[e];
     const int nid[4] = {t.x, t.y, t.z, t.w};
-    R q[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) q[a] = (R)B.q[(int64_t)a * B.n + e];
-    const R kc = (R)(B.kb * B.c[e]);
-    // s = sum_a q_a x_a, formed relative to node 0 (sum_a q_a = 0 for a
-    // translation-free hinge; the relative form only improves rounding and
-    // is exact for any q when the missing q-sum term is added back)
+    // s = sum_a q_a x_a, formed relative to node 0 (exact for any q once the
+    // q-sum term is added back; for a translation-free hinge it vanishes)
     double x0[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) x0[i] = S.x[3 * (int64_t)nid[0] + i];
@@ -373,9 +345,14 @@ __device__ void eval_hinge(const ElemLaunch& L, const SceneDev& S, const ElemBlo
     for (int a = 1; a < 4; ++a)
 #pragma unroll
         for (int i = 0; i < 3; ++i) sd[i] += qd[a] * (S.x[3 * (int64_t)nid[a] + i] - x0[i]);
-    o.E = 0.5 * B.kb * B.c[e] * (sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
-    const R s[3] = {(R)sd[0], (R)sd[1], (R)sd[2]};
+    const double kcd = B.kb * B.c[e];
+    o.E = 0.5 * kcd * (sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
     if (!isfinite(o.E)) o.nonfinite = 1;
+    const R kc = (R)kcd;
+    const R s[3] = {(R)sd[0], (R)sd[1], (R)sd[2]};
+    R q[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) q[a] = (R)qd[a];
     const int64_t gid = B.base + e;
     if (L.level >= 1) {
         double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
@@ -392,13 +369,13 @@ __device__ void eval_hinge(const ElemLaunch& L, const SceneDev& S, const ElemBlo
         };
         HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
         double* full = L.out_H ? L.out_H + 144 * e : nullptr;
-        write_blocks<R, HT>(blockfn, 0, nullptr, nullptr, staged, full, &o.nonfinite);
+        write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
     }
 }
 
 template <typename R, typename HT>
-__device__ void eval_barrier(const ElemLaunch& L, const SceneDev& S, const ElemBlock& B,
-                             int64_t e, ThreadOut& o)
+__device__ void eval_barrier(const ElemLaunch& L, int scene, int blk, const SceneDev& S,
+                             const ElemBlock& B, int64_t e, ThreadOut& o)
 {
     const int4 t = B.conn[e];
     const int nid[4] = {t.x, t.y, t.z, t.w};
@@ -415,12 +392,11 @@ __device__ void eval_barrier(const ElemLaunch& L, const SceneDev& S, const ElemB
     int st = barrier_eval<R>(xr, (R)B.dhat, (R)B.kappa, L.level, bo);
     double Ed = (double)bo.E;
     if (sizeof(R) != sizeof(double)) {
-        // the energy (line-search quantity) is always evaluated in double
+        // the energy (the line-search quantity) is always evaluated in double
         BarrierOut<double> bd;
-        int sd = barrier_eval<double>(xr, B.dhat, B.kappa, 0, bd);
-        if (sd < 0) st = sd;
+        const int sd = barrier_eval<double>(xr, B.dhat, B.kappa, 0, bd);
         Ed = (sd == 1) ? bd.E : 0.0;
-        if (sd != 1 && st == 1) st = sd;
+        if (sd != 1) st = sd;
     }
     const int64_t gid = B.base + e;
     if (st < 0) o.bad = 1;
@@ -432,49 +408,6 @@ __device__ void eval_barrier(const ElemLaunch& L, const SceneDev& S, const ElemB
         for (int k = 0; k < 12; ++k) gout[k] = (st == 1) ? (double)bo.g[k] : 0.0;
     }
     if (L.level >= 2) {
-        double lamv[9];
-        double U[12 * 9];
-        int nneg = 0;
-        if (st == 1 && L.project) {
-            double M[81];
-            // M = (Hd kron I3) H (Hd kron I3) restricted to the modes c, d = 1..3
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    // transform rows: T[a][c] blocks, entry (i,k)
-                    R Tm[4][3];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        R h0 = bo.H[(3 * a + i) * 12 + 0 * 3 + k];
-                        R h1 = bo.H[(3 * a + i) * 12 + 1 * 3 + k];
-                        R h2 = bo.H[(3 * a + i) * 12 + 2 * 3 + k];
-                        R h3 = bo.H[(3 * a + i) * 12 + 3 * 3 + k];
-                        had_fwd(h0, h1, h2, h3, Tm[a][0], Tm[a][1], Tm[a][2]);
-                    }
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        R y1, y2, y3;
-                        had_fwd(Tm[0][d], Tm[1][d], Tm[2][d], Tm[3][d], y1, y2, y3);
-                        M[(0 * 3 + i) * 9 + (3 * d + k)] = (double)y1;
-                        M[(1 * 3 + i) * 9 + (3 * d + k)] = (double)y2;
-                        M[(2 * 3 + i) * 9 + (3 * d + k)] = (double)y3;
-                    }
-                }
-            // symmetrize exactly
-#pragma unroll
-            for (int r = 0; r < 9; ++r)
-#pragma unroll
-                for (int c = r + 1; c < 9; ++c) {
-                    double m = 0.5 * (M[r * 9 + c] + M[c * 9 + r]);
-                    M[r * 9 + c] = m;
-                    M[c * 9 + r] = m;
-                }
-            int failed = 0;
-            nneg = project_negatives(M, lamv, U, &failed);
-            if (failed) o.nonfinite = 1;
-            o.clamped = nneg > 0;
-        }
         auto blockfn = [&](int a, int b, R* out) {
 #pragma unroll
             for (int i = 0; i < 3; ++i)
@@ -484,7 +417,35 @@ __device__ void eval_barrier(const ElemLaunch& L, const SceneDev& S, const ElemB
         };
         HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
         double* full = L.out_H ? L.out_H + 144 * e : nullptr;
-        write_blocks<R, HT>(blockfn, nneg, lamv, U, staged, full, &o.nonfinite);
+        write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
+        if (st == 1 && L.project) {
+            // M = (Hd kron I3) H (Hd kron I3) restricted to the modes c, d = 1..3
+            double M[45];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    double Tm[4][3];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        double h[4];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            h[b] = 0.5 * ((double)bo.H[(3 * a + i) * 12 + 3 * b + k] +
+                                          (double)bo.H[(3 * b + k) * 12 + 3 * a + i]);
+                        had_fwd(h[0], h[1], h[2], h[3], Tm[a][0], Tm[a][1], Tm[a][2]);
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        double y[3];
+                        had_fwd(Tm[0][d], Tm[1][d], Tm[2][d], Tm[3][d], y[0], y[1], y[2]);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            if (3 * c + i >= 3 * d + k) M[pk(3 * c + i, 3 * d + k)] = y[c];
+                    }
+                }
+            o.clamped = queue_if_indefinite(L, scene, blk, e, M);
+        }
     }
 }
 
@@ -509,11 +470,11 @@ k_elements(ElemLaunch L)
             if ((int)threadIdx.x < T.count) {
                 const int64_t e = T.start + threadIdx.x;
                 if (B.kind == SX_KIND_SNH_TET4)
-                    eval_snh<R, HT>(L, S, B, e, o);
+                    eval_snh<R, HT>(L, T.scene, T.blk, S, B, e, o);
                 else if (B.kind == SX_KIND_HINGE4)
                     eval_hinge<R, HT>(L, S, B, e, o);
                 else
-                    eval_barrier<R, HT>(L, S, B, e, o);
+                    eval_barrier<R, HT>(L, T.scene, T.blk, S, B, e, o);
                 if (L.out_E) L.out_E[e] = o.E;
                 else S.Ee[B.base + e] = o.E;
             }
@@ -543,6 +504,76 @@ k_elements(ElemLaunch L)
     }
 }
 
+// phase 2 of the projection: one thread per queued stencil; subtracts
+// sum_{lambda_t < -tau} lambda_t u_t u_t^T from its Hessian blocks
+template <typename HT>
+__global__ void __launch_bounds__(kClampThreads)
+k_clamp(ElemLaunch L)
+{
+    __shared__ double Xs[81 * kClampThreads];
+    const SmemMat X{Xs + threadIdx.x, kClampThreads};
+    const int count = min(*L.clamp_count, L.clamp_cap);
+    // every thread of a block takes the same number of trips
+    const int64_t span = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += span) {
+        const int64_t idx = base + threadIdx.x;
+        if (idx >= count) break;
+        const ClampRef ref = L.clamp_ref[idx];
+        const double* Mg = L.clamp_M + 45 * idx;
+        double tau;
+        {
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+#pragma unroll
+                for (int j = 0; j <= i; ++j) {
+                    const double v = Mg[pk(i, j)];
+                    s = fma((i == j ? 1.0 : 2.0) * v, v, s);
+                }
+            tau = 1e-13 * sqrt(s);
+        }
+        double lam[9];
+        eig9(Mg, X, lam);
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ok = ok && isfinite(lam[i]);
+        if (!ok) {
+            atomicAdd(L.clamp_failed, 1);
+            atomicExch(&L.scenes[ref.scene].sc->clamp_fail, 1);
+            continue;
+        }
+        const SceneDev& S = L.scenes[ref.scene];
+        const ElemBlock& B = S.blk[ref.blk];
+        HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (B.base + ref.e);
+        double* full = L.out_H ? L.out_H + 144 * ref.e : nullptr;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (!(lam[i] < -tau)) continue;
+            double u[12];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                had_inv(X(r, i), X(3 + r, i), X(6 + r, i), u[r], u[3 + r], u[6 + r], u[9 + r]);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = a; b < 4; ++b)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const double v = lam[i] * u[3 * a + r] * u[3 * b + c];
+                            if (staged) {
+                                HT* p = staged + 9 * up_index(a, b) + 3 * r + c;
+                                *p = (HT)((double)*p - v);
+                            } else {
+                                full[(3 * a + r) * 12 + 3 * b + c] -= v;
+                                if (a != b) full[(3 * b + c) * 12 + 3 * a + r] -= v;
+                            }
+                        }
+        }
+    }
+}
+
 const void* elements_kernel(int precision)
 {
     return precision == SX_FP32 ? (const void*)k_elements<float, float>
@@ -554,10 +585,27 @@ cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s)
     if (L.ntiles == 0) return cudaSuccess;
     cudaError_t err = cudaMemsetAsync(L.queue, 0, sizeof(int), s);
     if (err != cudaSuccess) return err;
+    if (L.level >= 2 && L.project) {
+        err = cudaMemsetAsync(L.clamp_count, 0, sizeof(int), s);
+        if (err != cudaSuccess) return err;
+    }
     if (L.precision == SX_FP32)
         k_elements<float, float><<<grid, kElemThreads, 0, s>>>(L);
     else
         k_elements<double, double><<<grid, kElemThreads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
+{
+    if (L.ntiles == 0 || !(L.level >= 2 && L.project)) return cudaSuccess;
+    // the queue length stays on the device; the grid covers it in
+    // grid-stride loops
+    const int cgrid = L.clamp_grid > 0 ? L.clamp_grid : 1;
+    if (L.precision == SX_FP32)
+        k_clamp<float><<<cgrid, kClampThreads, 0, s>>>(L);
+    else
+        k_clamp<double><<<cgrid, kClampThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
 

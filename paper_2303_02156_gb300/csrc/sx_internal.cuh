@@ -78,7 +78,7 @@ struct SceneScal {
     int bad_state;     // barrier pairs with d <= 0 in the last evaluation
     int nonfinite;     // non-finite values seen in the last evaluation
     int clamped;       // elements projected in the last EGH evaluation
-    int pad;
+    int clamp_fail;    // set by the projection kernel if QL did not converge
 };
 
 struct SceneDev {
@@ -133,6 +133,12 @@ struct Tile {
 
 // ---------------------------------------------------------------- kernels
 // element evaluation (sx_elements.cu)
+struct ClampRef {
+    int scene;
+    int blk;
+    int64_t e;   // element index inside its energy block
+};
+
 struct ElemLaunch {
     const SceneDev* scenes;
     const Tile* tiles;
@@ -152,8 +158,17 @@ struct ElemLaunch {
     double* out_E;
     double* out_g;
     double* out_H;
+    // projection queue: translation-free 9x9 Hessians (45 packed doubles)
+    // of the stencils that failed the PSD test, and where their blocks live
+    double* clamp_M;
+    ClampRef* clamp_ref;
+    int* clamp_count;
+    int* clamp_failed;
+    int clamp_cap;
+    int clamp_grid;
 };
 cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s);
+cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s);
 int elements_block_threads();
 const void* elements_kernel(int precision);
 
