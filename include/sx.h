@@ -214,6 +214,33 @@ int sx_eval_stats(sx_scene* scene, int* clamped, int* bad_state, int* nonfinite,
 int sx_eval_elements(sx_scene* scene, int energy_id, int project, int precision,
                      double* E, double* g, double* H, int32_t* slots, void* stream);
 
+/* ---- element-level outputs without device allocation -------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let a call allocate device memory -- for example an application
+ * whose device memory is already reserved by its own caching allocator,
+ * or a fixed-latency simulation loop that must not take the implicit
+ * device-wide synchronization of cudaMalloc/cudaFree. It computes exactly
+ * what sx_eval_elements computes (same kernels), but all of its scratch
+ * (tile table, projection queue of SX_NOALLOC_MAX_ELEMENTS x 45 doubles,
+ * counters, scene descriptor) lives in static device arrays of this
+ * library, about 25 MB that every GPU which loads the library holds until
+ * the process exits. It makes no cudaMalloc/cudaFree call and calls no
+ * allocating routine.
+ *  - Blocks with more than SX_NOALLOC_MAX_ELEMENTS elements are rejected
+ *    with SX_EINVAL.
+ *  - E, g, H: device outputs as in sx_eval_elements (n, n x 12,
+ *    n x 144); a NULL E or g sends that output to the scene's own staging
+ *    buffers instead. The call synchronizes `stream`.
+ *  - The first call on a device looks up the addresses of the static
+ *    arrays (cudaGetSymbolAddress) for that device; make that first call
+ *    before capturing any stream.
+ *  - Every call shares the same static arrays: calls that overlap on the
+ *    GPU (other streams, other host threads) race and must be serialized
+ *    by the caller. Counters are cleared by each call. */
+#define SX_NOALLOC_MAX_ELEMENTS 65536
+int sx_eval_elements_noalloc(sx_scene* scene, int energy_id, int project, int precision,
+                             double* E, double* g, double* H, void* stream);
+
 /* ---- backward-Euler Newton step (§3 Eqs. 2-3; §7.2 solver) ------------ */
 typedef struct {
     double newton_tol;   /* stop when ||g_free|| <= tol * ||g_free(x0)|| */

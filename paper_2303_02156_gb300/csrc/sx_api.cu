@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1334,3 +1335,118 @@ int sx_scene_bytes(sx_scene* s, int64_t* bytes)
 }
 
 }  // extern "C"
+
+// ==================================================================== no-alloc
+// Scratch of sx_eval_elements_noalloc: file-scope device arrays, so that
+// the call never allocates. In host code these names are only stand-ins
+// for the device symbols; their device addresses come from
+// cudaGetSymbolAddress, looked up once per device.
+namespace {
+
+constexpr int kNaMaxTiles = (SX_NOALLOC_MAX_ELEMENTS + 127) / 128;
+
+static __device__ __align__(256) SceneDev g_na_desc[1];
+static __device__ __align__(256) Tile g_na_tiles[kNaMaxTiles];
+static __device__ __align__(256) int g_na_counters[4];   // queue, clamp count, clamp failures
+static __device__ __align__(256) double g_na_clampM[(size_t)SX_NOALLOC_MAX_ELEMENTS * 45];
+static __device__ __align__(256) ClampRef g_na_clampRef[SX_NOALLOC_MAX_ELEMENTS];
+
+struct NaPtrs {
+    bool ready = false;
+    SceneDev* desc = nullptr;
+    Tile* tiles = nullptr;
+    int* counters = nullptr;
+    double* clampM = nullptr;
+    ClampRef* clampRef = nullptr;
+};
+
+constexpr int kNaMaxDevices = 64;
+NaPtrs g_na_ptrs[kNaMaxDevices];
+std::mutex g_na_mutex;
+
+// once per device, with that device current
+int na_setup(sx_ctx* ctx, NaPtrs** out)
+{
+    const int dev = ctx->device;
+    if (dev < 0 || dev >= kNaMaxDevices) return fail(ctx, SX_EINVAL, "noalloc: device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    NaPtrs& P = g_na_ptrs[dev];
+    if (!P.ready) {
+        int prev = -1;
+        CK(cudaGetDevice(&prev));
+        if (prev != dev) CK(cudaSetDevice(dev));
+        cudaError_t e = cudaGetSymbolAddress((void**)&P.desc, g_na_desc);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&P.tiles, g_na_tiles);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&P.counters, g_na_counters);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&P.clampM, g_na_clampM);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&P.clampRef, g_na_clampRef);
+        if (prev != dev) cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "noalloc: cudaGetSymbolAddress");
+        P.ready = true;
+    }
+    *out = &P;
+    return SX_OK;
+}
+
+}  // namespace
+
+extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project, int precision,
+                                        double* E, double* g, double* H, void* stream)
+{
+    int rc = check_scene_ready(s);
+    if (rc != SX_OK) return rc;
+    sx_ctx* ctx = s->ctx;
+    if (energy_id < 0 || energy_id >= (int)s->blocks.size())
+        return fail(ctx, SX_EINVAL, "eval_elements_noalloc: bad energy id");
+    if (precision != SX_FP64 && precision != SX_FP32)
+        return fail(ctx, SX_EINVAL, "eval_elements_noalloc: bad precision");
+    const BlockHost& b = s->blocks[energy_id];
+    if (b.n > SX_NOALLOC_MAX_ELEMENTS)
+        return fail(ctx, SX_EINVAL,
+                    "eval_elements_noalloc: block has " + std::to_string(b.n) +
+                        " elements, more than the static scratch holds (" +
+                        std::to_string(SX_NOALLOC_MAX_ELEMENTS) + ")");
+    if (b.n == 0) return SX_OK;
+    NaPtrs* P = nullptr;
+    if ((rc = na_setup(ctx, &P)) != SX_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    // scene descriptor and tile table into the static arrays (pageable
+    // sources: each copy returns once the source has been consumed)
+    const SceneDev desc = make_desc(s, false);
+    CK(cudaMemcpyAsync(P->desc, &desc, sizeof(desc), cudaMemcpyHostToDevice, st));
+    Tile tiles[kNaMaxTiles];
+    const int et = elements_block_threads();
+    int nt = 0;
+    for (int64_t k = 0; k < b.n; k += et)
+        tiles[nt++] = Tile{0, energy_id, k, (int)std::min<int64_t>(et, b.n - k), 0};
+    CK(cudaMemcpyAsync(P->tiles, tiles, nt * sizeof(Tile), cudaMemcpyHostToDevice, st));
+    static const int one = 1;
+    CK(cudaMemcpyAsync((char*)s->sc + offsetof(SceneScal, active), &one, sizeof(int),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(P->counters, 0, 4 * sizeof(int), st));
+    ElemLaunch L{};
+    L.scenes = P->desc;
+    L.tiles = P->tiles;
+    L.ntiles = nt;
+    L.level = H ? 2 : (g ? 1 : 0);
+    L.project = project;
+    L.precision = precision;
+    L.queue = P->counters;
+    L.out_E = E;
+    L.out_g = g;
+    L.out_H = H;
+    L.clamp_M = P->clampM;
+    L.clamp_ref = P->clampRef;
+    L.clamp_count = P->counters + 1;
+    L.clamp_failed = P->counters + 2;
+    L.clamp_cap = SX_NOALLOC_MAX_ELEMENTS;
+    L.clamp_grid = ctx->sm_count * 8;
+    const int grid = std::max(1, std::min<int>(nt, ctx->sm_count * ctx->elem_blocks_per_sm[precision == SX_FP32]));
+    PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
+    if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
+    int failed = 0;
+    CK(cudaMemcpyAsync(&failed, P->counters + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (failed) return fail(ctx, SX_ENAN, "eval_elements_noalloc: projection did not converge");
+    return SX_OK;
+}

@@ -35,8 +35,9 @@ EXPORTS = [
     "sx_get_grad", "sx_get_diag_slots", "sx_eval_elements", "sx_newton_opts_default",
     "sx_newton_step", "sx_newton_step_batch", "sx_scene_footprint", "sx_scene_bytes",
     "sx_copy_bsr", "sx_copy_grad", "sx_scene_info", "sx_block_info", "sx_eval_stats",
-    "sx_profile", "sx_profile_read",
+    "sx_profile", "sx_profile_read", "sx_eval_elements_noalloc",
 ]
+SX_NOALLOC_MAX_ELEMENTS = 65536
 PHASES = ["elements", "clamp", "assemble", "grad", "reduce", "spmv", "pcg", "newton", "other"]
 
 
@@ -103,6 +104,7 @@ _SIGS = {
     "sx_eval_stats": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), _P]),
     "sx_profile": (_I, [_P, _I]),
     "sx_profile_read": (_I, [_P, C.POINTER(_D), C.POINTER(_I64), _I]),
+    "sx_eval_elements_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
 }
 
 _lib = None
