@@ -251,9 +251,14 @@ typedef struct {
     int project;         /* project element Hessians to PSD */
     int precision;       /* SX_FP64 or SX_FP32 */
     double armijo_c;     /* sufficient-decrease constant */
+    int forcing;         /* 1: PCG stops at ||r|| <= eta_k ||b|| with the forcing
+                            sequence eta_k = min(1/2, sqrt(||g_k|| / ||g_0||))
+                            (the paper's solver, §7.2; Nocedal-Wright), never
+                            below pcg_tol; 0: fixed pcg_tol */
+    int reserved;
 } sx_newton_opts;
 
-/* Defaults: 1e-8, 1e-10, 100, 10000, 30, 1, SX_FP64, 1e-4. */
+/* Defaults: 1e-8, 1e-10, 100, 10000, 30, 1, SX_FP64, 1e-4, forcing 0. */
 void sx_newton_opts_default(sx_newton_opts* o);
 
 typedef struct {
@@ -315,6 +320,73 @@ typedef struct {
 int sx_scene_footprint(const sx_scene_desc* desc, int64_t* bytes);
 /* Device bytes this scene holds now. */
 int sx_scene_bytes(sx_scene* scene, int64_t* bytes);
+
+/* ---- serving: continuous batching of backward-Euler steps -------------
+ * A server owns a worker thread that, per tick, (1) admits waiting requests
+ * in arrival order while their device footprint fits the memory budget
+ * (registration, rest precompute and pattern build happen at admission),
+ * (2) runs one batched Newton step (sx_newton_step_batch) over every
+ * resident scene -- requests that arrived while others were on the GPU join
+ * the next tick at their own step 0 -- and (3) retires finished requests,
+ * keeping their final state on the host and freeing their device memory.
+ * Each scene's result does not depend on what it is batched with (all
+ * reductions are per scene and in a fixed order). While a server runs, its
+ * context must not be used by other calls. Step latency is measured from a
+ * step's eligibility (request admitted and its previous step done) to the
+ * end of the tick that completed it. */
+typedef struct {
+    int64_t n_nodes;
+    const double* X;          /* n_nodes x 3 rest positions (host) */
+    int64_t n_tets;
+    const int32_t* tets;      /* n_tets x 4 (host) */
+    const double* young;      /* n_tets (host) */
+    const double* poisson;    /* n_tets (host) */
+    double density;
+    int64_t n_pinned;
+    const int32_t* pinned;    /* n_pinned node ids (host, may be NULL) */
+    double gravity[3];
+} sx_snh_scene_spec;
+
+typedef struct {
+    int64_t req_id;
+    int status;               /* SX_OK or the failing code */
+    int steps;                /* steps taken */
+    int64_t n_tets;
+    double submit_ms;         /* times on the server clock (ms since create) */
+    double admit_ms;
+    double done_ms;
+    double mean_step_ms;
+} sx_completion;
+
+typedef struct {
+    int64_t submitted, admitted, completed, rejected;
+    int64_t element_steps;    /* sum over completed steps of the scene's tets */
+    double wall_ms;           /* since create */
+    double busy_ms;           /* time spent in ticks */
+    double step_p50_ms, step_p99_ms;
+    double request_p50_ms, request_p99_ms;   /* submit -> done */
+    int64_t bytes_in_use, peak_bytes;
+    int active, pending, ticks;
+} sx_serve_stats;
+
+/* opts: Newton options for every step (NULL = defaults). Synchronous. */
+int sx_server_create(sx_ctx* ctx, int64_t hbm_budget_bytes, const sx_newton_opts* opts,
+                     sx_server** srv);
+/* Copies the spec (the caller's arrays may be freed on return) and queues
+ * the request; SX_EBUDGET if its footprint alone exceeds the budget. */
+int sx_server_submit(sx_server* srv, const sx_snh_scene_spec* spec, int n_steps, double dt,
+                     int64_t* req_id);
+/* Up to `max` completions not yet returned; *n receives their number. */
+int sx_server_poll(sx_server* srv, sx_completion* out, int max, int* n);
+/* Final state of a completed request (host buffers, n_nodes x 3 each; either
+ * may be NULL); releases it. SX_EINVAL if unknown or not complete. */
+int sx_server_result(sx_server* srv, int64_t req_id, double* x, double* v);
+/* Blocks until nothing is pending or active (or timeout_ms elapses: then
+ * SX_ENOTCONV). */
+int sx_server_drain(sx_server* srv, double timeout_ms);
+int sx_server_stats(sx_server* srv, sx_serve_stats* st);
+/* Stops the worker after the current tick and frees everything. */
+int sx_server_destroy(sx_server* srv);
 
 #ifdef __cplusplus
 }

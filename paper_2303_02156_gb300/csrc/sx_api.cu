@@ -62,6 +62,12 @@ struct sx_ctx {
     std::string err;
     int* queue = nullptr;
     std::vector<std::unique_ptr<Batch>> batch_cache;
+    // projection queue shared by every evaluation of this context (grown on
+    // demand; a context runs one evaluation at a time)
+    double* clampM = nullptr;
+    ClampRef* clampRef = nullptr;
+    int* clampCount = nullptr;   // [0] count, [1] failures
+    int64_t clamp_cap = 0;
 };
 
 struct sx_scene {
@@ -126,13 +132,9 @@ struct Batch {
     double* d_ctl_d = nullptr;
     int* h_ctl_i = nullptr;
     double* h_ctl_d = nullptr;
-    double* d_clampM = nullptr;      // projection queue (45 doubles per entry)
-    ClampRef* d_clampRef = nullptr;
-    int* d_clampCount = nullptr;     // [0] count, [1] failures
-    int clamp_cap = 0;
+    int64_t clamp_need = 0;          // projectable stencils of the batch
     ~Batch()
     {
-        cudaFree(d_clampM); cudaFree(d_clampRef); cudaFree(d_clampCount);
         cudaFree(d_desc); cudaFree(d_desc_trial); cudaFree(d_elem); cudaFree(d_node);
         cudaFree(d_slot); cudaFree(d_elem_beg); cudaFree(d_elem_end); cudaFree(d_node_beg);
         cudaFree(d_node_end); cudaFree(d_part_elem); cudaFree(d_part_node); cudaFree(d_bad);
@@ -342,11 +344,7 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         for (sx_scene* s : B->scenes)
             for (auto& b : s->blocks)
                 if (b.kind != SX_KIND_HINGE4) cap += b.n;
-        B->clamp_cap = (int)std::min<int64_t>(std::max<int64_t>(cap, 1), INT32_MAX);
-        CK(cudaMalloc((void**)&B->d_clampM, (size_t)B->clamp_cap * 45 * sizeof(double)));
-        CK(cudaMalloc((void**)&B->d_clampRef, (size_t)B->clamp_cap * sizeof(ClampRef)));
-        CK(cudaMalloc((void**)&B->d_clampCount, 2 * sizeof(int)));
-        CK(cudaMemset(B->d_clampCount, 0, 2 * sizeof(int)));
+        B->clamp_need = std::max<int64_t>(cap, 1);
         CK(cudaMalloc((void**)&B->d_desc, n * sizeof(SceneDev)));
         CK(cudaMalloc((void**)&B->d_desc_trial, n * sizeof(SceneDev)));
         B->versions.assign(n, 0);
@@ -364,6 +362,28 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
     return SX_OK;
 }
 
+// grows the context's projection queue to hold `need` stencils
+int ensure_clamp_queue(sx_ctx* ctx, int64_t need)
+{
+    if (need > (int64_t)INT32_MAX) return fail(ctx, SX_EINVAL, "eval: too many projectable stencils");
+    if (ctx->clamp_cap >= need && ctx->clampM) return SX_OK;
+    cudaFree(ctx->clampM);
+    cudaFree(ctx->clampRef);
+    ctx->clampM = nullptr;
+    ctx->clampRef = nullptr;
+    if (!ctx->clampCount) CK(cudaMalloc((void**)&ctx->clampCount, 2 * sizeof(int)));
+    if (cudaMalloc((void**)&ctx->clampM, (size_t)need * 45 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->clampRef, (size_t)need * sizeof(ClampRef)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->clampM);
+        ctx->clampM = nullptr;
+        ctx->clamp_cap = 0;
+        return fail(ctx, SX_ENOMEM, "eval: device allocation failed (projection queue)");
+    }
+    ctx->clamp_cap = need;
+    return SX_OK;
+}
+
 Batch* get_batch(sx_ctx* ctx, sx_scene* const* scenes, int n)
 {
     for (auto& b : ctx->batch_cache) {
@@ -372,7 +392,7 @@ Batch* get_batch(sx_ctx* ctx, sx_scene* const* scenes, int n)
         for (int i = 0; i < n && same; ++i) same = b->scenes[i] == scenes[i];
         if (same) return b.get();
     }
-    if (ctx->batch_cache.size() >= 16) ctx->batch_cache.erase(ctx->batch_cache.begin());
+    if (ctx->batch_cache.size() >= 8) ctx->batch_cache.erase(ctx->batch_cache.begin());
     auto B = std::make_unique<Batch>();
     B->scenes.assign(scenes, scenes + n);
     ctx->batch_cache.push_back(std::move(B));
@@ -395,7 +415,7 @@ int set_active(sx_ctx* ctx, Batch* B, const std::vector<int>& act, cudaStream_t 
     const int n = (int)B->scenes.size();
     for (int i = 0; i < n; ++i) B->h_ctl_i[i] = act[i];
     CK(cudaMemcpyAsync(B->d_ctl_i, B->h_ctl_i, n * sizeof(int), cudaMemcpyHostToDevice, st));
-    PL(SX_PH_OTHER, 1, launch_set_scal(B->d_desc, n, B->d_ctl_i, nullptr, st));
+    PL(SX_PH_OTHER, 1, launch_set_scal(B->d_desc, n, B->d_ctl_i, nullptr, nullptr, st));
     return SX_OK;
 }
 
@@ -404,7 +424,16 @@ int set_alpha(sx_ctx* ctx, Batch* B, const std::vector<double>& a, cudaStream_t 
     const int n = (int)B->scenes.size();
     for (int i = 0; i < n; ++i) B->h_ctl_d[i] = a[i];
     CK(cudaMemcpyAsync(B->d_ctl_d, B->h_ctl_d, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    PL(SX_PH_OTHER, 1, launch_set_scal(B->d_desc, n, nullptr, B->d_ctl_d, st));
+    PL(SX_PH_OTHER, 1, launch_set_scal(B->d_desc, n, nullptr, B->d_ctl_d, nullptr, st));
+    return SX_OK;
+}
+
+int set_pcg_tol(sx_ctx* ctx, Batch* B, const std::vector<double>& t, cudaStream_t st)
+{
+    const int n = (int)B->scenes.size();
+    for (int i = 0; i < n; ++i) B->h_ctl_d[i] = t[i];
+    CK(cudaMemcpyAsync(B->d_ctl_d, B->h_ctl_d, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    PL(SX_PH_OTHER, 1, launch_set_scal(B->d_desc, n, nullptr, nullptr, B->d_ctl_d, st));
     return SX_OK;
 }
 
@@ -444,11 +473,15 @@ int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool 
     L.tile_nonfinite = B->d_nonfin;
     L.tile_clamped = B->d_clamped;
     L.queue = ctx->queue;
-    L.clamp_M = B->d_clampM;
-    L.clamp_ref = B->d_clampRef;
-    L.clamp_count = B->d_clampCount;
-    L.clamp_failed = B->d_clampCount + 1;
-    L.clamp_cap = B->clamp_cap;
+    if (level >= 2 && project) {
+        int rq = ensure_clamp_queue(ctx, B->clamp_need);
+        if (rq != SX_OK) return rq;
+    }
+    L.clamp_M = ctx->clampM;
+    L.clamp_ref = ctx->clampRef;
+    L.clamp_count = ctx->clampCount;
+    L.clamp_failed = ctx->clampCount + 1;
+    L.clamp_cap = (int)std::min<int64_t>(ctx->clamp_cap, INT32_MAX);
     L.clamp_grid = ctx->sm_count * 8;
     const int pidx = precision == SX_FP32 ? 1 : 0;
     int grid = std::min<int>(L.ntiles, ctx->sm_count * ctx->elem_blocks_per_sm[pidx]);
@@ -597,6 +630,9 @@ int sx_destroy(sx_ctx* ctx)
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     ctx->batch_cache.clear();
     cudaFree(ctx->queue);
+    cudaFree(ctx->clampM);
+    cudaFree(ctx->clampRef);
+    cudaFree(ctx->clampCount);
     delete ctx;
     return SX_OK;
 }
@@ -1149,6 +1185,8 @@ void sx_newton_opts_default(sx_newton_opts* o)
     o->project = 1;
     o->precision = SX_FP64;
     o->armijo_c = 1e-4;
+    o->forcing = 0;
+    o->reserved = 0;
 }
 
 int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
@@ -1178,7 +1216,10 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
     std::vector<double> g0(n, 0.0), gl(n, 0.0), E(n, 0.0);
     std::vector<int> act(n, 1);
     if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
-    PL(SX_PH_NEWTON, 1, launch_predict(B->d_desc, B->d_node, nnt, st));
+    PL(SX_PH_NEWTON, 1, launch_predict(B->d_desc, B->d_node, nnt, B->d_part_node, st));
+    PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_node, 1, 0, B->d_node_beg, B->d_node_end,
+                                            n, B->d_desc, F_FEXT2, 0, st));
+    std::vector<double> fext(n, 0.0);
     for (int it = 0; it <= o.max_newton; ++it) {
         for (int i = 0; i < n; ++i) act[i] = !done[i];
         if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
@@ -1193,8 +1234,16 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             if (sc.bad_state) { status[i] = SX_ESTATE; done[i] = 1; continue; }
             double gn = std::sqrt(sc.gnorm2);
             gl[i] = gn;
-            if (it == 0) g0[i] = gn;
-            if (gn <= o.newton_tol * std::max(g0[i], 1e-30)) { done[i] = 1; continue; }
+            if (it == 0) {
+                g0[i] = gn;
+                fext[i] = std::sqrt(sc.fext2);
+            }
+            // residual against the larger of the initial residual and the
+            // external force on the free DOFs
+            if (gn <= o.newton_tol * std::max(std::max(g0[i], fext[i]), 1e-30)) {
+                done[i] = 1;
+                continue;
+            }
             if (it == o.max_newton) { status[i] = SX_ENOTCONV; done[i] = 1; continue; }
             iters[i] = it + 1;
             ++live;
@@ -1202,7 +1251,16 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
         if (!live) break;
         for (int i = 0; i < n; ++i) act[i] = !done[i];
         if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
-        // ---- PCG on H dx = -g
+        // ---- PCG on H dx = -g (fixed tolerance or forcing sequence)
+        {
+            std::vector<double> tl(n, o.pcg_tol);
+            if (o.forcing)
+                for (int i = 0; i < n; ++i)
+                    if (act[i])
+                        tl[i] = std::max(o.pcg_tol,
+                                         std::min(0.5, std::sqrt(gl[i] / std::max(g0[i], 1e-300))));
+            if ((rc = set_pcg_tol(ctx, B, tl, st)) != SX_OK) return rc;
+        }
         PL(SX_PH_PCG, 1, launch_pcg_setup_p(B->d_desc, B->d_node, nnt, o.precision,
                                             B->d_part_node, st));
         PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg, B->d_node_end, n,
@@ -1259,8 +1317,11 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             for (int i = 0; i < n; ++i) {
                 if (!search[i]) continue;
                 const SceneScal& sc = B->h_scal[i];
+                // below the resolution of double energies (|g.dx| < 1e-12 |E|)
+                // the Armijo comparison is noise: take the full Newton step
+                const bool tiny = std::fabs(gdx[i]) < 1e-12 * std::fabs(E[i]);
                 bool ok = sc.bad_state == 0 && sc.nonfinite == 0 && std::isfinite(sc.E) &&
-                          sc.E <= E[i] + o.armijo_c * alpha[i] * gdx[i];
+                          (tiny || sc.E <= E[i] + o.armijo_c * alpha[i] * gdx[i]);
                 if (ok) {
                     acc[i] = 1;
                     search[i] = 0;

@@ -191,6 +191,7 @@ __device__ __forceinline__ double* scal_field(SceneScal* sc, int f)
     switch (f) {
         case F_E: return &sc->E;
         case F_GNORM2: return &sc->gnorm2;
+        case F_FEXT2: return &sc->fext2;
         default: return &sc->gdx;
     }
 }
@@ -287,20 +288,21 @@ cudaError_t launch_gather_scal(const SceneDev* scenes, int n, SceneScal* out, cu
 
 // write per-scene control values: active flags and (optionally) step sizes
 __global__ void k_set_scal(const SceneDev* scenes, int n, const int* active,
-                           const double* ls_alpha)
+                           const double* ls_alpha, const double* pcg_tol)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     SceneScal* sc = scenes[i].sc;
     if (active) sc->active = active[i];
     if (ls_alpha) sc->ls_alpha = ls_alpha[i];
+    if (pcg_tol) sc->pcg_tol = pcg_tol[i];
 }
 
 cudaError_t launch_set_scal(const SceneDev* scenes, int n, const int* active,
-                            const double* ls_alpha, cudaStream_t s)
+                            const double* ls_alpha, const double* pcg_tol, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_set_scal<<<(n + 127) / 128, 128, 0, s>>>(scenes, n, active, ls_alpha);
+    k_set_scal<<<(n + 127) / 128, 128, 0, s>>>(scenes, n, active, ls_alpha, pcg_tol);
     return cudaGetLastError();
 }
 

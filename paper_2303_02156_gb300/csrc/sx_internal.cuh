@@ -70,6 +70,8 @@ struct SceneScal {
     double pcg_alpha;
     double pcg_beta;
     double ls_alpha;   // line-search step
+    double pcg_tol;    // relative PCG tolerance of the current solve
+    double fext2;      // ||M g_ext||^2 over the free DOFs (Newton residual scale)
     double grav[3];    // external acceleration (M^-1 f_ext)
     int pcg_done;      // 1 once converged or stopped (kernels skip the scene)
     int pcg_iters;
@@ -209,7 +211,7 @@ cudaError_t launch_assemble_grad(const SceneDev* scenes, const Tile* node_tiles,
 cudaError_t launch_inertia_energy(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
                                   const double* unused, double* tile_part, int use_trial,
                                   cudaStream_t s);
-enum ScalField { F_E = 0, F_GNORM2 = 1, F_GDX = 2 };
+enum ScalField { F_E = 0, F_GNORM2 = 1, F_GDX = 2, F_FEXT2 = 3 };
 cudaError_t launch_scene_reduce(const double* part, int stride, int off, const int* tbeg,
                                 const int* tend, int nscenes, const SceneDev* scenes,
                                 int field, int accumulate, cudaStream_t s);
@@ -218,11 +220,11 @@ cudaError_t launch_scene_reduce_flags(const int* bad, const int* nonfin, const i
                                       const SceneDev* scenes, cudaStream_t s);
 cudaError_t launch_gather_scal(const SceneDev* scenes, int n, SceneScal* out, cudaStream_t s);
 cudaError_t launch_set_scal(const SceneDev* scenes, int n, const int* active,
-                            const double* ls_alpha, cudaStream_t s);
+                            const double* ls_alpha, const double* pcg_tol, cudaStream_t s);
 
 // solver (sx_solve.cu)
 cudaError_t launch_predict(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
-                           cudaStream_t s);
+                           double* part, cudaStream_t s);
 cudaError_t launch_pcg_setup_p(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
                                int precision, double* part, cudaStream_t s);
 cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int ntiles,

@@ -26,26 +26,41 @@ __device__ __forceinline__ bool scene_live(const SceneDev& S)
 }
 
 // ------------------------------------------------------------------ predictor
-__global__ void k_predict(const SceneDev* scenes, const Tile* tiles, int ntiles)
+// x_start = x, x~ = x + dt v + dt^2 g; tile partial: sum over free nodes of
+// m^2 |g|^2 (the external-force scale of the Newton residual test)
+__global__ void __launch_bounds__(kVecThreads)
+k_predict(const SceneDev* scenes, const Tile* tiles, int ntiles, double* part)
 {
+    __shared__ double sh[kVecThreads];
     const Tile T = tiles[blockIdx.x];
     const SceneDev& S = scenes[T.scene];
-    if (!scene_live(S) || (int)threadIdx.x >= T.count) return;
-    const int64_t n = T.start + threadIdx.x;
-    const double dt = S.dt;
+    double f2 = 0.0;
+    if (scene_live(S) && (int)threadIdx.x < T.count) {
+        const int64_t n = T.start + threadIdx.x;
+        const double dt = S.dt;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const double x = S.x[3 * n + i];
-        S.x_start[3 * n + i] = x;
-        S.x_tilde[3 * n + i] = x + dt * S.v[3 * n + i] + dt * dt * S.sc->grav[i];
+        for (int i = 0; i < 3; ++i) {
+            const double x = S.x[3 * n + i];
+            const double g = S.sc->grav[i];
+            S.x_start[3 * n + i] = x;
+            S.x_tilde[3 * n + i] = x + dt * S.v[3 * n + i] + dt * dt * g;
+            if (!S.pinned[n]) f2 += S.mass[n] * S.mass[n] * g * g;
+        }
     }
+    sh[threadIdx.x] = f2;
+    __syncthreads();
+    for (int w = kVecThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
 cudaError_t launch_predict(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
-                           cudaStream_t s)
+                           double* part, cudaStream_t s)
 {
     if (!ntiles) return cudaSuccess;
-    k_predict<<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles);
+    k_predict<<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, part);
     return cudaGetLastError();
 }
 
@@ -296,7 +311,8 @@ __global__ void k_pcg_reduce(const double* part, int nv, const int* tbeg, const 
         sc->rz_new = a;
         sc->rr = b;
         sc->pcg_iters += 1;
-        if (b <= tol * tol * sc->bnorm2) {
+        const double t = sc->pcg_tol > 0.0 ? sc->pcg_tol : tol;
+        if (b <= t * t * sc->bnorm2) {
             sc->pcg_done = 1;
         } else if (sc->pcg_iters >= max_iter || !isfinite(b)) {
             sc->pcg_done = 1;

@@ -211,3 +211,63 @@ class Scene:
         b = C.c_int64()
         self.ctx.check(sx.sx_scene_bytes(self.h, C.byref(b)))
         return b.value
+
+
+class Server:
+    """Continuous-batching request loop (include/sx.h serving section)."""
+
+    def __init__(self, ctx: Context, budget_bytes: int, **opts):
+        self.ctx = ctx
+        o = sx.newton_opts(**opts)
+        h = C.c_void_p()
+        ctx.check(sx.sx_server_create(ctx.h, int(budget_bytes), C.byref(o), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, X, tets, young, poisson, density=1000.0, pinned=None,
+               gravity=(0.0, 0.0, -9.81), n_steps=10, dt=0.01):
+        X = _f64(X).reshape(-1, 3); tets = _i32(tets)
+        n = tets.shape[0]
+        E = _f64(np.broadcast_to(young, (n,))); nu = _f64(np.broadcast_to(poisson, (n,)))
+        pn = None if pinned is None else _i32(pinned)
+        sp = sx.sx_snh_scene_spec()
+        sp.n_nodes = X.shape[0]; sp.X = X.ctypes.data
+        sp.n_tets = n; sp.tets = tets.ctypes.data
+        sp.young = E.ctypes.data; sp.poisson = nu.ctypes.data
+        sp.density = float(density)
+        sp.n_pinned = 0 if pn is None else pn.size
+        sp.pinned = None if pn is None or pn.size == 0 else pn.ctypes.data
+        for i in range(3):
+            sp.gravity[i] = float(gravity[i])
+        rid = C.c_int64()
+        rc = sx.sx_server_submit(self.h, C.byref(sp), int(n_steps), float(dt), C.byref(rid))
+        if rc != sx.SX_OK:
+            raise sx.SxError(rc, "server submit")
+        self._keep[rid.value] = X.shape[0]
+        return rid.value
+
+    def poll(self, max_n=1024):
+        arr = (sx.sx_completion * max_n)()
+        n = C.c_int()
+        self.ctx.check(sx.sx_server_poll(self.h, arr, max_n, C.byref(n)))
+        return [{k: getattr(arr[i], k) for k, _ in sx.sx_completion._fields_}
+                for i in range(n.value)]
+
+    def result(self, req_id):
+        N = self._keep.pop(req_id)
+        x = np.empty((N, 3)); v = np.empty((N, 3))
+        self.ctx.check(sx.sx_server_result(self.h, int(req_id), x.ctypes.data, v.ctypes.data))
+        return x, v
+
+    def drain(self, timeout_ms=600000.0):
+        return sx.sx_server_drain(self.h, float(timeout_ms))
+
+    def stats(self):
+        st = sx.sx_serve_stats()
+        self.ctx.check(sx.sx_server_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in sx.sx_serve_stats._fields_}
+
+    def close(self):
+        if self.h:
+            sx.sx_server_destroy(self.h)
+            self.h = None

@@ -36,6 +36,8 @@ EXPORTS = [
     "sx_newton_step", "sx_newton_step_batch", "sx_scene_footprint", "sx_scene_bytes",
     "sx_copy_bsr", "sx_copy_grad", "sx_scene_info", "sx_block_info", "sx_eval_stats",
     "sx_profile", "sx_profile_read", "sx_eval_elements_noalloc",
+    "sx_server_create", "sx_server_submit", "sx_server_poll", "sx_server_result",
+    "sx_server_drain", "sx_server_stats", "sx_server_destroy",
 ]
 SX_NOALLOC_MAX_ELEMENTS = 65536
 PHASES = ["elements", "clamp", "assemble", "grad", "reduce", "spmv", "pcg", "newton", "other"]
@@ -48,7 +50,8 @@ class sx_options(C.Structure):
 class sx_newton_opts(C.Structure):
     _fields_ = [("newton_tol", C.c_double), ("pcg_tol", C.c_double),
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("max_halvings", C.c_int),
-                ("project", C.c_int), ("precision", C.c_int), ("armijo_c", C.c_double)]
+                ("project", C.c_int), ("precision", C.c_int), ("armijo_c", C.c_double),
+                ("forcing", C.c_int), ("reserved", C.c_int)]
 
 
 class sx_step_report(C.Structure):
@@ -60,6 +63,28 @@ class sx_step_report(C.Structure):
 class sx_scene_desc(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_hinges", C.c_int64),
                 ("n_pairs", C.c_int64), ("nnzb_hint", C.c_int64)]
+
+
+class sx_snh_scene_spec(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("X", C.c_void_p), ("n_tets", C.c_int64),
+                ("tets", C.c_void_p), ("young", C.c_void_p), ("poisson", C.c_void_p),
+                ("density", C.c_double), ("n_pinned", C.c_int64), ("pinned", C.c_void_p),
+                ("gravity", C.c_double * 3)]
+
+
+class sx_completion(C.Structure):
+    _fields_ = [("req_id", C.c_int64), ("status", C.c_int), ("steps", C.c_int),
+                ("n_tets", C.c_int64), ("submit_ms", C.c_double), ("admit_ms", C.c_double),
+                ("done_ms", C.c_double), ("mean_step_ms", C.c_double)]
+
+
+class sx_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("element_steps", C.c_int64), ("wall_ms", C.c_double),
+                ("busy_ms", C.c_double), ("step_p50_ms", C.c_double), ("step_p99_ms", C.c_double),
+                ("request_p50_ms", C.c_double), ("request_p99_ms", C.c_double),
+                ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64), ("active", C.c_int),
+                ("pending", C.c_int), ("ticks", C.c_int)]
 
 
 _P = C.c_void_p
@@ -105,6 +130,13 @@ _SIGS = {
     "sx_profile": (_I, [_P, _I]),
     "sx_profile_read": (_I, [_P, C.POINTER(_D), C.POINTER(_I64), _I]),
     "sx_eval_elements_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
+    "sx_server_create": (_I, [_P, _I64, C.POINTER(sx_newton_opts), _PP]),
+    "sx_server_submit": (_I, [_P, C.POINTER(sx_snh_scene_spec), _I, _D, C.POINTER(_I64)]),
+    "sx_server_poll": (_I, [_P, C.POINTER(sx_completion), _I, C.POINTER(_I)]),
+    "sx_server_result": (_I, [_P, _I64, _P, _P]),
+    "sx_server_drain": (_I, [_P, _D]),
+    "sx_server_stats": (_I, [_P, C.POINTER(sx_serve_stats)]),
+    "sx_server_destroy": (_I, [_P]),
 }
 
 _lib = None

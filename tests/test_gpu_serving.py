@@ -1,0 +1,106 @@
+"""Serving form: continuous batching of backward-Euler steps (the benchmark spec
+"serving"). Each request's result must be the same alone and in the mix;
+admission respects the memory budget."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2303_02156_gb300 import scenes, sx
+
+
+def _requests(n, seed, tmin=60, tmax=900):
+    rng = scenes.rng_for(seed)
+    out = []
+    for k in range(n):
+        T = float(np.exp(rng.uniform(np.log(tmin), np.log(tmax))))
+        dims = scenes.random_box_dims(T, rng)
+        m = scenes.kuhn_box(*dims, h=0.05, seed=seed * 100 + k)
+        E = float(np.exp(rng.uniform(np.log(1e4), np.log(1e6))))
+        nu = float(rng.uniform(0.2, 0.45))
+        out.append((m, E, nu))
+    return out
+
+
+def test_footprint_estimate_grows_with_size():
+    d = sx.sx_scene_desc()
+    import ctypes as C
+    last = 0
+    for n in [10, 1000, 100000]:
+        d.n_nodes = n; d.n_tets = 5 * n; d.n_hinges = 0; d.n_pairs = 0; d.nnzb_hint = 0
+        b = C.c_int64()
+        assert sx.sx_scene_footprint(C.byref(d), C.byref(b)) == sx.SX_OK
+        assert b.value > last
+        last = b.value
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_02156_gb300.scene import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.gpu
+def test_alone_equals_mix_with_staggered_arrivals(ctx):
+    from paper_2303_02156_gb300.scene import Scene, Server
+    reqs = _requests(6, seed=7)
+    steps, dt, g = 3, 0.01, (0.0, 0.0, -9.81)
+    alone = []
+    for m, E, nu in reqs:
+        s = Scene(ctx, m["X"])
+        s.add_snh(m["tets"], E, nu, 1000.0)
+        s.set_pinned(m["pinned"])
+        s.set_gravity(g)
+        s.finalize()
+        for _ in range(steps):
+            s.newton_step(dt)
+        alone.append(s.get_state())
+        s.close()
+    srv = Server(ctx, 8 << 30)
+    ids = []
+    for k, (m, E, nu) in enumerate(reqs):
+        ids.append(srv.submit(m["X"], m["tets"], E, nu, 1000.0, pinned=m["pinned"], gravity=g,
+                              n_steps=steps, dt=dt))
+        if k == 2:
+            time.sleep(0.05)   # later requests arrive while the first are on the GPU
+    assert srv.drain(120000.0) == sx.SX_OK
+    done = {c["req_id"]: c for c in srv.poll()}
+    st = srv.stats()
+    assert st["completed"] == 6 and st["step_p99_ms"] >= st["step_p50_ms"] > 0
+    for rid, (xa, va) in zip(ids, alone):
+        assert done[rid]["status"] == sx.SX_OK and done[rid]["steps"] == steps
+        x, v = srv.result(rid)
+        assert np.array_equal(x, xa) and np.array_equal(v, va)
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_admission_by_budget_and_rejection(ctx):
+    from paper_2303_02156_gb300.scene import Server
+    reqs = _requests(4, seed=11, tmin=300, tmax=600)
+    import ctypes as C
+    fps = []
+    for m, E, nu in reqs:
+        d = sx.sx_scene_desc()
+        d.n_nodes = m["X"].shape[0]; d.n_tets = m["tets"].shape[0]
+        b = C.c_int64()
+        sx.sx_scene_footprint(C.byref(d), C.byref(b))
+        fps.append(b.value + d.n_tets * 360)
+    budget = int(max(fps) * 1.2)   # one scene at a time
+    srv = Server(ctx, budget)
+    for m, E, nu in reqs:
+        srv.submit(m["X"], m["tets"], E, nu, 1000.0, pinned=m["pinned"], n_steps=2, dt=0.01)
+    assert srv.drain(120000.0) == sx.SX_OK
+    st = srv.stats()
+    assert st["completed"] == 4 and st["peak_bytes"] <= budget and st["rejected"] == 0
+    big = scenes.kuhn_box(12, 12, 12, h=0.05, seed=1)
+    with pytest.raises(sx.SxError) as ei:
+        srv.submit(big["X"], big["tets"], 1e5, 0.3, n_steps=1, dt=0.01)
+    assert ei.value.code == sx.SX_EBUDGET
+    assert srv.stats()["rejected"] == 1
+    srv.close()
