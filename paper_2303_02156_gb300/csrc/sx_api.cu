@@ -92,6 +92,7 @@ struct sx_scene {
     double* He = nullptr;   // 90 doubles per stencil; float staging reuses it
     double* vals64 = nullptr;
     float* vals32 = nullptr;
+    float* p32 = nullptr;
     double* grad = nullptr;
     double *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
     double* Minv = nullptr;
@@ -113,8 +114,12 @@ struct Batch {
     std::vector<uint64_t> versions;
     SceneDev* d_desc = nullptr;
     SceneDev* d_desc_trial = nullptr;
-    std::vector<Tile> elem_tiles, node_tiles, slot_tiles;
+    std::vector<Tile> elem_tiles, node_tiles, slot_tiles, row_tiles;
     Tile* d_elem = nullptr;
+    Tile* d_row = nullptr;           // SpMV tiles (spmv_rows_per_tile() rows)
+    int* d_row_beg = nullptr;
+    int* d_row_end = nullptr;
+    double* d_part_row = nullptr;
     Tile* d_node = nullptr;
     Tile* d_slot = nullptr;
     int* d_elem_beg = nullptr;
@@ -135,6 +140,7 @@ struct Batch {
     int64_t clamp_need = 0;          // projectable stencils of the batch
     ~Batch()
     {
+        cudaFree(d_row); cudaFree(d_row_beg); cudaFree(d_row_end); cudaFree(d_part_row);
         cudaFree(d_desc); cudaFree(d_desc_trial); cudaFree(d_elem); cudaFree(d_node);
         cudaFree(d_slot); cudaFree(d_elem_beg); cudaFree(d_elem_end); cudaFree(d_node_beg);
         cudaFree(d_node_end); cudaFree(d_part_elem); cudaFree(d_part_node); cudaFree(d_bad);
@@ -273,6 +279,7 @@ SceneDev make_desc(const sx_scene* s, bool trial)
     d.z = s->z;
     d.p0 = s->p0;
     d.p1 = s->p1;
+    d.p32 = s->p32;
     d.q = s->q;
     d.Minv = s->Minv;
     d.sc = s->sc;
@@ -300,7 +307,8 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         desc_t[i] = make_desc(B->scenes[i], true);
     }
     if (B->d_desc == nullptr) {
-        std::vector<int> eb(n), ee(n), nb(n), ne(n);
+        std::vector<int> eb(n), ee(n), nb(n), ne(n), rb(n), re(n);
+        const int rt = spmv_rows_per_tile();
         for (int i = 0; i < n; ++i) {
             sx_scene* s = B->scenes[i];
             eb[i] = (int)B->elem_tiles.size();
@@ -315,6 +323,10 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
                 B->node_tiles.push_back(
                     Tile{i, 0, k, (int)std::min<int64_t>(kNodeTile, s->N - k), 0});
             ne[i] = (int)B->node_tiles.size();
+            rb[i] = (int)B->row_tiles.size();
+            for (int64_t k = 0; k < s->N; k += rt)
+                B->row_tiles.push_back(Tile{i, 0, k, (int)std::min<int64_t>(rt, s->N - k), 0});
+            re[i] = (int)B->row_tiles.size();
             for (int64_t k = 0; k < s->pat.nnzb; k += kSlotTile)
                 B->slot_tiles.push_back(
                     Tile{i, 0, k, (int)std::min<int64_t>(kSlotTile, s->pat.nnzb - k), 0});
@@ -327,6 +339,10 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         if ((rc = upload(ctx, &B->d_elem_end, ee, st)) != SX_OK) return rc;
         if ((rc = upload(ctx, &B->d_node_beg, nb, st)) != SX_OK) return rc;
         if ((rc = upload(ctx, &B->d_node_end, ne, st)) != SX_OK) return rc;
+        if ((rc = upload(ctx, &B->d_row, B->row_tiles, st)) != SX_OK) return rc;
+        if ((rc = upload(ctx, &B->d_row_beg, rb, st)) != SX_OK) return rc;
+        if ((rc = upload(ctx, &B->d_row_end, re, st)) != SX_OK) return rc;
+        CK(cudaMalloc((void**)&B->d_part_row, std::max<size_t>(B->row_tiles.size(), 1) * sizeof(double)));
         const size_t net = std::max<size_t>(B->elem_tiles.size(), 1);
         const size_t nnt = std::max<size_t>(B->node_tiles.size(), 1);
         CK(cudaMalloc((void**)&B->d_part_elem, net * sizeof(double)));
@@ -449,7 +465,8 @@ int read_scal(sx_ctx* ctx, Batch* B, cudaStream_t st)
 int ensure_vals32(sx_ctx* ctx, sx_scene* s)
 {
     if (s->vals32) return SX_OK;
-    if (dalloc(s, &s->vals32, 9 * (size_t)s->pat.nnzb) != SX_OK)
+    if (dalloc(s, &s->vals32, 9 * (size_t)s->pat.nnzb + 16) != SX_OK ||
+        dalloc(s, &s->p32, 3 * (size_t)s->N + 4) != SX_OK)
         return fail(ctx, SX_ENOMEM, "eval: device allocation failed (FP32 values)");
     s->version++;
     return SX_OK;
@@ -878,7 +895,7 @@ int sx_finalize(sx_scene* s, void* stream)
                                  s->mass, st));
     const size_t n3 = 3 * (size_t)s->N;
     if (dalloc(s, &s->Ee, (size_t)s->nst) || dalloc(s, &s->ge, 12 * (size_t)s->nst) ||
-        dalloc(s, &s->He, 90 * (size_t)s->nst) || dalloc(s, &s->vals64, 9 * (size_t)s->pat.nnzb) ||
+        dalloc(s, &s->He, 90 * (size_t)s->nst) || dalloc(s, &s->vals64, 9 * (size_t)s->pat.nnzb + 8) ||
         dalloc(s, &s->grad, n3) || dalloc(s, &s->r, n3) || dalloc(s, &s->z, n3) ||
         dalloc(s, &s->p0, n3) || dalloc(s, &s->p1, n3) || dalloc(s, &s->q, n3) ||
         dalloc(s, &s->Minv, 9 * (size_t)s->N))
@@ -1268,10 +1285,11 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
         int par = 0;
         for (int k = 0;; k += 8) {
             for (int j = 0; j < 8; ++j) {
-                PL(SX_PH_SPMV, 1, launch_spmv_pq(B->d_desc, B->d_node, nnt, o.precision, par,
-                                                 B->d_part_node, st));
-                PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 1, B->d_node_beg,
-                                                   B->d_node_end, n, B->d_desc, 1, o.pcg_tol,
+                PL(SX_PH_PCG, 1, launch_pcg_pdir(B->d_desc, B->d_node, nnt, o.precision, par, st));
+                PL(SX_PH_SPMV, 1, launch_spmv_pq(B->d_desc, B->d_row, (int)B->row_tiles.size(),
+                                                 o.precision, par, B->d_part_row, st));
+                PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_row, 1, B->d_row_beg,
+                                                   B->d_row_end, n, B->d_desc, 1, o.pcg_tol,
                                                    o.max_pcg, st));
                 PL(SX_PH_PCG, 1, launch_pcg_update(B->d_desc, B->d_node, nnt, par,
                                                    B->d_part_node, st));
@@ -1290,7 +1308,7 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             if (!act[i]) continue;
             pcg_it[i] += B->h_scal[i].pcg_iters;
             if (B->h_scal[i].pcg_status != 0) {
-                status[i] = SX_ENOTCONV;
+                status[i] = B->h_scal[i].pcg_status == 3 ? SX_ECUDA : SX_ENOTCONV;
                 done[i] = 1;
                 act[i] = 0;
             }

@@ -380,7 +380,8 @@ int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
     cudaMemcpyAsync(&nnz, P.row_ptr + N, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     P.nnzb = nnz;
-    if (cudaMalloc((void**)&P.col, (nnz + 1) * sizeof(int)) != cudaSuccess) {
+    // padded: staged SpMV tiles read 16-byte aligned windows
+    if (cudaMalloc((void**)&P.col, (nnz + 16) * sizeof(int)) != cudaSuccess) {
         *err = "finalize: device allocation failed (col)";
         return SX_ENOMEM;
     }

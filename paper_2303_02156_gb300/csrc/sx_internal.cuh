@@ -75,7 +75,7 @@ struct SceneScal {
     double grav[3];    // external acceleration (M^-1 f_ext)
     int pcg_done;      // 1 once converged or stopped (kernels skip the scene)
     int pcg_iters;
-    int pcg_status;    // 0 ok, 1 breakdown (p.Ap <= 0), 2 iteration cap
+    int pcg_status;    // 0 ok, 1 breakdown (p.Ap <= 0), 2 iteration cap, 3 copy timeout
     int active;        // scene takes part in the current batched phase
     int bad_state;     // barrier pairs with d <= 0 in the last evaluation
     int nonfinite;     // non-finite values seen in the last evaluation
@@ -120,6 +120,7 @@ struct SceneDev {
     double* z;
     double* p0;
     double* p1;
+    float* p32;     // FP32 form: float copy of the current direction
     double* q;
     double* Minv;
     SceneScal* sc;
@@ -229,6 +230,9 @@ cudaError_t launch_pcg_setup_p(const SceneDev* scenes, const Tile* node_tiles, i
                                int precision, double* part, cudaStream_t s);
 cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int ntiles,
                            int precision, int parity, double* part, cudaStream_t s);
+cudaError_t launch_pcg_pdir(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                            int precision, int parity, cudaStream_t s);
+int spmv_rows_per_tile();
 cudaError_t launch_pcg_update(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
                               int parity, double* part, cudaStream_t s);
 cudaError_t launch_pcg_reduce(const double* part, int nv, const int* tbeg, const int* tend,

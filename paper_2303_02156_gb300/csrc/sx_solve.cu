@@ -6,11 +6,11 @@
 //   p_new = z + beta p_old;  q = A p_new;  alpha = (r.z) / (p_new.q)
 //   dx += alpha p_new;  r -= alpha q;  z = Minv r
 //   stop when ||r|| <= tol ||b||;  beta = r.z_new / r.z
-// The direction update is fused into the SpMV (p_old and p_new alternate
-// between two buffers), so an iteration is two vector kernels and two
-// one-block-per-scene reductions that also form alpha and beta. Pinned
-// DOFs are eliminated by mask: their rows are identity and their columns
-// are skipped.
+// p_old and p_new alternate between two buffers. An iteration is three
+// vector kernels (direction, SpMV with the p.q partials, update with the
+// r.z and r.r partials) and two one-block-per-scene reductions that also
+// form alpha and beta. Pinned DOFs are eliminated by mask: their rows are
+// identity, and their columns drop out because p is zero there.
 #include <cuda_runtime.h>
 
 #include "sx_internal.cuh"
@@ -157,66 +157,218 @@ cudaError_t launch_pcg_setup_p(const SceneDev* scenes, const Tile* node_tiles, i
 }
 
 // ------------------------------------------------------------------ SpMV
-// q = A p_new with p_new = z + beta p_old formed on the fly; one thread
-// per block row. FP32 form: values and products in float, accumulation of
-// each row in float, p cast to float on load.
-template <typename VT>
+// p_new = z + beta p_old (own rows), then q = A p_new. The direction update
+// runs as its own vector pass so that the SpMV gathers a single vector and
+// spends exactly 9 multiply-adds per 3x3 block (on GB300 the FP64 SpMV is
+// bound by the FP64 pipe before HBM: 9 FMA per 76-byte block).
+template <bool F32>
 __global__ void __launch_bounds__(kVecThreads)
+k_pcg_pdir(const SceneDev* scenes, const Tile* tiles, int ntiles, int par)
+{
+    const Tile T = tiles[blockIdx.x];
+    const SceneDev& S = scenes[T.scene];
+    if (!scene_live(S) || S.sc->pcg_done || (int)threadIdx.x >= T.count) return;
+    const int64_t n = T.start + threadIdx.x;
+    const double beta = S.sc->pcg_beta;
+    const double* po = par ? S.p1 : S.p0;
+    double* pn = par ? S.p0 : S.p1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double p = fma(beta, po[3 * n + i], S.z[3 * n + i]);
+        pn[3 * n + i] = p;
+        // the FP32 SpMV gathers this rounded copy (no conversion per block)
+        if (F32) S.p32[3 * n + i] = (float)p;
+    }
+}
+
+cudaError_t launch_pcg_pdir(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                            int precision, int parity, cudaStream_t s)
+{
+    if (!ntiles) return cudaSuccess;
+    if (precision == SX_FP32)
+        k_pcg_pdir<true><<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity);
+    else
+        k_pcg_pdir<false><<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity);
+    return cudaGetLastError();
+}
+
+// --- TMA bulk copy (non-tensor form) helpers: global -> shared, completion
+// tracked by an mbarrier transaction count
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+#ifndef SX_SPMV_STAGE
+#define SX_SPMV_STAGE 1
+#endif
+static constexpr int kSpmvRows = 48;                 // block rows per tile
+static constexpr int kSpmvThreads = 3 * kSpmvRows;    // one thread per output component
+static constexpr int kSpmvSmemCols = 4 * 1024;        // bytes of staged column ids
+// bytes of staged values: 48 rows of up to ~20 blocks, in the value type
+template <typename VT>
+__host__ __device__ constexpr int spmv_smem_vals()
+{
+    return sizeof(VT) == 8 ? 56 * 1024 : 28 * 1024;
+}
+__device__ __forceinline__ double fma_vt(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_vt(float a, float b, float c) { return fmaf(a, b, c); }
+static constexpr long kWaitLimit = 1L << 24;          // bounded mbarrier wait
+
+template <typename VT>
+__global__ void __launch_bounds__(kSpmvThreads)
 k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part)
 {
-    __shared__ double sh[1][kVecThreads];
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double sh[kSpmvThreads];
+    __shared__ int s_mode;   // 1: staged in shared memory, 0: direct loads
+    __shared__ long s_vofs, s_cofs;
     const int ti = blockIdx.x;
     const Tile T = tiles[ti];
     const SceneDev& S = scenes[T.scene];
-    double v[1] = {0.0};
-    if (scene_live(S) && !S.sc->pcg_done && (int)threadIdx.x < T.count) {
-        const int64_t r = T.start + threadIdx.x;
-        const double beta = S.sc->pcg_beta;
-        const double* po = par ? S.p1 : S.p0;
-        double* pn = par ? S.p0 : S.p1;
-        double pr[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            pr[i] = S.z[3 * r + i] + beta * po[3 * r + i];
-            pn[3 * r + i] = pr[i];
-        }
-        double q[3];
-        if (S.pinned[r]) {
-            q[0] = pr[0]; q[1] = pr[1]; q[2] = pr[2];
-        } else {
-            const VT* vals = (sizeof(VT) == 8) ? (const VT*)S.vals64 : (const VT*)S.vals32;
-            VT acc[3] = {VT(0), VT(0), VT(0)};
-            const int b = S.row_ptr[r], e = S.row_ptr[r + 1];
-            for (int k = b; k < e; ++k) {
-                const int c = S.col[k];
-                if (S.pinned[c]) continue;
-                VT pc[3];
-#pragma unroll
-                for (int j = 0; j < 3; ++j) pc[j] = (VT)(S.z[3 * (int64_t)c + j] + beta * po[3 * (int64_t)c + j]);
-                const VT* B = vals + 9 * (int64_t)k;
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-                    acc[i] += B[3 * i] * pc[0] + B[3 * i + 1] * pc[1] + B[3 * i + 2] * pc[2];
+    const bool live = scene_live(S) && !S.sc->pcg_done;
+    const VT* vals = (sizeof(VT) == 8) ? (const VT*)S.vals64 : (const VT*)S.vals32;
+    const int64_t r0 = T.start, r1 = T.start + T.count;
+    if (threadIdx.x == 0) {
+        s_mode = 0;
+        if (live) {
+            const int64_t k0 = S.row_ptr[r0], k1 = S.row_ptr[r1];
+            // 16-byte aligned windows containing the tile's value and column
+            // segments (the allocations are padded for the rounded-up end)
+            const long vb0 = (long)(k0 * 9 * (int64_t)sizeof(VT)) & ~15L;
+            const long vb1 = ((long)(k1 * 9 * (int64_t)sizeof(VT)) + 15L) & ~15L;
+            const long cb0 = (long)(k0 * 4) & ~15L;
+            const long cb1 = ((long)(k1 * 4) + 15L) & ~15L;
+            if (SX_SPMV_STAGE && vb1 - vb0 <= spmv_smem_vals<VT>() && cb1 - cb0 <= kSpmvSmemCols &&
+                k1 > k0) {
+                s_mode = 1;
+                s_vofs = vb0;
+                s_cofs = cb0;
+                mbar_init(&bar, 1);
+                mbar_expect_tx(&bar, (unsigned)((vb1 - vb0) + (cb1 - cb0)));
+                bulk_g2s(smem, (const unsigned char*)vals + vb0, (unsigned)(vb1 - vb0), &bar);
+                bulk_g2s(smem + spmv_smem_vals<VT>(), (const unsigned char*)S.col + cb0,
+                         (unsigned)(cb1 - cb0), &bar);
             }
-            q[0] = (double)acc[0]; q[1] = (double)acc[1]; q[2] = (double)acc[2];
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            S.q[3 * r + i] = q[i];
-            v[0] += pr[i] * q[i];
         }
     }
-    block_reduce_store<1>(sh, v, part, ti);
+    __syncthreads();
+    const int mode = s_mode;
+    if (mode == 1) {
+        long it = 0;
+        while (!mbar_try_wait(&bar, 0) && ++it < kWaitLimit) {
+        }
+        if (it >= kWaitLimit) {
+            // the copy did not complete in time: report it through the
+            // scene's PCG status, wait (bounded) once more so that no write
+            // lands after exit, and skip the tile
+            if (threadIdx.x == 0) {
+                S.sc->pcg_status = 3;
+                S.sc->pcg_done = 1;
+            }
+            long it2 = 0;
+            while (!mbar_try_wait(&bar, 0) && ++it2 < kWaitLimit) {
+            }
+            return;
+        }
+    }
+    double v = 0.0;
+    const int lr = threadIdx.x / 3, ci = threadIdx.x - 3 * lr;
+    if (live && lr < T.count) {
+        const int64_t r = r0 + lr;
+        const double* pn = par ? S.p0 : S.p1;
+        double q;
+        if (S.pinned[r]) {
+            q = pn[3 * r + ci];
+        } else {
+            VT acc = VT(0);
+            const int b = S.row_ptr[r], e = S.row_ptr[r + 1];
+            // the gathered direction: p itself (FP64) or its float copy (FP32)
+            const VT* pg = (sizeof(VT) == 8) ? (const VT*)pn : (const VT*)S.p32;
+            const VT* vs = mode ? (const VT*)(smem + ((long)b * 9 * (long)sizeof(VT) - s_vofs))
+                                : vals + 9 * (int64_t)b;
+            const int* cs = mode ? (const int*)(smem + spmv_smem_vals<VT>() + ((long)b * 4 - s_cofs))
+                                 : S.col + b;
+            // p is exactly zero on pinned DOFs (their r, z and p stay 0), so
+            // pinned columns drop out without a test in the loop
+#pragma unroll 4
+            for (int k = 0; k < e - b; ++k) {
+                const int c = cs[k];
+                const VT* B = vs + 9 * k + 3 * ci;
+                // a chain of three fused multiply-adds: the minimum FP64
+                // instruction count per block row
+                acc = fma_vt(B[0], pg[3 * (int64_t)c], acc);
+                acc = fma_vt(B[1], pg[3 * (int64_t)c + 1], acc);
+                acc = fma_vt(B[2], pg[3 * (int64_t)c + 2], acc);
+            }
+            q = (double)acc;
+        }
+        S.q[3 * r + ci] = q;
+        v = pn[3 * r + ci] * q;
+    }
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < 128 && threadIdx.x + 128 < kSpmvThreads) sh[threadIdx.x] += sh[threadIdx.x + 128];
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[ti] = sh[0];
 }
+
+int spmv_rows_per_tile() { return kSpmvRows; }
 
 cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int ntiles,
                            int precision, int parity, double* part, cudaStream_t s)
 {
     if (!ntiles) return cudaSuccess;
+    const int smem64 = spmv_smem_vals<double>() + kSpmvSmemCols;
+    const int smem32 = spmv_smem_vals<float>() + kSpmvSmemCols;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_spmv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32);
+        cudaFuncSetAttribute(k_spmv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem64);
+        attr_set = true;
+    }
     if (precision == SX_FP32)
-        k_spmv<float><<<ntiles, kVecThreads, 0, s>>>(scenes, row_tiles, ntiles, parity, part);
+        k_spmv<float><<<ntiles, kSpmvThreads, smem32, s>>>(scenes, row_tiles, ntiles, parity, part);
     else
-        k_spmv<double><<<ntiles, kVecThreads, 0, s>>>(scenes, row_tiles, ntiles, parity, part);
+        k_spmv<double><<<ntiles, kSpmvThreads, smem64, s>>>(scenes, row_tiles, ntiles, parity, part);
     return cudaGetLastError();
 }
 
