@@ -13,13 +13,25 @@
 //   1. (element kernel) shifted LDL^T of M + tau I, tau = 1e-13 ||M||_F:
 //      if it succeeds the stencil is left as is (the change is at most
 //      tau); otherwise M is queued for phase 2;
-//   2. (clamp kernel, one thread per queued M) a full eigen-decomposition
-//      with no data-dependent control flow, so the 32 stencils of a warp run
-//      in lockstep: cyclic Jacobi in float from the identity (float is ~60x
-//      faster than double on this part), modified Gram-Schmidt of the float
-//      eigenvectors in double, At = X^T M X in double (now nearly diagonal)
-//      and two double Jacobi sweeps on At accumulated into X; eigenvalues
-//      below -tau are clamped.
+//   2. (clamp kernel, one thread per queued M) cyclic Jacobi in float from
+//      the identity (float is ~60x faster than double on this part); the
+//      approximate eigenpairs are ordered by ascending eigenvalue, and the
+//      first k (eigenvalue below delta = 1e-5 ||M||_F) form the block N
+//      that can hold negative eigenvalues. In double: modified Gram-Schmidt
+//      of the float eigenvectors, At = X^T M X (nearly diagonal), and
+//      Jacobi sweeps on At, accumulated into X, that rotate only the pairs
+//      (p, q) with p in N (p < k) and skip a rotation whose |a_pq| is at
+//      most theta ||M||_F, theta = 1e-13. Eigenvalues of the N block below
+//      -tau are clamped.
+//   Accuracy: clamping at zero is 1-Lipschitz in the Frobenius norm on
+//   symmetric matrices, so the projection is off by at most about twice the
+//   Frobenius norm of the N-N and N-P off-diagonal entries left in At
+//   (each at most theta ||M||_F once a sweep skips them all). The P block
+//   is left as it is: its eigenvalues are above delta minus the float
+//   error, which a Gershgorin test on the float matrix confirms (else k =
+//   9, a full Jacobi). A rotation runs for the warp when any of its lanes
+//   needs it, and a lane that does not keeps its entries unchanged, so each
+//   stencil's result does not depend on which stencils share its warp.
 // Matrices are kept packed (lower triangle, 45 entries) and every loop is
 // unrolled so they live in registers; the eigenvector matrix lives in
 // shared memory. Jacobi is the textbook symmetric Schur method (Golub &
@@ -33,7 +45,7 @@
 namespace sx {
 
 #ifndef SX_F64_SWEEPS
-#define SX_F64_SWEEPS 2
+#define SX_F64_SWEEPS 3
 #endif
 
 // packed lower-triangle index of (i, j), any order
@@ -155,14 +167,19 @@ struct SmemMat {
 // double sweep: the angle comes from float arithmetic (it only decides how
 // much a_pq shrinks), the rotation (c, s = t c with c = 1/sqrt(1+t^2)) and
 // the 2x2 update are exact in double, so A stays similar to M to working
-// precision
-__device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat& X)
+// precision. Pairs (p, q), p < q, with p >= k or |a_pq| <= thr are left
+// alone (their entries keep their values bit for bit); the warp skips a
+// pair that none of its lanes (mask live) needs.
+__device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat& X, int k,
+                                                 double thr, unsigned live)
 {
 #pragma unroll
     for (int p = 0; p < 8; ++p)
 #pragma unroll
         for (int q = p + 1; q < 9; ++q) {
             const double apq = A[pk(p, q)], app = A[pk(p, p)], aqq = A[pk(q, q)];
+            const bool need = (p < k) && (fabs(apq) > thr);
+            if (!__any_sync(live, need)) continue;
             const float fpq = (float)apq;
             const bool nz = fpq != 0.0f;
             const float tau = (float)(aqq - app) / (nz ? 2.0f * fpq : 1.0f);
@@ -170,44 +187,72 @@ __device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat&
             const double t = nz ? (double)tt : 0.0;
             const double c = rsqrt(fma(t, t, 1.0)), s = t * c;
             const double cc = c * c, ss = s * s, cs = c * s;
-            A[pk(p, p)] = fma(cc, app, fma(-2.0 * cs, apq, ss * aqq));
-            A[pk(q, q)] = fma(ss, app, fma(2.0 * cs, apq, cc * aqq));
-            A[pk(p, q)] = fma(cc - ss, apq, cs * (app - aqq));
+            const double npp = fma(cc, app, fma(-2.0 * cs, apq, ss * aqq));
+            const double nqq = fma(ss, app, fma(2.0 * cs, apq, cc * aqq));
+            const double npq = fma(cc - ss, apq, cs * (app - aqq));
+            A[pk(p, p)] = need ? npp : app;
+            A[pk(q, q)] = need ? nqq : aqq;
+            A[pk(p, q)] = need ? npq : apq;
 #pragma unroll
             for (int r = 0; r < 9; ++r) {
                 if (r == p || r == q) continue;
                 const double arp = A[pk(r, p)], arq = A[pk(r, q)];
-                A[pk(r, p)] = fma(c, arp, -s * arq);
-                A[pk(r, q)] = fma(s, arp, c * arq);
+                const double nrp = fma(c, arp, -s * arq), nrq = fma(s, arp, c * arq);
+                A[pk(r, p)] = need ? nrp : arp;
+                A[pk(r, q)] = need ? nrq : arq;
             }
+            if (need) {
 #pragma unroll
-            for (int r = 0; r < 9; ++r) {
-                const double xp = X(r, p), xq = X(r, q);
-                X(r, p) = fma(c, xp, -s * xq);
-                X(r, q) = fma(s, xp, c * xq);
+                for (int r = 0; r < 9; ++r) {
+                    const double xp = X(r, p), xq = X(r, q);
+                    X(r, p) = fma(c, xp, -s * xq);
+                    X(r, q) = fma(s, xp, c * xq);
+                }
             }
         }
 }
 
 // Phase 2 driver. Mg: packed 9x9 (double, global memory; read twice so that
-// it is not held in registers across the float phase). On return X holds an
-// orthonormal eigenbasis of M to working precision and lam the eigenvalues.
-__device__ __forceinline__ void eig9(const double* __restrict__ Mg, const SmemMat& X,
-                                     double (&lam)[9])
+// it is not held in registers across the float phase); fro = ||M||_F; live:
+// the lanes of the warp that run this call together. On return X holds an
+// orthonormal basis, ordered by ascending float eigenvalue, whose first k
+// columns are eigenvectors of M with eigenvalues lam[0..k-1] and whose
+// other columns span an invariant subspace on which M is positive definite
+// (lam[k..8] are then the diagonal of that block, all positive).
+__device__ __forceinline__ int eig9(const double* __restrict__ Mg, const SmemMat& X,
+                                    double (&lam)[9], double fro, unsigned live)
 {
-    // 1. float Jacobi from the identity
+    int k = 0;
+    // 1. float Jacobi from the identity, then order the columns
     {
         float A[45], Xf[81];
 #pragma unroll
-        for (int k = 0; k < 45; ++k) A[k] = (float)Mg[k];
+        for (int i = 0; i < 45; ++i) A[i] = (float)Mg[i];
 #pragma unroll
-        for (int k = 0; k < 81; ++k) Xf[k] = (k % 10 == 0) ? 1.0f : 0.0f;
+        for (int i = 0; i < 81; ++i) Xf[i] = (i % 10 == 0) ? 1.0f : 0.0f;
 #pragma unroll 1
         for (int sw = 0; sw < 5; ++sw) jacobi_sweep_f32(A, Xf);
+        const float delta = 1e-5f * (float)fro;
+        bool pblock_ok = true;
 #pragma unroll
-        for (int r = 0; r < 9; ++r)
+        for (int c = 0; c < 9; ++c) {
+            const float lc = A[pk(c, c)];
+            int rank = 0;
+            float rad = 0.0f;
 #pragma unroll
-            for (int c = 0; c < 9; ++c) X(r, c) = (double)Xf[r * 9 + c];
+            for (int j = 0; j < 9; ++j) {
+                if (j == c) continue;
+                const float lj = A[pk(j, j)];
+                rank += (lj < lc || (lj == lc && j < c)) ? 1 : 0;
+                rad += (lj >= delta) ? fabsf(A[pk(c, j)]) : 0.0f;
+            }
+            k += (lc < delta) ? 1 : 0;
+            // Gershgorin disc of the P block, with half of delta to spare
+            if (lc >= delta) pblock_ok = pblock_ok && (lc - rad > 0.5f * delta);
+#pragma unroll
+            for (int r = 0; r < 9; ++r) X(r, rank) = (double)Xf[r * 9 + c];
+        }
+        if (!pblock_ok) k = 9;
     }
     // 2. re-orthonormalize in double (modified Gram-Schmidt; X is already
     //    orthogonal to float precision, so one pass suffices)
@@ -228,7 +273,8 @@ __device__ __forceinline__ void eig9(const double* __restrict__ Mg, const SmemMa
 #pragma unroll
         for (int r = 0; r < 9; ++r) X(r, j) *= inv;
     }
-    // 3. At = X^T M X (nearly diagonal), then double Jacobi sweeps
+    // 3. At = X^T M X (nearly diagonal), then double Jacobi sweeps on the
+    //    rows of the N block
     double At[45];
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
@@ -248,10 +294,12 @@ __device__ __forceinline__ void eig9(const double* __restrict__ Mg, const SmemMa
             At[pk(i, j)] = s;
         }
     }
+    const double thr = 1e-13 * fro;
 #pragma unroll 1
-    for (int sw = 0; sw < SX_F64_SWEEPS; ++sw) jacobi_sweep_f64(At, X);
+    for (int sw = 0; sw < SX_F64_SWEEPS; ++sw) jacobi_sweep_f64(At, X, k, thr, live);
 #pragma unroll
     for (int i = 0; i < 9; ++i) lam[i] = At[pk(i, i)];
+    return k;
 }
 
 }  // namespace sx

@@ -517,10 +517,11 @@ k_clamp(ElemLaunch L)
     const int64_t span = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += span) {
         const int64_t idx = base + threadIdx.x;
+        const unsigned live = __ballot_sync(0xffffffffu, idx < count);
         if (idx >= count) break;
         const ClampRef ref = L.clamp_ref[idx];
         const double* Mg = L.clamp_M + 45 * idx;
-        double tau;
+        double tau, fro;
         {
             double s = 0.0;
 #pragma unroll
@@ -530,10 +531,11 @@ k_clamp(ElemLaunch L)
                     const double v = Mg[pk(i, j)];
                     s = fma((i == j ? 1.0 : 2.0) * v, v, s);
                 }
-            tau = 1e-13 * sqrt(s);
+            fro = sqrt(s);
+            tau = 1e-13 * fro;
         }
         double lam[9];
-        eig9(Mg, X, lam);
+        const int k = eig9(Mg, X, lam, fro, live);
         bool ok = true;
 #pragma unroll
         for (int i = 0; i < 9; ++i) ok = ok && isfinite(lam[i]);
@@ -548,7 +550,7 @@ k_clamp(ElemLaunch L)
         double* full = L.out_H ? L.out_H + 144 * ref.e : nullptr;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            if (!(lam[i] < -tau)) continue;
+            if (i >= k || !(lam[i] < -tau)) continue;
             double u[12];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
