@@ -132,9 +132,37 @@ __device__ __forceinline__ double snh_core(const double* xg, const double* Dinv,
         const R a = mu * Ic * inv1;
         // lam'(J - alpha) = lam'(J - 1) - 3/4 mu'
         const R b = (lamd != 0.0) ? (R)(lamd * Jm1 - 0.75 * mud) : R(0);
+        // P = a F + b cof F. Its two O(mu') parts cancel at rest, so it is
+        // formed from D = F - I: cof(I + D) = I + (tr D) I - D^T + cof D gives
+        // P = (a + b) I + a D + b ((tr D) I - D^T + cof D), where
+        // a + b = mu' Ic3 / (4 (Ic + 1)) + lam' (J - 1) (alpha = 1 + 3 mu' / (4 lam'))
+        // is taken in double; the rest is O(mu' |D|) and keeps R's relative
+        // precision (in FP32 this is what lets the assembled forces resolve
+        // below float epsilon times mu')
+        const double Icd = 3.0 + Ic3;
+        const R s0 = (lamd != 0.0) ? (R)(mud * Ic3 / (4.0 * (Icd + 1.0)) + lamd * Jm1)
+                                   : (R)(mud * Icd / (Icd + 1.0));
+        R Dr[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Dr[k] = (R)D[k];
+        const R trr = (R)trD;
+        R cofD[9];
+        cofD[0] = Dr[4] * Dr[8] - Dr[5] * Dr[7];
+        cofD[1] = Dr[5] * Dr[6] - Dr[3] * Dr[8];
+        cofD[2] = Dr[3] * Dr[7] - Dr[4] * Dr[6];
+        cofD[3] = Dr[2] * Dr[7] - Dr[1] * Dr[8];
+        cofD[4] = Dr[0] * Dr[8] - Dr[2] * Dr[6];
+        cofD[5] = Dr[1] * Dr[6] - Dr[0] * Dr[7];
+        cofD[6] = Dr[1] * Dr[5] - Dr[2] * Dr[4];
+        cofD[7] = Dr[2] * Dr[3] - Dr[0] * Dr[5];
+        cofD[8] = Dr[0] * Dr[4] - Dr[1] * Dr[3];
         R P[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) P[k] = a * F[k] + b * S.C[k];
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                P[i * 3 + j] = ((i == j) ? s0 + b * trr : R(0)) + a * Dr[i * 3 + j] +
+                               b * (cofD[i * 3 + j] - Dr[j * 3 + i]);
 #pragma unroll
         for (int n = 0; n < 4; ++n)
 #pragma unroll
