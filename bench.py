@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=6.0)
     p.add_argument("--serve-requests", type=int, default=48)
+    p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batch-scenes", type=int, default=512)
     return p.parse_args()
 
 
@@ -236,6 +239,139 @@ def run_serving(ctx, n_req, seed, rate=200.0, steps=10, dt=0.01, budget=150e9):
             "sample": "first %d requests of the 2,000-request stream" % n_req}
 
 
+# ------------------------------------------------------------------ mixed stencils
+def run_mixed(ctx, stream, flush, reps=5):
+    """One scene with an SNH block (55^3 cubes, 998,250 tets), a 1000 x 1000
+    quad sheet (2,998,000 hinge stencils, k_b = 1e-3) and 4,000,000
+    point-triangle pairs (d ~ U(1e-4, 1e-3) m, dhat = 1e-3 m, kappa = 1e4):
+    E + g + projected H + assembly, FP32 element math with the FP64 clamp
+    (and the FP64 form beside it), L2 flushed between passes."""
+    import numpy as np
+    import torch
+    from paper_2303_02156_gb300 import scenes, sx
+    from paper_2303_02156_gb300.scene import Scene
+    w = scenes.mixed_scene()
+    sh = stream.cuda_stream
+    s = Scene(ctx, w["X"], stream=sh)
+    s.add_snh(w["tets"], w["E"], w["nu"], 1000.0)
+    s.add_hinge(w["hinges"], w["q"], w["c"], w["kb"])
+    s.add_barrier(w["pairs"], w["dhat"], w["kappa"])
+    s.add_node_mass(w["extra_mass"])
+    s.set_pinned(w["pinned"])
+    s.finalize()
+    s.set_state(x=w["x"])
+    info = s.info()
+    n_st = int(info["n_stencils"])
+    out = {"workload": "mixed: snh 55^3 Kuhn block + 1000x1000 hinge sheet + 4M point-triangle pairs",
+           "tets": int(w["tets"].shape[0]), "hinges": int(w["hinges"].shape[0]),
+           "pairs": int(w["pairs"].shape[0]), "nodes": int(w["X"].shape[0]),
+           "nnzb": int(info["nnzb"]), "stencils": n_st}
+    for name, prec in (("fp32", sx.SX_FP32), ("fp64", sx.SX_FP64)):
+        for _ in range(3):
+            ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0.record(stream)
+            ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = s.stats()
+        med = statistics.median(ms)
+        out[name] = {"ms_per_step": med, "elements_per_s": n_st / (med / 1e3),
+                     "projected": st["clamped"], "bad_state": st["bad_state"],
+                     "nonfinite": st["nonfinite"]}
+    # deviation of the FP32 form from the FP64 form on the assembled output
+    ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, sx.SX_FP64, None, sh))
+    _, _, v64 = s.bsr(); g64 = s.grad()
+    ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, sx.SX_FP32, None, sh))
+    _, _, v32 = s.bsr(); g32 = s.grad()
+    out["fp32"]["bsr_rel_err_vs_fp64"] = float(np.linalg.norm(v32.astype(np.float64) - v64) /
+                                               np.linalg.norm(v64))
+    out["fp32"]["grad_rel_err_vs_fp64"] = float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64))
+    out["note"] = ("one particle per pair (no vertex sharing among contact points), so the "
+                   "barrier gathers reuse less than a real contact scene would")
+    s.close()
+    return out
+
+
+# ------------------------------------------------------------------ batched scenes
+def run_batched(ctx, stream, n_scenes, dt=0.01):
+    """``n_scenes`` independent Kuhn boxes (tet counts log-uniform in
+    [1e3, 2e5], aspect up to 8:1, per-scene materials, bottom layer pinned,
+    gravity): one batched E + g + projected H + assembly pass, the same
+    scenes evaluated one call each, and one backward-Euler Newton step of all
+    scenes in one batched call, FP64 and FP32."""
+    import numpy as np
+    import torch
+    from paper_2303_02156_gb300 import scenes, sx
+    from paper_2303_02156_gb300.scene import Scene
+    boxes = scenes.batch_boxes(n_scenes)
+    sh = stream.cuda_stream
+    sc = []
+    for b in boxes:
+        s = Scene(ctx, b["X"], stream=sh)
+        s.add_snh(b["tets"], b["E"], b["nu"], 1000.0)
+        s.set_pinned(b["pinned"])
+        s.set_gravity((0.0, 0.0, -9.81))
+        s.finalize()
+        sc.append(s)
+    T = int(sum(b["tets"].shape[0] for b in boxes))
+    out = {"workload": "%d Kuhn boxes, tets logU[1e3, 2e5], aspect <= 8:1" % n_scenes,
+           "scenes": n_scenes, "tets": T,
+           "tets_min": int(min(b["tets"].shape[0] for b in boxes)),
+           "tets_max": int(max(b["tets"].shape[0] for b in boxes))}
+    arr = (C.c_void_p * n_scenes)(*[s.h.value for s in sc])
+    for b, s in zip(boxes, sc):
+        s.set_state(x=scenes.jitter_state(b["X"], 0.002 * 0.02, seed=7))
+    for prec, name in ((sx.SX_FP64, "fp64"), (sx.SX_FP32, "fp32")):
+        for _ in range(2):
+            ctx.check(sx.sx_eval_batch(ctx.h, arr, n_scenes, sx.SX_EGH, 1, prec, None, sh))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.check(sx.sx_eval_batch(ctx.h, arr, n_scenes, sx.SX_EGH, 1, prec, None, sh))
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for s in sc:
+            ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter() - t0
+        out["eval_" + name] = {"batched_ms": tb * 1e3, "batched_elements_per_s": T / tb,
+                               "one_call_per_scene_ms": t1 * 1e3,
+                               "one_call_per_scene_elements_per_s": T / t1}
+    xs = {}
+    for prec, name, tol in ((sx.SX_FP64, "fp64", 1e-8), (sx.SX_FP32, "fp32", 1e-6)):
+        for b, s in zip(boxes, sc):
+            s.set_state(x=b["X"], v=np.zeros_like(b["X"]))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = (sx.sx_step_report * n_scenes)()
+        o = sx.newton_opts(precision=prec, newton_tol=tol, pcg_tol=1e-10 if prec == 0 else 1e-6)
+        rc = sx.sx_newton_step_batch(ctx.h, arr, n_scenes, float(dt), C.byref(o), reps, sh)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        xs[name] = [s.get_state()[0] for s in sc]
+        st = [r.status for r in reps]
+        out["newton_" + name] = {
+            "status": sx.STATUS_NAMES.get(rc, rc), "ms": t * 1e3, "element_steps_per_s": T / t,
+            "scenes_ok": int(sum(1 for v in st if v == 0)),
+            "newton_iters_max": int(max(r.newton_iters for r in reps)),
+            "pcg_iters_max": int(max(r.pcg_iters for r in reps)), "newton_tol": tol, "dt": dt}
+    dev = 0.0
+    for b, a32, a64 in zip(boxes, xs["fp32"], xs["fp64"]):
+        disp = np.abs(a64 - b["X"]).max()
+        if disp > 0:
+            dev = max(dev, float(np.abs(a32 - a64).max() / disp))
+    out["newton_fp32"]["dx_rel_err_vs_fp64"] = dev
+    for s in sc:
+        s.close()
+    return out
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -409,15 +545,31 @@ def main():
         rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-8, pcg_tol=1e-10)
         sx.sx_profile_read(ctx.h, ms_arr, ln_arr, 1)
         sx.sx_profile(ctx.h, 0)
+        x64 = s.get_state()[0]
         newton = {"status": sx.STATUS_NAMES.get(rc, rc), "ms": rep["ms"],
                   "newton_iters": rep["newton_iters"], "pcg_iters": rep["pcg_iters"],
                   "phase_ms": {sx.PHASES[i]: round(ms_arr[i], 3) for i in range(9)},
                   "dt": 0.005, "newton_tol": 1e-8, "pcg_tol": 1e-10}
+        # the FP32 form of the same step (FP64 clamp, residual norms and
+        # line-search energies), and its deviation from the FP64 step
+        s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+        rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-6, pcg_tol=1e-6,
+                                precision=sx.SX_FP32)
+        x32 = s.get_state()[0]
+        newton["fp32"] = {"status": sx.STATUS_NAMES.get(rc, rc), "ms": rep["ms"],
+                          "newton_iters": rep["newton_iters"], "pcg_iters": rep["pcg_iters"],
+                          "newton_tol": 1e-6, "pcg_tol": 1e-6,
+                          "dx_rel_err_vs_fp64": float(np.abs(x32 - x64).max() /
+                                                      max(np.abs(x64 - m["X"]).max(), 1e-300))}
 
     # ---- serving: Poisson stream of scene requests (bounded sample)
     serving = None
     if args.serve_requests > 0:
         serving = run_serving(ctx, args.serve_requests, seed=5)
+
+    # ---- mixed stencils in one scene, and batched independent scenes
+    mixed = None if args.no_mixed else run_mixed(ctx, stream, flush)
+    batched = None if args.no_batched else run_batched(ctx, stream, args.batch_scenes)
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -441,7 +593,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu,
             "phase_ms_per_step": {k: round(v, 4) for k, v in phases.items()},
             "projected_fraction": clamped / T, "fp32": fp32, "newton_step": newton,
-            "serving": serving,
+            "serving": serving, "mixed": mixed, "batched": batched,
             "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
                         "max": max(step_ms)},
         }

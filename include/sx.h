@@ -322,18 +322,27 @@ int sx_scene_footprint(const sx_scene_desc* desc, int64_t* bytes);
 int sx_scene_bytes(sx_scene* scene, int64_t* bytes);
 
 /* ---- serving: continuous batching of backward-Euler steps -------------
- * A server owns a worker thread that, per tick, (1) admits waiting requests
- * in arrival order while their device footprint fits the memory budget
- * (registration, rest precompute and pattern build happen at admission),
- * (2) runs one batched Newton step (sx_newton_step_batch) over every
- * resident scene -- requests that arrived while others were on the GPU join
- * the next tick at their own step 0 -- and (3) retires finished requests,
+ * (No counterpart in the paper, which takes one step of one scene; this
+ * is the request-loop form of the §3 time step.)
+ * Requests are split by tet count into size-class lanes (default 3:
+ * n_tets < 20,000, < 120,000, the rest). Each lane has its own context,
+ * CUDA stream (smaller classes at higher stream priority) and worker
+ * thread, all on the device current at sx_server_create. Per tick a lane
+ * (1) admits its waiting requests in arrival order while their device
+ * footprint fits the memory budget shared by all lanes (registration, rest
+ * precompute and pattern build happen at admission), (2) runs one batched
+ * Newton step (sx_newton_step_batch) over every scene resident in the lane
+ * -- requests that arrived while others were on the GPU join the lane's
+ * next tick at their own step 0 -- and (3) retires finished requests,
  * keeping their final state on the host and freeing their device memory.
- * Each scene's result does not depend on what it is batched with (all
- * reductions are per scene and in a fixed order). While a server runs, its
- * context must not be used by other calls. Step latency is measured from a
- * step's eligibility (request admitted and its previous step done) to the
- * end of the tick that completed it. */
+ * Lanes run concurrently, so a small scene's step does not wait for the
+ * PCG of a large one. Each scene's result does not depend on what it is
+ * batched with (all reductions are per scene and in a fixed order). The
+ * ctx passed to sx_server_create only names the device; it stays free for
+ * other calls. Step latency is measured from a step's eligibility (request
+ * admitted and its previous step done) to the end of the tick that
+ * completed it. */
+#define SX_SERVER_MAX_LANES 8
 typedef struct {
     int64_t n_nodes;
     const double* X;          /* n_nodes x 3 rest positions (host) */
@@ -372,6 +381,11 @@ typedef struct {
 /* opts: Newton options for every step (NULL = defaults). Synchronous. */
 int sx_server_create(sx_ctx* ctx, int64_t hbm_budget_bytes, const sx_newton_opts* opts,
                      sx_server** srv);
+/* Replaces the lanes: n_lanes in [1, SX_SERVER_MAX_LANES], bounds the
+ * n_lanes - 1 increasing tet-count limits (lane i takes n_tets < bounds[i],
+ * the last lane the rest; NULL if n_lanes == 1). Only before the first
+ * submit (else SX_EORDER). Synchronous. */
+int sx_server_set_lanes(sx_server* srv, int n_lanes, const int64_t* bounds);
 /* Copies the spec (the caller's arrays may be freed on return) and queues
  * the request; SX_EBUDGET if its footprint alone exceeds the budget. */
 int sx_server_submit(sx_server* srv, const sx_snh_scene_spec* spec, int n_steps, double dt,
@@ -385,7 +399,7 @@ int sx_server_result(sx_server* srv, int64_t req_id, double* x, double* v);
  * SX_ENOTCONV). */
 int sx_server_drain(sx_server* srv, double timeout_ms);
 int sx_server_stats(sx_server* srv, sx_serve_stats* st);
-/* Stops the worker after the current tick and frees everything. */
+/* Stops the lanes after their current ticks and frees everything. */
 int sx_server_destroy(sx_server* srv);
 
 #ifdef __cplusplus

@@ -39,7 +39,6 @@ struct BlockHost {
 };
 
 constexpr int kNodeTile = 256;
-constexpr int kSlotTile = 256;
 
 }  // namespace
 
@@ -271,6 +270,7 @@ SceneDev make_desc(const sx_scene* s, bool trial)
     d.slots = s->pat.slots;
     d.slot_ptr = s->pat.slot_ptr;
     d.slot_src = s->pat.slot_src;
+    d.slot_order = s->pat.slot_order;
     d.node_ptr = s->pat.node_ptr;
     d.node_src = s->pat.node_src;
     d.vals64 = s->vals64;
@@ -883,9 +883,9 @@ int sx_finalize(sx_scene* s, void* stream)
     if (rc != SX_OK) return fail(ctx, rc, err);
     for (void* p : {(void*)s->pat.row_ptr, (void*)s->pat.col, (void*)s->pat.diag_slot,
                     (void*)s->pat.slots, (void*)s->pat.slot_ptr, (void*)s->pat.slot_src,
-                    (void*)s->pat.node_ptr, (void*)s->pat.node_src})
+                    (void*)s->pat.slot_order, (void*)s->pat.node_ptr, (void*)s->pat.node_src})
         s->allocs.push_back(p);
-    s->bytes += (int64_t)(s->N + 1) * 8 + s->pat.nnzb * 8 + s->N * 4 + s->nst * 16 * 4 * 2 +
+    s->bytes += (int64_t)(s->N + 1) * 8 + s->pat.nnzb * 12 + s->N * 4 + s->nst * 16 * 4 * 2 +
                 s->nst * 4 * 4;
     // lumped mass: extra + rho V / 4 of every SNH tet, in element order
     CK(cudaMemcpyAsync(s->mass, s->extra_mass, s->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1400,7 +1400,7 @@ int sx_scene_footprint(const sx_scene_desc* d, int64_t* bytes)
     b += d->n_hinges * (16 + 5 * 8);
     b += d->n_pairs * 16;
     b += nst * (8 + 12 * 8 + 90 * 8 + 16 * 4 * 2 + 4 * 4); // staging, slots, lists
-    b += nnzb * (4 + 4 + 9 * 8);                            // col, slot_ptr, values
+    b += nnzb * (4 + 4 + 4 + 9 * 8);                        // col, slot_ptr, order, values
     b += 1 << 20;
     *bytes = b;
     return SX_OK;

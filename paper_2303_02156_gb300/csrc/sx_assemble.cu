@@ -17,7 +17,10 @@ namespace sx {
 
 static constexpr int kAsmThreads = 256;
 
-template <typename HT, typename VT>
+// one thread per BSR block; AT is the accumulation type (double in the FP64
+// form; float in the FP32 form, whose element blocks and stored values are
+// float: on this part a float-to-double conversion costs an FP64 slot)
+template <typename HT, typename VT, typename AT>
 __global__ void __launch_bounds__(kAsmThreads)
 k_assemble_vals(const SceneDev* scenes, const Tile* tiles, int ntiles)
 {
@@ -27,11 +30,13 @@ k_assemble_vals(const SceneDev* scenes, const Tile* tiles, int ntiles)
     const SceneDev& S = scenes[T.scene];
     if (S.sc && !S.sc->active) return;
     if ((int)threadIdx.x >= T.count) return;
-    const int64_t slot = T.start + threadIdx.x;
+    // the tile's blocks in ascending order of list length (a permutation
+    // within the tile), so that a warp's lists have similar lengths
+    const int64_t slot = S.slot_order[T.start + threadIdx.x];
     const HT* He = (const HT*)S.He;
-    double acc[9];
+    AT acc[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 9; ++k) acc[k] = AT(0);
     const int b = S.slot_ptr[slot], e = S.slot_ptr[slot + 1];
     for (int k = b; k < e; ++k) {
         const int code = S.slot_src[k];
@@ -41,13 +46,13 @@ k_assemble_vals(const SceneDev* scenes, const Tile* tiles, int ntiles)
         if (la <= lb) {
             blk = He + 90 * st + 9 * up_index(la, lb);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) acc[q] += (double)blk[q];
+            for (int q = 0; q < 9; ++q) acc[q] += (AT)blk[q];
         } else {
             blk = He + 90 * st + 9 * up_index(lb, la);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) acc[i * 3 + j] += (double)blk[j * 3 + i];
+                for (int j = 0; j < 3; ++j) acc[i * 3 + j] += (AT)blk[j * 3 + i];
         }
     }
     VT* out = (sizeof(VT) == 8) ? (VT*)S.vals64 : (VT*)S.vals32;
@@ -79,11 +84,11 @@ cudaError_t launch_assemble_vals(const AsmLaunch& L, cudaStream_t s)
 {
     if (L.ntiles == 0) return cudaSuccess;
     if (L.precision == SX_FP32)
-        k_assemble_vals<float, float><<<L.ntiles, kAsmThreads, 0, s>>>(L.scenes, L.tiles,
-                                                                     L.ntiles);
+        k_assemble_vals<float, float, float><<<L.ntiles, kAsmThreads, 0, s>>>(L.scenes, L.tiles,
+                                                                            L.ntiles);
     else
-        k_assemble_vals<double, double><<<L.ntiles, kAsmThreads, 0, s>>>(L.scenes, L.tiles,
-                                                                       L.ntiles);
+        k_assemble_vals<double, double, double><<<L.ntiles, kAsmThreads, 0, s>>>(
+            L.scenes, L.tiles, L.ntiles);
     return cudaGetLastError();
 }
 

@@ -21,8 +21,11 @@
 //      of the float eigenvectors, At = X^T M X (nearly diagonal), and
 //      Jacobi sweeps on At, accumulated into X, that rotate only the pairs
 //      (p, q) with p in N (p < k) and skip a rotation whose |a_pq| is at
-//      most theta ||M||_F, theta = 1e-13. Eigenvalues of the N block below
-//      -tau are clamped.
+//      most theta ||M||_F: theta = 1e-13 for an FP64 Hessian; 1e-9 for an
+//      FP32 one (its entries carry ~6e-8 relative rounding, which also
+//      spreads its exactly-zero eigenvalues over ~1e-7 ||M||, and the
+//      result is stored in float). Eigenvalues of the N block below -tau
+//      are clamped.
 //   Accuracy: clamping at zero is 1-Lipschitz in the Frobenius norm on
 //   symmetric matrices, so the projection is off by at most about twice the
 //   Frobenius norm of the N-N and N-P off-diagonal entries left in At
@@ -46,6 +49,10 @@ namespace sx {
 
 #ifndef SX_F64_SWEEPS
 #define SX_F64_SWEEPS 3
+#endif
+// rotation skip threshold (relative to ||M||_F) for a Hessian computed in FP32
+#ifndef SX_CLAMP_THETA32
+#define SX_CLAMP_THETA32 1e-9
 #endif
 
 // packed lower-triangle index of (i, j), any order
@@ -220,7 +227,7 @@ __device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat&
 // other columns span an invariant subspace on which M is positive definite
 // (lam[k..8] are then the diagonal of that block, all positive).
 __device__ __forceinline__ int eig9(const double* __restrict__ Mg, const SmemMat& X,
-                                    double (&lam)[9], double fro, unsigned live)
+                                    double (&lam)[9], double fro, double theta, unsigned live)
 {
     int k = 0;
     // 1. float Jacobi from the identity, then order the columns
@@ -294,7 +301,7 @@ __device__ __forceinline__ int eig9(const double* __restrict__ Mg, const SmemMat
             At[pk(i, j)] = s;
         }
     }
-    const double thr = 1e-13 * fro;
+    const double thr = theta * fro;
 #pragma unroll 1
     for (int sw = 0; sw < SX_F64_SWEEPS; ++sw) jacobi_sweep_f64(At, X, k, thr, live);
 #pragma unroll

@@ -563,7 +563,7 @@ k_clamp(ElemLaunch L)
             tau = 1e-13 * fro;
         }
         double lam[9];
-        const int k = eig9(Mg, X, lam, fro, live);
+        const int k = eig9(Mg, X, lam, fro, sizeof(HT) == 4 ? SX_CLAMP_THETA32 : 1e-13, live);
         bool ok = true;
 #pragma unroll
         for (int i = 0; i < 9; ++i) ok = ok && isfinite(lam[i]);

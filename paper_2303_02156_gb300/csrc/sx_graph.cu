@@ -339,6 +339,29 @@ __global__ void k_fill_slots(const int* slots, int64_t nst, const int* slot_ptr,
     }
 }
 
+// Within each tile of kSlotTile consecutive blocks, the blocks ordered by
+// ascending contributor count (ties by block index): the assembly threads
+// of a warp then walk lists of similar length. Only which thread sums a
+// block changes; each block's own summation order stays element order.
+__global__ void __launch_bounds__(kSlotTile)
+k_slot_order(const int* slot_ptr, int64_t nnz, int* order)
+{
+    __shared__ int len[kSlotTile];
+    const int64_t t0 = (int64_t)blockIdx.x * kSlotTile;
+    const int cnt = (nnz - t0 < (int64_t)kSlotTile) ? (int)(nnz - t0) : kSlotTile;
+    const int i = threadIdx.x;
+    len[i] = i < cnt ? slot_ptr[t0 + i + 1] - slot_ptr[t0 + i] : 0;
+    __syncthreads();
+    if (i >= cnt) return;
+    const int li = len[i];
+    int rank = 0;
+    for (int j = 0; j < cnt; ++j) {
+        const int lj = len[j];
+        rank += (lj < li || (lj == li && j < i)) ? 1 : 0;
+    }
+    order[t0 + rank] = (int)(t0 + i);
+}
+
 int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
                   std::string* err, cudaStream_t s)
 {
@@ -395,7 +418,8 @@ int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
         cudaMalloc((void**)&slot_deg, (nnz + 1) * sizeof(int)) != cudaSuccess ||
         cudaMalloc((void**)&fill, (nnz + 1) * sizeof(int)) != cudaSuccess ||
         cudaMalloc((void**)&P.slot_ptr, (nnz + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&P.slot_src, (16 * nst + 1) * sizeof(int)) != cudaSuccess) {
+        cudaMalloc((void**)&P.slot_src, (16 * nst + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&P.slot_order, (nnz + 1) * sizeof(int)) != cudaSuccess) {
         *err = "finalize: device allocation failed (slots)";
         return SX_ENOMEM;
     }
@@ -407,6 +431,7 @@ int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
     if (rc != SX_OK) return rc;
     if (nst) k_fill_slots<<<nblk(nst, 256), 256, 0, s>>>(P.slots, nst, P.slot_ptr, fill, P.slot_src);
     if (nnz) k_sort_segments<<<nblk(nnz, 128), 128, 0, s>>>(P.slot_ptr, nnz, P.slot_src);
+    if (nnz) k_slot_order<<<nblk(nnz, kSlotTile), kSlotTile, 0, s>>>(P.slot_ptr, nnz, P.slot_order);
     cudaFreeAsync(slot_deg, s);
     cudaFreeAsync(fill, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {

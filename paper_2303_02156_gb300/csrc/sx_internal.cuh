@@ -112,6 +112,7 @@ struct SceneDev {
     const int* slots;
     const int* slot_ptr;
     const int* slot_src;
+    const int* slot_order;
     const int* node_ptr;
     const int* node_src;
     double* vals64;
@@ -191,9 +192,12 @@ struct PatternOut {
     int* slots;
     int* slot_ptr;
     int* slot_src;
+    int* slot_order;   // per tile of kSlotTile blocks: the blocks by ascending list length
     int* node_ptr;
     int* node_src;
 };
+// BSR blocks per assembly tile (the unit of slot_order)
+constexpr int kSlotTile = 256;
 int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
                   std::string* err, cudaStream_t s);
 

@@ -1,11 +1,14 @@
 // sx_server.cu -- the serving form: a request loop with continuous batching
 // of backward-Euler steps (§3 Eqs. 2-3) over device-resident scenes.
 //
-// Built only on the public C ABI of include/sx.h: each request becomes a
-// scene of the server's context at admission; every tick runs one
-// sx_newton_step_batch over all resident scenes, so requests that arrive
-// while others are on the GPU join at the next tick and their work overlaps
-// with the others' inside the same launches.
+// Built only on the public C ABI of include/sx.h. Requests are split by tet
+// count into size-class lanes; each lane has its own context, CUDA stream
+// (smaller classes at higher stream priority) and worker thread. Every tick
+// of a lane admits that lane's waiting requests while they fit the shared
+// memory budget and runs one sx_newton_step_batch over all of its resident
+// scenes, so requests that arrive while others are on the GPU join at the
+// lane's next tick, their work overlaps with the others' inside the same
+// launches, and small scenes do not wait for the PCG of large ones.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,7 +34,7 @@ struct Request {
     std::vector<double> X, young, poisson;
     std::vector<int32_t> tets, pinned;
     double density = 0.0, gravity[3] = {0, 0, 0}, dt = 0.0;
-    int n_steps = 0;
+    int n_steps = 0, lane = 0;
     int64_t n_nodes = 0, n_tets = 0, footprint = 0;
     double t_submit = 0, t_admit = -1, t_eligible = 0, t_done = 0;
     int steps_done = 0, status = SX_OK;
@@ -52,27 +55,33 @@ double pct(std::vector<double> v, double p)
 
 }  // namespace
 
-struct sx_server {
+struct Lane {
+    int index = 0;
     sx_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    std::thread worker;
+    std::vector<Request*> active;
+    bool ticking = false;
+};
+
+struct sx_server {
     int device = 0;
     int64_t budget = 0;
     sx_newton_opts opts{};
     std::mutex mu;
     std::condition_variable cv, idle_cv;
     std::deque<Request*> pending;
-    std::vector<Request*> active;
+    std::vector<Lane*> lanes;
+    std::vector<int64_t> bounds;   // lane i takes n_tets < bounds[i]; the last lane the rest
     std::deque<sx_completion> completions;
     std::unordered_map<int64_t, Request*> finished;
-    std::thread worker;
     bool stop = false;
-    bool ticking = false;
     int64_t next_id = 1, in_use = 0, peak = 0;
     int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, element_steps = 0;
     int ticks = 0;
     double busy_ms = 0.0;
     std::vector<double> step_lat, req_lat;
     Clock::time_point t0;
-    cudaStream_t stream = nullptr;
 
     double now() const
     {
@@ -93,17 +102,17 @@ int64_t footprint(const Request& r)
 }
 
 // registration on the device; returns the status
-int admit(sx_server* S, Request* r)
+int admit(Lane* L, Request* r)
 {
     sx_scene* sc = nullptr;
-    int rc = sx_scene_create(S->ctx, r->n_nodes, r->X.data(), 3, S->stream, &sc);
+    int rc = sx_scene_create(L->ctx, r->n_nodes, r->X.data(), 3, L->stream, &sc);
     if (rc == SX_OK)
         rc = sx_add_snh_tet4(sc, r->tets.data(), r->n_tets, r->young.data(), r->poisson.data(),
-                             r->density, 0, S->stream, nullptr);
+                             r->density, 0, L->stream, nullptr);
     if (rc == SX_OK && !r->pinned.empty())
-        rc = sx_set_pinned(sc, r->pinned.data(), (int64_t)r->pinned.size(), S->stream);
+        rc = sx_set_pinned(sc, r->pinned.data(), (int64_t)r->pinned.size(), L->stream);
     if (rc == SX_OK) rc = sx_set_gravity(sc, r->gravity);
-    if (rc == SX_OK) rc = sx_finalize(sc, S->stream);
+    if (rc == SX_OK) rc = sx_finalize(sc, L->stream);
     if (rc != SX_OK) {
         if (sc) sx_scene_destroy(sc);
         return rc;
@@ -117,13 +126,13 @@ int admit(sx_server* S, Request* r)
     return SX_OK;
 }
 
-void retire(sx_server* S, Request* r, double t)
+void retire(sx_server* S, Lane* L, Request* r, double t)
 {
     if (r->scene) {
         r->x_final.resize(3 * r->n_nodes);
         r->v_final.resize(3 * r->n_nodes);
-        sx_get_state(r->scene, r->x_final.data(), r->v_final.data(), S->stream);
-        cudaStreamSynchronize(S->stream);
+        sx_get_state(r->scene, r->x_final.data(), r->v_final.data(), L->stream);
+        cudaStreamSynchronize(L->stream);
         sx_scene_destroy(r->scene);
         r->scene = nullptr;
     }
@@ -144,43 +153,65 @@ void retire(sx_server* S, Request* r, double t)
     S->finished[r->id] = r;
     S->completed++;
     S->req_lat.push_back(r->t_done - r->t_submit);
+    S->cv.notify_all();   // memory was released: other lanes may admit
 }
 
-void worker_loop(sx_server* S)
+// the lane's first waiting request (FIFO within a lane), or null
+Request* first_pending(sx_server* S, const Lane* L)
+{
+    for (Request* r : S->pending)
+        if (r->lane == L->index) return r;
+    return nullptr;
+}
+
+bool all_idle(sx_server* S)
+{
+    if (!S->pending.empty()) return false;
+    for (Lane* L : S->lanes)
+        if (L->ticking || !L->active.empty()) return false;
+    return true;
+}
+
+void lane_loop(sx_server* S, Lane* L)
 {
     cudaSetDevice(S->device);
     for (;;) {
         std::vector<Request*> to_admit;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
+            S->cv.wait(lk, [&] {
+                if (S->stop || !L->active.empty()) return true;
+                Request* f = first_pending(S, L);
+                return f != nullptr && S->in_use + f->footprint <= S->budget;
+            });
             if (S->stop) break;
-            while (!S->pending.empty() && S->in_use + S->pending.front()->footprint <= S->budget) {
-                Request* r = S->pending.front();
-                S->pending.pop_front();
+            for (auto it = S->pending.begin(); it != S->pending.end();) {
+                Request* r = *it;
+                if (r->lane != L->index) {
+                    ++it;
+                    continue;
+                }
+                if (S->in_use + r->footprint > S->budget) break;
                 S->in_use += r->footprint;
                 S->peak = std::max(S->peak, S->in_use);
                 to_admit.push_back(r);
+                it = S->pending.erase(it);
             }
-            S->ticking = true;
+            L->ticking = true;
         }
         for (Request* r : to_admit) {
-            int rc = admit(S, r);
+            int rc = admit(L, r);
             r->t_admit = r->t_eligible = S->now();
             if (rc != SX_OK) {
                 r->status = rc;
-                retire(S, r, S->now());
+                retire(S, L, r, S->now());
                 continue;
             }
             std::lock_guard<std::mutex> lk(S->mu);
             S->admitted++;
-            S->active.push_back(r);
+            L->active.push_back(r);
         }
-        std::vector<Request*> act;
-        {
-            std::lock_guard<std::mutex> lk(S->mu);
-            act = S->active;
-        }
+        std::vector<Request*> act = L->active;
         if (!act.empty()) {
             // one batched step per group of equal dt
             std::map<double, std::vector<Request*>> groups;
@@ -190,8 +221,8 @@ void worker_loop(sx_server* S)
                 std::vector<sx_scene*> sc;
                 for (Request* r : g.second) sc.push_back(r->scene);
                 std::vector<sx_step_report> rep(sc.size());
-                sx_newton_step_batch(S->ctx, sc.data(), (int)sc.size(), g.first, &S->opts, rep.data(),
-                                     S->stream);
+                sx_newton_step_batch(L->ctx, sc.data(), (int)sc.size(), g.first, &S->opts,
+                                     rep.data(), L->stream);
                 const double te = S->now();
                 for (size_t i = 0; i < g.second.size(); ++i) {
                     Request* r = g.second[i];
@@ -215,19 +246,63 @@ void worker_loop(sx_server* S)
                 std::lock_guard<std::mutex> lk(S->mu);
                 S->busy_ms += te - ts;
                 S->ticks++;
-                // requests admitted during this tick were appended after act
-                std::vector<Request*> rest(S->active.begin() + act.size(), S->active.end());
-                S->active = keep;
-                S->active.insert(S->active.end(), rest.begin(), rest.end());
+                L->active = keep;
             }
-            for (Request* r : fin) retire(S, r, te);
+            for (Request* r : fin) retire(S, L, r, te);
         }
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            S->ticking = false;
-            if (S->pending.empty() && S->active.empty()) S->idle_cv.notify_all();
+            L->ticking = false;
+            if (all_idle(S)) S->idle_cv.notify_all();
         }
     }
+}
+
+void stop_lanes(sx_server* S)
+{
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    for (Lane* L : S->lanes)
+        if (L->worker.joinable()) L->worker.join();
+    for (Lane* L : S->lanes) {
+        for (Request* r : L->active) {
+            if (r->scene) sx_scene_destroy(r->scene);
+            delete r;
+        }
+        if (L->ctx) sx_destroy(L->ctx);
+        if (L->stream) cudaStreamDestroy(L->stream);
+        delete L;
+    }
+    S->lanes.clear();
+    S->stop = false;
+}
+
+// one lane per size class; lane 0 (the smallest scenes) gets the highest
+// stream priority
+int start_lanes(sx_server* S, const std::vector<int64_t>& bounds)
+{
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    S->bounds = bounds;
+    const int n = (int)bounds.size() + 1;
+    for (int i = 0; i < n; ++i) {
+        auto* L = new Lane();
+        L->index = i;
+        S->lanes.push_back(L);
+        sx_options o{};
+        o.device = S->device;
+        const int prio = std::min(least, greatest + i);
+        if (sx_create(&L->ctx, &o) != SX_OK ||
+            cudaStreamCreateWithPriority(&L->stream, cudaStreamNonBlocking, prio) != cudaSuccess) {
+            stop_lanes(S);
+            return SX_ECUDA;
+        }
+    }
+    for (Lane* L : S->lanes) L->worker = std::thread(lane_loop, S, L);
+    return SX_OK;
 }
 
 }  // namespace
@@ -238,19 +313,38 @@ int sx_server_create(sx_ctx* ctx, int64_t budget, const sx_newton_opts* opts, sx
 {
     if (!ctx || !out || budget <= 0) return SX_EINVAL;
     auto* S = new sx_server();
-    S->ctx = ctx;
     S->budget = budget;
     if (opts) S->opts = *opts;
     else sx_newton_opts_default(&S->opts);
-    if (cudaGetDevice(&S->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
         delete S;
         return SX_ECUDA;
     }
     S->t0 = Clock::now();
-    S->worker = std::thread(worker_loop, S);
+    const int rc = start_lanes(S, {20000, 120000});
+    if (rc != SX_OK) {
+        delete S;
+        return rc;
+    }
     *out = S;
     return SX_OK;
+}
+
+int sx_server_set_lanes(sx_server* S, int n_lanes, const int64_t* bounds)
+{
+    if (!S || n_lanes < 1 || n_lanes > SX_SERVER_MAX_LANES || (n_lanes > 1 && !bounds))
+        return SX_EINVAL;
+    std::vector<int64_t> b;
+    for (int i = 0; i + 1 < n_lanes; ++i) {
+        if (bounds[i] <= 0 || (i > 0 && bounds[i] <= bounds[i - 1])) return SX_EINVAL;
+        b.push_back(bounds[i]);
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->submitted > 0) return SX_EORDER;
+    }
+    stop_lanes(S);
+    return start_lanes(S, b);
 }
 
 int sx_server_submit(sx_server* S, const sx_snh_scene_spec* spec, int n_steps, double dt,
@@ -273,6 +367,15 @@ int sx_server_submit(sx_server* S, const sx_snh_scene_spec* spec, int n_steps, d
     r->n_steps = n_steps;
     r->dt = dt;
     r->footprint = footprint(*r);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->lane = (int)S->bounds.size();
+        for (size_t i = 0; i < S->bounds.size(); ++i)
+            if (r->n_tets < S->bounds[i]) {
+                r->lane = (int)i;
+                break;
+            }
+    }
     std::lock_guard<std::mutex> lk(S->mu);
     S->submitted++;
     if (r->footprint > S->budget) {
@@ -284,7 +387,7 @@ int sx_server_submit(sx_server* S, const sx_snh_scene_spec* spec, int n_steps, d
     r->t_submit = S->now();
     if (req_id) *req_id = r->id;
     S->pending.push_back(r);
-    S->cv.notify_one();
+    S->cv.notify_all();
     return SX_OK;
 }
 
@@ -322,9 +425,8 @@ int sx_server_drain(sx_server* S, double timeout_ms)
 {
     if (!S) return SX_EINVAL;
     std::unique_lock<std::mutex> lk(S->mu);
-    bool ok = S->idle_cv.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), [&] {
-        return S->pending.empty() && S->active.empty() && !S->ticking;
-    });
+    bool ok = S->idle_cv.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms),
+                                  [&] { return all_idle(S); });
     return ok ? SX_OK : SX_ENOTCONV;
 }
 
@@ -345,7 +447,9 @@ int sx_server_stats(sx_server* S, sx_serve_stats* st)
     st->request_p99_ms = pct(S->req_lat, 0.99);
     st->bytes_in_use = S->in_use;
     st->peak_bytes = S->peak;
-    st->active = (int)S->active.size();
+    int act = 0;
+    for (Lane* L : S->lanes) act += (int)L->active.size();
+    st->active = act;
     st->pending = (int)S->pending.size();
     st->ticks = S->ticks;
     return SX_OK;
@@ -354,18 +458,9 @@ int sx_server_stats(sx_server* S, sx_serve_stats* st)
 int sx_server_destroy(sx_server* S)
 {
     if (!S) return SX_EINVAL;
-    {
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->stop = true;
-    }
-    S->cv.notify_all();
-    if (S->worker.joinable()) S->worker.join();
-    for (Request* r : S->active)
-        if (r->scene) sx_scene_destroy(r->scene);
-    for (Request* r : S->active) delete r;
+    stop_lanes(S);
     for (Request* r : S->pending) delete r;
     for (auto& kv : S->finished) delete kv.second;
-    cudaStreamDestroy(S->stream);
     delete S;
     return SX_OK;
 }

@@ -13,6 +13,8 @@
 // identity, and their columns drop out because p is zero there.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "sx_internal.cuh"
 
 namespace sx {
@@ -359,11 +361,16 @@ cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int nt
     if (!ntiles) return cudaSuccess;
     const int smem64 = spmv_smem_vals<double>() + kSpmvSmemCols;
     const int smem32 = spmv_smem_vals<float>() + kSpmvSmemCols;
-    static bool attr_set = false;
-    if (!attr_set) {
+    // the shared-memory opt-in is per device; contexts on several host
+    // threads may reach this concurrently (setting it twice is harmless)
+    static std::atomic<unsigned long long> attr_done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (!bit || !(attr_done.load(std::memory_order_acquire) & bit)) {
         cudaFuncSetAttribute(k_spmv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32);
         cudaFuncSetAttribute(k_spmv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem64);
-        attr_set = true;
+        attr_done.fetch_or(bit, std::memory_order_release);
     }
     if (precision == SX_FP32)
         k_spmv<float><<<ntiles, kSpmvThreads, smem32, s>>>(scenes, row_tiles, ntiles, parity, part);

@@ -216,13 +216,20 @@ class Scene:
 class Server:
     """Continuous-batching request loop (include/sx.h serving section)."""
 
-    def __init__(self, ctx: Context, budget_bytes: int, **opts):
+    def __init__(self, ctx: Context, budget_bytes: int, lanes=None, **opts):
+        """lanes: None (the default size classes) or the increasing tet-count
+        bounds of the lanes (e.g. [] for a single lane)."""
         self.ctx = ctx
         o = sx.newton_opts(**opts)
         h = C.c_void_p()
         ctx.check(sx.sx_server_create(ctx.h, int(budget_bytes), C.byref(o), C.byref(h)))
         self.h = h
         self._keep = {}
+        if lanes is not None:
+            b = (C.c_int64 * max(len(lanes), 1))(*[int(v) for v in lanes])
+            rc = sx.sx_server_set_lanes(self.h, len(lanes) + 1, b if lanes else None)
+            if rc != sx.SX_OK:
+                raise sx.SxError(rc, "server lanes")
 
     def submit(self, X, tets, young, poisson, density=1000.0, pinned=None,
                gravity=(0.0, 0.0, -9.81), n_steps=10, dt=0.01):

@@ -25,6 +25,10 @@ Table 3, which are not available as data):
   the interior of a triangle at a seeded distance (§6.4, Eq. 15 inputs).
 * ``random_box_dims``: grid dimensions for a box with a target tet count and
   a random aspect ratio (batched and served scenes).
+* ``mixed_scene``: one scene holding an SNH Kuhn block, a hinge sheet and
+  point-triangle pairs as stacked DOF sets (mixed-stencil workload).
+* ``batch_boxes``: independent Kuhn boxes with log-uniform tet counts and
+  per-scene materials (batched workload).
 """
 from __future__ import annotations
 
@@ -36,7 +40,7 @@ import numpy as np
 __all__ = [
     "rng_for", "kuhn_box", "two_tet", "material_uniform", "material_random",
     "jitter_state", "shell_sheet", "barrier_pairs", "random_box_dims",
-    "GRAVITY",
+    "mixed_scene", "batch_boxes", "GRAVITY",
 ]
 
 GRAVITY = (0.0, 0.0, -9.81)
@@ -256,3 +260,57 @@ def random_box_dims(n_tets_target: float, rng: np.random.Generator,
     s = (cells / np.prod(r)) ** (1.0 / 3.0)
     dims = np.maximum(1, np.rint(r * s)).astype(int)
     return tuple(int(v) for v in dims)
+
+
+def mixed_scene(n_grid: int = 55, n_sheet: int = 1000, n_pairs: int = 4_000_000,
+                seed: int = 3, kb: float = 1e-3, dhat: float = 1e-3, kappa: float = 1e4):
+    """SNH Kuhn block (``n_grid``^3 cubes, h = 1/n_grid, pinned bottom layer),
+    a flat ``n_sheet`` x ``n_sheet`` quad sheet 1 m wide above it (hinge
+    stencils, z noise 0.1 h_s) and ``n_pairs`` free points, each over its
+    own seeded sheet triangle at d ~ U(1e-4, 1e-3) m. Nodes are stacked
+    block, then sheet, then points.
+
+    Extra lumped masses (not given by the workload; a reading): sheet
+    vertices 0.1 kg/m^2 times a third of their incident triangle area,
+    points 1 g each. Returns dict with ``X``, ``x`` (the evaluated state: the
+    block jittered by U(+-0.02 h)), ``tets``, ``E``, ``nu``, ``hinges``,
+    ``q``, ``c``, ``kb``, ``pairs``, ``dhat``, ``kappa``, ``extra_mass``,
+    ``pinned`` and the counts.
+    """
+    m = kuhn_box(n_grid, n_grid, n_grid, h=1.0 / n_grid, seed=seed)
+    nt = m["X"].shape[0]
+    T = m["tets"].shape[0]
+    E, nu = material_random(T, seed)
+    xb = jitter_state(m["X"], 0.02 / n_grid, seed + 1)
+    sh = shell_sheet(n_sheet, length=1.0, z0=1.5, noise=0.1, seed=seed + 2, node_offset=nt)
+    ns = sh["x"].shape[0]
+    bp = barrier_pairs(sh["x"], sh["tris"] - nt, n_pairs, 1e-4, 1e-3, seed=seed + 3,
+                       tri_node_offset=nt, point_node_offset=nt + ns)
+    X = np.vstack([m["X"], sh["X"], bp["points"]])
+    x = np.vstack([xb, sh["x"], bp["points"]])
+    extra = np.zeros(X.shape[0])
+    extra[nt:nt + ns] = 0.1 * sh["h"] ** 2      # 6 half-cells x h^2/2 / 3 per vertex
+    extra[nt + ns:] = 1e-3
+    return {"X": X, "x": x, "tets": m["tets"], "E": E, "nu": nu,
+            "hinges": sh["hinges"], "q": sh["q"], "c": sh["c"], "kb": kb,
+            "pairs": bp["pairs"], "dhat": dhat, "kappa": kappa,
+            "extra_mass": extra, "pinned": m["pinned"],
+            "n_block_nodes": nt, "n_sheet_nodes": ns, "n_points": n_pairs}
+
+
+def batch_boxes(n_scenes: int = 512, t_min: float = 1e3, t_max: float = 2e5, seed: int = 4,
+                h: float = 0.02):
+    """``n_scenes`` independent Kuhn boxes: tet count log-uniform in
+    [t_min, t_max], aspect ratio up to 8:1 (``random_box_dims``), edge ``h``,
+    per-scene E ~ logU[1e4, 1e6] Pa and nu ~ U[0.2, 0.45]. Returns a list of
+    dicts with the ``kuhn_box`` fields plus ``E``, ``nu`` (scalars)."""
+    rng = rng_for(seed)
+    out = []
+    for k in range(n_scenes):
+        T = float(np.exp(rng.uniform(np.log(t_min), np.log(t_max))))
+        dims = random_box_dims(T, rng)
+        m = kuhn_box(*dims, h=h, seed=seed * 100000 + k)
+        m["E"] = float(np.exp(rng.uniform(np.log(1e4), np.log(1e6))))
+        m["nu"] = float(rng.uniform(0.2, 0.45))
+        out.append(m)
+    return out

@@ -21,6 +21,7 @@ SX_ENOTCONV, SX_ESTATE, SX_EDEGENERATE, SX_EBUDGET, SX_ELINESEARCH, SX_EORDER = 
 SX_E, SX_EG, SX_EGH = 0, 1, 2
 SX_FP64, SX_FP32 = 0, 1
 SX_KIND_SNH_TET4, SX_KIND_HINGE4, SX_KIND_PT_BARRIER = 0, 1, 2
+SX_SERVER_MAX_LANES = 8
 
 STATUS_NAMES = {0: "SX_OK", -1: "SX_EINVAL", -2: "SX_ENOMEM", -3: "SX_ECUDA", -4: "SX_ENAN",
                 -5: "SX_ENOTCONV", -6: "SX_ESTATE", -7: "SX_EDEGENERATE", -8: "SX_EBUDGET",
@@ -36,7 +37,7 @@ EXPORTS = [
     "sx_newton_step", "sx_newton_step_batch", "sx_scene_footprint", "sx_scene_bytes",
     "sx_copy_bsr", "sx_copy_grad", "sx_scene_info", "sx_block_info", "sx_eval_stats",
     "sx_profile", "sx_profile_read", "sx_eval_elements_noalloc",
-    "sx_server_create", "sx_server_submit", "sx_server_poll", "sx_server_result",
+    "sx_server_create", "sx_server_set_lanes", "sx_server_submit", "sx_server_poll", "sx_server_result",
     "sx_server_drain", "sx_server_stats", "sx_server_destroy",
 ]
 SX_NOALLOC_MAX_ELEMENTS = 65536
@@ -131,6 +132,7 @@ _SIGS = {
     "sx_profile_read": (_I, [_P, C.POINTER(_D), C.POINTER(_I64), _I]),
     "sx_eval_elements_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
     "sx_server_create": (_I, [_P, _I64, C.POINTER(sx_newton_opts), _PP]),
+    "sx_server_set_lanes": (_I, [_P, _I, C.POINTER(_I64)]),
     "sx_server_submit": (_I, [_P, C.POINTER(sx_snh_scene_spec), _I, _D, C.POINTER(_I64)]),
     "sx_server_poll": (_I, [_P, C.POINTER(sx_completion), _I, C.POINTER(_I)]),
     "sx_server_result": (_I, [_P, _I64, _P, _P]),

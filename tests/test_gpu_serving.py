@@ -46,7 +46,8 @@ def ctx():
 
 
 @pytest.mark.gpu
-def test_alone_equals_mix_with_staggered_arrivals(ctx):
+@pytest.mark.parametrize("lanes", [None, [], [250, 500]])
+def test_alone_equals_mix_with_staggered_arrivals(ctx, lanes):
     from paper_2303_02156_gb300.scene import Scene, Server
     reqs = _requests(6, seed=7)
     steps, dt, g = 3, 0.01, (0.0, 0.0, -9.81)
@@ -61,7 +62,7 @@ def test_alone_equals_mix_with_staggered_arrivals(ctx):
             s.newton_step(dt)
         alone.append(s.get_state())
         s.close()
-    srv = Server(ctx, 8 << 30)
+    srv = Server(ctx, 8 << 30, lanes=lanes)
     ids = []
     for k, (m, E, nu) in enumerate(reqs):
         ids.append(srv.submit(m["X"], m["tets"], E, nu, 1000.0, pinned=m["pinned"], gravity=g,
@@ -103,4 +104,20 @@ def test_admission_by_budget_and_rejection(ctx):
         srv.submit(big["X"], big["tets"], 1e5, 0.3, n_steps=1, dt=0.01)
     assert ei.value.code == sx.SX_EBUDGET
     assert srv.stats()["rejected"] == 1
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_lanes_fixed_after_first_submit(ctx):
+    import ctypes as C
+    from paper_2303_02156_gb300.scene import Server
+    srv = Server(ctx, 1 << 30)
+    b = (C.c_int64 * 2)(100, 50)   # not increasing
+    assert sx.sx_server_set_lanes(srv.h, 3, b) == sx.SX_EINVAL
+    assert sx.sx_server_set_lanes(srv.h, sx.SX_SERVER_MAX_LANES + 1, b) == sx.SX_EINVAL
+    m, E, nu = _requests(1, seed=3)[0]
+    srv.submit(m["X"], m["tets"], E, nu, 1000.0, pinned=m["pinned"], n_steps=1, dt=0.01)
+    b = (C.c_int64 * 1)(100)
+    assert sx.sx_server_set_lanes(srv.h, 2, b) == sx.SX_EORDER
+    assert srv.drain(60000.0) == sx.SX_OK
     srv.close()
