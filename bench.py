@@ -172,7 +172,7 @@ class ClockSampler:
 def clamp_traffic_per_element():
     """DRAM bytes per projected stencil of the clamp kernel from the
     committed ncu summary, if it was taken on the current sources."""
-    path = os.path.join(ROOT, "profiles", "k_clamp_snh_cube.md")
+    path = os.path.join(ROOT, "profiles", "k_clamp_snh_cube_40.md")
     if not os.path.exists(path):
         return None
     h = hashlib.sha256()
