@@ -83,6 +83,26 @@ def workload_config(n, m, nnzb):
             "seed": 2}
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(x, dist=None):
+    """The largest of every rank's ``x`` (the job is as slow as its slowest
+    rank); ``x`` itself without a process group. NCCL groups reduce on the
+    GPU, others (gloo) on the host."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, steps, seconds):
+    """Whole-job throughput: every rank processed ``units_per_rank`` per
+    step (independent replicas), over the slowest rank's time."""
+    return world * units_per_rank * steps / seconds
+
+
 # ------------------------------------------------------------------ CPU oracle
 def oracle_sample(m, E, nu, x, n_tets):
     """Bounded sample of the workload for the CPU oracle: the first n_tets
@@ -470,14 +490,10 @@ def main():
     sx.sx_profile_read(ctx.h, ms_arr, ln_arr, 1)
     sx.sx_profile(ctx.h, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist)
     phases = {sx.PHASES[i]: ms_arr[i] / args.steps for i in range(9)}
     launches = int(sum(ln_arr))
-    value = world * T * args.steps / (total_ms / 1e3)
+    value = job_value(world, T, args.steps, total_ms / 1e3)
 
     # ---- e2e through the C ABI with pinned host buffers
     xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
@@ -491,12 +507,8 @@ def main():
         ctx.check(rc)
         sx.sx_copy_grad(s.h, gh.data_ptr(), sh)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * T * args.steps / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e = {"value": job_value(world, T, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(gh.numel() * 8 + 8)}
 
     # ---- FP32 element-math form and its deviation from the FP64 form

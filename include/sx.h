@@ -79,7 +79,13 @@ typedef struct sx_server sx_server;
 
 typedef struct {
     int device;          /* CUDA device ordinal; -1 = the current device */
-    int reserved[7];
+    int share_sms;       /* 1: the register-heavy kernels (element evaluation,
+                            projection) leave room on every SM -- one block of
+                            each per SM less than fits -- so that work of other
+                            contexts on higher-priority streams (the serving
+                            lanes of smaller scenes) is not held behind their
+                            long-lived blocks; costs throughput. 0: default. */
+    int reserved[6];
 } sx_options;
 
 /* Create / destroy a context. */
@@ -255,10 +261,15 @@ typedef struct {
                             sequence eta_k = min(1/2, sqrt(||g_k|| / ||g_0||))
                             (the paper's solver, §7.2; Nocedal-Wright), never
                             below pcg_tol; 0: fixed pcg_tol */
-    int reserved;
+    int graphs;          /* 1: PCG runs in chunks of 8 iterations replayed from
+                            one CUDA graph per batch (built from kernel nodes
+                            on first use, no stream capture; not while
+                            sx_profile is on); 0: plain launches. Results are
+                            the same either way. */
 } sx_newton_opts;
 
-/* Defaults: 1e-8, 1e-10, 100, 10000, 30, 1, SX_FP64, 1e-4, forcing 0. */
+/* Defaults: 1e-8, 1e-10, 100, 10000, 30, 1, SX_FP64, 1e-4, forcing 0,
+ * graphs 1. */
 void sx_newton_opts_default(sx_newton_opts* o);
 
 typedef struct {
@@ -365,6 +376,8 @@ typedef struct {
     double admit_ms;
     double done_ms;
     double mean_step_ms;
+    char error[120];          /* the library's message for a failed request
+                                 (empty when status is SX_OK) */
 } sx_completion;
 
 typedef struct {

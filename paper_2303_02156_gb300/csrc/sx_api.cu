@@ -58,8 +58,16 @@ struct sx_ctx {
     double prof_ms[SX_PH_COUNT] = {0};
     int64_t prof_launches[SX_PH_COUNT] = {0};
     int elem_blocks_per_sm[2] = {1, 1};
+    bool share_sms = false;
     std::string err;
     int* queue = nullptr;
+    // pinned host staging of per-scene scalars and controls, shared by the
+    // batches of this context (a context runs one call at a time); grown on
+    // demand, freed with the context
+    SceneScal* h_scal = nullptr;
+    int* h_ctl_i = nullptr;
+    double* h_ctl_d = nullptr;
+    int h_cap = 0;
     std::vector<std::unique_ptr<Batch>> batch_cache;
     // projection queue shared by every evaluation of this context (grown on
     // demand; a context runs one evaluation at a time)
@@ -70,6 +78,9 @@ struct sx_ctx {
 };
 
 struct sx_scene {
+    // stream of the latest call on this scene: device memory is allocated
+    // and freed in order on it (stream-ordered pool memory)
+    cudaStream_t stream = nullptr;
     sx_ctx* ctx = nullptr;
     int64_t N = 0;
     double* X = nullptr;
@@ -131,24 +142,43 @@ struct Batch {
     int* d_nonfin = nullptr;
     int* d_clamped = nullptr;
     SceneScal* d_scal = nullptr;     // gathered scalars
-    SceneScal* h_scal = nullptr;     // pinned host mirror
+    SceneScal* h_scal = nullptr;     // pinned host mirror (the context's staging)
     int* d_ctl_i = nullptr;
     double* d_ctl_d = nullptr;
-    int* h_ctl_i = nullptr;
+    int* h_ctl_i = nullptr;          // (the context's staging)
     double* h_ctl_d = nullptr;
+    // stream of the latest call that used the batch: its memory is freed in
+    // order on it (stream-ordered pool memory, no device-wide synchronization)
+    cudaStream_t stream = nullptr;
     int64_t clamp_need = 0;          // projectable stencils of the batch
+    // the PCG chunk (8 iterations) as an instantiated graph, per precision,
+    // with the tolerance and cap it was built with
+    cudaGraphExec_t pcg_graph[2] = {nullptr, nullptr};
+    double pcg_graph_tol[2] = {0.0, 0.0};
+    int pcg_graph_max[2] = {0, 0};
+    bool pcg_graph_failed = false;
     ~Batch()
     {
-        cudaFree(d_row); cudaFree(d_row_beg); cudaFree(d_row_end); cudaFree(d_part_row);
-        cudaFree(d_desc); cudaFree(d_desc_trial); cudaFree(d_elem); cudaFree(d_node);
-        cudaFree(d_slot); cudaFree(d_elem_beg); cudaFree(d_elem_end); cudaFree(d_node_beg);
-        cudaFree(d_node_end); cudaFree(d_part_elem); cudaFree(d_part_node); cudaFree(d_bad);
-        cudaFree(d_nonfin); cudaFree(d_clamped); cudaFree(d_scal); cudaFreeHost(h_scal);
-        cudaFree(d_ctl_i); cudaFree(d_ctl_d); cudaFreeHost(h_ctl_i); cudaFreeHost(h_ctl_d);
+        for (auto& g : pcg_graph)
+            if (g) cudaGraphExecDestroy(g);
+        for (void* p : {(void*)d_row, (void*)d_row_beg, (void*)d_row_end, (void*)d_part_row,
+                        (void*)d_desc, (void*)d_desc_trial, (void*)d_elem, (void*)d_node,
+                        (void*)d_slot, (void*)d_elem_beg, (void*)d_elem_end, (void*)d_node_beg,
+                        (void*)d_node_end, (void*)d_part_elem, (void*)d_part_node, (void*)d_bad,
+                        (void*)d_nonfin, (void*)d_clamped, (void*)d_scal, (void*)d_ctl_i,
+                        (void*)d_ctl_d})
+            if (p) cudaFreeAsync(p, stream);
     }
 };
 
 namespace {
+
+// one projection thread per stencil that can be queued
+int clamp_grid_for(int64_t max_queued)
+{
+    const int64_t t = clamp_block_threads();
+    return (int)std::max<int64_t>(1, std::min<int64_t>((max_queued + t - 1) / t, INT32_MAX));
+}
 
 int fail(sx_ctx* c, int code, const std::string& msg)
 {
@@ -210,11 +240,17 @@ void prof_drain(sx_ctx* ctx)
         }                                                                     \
     } while (0)
 
+// Scene memory comes from the device's stream-ordered pool on the scene's
+// current stream: unlike cudaMalloc/cudaFree, neither allocation nor release
+// synchronizes the whole device, so contexts serving other requests on other
+// streams keep running. The stream is synchronized so that the memory is
+// ready for any stream when the call returns.
 template <typename T>
 int dalloc(sx_scene* s, T** p, size_t count)
 {
     size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+    if (cudaMallocAsync((void**)p, bytes, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return SX_ENOMEM;
@@ -289,9 +325,9 @@ SceneDev make_desc(const sx_scene* s, bool trial)
 template <typename T>
 int upload(sx_ctx* ctx, T** dptr, const std::vector<T>& v, cudaStream_t st)
 {
-    cudaFree(*dptr);
+    if (*dptr) CK(cudaFreeAsync(*dptr, st));
     *dptr = nullptr;
-    CK(cudaMalloc((void**)dptr, std::max<size_t>(v.size(), 1) * sizeof(T)));
+    CK(cudaMallocAsync((void**)dptr, std::max<size_t>(v.size(), 1) * sizeof(T), st));
     if (!v.empty()) CK(cudaMemcpyAsync(*dptr, v.data(), v.size() * sizeof(T),
                                        cudaMemcpyHostToDevice, st));
     return SX_OK;
@@ -342,29 +378,48 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         if ((rc = upload(ctx, &B->d_row, B->row_tiles, st)) != SX_OK) return rc;
         if ((rc = upload(ctx, &B->d_row_beg, rb, st)) != SX_OK) return rc;
         if ((rc = upload(ctx, &B->d_row_end, re, st)) != SX_OK) return rc;
-        CK(cudaMalloc((void**)&B->d_part_row, std::max<size_t>(B->row_tiles.size(), 1) * sizeof(double)));
+        CK(cudaMallocAsync((void**)&B->d_part_row,
+                           std::max<size_t>(B->row_tiles.size(), 1) * sizeof(double), st));
         const size_t net = std::max<size_t>(B->elem_tiles.size(), 1);
         const size_t nnt = std::max<size_t>(B->node_tiles.size(), 1);
-        CK(cudaMalloc((void**)&B->d_part_elem, net * sizeof(double)));
-        CK(cudaMalloc((void**)&B->d_part_node, 2 * nnt * sizeof(double)));
-        CK(cudaMalloc((void**)&B->d_bad, net * sizeof(int)));
-        CK(cudaMalloc((void**)&B->d_nonfin, net * sizeof(int)));
-        CK(cudaMalloc((void**)&B->d_clamped, net * sizeof(int)));
-        CK(cudaMalloc((void**)&B->d_scal, n * sizeof(SceneScal)));
-        CK(cudaMallocHost((void**)&B->h_scal, n * sizeof(SceneScal)));
-        CK(cudaMalloc((void**)&B->d_ctl_i, n * sizeof(int)));
-        CK(cudaMalloc((void**)&B->d_ctl_d, n * sizeof(double)));
-        CK(cudaMallocHost((void**)&B->h_ctl_i, n * sizeof(int)));
-        CK(cudaMallocHost((void**)&B->h_ctl_d, n * sizeof(double)));
+        CK(cudaMallocAsync((void**)&B->d_part_elem, net * sizeof(double), st));
+        CK(cudaMallocAsync((void**)&B->d_part_node, 2 * nnt * sizeof(double), st));
+        CK(cudaMallocAsync((void**)&B->d_bad, net * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&B->d_nonfin, net * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&B->d_clamped, net * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&B->d_scal, n * sizeof(SceneScal), st));
+        CK(cudaMallocAsync((void**)&B->d_ctl_i, n * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&B->d_ctl_d, n * sizeof(double), st));
         int64_t cap = 0;
         for (sx_scene* s : B->scenes)
             for (auto& b : s->blocks)
                 if (b.kind != SX_KIND_HINGE4) cap += b.n;
         B->clamp_need = std::max<int64_t>(cap, 1);
-        CK(cudaMalloc((void**)&B->d_desc, n * sizeof(SceneDev)));
-        CK(cudaMalloc((void**)&B->d_desc_trial, n * sizeof(SceneDev)));
+        CK(cudaMallocAsync((void**)&B->d_desc, n * sizeof(SceneDev), st));
+        CK(cudaMallocAsync((void**)&B->d_desc_trial, n * sizeof(SceneDev), st));
         B->versions.assign(n, 0);
     }
+    // host staging: the context's pinned buffers (grown when a larger batch
+    // comes; pinned allocation is the only synchronizing call left, and it
+    // happens once per context growth)
+    if (ctx->h_cap < n) {
+        cudaFreeHost(ctx->h_scal);
+        cudaFreeHost(ctx->h_ctl_i);
+        cudaFreeHost(ctx->h_ctl_d);
+        ctx->h_scal = nullptr;
+        ctx->h_ctl_i = nullptr;
+        ctx->h_ctl_d = nullptr;
+        ctx->h_cap = 0;
+        const int cap = std::max(n, 64);
+        CK(cudaMallocHost((void**)&ctx->h_scal, cap * sizeof(SceneScal)));
+        CK(cudaMallocHost((void**)&ctx->h_ctl_i, cap * sizeof(int)));
+        CK(cudaMallocHost((void**)&ctx->h_ctl_d, cap * sizeof(double)));
+        ctx->h_cap = cap;
+    }
+    B->h_scal = ctx->h_scal;
+    B->h_ctl_i = ctx->h_ctl_i;
+    B->h_ctl_d = ctx->h_ctl_d;
+    B->stream = st;
     bool dirty = false;
     for (int i = 0; i < n; ++i) dirty |= B->versions[i] != B->scenes[i]->version;
     if (dirty) {
@@ -379,19 +434,19 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
 }
 
 // grows the context's projection queue to hold `need` stencils
-int ensure_clamp_queue(sx_ctx* ctx, int64_t need)
+int ensure_clamp_queue(sx_ctx* ctx, int64_t need, cudaStream_t st)
 {
     if (need > (int64_t)INT32_MAX) return fail(ctx, SX_EINVAL, "eval: too many projectable stencils");
     if (ctx->clamp_cap >= need && ctx->clampM) return SX_OK;
-    cudaFree(ctx->clampM);
-    cudaFree(ctx->clampRef);
+    if (ctx->clampM) cudaFreeAsync(ctx->clampM, st);
+    if (ctx->clampRef) cudaFreeAsync(ctx->clampRef, st);
     ctx->clampM = nullptr;
     ctx->clampRef = nullptr;
-    if (!ctx->clampCount) CK(cudaMalloc((void**)&ctx->clampCount, 2 * sizeof(int)));
-    if (cudaMalloc((void**)&ctx->clampM, (size_t)need * 45 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->clampRef, (size_t)need * sizeof(ClampRef)) != cudaSuccess) {
+    if (!ctx->clampCount) CK(cudaMallocAsync((void**)&ctx->clampCount, 2 * sizeof(int), st));
+    if (cudaMallocAsync((void**)&ctx->clampM, (size_t)need * 45 * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&ctx->clampRef, (size_t)need * sizeof(ClampRef), st) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(ctx->clampM);
+        if (ctx->clampM) cudaFreeAsync(ctx->clampM, st);
         ctx->clampM = nullptr;
         ctx->clamp_cap = 0;
         return fail(ctx, SX_ENOMEM, "eval: device allocation failed (projection queue)");
@@ -491,7 +546,7 @@ int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool 
     L.tile_clamped = B->d_clamped;
     L.queue = ctx->queue;
     if (level >= 2 && project) {
-        int rq = ensure_clamp_queue(ctx, B->clamp_need);
+        int rq = ensure_clamp_queue(ctx, B->clamp_need, st);
         if (rq != SX_OK) return rq;
     }
     L.clamp_M = ctx->clampM;
@@ -499,7 +554,8 @@ int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool 
     L.clamp_count = ctx->clampCount;
     L.clamp_failed = ctx->clampCount + 1;
     L.clamp_cap = (int)std::min<int64_t>(ctx->clamp_cap, INT32_MAX);
-    L.clamp_grid = ctx->sm_count * 8;
+    L.clamp_grid = clamp_grid_for(B->clamp_need);
+    L.share_sms = ctx->share_sms;
     const int pidx = precision == SX_FP32 ? 1 : 0;
     int grid = std::min<int>(L.ntiles, ctx->sm_count * ctx->elem_blocks_per_sm[pidx]);
     grid = std::max(grid, 1);
@@ -626,11 +682,23 @@ int sx_create(sx_ctx** out, const sx_options* opt)
         delete ctx;
         return SX_ECUDA;
     }
+    ctx->share_sms = opt && opt->share_sms;
     for (int p = 0; p < 2; ++p) {
         int nb = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elements_kernel(p),
                                                       elements_block_threads(), 0);
-        ctx->elem_blocks_per_sm[p] = std::max(nb, 1);
+        // sharing: the persistent element grid holds one block per SM less
+        ctx->elem_blocks_per_sm[p] = std::max(ctx->share_sms ? nb - 1 : nb, 1);
+    }
+    {
+        // keep released pool memory mapped and cached for the next
+        // stream-ordered allocation (scenes and batches come and go)
+        cudaMemPool_t pool = nullptr;
+        if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
     }
     if (cudaMalloc((void**)&ctx->queue, sizeof(int)) != cudaSuccess) {
         delete ctx;
@@ -646,6 +714,9 @@ int sx_destroy(sx_ctx* ctx)
     prof_drain(ctx);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     ctx->batch_cache.clear();
+    cudaFreeHost(ctx->h_scal);
+    cudaFreeHost(ctx->h_ctl_i);
+    cudaFreeHost(ctx->h_ctl_d);
     cudaFree(ctx->queue);
     cudaFree(ctx->clampM);
     cudaFree(ctx->clampRef);
@@ -668,6 +739,7 @@ int sx_scene_create(sx_ctx* ctx, int64_t n_nodes, const double* X_rest, int64_t 
     cudaStream_t st = (cudaStream_t)stream;
     auto* s = new sx_scene();
     s->ctx = ctx;
+    s->stream = st;
     s->N = n_nodes;
     const size_t n3 = 3 * (size_t)n_nodes;
     int rc = SX_OK;
@@ -711,8 +783,11 @@ int sx_scene_destroy(sx_scene* s)
 {
     if (!s) return SX_EINVAL;
     if (s->ctx) drop_batches_with(s->ctx, s);
-    cudaDeviceSynchronize();
-    for (void* p : s->allocs) cudaFree(p);
+    // the work of the scene's latest stream ends before its memory goes back
+    // to the pool; only that stream is waited for, not the device
+    cudaStreamSynchronize(s->stream);
+    for (void* p : s->allocs) cudaFreeAsync(p, s->stream);
+    cudaStreamSynchronize(s->stream);
     delete s;
     return SX_OK;
 }
@@ -727,6 +802,7 @@ int sx_add_snh_tet4(sx_scene* s, const int32_t* tets, int64_t n, const double* y
     if (n < 0 || (n > 0 && (!tets || !young || !poisson)) || !(density >= 0.0))
         return fail(ctx, SX_EINVAL, "add_snh_tet4: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     BlockHost b;
     b.kind = SX_KIND_SNH_TET4;
     b.n = n;
@@ -771,6 +847,7 @@ int sx_add_hinge4(sx_scene* s, const int32_t* stencils, int64_t n, const double*
     if (n < 0 || (n > 0 && (!stencils || !q || !c)))
         return fail(ctx, SX_EINVAL, "add_hinge4: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     BlockHost b;
     b.kind = SX_KIND_HINGE4;
     b.n = n;
@@ -801,6 +878,7 @@ int sx_add_pt_barrier(sx_scene* s, const int32_t* pairs, int64_t n, double dhat,
     if (n < 0 || (n > 0 && !pairs) || !(dhat > 0.0) || !(kappa >= 0.0))
         return fail(ctx, SX_EINVAL, "add_pt_barrier: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     BlockHost b;
     b.kind = SX_KIND_PT_BARRIER;
     b.n = n;
@@ -817,6 +895,7 @@ int sx_add_node_mass(sx_scene* s, const double* mass, void* stream)
     if (!s || !mass) return SX_EINVAL;
     sx_ctx* ctx = s->ctx;
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     double* tmp = nullptr;
     CK(cudaMallocAsync((void**)&tmp, s->N * sizeof(double), st));
     CK(cudaMemcpyAsync(tmp, mass, s->N * sizeof(double), cudaMemcpyDefault, st));
@@ -834,6 +913,7 @@ int sx_set_pinned(sx_scene* s, const int32_t* nodes, int64_t n, void* stream)
     if (!s || n < 0 || (n > 0 && !nodes)) return SX_EINVAL;
     sx_ctx* ctx = s->ctx;
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     int* bad = nullptr;
     int32_t* tmp = nullptr;
     CK(cudaMallocAsync((void**)&bad, sizeof(int), st));
@@ -859,8 +939,9 @@ int sx_set_gravity(sx_scene* s, const double g[3])
     if (!s || !g) return SX_EINVAL;
     sx_ctx* ctx = s->ctx;
     for (int i = 0; i < 3; ++i) s->gravity[i] = g[i];
-    CK(cudaMemcpy((char*)s->sc + offsetof(SceneScal, grav), s->gravity, 3 * sizeof(double),
-                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync((char*)s->sc + offsetof(SceneScal, grav), s->gravity, 3 * sizeof(double),
+                       cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
     return SX_OK;
 }
 
@@ -869,17 +950,18 @@ int sx_finalize(sx_scene* s, void* stream)
     if (!s) return SX_EINVAL;
     sx_ctx* ctx = s->ctx;
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     if (s->finalized) return SX_OK;
     if (s->pat.row_ptr) return fail(ctx, SX_EORDER, "finalize: scene already finalized once");
     // concatenated stencils in registration order
     int4* conn = nullptr;
-    CK(cudaMalloc((void**)&conn, std::max<int64_t>(s->nst, 1) * sizeof(int4)));
+    CK(cudaMallocAsync((void**)&conn, std::max<int64_t>(s->nst, 1) * sizeof(int4), st));
     for (auto& b : s->blocks)
         if (b.n) CK(cudaMemcpyAsync(conn + b.base, b.conn, b.n * sizeof(int4),
                                     cudaMemcpyDeviceToDevice, st));
     std::string err;
     int rc = build_pattern(conn, s->nst, s->N, &s->pat, &err, st);
-    cudaFree(conn);
+    cudaFreeAsync(conn, st);
     if (rc != SX_OK) return fail(ctx, rc, err);
     for (void* p : {(void*)s->pat.row_ptr, (void*)s->pat.col, (void*)s->pat.diag_slot,
                     (void*)s->pat.slots, (void*)s->pat.slot_ptr, (void*)s->pat.slot_src,
@@ -914,6 +996,7 @@ int sx_set_state(sx_scene* s, const double* x, const double* v, void* stream)
     if (!s) return SX_EINVAL;
     sx_ctx* ctx = s->ctx;
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     const size_t b = 3 * (size_t)s->N * sizeof(double);
     if (x) CK(cudaMemcpyAsync(s->x, x, b, cudaMemcpyDefault, st));
     if (v) CK(cudaMemcpyAsync(s->v, v, b, cudaMemcpyDefault, st));
@@ -925,6 +1008,7 @@ int sx_get_state(sx_scene* s, double* x, double* v, void* stream)
     if (!s) return SX_EINVAL;
     sx_ctx* ctx = s->ctx;
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     const size_t b = 3 * (size_t)s->N * sizeof(double);
     if (x) CK(cudaMemcpyAsync(x, s->x, b, cudaMemcpyDefault, st));
     if (v) CK(cudaMemcpyAsync(v, s->v, b, cudaMemcpyDefault, st));
@@ -936,6 +1020,7 @@ int sx_set_inertia(sx_scene* s, double dt, const double* x_tilde, void* stream)
     if (!s) return SX_EINVAL;
     sx_ctx* ctx = s->ctx;
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     if (!x_tilde) {
         if (s->inertia_on) s->version++;
         s->inertia_on = false;
@@ -971,6 +1056,7 @@ int sx_eval_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, int level, int pr
         int rc = check_scene_ready(scenes[i]);
         if (rc != SX_OK) return rc;
         if (scenes[i]->ctx != ctx) return fail(ctx, SX_EINVAL, "eval: scene of another context");
+        scenes[i]->stream = st;
         if (level >= 2 && precision == SX_FP32 && (rc = ensure_vals32(ctx, scenes[i])) != SX_OK)
             return rc;
     }
@@ -1036,6 +1122,7 @@ int sx_copy_bsr(sx_scene* s, int32_t* row_ptr, int32_t* col, void* vals, int* dt
     if (rc != SX_OK) return rc;
     sx_ctx* ctx = s->ctx;
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     if (row_ptr)
         CK(cudaMemcpyAsync(row_ptr, s->pat.row_ptr, (s->N + 1) * sizeof(int32_t),
                            cudaMemcpyDefault, st));
@@ -1107,6 +1194,7 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     if (precision != SX_FP64 && precision != SX_FP32)
         return fail(ctx, SX_EINVAL, "eval_elements: bad precision");
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     const BlockHost& b = s->blocks[energy_id];
     if (slots && b.n)
         CK(cudaMemcpyAsync(slots, s->pat.slots + 16 * b.base, b.n * 16 * sizeof(int32_t),
@@ -1152,18 +1240,23 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     L.clamp_count = qC;
     L.clamp_failed = qC ? qC + 1 : nullptr;
     L.clamp_cap = (int)std::max<int64_t>(b.n, 1);
-    L.clamp_grid = ctx->sm_count * 8;
+    L.clamp_grid = clamp_grid_for(L.clamp_cap);
+    L.share_sms = ctx->share_sms;
     int grid = std::min<int>(L.ntiles, ctx->sm_count * ctx->elem_blocks_per_sm[precision == SX_FP32]);
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, std::max(grid, 1), st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     int qfail[2] = {0, 0};
     if (qC) CK(cudaMemcpyAsync(qfail, qC, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (qM) { cudaFree(qM); cudaFree(qR); cudaFree(qC); }
-    cudaFree(d_tiles);
+    if (qM) {
+        cudaFreeAsync(qM, st);
+        cudaFreeAsync(qR, st);
+        cudaFreeAsync(qC, st);
+    }
+    cudaFreeAsync(d_tiles, st);
+    if (tmpE) cudaFreeAsync(tmpE, st);
+    if (scratch_g) cudaFreeAsync(scratch_g, st);
     if (qfail[1]) return fail(ctx, SX_ENAN, "eval_elements: projection did not converge");
-    if (tmpE) cudaFree(tmpE);
-    if (scratch_g) cudaFree(scratch_g);
     return SX_OK;
 }
 
@@ -1203,8 +1296,60 @@ void sx_newton_opts_default(sx_newton_opts* o)
     o->precision = SX_FP64;
     o->armijo_c = 1e-4;
     o->forcing = 0;
-    o->reserved = 0;
+    o->graphs = 1;
 }
+
+}  // extern "C"
+
+namespace {
+
+int ensure_pcg_graph(sx_ctx* ctx, Batch* B, const sx_newton_opts& o)
+{
+    (void)ctx;
+    const int pi = o.precision == SX_FP32 ? 1 : 0;
+    if (B->pcg_graph_failed) return SX_ECUDA;
+    if (B->pcg_graph[pi] && B->pcg_graph_tol[pi] == o.pcg_tol && B->pcg_graph_max[pi] == o.max_pcg)
+        return SX_OK;
+    if (B->pcg_graph[pi]) {
+        cudaGraphExecDestroy(B->pcg_graph[pi]);
+        B->pcg_graph[pi] = nullptr;
+    }
+    PcgChunkArgs a{};
+    a.scenes = B->d_desc;
+    a.n_scenes = (int)B->scenes.size();
+    a.node_tiles = B->d_node;
+    a.n_node_tiles = (int)B->node_tiles.size();
+    a.row_tiles = B->d_row;
+    a.n_row_tiles = (int)B->row_tiles.size();
+    a.precision = o.precision;
+    a.part_row = B->d_part_row;
+    a.row_beg = B->d_row_beg;
+    a.row_end = B->d_row_end;
+    a.part_node = B->d_part_node;
+    a.node_beg = B->d_node_beg;
+    a.node_end = B->d_node_end;
+    a.tol = o.pcg_tol;
+    a.max_iter = o.max_pcg;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    if (ok) ok = add_pcg_chunk_nodes(g, a) == cudaSuccess;
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        cudaGetLastError();
+        B->pcg_graph_failed = true;   // plain launches from now on
+        return SX_ECUDA;
+    }
+    B->pcg_graph[pi] = ex;
+    B->pcg_graph_tol[pi] = o.pcg_tol;
+    B->pcg_graph_max[pi] = o.max_pcg;
+    return SX_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
                          const sx_newton_opts* opts_in, sx_step_report* reports, void* stream)
@@ -1218,6 +1363,7 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
     for (int i = 0; i < n; ++i) {
         int rc = check_scene_ready(scenes[i]);
         if (rc != SX_OK) return rc;
+        scenes[i]->stream = st;
         if (o.precision == SX_FP32 && (rc = ensure_vals32(ctx, scenes[i])) != SX_OK) return rc;
         sx_scene* s = scenes[i];
         if (!s->inertia_on || s->dt != dt || s->inertia_mode != 1) s->version++;
@@ -1230,6 +1376,7 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
     if (rc != SX_OK) return rc;
     const int nnt = (int)B->node_tiles.size();
     std::vector<int> done(n, 0), status(n, SX_OK), iters(n, 0), pcg_it(n, 0), halv(n, 0);
+    std::string why;   // the first failure's reason
     std::vector<double> g0(n, 0.0), gl(n, 0.0), E(n, 0.0);
     std::vector<int> act(n, 1);
     if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
@@ -1247,8 +1394,18 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             if (done[i]) continue;
             const SceneScal& sc = B->h_scal[i];
             E[i] = sc.E;
-            if (sc.nonfinite || !std::isfinite(sc.E)) { status[i] = SX_ENAN; done[i] = 1; continue; }
-            if (sc.bad_state) { status[i] = SX_ESTATE; done[i] = 1; continue; }
+            if (sc.nonfinite || !std::isfinite(sc.E)) {
+                status[i] = SX_ENAN;
+                done[i] = 1;
+                if (why.empty()) why = "non-finite energy, gradient, Hessian or projection";
+                continue;
+            }
+            if (sc.bad_state) {
+                status[i] = SX_ESTATE;
+                done[i] = 1;
+                if (why.empty()) why = "a barrier pair at distance <= 0";
+                continue;
+            }
             double gn = std::sqrt(sc.gnorm2);
             gl[i] = gn;
             if (it == 0) {
@@ -1261,7 +1418,12 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
                 done[i] = 1;
                 continue;
             }
-            if (it == o.max_newton) { status[i] = SX_ENOTCONV; done[i] = 1; continue; }
+            if (it == o.max_newton) {
+                status[i] = SX_ENOTCONV;
+                done[i] = 1;
+                if (why.empty()) why = "Newton iteration cap reached";
+                continue;
+            }
             iters[i] = it + 1;
             ++live;
         }
@@ -1282,21 +1444,29 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
                                             B->d_part_node, st));
         PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg, B->d_node_end, n,
                                            B->d_desc, 0, o.pcg_tol, o.max_pcg, st));
-        int par = 0;
+        const bool graph = o.graphs && !ctx->prof_on && ensure_pcg_graph(ctx, B, o) == SX_OK;
         for (int k = 0;; k += 8) {
-            for (int j = 0; j < 8; ++j) {
-                PL(SX_PH_PCG, 1, launch_pcg_pdir(B->d_desc, B->d_node, nnt, o.precision, par, st));
-                PL(SX_PH_SPMV, 1, launch_spmv_pq(B->d_desc, B->d_row, (int)B->row_tiles.size(),
-                                                 o.precision, par, B->d_part_row, st));
-                PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_row, 1, B->d_row_beg,
-                                                   B->d_row_end, n, B->d_desc, 1, o.pcg_tol,
-                                                   o.max_pcg, st));
-                PL(SX_PH_PCG, 1, launch_pcg_update(B->d_desc, B->d_node, nnt, par,
-                                                   B->d_part_node, st));
-                PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg,
-                                                   B->d_node_end, n, B->d_desc, 2, o.pcg_tol,
-                                                   o.max_pcg, st));
-                par ^= 1;
+            if (graph) {
+                const int pi = o.precision == SX_FP32 ? 1 : 0;
+                CK(cudaGraphLaunch(B->pcg_graph[pi], st));
+                ctx->prof_launches[SX_PH_SPMV] += 8;
+                ctx->prof_launches[SX_PH_PCG] += 32;
+            } else {
+                int par = 0;
+                for (int j = 0; j < 8; ++j) {
+                    PL(SX_PH_PCG, 1, launch_pcg_pdir(B->d_desc, B->d_node, nnt, o.precision, par, st));
+                    PL(SX_PH_SPMV, 1, launch_spmv_pq(B->d_desc, B->d_row, (int)B->row_tiles.size(),
+                                                     o.precision, par, B->d_part_row, st));
+                    PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_row, 1, B->d_row_beg,
+                                                       B->d_row_end, n, B->d_desc, 1, o.pcg_tol,
+                                                       o.max_pcg, st));
+                    PL(SX_PH_PCG, 1, launch_pcg_update(B->d_desc, B->d_node, nnt, par,
+                                                       B->d_part_node, st));
+                    PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg,
+                                                       B->d_node_end, n, B->d_desc, 2, o.pcg_tol,
+                                                       o.max_pcg, st));
+                    par ^= 1;
+                }
             }
             if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
             bool all = true;
@@ -1308,7 +1478,12 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             if (!act[i]) continue;
             pcg_it[i] += B->h_scal[i].pcg_iters;
             if (B->h_scal[i].pcg_status != 0) {
-                status[i] = B->h_scal[i].pcg_status == 3 ? SX_ECUDA : SX_ENOTCONV;
+                const int ps = B->h_scal[i].pcg_status;
+                status[i] = ps == 3 ? SX_ECUDA : SX_ENOTCONV;
+                if (why.empty())
+                    why = ps == 3 ? "PCG: a staged SpMV tile copy did not complete in time"
+                          : ps == 1 ? "PCG: p.q <= 0 (the system is not positive definite)"
+                                    : "PCG: iteration cap reached";
                 done[i] = 1;
                 act[i] = 0;
             }
@@ -1355,6 +1530,7 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             if (search[i]) {
                 status[i] = SX_ELINESEARCH;
                 done[i] = 1;
+                if (why.empty()) why = "line search: no sufficient decrease";
             }
     }
     std::vector<int> all(n, 1);
@@ -1377,7 +1553,8 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
         }
         if (status[i] != SX_OK) worst = status[i];
     }
-    if (worst != SX_OK) fail(ctx, worst, "newton_step: at least one scene did not converge");
+    if (worst != SX_OK)
+        fail(ctx, worst, "newton_step: at least one scene failed" + (why.empty() ? std::string() : " (" + why + ")"));
     return worst;
 }
 
@@ -1489,6 +1666,7 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
     NaPtrs* P = nullptr;
     if ((rc = na_setup(ctx, &P)) != SX_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
     // scene descriptor and tile table into the static arrays (pageable
     // sources: each copy returns once the source has been consumed)
     const SceneDev desc = make_desc(s, false);
@@ -1519,7 +1697,8 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
     L.clamp_count = P->counters + 1;
     L.clamp_failed = P->counters + 2;
     L.clamp_cap = SX_NOALLOC_MAX_ELEMENTS;
-    L.clamp_grid = ctx->sm_count * 8;
+    L.clamp_grid = clamp_grid_for(L.clamp_cap);
+    L.share_sms = ctx->share_sms;
     const int grid = std::max(1, std::min<int>(nt, ctx->sm_count * ctx->elem_blocks_per_sm[precision == SX_FP32]));
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));

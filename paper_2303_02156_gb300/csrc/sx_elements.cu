@@ -27,6 +27,8 @@
 // in float; the projection always runs in double.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "sx_barrier.cuh"
 #include "sx_clamp.cuh"
 #include "sx_internal.cuh"
@@ -35,8 +37,12 @@ namespace sx {
 
 static constexpr int kElemThreads = 128;
 static constexpr int kClampThreads = 64;
+// 64 threads x 81 doubles of eigenvectors = 41.5 KB static; + 17 KB makes
+// 58.5 KB, so at most 3 blocks share an SM's 228 KB
+static constexpr int kClampSharePad = 17 * 1024;
 
 int elements_block_threads() { return kElemThreads; }
+int clamp_block_threads() { return kClampThreads; }
 
 template <typename R>
 struct Vec3 {
@@ -532,7 +538,8 @@ k_elements(ElemLaunch L)
     }
 }
 
-// phase 2 of the projection: one thread per queued stencil; subtracts
+// phase 2 of the projection: one thread per queued stencil (the loop takes
+// more than one trip only if the grid is smaller than the queue); subtracts
 // sum_{lambda_t < -tau} lambda_t u_t u_t^T from its Hessian blocks
 template <typename HT>
 __global__ void __launch_bounds__(kClampThreads)
@@ -629,13 +636,29 @@ cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s)
 cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
 {
     if (L.ntiles == 0 || !(L.level >= 2 && L.project)) return cudaSuccess;
-    // the queue length stays on the device; the grid covers it in
-    // grid-stride loops
+    // the queue length stays on the device: the grid covers the largest
+    // possible queue with one stencil per thread, and blocks past the actual
+    // length exit at once. Short-lived blocks let work of higher-priority
+    // streams (the serving lanes of small scenes) in between.
     const int cgrid = L.clamp_grid > 0 ? L.clamp_grid : 1;
+    // sharing: unused dynamic shared memory lowers the resident blocks per
+    // SM from 4 (register limit) to 3, keeping a quarter of the registers free
+    const int pad = L.share_sms ? kClampSharePad : 0;
+    if (pad) {
+        static std::atomic<unsigned long long> attr_done{0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+        if (!bit || !(attr_done.load(std::memory_order_acquire) & bit)) {
+            cudaFuncSetAttribute(k_clamp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, pad);
+            cudaFuncSetAttribute(k_clamp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, pad);
+            attr_done.fetch_or(bit, std::memory_order_release);
+        }
+    }
     if (L.precision == SX_FP32)
-        k_clamp<float><<<cgrid, kClampThreads, 0, s>>>(L);
+        k_clamp<float><<<cgrid, kClampThreads, pad, s>>>(L);
     else
-        k_clamp<double><<<cgrid, kClampThreads, 0, s>>>(L);
+        k_clamp<double><<<cgrid, kClampThreads, pad, s>>>(L);
     return cudaGetLastError();
 }
 

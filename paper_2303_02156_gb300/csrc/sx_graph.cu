@@ -223,12 +223,13 @@ int build_incidence(const int4* conn, int64_t nst, int64_t N, int** ptr_out, int
                     std::string* err, cudaStream_t s)
 {
     int *deg = nullptr, *ptr = nullptr, *src = nullptr, *fill = nullptr;
-    if (cudaMalloc((void**)&deg, N * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&ptr, (N + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&src, (4 * nst + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&fill, N * sizeof(int)) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&deg, N * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&ptr, (N + 1) * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&src, (4 * nst + 1) * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&fill, N * sizeof(int), s) != cudaSuccess) {
         *err = "incidence: device allocation failed";
-        cudaFree(deg); cudaFree(ptr); cudaFree(src); cudaFree(fill);
+        for (void* p : {(void*)deg, (void*)ptr, (void*)src, (void*)fill})
+            if (p) cudaFreeAsync(p, s);
         return SX_ENOMEM;
     }
     cudaMemsetAsync(deg, 0, N * sizeof(int), s);
@@ -369,13 +370,13 @@ int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
     int rc;
     {
         int* bad = nullptr;
-        cudaMalloc((void**)&bad, sizeof(int));
+        cudaMallocAsync((void**)&bad, sizeof(int), s);
         cudaMemsetAsync(bad, 0, sizeof(int), s);
         if (nst) k_check_ids<<<nblk(nst, 256), 256, 0, s>>>(conn, nst, N, bad);
         int h = 0;
         cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
-        cudaFree(bad);
+        cudaFreeAsync(bad, s);
         if (h) {
             *err = "finalize: a stencil references a node id outside [0, n_nodes)";
             return SX_EINVAL;
@@ -389,9 +390,9 @@ int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
     if (rc != SX_OK) return rc;
     // candidate rows
     int *cand = nullptr, *row_len = nullptr;
-    if (cudaMalloc((void**)&cand, (16 * nst + N) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&row_len, N * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&P.row_ptr, (N + 1) * sizeof(int)) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&cand, (16 * nst + N) * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&row_len, N * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&P.row_ptr, (N + 1) * sizeof(int), s) != cudaSuccess) {
         *err = "finalize: device allocation failed (pattern)";
         return SX_ENOMEM;
     }
@@ -404,7 +405,7 @@ int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
     cudaStreamSynchronize(s);
     P.nnzb = nnz;
     // padded: staged SpMV tiles read 16-byte aligned windows
-    if (cudaMalloc((void**)&P.col, (nnz + 16) * sizeof(int)) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&P.col, (nnz + 16) * sizeof(int), s) != cudaSuccess) {
         *err = "finalize: device allocation failed (col)";
         return SX_ENOMEM;
     }
@@ -413,13 +414,13 @@ int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
     cudaFreeAsync(row_len, s);
     // slots, diagonal slots, slot contributor lists
     int *slot_deg = nullptr, *fill = nullptr;
-    if (cudaMalloc((void**)&P.slots, (16 * nst + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&P.diag_slot, N * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&slot_deg, (nnz + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&fill, (nnz + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&P.slot_ptr, (nnz + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&P.slot_src, (16 * nst + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&P.slot_order, (nnz + 1) * sizeof(int)) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&P.slots, (16 * nst + 1) * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&P.diag_slot, N * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&slot_deg, (nnz + 1) * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&fill, (nnz + 1) * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&P.slot_ptr, (nnz + 1) * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&P.slot_src, (16 * nst + 1) * sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&P.slot_order, (nnz + 1) * sizeof(int), s) != cudaSuccess) {
         *err = "finalize: device allocation failed (slots)";
         return SX_ENOMEM;
     }

@@ -170,10 +170,12 @@ struct ElemLaunch {
     int* clamp_failed;
     int clamp_cap;
     int clamp_grid;
+    int share_sms;        // leave one projection block per SM for other work
 };
 cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s);
 cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s);
 int elements_block_threads();
+int clamp_block_threads();
 const void* elements_kernel(int precision);
 
 // registration and pattern (sx_graph.cu)
@@ -237,6 +239,27 @@ cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int nt
 cudaError_t launch_pcg_pdir(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
                             int precision, int parity, cudaStream_t s);
 int spmv_rows_per_tile();
+// sets the SpMV kernels' shared-memory opt-in on the current device (once)
+void prepare_spmv();
+// eight PCG iterations as a chain of kernel nodes appended to `graph`
+struct PcgChunkArgs {
+    const SceneDev* scenes;
+    int n_scenes;
+    const Tile* node_tiles;
+    int n_node_tiles;
+    const Tile* row_tiles;
+    int n_row_tiles;
+    int precision;
+    double* part_row;
+    const int* row_beg;
+    const int* row_end;
+    double* part_node;
+    const int* node_beg;
+    const int* node_end;
+    double tol;
+    int max_iter;
+};
+cudaError_t add_pcg_chunk_nodes(cudaGraph_t graph, const PcgChunkArgs& a);
 cudaError_t launch_pcg_update(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
                               int parity, double* part, cudaStream_t s);
 cudaError_t launch_pcg_reduce(const double* part, int nv, const int* tbeg, const int* tend,

@@ -41,6 +41,7 @@ struct Request {
     sx_scene* scene = nullptr;
     double step_sum = 0.0;
     std::vector<double> x_final, v_final;
+    std::string error;
 };
 
 double pct(std::vector<double> v, double p)
@@ -147,6 +148,8 @@ void retire(sx_server* S, Lane* L, Request* r, double t)
     c.admit_ms = r->t_admit;
     c.done_ms = r->t_done;
     c.mean_step_ms = r->steps_done ? r->step_sum / r->steps_done : 0.0;
+    std::strncpy(c.error, r->error.c_str(), sizeof(c.error) - 1);
+    c.error[sizeof(c.error) - 1] = 0;
     std::lock_guard<std::mutex> lk(S->mu);
     S->in_use -= r->footprint;
     S->completions.push_back(c);
@@ -204,6 +207,7 @@ void lane_loop(sx_server* S, Lane* L)
             r->t_admit = r->t_eligible = S->now();
             if (rc != SX_OK) {
                 r->status = rc;
+                r->error = std::string("admission: ") + sx_last_error(L->ctx);
                 retire(S, L, r, S->now());
                 continue;
             }
@@ -230,7 +234,11 @@ void lane_loop(sx_server* S, Lane* L)
                     r->step_sum += lat;
                     r->steps_done++;
                     r->t_eligible = te;
-                    if (rep[i].status != SX_OK) r->status = rep[i].status;
+                    if (rep[i].status != SX_OK && r->status == SX_OK) {
+                        r->status = rep[i].status;
+                        r->error = std::string("step ") + std::to_string(r->steps_done) +
+                                   ": " + sx_last_error(L->ctx);
+                    }
                     std::lock_guard<std::mutex> lk(S->mu);
                     S->step_lat.push_back(lat);
                     S->element_steps += r->n_tets;
@@ -294,6 +302,9 @@ int start_lanes(sx_server* S, const std::vector<int64_t>& bounds)
         S->lanes.push_back(L);
         sx_options o{};
         o.device = S->device;
+        // every lane but the one of the smallest scenes leaves room on the
+        // SMs for the lanes below it
+        o.share_sms = i > 0 ? 1 : 0;
         const int prio = std::min(least, greatest + i);
         if (sx_create(&L->ctx, &o) != SX_OK ||
             cudaStreamCreateWithPriority(&L->stream, cudaStreamNonBlocking, prio) != cudaSuccess) {

@@ -355,12 +355,8 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
 
 int spmv_rows_per_tile() { return kSpmvRows; }
 
-cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int ntiles,
-                           int precision, int parity, double* part, cudaStream_t s)
+void prepare_spmv()
 {
-    if (!ntiles) return cudaSuccess;
-    const int smem64 = spmv_smem_vals<double>() + kSpmvSmemCols;
-    const int smem32 = spmv_smem_vals<float>() + kSpmvSmemCols;
     // the shared-memory opt-in is per device; contexts on several host
     // threads may reach this concurrently (setting it twice is harmless)
     static std::atomic<unsigned long long> attr_done{0};
@@ -368,10 +364,21 @@ cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int nt
     cudaGetDevice(&dev);
     const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
     if (!bit || !(attr_done.load(std::memory_order_acquire) & bit)) {
-        cudaFuncSetAttribute(k_spmv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32);
-        cudaFuncSetAttribute(k_spmv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem64);
+        cudaFuncSetAttribute(k_spmv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             spmv_smem_vals<float>() + kSpmvSmemCols);
+        cudaFuncSetAttribute(k_spmv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             spmv_smem_vals<double>() + kSpmvSmemCols);
         attr_done.fetch_or(bit, std::memory_order_release);
     }
+}
+
+cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int ntiles,
+                           int precision, int parity, double* part, cudaStream_t s)
+{
+    if (!ntiles) return cudaSuccess;
+    const int smem64 = spmv_smem_vals<double>() + kSpmvSmemCols;
+    const int smem32 = spmv_smem_vals<float>() + kSpmvSmemCols;
+    prepare_spmv();
     if (precision == SX_FP32)
         k_spmv<float><<<ntiles, kSpmvThreads, smem32, s>>>(scenes, row_tiles, ntiles, parity, part);
     else
@@ -490,6 +497,73 @@ cudaError_t launch_pcg_reduce(const double* part, int nv, const int* tbeg, const
     if (!nscenes) return cudaSuccess;
     k_pcg_reduce<<<nscenes, kRedT, 0, s>>>(part, nv, tbeg, tend, scenes, stage, tol, max_iter);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ PCG chunk graph
+// The eight iterations of launch order (direction, SpMV, p.q reduction,
+// update, r.z reduction) as kernel nodes of an explicitly built graph, each
+// node depending on the one before: the same kernels, arguments and order as
+// the plain launches. Built without stream capture, so host threads of other
+// contexts may synchronize the device while it is built.
+namespace {
+struct NodeChain {
+    cudaGraph_t g;
+    cudaGraphNode_t last = nullptr;
+    cudaError_t add(const void* func, unsigned grid, unsigned block, unsigned smem, void** args)
+    {
+        if (grid == 0) return cudaSuccess;
+        cudaKernelNodeParams p{};
+        p.func = const_cast<void*>(func);
+        p.gridDim = dim3(grid);
+        p.blockDim = dim3(block);
+        p.sharedMemBytes = smem;
+        p.kernelParams = args;
+        p.extra = nullptr;
+        cudaGraphNode_t n = nullptr;
+        cudaError_t e = cudaGraphAddKernelNode(&n, g, last ? &last : nullptr, last ? 1 : 0, &p);
+        if (e == cudaSuccess) last = n;
+        return e;
+    }
+};
+}  // namespace
+
+cudaError_t add_pcg_chunk_nodes(cudaGraph_t graph, const PcgChunkArgs& a)
+{
+    prepare_spmv();
+    NodeChain c{graph};
+    const bool f32 = a.precision == SX_FP32;
+    const void* pdir = f32 ? (const void*)k_pcg_pdir<true> : (const void*)k_pcg_pdir<false>;
+    const void* spmv = f32 ? (const void*)k_spmv<float> : (const void*)k_spmv<double>;
+    const unsigned smem = (unsigned)(kSpmvSmemCols + (f32 ? spmv_smem_vals<float>()
+                                                          : spmv_smem_vals<double>()));
+    // argument values must outlive each cudaGraphAddKernelNode call only
+    const SceneDev* scenes = a.scenes;
+    const Tile* nt = a.node_tiles;
+    const Tile* rt = a.row_tiles;
+    int nnt = a.n_node_tiles, nrt = a.n_row_tiles;
+    double* prow = a.part_row;
+    double* pnode = a.part_node;
+    const int *rb = a.row_beg, *re = a.row_end, *nb = a.node_beg, *ne = a.node_end;
+    double tol = a.tol;
+    int maxit = a.max_iter;
+    int nv1 = 1, nv2 = 2, st1 = 1, st2 = 2;
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < 8 && e == cudaSuccess; ++j) {
+        int par = j & 1;
+        void* a_pdir[] = {&scenes, &nt, &nnt, &par};
+        void* a_spmv[] = {&scenes, &rt, &nrt, &par, &prow};
+        void* a_red1[] = {&prow, &nv1, &rb, &re, &scenes, &st1, &tol, &maxit};
+        void* a_upd[] = {&scenes, &nt, &nnt, &par, &pnode};
+        void* a_red2[] = {&pnode, &nv2, &nb, &ne, &scenes, &st2, &tol, &maxit};
+        if (e == cudaSuccess) e = c.add(pdir, (unsigned)nnt, kVecThreads, 0, a_pdir);
+        if (e == cudaSuccess) e = c.add(spmv, (unsigned)nrt, kSpmvThreads, smem, a_spmv);
+        if (e == cudaSuccess)
+            e = c.add((const void*)k_pcg_reduce, (unsigned)a.n_scenes, kRedT, 0, a_red1);
+        if (e == cudaSuccess) e = c.add((const void*)k_pcg_update, (unsigned)nnt, kVecThreads, 0, a_upd);
+        if (e == cudaSuccess)
+            e = c.add((const void*)k_pcg_reduce, (unsigned)a.n_scenes, kRedT, 0, a_red2);
+    }
+    return e;
 }
 
 // ------------------------------------------------------------------ line search

@@ -45,14 +45,14 @@ PHASES = ["elements", "clamp", "assemble", "grad", "reduce", "spmv", "pcg", "new
 
 
 class sx_options(C.Structure):
-    _fields_ = [("device", C.c_int), ("reserved", C.c_int * 7)]
+    _fields_ = [("device", C.c_int), ("share_sms", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class sx_newton_opts(C.Structure):
     _fields_ = [("newton_tol", C.c_double), ("pcg_tol", C.c_double),
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("max_halvings", C.c_int),
                 ("project", C.c_int), ("precision", C.c_int), ("armijo_c", C.c_double),
-                ("forcing", C.c_int), ("reserved", C.c_int)]
+                ("forcing", C.c_int), ("graphs", C.c_int)]
 
 
 class sx_step_report(C.Structure):
@@ -76,7 +76,8 @@ class sx_snh_scene_spec(C.Structure):
 class sx_completion(C.Structure):
     _fields_ = [("req_id", C.c_int64), ("status", C.c_int), ("steps", C.c_int),
                 ("n_tets", C.c_int64), ("submit_ms", C.c_double), ("admit_ms", C.c_double),
-                ("done_ms", C.c_double), ("mean_step_ms", C.c_double)]
+                ("done_ms", C.c_double), ("mean_step_ms", C.c_double),
+                ("error", C.c_char * 120)]
 
 
 class sx_serve_stats(C.Structure):

@@ -74,7 +74,7 @@ def test_alone_equals_mix_with_staggered_arrivals(ctx, lanes):
     st = srv.stats()
     assert st["completed"] == 6 and st["step_p99_ms"] >= st["step_p50_ms"] > 0
     for rid, (xa, va) in zip(ids, alone):
-        assert done[rid]["status"] == sx.SX_OK and done[rid]["steps"] == steps
+        assert done[rid]["status"] == sx.SX_OK and done[rid]["steps"] == steps, done[rid]["error"]
         x, v = srv.result(rid)
         assert np.array_equal(x, xa) and np.array_equal(v, va)
     srv.close()
