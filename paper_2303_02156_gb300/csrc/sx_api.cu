@@ -150,6 +150,13 @@ struct Batch {
     // stream of the latest call that used the batch: its memory is freed in
     // order on it (stream-ordered pool memory, no device-wide synchronization)
     cudaStream_t stream = nullptr;
+    // per-scene tile ranges of the full node and row lists (host copies)
+    std::vector<int> h_nb, h_ne, h_rb, h_re;
+    // PCG tile lists compacted to the scenes still iterating (same tiles in
+    // the same order per scene, so every per-scene sum is unchanged)
+    Tile* d_node_c = nullptr;
+    Tile* d_row_c = nullptr;
+    int *d_nb_c = nullptr, *d_ne_c = nullptr, *d_rb_c = nullptr, *d_re_c = nullptr;
     int64_t clamp_need = 0;          // projectable stencils of the batch
     // the PCG chunk (8 iterations) as an instantiated graph, per precision,
     // with the tolerance and cap it was built with
@@ -166,7 +173,8 @@ struct Batch {
                         (void*)d_slot, (void*)d_elem_beg, (void*)d_elem_end, (void*)d_node_beg,
                         (void*)d_node_end, (void*)d_part_elem, (void*)d_part_node, (void*)d_bad,
                         (void*)d_nonfin, (void*)d_clamped, (void*)d_scal, (void*)d_ctl_i,
-                        (void*)d_ctl_d})
+                        (void*)d_ctl_d, (void*)d_node_c, (void*)d_row_c, (void*)d_nb_c,
+                        (void*)d_ne_c, (void*)d_rb_c, (void*)d_re_c})
             if (p) cudaFreeAsync(p, stream);
     }
 };
@@ -378,6 +386,10 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         if ((rc = upload(ctx, &B->d_row, B->row_tiles, st)) != SX_OK) return rc;
         if ((rc = upload(ctx, &B->d_row_beg, rb, st)) != SX_OK) return rc;
         if ((rc = upload(ctx, &B->d_row_end, re, st)) != SX_OK) return rc;
+        B->h_nb = nb;
+        B->h_ne = ne;
+        B->h_rb = rb;
+        B->h_re = re;
         CK(cudaMallocAsync((void**)&B->d_part_row,
                            std::max<size_t>(B->row_tiles.size(), 1) * sizeof(double), st));
         const size_t net = std::max<size_t>(B->elem_tiles.size(), 1);
@@ -430,6 +442,46 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         CK(cudaStreamSynchronize(st));
         for (int i = 0; i < n; ++i) B->versions[i] = B->scenes[i]->version;
     }
+    return SX_OK;
+}
+
+// Fills the batch's compacted PCG tile lists with the tiles of the scenes
+// flagged in `keep` (node and row tiles, and per-scene ranges; other scenes
+// get empty ranges). Returns the tile counts through nnt_c, nrt_c.
+int compact_pcg_tiles(sx_ctx* ctx, Batch* B, const std::vector<int>& keep, int* nnt_c,
+                      int* nrt_c, cudaStream_t st)
+{
+    const int n = (int)B->scenes.size();
+    if (!B->d_node_c) {
+        CK(cudaMallocAsync((void**)&B->d_node_c, std::max<size_t>(B->node_tiles.size(), 1) * sizeof(Tile), st));
+        CK(cudaMallocAsync((void**)&B->d_row_c, std::max<size_t>(B->row_tiles.size(), 1) * sizeof(Tile), st));
+        CK(cudaMallocAsync((void**)&B->d_nb_c, n * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&B->d_ne_c, n * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&B->d_rb_c, n * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&B->d_re_c, n * sizeof(int), st));
+    }
+    std::vector<Tile> nodes, rows;
+    std::vector<int> nb(n, 0), ne(n, 0), rb(n, 0), re(n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (!keep[i]) continue;
+        nb[i] = (int)nodes.size();
+        nodes.insert(nodes.end(), B->node_tiles.begin() + B->h_nb[i], B->node_tiles.begin() + B->h_ne[i]);
+        ne[i] = (int)nodes.size();
+        rb[i] = (int)rows.size();
+        rows.insert(rows.end(), B->row_tiles.begin() + B->h_rb[i], B->row_tiles.begin() + B->h_re[i]);
+        re[i] = (int)rows.size();
+    }
+    if (!nodes.empty())
+        CK(cudaMemcpyAsync(B->d_node_c, nodes.data(), nodes.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
+    if (!rows.empty())
+        CK(cudaMemcpyAsync(B->d_row_c, rows.data(), rows.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B->d_nb_c, nb.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B->d_ne_c, ne.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B->d_rb_c, rb.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B->d_re_c, re.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));   // the host vectors are pageable
+    *nnt_c = (int)nodes.size();
+    *nrt_c = (int)rows.size();
     return SX_OK;
 }
 
@@ -1445,8 +1497,17 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
         PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg, B->d_node_end, n,
                                            B->d_desc, 0, o.pcg_tol, o.max_pcg, st));
         const bool graph = o.graphs && !ctx->prof_on && ensure_pcg_graph(ctx, B, o) == SX_OK;
+        // the PCG runs over the full tile lists until at most half of the
+        // scenes they cover are still iterating; then over lists compacted
+        // to those scenes (plain launches), compacting again at each halving
+        bool compacted = false;
+        int included = n;
+        const Tile *cn = B->d_node, *cr = B->d_row;
+        const int *cnb = B->d_node_beg, *cne = B->d_node_end, *crb = B->d_row_beg,
+                  *cre = B->d_row_end;
+        int cnnt = nnt, cnrt = (int)B->row_tiles.size();
         for (int k = 0;; k += 8) {
-            if (graph) {
+            if (graph && !compacted) {
                 const int pi = o.precision == SX_FP32 ? 1 : 0;
                 CK(cudaGraphLaunch(B->pcg_graph[pi], st));
                 ctx->prof_launches[SX_PH_SPMV] += 8;
@@ -1454,25 +1515,38 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             } else {
                 int par = 0;
                 for (int j = 0; j < 8; ++j) {
-                    PL(SX_PH_PCG, 1, launch_pcg_pdir(B->d_desc, B->d_node, nnt, o.precision, par, st));
-                    PL(SX_PH_SPMV, 1, launch_spmv_pq(B->d_desc, B->d_row, (int)B->row_tiles.size(),
-                                                     o.precision, par, B->d_part_row, st));
-                    PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_row, 1, B->d_row_beg,
-                                                       B->d_row_end, n, B->d_desc, 1, o.pcg_tol,
-                                                       o.max_pcg, st));
-                    PL(SX_PH_PCG, 1, launch_pcg_update(B->d_desc, B->d_node, nnt, par,
-                                                       B->d_part_node, st));
-                    PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, B->d_node_beg,
-                                                       B->d_node_end, n, B->d_desc, 2, o.pcg_tol,
-                                                       o.max_pcg, st));
+                    PL(SX_PH_PCG, 1, launch_pcg_pdir(B->d_desc, cn, cnnt, o.precision, par, st));
+                    PL(SX_PH_SPMV, 1, launch_spmv_pq(B->d_desc, cr, cnrt, o.precision, par,
+                                                     B->d_part_row, st));
+                    PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_row, 1, crb, cre, n, B->d_desc,
+                                                       1, o.pcg_tol, o.max_pcg, st));
+                    PL(SX_PH_PCG, 1, launch_pcg_update(B->d_desc, cn, cnnt, par, B->d_part_node,
+                                                       st));
+                    PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, cnb, cne, n, B->d_desc,
+                                                       2, o.pcg_tol, o.max_pcg, st));
                     par ^= 1;
                 }
             }
             if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
-            bool all = true;
+            std::vector<int> running(n, 0);
+            int nrun = 0;
             for (int i = 0; i < n; ++i)
-                if (act[i] && !B->h_scal[i].pcg_done) all = false;
-            if (all) break;
+                if (act[i] && !B->h_scal[i].pcg_done) {
+                    running[i] = 1;
+                    ++nrun;
+                }
+            if (nrun == 0) break;
+            if (n > 1 && 2 * nrun <= included) {
+                if ((rc = compact_pcg_tiles(ctx, B, running, &cnnt, &cnrt, st)) != SX_OK) return rc;
+                compacted = true;
+                included = nrun;
+                cn = B->d_node_c;
+                cr = B->d_row_c;
+                cnb = B->d_nb_c;
+                cne = B->d_ne_c;
+                crb = B->d_rb_c;
+                cre = B->d_re_c;
+            }
         }
         for (int i = 0; i < n; ++i) {
             if (!act[i]) continue;
