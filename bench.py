@@ -286,6 +286,8 @@ def run_mixed(ctx, stream, flush, reps=5):
            "tets": int(w["tets"].shape[0]), "hinges": int(w["hinges"].shape[0]),
            "pairs": int(w["pairs"].shape[0]), "nodes": int(w["X"].shape[0]),
            "nnzb": int(info["nnzb"]), "stencils": n_st}
+    out["autotune"] = {"fp32": ctx.autotune([s], sx.SX_FP32, sh),
+                       "fp64": ctx.autotune([s], sx.SX_FP64, sh)}
     for name, prec in (("fp32", sx.SX_FP32), ("fp64", sx.SX_FP64)):
         for _ in range(3):
             ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh))
@@ -347,6 +349,8 @@ def run_batched(ctx, stream, n_scenes, dt=0.01):
     arr = (C.c_void_p * n_scenes)(*[s.h.value for s in sc])
     for b, s in zip(boxes, sc):
         s.set_state(x=scenes.jitter_state(b["X"], 0.002 * 0.02, seed=7))
+    # launch shapes for the batch from the library's autotuner
+    out["autotune"] = {"fp64": ctx.autotune(sc, sx.SX_FP64, sh), "fp32": ctx.autotune(sc, sx.SX_FP32, sh)}
     for prec, name in ((sx.SX_FP64, "fp64"), (sx.SX_FP32, "fp32")):
         for _ in range(2):
             ctx.check(sx.sx_eval_batch(ctx.h, arr, n_scenes, sx.SX_EGH, 1, prec, None, sh))
@@ -460,6 +464,10 @@ def main():
         rc = sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh)
         if rc != sx.SX_OK:
             ctx.check(rc)
+
+    # launch shapes picked by the library's autotuner on this scene
+    tune = {"fp64": ctx.autotune([s], sx.SX_FP64, sh), "fp32": ctx.autotune([s], sx.SX_FP32, sh)}
+    s.set_state(x=x)
 
     for _ in range(args.warmup):
         eval_async()
@@ -605,7 +613,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu,
             "phase_ms_per_step": {k: round(v, 4) for k, v in phases.items()},
             "projected_fraction": clamped / T, "fp32": fp32, "newton_step": newton,
-            "serving": serving, "mixed": mixed, "batched": batched,
+            "serving": serving, "mixed": mixed, "batched": batched, "autotune": tune,
             "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
                         "max": max(step_ms)},
         }

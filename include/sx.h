@@ -318,6 +318,32 @@ int sx_profile(sx_ctx* ctx, int enable);
  * whether or not timing is enabled). reset != 0 clears both. */
 int sx_profile_read(sx_ctx* ctx, double* ms, int64_t* launches, int reset);
 
+/* ---- launch shapes and the autotuner -----------------------------------
+ * (No counterpart in the paper: these pick GPU launch configurations.)
+ * Per context and precision: the projection kernel's block size (32, 64 or
+ * 128 threads; default 64) and the element kernel's grid (blocks per SM of
+ * the persistent launch, at most what fits -- the default; 0 = one 128-
+ * element tile per block). Every shape computes bit-identical results. */
+typedef struct {
+    int clamp_threads;        /* chosen projection block size */
+    int elem_blocks_per_sm;   /* chosen element grid (0 = one tile per block) */
+    double default_ms;        /* one E+g+projected H+assembly pass, default shape */
+    double tuned_ms;          /* the same pass with the chosen shape */
+    int candidates;           /* shapes timed */
+} sx_tune_report;
+
+/* Times one E+g+projected-H+assembly pass of the batch (best of 3 after a
+ * warm-up, CUDA events on `stream`) under the default shape, each other
+ * projection block size, and each element-grid choice, and keeps the
+ * fastest for `precision` in the context (used by every later call of the
+ * context). Overwrites the scenes' assembled outputs. Synchronous. */
+int sx_autotune(sx_ctx* ctx, sx_scene* const* scenes, int n, int precision,
+                sx_tune_report* report, void* stream);
+/* Sets / reads a shape directly (SX_EINVAL for an unsupported block size;
+ * the element grid is capped at what fits). */
+int sx_set_launch_shape(sx_ctx* ctx, int precision, int clamp_threads, int elem_blocks_per_sm);
+int sx_get_launch_shape(sx_ctx* ctx, int precision, int* clamp_threads, int* elem_blocks_per_sm);
+
 /* ---- footprint (for admission by memory) ------------------------------ */
 typedef struct {
     int64_t n_nodes;

@@ -57,8 +57,13 @@ struct sx_ctx {
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[SX_PH_COUNT] = {0};
     int64_t prof_launches[SX_PH_COUNT] = {0};
-    int elem_blocks_per_sm[2] = {1, 1};
+    int elem_blocks_per_sm[2] = {1, 1};   // occupancy limit of the element kernel
     bool share_sms = false;
+    // launch shapes per precision (sx_autotune / sx_set_launch_shape):
+    // projection block size, and element-kernel blocks per SM of the
+    // persistent grid (0: one tile per block)
+    int clamp_threads[2] = {64, 64};
+    int elem_bps[2] = {1, 1};
     std::string err;
     int* queue = nullptr;
     // pinned host staging of per-scene scalars and controls, shared by the
@@ -182,10 +187,19 @@ struct Batch {
 namespace {
 
 // one projection thread per stencil that can be queued
-int clamp_grid_for(int64_t max_queued)
+int clamp_grid_for(int64_t max_queued, int threads)
 {
-    const int64_t t = clamp_block_threads();
+    const int64_t t = threads;
     return (int)std::max<int64_t>(1, std::min<int64_t>((max_queued + t - 1) / t, INT32_MAX));
+}
+
+// element-kernel grid for `ntiles` tiles under the context's launch shape
+int elem_grid(const sx_ctx* ctx, int precision, int ntiles)
+{
+    const int p = precision == SX_FP32 ? 1 : 0;
+    const int bps = ctx->elem_bps[p];
+    const int g = bps <= 0 ? ntiles : std::min<int>(ntiles, ctx->sm_count * bps);
+    return std::max(g, 1);
 }
 
 int fail(sx_ctx* c, int code, const std::string& msg)
@@ -606,11 +620,11 @@ int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool 
     L.clamp_count = ctx->clampCount;
     L.clamp_failed = ctx->clampCount + 1;
     L.clamp_cap = (int)std::min<int64_t>(ctx->clamp_cap, INT32_MAX);
-    L.clamp_grid = clamp_grid_for(B->clamp_need);
-    L.share_sms = ctx->share_sms;
     const int pidx = precision == SX_FP32 ? 1 : 0;
-    int grid = std::min<int>(L.ntiles, ctx->sm_count * ctx->elem_blocks_per_sm[pidx]);
-    grid = std::max(grid, 1);
+    L.clamp_threads = ctx->clamp_threads[pidx];
+    L.clamp_grid = clamp_grid_for(B->clamp_need, L.clamp_threads);
+    L.share_sms = ctx->share_sms;
+    const int grid = elem_grid(ctx, precision, L.ntiles);
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (level >= 2 && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_elem, 1, 0, B->d_elem_beg, B->d_elem_end,
@@ -741,6 +755,7 @@ int sx_create(sx_ctx** out, const sx_options* opt)
                                                       elements_block_threads(), 0);
         // sharing: the persistent element grid holds one block per SM less
         ctx->elem_blocks_per_sm[p] = std::max(ctx->share_sms ? nb - 1 : nb, 1);
+        ctx->elem_bps[p] = ctx->elem_blocks_per_sm[p];
     }
     {
         // keep released pool memory mapped and cached for the next
@@ -1292,10 +1307,10 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     L.clamp_count = qC;
     L.clamp_failed = qC ? qC + 1 : nullptr;
     L.clamp_cap = (int)std::max<int64_t>(b.n, 1);
-    L.clamp_grid = clamp_grid_for(L.clamp_cap);
+    L.clamp_threads = ctx->clamp_threads[precision == SX_FP32 ? 1 : 0];
+    L.clamp_grid = clamp_grid_for(L.clamp_cap, L.clamp_threads);
     L.share_sms = ctx->share_sms;
-    int grid = std::min<int>(L.ntiles, ctx->sm_count * ctx->elem_blocks_per_sm[precision == SX_FP32]);
-    PL(SX_PH_ELEMENTS, 1, launch_elements(L, std::max(grid, 1), st));
+    PL(SX_PH_ELEMENTS, 1, launch_elements(L, elem_grid(ctx, precision, L.ntiles), st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     int qfail[2] = {0, 0};
     if (qC) CK(cudaMemcpyAsync(qfail, qC, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1664,6 +1679,101 @@ int sx_scene_bytes(sx_scene* s, int64_t* bytes)
     return SX_OK;
 }
 
+int sx_set_launch_shape(sx_ctx* ctx, int precision, int clamp_threads, int elem_blocks_per_sm)
+{
+    if (!ctx || (precision != SX_FP64 && precision != SX_FP32) ||
+        (clamp_threads != 32 && clamp_threads != 64 && clamp_threads != 128) ||
+        elem_blocks_per_sm < 0)
+        return SX_EINVAL;
+    const int p = precision == SX_FP32 ? 1 : 0;
+    ctx->clamp_threads[p] = clamp_threads;
+    ctx->elem_bps[p] = std::min(elem_blocks_per_sm, ctx->elem_blocks_per_sm[p]);
+    return SX_OK;
+}
+
+int sx_get_launch_shape(sx_ctx* ctx, int precision, int* clamp_threads, int* elem_blocks_per_sm)
+{
+    if (!ctx || (precision != SX_FP64 && precision != SX_FP32)) return SX_EINVAL;
+    const int p = precision == SX_FP32 ? 1 : 0;
+    if (clamp_threads) *clamp_threads = ctx->clamp_threads[p];
+    if (elem_blocks_per_sm) *elem_blocks_per_sm = ctx->elem_bps[p];
+    return SX_OK;
+}
+
+// Launch-shape autotuner: times E + g + projected H + assembly of this batch
+// (CUDA events on the caller's stream, best of 3 after a warm-up pass) for
+// the default shape, then for each other projection block size, then for
+// each element-grid choice with the best block size, and keeps the fastest
+// for `precision` in the context. Every shape computes the same result (the
+// per-element work and every sum are independent of the grid).
+int sx_autotune(sx_ctx* ctx, sx_scene* const* scenes, int n, int precision,
+                sx_tune_report* report, void* stream)
+{
+    if (!ctx || !scenes || n <= 0 || (precision != SX_FP64 && precision != SX_FP32))
+        return SX_EINVAL;
+    const int p = precision == SX_FP32 ? 1 : 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    int cand = 0;
+    auto timed = [&](int ct, int bps, double* ms) -> int {
+        ctx->clamp_threads[p] = ct;
+        ctx->elem_bps[p] = bps;
+        int rc = sx_eval_batch(ctx, scenes, n, SX_EGH, 1, precision, nullptr, stream);
+        if (rc != SX_OK) return rc;
+        double best = 1e300;
+        for (int r = 0; r < 3; ++r) {
+            CK(cudaEventRecord(a, st));
+            rc = sx_eval_batch(ctx, scenes, n, SX_EGH, 1, precision, nullptr, stream);
+            if (rc != SX_OK) return rc;
+            CK(cudaEventRecord(b, st));
+            CK(cudaEventSynchronize(b));
+            float t = 0.0f;
+            CK(cudaEventElapsedTime(&t, a, b));
+            best = std::min(best, (double)t);
+        }
+        ++cand;
+        *ms = best;
+        return SX_OK;
+    };
+    const int occ = ctx->elem_blocks_per_sm[p];
+    int best_ct = 64, best_bps = occ;
+    double def_ms = 0.0, best_ms = 0.0, ms = 0.0;
+    int rc = timed(best_ct, best_bps, &def_ms);
+    best_ms = def_ms;
+    for (int ct : {32, 128}) {
+        if (rc != SX_OK) break;
+        rc = timed(ct, best_bps, &ms);
+        if (rc == SX_OK && ms < best_ms) {
+            best_ms = ms;
+            best_ct = ct;
+        }
+    }
+    for (int bps : {occ - 1, 0}) {
+        if (rc != SX_OK || bps < 0 || (bps == 0 && occ == 0)) continue;
+        if (bps == occ - 1 && bps < 1) continue;
+        rc = timed(best_ct, bps, &ms);
+        if (rc == SX_OK && ms < best_ms) {
+            best_ms = ms;
+            best_bps = bps;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->clamp_threads[p] = best_ct;
+    ctx->elem_bps[p] = best_bps;
+    if (rc != SX_OK) return rc;
+    if (report) {
+        report->clamp_threads = best_ct;
+        report->elem_blocks_per_sm = best_bps;
+        report->default_ms = def_ms;
+        report->tuned_ms = best_ms;
+        report->candidates = cand;
+    }
+    return SX_OK;
+}
+
 }  // extern "C"
 
 // ==================================================================== no-alloc
@@ -1771,9 +1881,10 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
     L.clamp_count = P->counters + 1;
     L.clamp_failed = P->counters + 2;
     L.clamp_cap = SX_NOALLOC_MAX_ELEMENTS;
-    L.clamp_grid = clamp_grid_for(L.clamp_cap);
+    L.clamp_threads = ctx->clamp_threads[precision == SX_FP32 ? 1 : 0];
+    L.clamp_grid = clamp_grid_for(L.clamp_cap, L.clamp_threads);
     L.share_sms = ctx->share_sms;
-    const int grid = std::max(1, std::min<int>(nt, ctx->sm_count * ctx->elem_blocks_per_sm[precision == SX_FP32]));
+    const int grid = elem_grid(ctx, precision, nt);
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     int failed = 0;

@@ -36,10 +36,14 @@
 namespace sx {
 
 static constexpr int kElemThreads = 128;
+// projection block sizes the launch may use (picked by sx_autotune; 64 by
+// default); each thread keeps its 9x9 eigenvector matrix (648 B) in dynamic
+// shared memory
 static constexpr int kClampThreads = 64;
-// 64 threads x 81 doubles of eigenvectors = 41.5 KB static; + 17 KB makes
+// sharing (64-thread blocks): 41.5 KB of eigenvectors + 17 KB unused makes
 // 58.5 KB, so at most 3 blocks share an SM's 228 KB
 static constexpr int kClampSharePad = 17 * 1024;
+static constexpr int kClampMaxSmem = 81 * 8 * 128 + kClampSharePad;
 
 int elements_block_threads() { return kElemThreads; }
 int clamp_block_threads() { return kClampThreads; }
@@ -541,12 +545,12 @@ k_elements(ElemLaunch L)
 // phase 2 of the projection: one thread per queued stencil (the loop takes
 // more than one trip only if the grid is smaller than the queue); subtracts
 // sum_{lambda_t < -tau} lambda_t u_t u_t^T from its Hessian blocks
-template <typename HT>
-__global__ void __launch_bounds__(kClampThreads)
+template <typename HT, int NT>
+__global__ void __launch_bounds__(NT)
 k_clamp(ElemLaunch L)
 {
-    __shared__ double Xs[81 * kClampThreads];
-    const SmemMat X{Xs + threadIdx.x, kClampThreads};
+    extern __shared__ __align__(16) double Xs[];   // [81][NT]
+    const SmemMat X{Xs + threadIdx.x, NT};
     const int count = min(*L.clamp_count, L.clamp_cap);
     // every thread of a block takes the same number of trips
     const int64_t span = (int64_t)gridDim.x * blockDim.x;
@@ -641,24 +645,34 @@ cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
     // length exit at once. Short-lived blocks let work of higher-priority
     // streams (the serving lanes of small scenes) in between.
     const int cgrid = L.clamp_grid > 0 ? L.clamp_grid : 1;
-    // sharing: unused dynamic shared memory lowers the resident blocks per
-    // SM from 4 (register limit) to 3, keeping a quarter of the registers free
-    const int pad = L.share_sms ? kClampSharePad : 0;
-    if (pad) {
-        static std::atomic<unsigned long long> attr_done{0};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
-        if (!bit || !(attr_done.load(std::memory_order_acquire) & bit)) {
-            cudaFuncSetAttribute(k_clamp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, pad);
-            cudaFuncSetAttribute(k_clamp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, pad);
-            attr_done.fetch_or(bit, std::memory_order_release);
-        }
+    const int nt = (L.clamp_threads == 32 || L.clamp_threads == 128) ? L.clamp_threads : 64;
+    // sharing: unused dynamic shared memory lowers the resident 64-thread
+    // blocks per SM from 4 (register limit) to 3, keeping a quarter of the
+    // registers free
+    const int smem = 81 * 8 * nt + ((L.share_sms && nt == 64) ? kClampSharePad : 0);
+    static std::atomic<unsigned long long> attr_done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (!bit || !(attr_done.load(std::memory_order_acquire) & bit)) {
+        const void* fns[] = {(const void*)k_clamp<float, 32>, (const void*)k_clamp<float, 64>,
+                             (const void*)k_clamp<float, 128>, (const void*)k_clamp<double, 32>,
+                             (const void*)k_clamp<double, 64>, (const void*)k_clamp<double, 128>};
+        for (const void* f : fns)
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kClampMaxSmem);
+        attr_done.fetch_or(bit, std::memory_order_release);
     }
-    if (L.precision == SX_FP32)
-        k_clamp<float><<<cgrid, kClampThreads, pad, s>>>(L);
-    else
-        k_clamp<double><<<cgrid, kClampThreads, pad, s>>>(L);
+    const bool f32 = L.precision == SX_FP32;
+    if (nt == 32) {
+        if (f32) k_clamp<float, 32><<<cgrid, 32, smem, s>>>(L);
+        else k_clamp<double, 32><<<cgrid, 32, smem, s>>>(L);
+    } else if (nt == 128) {
+        if (f32) k_clamp<float, 128><<<cgrid, 128, smem, s>>>(L);
+        else k_clamp<double, 128><<<cgrid, 128, smem, s>>>(L);
+    } else {
+        if (f32) k_clamp<float, 64><<<cgrid, 64, smem, s>>>(L);
+        else k_clamp<double, 64><<<cgrid, 64, smem, s>>>(L);
+    }
     return cudaGetLastError();
 }
 

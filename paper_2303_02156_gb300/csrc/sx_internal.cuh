@@ -170,6 +170,7 @@ struct ElemLaunch {
     int* clamp_failed;
     int clamp_cap;
     int clamp_grid;
+    int clamp_threads;    // projection block size: 32, 64 (default) or 128
     int share_sms;        // leave one projection block per SM for other work
 };
 cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s);

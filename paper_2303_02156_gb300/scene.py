@@ -48,6 +48,16 @@ class Context:
         self.check(rc)
         return np.array(E[:]) if want_energy else None
 
+    def autotune(self, scenes, precision=sx.SX_FP64, stream=0):
+        """Pick the fastest launch shape for this batch (sx_autotune)."""
+        arr = (C.c_void_p * len(scenes))(*[s.h.value for s in scenes])
+        rep = sx.sx_tune_report()
+        self.check(sx.sx_autotune(self.h, arr, len(scenes), precision, C.byref(rep), stream))
+        return {k: getattr(rep, k) for k, _ in sx.sx_tune_report._fields_}
+
+    def set_launch_shape(self, precision, clamp_threads, elem_blocks_per_sm):
+        self.check(sx.sx_set_launch_shape(self.h, precision, clamp_threads, elem_blocks_per_sm))
+
     def newton_step_batch(self, scenes, dt, stream=0, raise_on_error=True, **opts):
         arr = (C.c_void_p * len(scenes))(*[s.h.value for s in scenes])
         reps = (sx.sx_step_report * len(scenes))()

@@ -37,6 +37,7 @@ EXPORTS = [
     "sx_newton_step", "sx_newton_step_batch", "sx_scene_footprint", "sx_scene_bytes",
     "sx_copy_bsr", "sx_copy_grad", "sx_scene_info", "sx_block_info", "sx_eval_stats",
     "sx_profile", "sx_profile_read", "sx_eval_elements_noalloc",
+    "sx_autotune", "sx_set_launch_shape", "sx_get_launch_shape",
     "sx_server_create", "sx_server_set_lanes", "sx_server_submit", "sx_server_poll", "sx_server_result",
     "sx_server_drain", "sx_server_stats", "sx_server_destroy",
 ]
@@ -78,6 +79,11 @@ class sx_completion(C.Structure):
                 ("n_tets", C.c_int64), ("submit_ms", C.c_double), ("admit_ms", C.c_double),
                 ("done_ms", C.c_double), ("mean_step_ms", C.c_double),
                 ("error", C.c_char * 120)]
+
+
+class sx_tune_report(C.Structure):
+    _fields_ = [("clamp_threads", C.c_int), ("elem_blocks_per_sm", C.c_int),
+                ("default_ms", C.c_double), ("tuned_ms", C.c_double), ("candidates", C.c_int)]
 
 
 class sx_serve_stats(C.Structure):
@@ -133,6 +139,9 @@ _SIGS = {
     "sx_profile_read": (_I, [_P, C.POINTER(_D), C.POINTER(_I64), _I]),
     "sx_eval_elements_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
     "sx_server_create": (_I, [_P, _I64, C.POINTER(sx_newton_opts), _PP]),
+    "sx_autotune": (_I, [_P, C.POINTER(_P), _I, _I, C.POINTER(sx_tune_report), _P]),
+    "sx_set_launch_shape": (_I, [_P, _I, _I, _I]),
+    "sx_get_launch_shape": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I)]),
     "sx_server_set_lanes": (_I, [_P, _I, C.POINTER(_I64)]),
     "sx_server_submit": (_I, [_P, C.POINTER(sx_snh_scene_spec), _I, _D, C.POINTER(_I64)]),
     "sx_server_poll": (_I, [_P, C.POINTER(sx_completion), _I, C.POINTER(_I)]),

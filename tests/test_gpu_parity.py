@@ -425,3 +425,29 @@ def test_pcg_graph_replay_matches_plain_launches(ctx, precision):
         assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     for s, _ in sc:
         s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [sx.SX_FP64, sx.SX_FP32])
+def test_launch_shapes_are_bit_identical_and_autotune(ctx, precision):
+    """Every projection block size and element grid computes the same bits;
+    the autotuner picks one of them and leaves the result unchanged."""
+    m, E, nu, x, snh, mass = _snh_case(dims=(9, 8, 7), seed=4)
+    s, eid = _gpu_snh_scene(ctx, m, E, nu, x)
+    ref = None
+    for ct in (32, 64, 128):
+        for bps in (0, 1, 2):
+            ctx.set_launch_shape(precision, ct, bps)
+            s.eval(sx.SX_EGH, True, precision)
+            out = (s.bsr()[2].copy(), s.grad())
+            if ref is None:
+                ref = out
+            else:
+                assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), (ct, bps)
+    rep = ctx.autotune([s], precision)
+    assert rep["clamp_threads"] in (32, 64, 128) and rep["candidates"] >= 3
+    assert 0 < rep["tuned_ms"] <= rep["default_ms"]
+    s.eval(sx.SX_EGH, True, precision)
+    assert np.array_equal(s.bsr()[2], ref[0]) and np.array_equal(s.grad(), ref[1])
+    ctx.set_launch_shape(precision, 64, 8)   # back to the default (capped at what fits)
+    s.close()
