@@ -320,8 +320,8 @@ int sx_profile_read(sx_ctx* ctx, double* ms, int64_t* launches, int reset);
 
 /* ---- launch shapes and the autotuner -----------------------------------
  * (No counterpart in the paper: these pick GPU launch configurations.)
- * Per context and precision: the projection kernel's block size (32, 64 or
- * 128 threads; default 64) and the element kernel's grid (blocks per SM of
+ * Per context and precision: the projection kernel's block size (32, 64,
+ * 128 or 256 threads; default 128) and the element kernel's grid (blocks per SM of
  * the persistent launch, at most what fits -- the default; 0 = one 128-
  * element tile per block). Every shape computes bit-identical results. */
 typedef struct {

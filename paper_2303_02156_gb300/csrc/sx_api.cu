@@ -62,7 +62,7 @@ struct sx_ctx {
     // launch shapes per precision (sx_autotune / sx_set_launch_shape):
     // projection block size, and element-kernel blocks per SM of the
     // persistent grid (0: one tile per block)
-    int clamp_threads[2] = {64, 64};
+    int clamp_threads[2] = {128, 128};
     int elem_bps[2] = {1, 1};
     std::string err;
     int* queue = nullptr;
@@ -1682,7 +1682,8 @@ int sx_scene_bytes(sx_scene* s, int64_t* bytes)
 int sx_set_launch_shape(sx_ctx* ctx, int precision, int clamp_threads, int elem_blocks_per_sm)
 {
     if (!ctx || (precision != SX_FP64 && precision != SX_FP32) ||
-        (clamp_threads != 32 && clamp_threads != 64 && clamp_threads != 128) ||
+        (clamp_threads != 32 && clamp_threads != 64 && clamp_threads != 128 &&
+         clamp_threads != 256) ||
         elem_blocks_per_sm < 0)
         return SX_EINVAL;
     const int p = precision == SX_FP32 ? 1 : 0;
@@ -1738,11 +1739,11 @@ int sx_autotune(sx_ctx* ctx, sx_scene* const* scenes, int n, int precision,
         return SX_OK;
     };
     const int occ = ctx->elem_blocks_per_sm[p];
-    int best_ct = 64, best_bps = occ;
+    int best_ct = 128, best_bps = occ;
     double def_ms = 0.0, best_ms = 0.0, ms = 0.0;
     int rc = timed(best_ct, best_bps, &def_ms);
     best_ms = def_ms;
-    for (int ct : {32, 128}) {
+    for (int ct : {32, 64, 256}) {
         if (rc != SX_OK) break;
         rc = timed(ct, best_bps, &ms);
         if (rc == SX_OK && ms < best_ms) {

@@ -36,14 +36,19 @@
 namespace sx {
 
 static constexpr int kElemThreads = 128;
-// projection block sizes the launch may use (picked by sx_autotune; 64 by
-// default); each thread keeps its 9x9 eigenvector matrix (648 B) in dynamic
-// shared memory
+// projection block sizes the launch may use: 32, 64, 128 (the default) or
+// 256, picked by sx_autotune; each thread keeps its 9x9 eigenvector matrix
+// (648 B) in dynamic shared memory
 static constexpr int kClampThreads = 64;
-// sharing (64-thread blocks): 41.5 KB of eigenvectors + 17 KB unused makes
-// 58.5 KB, so at most 3 blocks share an SM's 228 KB
-static constexpr int kClampSharePad = 17 * 1024;
-static constexpr int kClampMaxSmem = 81 * 8 * 128 + kClampSharePad;
+// sharing: unused dynamic shared memory per block that lowers the resident
+// blocks per SM by one (from the register limit of 255-register threads):
+// 32 threads 20.3 + 8 KB (8 -> 7), 64 threads 40.5 + 17 KB (4 -> 3),
+// 128 threads 81 + 32 KB (2 -> 1); 256-thread blocks are alone on an SM
+__host__ __device__ constexpr int clamp_share_pad(int nt)
+{
+    return nt == 32 ? 8 * 1024 : nt == 64 ? 17 * 1024 : nt == 128 ? 32 * 1024 : 0;
+}
+static constexpr int kClampMaxSmem = 81 * 8 * 256;
 
 int elements_block_threads() { return kElemThreads; }
 int clamp_block_threads() { return kClampThreads; }
@@ -645,19 +650,19 @@ cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
     // length exit at once. Short-lived blocks let work of higher-priority
     // streams (the serving lanes of small scenes) in between.
     const int cgrid = L.clamp_grid > 0 ? L.clamp_grid : 1;
-    const int nt = (L.clamp_threads == 32 || L.clamp_threads == 128) ? L.clamp_threads : 64;
-    // sharing: unused dynamic shared memory lowers the resident 64-thread
-    // blocks per SM from 4 (register limit) to 3, keeping a quarter of the
-    // registers free
-    const int smem = 81 * 8 * nt + ((L.share_sms && nt == 64) ? kClampSharePad : 0);
+    const int nt = (L.clamp_threads == 32 || L.clamp_threads == 128 || L.clamp_threads == 256)
+                       ? L.clamp_threads
+                       : 64;
+    const int smem = 81 * 8 * nt + (L.share_sms ? clamp_share_pad(nt) : 0);
     static std::atomic<unsigned long long> attr_done{0};
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
     if (!bit || !(attr_done.load(std::memory_order_acquire) & bit)) {
         const void* fns[] = {(const void*)k_clamp<float, 32>, (const void*)k_clamp<float, 64>,
-                             (const void*)k_clamp<float, 128>, (const void*)k_clamp<double, 32>,
-                             (const void*)k_clamp<double, 64>, (const void*)k_clamp<double, 128>};
+                             (const void*)k_clamp<float, 128>, (const void*)k_clamp<float, 256>,
+                             (const void*)k_clamp<double, 32>, (const void*)k_clamp<double, 64>,
+                             (const void*)k_clamp<double, 128>, (const void*)k_clamp<double, 256>};
         for (const void* f : fns)
             cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kClampMaxSmem);
         attr_done.fetch_or(bit, std::memory_order_release);
@@ -669,6 +674,9 @@ cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
     } else if (nt == 128) {
         if (f32) k_clamp<float, 128><<<cgrid, 128, smem, s>>>(L);
         else k_clamp<double, 128><<<cgrid, 128, smem, s>>>(L);
+    } else if (nt == 256) {
+        if (f32) k_clamp<float, 256><<<cgrid, 256, smem, s>>>(L);
+        else k_clamp<double, 256><<<cgrid, 256, smem, s>>>(L);
     } else {
         if (f32) k_clamp<float, 64><<<cgrid, 64, smem, s>>>(L);
         else k_clamp<double, 64><<<cgrid, 64, smem, s>>>(L);

@@ -435,7 +435,7 @@ def test_launch_shapes_are_bit_identical_and_autotune(ctx, precision):
     m, E, nu, x, snh, mass = _snh_case(dims=(9, 8, 7), seed=4)
     s, eid = _gpu_snh_scene(ctx, m, E, nu, x)
     ref = None
-    for ct in (32, 64, 128):
+    for ct in (32, 64, 128, 256):
         for bps in (0, 1, 2):
             ctx.set_launch_shape(precision, ct, bps)
             s.eval(sx.SX_EGH, True, precision)
@@ -445,9 +445,9 @@ def test_launch_shapes_are_bit_identical_and_autotune(ctx, precision):
             else:
                 assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), (ct, bps)
     rep = ctx.autotune([s], precision)
-    assert rep["clamp_threads"] in (32, 64, 128) and rep["candidates"] >= 3
+    assert rep["clamp_threads"] in (32, 64, 128, 256) and rep["candidates"] >= 3
     assert 0 < rep["tuned_ms"] <= rep["default_ms"]
     s.eval(sx.SX_EGH, True, precision)
     assert np.array_equal(s.bsr()[2], ref[0]) and np.array_equal(s.grad(), ref[1])
-    ctx.set_launch_shape(precision, 64, 8)   # back to the default (capped at what fits)
+    ctx.set_launch_shape(precision, 128, 8)   # back to the default (capped at what fits)
     s.close()
