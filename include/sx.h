@@ -321,12 +321,13 @@ int sx_profile_read(sx_ctx* ctx, double* ms, int64_t* launches, int reset);
 /* ---- launch shapes and the autotuner -----------------------------------
  * (No counterpart in the paper: these pick GPU launch configurations.)
  * Per context and precision: the projection kernel's block size (32, 64,
- * 128 or 256 threads; default 128) and the element kernel's grid (blocks per SM of
- * the persistent launch, at most what fits -- the default; 0 = one 128-
- * element tile per block). Every shape computes bit-identical results. */
+ * 128 or 256 threads; default 128) and the element kernel's grid (-1: a
+ * persistent launch with as many blocks per SM as fit -- the default;
+ * k >= 1: k blocks per SM, capped at what fits; 0: one 128-element tile per
+ * block). Every shape computes bit-identical results. */
 typedef struct {
     int clamp_threads;        /* chosen projection block size */
-    int elem_blocks_per_sm;   /* chosen element grid (0 = one tile per block) */
+    int elem_blocks_per_sm;   /* chosen element grid (-1, k >= 1 or 0, as above) */
     double default_ms;        /* one E+g+projected H+assembly pass, default shape */
     double tuned_ms;          /* the same pass with the chosen shape */
     int candidates;           /* shapes timed */
@@ -339,8 +340,8 @@ typedef struct {
  * context). Overwrites the scenes' assembled outputs. Synchronous. */
 int sx_autotune(sx_ctx* ctx, sx_scene* const* scenes, int n, int precision,
                 sx_tune_report* report, void* stream);
-/* Sets / reads a shape directly (SX_EINVAL for an unsupported block size;
- * the element grid is capped at what fits). */
+/* Sets / reads a shape directly (SX_EINVAL for an unsupported block size
+ * or an element grid below -1). */
 int sx_set_launch_shape(sx_ctx* ctx, int precision, int clamp_threads, int elem_blocks_per_sm);
 int sx_get_launch_shape(sx_ctx* ctx, int precision, int* clamp_threads, int* elem_blocks_per_sm);
 

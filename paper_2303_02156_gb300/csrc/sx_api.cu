@@ -57,13 +57,14 @@ struct sx_ctx {
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[SX_PH_COUNT] = {0};
     int64_t prof_launches[SX_PH_COUNT] = {0};
-    int elem_blocks_per_sm[2] = {1, 1};   // occupancy limit of the element kernel
+    // occupancy limit of the element kernel [precision][all kinds, SNH only]
+    int elem_occ[2][2] = {{1, 1}, {1, 1}};
     bool share_sms = false;
     // launch shapes per precision (sx_autotune / sx_set_launch_shape):
     // projection block size, and element-kernel blocks per SM of the
     // persistent grid (0: one tile per block)
     int clamp_threads[2] = {128, 128};
-    int elem_bps[2] = {1, 1};
+    int elem_bps[2] = {-1, -1};   // -1: as many as fit; 0: one tile per block
     std::string err;
     int* queue = nullptr;
     // pinned host staging of per-scene scalars and controls, shared by the
@@ -163,6 +164,7 @@ struct Batch {
     Tile* d_row_c = nullptr;
     int *d_nb_c = nullptr, *d_ne_c = nullptr, *d_rb_c = nullptr, *d_re_c = nullptr;
     int64_t clamp_need = 0;          // projectable stencils of the batch
+    int kinds = 0;                   // stencil kinds present (bit mask)
     // the PCG chunk (8 iterations) as an instantiated graph, per precision,
     // with the tolerance and cap it was built with
     cudaGraphExec_t pcg_graph[2] = {nullptr, nullptr};
@@ -193,13 +195,20 @@ int clamp_grid_for(int64_t max_queued, int threads)
     return (int)std::max<int64_t>(1, std::min<int64_t>((max_queued + t - 1) / t, INT32_MAX));
 }
 
-// element-kernel grid for `ntiles` tiles under the context's launch shape
-int elem_grid(const sx_ctx* ctx, int precision, int ntiles)
+// element-kernel grid for `ntiles` tiles of the given kinds under the
+// context's launch shape
+int elem_grid(const sx_ctx* ctx, int precision, int kinds, int ntiles)
 {
     const int p = precision == SX_FP32 ? 1 : 0;
-    const int bps = ctx->elem_bps[p];
-    const int g = bps <= 0 ? ntiles : std::min<int>(ntiles, ctx->sm_count * bps);
+    const int occ = ctx->elem_occ[p][kinds == 1 ? 1 : 0];
+    const int bps = ctx->elem_bps[p] < 0 ? occ : std::min(ctx->elem_bps[p], occ);
+    const int g = bps == 0 ? ntiles : std::min<int>(ntiles, ctx->sm_count * bps);
     return std::max(g, 1);
+}
+
+int kind_bit(int kind)
+{
+    return kind == SX_KIND_SNH_TET4 ? 1 : kind == SX_KIND_HINGE4 ? 2 : 4;
 }
 
 int fail(sx_ctx* c, int code, const std::string& msg)
@@ -417,9 +426,13 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         CK(cudaMallocAsync((void**)&B->d_ctl_i, n * sizeof(int), st));
         CK(cudaMallocAsync((void**)&B->d_ctl_d, n * sizeof(double), st));
         int64_t cap = 0;
+        B->kinds = 0;
         for (sx_scene* s : B->scenes)
-            for (auto& b : s->blocks)
+            for (auto& b : s->blocks) {
                 if (b.kind != SX_KIND_HINGE4) cap += b.n;
+                if (b.n) B->kinds |= kind_bit(b.kind);
+            }
+        if (!B->kinds) B->kinds = 1;
         B->clamp_need = std::max<int64_t>(cap, 1);
         CK(cudaMallocAsync((void**)&B->d_desc, n * sizeof(SceneDev), st));
         CK(cudaMallocAsync((void**)&B->d_desc_trial, n * sizeof(SceneDev), st));
@@ -624,7 +637,8 @@ int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool 
     L.clamp_threads = ctx->clamp_threads[pidx];
     L.clamp_grid = clamp_grid_for(B->clamp_need, L.clamp_threads);
     L.share_sms = ctx->share_sms;
-    const int grid = elem_grid(ctx, precision, L.ntiles);
+    L.kinds = B->kinds;
+    const int grid = elem_grid(ctx, precision, L.kinds, L.ntiles);
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (level >= 2 && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_elem, 1, 0, B->d_elem_beg, B->d_elem_end,
@@ -749,14 +763,14 @@ int sx_create(sx_ctx** out, const sx_options* opt)
         return SX_ECUDA;
     }
     ctx->share_sms = opt && opt->share_sms;
-    for (int p = 0; p < 2; ++p) {
-        int nb = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elements_kernel(p),
-                                                      elements_block_threads(), 0);
-        // sharing: the persistent element grid holds one block per SM less
-        ctx->elem_blocks_per_sm[p] = std::max(ctx->share_sms ? nb - 1 : nb, 1);
-        ctx->elem_bps[p] = ctx->elem_blocks_per_sm[p];
-    }
+    for (int p = 0; p < 2; ++p)
+        for (int v = 0; v < 2; ++v) {
+            int nb = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elements_kernel(p, v),
+                                                          elements_block_threads(), 0);
+            // sharing: the persistent element grid holds one block per SM less
+            ctx->elem_occ[p][v] = std::max(ctx->share_sms ? nb - 1 : nb, 1);
+        }
     {
         // keep released pool memory mapped and cached for the next
         // stream-ordered allocation (scenes and batches come and go)
@@ -1310,7 +1324,8 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     L.clamp_threads = ctx->clamp_threads[precision == SX_FP32 ? 1 : 0];
     L.clamp_grid = clamp_grid_for(L.clamp_cap, L.clamp_threads);
     L.share_sms = ctx->share_sms;
-    PL(SX_PH_ELEMENTS, 1, launch_elements(L, elem_grid(ctx, precision, L.ntiles), st));
+    L.kinds = kind_bit(b.kind);
+    PL(SX_PH_ELEMENTS, 1, launch_elements(L, elem_grid(ctx, precision, L.kinds, L.ntiles), st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     int qfail[2] = {0, 0};
     if (qC) CK(cudaMemcpyAsync(qfail, qC, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1684,11 +1699,11 @@ int sx_set_launch_shape(sx_ctx* ctx, int precision, int clamp_threads, int elem_
     if (!ctx || (precision != SX_FP64 && precision != SX_FP32) ||
         (clamp_threads != 32 && clamp_threads != 64 && clamp_threads != 128 &&
          clamp_threads != 256) ||
-        elem_blocks_per_sm < 0)
+        elem_blocks_per_sm < -1)
         return SX_EINVAL;
     const int p = precision == SX_FP32 ? 1 : 0;
     ctx->clamp_threads[p] = clamp_threads;
-    ctx->elem_bps[p] = std::min(elem_blocks_per_sm, ctx->elem_blocks_per_sm[p]);
+    ctx->elem_bps[p] = elem_blocks_per_sm;   // capped at what fits when launched
     return SX_OK;
 }
 
@@ -1738,8 +1753,7 @@ int sx_autotune(sx_ctx* ctx, sx_scene* const* scenes, int n, int precision,
         *ms = best;
         return SX_OK;
     };
-    const int occ = ctx->elem_blocks_per_sm[p];
-    int best_ct = 128, best_bps = occ;
+    int best_ct = 128, best_bps = -1;
     double def_ms = 0.0, best_ms = 0.0, ms = 0.0;
     int rc = timed(best_ct, best_bps, &def_ms);
     best_ms = def_ms;
@@ -1751,9 +1765,10 @@ int sx_autotune(sx_ctx* ctx, sx_scene* const* scenes, int n, int precision,
             best_ct = ct;
         }
     }
-    for (int bps : {occ - 1, 0}) {
-        if (rc != SX_OK || bps < 0 || (bps == 0 && occ == 0)) continue;
-        if (bps == occ - 1 && bps < 1) continue;
+    // element grid: as many blocks as fit (default), one per SM, one tile
+    // per block
+    for (int bps : {1, 0}) {
+        if (rc != SX_OK) break;
         rc = timed(best_ct, bps, &ms);
         if (rc == SX_OK && ms < best_ms) {
             best_ms = ms;
@@ -1885,7 +1900,8 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
     L.clamp_threads = ctx->clamp_threads[precision == SX_FP32 ? 1 : 0];
     L.clamp_grid = clamp_grid_for(L.clamp_cap, L.clamp_threads);
     L.share_sms = ctx->share_sms;
-    const int grid = elem_grid(ctx, precision, nt);
+    L.kinds = kind_bit(b.kind);
+    const int grid = elem_grid(ctx, precision, L.kinds, nt);
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     int failed = 0;

@@ -121,6 +121,55 @@ __device__ __forceinline__ bool psd_by_ldlt(const double (&M)[45])
     return pd;
 }
 
+// Phase 1 pre-test in float, with a margin delta = 1e-4 ||M||_F that covers
+// the backward error of a float LDL^T of a 9x9 (about 9 * 2^-24 times a
+// small constant, relative to ||M||): LDL^T of M - delta I succeeding
+// proves M positive definite (+1); LDL^T of M + delta I failing proves an
+// eigenvalue below -delta/2 (-1). Both decide as the double test would;
+// 0 leaves the decision to it.
+__device__ __forceinline__ bool ldlt_f32_pd(const float (&A)[45], float shift)
+{
+    float L[45];
+    float dg[9];
+    bool pd = true;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        float s = A[pk(j, j)] + shift;
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= L[pk(j, k)] * L[pk(j, k)] * dg[k];
+        pd = pd && (s > 0.0f);
+        dg[j] = s;
+        const float inv = 1.0f / s;
+#pragma unroll
+        for (int i = j + 1; i < 9; ++i) {
+            float t = A[pk(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= L[pk(i, k)] * L[pk(j, k)] * dg[k];
+            L[pk(i, j)] = t * inv;
+        }
+    }
+    return pd;
+}
+
+__device__ __forceinline__ int psd_class_f32(const double (&M)[45])
+{
+    float A[45];
+    float f2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            const float v = (float)M[pk(i, j)];
+            A[pk(i, j)] = v;
+            f2 = fmaf((i == j ? 1.0f : 2.0f) * v, v, f2);
+        }
+    const float delta = 1e-4f * sqrtf(f2);
+    if (!(delta > 0.0f) || !isfinite(delta)) return 0;
+    if (ldlt_f32_pd(A, -delta)) return 1;
+    if (!ldlt_f32_pd(A, delta)) return -1;
+    return 0;
+}
+
 // ---------------------------------------------------------------- phase 2
 // Cyclic Jacobi (symmetric Schur rotations, Golub & Van Loan 8.5) on the
 // packed 9x9 A with the rotations accumulated into X (row-major, column c =

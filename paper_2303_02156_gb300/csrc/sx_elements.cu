@@ -295,7 +295,8 @@ __device__ __forceinline__ void write_blocks(BlockFn blockfn, HT* staged, double
 __device__ __forceinline__ bool queue_if_indefinite(const ElemLaunch& L, int scene, int blk,
                                                     int64_t e, const double (&M)[45])
 {
-    if (psd_by_ldlt(M)) return false;
+    const int cls = psd_class_f32(M);
+    if (cls > 0 || (cls == 0 && psd_by_ldlt(M))) return false;
     const int slot = atomicAdd(L.clamp_count, 1);
     if (slot >= L.clamp_cap) return false;   // cannot happen: capacity = stencils
     double* dst = L.clamp_M + 45 * (int64_t)slot;
@@ -492,7 +493,10 @@ __device__ void eval_barrier(const ElemLaunch& L, int scene, int blk, const Scen
     }
 }
 
-template <typename R, typename HT>
+// KINDS: bit mask of the stencil kinds compiled in (1 SNH, 2 hinge, 4
+// barrier). A batch with SNH tets only runs the SNH-only instantiation,
+// which needs fewer registers than the one that can take every kind.
+template <typename R, typename HT, int KINDS>
 __global__ void __launch_bounds__(kElemThreads)
 k_elements(ElemLaunch L)
 {
@@ -512,11 +516,11 @@ k_elements(ElemLaunch L)
             const ElemBlock& B = S.blk[T.blk];
             if ((int)threadIdx.x < T.count) {
                 const int64_t e = T.start + threadIdx.x;
-                if (B.kind == SX_KIND_SNH_TET4)
+                if ((KINDS & 1) && B.kind == SX_KIND_SNH_TET4)
                     eval_snh<R, HT>(L, T.scene, T.blk, S, B, e, o);
-                else if (B.kind == SX_KIND_HINGE4)
+                else if ((KINDS & 2) && B.kind == SX_KIND_HINGE4)
                     eval_hinge<R, HT>(L, S, B, e, o);
-                else
+                else if ((KINDS & 4) && B.kind == SX_KIND_PT_BARRIER)
                     eval_barrier<R, HT>(L, T.scene, T.blk, S, B, e, o);
                 if (L.out_E) L.out_E[e] = o.E;
                 else S.Ee[B.base + e] = o.E;
@@ -595,10 +599,13 @@ k_clamp(ElemLaunch L)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (i >= k || !(lam[i] < -tau)) continue;
-            double u[12];
+            double u[12], w[12];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
                 had_inv(X(r, i), X(3 + r, i), X(6 + r, i), u[r], u[3 + r], u[6 + r], u[9 + r]);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) w[q] = lam[i] * u[q];
+            // H -= (lambda u) u^T: one fused multiply-add per entry
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -607,23 +614,30 @@ k_clamp(ElemLaunch L)
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            const double v = lam[i] * u[3 * a + r] * u[3 * b + c];
+                            const double wr = w[3 * a + r], uc = u[3 * b + c];
                             if (staged) {
                                 HT* p = staged + 9 * up_index(a, b) + 3 * r + c;
-                                *p = (HT)((double)*p - v);
+                                *p = (HT)fma(-wr, uc, (double)*p);
                             } else {
-                                full[(3 * a + r) * 12 + 3 * b + c] -= v;
-                                if (a != b) full[(3 * b + c) * 12 + 3 * a + r] -= v;
+                                double* p = full + (3 * a + r) * 12 + 3 * b + c;
+                                *p = fma(-wr, uc, *p);
+                                if (a != b) {
+                                    double* q = full + (3 * b + c) * 12 + 3 * a + r;
+                                    *q = fma(-wr, uc, *q);
+                                }
                             }
                         }
         }
     }
 }
 
-const void* elements_kernel(int precision)
+const void* elements_kernel(int precision, int snh_only)
 {
-    return precision == SX_FP32 ? (const void*)k_elements<float, float>
-                                : (const void*)k_elements<double, double>;
+    if (snh_only)
+        return precision == SX_FP32 ? (const void*)k_elements<float, float, 1>
+                                    : (const void*)k_elements<double, double, 1>;
+    return precision == SX_FP32 ? (const void*)k_elements<float, float, 7>
+                                : (const void*)k_elements<double, double, 7>;
 }
 
 cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s)
@@ -635,10 +649,14 @@ cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s)
         err = cudaMemsetAsync(L.clamp_count, 0, sizeof(int), s);
         if (err != cudaSuccess) return err;
     }
-    if (L.precision == SX_FP32)
-        k_elements<float, float><<<grid, kElemThreads, 0, s>>>(L);
-    else
-        k_elements<double, double><<<grid, kElemThreads, 0, s>>>(L);
+    const bool snh_only = L.kinds == 1;
+    if (L.precision == SX_FP32) {
+        if (snh_only) k_elements<float, float, 1><<<grid, kElemThreads, 0, s>>>(L);
+        else k_elements<float, float, 7><<<grid, kElemThreads, 0, s>>>(L);
+    } else {
+        if (snh_only) k_elements<double, double, 1><<<grid, kElemThreads, 0, s>>>(L);
+        else k_elements<double, double, 7><<<grid, kElemThreads, 0, s>>>(L);
+    }
     return cudaGetLastError();
 }
 

@@ -170,14 +170,16 @@ struct ElemLaunch {
     int* clamp_failed;
     int clamp_cap;
     int clamp_grid;
-    int clamp_threads;    // projection block size: 32, 64 (default) or 128
+    int clamp_threads;    // projection block size: 32, 64, 128 (default) or 256
+    int kinds;            // stencil kinds present (1 SNH, 2 hinge, 4 barrier)
     int share_sms;        // leave one projection block per SM for other work
 };
 cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s);
 cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s);
 int elements_block_threads();
 int clamp_block_threads();
-const void* elements_kernel(int precision);
+// the element kernel for a precision; snh_only: the SNH-only instantiation
+const void* elements_kernel(int precision, int snh_only);
 
 // registration and pattern (sx_graph.cu)
 cudaError_t launch_snh_rest(const double* X, int64_t N, const int4* tets, int64_t n,

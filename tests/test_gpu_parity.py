@@ -436,7 +436,7 @@ def test_launch_shapes_are_bit_identical_and_autotune(ctx, precision):
     s, eid = _gpu_snh_scene(ctx, m, E, nu, x)
     ref = None
     for ct in (32, 64, 128, 256):
-        for bps in (0, 1, 2):
+        for bps in (-1, 0, 1, 2):
             ctx.set_launch_shape(precision, ct, bps)
             s.eval(sx.SX_EGH, True, precision)
             out = (s.bsr()[2].copy(), s.grad())
@@ -449,5 +449,5 @@ def test_launch_shapes_are_bit_identical_and_autotune(ctx, precision):
     assert 0 < rep["tuned_ms"] <= rep["default_ms"]
     s.eval(sx.SX_EGH, True, precision)
     assert np.array_equal(s.bsr()[2], ref[0]) and np.array_equal(s.grad(), ref[1])
-    ctx.set_launch_shape(precision, 128, 8)   # back to the default (capped at what fits)
+    ctx.set_launch_shape(precision, 128, -1)   # back to the default
     s.close()
