@@ -451,3 +451,147 @@ def test_launch_shapes_are_bit_identical_and_autotune(ctx, precision):
     assert np.array_equal(s.bsr()[2], ref[0]) and np.array_equal(s.grad(), ref[1])
     ctx.set_launch_shape(precision, 128, -1)   # back to the default
     s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [sx.SX_FP64, sx.SX_FP32])
+def test_projection_parity_strongly_deformed(ctx, precision):
+    """Large node jitter (some tets inverted, J < 0): many stencils with
+    several negative eigenvalues go through the projection."""
+    m, E, nu, x, snh, mass = _snh_case(dims=(6, 5, 4), seed=21, jitter=0.45)
+    s, eid = _gpu_snh_scene(ctx, m, E, nu, x)
+    out = s.eval_elements(eid, project=True, precision=precision)
+    Ee, ge, He = orc.snh_batch(x, snh["tets"], snh["Dminv"], snh["V"], snh["mu"], snh["lam"],
+                               2, True)
+    # the state has inverted tets and strongly indefinite Hessians
+    F_dets = []
+    for e in range(snh["tets"].shape[0]):
+        Ds = (x[snh["tets"][e, 1:]] - x[snh["tets"][e, 0]]).T
+        F_dets.append(np.linalg.det(Ds @ snh["Dminv"][e].reshape(3, 3)))
+    assert min(F_dets) < 0
+    tol = TOL64 if precision == sx.SX_FP64 else TOL32
+    scale = snh["V"] * snh["mu"]
+    worst = 0.0
+    for e in range(Ee.size):
+        worst = max(worst, _relerr(out["H"][e], He[e], scale[e]))
+    assert worst <= tol, worst
+    w = np.linalg.eigvalsh(out["H"])
+    assert w.min() >= -(1e-9 if precision == sx.SX_FP64 else 1e-6) * np.abs(w).max()
+    s.close()
+
+
+def _mixed_small():
+    m = scenes.kuhn_box(3, 3, 2, h=0.01, seed=2)
+    nt = m["X"].shape[0]
+    sh = scenes.shell_sheet(6, length=0.03, z0=0.03, noise=0.05, seed=2, node_offset=nt)
+    ns = sh["x"].shape[0]
+    bp = scenes.barrier_pairs(sh["x"], sh["tris"] - nt, 40, 2e-4, 8e-4, seed=2,
+                              tri_node_offset=nt, point_node_offset=nt + ns)
+    X = np.vstack([m["X"], sh["X"], bp["points"]])
+    x0 = np.vstack([m["X"], sh["x"], bp["points"]])
+    T = m["tets"].shape[0]
+    E, nu = scenes.material_random(T, 2)
+    extra = np.zeros(X.shape[0])
+    extra[nt:nt + ns] = 1e-4
+    extra[nt + ns:] = 1e-3
+    return m, sh, bp, X, x0, E, nu, extra, nt
+
+
+@pytest.mark.gpu
+def test_newton_step_mixed_stencils_matches_oracle(ctx):
+    """One backward-Euler step of an SNH block + hinge sheet + barrier points
+    (line search keeps every barrier distance positive) against the oracle."""
+    from paper_2303_02156_gb300.scene import Scene
+    m, sh, bp, X, x0, E, nu, extra, nt = _mixed_small()
+    N = X.shape[0]
+    s = Scene(ctx, X)
+    s.add_snh(m["tets"], E, nu, 1000.0)
+    s.add_hinge(sh["hinges"], sh["q"], sh["c"], 1e-3)
+    s.add_barrier(bp["pairs"], 1e-3, 1e4)
+    s.add_node_mass(extra)
+    s.set_pinned(m["pinned"])
+    s.set_gravity((0.0, 0.0, -9.81))
+    s.finalize()
+    s.set_state(x=x0, v=np.zeros_like(x0))
+    rc, r = s.newton_step(0.01, newton_tol=1e-8, pcg_tol=1e-10)
+    assert rc == sx.SX_OK, r
+    x, v = s.get_state()
+    snh, mass, _ = orc.snh_scene_inputs(m["X"], m["tets"], E, nu, 1000.0)
+    mass_all = np.concatenate([mass, np.zeros(N - nt)]) + extra
+    sc = orc.Scene(N, mass=mass_all, snh=snh,
+                   hinge={"stencils": sh["hinges"], "q": sh["q"], "c": sh["c"], "kb": 1e-3},
+                   pt={"pairs": bp["pairs"], "dhat": 1e-3, "kappa": 1e4}, pinned=m["pinned"])
+    xo, vo, st, rep = sc.newton_step(x0, np.zeros_like(x0), 0.01)
+    assert st == 0
+    ref = np.abs(xo - x0).max()
+    assert np.abs(x - xo).max() <= 1e-8 * ref + 1e-12
+    s.close()
+
+
+@pytest.mark.gpu
+def test_newton_step_fp32_close_to_oracle(ctx):
+    """The FP32 form of a C1 step (FP64 projection, residual norms and
+    line-search energies) against the FP64 oracle: displacement error
+    within 1e-5 of the displacement at Newton tolerance 1e-6."""
+    from paper_2303_02156_gb300.scene import Scene
+    m, E, nu = _c1()
+    snh, mass, _ = orc.snh_scene_inputs(m["X"], m["tets"], E, nu, 1000.0)
+    sc = orc.Scene(m["X"].shape[0], mass=mass, snh=snh, pinned=m["pinned"])
+    xo, vo, st, rep = sc.newton_step(m["X"], np.zeros_like(m["X"]), 0.01)
+    assert st == 0
+    s = Scene(ctx, m["X"])
+    s.add_snh(m["tets"], E, nu, 1000.0)
+    s.set_pinned(m["pinned"])
+    s.set_gravity((0.0, 0.0, -9.81))
+    s.finalize()
+    rc, r = s.newton_step(0.01, newton_tol=1e-6, pcg_tol=1e-6, precision=sx.SX_FP32)
+    assert rc == sx.SX_OK
+    x, v = s.get_state()
+    assert np.abs(x - xo).max() <= 1e-5 * np.abs(xo - m["X"]).max()
+    s.close()
+
+
+@pytest.mark.gpu
+def test_all_pinned_scene_does_not_move(ctx):
+    from paper_2303_02156_gb300.scene import Scene
+    m = scenes.kuhn_box(2, 2, 2, h=0.5, seed=4)
+    s = Scene(ctx, m["X"])
+    s.add_snh(m["tets"], 1e5, 0.3, 1000.0)
+    s.set_pinned(np.arange(m["X"].shape[0]))
+    s.set_gravity((0.0, 0.0, -9.81))
+    s.finalize()
+    rc, r = s.newton_step(0.01)
+    assert rc == sx.SX_OK
+    x, v = s.get_state()
+    assert np.array_equal(x, m["X"]) and not v.any()
+    s.close()
+
+
+@pytest.mark.gpu
+def test_api_misuse_returns_status_codes(ctx):
+    import ctypes as C
+    from paper_2303_02156_gb300.scene import Scene
+    m = scenes.two_tet()
+    s = Scene(ctx, m["X"])
+    s.add_snh(m["tets"], 1e5, 0.3, 1000.0)
+    # evaluation and stepping need a finalized scene
+    rc, _ = s.eval(sx.SX_EGH, True, sx.SX_FP64, check=False)
+    assert rc == sx.SX_EORDER
+    rc, _ = s.newton_step(0.01, raise_on_error=False)
+    assert rc == sx.SX_EORDER
+    # node ids out of range, bad level, bad dt
+    with pytest.raises(sx.SxError) as ei:
+        s.add_barrier(np.array([[0, 1, 2, 7]]), 1e-3, 1e4)
+        s.finalize()
+    assert ei.value.code == sx.SX_EINVAL
+    s.close()
+    s = Scene(ctx, m["X"])
+    s.add_snh(m["tets"], 1e5, 0.3, 1000.0)
+    s.finalize()
+    assert sx.sx_eval(s.h, 7, 1, sx.SX_FP64, None, None) == sx.SX_EINVAL
+    o = sx.newton_opts()
+    assert sx.sx_newton_step(s.h, 0.0, C.byref(o), None, None) == sx.SX_EINVAL
+    h = C.c_void_p()
+    X = np.zeros((0, 3))
+    assert sx.sx_scene_create(ctx.h, 0, X.ctypes.data, 3, None, C.byref(h)) == sx.SX_EINVAL
+    s.close()
