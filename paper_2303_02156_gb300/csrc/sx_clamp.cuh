@@ -25,7 +25,9 @@
 //      FP32 one (its entries carry ~6e-8 relative rounding, which also
 //      spreads its exactly-zero eigenvalues over ~1e-7 ||M||, and the
 //      result is stored in float). Eigenvalues of the N block below -tau
-//      are clamped.
+//      are clamped: M' = M - sum of lambda v v^T over them, and the
+//      stencil's Hessian is rewritten as (Hd kron I3) diag(0, M')
+//      (Hd kron I3)^T.
 //   Accuracy: clamping at zero is 1-Lipschitz in the Frobenius norm on
 //   symmetric matrices, so the projection is off by at most about twice the
 //   Frobenius norm of the N-N and N-P off-diagonal entries left in At

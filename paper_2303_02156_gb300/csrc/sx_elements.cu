@@ -596,37 +596,61 @@ k_clamp(ElemLaunch L)
         const ElemBlock& B = S.blk[ref.blk];
         HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (B.base + ref.e);
         double* full = L.out_H ? L.out_H + 144 * ref.e : nullptr;
+        // M' = M - sum of lambda v v^T over the N-block eigenvalues below -tau
+        // (v in the Hadamard basis), then H' = (Hd kron I3) diag(0, M')
+        // (Hd kron I3)^T written once: no read of the staged H, one store per
+        // entry whatever the number of negative eigenvalues. (The element H
+        // has the three translations as an exact null space up to rounding,
+        // so H' differs from H - sum lambda u u^T only by rounding.)
+        bool any_neg = false;
+        double Mp[45];
+#pragma unroll
+        for (int q = 0; q < 45; ++q) Mp[q] = __ldg(Mg + q);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            if (i >= k || !(lam[i] < -tau)) continue;
-            double u[12], w[12];
+            const bool neg = i < k && lam[i] < -tau;
+            if (!__any_sync(live, neg)) continue;
+            if (neg) {
+                any_neg = true;
+                double v[9];
+#pragma unroll
+                for (int r = 0; r < 9; ++r) v[r] = X(r, i);
+#pragma unroll
+                for (int r = 0; r < 9; ++r) {
+                    const double lv = lam[i] * v[r];
+#pragma unroll
+                    for (int c = 0; c <= r; ++c) Mp[pk(r, c)] = fma(-lv, v[c], Mp[pk(r, c)]);
+                }
+            }
+        }
+        if (!any_neg) continue;
+        // Hd[a][m + 1] = SG[a][m] / 2 for the three non-translation modes
+        constexpr int SG[4][3] = {{1, 1, 1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, 1}};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            // Ta[r][j] = sum_m SG[a][m] M'[(3m + r), j]
+            double Ta[3][9];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
-                had_inv(X(r, i), X(3 + r, i), X(6 + r, i), u[r], u[3 + r], u[6 + r], u[9 + r]);
 #pragma unroll
-            for (int q = 0; q < 12; ++q) w[q] = lam[i] * u[q];
-            // H -= (lambda u) u^T: one fused multiply-add per entry
+                for (int j = 0; j < 9; ++j)
+                    Ta[r][j] = SG[a][0] * Mp[pk(r, j)] + SG[a][1] * Mp[pk(3 + r, j)] +
+                               SG[a][2] * Mp[pk(6 + r, j)];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int b = a; b < 4; ++b)
 #pragma unroll
-                for (int b = a; b < 4; ++b)
+                for (int r = 0; r < 3; ++r)
 #pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const double wr = w[3 * a + r], uc = u[3 * b + c];
-                            if (staged) {
-                                HT* p = staged + 9 * up_index(a, b) + 3 * r + c;
-                                *p = (HT)fma(-wr, uc, (double)*p);
-                            } else {
-                                double* p = full + (3 * a + r) * 12 + 3 * b + c;
-                                *p = fma(-wr, uc, *p);
-                                if (a != b) {
-                                    double* q = full + (3 * b + c) * 12 + 3 * a + r;
-                                    *q = fma(-wr, uc, *q);
-                                }
-                            }
+                    for (int c = 0; c < 3; ++c) {
+                        const double h = 0.25 * (SG[b][0] * Ta[r][c] + SG[b][1] * Ta[r][3 + c] +
+                                                 SG[b][2] * Ta[r][6 + c]);
+                        if (staged) {
+                            staged[9 * up_index(a, b) + 3 * r + c] = (HT)h;
+                        } else {
+                            full[(3 * a + r) * 12 + 3 * b + c] = h;
+                            if (a != b) full[(3 * b + c) * 12 + 3 * a + r] = h;
                         }
+                    }
         }
     }
 }
