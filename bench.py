@@ -581,6 +581,33 @@ def main():
                           "newton_tol": 1e-6, "pcg_tol": 1e-6,
                           "dx_rel_err_vs_fp64": float(np.abs(x32 - x64).max() /
                                                       max(np.abs(x64 - m["X"]).max(), 1e-300))}
+        # the whole trajectory of the workload: 10 steps from rest, each
+        # form, timed on the host around each step (plain Newton path: graph
+        # replay, tracer off); the FP32 form's deviation after 10 steps
+        traj = {}
+        for name, prec, tol, ptol in (("fp64", sx.SX_FP64, 1e-8, 1e-10),
+                                      ("fp32", sx.SX_FP32, 1e-6, 1e-6)):
+            s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+            torch.cuda.synchronize()
+            per, its, pcg, st = [], 0, 0, []
+            for _ in range(10):
+                t0 = time.perf_counter()
+                rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=tol,
+                                        pcg_tol=ptol, precision=prec)
+                per.append((time.perf_counter() - t0) * 1e3)
+                its += rep["newton_iters"]
+                pcg += rep["pcg_iters"]
+                st.append(rc)
+            xs = s.get_state()[0]
+            traj[name] = {"steps": 10, "dt": 0.005, "total_ms": sum(per),
+                          "step_ms_median": statistics.median(per), "newton_iters": its,
+                          "pcg_iters": pcg, "ok_steps": sum(1 for v in st if v == 0),
+                          "element_steps_per_s": 10 * T / (sum(per) / 1e3), "x": xs}
+        disp = max(np.abs(traj["fp64"]["x"] - m["X"]).max(), 1e-300)
+        traj["fp32"]["x_rel_err_vs_fp64"] = float(np.abs(traj["fp32"]["x"] - traj["fp64"]["x"]).max() / disp)
+        for v in traj.values():
+            v.pop("x")
+        newton["trajectory_10_steps"] = traj
 
     # ---- serving: Poisson stream of scene requests (bounded sample)
     serving = None

@@ -1541,19 +1541,15 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
                 const int pi = o.precision == SX_FP32 ? 1 : 0;
                 CK(cudaGraphLaunch(B->pcg_graph[pi], st));
                 ctx->prof_launches[SX_PH_SPMV] += 8;
-                ctx->prof_launches[SX_PH_PCG] += 32;
+                ctx->prof_launches[SX_PH_PCG] += 16;
             } else {
                 int par = 0;
                 for (int j = 0; j < 8; ++j) {
                     PL(SX_PH_PCG, 1, launch_pcg_pdir(B->d_desc, cn, cnnt, o.precision, par, st));
                     PL(SX_PH_SPMV, 1, launch_spmv_pq(B->d_desc, cr, cnrt, o.precision, par,
-                                                     B->d_part_row, st));
-                    PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_row, 1, crb, cre, n, B->d_desc,
-                                                       1, o.pcg_tol, o.max_pcg, st));
+                                                     B->d_part_row, crb, cre, st));
                     PL(SX_PH_PCG, 1, launch_pcg_update(B->d_desc, cn, cnnt, par, B->d_part_node,
-                                                       st));
-                    PL(SX_PH_PCG, 1, launch_pcg_reduce(B->d_part_node, 2, cnb, cne, n, B->d_desc,
-                                                       2, o.pcg_tol, o.max_pcg, st));
+                                                       cnb, cne, o.pcg_tol, o.max_pcg, st));
                     par ^= 1;
                 }
             }

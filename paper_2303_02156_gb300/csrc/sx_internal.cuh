@@ -81,6 +81,8 @@ struct SceneScal {
     int nonfinite;     // non-finite values seen in the last evaluation
     int clamped;       // elements projected in the last EGH evaluation
     int clamp_fail;    // set by the projection kernel if QL did not converge
+    int cnt_spmv;      // PCG: row tiles of this scene done in the current SpMV
+    int cnt_update;    // PCG: node tiles of this scene done in the current update
 };
 
 struct SceneDev {
@@ -237,15 +239,19 @@ cudaError_t launch_predict(const SceneDev* scenes, const Tile* node_tiles, int n
                            double* part, cudaStream_t s);
 cudaError_t launch_pcg_setup_p(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
                                int precision, double* part, cudaStream_t s);
+// q = A p with the p.q partials per row tile; the last tile of each scene
+// to finish also forms that scene's p.q and alpha (tbeg/tend: the scene's
+// tile range in `row_tiles`)
 cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int ntiles,
-                           int precision, int parity, double* part, cudaStream_t s);
+                           int precision, int parity, double* part, const int* tbeg,
+                           const int* tend, cudaStream_t s);
 cudaError_t launch_pcg_pdir(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
                             int precision, int parity, cudaStream_t s);
 int spmv_rows_per_tile();
 // sets the SpMV kernels' shared-memory opt-in on the current device (once)
 void prepare_spmv();
 // eight PCG iterations as a chain of kernel nodes appended to `graph`
-struct PcgChunkArgs {
+struct PcgChunkArgs {   // (the fused kernels take the scenes' tile ranges)
     const SceneDev* scenes;
     int n_scenes;
     const Tile* node_tiles;
@@ -263,8 +269,11 @@ struct PcgChunkArgs {
     int max_iter;
 };
 cudaError_t add_pcg_chunk_nodes(cudaGraph_t graph, const PcgChunkArgs& a);
+// dx += alpha p, r -= alpha q, z = Minv r with the r.z and r.r partials;
+// the last tile of each scene forms its convergence test and beta
 cudaError_t launch_pcg_update(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
-                              int parity, double* part, cudaStream_t s);
+                              int parity, double* part, const int* tbeg, const int* tend,
+                              double tol, int max_iter, cudaStream_t s);
 cudaError_t launch_pcg_reduce(const double* part, int nv, const int* tbeg, const int* tend,
                               int nscenes, const SceneDev* scenes, int stage, double tol,
                               int max_iter, cudaStream_t s);

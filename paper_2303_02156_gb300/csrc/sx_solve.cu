@@ -7,10 +7,11 @@
 //   dx += alpha p_new;  r -= alpha q;  z = Minv r
 //   stop when ||r|| <= tol ||b||;  beta = r.z_new / r.z
 // p_old and p_new alternate between two buffers. An iteration is three
-// vector kernels (direction, SpMV with the p.q partials, update with the
-// r.z and r.r partials) and two one-block-per-scene reductions that also
-// form alpha and beta. Pinned DOFs are eliminated by mask: their rows are
-// identity, and their columns drop out because p is zero there.
+// kernels: direction; SpMV with the p.q partials, whose last tile per scene
+// sums them and forms alpha; update with the r.z and r.r partials, whose
+// last tile per scene sums them, tests convergence and forms beta. Pinned
+// DOFs are eliminated by mask: their rows are identity, and their columns
+// drop out because p is zero there.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -158,6 +159,73 @@ cudaError_t launch_pcg_setup_p(const SceneDev* scenes, const Tile* node_tiles, i
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ scene sums in the last tile
+// Each tile of a live scene stores its partial(s), then counts itself done
+// on the scene's counter; the block that completes the count sums the
+// scene's partials over its tile range in a fixed order (so the result does
+// not depend on which block was last) and resets the counter.
+template <int NV, int NT>
+__device__ __forceinline__ bool last_tile_sums(const double (&v)[NV], double (*sh)[NT],
+                                               double* part, int ti, int* counter, int tb,
+                                               int te, double (&out)[NV])
+{
+    __shared__ int s_last;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w && (int)threadIdx.x + w < NT)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[(int64_t)NV * ti + k] = sh[k][0];
+        __threadfence();
+        s_last = atomicAdd(counter, 1) == te - tb - 1;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    // four interleaved accumulators per thread (independent loads and adds),
+    // combined in a fixed order
+    double a[4][NV];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) a[j][k] = 0.0;
+    int t = tb + threadIdx.x;
+    for (; t + 3 * NT < te; t += 4 * NT)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) a[j][k] += __ldcg(part + (int64_t)NV * (t + j * NT) + k);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)   // fewer than 4 strides left
+        if (t < te) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) a[j][k] += __ldcg(part + (int64_t)NV * t + k);
+            t += NT;
+        }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) a[0][k] = (a[0][k] + a[1][k]) + (a[2][k] + a[3][k]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = a[0][k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w && (int)threadIdx.x + w < NT)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = sh[k][0];
+    if (threadIdx.x == 0) *counter = 0;
+    return true;
+}
+
 // ------------------------------------------------------------------ SpMV
 // p_new = z + beta p_old (own rows), then q = A p_new. The direction update
 // runs as its own vector pass so that the SpMV gathers a single vector and
@@ -252,11 +320,12 @@ static constexpr long kWaitLimit = 1L << 24;          // bounded mbarrier wait
 
 template <typename VT>
 __global__ void __launch_bounds__(kSpmvThreads)
-k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part)
+k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part,
+       const int* tbeg, const int* tend)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ double sh[kSpmvThreads];
+    __shared__ double sh[1][kSpmvThreads];
     __shared__ int s_mode;   // 1: staged in shared memory, 0: direct loads
     __shared__ long s_vofs, s_cofs;
     const int ti = blockIdx.x;
@@ -296,14 +365,20 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
         }
         if (it >= kWaitLimit) {
             // the copy did not complete in time: report it through the
-            // scene's PCG status, wait (bounded) once more so that no write
-            // lands after exit, and skip the tile
-            if (threadIdx.x == 0) {
-                S.sc->pcg_status = 3;
-                S.sc->pcg_done = 1;
-            }
+            // scene's PCG status (the scene's last tile then stops its PCG),
+            // wait (bounded) once more so that no write lands after exit, and
+            // count the tile with a zero partial
+            if (threadIdx.x == 0) S.sc->pcg_status = 3;
             long it2 = 0;
             while (!mbar_try_wait(&bar, 0) && ++it2 < kWaitLimit) {
+            }
+            const double z[1] = {0.0};
+            double tot[1];
+            if (last_tile_sums<1, kSpmvThreads>(z, sh, part, ti, &S.sc->cnt_spmv, tbeg[T.scene],
+                                                tend[T.scene], tot) &&
+                threadIdx.x == 0) {
+                S.sc->pcg_done = 1;
+                S.sc->pcg_alpha = 0.0;
             }
             return;
         }
@@ -342,15 +417,25 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
         S.q[3 * r + ci] = q;
         v = pn[3 * r + ci] * q;
     }
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    if (threadIdx.x < 128 && threadIdx.x + 128 < kSpmvThreads) sh[threadIdx.x] += sh[threadIdx.x + 128];
-    __syncthreads();
-    for (int w = 64; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
+    if (!live) return;   // every tile of the scene sees the same state
+    const double vv[1] = {v};
+    double pq[1];
+    if (last_tile_sums<1, kSpmvThreads>(vv, sh, part, ti, &S.sc->cnt_spmv, tbeg[T.scene],
+                                        tend[T.scene], pq) &&
+        threadIdx.x == 0) {
+        SceneScal* sc = S.sc;
+        sc->pq = pq[0];
+        if (sc->pcg_status == 3) {
+            sc->pcg_done = 1;
+            sc->pcg_alpha = 0.0;
+        } else if (!(pq[0] > 0.0) || !isfinite(pq[0])) {   // not a descent system: stop
+            sc->pcg_done = 1;
+            sc->pcg_status = 1;
+            sc->pcg_alpha = 0.0;
+        } else {
+            sc->pcg_alpha = sc->rz / pq[0];
+        }
     }
-    if (threadIdx.x == 0) part[ti] = sh[0];
 }
 
 int spmv_rows_per_tile() { return kSpmvRows; }
@@ -373,29 +458,34 @@ void prepare_spmv()
 }
 
 cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int ntiles,
-                           int precision, int parity, double* part, cudaStream_t s)
+                           int precision, int parity, double* part, const int* tbeg,
+                           const int* tend, cudaStream_t s)
 {
     if (!ntiles) return cudaSuccess;
     const int smem64 = spmv_smem_vals<double>() + kSpmvSmemCols;
     const int smem32 = spmv_smem_vals<float>() + kSpmvSmemCols;
     prepare_spmv();
     if (precision == SX_FP32)
-        k_spmv<float><<<ntiles, kSpmvThreads, smem32, s>>>(scenes, row_tiles, ntiles, parity, part);
+        k_spmv<float><<<ntiles, kSpmvThreads, smem32, s>>>(scenes, row_tiles, ntiles, parity, part,
+                                                           tbeg, tend);
     else
-        k_spmv<double><<<ntiles, kSpmvThreads, smem64, s>>>(scenes, row_tiles, ntiles, parity, part);
+        k_spmv<double><<<ntiles, kSpmvThreads, smem64, s>>>(scenes, row_tiles, ntiles, parity,
+                                                            part, tbeg, tend);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ update
 __global__ void __launch_bounds__(kVecThreads)
-k_pcg_update(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part)
+k_pcg_update(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part,
+             const int* tbeg, const int* tend, double tol, int max_iter)
 {
     __shared__ double sh[2][kVecThreads];
     const int ti = blockIdx.x;
     const Tile T = tiles[ti];
     const SceneDev& S = scenes[T.scene];
+    if (!scene_live(S) || S.sc->pcg_done) return;   // the same for every tile of the scene
     double v[2] = {0.0, 0.0};
-    if (scene_live(S) && !S.sc->pcg_done && (int)threadIdx.x < T.count) {
+    if ((int)threadIdx.x < T.count) {
         const int64_t n = T.start + threadIdx.x;
         const double alpha = S.sc->pcg_alpha;
         const double* pn = par ? S.p0 : S.p1;
@@ -415,14 +505,35 @@ k_pcg_update(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, dou
             v[1] += r[i] * r[i];
         }
     }
-    block_reduce_store<2>(sh, v, part, ti);
+    double rzr[2];
+    if (last_tile_sums<2, kVecThreads>(v, sh, part, ti, &S.sc->cnt_update, tbeg[T.scene],
+                                       tend[T.scene], rzr) &&
+        threadIdx.x == 0) {
+        // convergence test and beta (the update of the chunk's p.q stage)
+        SceneScal* sc = S.sc;
+        sc->rz_new = rzr[0];
+        sc->rr = rzr[1];
+        sc->pcg_iters += 1;
+        const double t = sc->pcg_tol > 0.0 ? sc->pcg_tol : tol;
+        if (rzr[1] <= t * t * sc->bnorm2) {
+            sc->pcg_done = 1;
+        } else if (sc->pcg_iters >= max_iter || !isfinite(rzr[1])) {
+            sc->pcg_done = 1;
+            sc->pcg_status = 2;
+        } else {
+            sc->pcg_beta = rzr[0] / sc->rz;
+            sc->rz = rzr[0];
+        }
+    }
 }
 
 cudaError_t launch_pcg_update(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
-                              int parity, double* part, cudaStream_t s)
+                              int parity, double* part, const int* tbeg, const int* tend,
+                              double tol, int max_iter, cudaStream_t s)
 {
     if (!ntiles) return cudaSuccess;
-    k_pcg_update<<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity, part);
+    k_pcg_update<<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity, part, tbeg,
+                                                tend, tol, max_iter);
     return cudaGetLastError();
 }
 
@@ -460,6 +571,8 @@ __global__ void k_pcg_reduce(const double* part, int nv, const int* tbeg, const 
         sc->bnorm2 = a;
         sc->rz = b;
         sc->rr = a;
+        sc->cnt_spmv = 0;
+        sc->cnt_update = 0;
         sc->pcg_iters = 0;
         sc->pcg_beta = 0.0;
         sc->pcg_status = 0;
@@ -500,8 +613,8 @@ cudaError_t launch_pcg_reduce(const double* part, int nv, const int* tbeg, const
 }
 
 // ------------------------------------------------------------------ PCG chunk graph
-// The eight iterations of launch order (direction, SpMV, p.q reduction,
-// update, r.z reduction) as kernel nodes of an explicitly built graph, each
+// The eight iterations of launch order (direction, SpMV with the p.q sums,
+// update with the r.z / r.r sums) as kernel nodes of an explicitly built graph, each
 // node depending on the one before: the same kernels, arguments and order as
 // the plain launches. Built without stream capture, so host threads of other
 // contexts may synchronize the device while it is built.
@@ -546,22 +659,15 @@ cudaError_t add_pcg_chunk_nodes(cudaGraph_t graph, const PcgChunkArgs& a)
     const int *rb = a.row_beg, *re = a.row_end, *nb = a.node_beg, *ne = a.node_end;
     double tol = a.tol;
     int maxit = a.max_iter;
-    int nv1 = 1, nv2 = 2, st1 = 1, st2 = 2;
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < 8 && e == cudaSuccess; ++j) {
         int par = j & 1;
         void* a_pdir[] = {&scenes, &nt, &nnt, &par};
-        void* a_spmv[] = {&scenes, &rt, &nrt, &par, &prow};
-        void* a_red1[] = {&prow, &nv1, &rb, &re, &scenes, &st1, &tol, &maxit};
-        void* a_upd[] = {&scenes, &nt, &nnt, &par, &pnode};
-        void* a_red2[] = {&pnode, &nv2, &nb, &ne, &scenes, &st2, &tol, &maxit};
+        void* a_spmv[] = {&scenes, &rt, &nrt, &par, &prow, &rb, &re};
+        void* a_upd[] = {&scenes, &nt, &nnt, &par, &pnode, &nb, &ne, &tol, &maxit};
         if (e == cudaSuccess) e = c.add(pdir, (unsigned)nnt, kVecThreads, 0, a_pdir);
         if (e == cudaSuccess) e = c.add(spmv, (unsigned)nrt, kSpmvThreads, smem, a_spmv);
-        if (e == cudaSuccess)
-            e = c.add((const void*)k_pcg_reduce, (unsigned)a.n_scenes, kRedT, 0, a_red1);
         if (e == cudaSuccess) e = c.add((const void*)k_pcg_update, (unsigned)nnt, kVecThreads, 0, a_upd);
-        if (e == cudaSuccess)
-            e = c.add((const void*)k_pcg_reduce, (unsigned)a.n_scenes, kRedT, 0, a_red2);
     }
     return e;
 }
