@@ -79,6 +79,11 @@ struct sx_ctx {
     // demand; a context runs one evaluation at a time)
     double* clampM = nullptr;
     ClampRef* clampRef = nullptr;
+    // two-launch projection scratch (same capacity as the queue)
+    float* clampX = nullptr;
+    double* clampFro = nullptr;
+    int* clampBucket = nullptr;
+    int* clampBucketCount = nullptr;
     int* clampCount = nullptr;   // [0] count, [1] failures
     int64_t clamp_cap = 0;
 };
@@ -517,16 +522,31 @@ int ensure_clamp_queue(sx_ctx* ctx, int64_t need, cudaStream_t st)
 {
     if (need > (int64_t)INT32_MAX) return fail(ctx, SX_EINVAL, "eval: too many projectable stencils");
     if (ctx->clamp_cap >= need && ctx->clampM) return SX_OK;
-    if (ctx->clampM) cudaFreeAsync(ctx->clampM, st);
-    if (ctx->clampRef) cudaFreeAsync(ctx->clampRef, st);
+    for (void* p : {(void*)ctx->clampM, (void*)ctx->clampRef, (void*)ctx->clampX,
+                    (void*)ctx->clampFro, (void*)ctx->clampBucket})
+        if (p) cudaFreeAsync(p, st);
     ctx->clampM = nullptr;
     ctx->clampRef = nullptr;
+    ctx->clampX = nullptr;
+    ctx->clampFro = nullptr;
+    ctx->clampBucket = nullptr;
     if (!ctx->clampCount) CK(cudaMallocAsync((void**)&ctx->clampCount, 2 * sizeof(int), st));
+    if (!ctx->clampBucketCount)
+        CK(cudaMallocAsync((void**)&ctx->clampBucketCount, 10 * sizeof(int), st));
     if (cudaMallocAsync((void**)&ctx->clampM, (size_t)need * 45 * sizeof(double), st) != cudaSuccess ||
-        cudaMallocAsync((void**)&ctx->clampRef, (size_t)need * sizeof(ClampRef), st) != cudaSuccess) {
+        cudaMallocAsync((void**)&ctx->clampRef, (size_t)need * sizeof(ClampRef), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&ctx->clampX, (size_t)need * 81 * sizeof(float), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&ctx->clampFro, (size_t)need * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&ctx->clampBucket, (size_t)need * 10 * sizeof(int), st) != cudaSuccess) {
         cudaGetLastError();
-        if (ctx->clampM) cudaFreeAsync(ctx->clampM, st);
+        for (void* p : {(void*)ctx->clampM, (void*)ctx->clampRef, (void*)ctx->clampX,
+                        (void*)ctx->clampFro, (void*)ctx->clampBucket})
+            if (p) cudaFreeAsync(p, st);
         ctx->clampM = nullptr;
+        ctx->clampRef = nullptr;
+        ctx->clampX = nullptr;
+        ctx->clampFro = nullptr;
+        ctx->clampBucket = nullptr;
         ctx->clamp_cap = 0;
         return fail(ctx, SX_ENOMEM, "eval: device allocation failed (projection queue)");
     }
@@ -633,6 +653,12 @@ int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool 
     L.clamp_count = ctx->clampCount;
     L.clamp_failed = ctx->clampCount + 1;
     L.clamp_cap = (int)std::min<int64_t>(ctx->clamp_cap, INT32_MAX);
+    if (level >= 2 && project) {
+        L.clamp_X = ctx->clampX;
+        L.clamp_fro = ctx->clampFro;
+        L.clamp_bucket = ctx->clampBucket;
+        L.clamp_bucket_count = ctx->clampBucketCount;
+    }
     const int pidx = precision == SX_FP32 ? 1 : 0;
     L.clamp_threads = ctx->clamp_threads[pidx];
     L.clamp_grid = clamp_grid_for(B->clamp_need, L.clamp_threads);
@@ -802,6 +828,10 @@ int sx_destroy(sx_ctx* ctx)
     cudaFree(ctx->clampM);
     cudaFree(ctx->clampRef);
     cudaFree(ctx->clampCount);
+    cudaFree(ctx->clampX);
+    cudaFree(ctx->clampFro);
+    cudaFree(ctx->clampBucket);
+    cudaFree(ctx->clampBucketCount);
     delete ctx;
     return SX_OK;
 }
@@ -1810,6 +1840,11 @@ struct NaPtrs {
     int* counters = nullptr;
     double* clampM = nullptr;
     ClampRef* clampRef = nullptr;
+    // two-launch projection scratch (same capacity as the queue)
+    float* clampX = nullptr;
+    double* clampFro = nullptr;
+    int* clampBucket = nullptr;
+    int* clampBucketCount = nullptr;
 };
 
 constexpr int kNaMaxDevices = 64;

@@ -270,50 +270,57 @@ __device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat&
         }
 }
 
-// Phase 2 driver. Mg: packed 9x9 (double, global memory; read twice so that
-// it is not held in registers across the float phase); fro = ||M||_F; live:
-// the lanes of the warp that run this call together. On return X holds an
-// orthonormal basis, ordered by ascending float eigenvalue, whose first k
-// columns are eigenvectors of M with eigenvalues lam[0..k-1] and whose
-// other columns span an invariant subspace on which M is positive definite
-// (lam[k..8] are then the diagonal of that block, all positive).
-__device__ __forceinline__ int eig9(const double* __restrict__ Mg, const SmemMat& X,
-                                    double (&lam)[9], double fro, double theta, unsigned live)
+// Phase 2, float part. Mg: packed 9x9 (double, global memory); fro =
+// ||M||_F. Cyclic Jacobi in float from the identity, then the eigenvector
+// columns ordered by ascending float eigenvalue: put(r, slot, value) stores
+// entry r of the column that lands in `slot`. Returns k, the number of
+// eigenvalues below delta = 1e-5 ||M||_F (9 when a Gershgorin test on the
+// float matrix cannot confirm that the rest is a positive definite block).
+template <typename Put>
+__device__ __forceinline__ int eig9_float(const double* __restrict__ Mg, double fro, Put put)
 {
     int k = 0;
-    // 1. float Jacobi from the identity, then order the columns
-    {
-        float A[45], Xf[81];
+    float A[45], Xf[81];
 #pragma unroll
-        for (int i = 0; i < 45; ++i) A[i] = (float)Mg[i];
+    for (int i = 0; i < 45; ++i) A[i] = (float)Mg[i];
 #pragma unroll
-        for (int i = 0; i < 81; ++i) Xf[i] = (i % 10 == 0) ? 1.0f : 0.0f;
+    for (int i = 0; i < 81; ++i) Xf[i] = (i % 10 == 0) ? 1.0f : 0.0f;
 #pragma unroll 1
-        for (int sw = 0; sw < 5; ++sw) jacobi_sweep_f32(A, Xf);
-        const float delta = 1e-5f * (float)fro;
-        bool pblock_ok = true;
+    for (int sw = 0; sw < 5; ++sw) jacobi_sweep_f32(A, Xf);
+    const float delta = 1e-5f * (float)fro;
+    bool pblock_ok = true;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-            const float lc = A[pk(c, c)];
-            int rank = 0;
-            float rad = 0.0f;
+    for (int c = 0; c < 9; ++c) {
+        const float lc = A[pk(c, c)];
+        int rank = 0;
+        float rad = 0.0f;
 #pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                if (j == c) continue;
-                const float lj = A[pk(j, j)];
-                rank += (lj < lc || (lj == lc && j < c)) ? 1 : 0;
-                rad += (lj >= delta) ? fabsf(A[pk(c, j)]) : 0.0f;
-            }
-            k += (lc < delta) ? 1 : 0;
-            // Gershgorin disc of the P block, with half of delta to spare
-            if (lc >= delta) pblock_ok = pblock_ok && (lc - rad > 0.5f * delta);
-#pragma unroll
-            for (int r = 0; r < 9; ++r) X(r, rank) = (double)Xf[r * 9 + c];
+        for (int j = 0; j < 9; ++j) {
+            if (j == c) continue;
+            const float lj = A[pk(j, j)];
+            rank += (lj < lc || (lj == lc && j < c)) ? 1 : 0;
+            rad += (lj >= delta) ? fabsf(A[pk(c, j)]) : 0.0f;
         }
-        if (!pblock_ok) k = 9;
+        k += (lc < delta) ? 1 : 0;
+        // Gershgorin disc of the P block, with half of delta to spare
+        if (lc >= delta) pblock_ok = pblock_ok && (lc - rad > 0.5f * delta);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) put(r, rank, Xf[r * 9 + c]);
     }
-    // 2. re-orthonormalize in double (modified Gram-Schmidt; X is already
-    //    orthogonal to float precision, so one pass suffices)
+    return pblock_ok ? k : 9;
+}
+
+// Phase 2, double part: X (shared memory, columns ordered as above) is
+// re-orthonormalized, At = X^T M X formed and the N-block rows rotated. On
+// return the first k columns of X are eigenvectors of M with eigenvalues
+// lam[0..k-1]; the other columns span an invariant subspace on which M is
+// positive definite (lam[k..8] are then the diagonal of that block).
+__device__ __forceinline__ void eig9_double(const double* __restrict__ Mg, const SmemMat& X,
+                                            double (&lam)[9], double fro, double theta, int k,
+                                            unsigned live)
+{
+    // re-orthonormalize in double (modified Gram-Schmidt; X is already
+    // orthogonal to float precision, so one pass suffices)
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
 #pragma unroll
@@ -331,8 +338,8 @@ __device__ __forceinline__ int eig9(const double* __restrict__ Mg, const SmemMat
 #pragma unroll
         for (int r = 0; r < 9; ++r) X(r, j) *= inv;
     }
-    // 3. At = X^T M X (nearly diagonal), then double Jacobi sweeps on the
-    //    rows of the N block
+    // At = X^T M X (nearly diagonal), then double Jacobi sweeps on the rows
+    // of the N block
     double At[45];
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
@@ -357,6 +364,14 @@ __device__ __forceinline__ int eig9(const double* __restrict__ Mg, const SmemMat
     for (int sw = 0; sw < SX_F64_SWEEPS; ++sw) jacobi_sweep_f64(At, X, k, thr, live);
 #pragma unroll
     for (int i = 0; i < 9; ++i) lam[i] = At[pk(i, i)];
+}
+
+// Both parts for one stencil (the eigenvector matrix X in shared memory).
+__device__ __forceinline__ int eig9(const double* __restrict__ Mg, const SmemMat& X,
+                                    double (&lam)[9], double fro, double theta, unsigned live)
+{
+    const int k = eig9_float(Mg, fro, [&](int r, int slot, float v) { X(r, slot) = (double)v; });
+    eig9_double(Mg, X, lam, fro, theta, k, live);
     return k;
 }
 

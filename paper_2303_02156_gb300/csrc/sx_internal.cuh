@@ -172,6 +172,13 @@ struct ElemLaunch {
     int* clamp_failed;
     int clamp_cap;
     int clamp_grid;
+    // two-launch projection (batched evaluations; null: one fused launch):
+    // float eigenvectors [81][clamp_cap], ||M||_F per queued stencil, and
+    // the queue positions binned by N-block size k (10 bins of clamp_cap)
+    float* clamp_X;
+    double* clamp_fro;
+    int* clamp_bucket;
+    int* clamp_bucket_count;
     int clamp_threads;    // projection block size: 32, 64, 128 (default) or 256
     int kinds;            // stencil kinds present (1 SNH, 2 hinge, 4 barrier)
     int share_sms;        // leave one projection block per SM for other work
