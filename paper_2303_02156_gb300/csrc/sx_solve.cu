@@ -16,6 +16,8 @@
 
 #include <atomic>
 
+#include <cuda/atomic>
+
 #include "sx_internal.cuh"
 
 namespace sx {
@@ -182,12 +184,13 @@ __device__ __forceinline__ bool last_tile_sums(const double (&v)[NV], double (*s
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) part[(int64_t)NV * ti + k] = sh[k][0];
-        __threadfence();
-        s_last = atomicAdd(counter, 1) == te - tb - 1;
+        // release: this tile's partial is visible to whoever counts last;
+        // acquire: the last one sees every partial released before it
+        cuda::atomic_ref<int, cuda::thread_scope_device> cnt(*counter);
+        s_last = cnt.fetch_add(1, cuda::memory_order_acq_rel) == te - tb - 1;
     }
     __syncthreads();
     if (!s_last) return false;
-    __threadfence();
     // four interleaved accumulators per thread (independent loads and adds),
     // combined in a fixed order
     double a[4][NV];
