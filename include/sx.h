@@ -354,7 +354,8 @@ typedef struct {
     int64_t nnzb_hint;   /* 0: estimate from the counts */
 } sx_scene_desc;
 
-/* Device bytes a finalized scene of this shape holds (upper estimate). */
+/* Device bytes a finalized scene of this shape holds (upper estimate),
+ * including its share of the context's projection scratch. */
 int sx_scene_footprint(const sx_scene_desc* desc, int64_t* bytes);
 /* Device bytes this scene holds now. */
 int sx_scene_bytes(sx_scene* scene, int64_t* bytes);

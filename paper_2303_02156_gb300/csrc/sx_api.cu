@@ -1707,6 +1707,9 @@ int sx_scene_footprint(const sx_scene_desc* d, int64_t* bytes)
     b += d->n_hinges * (16 + 5 * 8);
     b += d->n_pairs * 16;
     b += nst * (8 + 12 * 8 + 90 * 8 + 16 * 4 * 2 + 4 * 4); // staging, slots, lists
+    // the context's projection scratch for the scene's projectable stencils
+    // (tets and pairs): 9x9 matrix, reference, float eigenvectors, norm, bins
+    b += (d->n_tets + d->n_pairs) * (45 * 8 + 16 + 81 * 4 + 8 + 10 * 4);
     b += nnzb * (4 + 4 + 4 + 9 * 8);                        // col, slot_ptr, order, values
     b += 1 << 20;
     *bytes = b;

@@ -104,8 +104,8 @@ int64_t footprint(const Request& r)
     d.n_nodes = r.n_nodes;
     d.n_tets = r.n_tets;
     int64_t b = 0;
-    sx_scene_footprint(&d, &b);
-    return b + r.n_tets * 45 * 8;   // share of the context's projection queue
+    sx_scene_footprint(&d, &b);   // includes the projection scratch share
+    return b;
 }
 
 // registration on the device; returns the status

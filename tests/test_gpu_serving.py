@@ -91,7 +91,7 @@ def test_admission_by_budget_and_rejection(ctx):
         d.n_nodes = m["X"].shape[0]; d.n_tets = m["tets"].shape[0]
         b = C.c_int64()
         sx.sx_scene_footprint(C.byref(d), C.byref(b))
-        fps.append(b.value + d.n_tets * 360)
+        fps.append(b.value)
     budget = int(max(fps) * 1.2)   # one scene at a time
     srv = Server(ctx, budget)
     for m, E, nu in reqs:
