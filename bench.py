@@ -434,11 +434,13 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     from oracle import oracle as orc
     value = n_tets * args.steps / dt
+    # the workload's block count (the oracle's pattern of the whole cube)
+    nnzb = int(orc.bsr_pattern(m["X"].shape[0], m["tets"])[1].size)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(args.size, m, 0),
+        "data": "synthetic", "config": workload_config(args.size, m, nnzb),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
                          "sample": "first %d tets (two bottom layers) of the cube, E+g+H+12x12 "
                                    "Jacobi clamp+BSR assembly per step; host %s"
