@@ -155,6 +155,23 @@ int sx_set_gravity(sx_scene* scene, const double g[3]);
  * and precede any evaluation. Synchronous. */
 int sx_finalize(sx_scene* scene, void* stream);
 
+/* ---- changing contact pairs (§5.3: the pattern of a barrier block follows
+ *      the active pairs; §6.4, Eq. 15: a pair contributes only while
+ *      0 < d < dhat) ------------------------------------------------------
+ * Both calls keep the scene's state (x, v), masses, pins and inertia
+ * setting, replace the pairs of point-triangle block `energy_id` and, if
+ * the scene was finalized, rebuild its pattern, index maps and buffers (a
+ * new fixed pattern: blocks of pairs that left disappear, blocks of new
+ * pairs appear). Earlier sx_get_* views and assembled outputs are invalid
+ * afterwards. Synchronous on `stream`.
+ * sx_set_pairs: n new pairs (point, t0, t1, t2), host or device, n >= 0.
+ * sx_compact_pairs: keeps, in their order, the pairs that are active at the
+ *   current state (0 < d < dhat) or in the error state d <= 0 (so that the
+ *   next evaluation still reports SX_ESTATE); *n_active (may be NULL)
+ *   receives their number. */
+int sx_set_pairs(sx_scene* scene, int energy_id, const int32_t* pairs, int64_t n, void* stream);
+int sx_compact_pairs(sx_scene* scene, int energy_id, int64_t* n_active, void* stream);
+
 /* ---- state ------------------------------------------------------------ */
 /* x, v: n_nodes x 3 doubles (either may be NULL). */
 int sx_set_state(sx_scene* scene, const double* x, const double* v, void* stream);

@@ -127,6 +127,10 @@ struct sx_scene {
     int64_t bytes = 0;
     uint64_t version = 1;   // bumps whenever the device descriptor changes
     std::vector<void*> allocs;
+    // the part of allocs that finalize made (pattern, per-stencil staging,
+    // assembled outputs, solver vectors): released when the topology changes
+    std::vector<void*> fin_allocs;
+    int64_t fin_bytes = 0;
 };
 
 // ---------------------------------------------------------------- batches
@@ -294,6 +298,28 @@ int dalloc(sx_scene* s, T** p, size_t count)
     s->allocs.push_back((void*)*p);
     s->bytes += (int64_t)bytes;
     return SX_OK;
+}
+
+// allocation that belongs to the finalized topology (see fin_allocs)
+template <typename T>
+int dalloc_fin(sx_scene* s, T** p, size_t count)
+{
+    const int64_t before = s->bytes;
+    const int rc = dalloc(s, p, count);
+    if (rc == SX_OK) {
+        s->fin_allocs.push_back((void*)*p);
+        s->fin_bytes += s->bytes - before;
+    }
+    return rc;
+}
+
+// frees one scene allocation now (stream-ordered) and forgets it
+void free_scene_alloc(sx_scene* s, void* p, int64_t bytes)
+{
+    auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+    if (it != s->allocs.end()) s->allocs.erase(it);
+    cudaFreeAsync(p, s->stream);
+    s->bytes -= bytes;
 }
 
 SceneDev make_desc(const sx_scene* s, bool trial)
@@ -619,8 +645,8 @@ int read_scal(sx_ctx* ctx, Batch* B, cudaStream_t st)
 int ensure_vals32(sx_ctx* ctx, sx_scene* s)
 {
     if (s->vals32) return SX_OK;
-    if (dalloc(s, &s->vals32, 9 * (size_t)s->pat.nnzb + 16) != SX_OK ||
-        dalloc(s, &s->p32, 3 * (size_t)s->N + 4) != SX_OK)
+    if (dalloc_fin(s, &s->vals32, 9 * (size_t)s->pat.nnzb + 16) != SX_OK ||
+        dalloc_fin(s, &s->p32, 3 * (size_t)s->N + 4) != SX_OK)
         return fail(ctx, SX_ENOMEM, "eval: device allocation failed (FP32 values)");
     s->version++;
     return SX_OK;
@@ -1076,10 +1102,14 @@ int sx_finalize(sx_scene* s, void* stream)
     if (rc != SX_OK) return fail(ctx, rc, err);
     for (void* p : {(void*)s->pat.row_ptr, (void*)s->pat.col, (void*)s->pat.diag_slot,
                     (void*)s->pat.slots, (void*)s->pat.slot_ptr, (void*)s->pat.slot_src,
-                    (void*)s->pat.slot_order, (void*)s->pat.node_ptr, (void*)s->pat.node_src})
+                    (void*)s->pat.slot_order, (void*)s->pat.node_ptr, (void*)s->pat.node_src}) {
         s->allocs.push_back(p);
-    s->bytes += (int64_t)(s->N + 1) * 8 + s->pat.nnzb * 12 + s->N * 4 + s->nst * 16 * 4 * 2 +
-                s->nst * 4 * 4;
+        s->fin_allocs.push_back(p);
+    }
+    const int64_t pat_bytes = (int64_t)(s->N + 1) * 8 + s->pat.nnzb * 12 + s->N * 4 +
+                              s->nst * 16 * 4 * 2 + s->nst * 4 * 4;
+    s->bytes += pat_bytes;
+    s->fin_bytes += pat_bytes;
     // lumped mass: extra + rho V / 4 of every SNH tet, in element order
     CK(cudaMemcpyAsync(s->mass, s->extra_mass, s->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     for (auto& b : s->blocks)
@@ -1087,11 +1117,12 @@ int sx_finalize(sx_scene* s, void* stream)
             CK(launch_block_mass(s->pat.node_ptr, s->pat.node_src, s->N, b.base, b.n, b.V, b.rho,
                                  s->mass, st));
     const size_t n3 = 3 * (size_t)s->N;
-    if (dalloc(s, &s->Ee, (size_t)s->nst) || dalloc(s, &s->ge, 12 * (size_t)s->nst) ||
-        dalloc(s, &s->He, 90 * (size_t)s->nst) || dalloc(s, &s->vals64, 9 * (size_t)s->pat.nnzb + 8) ||
-        dalloc(s, &s->grad, n3) || dalloc(s, &s->r, n3) || dalloc(s, &s->z, n3) ||
-        dalloc(s, &s->p0, n3) || dalloc(s, &s->p1, n3) || dalloc(s, &s->q, n3) ||
-        dalloc(s, &s->Minv, 9 * (size_t)s->N))
+    if (dalloc_fin(s, &s->Ee, (size_t)s->nst) || dalloc_fin(s, &s->ge, 12 * (size_t)s->nst) ||
+        dalloc_fin(s, &s->He, 90 * (size_t)s->nst) ||
+        dalloc_fin(s, &s->vals64, 9 * (size_t)s->pat.nnzb + 8) || dalloc_fin(s, &s->grad, n3) ||
+        dalloc_fin(s, &s->r, n3) || dalloc_fin(s, &s->z, n3) || dalloc_fin(s, &s->p0, n3) ||
+        dalloc_fin(s, &s->p1, n3) || dalloc_fin(s, &s->q, n3) ||
+        dalloc_fin(s, &s->Minv, 9 * (size_t)s->N))
         return fail(ctx, SX_ENOMEM, "finalize: device allocation failed");
     CK(cudaMemsetAsync(s->grad, 0, n3 * sizeof(double), st));
     CK(cudaMemsetAsync(s->vals64, 0, 9 * (size_t)s->pat.nnzb * sizeof(double), st));
@@ -1100,6 +1131,106 @@ int sx_finalize(sx_scene* s, void* stream)
     s->version++;
     drop_batches_with(ctx, s);
     return SX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Releases everything the last finalize built (the scene is back to its
+// registered, unfinalized form; state, masses and pins are kept).
+void release_finalized(sx_scene* s)
+{
+    drop_batches_with(s->ctx, s);
+    cudaStreamSynchronize(s->stream);
+    for (void* p : s->fin_allocs) {
+        auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+        if (it != s->allocs.end()) s->allocs.erase(it);
+        cudaFreeAsync(p, s->stream);
+    }
+    cudaStreamSynchronize(s->stream);
+    s->fin_allocs.clear();
+    s->bytes -= s->fin_bytes;
+    s->fin_bytes = 0;
+    s->pat = PatternOut{};
+    s->Ee = s->ge = s->He = s->vals64 = s->grad = nullptr;
+    s->r = s->z = s->p0 = s->p1 = s->q = s->Minv = nullptr;
+    s->vals32 = nullptr;
+    s->p32 = nullptr;
+    s->finalized = false;
+    s->last_level = -1;
+    s->version++;
+}
+
+// Puts `conn` (n pairs, device, owned by the scene) in place of barrier
+// block b's pairs, re-bases the blocks and rebuilds the topology.
+int replace_pairs(sx_scene* s, int b, int4* conn, int64_t n, cudaStream_t st)
+{
+    BlockHost& blk = s->blocks[b];
+    if (blk.conn) free_scene_alloc(s, blk.conn, std::max<int64_t>(blk.n, 1) * (int64_t)sizeof(int4));
+    blk.conn = conn;
+    blk.n = n;
+    int64_t base = 0;
+    for (auto& bb : s->blocks) {
+        bb.base = base;
+        base += bb.n;
+    }
+    s->nst = base;
+    const bool was = s->finalized;
+    release_finalized(s);
+    if (!was) return SX_OK;
+    return sx_finalize(s, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sx_set_pairs(sx_scene* s, int energy_id, const int32_t* pairs, int64_t n, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    if (energy_id < 0 || energy_id >= (int)s->blocks.size() ||
+        s->blocks[energy_id].kind != SX_KIND_PT_BARRIER || n < 0 || (n > 0 && !pairs))
+        return fail(ctx, SX_EINVAL, "set_pairs: needs a point-triangle block and n >= 0 pairs");
+    cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
+    int4* conn = nullptr;
+    int rc = copy_conn(ctx, s, pairs, n, &conn, st);
+    if (rc != SX_OK) return rc;
+    CK(cudaStreamSynchronize(st));
+    return replace_pairs(s, energy_id, conn, n, st);
+}
+
+int sx_compact_pairs(sx_scene* s, int energy_id, int64_t* n_active, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    if (energy_id < 0 || energy_id >= (int)s->blocks.size() ||
+        s->blocks[energy_id].kind != SX_KIND_PT_BARRIER)
+        return fail(ctx, SX_EINVAL, "compact_pairs: needs a point-triangle block");
+    cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
+    const BlockHost& blk = s->blocks[energy_id];
+    const int64_t n = blk.n;
+    int *keep = nullptr, *off = nullptr;
+    CK(cudaMallocAsync((void**)&keep, std::max<int64_t>(n, 1) * sizeof(int), st));
+    CK(cudaMallocAsync((void**)&off, (n + 1) * sizeof(int), st));
+    CK(launch_pair_activity(s->x, blk.conn, n, blk.dhat, keep, st));
+    std::string err;
+    int rc = scan_counts(keep, n, off, st, &err);
+    if (rc != SX_OK) return fail(ctx, rc, err);
+    int cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, off + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int4* conn = nullptr;
+    if (dalloc(s, &conn, (size_t)cnt) != SX_OK) return fail(ctx, SX_ENOMEM, "compact_pairs: allocation failed");
+    CK(launch_gather_pairs(blk.conn, keep, off, n, conn, st));
+    CK(cudaFreeAsync(keep, st));
+    CK(cudaFreeAsync(off, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_active) *n_active = cnt;
+    return replace_pairs(s, energy_id, conn, cnt, st);
 }
 
 int sx_set_state(sx_scene* s, const double* x, const double* v, void* stream)

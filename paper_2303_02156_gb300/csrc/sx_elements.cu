@@ -750,6 +750,55 @@ k_clamp_double(ElemLaunch L)
     clamp_finish<HT>(L, ref, Mg, X, lam, k, tau, live);
 }
 
+// Activation of point-triangle pairs at the state x (the classification
+// and distance of Eq. 15's barrier in double): keep[e] = 1 when the pair
+// contributes (0 < d < dhat) or is in an error state (d <= 0, so that the
+// next evaluation still reports it), 0 when it is inactive (d >= dhat).
+__global__ void k_pair_activity(const double* __restrict__ x, const int4* __restrict__ conn,
+                                int64_t n, double dhat, int* keep)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int4 t = conn[e];
+    const int nid[4] = {t.x, t.y, t.z, t.w};
+    double xr[12];
+    double p0[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) p0[i] = x[3 * (int64_t)nid[0] + i];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xr[3 * a + i] = x[3 * (int64_t)nid[a] + i] - p0[i];
+    BarrierOut<double> bo;
+    const int st = barrier_eval<double>(xr, dhat, 0.0, 0, bo);
+    keep[e] = st != 0 ? 1 : 0;
+}
+
+// order-preserving gather of the kept pairs (offsets: exclusive scan of keep)
+__global__ void k_gather_pairs(const int4* __restrict__ conn, const int* __restrict__ keep,
+                               const int* __restrict__ offsets, int64_t n, int4* out)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n || !keep[e]) return;
+    out[offsets[e]] = conn[e];
+}
+
+cudaError_t launch_pair_activity(const double* x, const int4* conn, int64_t n, double dhat,
+                                 int* keep, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_pair_activity<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(x, conn, n, dhat, keep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pairs(const int4* conn, const int* keep, const int* offsets, int64_t n,
+                                int4* out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_gather_pairs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(conn, keep, offsets, n, out);
+    return cudaGetLastError();
+}
+
 const void* elements_kernel(int precision, int snh_only)
 {
     if (snh_only)

@@ -168,6 +168,11 @@ static int exclusive_scan(const int* in, int64_t n, int* out, cudaStream_t s,
     return cudaGetLastError() == cudaSuccess ? SX_OK : SX_ECUDA;
 }
 
+int scan_counts(const int* in, int64_t n, int* out, cudaStream_t s, std::string* err)
+{
+    return exclusive_scan(in, n, out, s, err);
+}
+
 // ------------------------------------------------------------------ incidence
 __global__ void k_count_nodes(const int4* conn, int64_t nst, int* deg)
 {

@@ -190,6 +190,13 @@ int clamp_block_threads();
 // the element kernel for a precision; snh_only: the SNH-only instantiation
 const void* elements_kernel(int precision, int snh_only);
 
+// point-triangle pair activation and order-preserving compaction
+// (sx_elements.cu)
+cudaError_t launch_pair_activity(const double* x, const int4* conn, int64_t n, double dhat,
+                                 int* keep, cudaStream_t s);
+cudaError_t launch_gather_pairs(const int4* conn, const int* keep, const int* offsets, int64_t n,
+                                int4* out, cudaStream_t s);
+
 // registration and pattern (sx_graph.cu)
 cudaError_t launch_snh_rest(const double* X, int64_t N, const int4* tets, int64_t n,
                             const double* young, const double* poisson, double rho,
@@ -214,6 +221,8 @@ struct PatternOut {
 constexpr int kSlotTile = 256;
 int build_pattern(const int4* conn, int64_t nst, int64_t N, PatternOut* out,
                   std::string* err, cudaStream_t s);
+// exclusive prefix sum of n int32 counts into out[0..n] (out[n] = total)
+int scan_counts(const int* in, int64_t n, int* out, cudaStream_t s, std::string* err);
 
 // assembly and reductions (sx_assemble.cu)
 struct AsmLaunch {

@@ -119,6 +119,23 @@ class Scene:
                                   self.stream, C.byref(eid))
         return self._id(rc, eid, sx.SX_KIND_PT_BARRIER, n)
 
+    def set_pairs(self, energy_id, pairs):
+        """Replace the pairs of a barrier block (the pattern is rebuilt)."""
+        pr = _i32(pairs)
+        n = pr.shape[0]
+        self.ctx.check(sx.sx_set_pairs(self.h, energy_id, pr.ctypes.data if n else None, n,
+                                       self.stream))
+        kind, _ = self.blocks[energy_id]
+        self.blocks[energy_id] = (kind, n)
+
+    def compact_pairs(self, energy_id):
+        """Keep only the pairs active at the current state; returns their count."""
+        c = C.c_int64()
+        self.ctx.check(sx.sx_compact_pairs(self.h, energy_id, C.byref(c), self.stream))
+        kind, _ = self.blocks[energy_id]
+        self.blocks[energy_id] = (kind, c.value)
+        return c.value
+
     def add_node_mass(self, m):
         m = _f64(m)
         self.ctx.check(sx.sx_add_node_mass(self.h, m.ctypes.data, self.stream))

@@ -37,7 +37,8 @@ EXPORTS = [
     "sx_newton_step", "sx_newton_step_batch", "sx_scene_footprint", "sx_scene_bytes",
     "sx_copy_bsr", "sx_copy_grad", "sx_scene_info", "sx_block_info", "sx_eval_stats",
     "sx_profile", "sx_profile_read", "sx_eval_elements_noalloc",
-    "sx_autotune", "sx_set_launch_shape", "sx_get_launch_shape",
+    "sx_autotune", "sx_set_launch_shape", "sx_get_launch_shape", "sx_set_pairs",
+    "sx_compact_pairs",
     "sx_server_create", "sx_server_set_lanes", "sx_server_submit", "sx_server_poll", "sx_server_result",
     "sx_server_drain", "sx_server_stats", "sx_server_destroy",
 ]
@@ -140,6 +141,8 @@ _SIGS = {
     "sx_eval_elements_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
     "sx_server_create": (_I, [_P, _I64, C.POINTER(sx_newton_opts), _PP]),
     "sx_autotune": (_I, [_P, C.POINTER(_P), _I, _I, C.POINTER(sx_tune_report), _P]),
+    "sx_set_pairs": (_I, [_P, _I, _P, _I64, _P]),
+    "sx_compact_pairs": (_I, [_P, _I, C.POINTER(_I64), _P]),
     "sx_set_launch_shape": (_I, [_P, _I, _I, _I]),
     "sx_get_launch_shape": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I)]),
     "sx_server_set_lanes": (_I, [_P, _I, C.POINTER(_I64)]),
