@@ -57,6 +57,9 @@ def lib():
     L.orc_lumped_mass.argtypes = [C.c_int, C.c_int, _ip, _dp, _dp, _dp]
     L.orc_snh_element.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double,
                                   _dp, _dp, _dp]
+    L.orc_snh_dPdF.argtypes = [_dp, _dp, C.c_double, C.c_double, _dp]
+    L.orc_snh_element_fproj.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double,
+                                        _dp, _dp, _dp]
     L.orc_snh_batch.argtypes = [C.c_int, _dp, _ip, _dp, _dp, _dp, _dp, C.c_int,
                                 C.c_int, _dp, C.c_void_p, C.c_void_p]
     L.orc_hinge_element.argtypes = [_dp, _dp, C.c_double, C.c_double, _dp, _dp, _dp]
@@ -152,7 +155,23 @@ def snh_element(xe, Dminv, V, mu, lam):
     return E[0], g, H.reshape(12, 12)
 
 
+def snh_dPdF(xe, Dminv, mu, lam):
+    """d2psi/dF2 (9x9, vec index 3i+j) of one SNH tet."""
+    A = np.zeros(81)
+    lib().orc_snh_dPdF(_f64(xe), _f64(Dminv), float(mu), float(lam), A)
+    return A.reshape(9, 9)
+
+
+def snh_element_fproj(xe, Dminv, V, mu, lam):
+    """E, g and the element Hessian with d2psi/dF2 clamped to PSD (F-space
+    projection)."""
+    E = np.zeros(1); g = np.zeros(12); H = np.zeros(144)
+    lib().orc_snh_element_fproj(_f64(xe), _f64(Dminv), float(V), float(mu), float(lam), E, g, H)
+    return E[0], g, H.reshape(12, 12)
+
+
 def snh_batch(x, tets, Dminv, V, mu, lam, level=LEVEL_EGH, project=False):
+    """project: False/0 none, True/1 clamp of the 12x12, 2 clamp of d2psi/dF2."""
     tets = _i32(tets); T = tets.shape[0]
     E = np.empty(T)
     g = np.empty((T, 12)) if level >= 1 else None

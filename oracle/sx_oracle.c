@@ -629,7 +629,68 @@ static void gather4(const double* x, const int* t, double xe[12])
         for (int i = 0; i < 3; ++i) xe[3 * a + i] = x[3 * t[a] + i];
 }
 
-/* level: 0 = E, 1 = E+g, 2 = E+g+H. H_e is 144 per element (row-major). */
+/* The SNH element Hessian with the material Hessian d2psi/dF2 projected to
+ * positive semi-definiteness before the chain rule: H = V B^T proj(d2psi/dF2) B
+ * with proj the eigenvalue clamp at zero of the 9x9 (§5.2's projection taken
+ * on the F-space Hessian rather than on the 12x12 element Hessian; the
+ * survey's "next" row of an analytic projection). The 9x9 is clamped by the
+ * same cyclic Jacobi as the 12x12. E and g are those of orc_snh_element. */
+void orc_snh_element_fproj(const double* xe, const double* Dminv, double V,
+                           double mu, double lam, double* E, double* g, double* H)
+{
+    double B[9 * 12];
+    tet_B(Dminv, B);
+    double F[9];
+    for (int r = 0; r < 9; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < 12; ++c) s += B[r * 12 + c] * xe[c];
+        F[r] = s;
+    }
+    double psi, P[9], A[81];
+    snh_density(F, mu, lam, &psi, P, A);
+    *E = V * psi;
+    if (g)
+        for (int c = 0; c < 12; ++c) {
+            double s = 0.0;
+            for (int r = 0; r < 9; ++r) s += B[r * 12 + c] * P[r];
+            g[c] = V * s;
+        }
+    if (H) {
+        orc_clamp_psd(9, A);
+        double AB[9 * 12];
+        for (int r = 0; r < 9; ++r)
+            for (int c = 0; c < 12; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 9; ++k) s += A[r * 9 + k] * B[k * 12 + c];
+                AB[r * 12 + c] = s;
+            }
+        for (int r = 0; r < 12; ++r)
+            for (int c = 0; c < 12; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 9; ++k) s += B[k * 12 + r] * AB[k * 12 + c];
+                H[r * 12 + c] = V * s;
+            }
+    }
+}
+
+/* d2psi/dF2 (9x9, vec index 3i+j) of one SNH tet at its deformation
+ * gradient, for checks of the F-space projection. */
+void orc_snh_dPdF(const double* xe, const double* Dminv, double mu, double lam, double* A)
+{
+    double B[9 * 12];
+    tet_B(Dminv, B);
+    double F[9];
+    for (int r = 0; r < 9; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < 12; ++c) s += B[r * 12 + c] * xe[c];
+        F[r] = s;
+    }
+    double psi, P[9];
+    snh_density(F, mu, lam, &psi, P, A);
+}
+
+/* level: 0 = E, 1 = E+g, 2 = E+g+H. H_e is 144 per element (row-major).
+ * project: 0 none, 1 clamp of the 12x12 H, 2 clamp of d2psi/dF2. */
 void orc_snh_batch(int T, const double* x, const int* tets, const double* Dminv,
                    const double* V, const double* mu, const double* lam,
                    int level, int project, double* E_e, double* g_e, double* H_e)
@@ -638,6 +699,11 @@ void orc_snh_batch(int T, const double* x, const int* tets, const double* Dminv,
     for (int e = 0; e < T; ++e) {
         double xe[12];
         gather4(x, tets + 4 * e, xe);
+        if (level >= 2 && project == 2) {
+            orc_snh_element_fproj(xe, Dminv + 9 * e, V[e], mu[e], lam[e], E_e + e,
+                                  g_e + 12 * (size_t)e, H_e + 144 * (size_t)e);
+            continue;
+        }
         orc_snh_element(xe, Dminv + 9 * e, V[e], mu[e], lam[e], E_e + e,
                         level >= 1 ? g_e + 12 * (size_t)e : NULL,
                         level >= 2 ? H_e + 144 * (size_t)e : NULL);
