@@ -68,6 +68,11 @@ extern "C" {
                        gradient assembly, energy sums, residual norms and PCG
                        dot products stay in double */
 
+/* PSD projection modes (sx_eval) */
+#define SX_PROJECT_NONE 0
+#define SX_PROJECT_ELEMENT 1
+#define SX_PROJECT_MATERIAL 2
+
 /* ---- energy kinds ----------------------------------------------------- */
 #define SX_KIND_SNH_TET4 0
 #define SX_KIND_HINGE4 1
@@ -183,9 +188,14 @@ int sx_get_state(sx_scene* scene, double* x, double* v, void* stream);
 int sx_set_inertia(sx_scene* scene, double dt, const double* x_tilde, void* stream);
 
 /* ---- evaluation (§5.2; Algorithm 1) -----------------------------------
- * level: SX_E, SX_EG or SX_EGH. project != 0 projects every non-convex
- * element Hessian (SNH, barrier) to PSD by clamping its eigenvalues at 0
- * (FP64 always). precision: SX_FP64 or SX_FP32. E_out (host, may be NULL)
+ * level: SX_E, SX_EG or SX_EGH. project: SX_PROJECT_NONE, SX_PROJECT_ELEMENT
+ * (1: every non-convex element Hessian -- SNH, barrier -- projected to PSD
+ * by clamping the eigenvalues of its 12x12 at 0, FP64 always) or
+ * SX_PROJECT_MATERIAL (2: for SNH tets the material Hessian d2psi/dF2 is
+ * clamped instead, H = V B^T proj(d2psi/dF2) B, in closed form in the frame
+ * of the signed SVD of F (FP64) -- a different PSD Hessian, above the plain
+ * one, cheaper than the 12x12 clamp; barriers as in 1). precision: SX_FP64
+ * or SX_FP32. E_out (host, may be NULL)
  * receives the total energy; the assembled gradient (FP64) and BSR values
  * stay on the device (sx_get_grad, sx_get_bsr). Synchronous when E_out is
  * given. */
@@ -271,7 +281,7 @@ typedef struct {
     int max_newton;      /* Newton iteration cap */
     int max_pcg;         /* PCG iteration cap per solve */
     int max_halvings;    /* line-search halvings cap */
-    int project;         /* project element Hessians to PSD */
+    int project;         /* SX_PROJECT_* (see sx_eval) */
     int precision;       /* SX_FP64 or SX_FP32 */
     double armijo_c;     /* sufficient-decrease constant */
     int forcing;         /* 1: PCG stops at ||r|| <= eta_k ||b|| with the forcing

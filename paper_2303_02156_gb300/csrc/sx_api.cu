@@ -57,8 +57,8 @@ struct sx_ctx {
     std::vector<cudaEvent_t> prof_pool;
     double prof_ms[SX_PH_COUNT] = {0};
     int64_t prof_launches[SX_PH_COUNT] = {0};
-    // occupancy limit of the element kernel [precision][all kinds, SNH only]
-    int elem_occ[2][2] = {{1, 1}, {1, 1}};
+    // occupancy limit of the element kernel [precision][instantiation]
+    int elem_occ[2][4] = {{1, 1, 1, 1}, {1, 1, 1, 1}};
     bool share_sms = false;
     // launch shapes per precision (sx_autotune / sx_set_launch_shape):
     // projection block size, and element-kernel blocks per SM of the
@@ -206,10 +206,10 @@ int clamp_grid_for(int64_t max_queued, int threads)
 
 // element-kernel grid for `ntiles` tiles of the given kinds under the
 // context's launch shape
-int elem_grid(const sx_ctx* ctx, int precision, int kinds, int ntiles)
+int elem_grid(const sx_ctx* ctx, int precision, int kinds, int project, int ntiles)
 {
     const int p = precision == SX_FP32 ? 1 : 0;
-    const int occ = ctx->elem_occ[p][kinds == 1 ? 1 : 0];
+    const int occ = ctx->elem_occ[p][elements_variant(kinds, project)];
     const int bps = ctx->elem_bps[p] < 0 ? occ : std::min(ctx->elem_bps[p], occ);
     const int g = bps == 0 ? ntiles : std::min<int>(ntiles, ctx->sm_count * bps);
     return std::max(g, 1);
@@ -690,7 +690,7 @@ int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool 
     L.clamp_grid = clamp_grid_for(B->clamp_need, L.clamp_threads);
     L.share_sms = ctx->share_sms;
     L.kinds = B->kinds;
-    const int grid = elem_grid(ctx, precision, L.kinds, L.ntiles);
+    const int grid = elem_grid(ctx, precision, L.kinds, level >= 2 ? project : 0, L.ntiles);
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (level >= 2 && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_elem, 1, 0, B->d_elem_beg, B->d_elem_end,
@@ -816,7 +816,7 @@ int sx_create(sx_ctx** out, const sx_options* opt)
     }
     ctx->share_sms = opt && opt->share_sms;
     for (int p = 0; p < 2; ++p)
-        for (int v = 0; v < 2; ++v) {
+        for (int v = 0; v < 4; ++v) {
             int nb = 1;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elements_kernel(p, v),
                                                           elements_block_threads(), 0);
@@ -1486,7 +1486,8 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     L.clamp_grid = clamp_grid_for(L.clamp_cap, L.clamp_threads);
     L.share_sms = ctx->share_sms;
     L.kinds = kind_bit(b.kind);
-    PL(SX_PH_ELEMENTS, 1, launch_elements(L, elem_grid(ctx, precision, L.kinds, L.ntiles), st));
+    PL(SX_PH_ELEMENTS, 1, launch_elements(L, elem_grid(ctx, precision, L.kinds, H ? project : 0,
+                                                         L.ntiles), st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     int qfail[2] = {0, 0};
     if (qC) CK(cudaMemcpyAsync(qfail, qC, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -2066,7 +2067,7 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
     L.clamp_grid = clamp_grid_for(L.clamp_cap, L.clamp_threads);
     L.share_sms = ctx->share_sms;
     L.kinds = kind_bit(b.kind);
-    const int grid = elem_grid(ctx, precision, L.kinds, nt);
+    const int grid = elem_grid(ctx, precision, L.kinds, H ? project : 0, nt);
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     int failed = 0;

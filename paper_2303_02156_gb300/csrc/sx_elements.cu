@@ -315,7 +315,222 @@ struct ThreadOut {
     int clamped;    // queued for the projection
 };
 
-template <typename R, typename HT>
+// ---------------------------------------------------------------- F-space projection
+// Cyclic Jacobi on a symmetric 3x3 in double (A packed lower: 00,10,11,20,21,22),
+// eigenvectors accumulated into the columns of Q (row-major). Stops once
+// the off-diagonal is below 1e-17 of the diagonal scale (at most 8 sweeps).
+__device__ __forceinline__ void jacobi3(double (&A)[6], double (&Q)[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Q[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    for (int sw = 0; sw < 8; ++sw) {
+        const double off = fabs(A[1]) + fabs(A[3]) + fabs(A[4]);
+        const double dia = fabs(A[0]) + fabs(A[2]) + fabs(A[5]);
+        if (!(off > 1e-17 * dia)) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            const int ipq = pk(p, q), ipp = pk(p, p), iqq = pk(q, q);
+            const double apq = A[ipq];
+            if (apq == 0.0) continue;
+            const double tau = (A[iqq] - A[ipp]) / (2.0 * apq);
+            const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+            const double c = rsqrt(fma(t, t, 1.0)), sn = t * c;
+            A[ipp] -= t * apq;
+            A[iqq] += t * apq;
+            A[ipq] = 0.0;
+            const int r = 3 - p - q;
+            const double arp = A[pk(r, p)], arq = A[pk(r, q)];
+            A[pk(r, p)] = c * arp - sn * arq;
+            A[pk(r, q)] = sn * arp + c * arq;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double xp = Q[3 * i + p], xq = Q[3 * i + q];
+                Q[3 * i + p] = c * xp - sn * xq;
+                Q[3 * i + q] = sn * xp + c * xq;
+            }
+        }
+    }
+}
+
+// project mode 2 for one SNH tet: removes from its Hessian blocks the
+// negative modes of d2psi/dF2 (H = V B^T proj(d2psi/dF2) B). In the frame
+// of the signed SVD F = U diag(s) V^T (U, V rotations) the material Hessian
+// a I + gam F F^T + lam' C C^T + b dC/dF splits into three twist/flip pairs,
+// eigenvalue a - b s_k on (u_i v_j^T + u_j v_i^T)/sqrt2 and a + b s_k on
+// (u_i v_j^T - u_j v_i^T)/sqrt2 ({i, j, k} = {0, 1, 2}), and the stretch
+// block a I + gam s s^T + lam' p p^T + b K on U diag(q) V^T, with
+// p = (s1 s2, s0 s2, s0 s1) and K the symmetric 3x3 with zero diagonal and
+// K01 = s2, K02 = s1, K12 = s0. A negative mode (lambda, E) changes block
+// (a, b) by -V lambda (E G_a)(E G_b)^T. Returns the number of modes removed.
+template <typename HT>
+__device__ int snh_fproj(const double* xg, const double* Dinv, double Vd, double mud,
+                         double lamd, HT* staged, double* full)
+{
+    double F[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double d1 = xg[3 + i] - xg[i], d2 = xg[6 + i] - xg[i], d3 = xg[9 + i] - xg[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            F[3 * i + j] = d1 * Dinv[j] + d2 * Dinv[3 + j] + d3 * Dinv[6 + j];
+    }
+    double Ic = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ic = fma(F[k], F[k], Ic);
+    const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                     F[2] * (F[3] * F[7] - F[4] * F[6]);
+    const double a = mud * Ic / (Ic + 1.0);
+    const double gam = 2.0 * mud / ((Ic + 1.0) * (Ic + 1.0));
+    const double b = (lamd != 0.0) ? lamd * (J - 1.0) - 0.75 * mud : 0.0;
+    // V: eigenvectors of F^T F
+    double S[6];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q <= p; ++q)
+            S[pk(p, q)] = F[p] * F[q] + F[3 + p] * F[3 + q] + F[6 + p] * F[6 + q];
+    double Vm[9];
+    jacobi3(S, Vm);
+    // a proper rotation V
+    const double dv = Vm[0] * (Vm[4] * Vm[8] - Vm[5] * Vm[7]) -
+                      Vm[1] * (Vm[3] * Vm[8] - Vm[5] * Vm[6]) +
+                      Vm[2] * (Vm[3] * Vm[7] - Vm[4] * Vm[6]);
+    if (dv < 0.0) {
+        Vm[2] = -Vm[2];
+        Vm[5] = -Vm[5];
+        Vm[8] = -Vm[8];
+    }
+    // U from F V: the two larger directions by normalization, the third by
+    // the right-handed cross product; its singular value keeps the sign of J
+    int m = 0;
+    if (S[pk(1, 1)] < S[pk(m, m)]) m = 1;
+    if (S[pk(2, 2)] < S[pk(m, m)]) m = 2;
+    const int i0 = (m + 1) % 3, j0 = (m + 2) % 3;
+    double fv[3][3];   // fv[k] = F v_k
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            fv[k][r] = F[3 * r] * Vm[k] + F[3 * r + 1] * Vm[3 + k] + F[3 * r + 2] * Vm[6 + k];
+    double U[3][3];   // U[k] = u_k
+    double sg[3];
+    {
+        double fi[3], fj[3], fm[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            fi[r] = (i0 == 0) ? fv[0][r] : (i0 == 1) ? fv[1][r] : fv[2][r];
+            fj[r] = (j0 == 0) ? fv[0][r] : (j0 == 1) ? fv[1][r] : fv[2][r];
+            fm[r] = (m == 0) ? fv[0][r] : (m == 1) ? fv[1][r] : fv[2][r];
+        }
+        const double si = sqrt(fi[0] * fi[0] + fi[1] * fi[1] + fi[2] * fi[2]);
+        double ui[3], uj[3], um[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) ui[r] = fi[r] / si;
+        const double pr = ui[0] * fj[0] + ui[1] * fj[1] + ui[2] * fj[2];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) uj[r] = fj[r] - pr * ui[r];
+        const double nj = sqrt(uj[0] * uj[0] + uj[1] * uj[1] + uj[2] * uj[2]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) uj[r] /= nj;
+        const double sj = uj[0] * fj[0] + uj[1] * fj[1] + uj[2] * fj[2];
+        cross3(ui, uj, um);
+        const double sm = um[0] * fm[0] + um[1] * fm[1] + um[2] * fm[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) U[k][r] = (k == i0) ? ui[r] : (k == j0) ? uj[r] : um[r];
+            sg[k] = (k == i0) ? si : (k == j0) ? sj : sm;
+        }
+    }
+    // g[a][k] = v_k . G_a
+    double G[4][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        G[1][j] = Dinv[j];
+        G[2][j] = Dinv[3 + j];
+        G[3][j] = Dinv[6 + j];
+        G[0][j] = -(Dinv[j] + Dinv[3 + j] + Dinv[6 + j]);
+    }
+    double g[4][3];
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            g[n][k] = G[n][0] * Vm[k] + G[n][1] * Vm[3 + k] + G[n][2] * Vm[6 + k];
+    int removed = 0;
+    auto remove = [&](double lambda, const double (&w)[12]) {
+        const double sc = Vd * lambda;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int bb = a; bb < 4; ++bb)
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const double wr = sc * w[3 * a + r], wc = w[3 * bb + c];
+                        if (staged) {
+                            HT* p = staged + 9 * up_index(a, bb) + 3 * r + c;
+                            *p = (HT)fma(-wr, wc, (double)*p);
+                        } else {
+                            double* p = full + (3 * a + r) * 12 + 3 * bb + c;
+                            *p = fma(-wr, wc, *p);
+                            if (a != bb) {
+                                double* q = full + (3 * bb + c) * 12 + 3 * a + r;
+                                *q = fma(-wr, wc, *q);
+                            }
+                        }
+                    }
+        ++removed;
+    };
+    const double h = 0.70710678118654752440;   // 1/sqrt(2)
+    // twist / flip pairs
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+#pragma unroll
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            const double lambda = a + sgn * b * sg[k];   // sgn -1: symmetric, +1: antisymmetric
+            if (!(lambda < 0.0)) continue;
+            const double sym = (sgn < 0) ? 1.0 : -1.0;
+            double w[12];
+#pragma unroll
+            for (int n = 0; n < 4; ++n)
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    w[3 * n + r] = h * (U[i][r] * g[n][j] + sym * U[j][r] * g[n][i]);
+            remove(lambda, w);
+        }
+    }
+    // stretch block
+    const double pv[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};
+    double A3[6];
+    A3[pk(0, 0)] = a + gam * sg[0] * sg[0] + lamd * pv[0] * pv[0];
+    A3[pk(1, 1)] = a + gam * sg[1] * sg[1] + lamd * pv[1] * pv[1];
+    A3[pk(2, 2)] = a + gam * sg[2] * sg[2] + lamd * pv[2] * pv[2];
+    A3[pk(1, 0)] = gam * sg[1] * sg[0] + lamd * pv[1] * pv[0] + b * sg[2];
+    A3[pk(2, 0)] = gam * sg[2] * sg[0] + lamd * pv[2] * pv[0] + b * sg[1];
+    A3[pk(2, 1)] = gam * sg[2] * sg[1] + lamd * pv[2] * pv[1] + b * sg[0];
+    double Q3[9];
+    jacobi3(A3, Q3);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const double lambda = A3[pk(e, e)];
+        if (!(lambda < 0.0)) continue;
+        double w[12];
+#pragma unroll
+        for (int n = 0; n < 4; ++n)
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                w[3 * n + r] = Q3[0 + e] * g[n][0] * U[0][r] + Q3[3 + e] * g[n][1] * U[1][r] +
+                               Q3[6 + e] * g[n][2] * U[2][r];
+        remove(lambda, w);
+    }
+    return removed;
+}
+
+template <typename R, typename HT, bool FPROJ>
 __device__ void eval_snh(const ElemLaunch& L, int scene, int blk, const SceneDev& S,
                          const ElemBlock& B, int64_t e, ThreadOut& o)
 {
@@ -360,7 +575,11 @@ __device__ void eval_snh(const ElemLaunch& L, int scene, int blk, const SceneDev
             double* full = L.out_H ? L.out_H + 144 * e : nullptr;
             write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
         }
-        if (L.project) {
+        if (FPROJ && L.project == 2) {
+            HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
+            double* full = L.out_H ? L.out_H + 144 * e : nullptr;
+            o.clamped = snh_fproj<HT>(xg, Dinv, B.V[e], B.mu[e], B.lam[e], staged, full) > 0;
+        } else if (L.project) {
             double M[45];
             snh_M<R>(C, M);
             o.clamped = queue_if_indefinite(L, scene, blk, e, M);
@@ -495,8 +714,9 @@ __device__ void eval_barrier(const ElemLaunch& L, int scene, int blk, const Scen
 }
 
 // KINDS: bit mask of the stencil kinds compiled in (1 SNH, 2 hinge, 4
-// barrier). A batch with SNH tets only runs the SNH-only instantiation,
-// which needs fewer registers than the one that can take every kind.
+// barrier), and 8 for the F-space projection of the SNH tets (project mode
+// 2). A batch with SNH tets only runs an SNH-only instantiation, which needs
+// fewer registers than the one that can take every kind.
 template <typename R, typename HT, int KINDS>
 __global__ void __launch_bounds__(kElemThreads)
 k_elements(ElemLaunch L)
@@ -518,7 +738,7 @@ k_elements(ElemLaunch L)
             if ((int)threadIdx.x < T.count) {
                 const int64_t e = T.start + threadIdx.x;
                 if ((KINDS & 1) && B.kind == SX_KIND_SNH_TET4)
-                    eval_snh<R, HT>(L, T.scene, T.blk, S, B, e, o);
+                    eval_snh<R, HT, (KINDS & 8) != 0>(L, T.scene, T.blk, S, B, e, o);
                 else if ((KINDS & 2) && B.kind == SX_KIND_HINGE4)
                     eval_hinge<R, HT>(L, S, B, e, o);
                 else if ((KINDS & 4) && B.kind == SX_KIND_PT_BARRIER)
@@ -799,13 +1019,21 @@ cudaError_t launch_gather_pairs(const int4* conn, const int* keep, const int* of
     return cudaGetLastError();
 }
 
-const void* elements_kernel(int precision, int snh_only)
+const void* elements_kernel(int precision, int variant)
 {
-    if (snh_only)
-        return precision == SX_FP32 ? (const void*)k_elements<float, float, 1>
-                                    : (const void*)k_elements<double, double, 1>;
-    return precision == SX_FP32 ? (const void*)k_elements<float, float, 7>
-                                : (const void*)k_elements<double, double, 7>;
+    const bool f = precision == SX_FP32;
+    switch (variant) {
+    case 1: return f ? (const void*)k_elements<float, float, 1> : (const void*)k_elements<double, double, 1>;
+    case 2: return f ? (const void*)k_elements<float, float, 15> : (const void*)k_elements<double, double, 15>;
+    case 3: return f ? (const void*)k_elements<float, float, 9> : (const void*)k_elements<double, double, 9>;
+    default: return f ? (const void*)k_elements<float, float, 7> : (const void*)k_elements<double, double, 7>;
+    }
+}
+
+int elements_variant(int kinds, int project)
+{
+    const bool snh_only = kinds == 1;
+    return project == 2 ? (snh_only ? 3 : 2) : (snh_only ? 1 : 0);
 }
 
 cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s)
@@ -819,12 +1047,16 @@ cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s)
             err = cudaMemsetAsync(L.clamp_bucket_count, 0, 10 * sizeof(int), s);
         if (err != cudaSuccess) return err;
     }
-    const bool snh_only = L.kinds == 1;
+    const int v = elements_variant(L.kinds, L.level >= 2 ? L.project : 0);
     if (L.precision == SX_FP32) {
-        if (snh_only) k_elements<float, float, 1><<<grid, kElemThreads, 0, s>>>(L);
+        if (v == 1) k_elements<float, float, 1><<<grid, kElemThreads, 0, s>>>(L);
+        else if (v == 2) k_elements<float, float, 15><<<grid, kElemThreads, 0, s>>>(L);
+        else if (v == 3) k_elements<float, float, 9><<<grid, kElemThreads, 0, s>>>(L);
         else k_elements<float, float, 7><<<grid, kElemThreads, 0, s>>>(L);
     } else {
-        if (snh_only) k_elements<double, double, 1><<<grid, kElemThreads, 0, s>>>(L);
+        if (v == 1) k_elements<double, double, 1><<<grid, kElemThreads, 0, s>>>(L);
+        else if (v == 2) k_elements<double, double, 15><<<grid, kElemThreads, 0, s>>>(L);
+        else if (v == 3) k_elements<double, double, 9><<<grid, kElemThreads, 0, s>>>(L);
         else k_elements<double, double, 7><<<grid, kElemThreads, 0, s>>>(L);
     }
     return cudaGetLastError();

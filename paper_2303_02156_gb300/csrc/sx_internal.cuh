@@ -187,8 +187,10 @@ cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s);
 cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s);
 int elements_block_threads();
 int clamp_block_threads();
-// the element kernel for a precision; snh_only: the SNH-only instantiation
-const void* elements_kernel(int precision, int snh_only);
+// the element kernel instantiations: variant 0 every kind, 1 SNH only, 2
+// every kind with the F-space projection, 3 SNH only with it
+const void* elements_kernel(int precision, int variant);
+int elements_variant(int kinds, int project);
 
 // point-triangle pair activation and order-preserving compaction
 // (sx_elements.cu)

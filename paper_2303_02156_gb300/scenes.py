@@ -263,11 +263,13 @@ def random_box_dims(n_tets_target: float, rng: np.random.Generator,
 
 
 def mixed_scene(n_grid: int = 55, n_sheet: int = 1000, n_pairs: int = 4_000_000,
-                seed: int = 3, kb: float = 1e-3, dhat: float = 1e-3, kappa: float = 1e4):
+                seed: int = 3, kb: float = 1e-3, dhat: float = 1e-3, kappa: float = 1e4,
+                pair_dmax: float = 1e-3):
     """SNH Kuhn block (``n_grid``^3 cubes, h = 1/n_grid, pinned bottom layer),
     a flat ``n_sheet`` x ``n_sheet`` quad sheet 1 m wide above it (hinge
     stencils, z noise 0.1 h_s) and ``n_pairs`` free points, each over its
-    own seeded sheet triangle at d ~ U(1e-4, 1e-3) m. Nodes are stacked
+    own seeded sheet triangle at d ~ U(1e-4, pair_dmax) m (pair_dmax > dhat
+    leaves the farther pairs inactive). Nodes are stacked
     block, then sheet, then points.
 
     Extra lumped masses (not given by the workload; a reading): sheet
@@ -284,7 +286,7 @@ def mixed_scene(n_grid: int = 55, n_sheet: int = 1000, n_pairs: int = 4_000_000,
     xb = jitter_state(m["X"], 0.02 / n_grid, seed + 1)
     sh = shell_sheet(n_sheet, length=1.0, z0=1.5, noise=0.1, seed=seed + 2, node_offset=nt)
     ns = sh["x"].shape[0]
-    bp = barrier_pairs(sh["x"], sh["tris"] - nt, n_pairs, 1e-4, 1e-3, seed=seed + 3,
+    bp = barrier_pairs(sh["x"], sh["tris"] - nt, n_pairs, 1e-4, pair_dmax, seed=seed + 3,
                        tri_node_offset=nt, point_node_offset=nt + ns)
     X = np.vstack([m["X"], sh["X"], bp["points"]])
     x = np.vstack([xb, sh["x"], bp["points"]])

@@ -22,6 +22,7 @@ SX_E, SX_EG, SX_EGH = 0, 1, 2
 SX_FP64, SX_FP32 = 0, 1
 SX_KIND_SNH_TET4, SX_KIND_HINGE4, SX_KIND_PT_BARRIER = 0, 1, 2
 SX_SERVER_MAX_LANES = 8
+SX_PROJECT_NONE, SX_PROJECT_ELEMENT, SX_PROJECT_MATERIAL = 0, 1, 2
 
 STATUS_NAMES = {0: "SX_OK", -1: "SX_EINVAL", -2: "SX_ENOMEM", -3: "SX_ECUDA", -4: "SX_ENAN",
                 -5: "SX_ENOTCONV", -6: "SX_ESTATE", -7: "SX_EDEGENERATE", -8: "SX_EBUDGET",

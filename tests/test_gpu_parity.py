@@ -595,3 +595,73 @@ def test_api_misuse_returns_status_codes(ctx):
     X = np.zeros((0, 3))
     assert sx.sx_scene_create(ctx.h, 0, X.ctypes.data, 3, None, C.byref(h)) == sx.SX_EINVAL
     s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [sx.SX_FP64, sx.SX_FP32])
+@pytest.mark.parametrize("jitter", [0.04, 0.45])
+def test_material_projection_parity(ctx, precision, jitter):
+    """project = 2: the SNH material Hessian clamped in the frame of the
+    signed SVD of F (closed form on the GPU) against the oracle's numerical
+    clamp of its explicit 9x9 d2psi/dF2."""
+    m, E, nu, x, snh, mass = _snh_case(dims=(6, 5, 4), seed=31, jitter=jitter)
+    s, eid = _gpu_snh_scene(ctx, m, E, nu, x)
+    out = s.eval_elements(eid, project=sx.SX_PROJECT_MATERIAL, precision=precision)
+    Ee, ge, He = orc.snh_batch(x, snh["tets"], snh["Dminv"], snh["V"], snh["mu"], snh["lam"],
+                               2, 2)
+    tol = TOL64 if precision == sx.SX_FP64 else TOL32
+    scale = snh["V"] * snh["mu"]
+    worst = 0.0
+    for e in range(Ee.size):
+        worst = max(worst, _relerr(out["H"][e], He[e], scale[e]))
+    assert worst <= tol, worst
+    w = np.linalg.eigvalsh(out["H"])
+    assert w.min() >= -(1e-9 if precision == sx.SX_FP64 else 1e-6) * np.abs(w).max()
+    s.close()
+
+
+@pytest.mark.gpu
+def test_material_projection_assembly_and_newton(ctx):
+    from paper_2303_02156_gb300.scene import Scene
+    # assembled: SNH block (material projection) + barriers (12x12 clamp)
+    m, sh, bp, X, x0, E, nu, extra, nt = _mixed_small()
+    N = X.shape[0]
+    s = Scene(ctx, X)
+    s.add_snh(m["tets"], E, nu, 1000.0)
+    s.add_hinge(sh["hinges"], sh["q"], sh["c"], 1e-3)
+    s.add_barrier(bp["pairs"], 1e-3, 1e4)
+    s.add_node_mass(extra)
+    s.finalize()
+    x = x0.copy()
+    x[:nt] = scenes.jitter_state(m["X"], 3e-3, 12)
+    s.set_state(x=x)
+    Eg = s.eval(sx.SX_EGH, sx.SX_PROJECT_MATERIAL, sx.SX_FP64)
+    rp, col, vals = s.bsr()
+    snh, mass, _ = orc.snh_scene_inputs(m["X"], m["tets"], E, nu, 1000.0)
+    mass_all = np.concatenate([mass, np.zeros(N - nt)]) + extra
+    sc = orc.Scene(N, mass=mass_all, snh=snh,
+                   hinge={"stencils": sh["hinges"], "q": sh["q"], "c": sh["c"], "kb": 1e-3},
+                   pt={"pairs": bp["pairs"], "dhat": 1e-3, "kappa": 1e4})
+    Eo, go, vo, bad = sc.eval(x, level=2, project=2)
+    assert bad == 0
+    assert abs(Eg - Eo) <= TOL64 * abs(Eo)
+    assert _relerr(vals, vo, 0) <= TOL64 and _relerr(s.grad(), go, 0) <= TOL64
+    assert s.stats()["clamped"] > 0
+    s.close()
+    # a C1 backward-Euler step with the material projection
+    m, E, nu = _c1()
+    snh, mass, _ = orc.snh_scene_inputs(m["X"], m["tets"], E, nu, 1000.0)
+    sc = orc.Scene(m["X"].shape[0], mass=mass, snh=snh, pinned=m["pinned"])
+    xo, vo, st, rep = sc.newton_step(m["X"], np.zeros_like(m["X"]), 0.01, project=2)
+    assert st == 0
+    s = Scene(ctx, m["X"])
+    s.add_snh(m["tets"], E, nu, 1000.0)
+    s.set_pinned(m["pinned"])
+    s.set_gravity((0.0, 0.0, -9.81))
+    s.finalize()
+    rc, r = s.newton_step(0.01, newton_tol=1e-8, pcg_tol=1e-10, project=sx.SX_PROJECT_MATERIAL)
+    assert rc == sx.SX_OK
+    xg, vg = s.get_state()
+    ref = np.abs(xo - m["X"]).max()
+    assert np.abs(xg - xo).max() <= 1e-8 * ref + 1e-12
+    s.close()
