@@ -340,6 +340,48 @@ def run_mixed(ctx, stream, flush, reps=5):
     out["note"] = ("one particle per pair (no vertex sharing among contact points), so the "
                    "barrier gathers reuse less than a real contact scene would")
     s.close()
+    # changing contact pairs: the same scene with pair distances up to 2 dhat
+    # (about half the pairs inactive), activation compaction + pattern
+    # rebuild, and the FP32 pass before and after
+    w = scenes.mixed_scene(pair_dmax=2e-3)
+    s = Scene(ctx, w["X"], stream=sh)
+    s.add_snh(w["tets"], w["E"], w["nu"], 1000.0)
+    s.add_hinge(w["hinges"], w["q"], w["c"], w["kb"])
+    eb = s.add_barrier(w["pairs"], w["dhat"], w["kappa"])
+    s.add_node_mass(w["extra_mass"])
+    s.set_pinned(w["pinned"])
+    s.finalize()
+    s.set_state(x=w["x"])
+
+    def egh_ms():
+        for _ in range(2):
+            ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, sx.SX_FP32, None, sh))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(3):
+            flush.zero_()
+            e0.record(stream)
+            ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, sx.SX_FP32, None, sh))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    before = egh_ms()
+    nnz0 = s.info()["nnzb"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_act = s.compact_pairs(eb)
+    torch.cuda.synchronize()
+    t_compact = (time.perf_counter() - t0) * 1e3
+    after = egh_ms()
+    out["contact_compaction"] = {
+        "pairs": int(w["pairs"].shape[0]), "active": int(n_act), "pair_d": "U(1e-4, 2e-3) m",
+        "compact_and_rebuild_ms": t_compact, "nnzb_before": int(nnz0),
+        "nnzb_after": int(s.info()["nnzb"]), "fp32_egh_ms_before": before,
+        "fp32_egh_ms_after": after}
+    s.close()
     return out
 
 
@@ -568,6 +610,31 @@ def main():
             "bsr_rel_err_vs_fp64": float(np.linalg.norm(v32.astype(np.float64) - v64) / np.linalg.norm(v64)),
             "grad_rel_err_vs_fp64": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64))}
 
+    # ---- the material projection (project = 2, closed form in the SVD frame
+    # of F) beside the element-Hessian clamp: pass time and how far the
+    # assembled Hessian moves (a different PSD matrix by construction)
+    matproj = {}
+    for name, prec in (("fp64", sx.SX_FP64), ("fp32", sx.SX_FP32)):
+        s.set_state(x=x)
+        for _ in range(3):
+            ctx.check(sx.sx_eval(s.h, sx.SX_EGH, sx.SX_PROJECT_MATERIAL, prec, None, sh))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(5):
+            flush.zero_()
+            e0.record(stream)
+            ctx.check(sx.sx_eval(s.h, sx.SX_EGH, sx.SX_PROJECT_MATERIAL, prec, None, sh))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        matproj[name] = {"ms_per_step": med, "elements_per_s": T / (med / 1e3),
+                         "projected": s.stats()["clamped"]}
+    ctx.check(sx.sx_eval(s.h, sx.SX_EGH, sx.SX_PROJECT_MATERIAL, sx.SX_FP64, None, sh))
+    _, _, vm = s.bsr()
+    matproj["bsr_rel_diff_vs_element_clamp"] = float(np.linalg.norm(vm - v64) / np.linalg.norm(v64))
+
     # ---- roofline of the dominant kernel (the FP64 eigen-clamp). The work
     # per projected stencil is the FP64 flops this algorithm executes (ncu
     # count of DFMA x 2 + DMUL + DADD, profiles/k_clamp_snh_cube_40.md);
@@ -643,6 +710,16 @@ def main():
         for v in traj.values():
             v.pop("x")
         newton["trajectory_10_steps"] = traj
+        # one step with the material projection, and its deviation
+        s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+        rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-8, pcg_tol=1e-10,
+                                project=sx.SX_PROJECT_MATERIAL)
+        xm = s.get_state()[0]
+        newton["material_projection"] = {
+            "status": sx.STATUS_NAMES.get(rc, rc), "ms": rep["ms"],
+            "newton_iters": rep["newton_iters"], "pcg_iters": rep["pcg_iters"],
+            "dx_rel_diff_vs_element_clamp": float(np.abs(xm - x64).max() /
+                                                  max(np.abs(x64 - m["X"]).max(), 1e-300))}
 
     # ---- serving: Poisson stream of scene requests (bounded sample)
     serving = None
@@ -676,6 +753,7 @@ def main():
             "phase_ms_per_step": {k: round(v, 4) for k, v in phases.items()},
             "projected_fraction": clamped / T, "fp32": fp32, "newton_step": newton,
             "serving": serving, "mixed": mixed, "batched": batched, "autotune": tune,
+            "material_projection": matproj,
             "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
                         "max": max(step_ms)},
         }
