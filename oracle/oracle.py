@@ -62,6 +62,12 @@ def lib():
                                         _dp, _dp, _dp]
     L.orc_snh_batch.argtypes = [C.c_int, _dp, _ip, _dp, _dp, _dp, _dp, C.c_int,
                                 C.c_int, _dp, C.c_void_p, C.c_void_p]
+    L.orc_tet_element.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double,
+                                  C.c_void_p, _dp, _dp, _dp]
+    L.orc_tet_element.restype = C.c_int
+    L.orc_tet_batch.argtypes = [C.c_int, C.c_int, _dp, _ip, _dp, _dp, _dp, _dp, C.c_void_p,
+                                C.c_int, C.c_int, _dp, C.c_void_p, C.c_void_p]
+    L.orc_tet_batch.restype = C.c_int
     L.orc_hinge_element.argtypes = [_dp, _dp, C.c_double, C.c_double, _dp, _dp, _dp]
     L.orc_hinge_batch.argtypes = [C.c_int, _dp, _ip, _dp, _dp, C.c_double, C.c_int,
                                   _dp, C.c_void_p, C.c_void_p]
@@ -179,6 +185,50 @@ def snh_batch(x, tets, Dminv, V, mu, lam, level=LEVEL_EGH, project=False):
     lib().orc_snh_batch(T, _f64(x), tets, _f64(Dminv), _f64(V), _f64(mu), _f64(lam),
                         level, int(project), E, _ptr(g), _ptr(H))
     return E, g, H
+
+
+# ---------------------------------------------------------------- other models
+MODEL_SNH, MODEL_NH, MODEL_STVK, MODEL_COROT, MODEL_ARAP = 0, 1, 2, 3, 4
+
+
+def tet_element(model, xe, Dminv, V, mu, lam, R=None):
+    """E, g, H of one tet of any model; returns (bad, E, g, H), bad = 1 for
+    an invalid state (Neo-Hookean J <= 0)."""
+    E = np.zeros(1); g = np.zeros(12); H = np.zeros(144)
+    Rp = None if R is None else _f64(R).ravel()
+    bad = lib().orc_tet_element(int(model), _f64(xe).ravel(), _f64(Dminv).ravel(), float(V),
+                                float(mu), float(lam), _ptr(Rp), E, g, H)
+    return bad, E[0], g, H.reshape(12, 12)
+
+
+def tet_batch(model, x, tets, Dminv, V, mu, lam, R=None, level=LEVEL_EGH, project=False):
+    tets = _i32(tets); T = tets.shape[0]
+    E = np.empty(T)
+    g = np.empty((T, 12)) if level >= 1 else None
+    H = np.empty((T, 12, 12)) if level >= 2 else None
+    Rp = None if R is None else _f64(R).reshape(T, 9)
+    bad = lib().orc_tet_batch(int(model), T, _f64(x), tets, _f64(Dminv), _f64(V), _f64(mu),
+                              _f64(lam), _ptr(Rp), level, int(project), E, _ptr(g), _ptr(H))
+    return E, g, H, bad
+
+
+def deformation_gradients(x, tets, Dminv):
+    """F = Ds Dm^-1 per tet (T x 3 x 3), numpy."""
+    x = _f64(x).reshape(-1, 3); tets = np.asarray(tets)
+    Ds = np.stack([x[tets[:, k]] - x[tets[:, 0]] for k in (1, 2, 3)], axis=2)
+    return Ds @ _f64(Dminv).reshape(-1, 3, 3)
+
+
+def lagged_rotations(x, tets, Dminv):
+    """Rotation of the polar decomposition of F per tet (T x 9 row-major),
+    by numpy's SVD (library routine): F = U S V^T, R = U V^T, with the
+    column of U of the smallest singular value negated when det(U V^T) < 0,
+    so R is a rotation (the nearest one to F)."""
+    F = deformation_gradients(x, tets, Dminv)
+    U, _, Vt = np.linalg.svd(F)
+    neg = np.linalg.det(U @ Vt) < 0
+    U[neg, :, 2] *= -1
+    return (U @ Vt).reshape(-1, 9)
 
 
 # ---------------------------------------------------------------- hinge
@@ -300,6 +350,7 @@ class _OrcScene(C.Structure):
         ("kappa", C.c_double), ("pinned", C.c_void_p),
         ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("slots", C.c_void_p),
         ("diag_slot", C.c_void_p), ("nnzb", C.c_longlong),
+        ("snh_model", C.c_int), ("snh_R", C.c_void_p),
     ]
 
 
@@ -324,6 +375,8 @@ class Scene:
     def __init__(self, N, mass=None, snh=None, hinge=None, pt=None, pinned=None):
         self.N = int(N)
         self._keep = []
+        self.R = None
+        self.model = MODEL_SNH
         s = _OrcScene()
         s.N = self.N
         self.mass = None if mass is None else _f64(mass)
@@ -336,6 +389,15 @@ class Scene:
             s.n_snh = tets.shape[0]
             s.snh_tets, s.snh_Dminv, s.snh_V = _ptr(tets), _ptr(Dminv), _ptr(V)
             s.snh_mu, s.snh_lam = _ptr(mu), _ptr(lam)
+            s.snh_model = int(snh.get("model", MODEL_SNH))
+            self.model = s.snh_model
+            self.tets, self.Dminv = tets, Dminv
+            self.R = None
+            if s.snh_model in (MODEL_COROT, MODEL_ARAP):
+                R = snh.get("R")
+                self.R = (np.tile(np.eye(3).ravel(), (tets.shape[0], 1)) if R is None
+                          else _f64(R).reshape(-1, 9).copy())
+                s.snh_R = _ptr(self.R)
             conns.append(tets)
         if hinge is not None:
             st, q, c = _i32(hinge["stencils"]), _f64(hinge["q"]), _f64(hinge["c"])
@@ -378,10 +440,19 @@ class Scene:
                                    int(project), C.byref(E), _ptr(grad), _ptr(vals))
         return E.value, grad, vals, bad
 
+    def set_rotations(self, R):
+        """Lagged rotations of the tet block (COROT / ARAP), 9 per tet."""
+        self.R[:] = _f64(R).reshape(self.R.shape)
+
     def newton_step(self, x, v, dt, gravity=(0.0, 0.0, -9.81), newton_tol=1e-8,
                     pcg_tol=1e-10, max_newton=100, max_pcg=10000, max_halvings=30,
                     armijo_c=1e-4, project=True):
+        """One backward-Euler step. The lagged rotations of a COROT / ARAP
+        block are taken at the start-of-step state and held for the step
+        (§7.1: rotations constant per time step)."""
         x = _f64(x).ravel().copy(); v = _f64(v).ravel().copy()
+        if self.R is not None:
+            self.set_rotations(lagged_rotations(x.reshape(-1, 3), self.tets, self.Dminv))
         o = _OrcOpts(newton_tol, pcg_tol, max_newton, max_pcg, max_halvings, armijo_c,
                      int(project))
         r = _OrcReport()
@@ -389,6 +460,14 @@ class Scene:
                                    C.byref(o), x, v, C.byref(r))
         rep = {k: getattr(r, k) for k, _ in _OrcReport._fields_}
         return x.reshape(-1, 3), v.reshape(-1, 3), st, rep
+
+
+def tet_scene_inputs(model, X, tets, E, nu, rho=1000.0):
+    """Rest precompute of a tet block of any model: the SNH model takes the
+    re-parameterized (mu', lambda'), the others the plain Lame pair."""
+    d, m, bad = snh_scene_inputs(X, tets, E, nu, rho, literal=(model != MODEL_SNH))
+    d["model"] = model
+    return d, m, bad
 
 
 def snh_scene_inputs(X, tets, E, nu, rho=1000.0, literal=False):

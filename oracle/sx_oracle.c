@@ -14,6 +14,10 @@
  *     [App. B, "Eq. 14 from Smith et al."]; derivatives by the chain rule
  *     through P = dpsi/dF and d2psi/dF2 and the constant 9x12 map vec(F) =
  *     B xhat built from Dm^-1 [App. A, tet4 shape functions].
+ *   - The other tet4 densities of §7.1 / App. B (Neo-Hookean, St.
+ *     Venant-Kirchhoff, fixed co-rotational and ARAP with lagged rotations)
+ *     written as plain expressions of F and differentiated by second-order
+ *     forward-mode arithmetic in the 12 stencil coordinates.
  *   - Quadratic hinge bending E = k_b/2 x^T Q x [§6.3, Eq. 13].
  *   - IPC log barrier E = -k (d - dhat)^2 ln(d/dhat) on the unsigned
  *     point-triangle distance [§6.4, Eq. 15], active only for d < dhat
@@ -748,6 +752,222 @@ int orc_barrier_batch(int P, const double* x, const int* pairs, double dhat,
 }
 
 /* ------------------------------------------------------------------ */
+/* Other tet4 densities (§7.1 "Non-linear material models", App. B):    */
+/* Neo-Hookean, St. Venant-Kirchhoff, fixed co-rotational and ARAP with */
+/* a volume term, the two co-rotational ones with a lagged rotation R   */
+/* ------------------------------------------------------------------ */
+
+#define ORC_MODEL_SNH 0
+#define ORC_MODEL_NH 1
+#define ORC_MODEL_STVK 2
+#define ORC_MODEL_COROT 3
+#define ORC_MODEL_ARAP 4
+
+/* u - ln(1 + u) without cancellation: for |u| < 1/16 the alternating
+ * series sum_{k >= 2} (-1)^k u^k / k, up to k = 20 (the tail is below
+ * 1e-20 of the sum there); otherwise the direct difference. */
+static double u_minus_log1p(double u)
+{
+    if (fabs(u) < 0.0625) {
+        double s = 0.0, p = u * u;
+        for (int k = 2; k <= 20; ++k) {
+            s += ((k & 1) ? -p : p) / (double)k;
+            p *= u;
+        }
+        return s;
+    }
+    return u - log1p(u);
+}
+
+/* F_ij = sum_a x_{a,i} G_{a,j} as second-order jets in the 12 stencil
+ * coordinates (F is linear in them: constant gradient, zero Hessian). */
+static void tet_F_jets(const double* xe, const double Dminv[9], q2 F[9])
+{
+    double B[9 * 12];
+    tet_B(Dminv, B);
+    for (int r = 0; r < 9; ++r) {
+        q2_const(&F[r], 0.0);
+        for (int c = 0; c < 12; ++c) {
+            F[r].v += B[r * 12 + c] * xe[c];
+            F[r].g[c] = B[r * 12 + c];
+        }
+    }
+}
+
+static void q2_sq_sum(q2* r, const q2* a, int n)
+{
+    q2 s;
+    q2_const(&s, 0.0);
+    for (int k = 0; k < n; ++k) {
+        q2 t;
+        q2_mul(&t, &a[k], &a[k]);
+        q2_add(&s, &s, &t, 1.0);
+    }
+    *r = s;
+}
+
+/* J - 1 = det(I + D) - 1 = tr D + (sum of principal 2x2 minors of D) + det D
+ * for D = F - I, as a jet (no O(1) quantity is subtracted). */
+static void q2_jm1(q2* r, const q2 D[9])
+{
+    q2 s, t, u;
+    q2_add(&s, &D[0], &D[4], 1.0);
+    q2_add(&s, &s, &D[8], 1.0);
+    static const int mi[3][4] = {{0, 4, 1, 3}, {0, 8, 2, 6}, {4, 8, 5, 7}};
+    for (int m = 0; m < 3; ++m) {
+        q2_mul(&t, &D[mi[m][0]], &D[mi[m][1]]);
+        q2_mul(&u, &D[mi[m][2]], &D[mi[m][3]]);
+        q2_add(&t, &t, &u, -1.0);
+        q2_add(&s, &s, &t, 1.0);
+    }
+    /* det D by the permutation sum eps_ijk D_0i D_1j D_2k */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) {
+                int e = levi(i, j, k);
+                if (!e) continue;
+                q2_mul(&t, &D[0 * 3 + i], &D[1 * 3 + j]);
+                q2_mul(&t, &t, &D[2 * 3 + k]);
+                q2_add(&s, &s, &t, (double)e);
+            }
+    *r = s;
+}
+
+/* psi of a non-SNH model as a jet in the stencil coordinates. Returns 1
+ * for a state where the density is undefined (Neo-Hookean with J <= 0).
+ * Each density is written as its definition with F = I + D:
+ *   NH    mu/2 (Ic - 3) - mu ln J + lambda/2 ln^2 J (Smith et al. Eq. 5; the
+ *         text form of §3.1 prints +mu ln J, READING: the minus sign, the
+ *         only one for which the rest state is stress-free), expanded as
+ *         mu/2 |D|^2 - mu (minors + det D) + mu (u - ln(1+u))
+ *         + lambda/2 ln^2(1+u), u = J - 1, which is the same function;
+ *   StVK  mu |E|^2 + lambda/2 tr(E)^2, E = (F^T F - I)/2 = (D + D^T + D^T D)/2;
+ *   COROT mu |F - R|^2 + lambda/2 (J - 1)^2;
+ *   ARAP  mu/2 (Ic - 2 tr(F^T R) + 3) + lambda/2 (J - 1)^2, written as
+ *         mu/2 |F - R|^2 (equal for a rotation R, |R|^2 = 3).
+ * R (row-major) is constant: the rotation is lagged (held for the time
+ * step), so no derivative of R enters. */
+static int tet_psi_jet(int model, const q2 F[9], const double R[9], double mu, double lam,
+                       q2* psi)
+{
+    q2 D[9];
+    for (int k = 0; k < 9; ++k) {
+        D[k] = F[k];
+        if (k % 4 == 0) D[k].v -= 1.0;
+    }
+    q2 t, u;
+    if (model == ORC_MODEL_NH) {
+        q2 jm1;
+        q2_jm1(&jm1, D);
+        if (!(jm1.v > -1.0)) return 1;
+        q2_sq_sum(psi, D, 9);
+        q2_apply(psi, psi, 0.5 * mu * psi->v, 0.5 * mu, 0.0);
+        /* minors + det D = (J - 1) - tr D */
+        q2_add(&t, &jm1, &D[0], -1.0);
+        q2_add(&t, &t, &D[4], -1.0);
+        q2_add(&t, &t, &D[8], -1.0);
+        q2_add(psi, psi, &t, -mu);
+        const double w = jm1.v, ip = 1.0 / (1.0 + w);
+        /* f(u) = u - ln(1+u): f' = u/(1+u), f'' = 1/(1+u)^2 */
+        q2_apply(&t, &jm1, u_minus_log1p(w), w * ip, ip * ip);
+        q2_add(psi, psi, &t, mu);
+        /* ln(1+u): derivatives 1/(1+u), -1/(1+u)^2; then its square */
+        q2_apply(&u, &jm1, log1p(w), ip, -ip * ip);
+        q2_mul(&t, &u, &u);
+        q2_add(psi, psi, &t, 0.5 * lam);
+        return 0;
+    }
+    if (model == ORC_MODEL_STVK) {
+        q2 E[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                q2 s;
+                q2_add(&s, &D[i * 3 + j], &D[j * 3 + i], 1.0);
+                for (int m = 0; m < 3; ++m) {
+                    q2_mul(&t, &D[m * 3 + i], &D[m * 3 + j]);
+                    q2_add(&s, &s, &t, 1.0);
+                }
+                q2_apply(&E[i * 3 + j], &s, 0.5 * s.v, 0.5, 0.0);
+            }
+        q2_sq_sum(psi, E, 9);
+        q2_apply(psi, psi, mu * psi->v, mu, 0.0);
+        q2_add(&t, &E[0], &E[4], 1.0);
+        q2_add(&t, &t, &E[8], 1.0);
+        q2_mul(&u, &t, &t);
+        q2_add(psi, psi, &u, 0.5 * lam);
+        return 0;
+    }
+    /* COROT / ARAP */
+    q2 FR[9];
+    for (int k = 0; k < 9; ++k) {
+        FR[k] = F[k];
+        FR[k].v -= R[k];
+    }
+    q2_sq_sum(psi, FR, 9);
+    const double c = (model == ORC_MODEL_COROT) ? mu : 0.5 * mu;
+    q2_apply(psi, psi, c * psi->v, c, 0.0);
+    q2 jm1;
+    q2_jm1(&jm1, D);
+    q2_mul(&t, &jm1, &jm1);
+    q2_add(psi, psi, &t, 0.5 * lam);
+    return 0;
+}
+
+/* One tet of any model: E = V psi, g = V dpsi/dx, H = V d2psi/dx2 (the
+ * SNH model goes through orc_snh_element). R: row-major 3x3, used by
+ * COROT and ARAP only (may be NULL otherwise). Returns 1 for an invalid
+ * state (NH with J <= 0; E, g and H are then zero). */
+int orc_tet_element(int model, const double* xe, const double* Dminv, double V,
+                    double mu, double lam, const double* R, double* E, double* g, double* H)
+{
+    if (model == ORC_MODEL_SNH) {
+        orc_snh_element(xe, Dminv, V, mu, lam, E, g, H);
+        return 0;
+    }
+    q2 F[9], psi;
+    tet_F_jets(xe, Dminv, F);
+    static const double I3[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (tet_psi_jet(model, F, R ? R : I3, mu, lam, &psi)) {
+        *E = 0.0;
+        if (g) memset(g, 0, 12 * sizeof(double));
+        if (H) memset(H, 0, 144 * sizeof(double));
+        return 1;
+    }
+    *E = V * psi.v;
+    if (g)
+        for (int c = 0; c < 12; ++c) g[c] = V * psi.g[c];
+    if (H)
+        for (int c = 0; c < 144; ++c) H[c] = V * psi.H[c];
+    return 0;
+}
+
+/* Batch of one model. project: 0 none, 1 clamp of the 12x12, 2 clamp of
+ * d2psi/dF2 for SNH (READING: other models have no F-space projection
+ * and take the 12x12 clamp). R: 9 per tet (COROT / ARAP). Returns the
+ * number of tets in an invalid state. */
+int orc_tet_batch(int model, int T, const double* x, const int* tets, const double* Dminv,
+                  const double* V, const double* mu, const double* lam, const double* R,
+                  int level, int project, double* E_e, double* g_e, double* H_e)
+{
+    if (model == ORC_MODEL_SNH) {
+        orc_snh_batch(T, x, tets, Dminv, V, mu, lam, level, project, E_e, g_e, H_e);
+        return 0;
+    }
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)
+    for (int e = 0; e < T; ++e) {
+        double xe[12];
+        gather4(x, tets + 4 * e, xe);
+        bad += orc_tet_element(model, xe, Dminv + 9 * e, V[e], mu[e], lam[e],
+                               R ? R + 9 * (size_t)e : NULL, E_e + e,
+                               level >= 1 ? g_e + 12 * (size_t)e : NULL,
+                               level >= 2 ? H_e + 144 * (size_t)e : NULL);
+        if (level >= 2 && project) orc_clamp_psd(12, H_e + 144 * (size_t)e);
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
 /* 3x3 block CRS pattern and slot maps (§5.3)                           */
 /* ------------------------------------------------------------------ */
 
@@ -997,11 +1217,16 @@ typedef struct {
     const int* slots;
     const int* diag_slot;
     long long nnzb;
+    /* density of the tet block (ORC_MODEL_*) and its lagged rotations
+     * (9 per tet, COROT / ARAP) */
+    int snh_model;
+    const double* snh_R;
 } orc_scene;
 
 /* Full evaluation of E_BE = inertia + sum of element energies at x
- * (Eq. 2 with Eq. 5). level as above. Returns the number of barrier pairs
- * in an invalid (d <= 0) state. grad/vals are overwritten. */
+ * (Eq. 2 with Eq. 5). level as above. Returns the number of stencils in
+ * an invalid state (barrier d <= 0, Neo-Hookean J <= 0). grad/vals are
+ * overwritten. */
 static int scene_eval_impl(const orc_scene* s, const double* x, const double* x0,
                            const double* xt, double dt, int level, int project,
                            double* E_out, double* grad, double* vals)
@@ -1022,8 +1247,8 @@ static int scene_eval_impl(const orc_scene* s, const double* x, const double* x0
         const int* conn;
         if (kind == 0) {
             conn = s->snh_tets;
-            orc_snh_batch(n, x, conn, s->snh_Dminv, s->snh_V, s->snh_mu, s->snh_lam,
-                          level, project, Ee, ge, He);
+            bad += orc_tet_batch(s->snh_model, n, x, conn, s->snh_Dminv, s->snh_V, s->snh_mu,
+                                 s->snh_lam, s->snh_R, level, project, Ee, ge, He);
         } else if (kind == 1) {
             conn = s->hinge;
             orc_hinge_batch(n, x, conn, s->hinge_q, s->hinge_c, s->kb, level, Ee, ge, He);
