@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batch-scenes", type=int, default=512)
+    p.add_argument("--no-models", action="store_true")
     return p.parse_args()
 
 
@@ -382,6 +383,53 @@ def run_mixed(ctx, stream, flush, reps=5):
         "nnzb_after": int(s.info()["nnzb"]), "fp32_egh_ms_before": before,
         "fp32_egh_ms_after": after}
     s.close()
+    return out
+
+
+# ------------------------------------------------------------------ other densities
+def run_models(ctx, stream, flush, m, E, nu, x, reps=5):
+    """The bench cube with each of the other tet4 densities (§7.1): one
+    E + g + projected H + assembly pass at the jittered state (FP64, FP32)
+    and one backward-Euler Newton step from rest (FP64, dt = 0.005)."""
+    import numpy as np
+    import torch
+    from paper_2303_02156_gb300 import sx
+    from paper_2303_02156_gb300.scene import Scene
+    sh = stream.cuda_stream
+    T = m["tets"].shape[0]
+    out = {}
+    names = {sx.SX_MODEL_NH: "neo_hookean", sx.SX_MODEL_STVK: "stvk",
+             sx.SX_MODEL_COROT: "fixed_corotated", sx.SX_MODEL_ARAP: "arap"}
+    for model, name in names.items():
+        s = Scene(ctx, m["X"], stream=sh)
+        s.add_tet(model, m["tets"], E, nu, 1000.0)
+        s.set_pinned(m["pinned"])
+        s.set_gravity((0.0, 0.0, -9.81))
+        s.finalize()
+        s.set_state(x=x)
+        r = {}
+        for pname, prec in (("fp64", sx.SX_FP64), ("fp32", sx.SX_FP32)):
+            for _ in range(3):
+                ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                e0.record(stream)
+                ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            med = statistics.median(ms)
+            r[pname] = {"ms_per_step": med, "elements_per_s": T / (med / 1e3),
+                        "projected": s.stats()["clamped"]}
+        s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+        rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-8, pcg_tol=1e-10)
+        r["newton_step"] = {"status": sx.STATUS_NAMES.get(rc, rc), "ms": rep["ms"],
+                            "newton_iters": rep["newton_iters"], "pcg_iters": rep["pcg_iters"]}
+        out[name] = r
+        s.close()
     return out
 
 
@@ -721,6 +769,9 @@ def main():
             "dx_rel_diff_vs_element_clamp": float(np.abs(xm - x64).max() /
                                                   max(np.abs(x64 - m["X"]).max(), 1e-300))}
 
+    # ---- the other tet4 densities on the same cube
+    models = None if args.no_models else run_models(ctx, stream, flush, m, E, nu, x)
+
     # ---- serving: Poisson stream of scene requests (bounded sample)
     serving = None
     if args.serve_requests > 0:
@@ -753,7 +804,7 @@ def main():
             "phase_ms_per_step": {k: round(v, 4) for k, v in phases.items()},
             "projected_fraction": clamped / T, "fp32": fp32, "newton_step": newton,
             "serving": serving, "mixed": mixed, "batched": batched, "autotune": tune,
-            "material_projection": matproj,
+            "material_projection": matproj, "models": models,
             "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
                         "max": max(step_ms)},
         }

@@ -74,9 +74,31 @@ extern "C" {
 #define SX_PROJECT_MATERIAL 2
 
 /* ---- energy kinds ----------------------------------------------------- */
-#define SX_KIND_SNH_TET4 0
+#define SX_KIND_SNH_TET4 0     /* linear tets of any SX_MODEL_* density */
+#define SX_KIND_TET4 SX_KIND_SNH_TET4
 #define SX_KIND_HINGE4 1
 #define SX_KIND_PT_BARRIER 2
+
+/* ---- tet4 densities (§7.1 "Non-linear material models", App. B) -------
+ * SNH    Stable Neo-Hookean (§3.1 Eq. 7), parameters mu', lambda' as in
+ *        sx_add_snh_tet4;
+ * NH     Neo-Hookean mu/2 (Ic - 3) - mu ln J + lambda/2 ln^2 J (the text
+ *        form of §3.1 prints +mu ln J; the minus sign is the one whose rest
+ *        state is stress-free); J <= 0 is an invalid state (SX_ESTATE, like
+ *        a barrier pair at d <= 0);
+ * STVK   St. Venant-Kirchhoff mu |E|^2 + lambda/2 tr(E)^2, E = (F^T F - I)/2;
+ * COROT  fixed co-rotational mu |F - R|^2 + lambda/2 (J - 1)^2;
+ * ARAP   as-rigid-as-possible with a volume term
+ *        mu/2 |F - R|^2 + lambda/2 (J - 1)^2.
+ * COROT and ARAP use a lagged rotation R per tet (constant within a time
+ * step, §7.1; not differentiated): the rotation of the polar decomposition
+ * of F, taken at the start of every Newton step and by
+ * sx_update_rotations; the identity when the block is added. */
+#define SX_MODEL_SNH 0
+#define SX_MODEL_NH 1
+#define SX_MODEL_STVK 2
+#define SX_MODEL_COROT 3
+#define SX_MODEL_ARAP 4
 
 typedef struct sx_ctx sx_ctx;
 typedef struct sx_scene sx_scene;
@@ -122,6 +144,27 @@ int sx_scene_destroy(sx_scene* scene);
 int sx_add_snh_tet4(sx_scene* scene, const int32_t* tets, int64_t n,
                     const double* young, const double* poisson, double density,
                     int literal_params, void* stream, int* energy_id);
+
+/* Linear tets of density `model` (SX_MODEL_*). Arguments and rest
+ * precompute as sx_add_snh_tet4; SX_MODEL_SNH takes the re-parameterized
+ * (mu', lambda'), the other models the plain Lame pair (mu, lambda).
+ * SX_EINVAL for an unknown model. Synchronous. */
+int sx_add_tet4(sx_scene* scene, int model, const int32_t* tets, int64_t n,
+                const double* young, const double* poisson, double density, void* stream,
+                int* energy_id);
+
+/* Lagged rotations of the COROT / ARAP blocks of a scene (§7.1).
+ * sx_update_rotations: R of every tet of those blocks := the rotation of
+ * the polar decomposition of F at the current state (F = U S V^T with
+ * singular values in descending order, R = U V^T, the column of U of the
+ * smallest singular value negated if that makes R a rotation; the identity
+ * for F = 0). Stream-ordered.
+ * sx_get_rotations / sx_set_rotations: n x 9 doubles (row-major 3x3 per
+ * tet) of block `energy_id` (COROT / ARAP, else SX_EINVAL), host or
+ * device; get synchronizes `stream`. */
+int sx_update_rotations(sx_scene* scene, void* stream);
+int sx_get_rotations(sx_scene* scene, int energy_id, double* R, void* stream);
+int sx_set_rotations(sx_scene* scene, int energy_id, const double* R, void* stream);
 
 /* Quadratic hinge bending E = k_b/2 x^T Q x (§6.3, Eq. 13) over 4-node
  * stencils (e0, e1, o0, o1): shared edge then the two opposite vertices.
@@ -194,7 +237,8 @@ int sx_set_inertia(sx_scene* scene, double dt, const double* x_tilde, void* stre
  * SX_PROJECT_MATERIAL (2: for SNH tets the material Hessian d2psi/dF2 is
  * clamped instead, H = V B^T proj(d2psi/dF2) B, in closed form in the frame
  * of the signed SVD of F (FP64) -- a different PSD Hessian, above the plain
- * one, cheaper than the 12x12 clamp; barriers as in 1). precision: SX_FP64
+ * one, cheaper than the 12x12 clamp; tets of the other models and barriers
+ * as in 1). precision: SX_FP64
  * or SX_FP32. E_out (host, may be NULL)
  * receives the total energy; the assembled gradient (FP64) and BSR values
  * stay on the device (sx_get_grad, sx_get_bsr). Synchronous when E_out is
@@ -232,7 +276,8 @@ int sx_scene_info(sx_scene* scene, int64_t* n_nodes, int64_t* nnzb, int64_t* n_s
 /* Kind (SX_KIND_*) and element count of energy block `energy_id`. */
 int sx_block_info(sx_scene* scene, int energy_id, int* kind, int64_t* n);
 /* Counters of the last evaluation: elements whose Hessian was projected
- * (SX_EGH with project), barrier pairs with d <= 0, non-finite flag.
+ * (SX_EGH with project), stencils in an invalid state (barrier pairs with
+ * d <= 0, Neo-Hookean tets with J <= 0), non-finite flag.
  * Synchronizes `stream`. */
 int sx_eval_stats(sx_scene* scene, int* clamped, int* bad_state, int* nonfinite,
                   void* stream);

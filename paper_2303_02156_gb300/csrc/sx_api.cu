@@ -24,6 +24,8 @@ namespace {
 
 struct BlockHost {
     int kind = 0;
+    int model = SX_MODEL_SNH;   // tet4 blocks
+    double* Rot = nullptr;      // [9][n] lagged rotations (COROT, ARAP)
     int64_t n = 0;
     int64_t base = 0;
     int4* conn = nullptr;
@@ -58,7 +60,7 @@ struct sx_ctx {
     double prof_ms[SX_PH_COUNT] = {0};
     int64_t prof_launches[SX_PH_COUNT] = {0};
     // occupancy limit of the element kernel [precision][instantiation]
-    int elem_occ[2][4] = {{1, 1, 1, 1}, {1, 1, 1, 1}};
+    int elem_occ[2][kElemVariants] = {{1, 1, 1, 1, 1, 1}, {1, 1, 1, 1, 1, 1}};
     bool share_sms = false;
     // launch shapes per precision (sx_autotune / sx_set_launch_shape):
     // projection block size, and element-kernel blocks per SM of the
@@ -215,9 +217,16 @@ int elem_grid(const sx_ctx* ctx, int precision, int kinds, int project, int ntil
     return std::max(g, 1);
 }
 
-int kind_bit(int kind)
+// instantiation bits of a block (tets of a density other than SNH add 16)
+int kind_bit(const BlockHost& b)
 {
-    return kind == SX_KIND_SNH_TET4 ? 1 : kind == SX_KIND_HINGE4 ? 2 : 4;
+    if (b.kind == SX_KIND_SNH_TET4) return b.model == SX_MODEL_SNH ? 1 : 1 | 16;
+    return b.kind == SX_KIND_HINGE4 ? 2 : 4;
+}
+
+bool lagged_model(const BlockHost& b)
+{
+    return b.kind == SX_KIND_SNH_TET4 && (b.model == SX_MODEL_COROT || b.model == SX_MODEL_ARAP);
 }
 
 int fail(sx_ctx* c, int code, const std::string& msg)
@@ -337,6 +346,8 @@ SceneDev make_desc(const sx_scene* s, bool trial)
         const BlockHost& h = s->blocks[b];
         ElemBlock& e = d.blk[b];
         e.kind = h.kind;
+        e.model = h.model;
+        e.R = h.Rot;
         e.n = h.n;
         e.base = h.base;
         e.conn = h.conn;
@@ -461,7 +472,7 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         for (sx_scene* s : B->scenes)
             for (auto& b : s->blocks) {
                 if (b.kind != SX_KIND_HINGE4) cap += b.n;
-                if (b.n) B->kinds |= kind_bit(b.kind);
+                if (b.n) B->kinds |= kind_bit(b);
             }
         if (!B->kinds) B->kinds = 1;
         B->clamp_need = std::max<int64_t>(cap, 1);
@@ -816,7 +827,7 @@ int sx_create(sx_ctx** out, const sx_options* opt)
     }
     ctx->share_sms = opt && opt->share_sms;
     for (int p = 0; p < 2; ++p)
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < kElemVariants; ++v) {
             int nb = 1;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, elements_kernel(p, v),
                                                           elements_block_threads(), 0);
@@ -929,25 +940,54 @@ int sx_scene_destroy(sx_scene* s)
     return SX_OK;
 }
 
-int sx_add_snh_tet4(sx_scene* s, const int32_t* tets, int64_t n, const double* young,
-                    const double* poisson, double density, int literal_params, void* stream,
-                    int* energy_id)
+namespace {
+
+__global__ void k_identity_rotations(int64_t n, double* R)
 {
-    int rc = add_block_common(s, "add_snh_tet4");
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[(int64_t)k * n + e] = (k % 4 == 0) ? 1.0 : 0.0;
+}
+
+// row-major 3x3 per tet (n x 9) <-> the block's [9][n] layout
+__global__ void k_rot_transpose(const double* __restrict__ in, int64_t n, int to_soa,
+                                double* __restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 9 * n) return;
+    const int64_t e = i / 9, k = i % 9;
+    if (to_soa) out[k * n + e] = in[i];
+    else out[i] = in[k * n + e];
+}
+
+int add_tet_block(sx_scene* s, int model, const int32_t* tets, int64_t n, const double* young,
+                  const double* poisson, double density, int literal_params, void* stream,
+                  int* energy_id, const char* what)
+{
+    int rc = add_block_common(s, what);
     if (rc != SX_OK) return rc;
     sx_ctx* ctx = s->ctx;
     if (n < 0 || (n > 0 && (!tets || !young || !poisson)) || !(density >= 0.0))
-        return fail(ctx, SX_EINVAL, "add_snh_tet4: bad arguments");
+        return fail(ctx, SX_EINVAL, std::string(what) + ": bad arguments");
+    if (model < SX_MODEL_SNH || model > SX_MODEL_ARAP)
+        return fail(ctx, SX_EINVAL, std::string(what) + ": unknown model");
     cudaStream_t st = (cudaStream_t)stream;
     s->stream = st;
     BlockHost b;
     b.kind = SX_KIND_SNH_TET4;
+    b.model = model;
     b.n = n;
     b.rho = density;
     if ((rc = copy_conn(ctx, s, tets, n, &b.conn, st)) != SX_OK) return rc;
     if (dalloc(s, &b.Dminv, 9 * (size_t)n) || dalloc(s, &b.V, (size_t)n) ||
         dalloc(s, &b.mu, (size_t)n) || dalloc(s, &b.lam, (size_t)n))
-        return fail(ctx, SX_ENOMEM, "add_snh_tet4: allocation failed");
+        return fail(ctx, SX_ENOMEM, std::string(what) + ": allocation failed");
+    if (lagged_model(b)) {
+        if (dalloc(s, &b.Rot, 9 * (size_t)std::max<int64_t>(n, 1)))
+            return fail(ctx, SX_ENOMEM, std::string(what) + ": allocation failed");
+        if (n) k_identity_rotations<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, b.Rot);
+    }
     double *dy = nullptr, *dp = nullptr;
     int* bad = nullptr;
     CK(cudaMallocAsync((void**)&dy, std::max<int64_t>(n, 1) * sizeof(double), st));
@@ -958,7 +998,8 @@ int sx_add_snh_tet4(sx_scene* s, const int32_t* tets, int64_t n, const double* y
         CK(cudaMemcpyAsync(dy, young, n * sizeof(double), cudaMemcpyDefault, st));
         CK(cudaMemcpyAsync(dp, poisson, n * sizeof(double), cudaMemcpyDefault, st));
     }
-    CK(launch_snh_rest(s->X, s->N, b.conn, n, dy, dp, density, literal_params, b.Dminv, b.V,
+    CK(launch_snh_rest(s->X, s->N, b.conn, n, dy, dp, density,
+                       model == SX_MODEL_SNH ? literal_params : 1, b.Dminv, b.V,
                        b.mu, b.lam, bad, st));
     int h_bad2[2] = {0, 0};
     CK(cudaMemcpyAsync(h_bad2, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -967,11 +1008,92 @@ int sx_add_snh_tet4(sx_scene* s, const int32_t* tets, int64_t n, const double* y
     CK(cudaFreeAsync(bad, st));
     CK(cudaStreamSynchronize(st));
     if (h_bad2[1])
-        return fail(ctx, SX_EINVAL, "add_snh_tet4: node id out of range");
+        return fail(ctx, SX_EINVAL, std::string(what) + ": node id out of range");
     if (h_bad2[0])
         return fail(ctx, SX_EDEGENERATE,
-                    "add_snh_tet4: " + std::to_string(h_bad2[0]) + " tets with det(Dm) <= 0");
+                    std::string(what) + ": " + std::to_string(h_bad2[0]) +
+                        " tets with det(Dm) <= 0");
     register_block(s, std::move(b), energy_id);
+    return SX_OK;
+}
+
+// the lagged-rotation block `energy_id` of a scene, or null
+BlockHost* lagged_block(sx_scene* s, int energy_id)
+{
+    if (!s || energy_id < 0 || energy_id >= (int)s->blocks.size()) return nullptr;
+    BlockHost& b = s->blocks[energy_id];
+    return lagged_model(b) ? &b : nullptr;
+}
+
+// R of every lagged block of the scene at its current state
+cudaError_t update_rotations(sx_scene* s, cudaStream_t st)
+{
+    for (auto& b : s->blocks)
+        if (lagged_model(b) && b.n) {
+            cudaError_t e = launch_tet_rotations(b.conn, s->x, b.Dminv, b.n, b.Rot, st);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int sx_add_snh_tet4(sx_scene* s, const int32_t* tets, int64_t n, const double* young,
+                    const double* poisson, double density, int literal_params, void* stream,
+                    int* energy_id)
+{
+    return add_tet_block(s, SX_MODEL_SNH, tets, n, young, poisson, density, literal_params,
+                         stream, energy_id, "add_snh_tet4");
+}
+
+int sx_add_tet4(sx_scene* s, int model, const int32_t* tets, int64_t n, const double* young,
+                const double* poisson, double density, void* stream, int* energy_id)
+{
+    return add_tet_block(s, model, tets, n, young, poisson, density, 0, stream, energy_id,
+                         "add_tet4");
+}
+
+int sx_update_rotations(sx_scene* s, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
+    CK(update_rotations(s, st));
+    return SX_OK;
+}
+
+int sx_get_rotations(sx_scene* s, int energy_id, double* R, void* stream)
+{
+    BlockHost* b = lagged_block(s, energy_id);
+    if (!b || (!R && b->n)) return s ? fail(s->ctx, SX_EINVAL, "get_rotations: not a COROT / ARAP block") : SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!b->n) return SX_OK;
+    double* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, 9 * b->n * sizeof(double), st));
+    k_rot_transpose<<<(unsigned)((9 * b->n + 255) / 256), 256, 0, st>>>(b->Rot, b->n, 0, tmp);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(R, tmp, 9 * b->n * sizeof(double), cudaMemcpyDefault, st));
+    CK(cudaFreeAsync(tmp, st));
+    CK(cudaStreamSynchronize(st));
+    return SX_OK;
+}
+
+int sx_set_rotations(sx_scene* s, int energy_id, const double* R, void* stream)
+{
+    BlockHost* b = lagged_block(s, energy_id);
+    if (!b || (!R && b->n)) return s ? fail(s->ctx, SX_EINVAL, "set_rotations: not a COROT / ARAP block") : SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
+    if (!b->n) return SX_OK;
+    double* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, 9 * b->n * sizeof(double), st));
+    CK(cudaMemcpyAsync(tmp, R, 9 * b->n * sizeof(double), cudaMemcpyDefault, st));
+    k_rot_transpose<<<(unsigned)((9 * b->n + 255) / 256), 256, 0, st>>>(tmp, b->n, 1, b->Rot);
+    CK(cudaGetLastError());
+    CK(cudaFreeAsync(tmp, st));
     return SX_OK;
 }
 
@@ -1485,7 +1607,7 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     L.clamp_threads = ctx->clamp_threads[precision == SX_FP32 ? 1 : 0];
     L.clamp_grid = clamp_grid_for(L.clamp_cap, L.clamp_threads);
     L.share_sms = ctx->share_sms;
-    L.kinds = kind_bit(b.kind);
+    L.kinds = kind_bit(b);
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, elem_grid(ctx, precision, L.kinds, H ? project : 0,
                                                          L.ntiles), st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
@@ -1624,6 +1746,9 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
     std::vector<double> g0(n, 0.0), gl(n, 0.0), E(n, 0.0);
     std::vector<int> act(n, 1);
     if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
+    // lagged rotations (COROT, ARAP): taken at the start-of-step state and
+    // held for the step (§7.1)
+    for (int i = 0; i < n; ++i) CK(update_rotations(scenes[i], st));
     PL(SX_PH_NEWTON, 1, launch_predict(B->d_desc, B->d_node, nnt, B->d_part_node, st));
     PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_node, 1, 0, B->d_node_beg, B->d_node_end,
                                             n, B->d_desc, F_FEXT2, 0, st));
@@ -1647,7 +1772,9 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             if (sc.bad_state) {
                 status[i] = SX_ESTATE;
                 done[i] = 1;
-                if (why.empty()) why = "a barrier pair at distance <= 0";
+                if (why.empty())
+                    why = "a stencil in an invalid state (barrier pair at d <= 0, "
+                          "Neo-Hookean tet at J <= 0)";
                 continue;
             }
             double gn = std::sqrt(sc.gnorm2);
@@ -2066,7 +2193,7 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
     L.clamp_threads = ctx->clamp_threads[precision == SX_FP32 ? 1 : 0];
     L.clamp_grid = clamp_grid_for(L.clamp_cap, L.clamp_threads);
     L.share_sms = ctx->share_sms;
-    L.kinds = kind_bit(b.kind);
+    L.kinds = kind_bit(b);
     const int grid = elem_grid(ctx, precision, L.kinds, H ? project : 0, nt);
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));

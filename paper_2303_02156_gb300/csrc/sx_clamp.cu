@@ -1,0 +1,284 @@
+// sx_clamp.cu -- phase 2 of the per-element projection to positive
+// semi-definiteness (§5.2 "Projection to positive semi-definiteness",
+// Algorithm 1): the queued 9x9 translation-free Hessians are
+// eigen-decomposed (float Jacobi, then double Gram-Schmidt and
+// block-restricted double sweeps, sx_clamp.cuh), their negative eigenvalues
+// clamped and the stencils' Hessian blocks rewritten.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "sx_elements.cuh"
+
+namespace sx {
+
+// After the eigen-decomposition: flags a non-finite result, else clamps
+// the N-block eigenvalues below -tau in the Hadamard basis and rewrites the
+// stencil's Hessian blocks (both projection launches end with this).
+template <typename HT>
+__device__ __forceinline__ void clamp_finish(const ElemLaunch& L, const ClampRef& ref,
+                                             const double* __restrict__ Mg, const SmemMat& X,
+                                             const double (&lam)[9], int k, double tau,
+                                             unsigned live)
+{
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ok = ok && isfinite(lam[i]);
+    if (!ok) {
+        atomicAdd(L.clamp_failed, 1);
+        atomicExch(&L.scenes[ref.scene].sc->clamp_fail, 1);
+        return;
+    }
+    const SceneDev& S = L.scenes[ref.scene];
+    const ElemBlock& B = S.blk[ref.blk];
+    HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (B.base + ref.e);
+    double* full = L.out_H ? L.out_H + 144 * ref.e : nullptr;
+    // M' = M - sum of lambda v v^T over the N-block eigenvalues below -tau
+    // (v in the Hadamard basis), then H' = (Hd kron I3) diag(0, M')
+    // (Hd kron I3)^T written once: no read of the staged H, one store per
+    // entry whatever the number of negative eigenvalues. (The element H
+    // has the three translations as an exact null space up to rounding,
+    // so H' differs from H - sum lambda u u^T only by rounding.)
+    bool any_neg = false;
+    double Mp[45];
+#pragma unroll
+    for (int q = 0; q < 45; ++q) Mp[q] = __ldg(Mg + q);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const bool neg = i < k && lam[i] < -tau;
+        if (!__any_sync(live, neg)) continue;
+        if (neg) {
+            any_neg = true;
+            double v[9];
+#pragma unroll
+            for (int r = 0; r < 9; ++r) v[r] = X(r, i);
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                const double lv = lam[i] * v[r];
+#pragma unroll
+                for (int c = 0; c <= r; ++c) Mp[pk(r, c)] = fma(-lv, v[c], Mp[pk(r, c)]);
+            }
+        }
+    }
+    if (!any_neg) return;
+    // Hd[a][m + 1] = SG[a][m] / 2 for the three non-translation modes
+    constexpr int SG[4][3] = {{1, 1, 1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, 1}};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        // Ta[r][j] = sum_m SG[a][m] M'[(3m + r), j]
+        double Ta[3][9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 9; ++j)
+                Ta[r][j] = SG[a][0] * Mp[pk(r, j)] + SG[a][1] * Mp[pk(3 + r, j)] +
+                           SG[a][2] * Mp[pk(6 + r, j)];
+#pragma unroll
+        for (int b = a; b < 4; ++b)
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double h = 0.25 * (SG[b][0] * Ta[r][c] + SG[b][1] * Ta[r][3 + c] +
+                                             SG[b][2] * Ta[r][6 + c]);
+                    if (staged) {
+                        staged[9 * up_index(a, b) + 3 * r + c] = (HT)h;
+                    } else {
+                        full[(3 * a + r) * 12 + 3 * b + c] = h;
+                        if (a != b) full[(3 * b + c) * 12 + 3 * a + r] = h;
+                    }
+                }
+    }
+}
+
+// phase 2 of the projection: one thread per queued stencil (the loop takes
+// more than one trip only if the grid is smaller than the queue); subtracts
+// sum_{lambda_t < -tau} lambda_t u_t u_t^T from its Hessian blocks
+template <typename HT, int NT>
+__global__ void __launch_bounds__(NT)
+k_clamp(ElemLaunch L)
+{
+    extern __shared__ __align__(16) double Xs[];   // [81][NT]
+    const SmemMat X{Xs + threadIdx.x, NT};
+    const int count = min(*L.clamp_count, L.clamp_cap);
+    // every thread of a block takes the same number of trips
+    const int64_t span = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += span) {
+        const int64_t idx = base + threadIdx.x;
+        const unsigned live = __ballot_sync(0xffffffffu, idx < count);
+        if (idx >= count) break;
+        const ClampRef ref = L.clamp_ref[idx];
+        const double* Mg = L.clamp_M + 45 * idx;
+        double tau, fro;
+        {
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+#pragma unroll
+                for (int j = 0; j <= i; ++j) {
+                    const double v = Mg[pk(i, j)];
+                    s = fma((i == j ? 1.0 : 2.0) * v, v, s);
+                }
+            fro = sqrt(s);
+            tau = 1e-13 * fro;
+        }
+        double lam[9];
+        const int k = eig9(Mg, X, lam, fro, sizeof(HT) == 4 ? SX_CLAMP_THETA32 : 1e-13, live);
+        clamp_finish<HT>(L, ref, Mg, X, lam, k, tau, live);
+    }
+}
+
+// The projection of a batched evaluation in two launches. The float part
+// runs per queued stencil and bins the stencil by k (the size of its N
+// block, 0..9); the double part then takes the stencils bucket by bucket,
+// so the 32 stencils of a warp share k and the warp runs only the rotations
+// they all need. Every stencil's arithmetic is the same as in k_clamp.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_clamp_float(ElemLaunch L)
+{
+    const int count = min(*L.clamp_count, L.clamp_cap);
+    const int64_t idx = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (idx >= count) return;
+    const double* Mg = L.clamp_M + 45 * idx;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            const double v = Mg[pk(i, j)];
+            s = fma((i == j ? 1.0 : 2.0) * v, v, s);
+        }
+    const double fro = sqrt(s);
+    const int64_t cap = L.clamp_cap;
+    float* Xg = L.clamp_X;   // [81][cap], entry r*9 + slot of stencil idx
+    const int k = eig9_float(Mg, fro, [&](int r, int slot, float v) {
+        Xg[(int64_t)(r * 9 + slot) * cap + idx] = v;
+    });
+    L.clamp_fro[idx] = fro;
+    // bucket slot: one atomic per (warp, k) for the lanes that share k
+    const unsigned peers = __match_any_sync(__activemask(), k);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(L.clamp_bucket_count + k, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const int pos = base + __popc(peers & ((1u << lane) - 1u));
+    L.clamp_bucket[(int64_t)k * cap + pos] = (int)idx;
+}
+
+template <typename HT, int NT>
+__global__ void __launch_bounds__(NT)
+k_clamp_double(ElemLaunch L)
+{
+    extern __shared__ __align__(16) double Xs[];   // [81][NT]
+    const SmemMat X{Xs + threadIdx.x, NT};
+    __shared__ int s_k, s_off;
+    if (threadIdx.x == 0) {
+        // block -> (bucket, offset): buckets in order, ceil(count / NT) blocks each
+        int b = blockIdx.x;
+        s_k = -1;
+        s_off = 0;
+        for (int kk = 0; kk < 10; ++kk) {
+            const int nb = (L.clamp_bucket_count[kk] + NT - 1) / NT;
+            if (b < nb) {
+                s_k = kk;
+                s_off = b * NT;
+                break;
+            }
+            b -= nb;
+        }
+    }
+    __syncthreads();
+    const int k = s_k;
+    if (k < 0) return;
+    const int cntk = L.clamp_bucket_count[k];
+    const int jj = s_off + threadIdx.x;
+    const unsigned live = __ballot_sync(0xffffffffu, jj < cntk);
+    if (jj >= cntk) return;
+    const int64_t cap = L.clamp_cap;
+    const int64_t idx = L.clamp_bucket[(int64_t)k * cap + jj];
+    const float* Xg = L.clamp_X;
+#pragma unroll
+    for (int q = 0; q < 81; ++q) X(q / 9, q % 9) = (double)Xg[(int64_t)q * cap + idx];
+    const ClampRef ref = L.clamp_ref[idx];
+    const double* Mg = L.clamp_M + 45 * idx;
+    const double fro = L.clamp_fro[idx];
+    const double tau = 1e-13 * fro;
+    double lam[9];
+    eig9_double(Mg, X, lam, fro, sizeof(HT) == 4 ? SX_CLAMP_THETA32 : 1e-13, k, live);
+    clamp_finish<HT>(L, ref, Mg, X, lam, k, tau, live);
+}
+cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
+{
+    if (L.ntiles == 0 || !(L.level >= 2 && L.project)) return cudaSuccess;
+    // the queue length stays on the device: the grid covers the largest
+    // possible queue with one stencil per thread, and blocks past the actual
+    // length exit at once. Short-lived blocks let work of higher-priority
+    // streams (the serving lanes of small scenes) in between.
+    const int cgrid = L.clamp_grid > 0 ? L.clamp_grid : 1;
+    const int nt = (L.clamp_threads == 32 || L.clamp_threads == 128 || L.clamp_threads == 256)
+                       ? L.clamp_threads
+                       : 64;
+    const int smem = 81 * 8 * nt + (L.share_sms ? clamp_share_pad(nt) : 0);
+    static std::atomic<unsigned long long> attr_done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (!bit || !(attr_done.load(std::memory_order_acquire) & bit)) {
+        const void* fns[] = {(const void*)k_clamp<float, 32>, (const void*)k_clamp<float, 64>,
+                             (const void*)k_clamp<float, 128>, (const void*)k_clamp<float, 256>,
+                             (const void*)k_clamp<double, 32>, (const void*)k_clamp<double, 64>,
+                             (const void*)k_clamp<double, 128>, (const void*)k_clamp<double, 256>,
+                             (const void*)k_clamp_double<float, 32>,
+                             (const void*)k_clamp_double<float, 64>,
+                             (const void*)k_clamp_double<float, 128>,
+                             (const void*)k_clamp_double<float, 256>,
+                             (const void*)k_clamp_double<double, 32>,
+                             (const void*)k_clamp_double<double, 64>,
+                             (const void*)k_clamp_double<double, 128>,
+                             (const void*)k_clamp_double<double, 256>};
+        for (const void* f : fns)
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kClampMaxSmem);
+        attr_done.fetch_or(bit, std::memory_order_release);
+    }
+    const bool f32 = L.precision == SX_FP32;
+    if (L.clamp_X) {
+        // two launches: float part binned by k, then the double part per bucket
+        const int64_t cap = L.clamp_cap;
+        const int ga = (int)std::max<int64_t>(1, (cap + 127) / 128);
+        k_clamp_float<128><<<ga, 128, 0, s>>>(L);
+        const int gb = (int)std::max<int64_t>(1, (cap + nt - 1) / nt + 10);
+        if (nt == 32) {
+            if (f32) k_clamp_double<float, 32><<<gb, 32, smem, s>>>(L);
+            else k_clamp_double<double, 32><<<gb, 32, smem, s>>>(L);
+        } else if (nt == 128) {
+            if (f32) k_clamp_double<float, 128><<<gb, 128, smem, s>>>(L);
+            else k_clamp_double<double, 128><<<gb, 128, smem, s>>>(L);
+        } else if (nt == 256) {
+            if (f32) k_clamp_double<float, 256><<<gb, 256, smem, s>>>(L);
+            else k_clamp_double<double, 256><<<gb, 256, smem, s>>>(L);
+        } else {
+            if (f32) k_clamp_double<float, 64><<<gb, 64, smem, s>>>(L);
+            else k_clamp_double<double, 64><<<gb, 64, smem, s>>>(L);
+        }
+        return cudaGetLastError();
+    }
+    if (nt == 32) {
+        if (f32) k_clamp<float, 32><<<cgrid, 32, smem, s>>>(L);
+        else k_clamp<double, 32><<<cgrid, 32, smem, s>>>(L);
+    } else if (nt == 128) {
+        if (f32) k_clamp<float, 128><<<cgrid, 128, smem, s>>>(L);
+        else k_clamp<double, 128><<<cgrid, 128, smem, s>>>(L);
+    } else if (nt == 256) {
+        if (f32) k_clamp<float, 256><<<cgrid, 256, smem, s>>>(L);
+        else k_clamp<double, 256><<<cgrid, 256, smem, s>>>(L);
+    } else {
+        if (f32) k_clamp<float, 64><<<cgrid, 64, smem, s>>>(L);
+        else k_clamp<double, 64><<<cgrid, 64, smem, s>>>(L);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sx

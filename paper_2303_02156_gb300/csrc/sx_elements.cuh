@@ -1,0 +1,1104 @@
+// sx_elements.cuh -- per-element energy, gradient and Hessian kernels
+// (the parallel element loop of Algorithm 1: gather, evaluate, project,
+// stage for assembly).
+//
+// Stable Neo-Hookean tet4 (§3.1 Eq. 7, App. B): with F = Ds Dm^-1,
+// Ic = |F|^2, J = det F, C = cof F (dJ/dF), the density's first and
+// second derivatives are P = a F + b C and
+//   d2psi/dF2 = a I9 + gam vec(F)vec(F)^T + lam' vec(C)vec(C)^T + b dC/dF,
+// a = mu' Ic/(Ic+1), gam = 2 mu'/(Ic+1)^2, b = lam'(J - alpha). Because F
+// is linear in the vertices through the shape-function gradients G_a
+// (F = sum_a x_a G_a^T), each 3x3 block of the element Hessian has the
+// closed form
+//   H_ab = V [ a (G_a.G_b) I3 + gam (F G_a)(F G_b)^T + lam' (C G_a)(C G_b)^T
+//              + b S(F (G_a x G_b)) ],   S(w)_ik = eps_ikn w_n,
+// so no 9x12 map is formed. The same expression with the Hadamard
+// combinations K_c of the G_a gives the 9x9 translation-free Hessian M
+// that the PSD projection works on (sx_clamp.cuh).
+//
+// Hinge bending (§6.3 Eq. 13): Q = c (q q^T kron I3), so
+// E = k_b c |sum_a q_a x_a|^2 / 2, g_a = k_b c q_a s, H_ab = k_b c q_a q_b I3
+// with s = sum_a q_a x_a; Q is PSD and never projected.
+//
+// Other tet4 densities (§7.1, App. B; compiled into separate
+// instantiations, KINDS bit 16): Neo-Hookean, fixed co-rotational and ARAP
+// have the same Hessian form with gam = 0 and their own coefficients; St.
+// Venant-Kirchhoff has its own blocks (see model_core).
+//
+// Point-triangle barrier (§6.4 Eq. 15) lives in sx_barrier.cuh.
+//
+// Precision: SX_FP64 computes everything in double. SX_FP32 forms the
+// gathered edge vectors (x_a - x_0) in double, then does the element math
+// in float; the projection always runs in double.
+//
+// The element kernel k_elements<R, HT, KINDS> is instantiated in three
+// translation units (sx_elements.cu: KINDS 1, 7; sx_elements_fproj.cu: 9,
+// 15; sx_elements_models.cu: 25, 31) so that they compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sx_barrier.cuh"
+#include "sx_clamp.cuh"
+#include "sx_internal.cuh"
+
+namespace sx {
+
+static constexpr int kElemThreads = 128;
+// projection block sizes the launch may use: 32, 64, 128 (the default) or
+// 256, picked by sx_autotune; each thread keeps its 9x9 eigenvector matrix
+// (648 B) in dynamic shared memory
+static constexpr int kClampThreads = 64;
+// sharing: unused dynamic shared memory per block that lowers the resident
+// blocks per SM by one (from the register limit of 255-register threads):
+// 32 threads 20.3 + 8 KB (8 -> 7), 64 threads 40.5 + 17 KB (4 -> 3),
+// 128 threads 81 + 32 KB (2 -> 1); 256-thread blocks are alone on an SM
+__host__ __device__ constexpr int clamp_share_pad(int nt)
+{
+    return nt == 32 ? 8 * 1024 : nt == 64 ? 17 * 1024 : nt == 128 ? 32 * 1024 : 0;
+}
+static constexpr int kClampMaxSmem = 81 * 8 * 256;
+
+template <typename R>
+struct Vec3 {
+    R x, y, z;
+};
+
+// ------------------------------------------------------------------ SNH
+template <typename R>
+struct SnhCore {
+    R G[4][3];   // shape-function gradients (row a)
+    R F[9];      // row-major
+    R C[9];      // cofactor
+    R cI, cF, cC, cS;   // V*a, V*gam, V*lam', V*b
+};
+
+template <typename R>
+__device__ __forceinline__ void cross3(const R* u, const R* v, R* w)
+{
+    w[0] = u[1] * v[2] - u[2] * v[1];
+    w[1] = u[2] * v[0] - u[0] * v[2];
+    w[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+// Evaluates, always in double, F = Ds Dm^-1 and the rest-relative energy
+// E = V (psi(F) - psi(I)) free of cancellation: with D = F - I,
+//   Ic - 3 = |D|^2 + 2 tr D,   J - 1 = tr D + c2(D) + det D
+// (c2 = sum of principal 2x2 minors), and since alpha - 1 = 3 mu'/(4 lam'),
+//   lam'/2 [(J-alpha)^2 - (1-alpha)^2] = lam'/2 (J-1)^2 - 3/4 mu' (J-1),
+//   mu'/2 [ln(Ic+1) - ln 4] = mu'/2 log1p((Ic-3)/4).
+// No O(1) quantities are subtracted, so the line search can resolve the
+// last Newton decreases. Then, in the element precision R, the gradient
+// (12, node-major) and the Hessian coefficients.
+template <typename R>
+__device__ __forceinline__ double snh_core(const double* xg, const double* Dinv, double Vd,
+                                           double mud, double lamd, int level, SnhCore<R>& S,
+                                           R* g)
+{
+    double Ds[3][3];  // Ds[i][k] = x_{k+1,i} - x_{0,i}
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Ds[i][k] = xg[3 * (k + 1) + i] - xg[i];
+    double Fd[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Fd[i * 3 + j] = Ds[i][0] * Dinv[0 * 3 + j] + Ds[i][1] * Dinv[1 * 3 + j] +
+                            Ds[i][2] * Dinv[2 * 3 + j];
+    double D[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) D[k] = Fd[k] - ((k % 4 == 0) ? 1.0 : 0.0);
+    const double trD = D[0] + D[4] + D[8];
+    double Ic3 = 2.0 * trD;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ic3 = fma(D[k], D[k], Ic3);
+    const double c2 = (D[0] * D[4] - D[1] * D[3]) + (D[0] * D[8] - D[2] * D[6]) +
+                      (D[4] * D[8] - D[5] * D[7]);
+    const double detD = D[0] * (D[4] * D[8] - D[5] * D[7]) - D[1] * (D[3] * D[8] - D[5] * D[6]) +
+                        D[2] * (D[3] * D[7] - D[4] * D[6]);
+    const double Jm1 = trD + c2 + detD;
+    double psi = 0.5 * mud * Ic3 - 0.5 * mud * log1p(0.25 * Ic3);
+    if (lamd != 0.0) psi += 0.5 * lamd * Jm1 * Jm1 - 0.75 * mud * Jm1;
+    const double E = Vd * psi;
+    if (level >= 1) {
+        const R V = (R)Vd, mu = (R)mud, lam = (R)lamd;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            S.G[1][j] = (R)Dinv[0 * 3 + j];
+            S.G[2][j] = (R)Dinv[1 * 3 + j];
+            S.G[3][j] = (R)Dinv[2 * 3 + j];
+            S.G[0][j] = (R)(-(Dinv[0 * 3 + j] + Dinv[1 * 3 + j] + Dinv[2 * 3 + j]));
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) S.F[k] = (R)Fd[k];
+        const R* F = S.F;
+        // cofactor columns: dJ/dF columns are f1 x f2, f2 x f0, f0 x f1
+        {
+            R f0[3] = {F[0], F[3], F[6]}, f1[3] = {F[1], F[4], F[7]}, f2[3] = {F[2], F[5], F[8]};
+            R c0[3], c1[3], cc2[3];
+            cross3(f1, f2, c0);
+            cross3(f2, f0, c1);
+            cross3(f0, f1, cc2);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                S.C[i * 3 + 0] = c0[i];
+                S.C[i * 3 + 1] = c1[i];
+                S.C[i * 3 + 2] = cc2[i];
+            }
+        }
+        const R Ic = (R)(3.0 + Ic3);
+        const R inv1 = R(1) / (Ic + R(1));
+        const R a = mu * Ic * inv1;
+        // lam'(J - alpha) = lam'(J - 1) - 3/4 mu'
+        const R b = (lamd != 0.0) ? (R)(lamd * Jm1 - 0.75 * mud) : R(0);
+        // P = a F + b cof F. Its two O(mu') parts cancel at rest, so it is
+        // formed from D = F - I: cof(I + D) = I + (tr D) I - D^T + cof D gives
+        // P = (a + b) I + a D + b ((tr D) I - D^T + cof D), where
+        // a + b = mu' Ic3 / (4 (Ic + 1)) + lam' (J - 1) (alpha = 1 + 3 mu' / (4 lam'))
+        // is taken in double; the rest is O(mu' |D|) and keeps R's relative
+        // precision (in FP32 this is what lets the assembled forces resolve
+        // below float epsilon times mu')
+        const double Icd = 3.0 + Ic3;
+        const R s0 = (lamd != 0.0) ? (R)(mud * Ic3 / (4.0 * (Icd + 1.0)) + lamd * Jm1)
+                                   : (R)(mud * Icd / (Icd + 1.0));
+        R Dr[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Dr[k] = (R)D[k];
+        const R trr = (R)trD;
+        R cofD[9];
+        cofD[0] = Dr[4] * Dr[8] - Dr[5] * Dr[7];
+        cofD[1] = Dr[5] * Dr[6] - Dr[3] * Dr[8];
+        cofD[2] = Dr[3] * Dr[7] - Dr[4] * Dr[6];
+        cofD[3] = Dr[2] * Dr[7] - Dr[1] * Dr[8];
+        cofD[4] = Dr[0] * Dr[8] - Dr[2] * Dr[6];
+        cofD[5] = Dr[1] * Dr[6] - Dr[0] * Dr[7];
+        cofD[6] = Dr[1] * Dr[5] - Dr[2] * Dr[4];
+        cofD[7] = Dr[2] * Dr[3] - Dr[0] * Dr[5];
+        cofD[8] = Dr[0] * Dr[4] - Dr[1] * Dr[3];
+        R P[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                P[i * 3 + j] = ((i == j) ? s0 + b * trr : R(0)) + a * Dr[i * 3 + j] +
+                               b * (cofD[i * 3 + j] - Dr[j * 3 + i]);
+#pragma unroll
+        for (int n = 0; n < 4; ++n)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                g[3 * n + i] = V * (P[i * 3 + 0] * S.G[n][0] + P[i * 3 + 1] * S.G[n][1] +
+                                    P[i * 3 + 2] * S.G[n][2]);
+        S.cI = V * a;
+        S.cF = V * R(2) * mu * inv1 * inv1;
+        S.cC = V * lam;
+        S.cS = V * b;
+    }
+    return E;
+}
+
+// one 3x3 block V[ a (Ga.Gb) I + gam uu^T + lam' vv^T + b S(F (Ga x Gb)) ]
+template <typename R>
+__device__ __forceinline__ void snh_block(const SnhCore<R>& S, const R* Ga, const R* Gb,
+                                          const R* ua, const R* ub, const R* va,
+                                          const R* vb, bool diag, R* out)
+{
+    const R gg = Ga[0] * Gb[0] + Ga[1] * Gb[1] + Ga[2] * Gb[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            out[i * 3 + k] = S.cF * ua[i] * ub[k] + S.cC * va[i] * vb[k] +
+                             (i == k ? S.cI * gg : R(0));
+    if (!diag) {
+        R c[3], w[3];
+        cross3(Ga, Gb, c);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            w[i] = S.F[i * 3 + 0] * c[0] + S.F[i * 3 + 1] * c[1] + S.F[i * 3 + 2] * c[2];
+        // S(w) = [[0, w2, -w1], [-w2, 0, w0], [w1, -w0, 0]]
+        out[1] += S.cS * w[2];
+        out[2] -= S.cS * w[1];
+        out[3] -= S.cS * w[2];
+        out[5] += S.cS * w[0];
+        out[6] += S.cS * w[1];
+        out[7] -= S.cS * w[0];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void matvec3(const R* M, const R* v, R* o)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o[i] = M[i * 3 + 0] * v[0] + M[i * 3 + 1] * v[1] + M[i * 3 + 2] * v[2];
+}
+
+// 9x9 translation-free Hessian M (double, packed lower) of an SNH tet.
+template <typename R>
+__device__ __forceinline__ void snh_M(const SnhCore<R>& S, double (&M)[45])
+{
+    R K[3][3];   // K_c, c = 1..3 stored at [c-1]
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        had_fwd(S.G[0][j], S.G[1][j], S.G[2][j], S.G[3][j], K[0][j], K[1][j], K[2][j]);
+    R u[3][3], v[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        matvec3(S.F, K[c], u[c]);
+        matvec3(S.C, K[c], v[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = c; d < 3; ++d) {
+            R blk[9];
+            snh_block(S, K[c], K[d], u[c], u[d], v[c], v[d], c == d, blk);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (3 * d + k <= 3 * c + i || c != d)
+                        M[pk(3 * d + k, 3 * c + i)] = (double)blk[i * 3 + k];
+        }
+}
+
+// ------------------------------------------------------------------ output
+// Writes the 10 upper blocks produced by `blockfn(a, b, out9)` (element
+// precision) to the staged buffer, or the full 12x12 to `full`.
+template <typename R, typename HT, typename BlockFn>
+__device__ __forceinline__ void write_blocks(BlockFn blockfn, HT* staged, double* full,
+                                             int* nonfinite)
+{
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a; b < 4; ++b) {
+            R blk[9];
+            blockfn(a, b, blk);
+            bool bad = false;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) bad |= !isfinite((double)blk[k]);
+            if (bad) *nonfinite = 1;
+            if (staged) {
+                HT* dst = staged + 9 * up_index(a, b);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) dst[k] = (HT)blk[k];
+            }
+            if (full) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        full[(3 * a + i) * 12 + (3 * b + k)] = (double)blk[i * 3 + k];
+                        full[(3 * b + k) * 12 + (3 * a + i)] = (double)blk[i * 3 + k];
+                    }
+            }
+        }
+}
+
+// phase 1 of the projection: queue M unless M + tau I is PD
+__device__ __forceinline__ bool queue_if_indefinite(const ElemLaunch& L, int scene, int blk,
+                                                    int64_t e, const double (&M)[45])
+{
+    const int cls = psd_class_f32(M);
+    if (cls > 0 || (cls == 0 && psd_by_ldlt(M))) return false;
+    const int slot = atomicAdd(L.clamp_count, 1);
+    if (slot >= L.clamp_cap) return false;   // cannot happen: capacity = stencils
+    double* dst = L.clamp_M + 45 * (int64_t)slot;
+#pragma unroll
+    for (int k = 0; k < 45; ++k) dst[k] = M[k];
+    L.clamp_ref[slot] = ClampRef{scene, blk, e};
+    return true;
+}
+
+// ------------------------------------------------------------------ kernel
+struct ThreadOut {
+    double E;
+    int bad;        // barrier d <= 0
+    int nonfinite;
+    int clamped;    // queued for the projection
+};
+
+// ---------------------------------------------------------------- F-space projection
+// Cyclic Jacobi on a symmetric 3x3 in double (A packed lower: 00,10,11,20,21,22),
+// eigenvectors accumulated into the columns of Q (row-major). Stops once
+// the off-diagonal is below 1e-17 of the diagonal scale (at most 8 sweeps).
+__device__ __forceinline__ void jacobi3(double (&A)[6], double (&Q)[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Q[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    for (int sw = 0; sw < 8; ++sw) {
+        const double off = fabs(A[1]) + fabs(A[3]) + fabs(A[4]);
+        const double dia = fabs(A[0]) + fabs(A[2]) + fabs(A[5]);
+        if (!(off > 1e-17 * dia)) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            const int ipq = pk(p, q), ipp = pk(p, p), iqq = pk(q, q);
+            const double apq = A[ipq];
+            if (apq == 0.0) continue;
+            const double tau = (A[iqq] - A[ipp]) / (2.0 * apq);
+            const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+            const double c = rsqrt(fma(t, t, 1.0)), sn = t * c;
+            A[ipp] -= t * apq;
+            A[iqq] += t * apq;
+            A[ipq] = 0.0;
+            const int r = 3 - p - q;
+            const double arp = A[pk(r, p)], arq = A[pk(r, q)];
+            A[pk(r, p)] = c * arp - sn * arq;
+            A[pk(r, q)] = sn * arp + c * arq;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double xp = Q[3 * i + p], xq = Q[3 * i + q];
+                Q[3 * i + p] = c * xp - sn * xq;
+                Q[3 * i + q] = sn * xp + c * xq;
+            }
+        }
+    }
+}
+
+// project mode 2 for one SNH tet: removes from its Hessian blocks the
+// negative modes of d2psi/dF2 (H = V B^T proj(d2psi/dF2) B). In the frame
+// of the signed SVD F = U diag(s) V^T (U, V rotations) the material Hessian
+// a I + gam F F^T + lam' C C^T + b dC/dF splits into three twist/flip pairs,
+// eigenvalue a - b s_k on (u_i v_j^T + u_j v_i^T)/sqrt2 and a + b s_k on
+// (u_i v_j^T - u_j v_i^T)/sqrt2 ({i, j, k} = {0, 1, 2}), and the stretch
+// block a I + gam s s^T + lam' p p^T + b K on U diag(q) V^T, with
+// p = (s1 s2, s0 s2, s0 s1) and K the symmetric 3x3 with zero diagonal and
+// K01 = s2, K02 = s1, K12 = s0. A negative mode (lambda, E) changes block
+// (a, b) by -V lambda (E G_a)(E G_b)^T. Returns the number of modes removed.
+template <typename HT>
+__device__ int snh_fproj(const double* xg, const double* Dinv, double Vd, double mud,
+                         double lamd, HT* staged, double* full)
+{
+    double F[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double d1 = xg[3 + i] - xg[i], d2 = xg[6 + i] - xg[i], d3 = xg[9 + i] - xg[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            F[3 * i + j] = d1 * Dinv[j] + d2 * Dinv[3 + j] + d3 * Dinv[6 + j];
+    }
+    double Ic = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ic = fma(F[k], F[k], Ic);
+    const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                     F[2] * (F[3] * F[7] - F[4] * F[6]);
+    const double a = mud * Ic / (Ic + 1.0);
+    const double gam = 2.0 * mud / ((Ic + 1.0) * (Ic + 1.0));
+    const double b = (lamd != 0.0) ? lamd * (J - 1.0) - 0.75 * mud : 0.0;
+    // V: eigenvectors of F^T F
+    double S[6];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q <= p; ++q)
+            S[pk(p, q)] = F[p] * F[q] + F[3 + p] * F[3 + q] + F[6 + p] * F[6 + q];
+    double Vm[9];
+    jacobi3(S, Vm);
+    // a proper rotation V
+    const double dv = Vm[0] * (Vm[4] * Vm[8] - Vm[5] * Vm[7]) -
+                      Vm[1] * (Vm[3] * Vm[8] - Vm[5] * Vm[6]) +
+                      Vm[2] * (Vm[3] * Vm[7] - Vm[4] * Vm[6]);
+    if (dv < 0.0) {
+        Vm[2] = -Vm[2];
+        Vm[5] = -Vm[5];
+        Vm[8] = -Vm[8];
+    }
+    // U from F V: the two larger directions by normalization, the third by
+    // the right-handed cross product; its singular value keeps the sign of J
+    int m = 0;
+    if (S[pk(1, 1)] < S[pk(m, m)]) m = 1;
+    if (S[pk(2, 2)] < S[pk(m, m)]) m = 2;
+    const int i0 = (m + 1) % 3, j0 = (m + 2) % 3;
+    double fv[3][3];   // fv[k] = F v_k
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            fv[k][r] = F[3 * r] * Vm[k] + F[3 * r + 1] * Vm[3 + k] + F[3 * r + 2] * Vm[6 + k];
+    double U[3][3];   // U[k] = u_k
+    double sg[3];
+    {
+        double fi[3], fj[3], fm[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            fi[r] = (i0 == 0) ? fv[0][r] : (i0 == 1) ? fv[1][r] : fv[2][r];
+            fj[r] = (j0 == 0) ? fv[0][r] : (j0 == 1) ? fv[1][r] : fv[2][r];
+            fm[r] = (m == 0) ? fv[0][r] : (m == 1) ? fv[1][r] : fv[2][r];
+        }
+        const double si = sqrt(fi[0] * fi[0] + fi[1] * fi[1] + fi[2] * fi[2]);
+        double ui[3], uj[3], um[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) ui[r] = fi[r] / si;
+        const double pr = ui[0] * fj[0] + ui[1] * fj[1] + ui[2] * fj[2];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) uj[r] = fj[r] - pr * ui[r];
+        const double nj = sqrt(uj[0] * uj[0] + uj[1] * uj[1] + uj[2] * uj[2]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) uj[r] /= nj;
+        const double sj = uj[0] * fj[0] + uj[1] * fj[1] + uj[2] * fj[2];
+        cross3(ui, uj, um);
+        const double sm = um[0] * fm[0] + um[1] * fm[1] + um[2] * fm[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) U[k][r] = (k == i0) ? ui[r] : (k == j0) ? uj[r] : um[r];
+            sg[k] = (k == i0) ? si : (k == j0) ? sj : sm;
+        }
+    }
+    // g[a][k] = v_k . G_a
+    double G[4][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        G[1][j] = Dinv[j];
+        G[2][j] = Dinv[3 + j];
+        G[3][j] = Dinv[6 + j];
+        G[0][j] = -(Dinv[j] + Dinv[3 + j] + Dinv[6 + j]);
+    }
+    double g[4][3];
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            g[n][k] = G[n][0] * Vm[k] + G[n][1] * Vm[3 + k] + G[n][2] * Vm[6 + k];
+    int removed = 0;
+    auto remove = [&](double lambda, const double (&w)[12]) {
+        const double sc = Vd * lambda;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int bb = a; bb < 4; ++bb)
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const double wr = sc * w[3 * a + r], wc = w[3 * bb + c];
+                        if (staged) {
+                            HT* p = staged + 9 * up_index(a, bb) + 3 * r + c;
+                            *p = (HT)fma(-wr, wc, (double)*p);
+                        } else {
+                            double* p = full + (3 * a + r) * 12 + 3 * bb + c;
+                            *p = fma(-wr, wc, *p);
+                            if (a != bb) {
+                                double* q = full + (3 * bb + c) * 12 + 3 * a + r;
+                                *q = fma(-wr, wc, *q);
+                            }
+                        }
+                    }
+        ++removed;
+    };
+    const double h = 0.70710678118654752440;   // 1/sqrt(2)
+    // twist / flip pairs
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+#pragma unroll
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            const double lambda = a + sgn * b * sg[k];   // sgn -1: symmetric, +1: antisymmetric
+            if (!(lambda < 0.0)) continue;
+            const double sym = (sgn < 0) ? 1.0 : -1.0;
+            double w[12];
+#pragma unroll
+            for (int n = 0; n < 4; ++n)
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    w[3 * n + r] = h * (U[i][r] * g[n][j] + sym * U[j][r] * g[n][i]);
+            remove(lambda, w);
+        }
+    }
+    // stretch block
+    const double pv[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};
+    double A3[6];
+    A3[pk(0, 0)] = a + gam * sg[0] * sg[0] + lamd * pv[0] * pv[0];
+    A3[pk(1, 1)] = a + gam * sg[1] * sg[1] + lamd * pv[1] * pv[1];
+    A3[pk(2, 2)] = a + gam * sg[2] * sg[2] + lamd * pv[2] * pv[2];
+    A3[pk(1, 0)] = gam * sg[1] * sg[0] + lamd * pv[1] * pv[0] + b * sg[2];
+    A3[pk(2, 0)] = gam * sg[2] * sg[0] + lamd * pv[2] * pv[0] + b * sg[1];
+    A3[pk(2, 1)] = gam * sg[2] * sg[1] + lamd * pv[2] * pv[1] + b * sg[0];
+    double Q3[9];
+    jacobi3(A3, Q3);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const double lambda = A3[pk(e, e)];
+        if (!(lambda < 0.0)) continue;
+        double w[12];
+#pragma unroll
+        for (int n = 0; n < 4; ++n)
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                w[3 * n + r] = Q3[0 + e] * g[n][0] * U[0][r] + Q3[3 + e] * g[n][1] * U[1][r] +
+                               Q3[6 + e] * g[n][2] * U[2][r];
+        remove(lambda, w);
+    }
+    return removed;
+}
+
+template <typename R, typename HT, bool FPROJ>
+__device__ void eval_snh(const ElemLaunch& L, int scene, int blk, const SceneDev& S,
+                         const ElemBlock& B, int64_t e, ThreadOut& o)
+{
+    const int4 t = B.conn[e];
+    double xg[12];
+    const int nid[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const double* p = S.x + 3 * (int64_t)nid[a];
+        xg[3 * a + 0] = p[0];
+        xg[3 * a + 1] = p[1];
+        xg[3 * a + 2] = p[2];
+    }
+    double Dinv[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Dinv[k] = B.Dminv[(int64_t)k * B.n + e];
+    SnhCore<R> C;
+    R g[12];
+    o.E = snh_core<R>(xg, Dinv, B.V[e], B.mu[e], B.lam[e], L.level, C, g);
+    if (!isfinite(o.E)) o.nonfinite = 1;
+    const int64_t gid = B.base + e;
+    if (L.level >= 1) {
+        double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            gout[k] = (double)g[k];
+            if (!isfinite((double)g[k])) o.nonfinite = 1;
+        }
+    }
+    if (L.level >= 2) {
+        {
+            R u[4][3], v[4][3];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                matvec3(C.F, C.G[a], u[a]);
+                matvec3(C.C, C.G[a], v[a]);
+            }
+            auto blockfn = [&](int a, int b, R* out) {
+                snh_block(C, C.G[a], C.G[b], u[a], u[b], v[a], v[b], a == b, out);
+            };
+            HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
+            double* full = L.out_H ? L.out_H + 144 * e : nullptr;
+            write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
+        }
+        if (FPROJ && L.project == 2) {
+            HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
+            double* full = L.out_H ? L.out_H + 144 * e : nullptr;
+            o.clamped = snh_fproj<HT>(xg, Dinv, B.V[e], B.mu[e], B.lam[e], staged, full) > 0;
+        } else if (L.project) {
+            double M[45];
+            snh_M<R>(C, M);
+            o.clamped = queue_if_indefinite(L, scene, blk, e, M);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ other tet4 densities
+// With F = I + D (D formed from the gathered edge vectors in double), the
+// energies are written without subtracting O(1) quantities:
+//   NH    mu/2 |D|^2 - mu (c2(D) + det D) + mu (u - ln(1+u)) + lambda/2 ln^2(1+u),
+//         u = J - 1 = tr D + c2(D) + det D (the same function as
+//         mu/2 (Ic - 3) - mu ln J + lambda/2 ln^2 J);
+//   StVK  mu |E|^2 + lambda/2 tr(E)^2 with E = (D + D^T + D^T D)/2;
+//   COROT k mu |F - R|^2 + lambda/2 u^2, k = 1 (ARAP: k = 1/2).
+// Derivatives (R lagged, constant):
+//   NH      P = mu F + h C, h = (lambda ln J - mu)/J;
+//           d2psi/dF2 = mu I + h' c c^T + h dC/dF, h' = (lambda + mu - lambda ln J)/J^2
+//   COROT   P = 2k mu (F - R) + lambda u C;
+//           d2psi/dF2 = 2k mu I + lambda c c^T + lambda u dC/dF
+//   StVK    P = F S, S = 2 mu E + lambda tr(E) I; with u_a = F G_a
+//           H_ab = V [ (G_a.S G_b) I3 + mu (G_a.G_b) F F^T + mu u_b u_a^T + lambda u_a u_b^T ]
+// The first two are SNH-shaped (snh_block with gam = 0).
+template <typename R>
+struct StvkCore {
+    R Sm[9];   // V S
+    R FF[9];   // V mu F F^T
+    R cU, cL;  // V mu, V lambda
+};
+
+// u - ln(1 + u): for |u| < 1/16 the series u^2 sum_{j=0}^{18} (-1)^j u^j / (j + 2)
+// in Horner form (the tail beyond is below 1e-20 of the value), the
+// direct difference otherwise.
+__device__ __forceinline__ double u_minus_log1p(double u)
+{
+    if (fabs(u) < 0.0625) {
+        double t = 1.0 / 20.0;
+#pragma unroll
+        for (int j = 17; j >= 0; --j) t = fma(t, u, ((j & 1) ? -1.0 : 1.0) / (double)(j + 2));
+        return u * u * t;
+    }
+    return u - log1p(u);
+}
+
+// E (double) of one tet of model != SNH; at level >= 1 the gradient g (R)
+// and the Hessian coefficients (S for the SNH-shaped models, T for StVK).
+// Sets bad for an invalid state (NH with J <= 0).
+template <typename R>
+__device__ __forceinline__ double model_core(int model, const double* xg, const double* Dinv,
+                                             const double* Rl, double Vd, double mud,
+                                             double lamd, int level, SnhCore<R>& S,
+                                             StvkCore<R>& T, R* g, int& bad)
+{
+    double Fd[9], D[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double f = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) f = fma(xg[3 * (k + 1) + i] - xg[i], Dinv[k * 3 + j], f);
+            Fd[i * 3 + j] = f;
+            D[i * 3 + j] = f - (i == j ? 1.0 : 0.0);
+        }
+    const double trD = D[0] + D[4] + D[8];
+    const double c2 = (D[0] * D[4] - D[1] * D[3]) + (D[0] * D[8] - D[2] * D[6]) +
+                      (D[4] * D[8] - D[5] * D[7]);
+    const double detD = D[0] * (D[4] * D[8] - D[5] * D[7]) - D[1] * (D[3] * D[8] - D[5] * D[6]) +
+                        D[2] * (D[3] * D[7] - D[4] * D[6]);
+    const double Jm1 = trD + c2 + detD;
+    const double J = 1.0 + Jm1;
+    double psi, Pd[9];
+    double Eg[9];   // StVK Green strain
+    double lnJ = 0.0;
+    const double kmu = (model == SX_MODEL_ARAP) ? 0.5 * mud : mud;
+    if (model == SX_MODEL_NH) {
+        if (!(Jm1 > -1.0)) {
+            bad = 1;
+            return 0.0;
+        }
+        double D2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) D2 = fma(D[k], D[k], D2);
+        lnJ = log1p(Jm1);
+        psi = 0.5 * mud * D2 - mud * (c2 + detD) + mud * u_minus_log1p(Jm1) +
+              0.5 * lamd * lnJ * lnJ;
+    } else if (model == SX_MODEL_STVK) {
+        double e2 = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                double v = D[i * 3 + j] + D[j * 3 + i];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) v = fma(D[m * 3 + i], D[m * 3 + j], v);
+                Eg[i * 3 + j] = 0.5 * v;
+                e2 = fma(Eg[i * 3 + j], Eg[i * 3 + j], e2);
+            }
+        const double trE = Eg[0] + Eg[4] + Eg[8];
+        psi = mud * e2 + 0.5 * lamd * trE * trE;
+    } else {   // COROT, ARAP
+        double r2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const double d = Fd[k] - Rl[k];
+            Pd[k] = d;
+            r2 = fma(d, d, r2);
+        }
+        psi = kmu * r2 + 0.5 * lamd * Jm1 * Jm1;
+    }
+    const double E = Vd * psi;
+    if (level < 1) return E;
+    const R V = (R)Vd;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        S.G[1][j] = (R)Dinv[0 * 3 + j];
+        S.G[2][j] = (R)Dinv[1 * 3 + j];
+        S.G[3][j] = (R)Dinv[2 * 3 + j];
+        S.G[0][j] = (R)(-(Dinv[0 * 3 + j] + Dinv[1 * 3 + j] + Dinv[2 * 3 + j]));
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S.F[k] = (R)Fd[k];
+    R P[9];
+    if (model == SX_MODEL_STVK) {
+        const double trE = Eg[0] + Eg[4] + Eg[8];
+        R Sr[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            Sr[k] = (R)(2.0 * mud * Eg[k] + ((k % 4 == 0) ? lamd * trE : 0.0));
+            T.Sm[k] = V * Sr[k];
+        }
+        // P = F S = S + D S (S is O(|D|): keeps R's relative precision)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                P[i * 3 + j] = Sr[i * 3 + j] + (R)D[i * 3 + 0] * Sr[0 * 3 + j] +
+                               (R)D[i * 3 + 1] * Sr[1 * 3 + j] + (R)D[i * 3 + 2] * Sr[2 * 3 + j];
+        const R mu = (R)mud;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                T.FF[i * 3 + k] = V * mu * (S.F[i * 3 + 0] * S.F[k * 3 + 0] +
+                                            S.F[i * 3 + 1] * S.F[k * 3 + 1] +
+                                            S.F[i * 3 + 2] * S.F[k * 3 + 2]);
+        T.cU = V * mu;
+        T.cL = V * (R)lamd;
+    } else {
+        const R* F = S.F;
+        {
+            R f0[3] = {F[0], F[3], F[6]}, f1[3] = {F[1], F[4], F[7]}, f2[3] = {F[2], F[5], F[8]};
+            R c0[3], c1[3], cc2[3];
+            cross3(f1, f2, c0);
+            cross3(f2, f0, c1);
+            cross3(f0, f1, cc2);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                S.C[i * 3 + 0] = c0[i];
+                S.C[i * 3 + 1] = c1[i];
+                S.C[i * 3 + 2] = cc2[i];
+            }
+        }
+        S.cF = R(0);
+        if (model == SX_MODEL_NH) {
+            // P = (mu + h) I + mu D + h ((tr D) I - D^T + cof D) (cof(I + D) =
+            // (1 + tr D) I - D^T + cof D), mu + h = (mu u + lambda ln J)/J in
+            // double: the O(mu) parts of mu F and h C cancel at rest
+            const double h = (lamd * lnJ - mud) / J;
+            const double s0 = (mud * Jm1 + lamd * lnJ) / J;
+            R cofD[9];
+            cofD[0] = (R)(D[4] * D[8] - D[5] * D[7]);
+            cofD[1] = (R)(D[5] * D[6] - D[3] * D[8]);
+            cofD[2] = (R)(D[3] * D[7] - D[4] * D[6]);
+            cofD[3] = (R)(D[2] * D[7] - D[1] * D[8]);
+            cofD[4] = (R)(D[0] * D[8] - D[2] * D[6]);
+            cofD[5] = (R)(D[1] * D[6] - D[0] * D[7]);
+            cofD[6] = (R)(D[1] * D[5] - D[2] * D[4]);
+            cofD[7] = (R)(D[2] * D[3] - D[0] * D[5]);
+            cofD[8] = (R)(D[0] * D[4] - D[1] * D[3]);
+            const R hr = (R)h, mr = (R)mud, sr = (R)s0, tr = (R)trD;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    P[i * 3 + j] = ((i == j) ? sr + hr * tr : R(0)) + mr * (R)D[i * 3 + j] +
+                                   hr * (cofD[i * 3 + j] - (R)D[j * 3 + i]);
+            S.cI = V * mr;
+            S.cC = V * (R)((lamd + mud - lamd * lnJ) / (J * J));
+            S.cS = V * hr;
+        } else {
+            const R k2 = (R)(2.0 * kmu), lr = (R)lamd, ur = (R)Jm1;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) P[k] = k2 * (R)Pd[k] + lr * ur * S.C[k];
+            S.cI = V * k2;
+            S.cC = V * lr;
+            S.cS = V * lr * ur;
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            g[3 * n + i] = V * (P[i * 3 + 0] * S.G[n][0] + P[i * 3 + 1] * S.G[n][1] +
+                                P[i * 3 + 2] * S.G[n][2]);
+    return E;
+}
+
+// one 3x3 StVK block (a, b) from u_a = F G_a
+template <typename R>
+__device__ __forceinline__ void stvk_block(const StvkCore<R>& T, const R* Ga, const R* Gb,
+                                           const R* ua, const R* ub, R* out)
+{
+    R sg[3];
+    matvec3(T.Sm, Gb, sg);
+    const R gsg = Ga[0] * sg[0] + Ga[1] * sg[1] + Ga[2] * sg[2];
+    const R gg = Ga[0] * Gb[0] + Ga[1] * Gb[1] + Ga[2] * Gb[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            out[i * 3 + k] = gg * T.FF[i * 3 + k] + T.cU * ub[i] * ua[k] +
+                             T.cL * ua[i] * ub[k] + (i == k ? gsg : R(0));
+}
+
+template <typename R, typename HT>
+__device__ __noinline__ void eval_model(const ElemLaunch& L, int scene, int blk, const SceneDev& S,
+                           const ElemBlock& B, int64_t e, ThreadOut& o)
+{
+    const int4 t = B.conn[e];
+    double xg[12];
+    const int nid[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const double* p = S.x + 3 * (int64_t)nid[a];
+        xg[3 * a + 0] = p[0];
+        xg[3 * a + 1] = p[1];
+        xg[3 * a + 2] = p[2];
+    }
+    double Dinv[9], Rl[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Dinv[k] = B.Dminv[(int64_t)k * B.n + e];
+    const int model = B.model;
+    const bool lagged = model == SX_MODEL_COROT || model == SX_MODEL_ARAP;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rl[k] = lagged ? B.R[(int64_t)k * B.n + e] : 0.0;
+    SnhCore<R> C;
+    StvkCore<R> T;
+    R g[12];
+    int bad = 0;
+    o.E = model_core<R>(model, xg, Dinv, Rl, B.V[e], B.mu[e], B.lam[e], L.level, C, T, g, bad);
+    if (bad) o.bad = 1;
+    if (!isfinite(o.E)) o.nonfinite = 1;
+    const int64_t gid = B.base + e;
+    if (L.level >= 1) {
+        double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            gout[k] = bad ? 0.0 : (double)g[k];
+            if (!bad && !isfinite((double)g[k])) o.nonfinite = 1;
+        }
+    }
+    if (L.level >= 2) {
+        const bool stvk = model == SX_MODEL_STVK;
+        R u[4][3], v[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            matvec3(C.F, C.G[a], u[a]);
+            if (!stvk) matvec3(C.C, C.G[a], v[a]);
+        }
+        auto blockfn = [&](int a, int b, R* out) {
+            if (bad) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) out[k] = R(0);
+            } else if (stvk) {
+                stvk_block(T, C.G[a], C.G[b], u[a], u[b], out);
+            } else {
+                snh_block(C, C.G[a], C.G[b], u[a], u[b], v[a], v[b], a == b, out);
+            }
+        };
+        HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
+        double* full = L.out_H ? L.out_H + 144 * e : nullptr;
+        write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
+        if (L.project && !bad) {
+            // 9x9 translation-free block: the same block forms on the
+            // Hadamard combinations K_c of the G_a
+            R K[3][3], uk[3][3], vk[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                had_fwd(C.G[0][j], C.G[1][j], C.G[2][j], C.G[3][j], K[0][j], K[1][j], K[2][j]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                matvec3(C.F, K[c], uk[c]);
+                if (!stvk) matvec3(C.C, K[c], vk[c]);
+            }
+            double M[45];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int d = c; d < 3; ++d) {
+                    R bl[9];
+                    if (stvk) stvk_block(T, K[c], K[d], uk[c], uk[d], bl);
+                    else snh_block(C, K[c], K[d], uk[c], uk[d], vk[c], vk[d], c == d, bl);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+                            if (3 * d + k <= 3 * c + i || c != d)
+                                M[pk(3 * d + k, 3 * c + i)] = (double)bl[i * 3 + k];
+                }
+            o.clamped = queue_if_indefinite(L, scene, blk, e, M);
+        }
+    }
+}
+
+template <typename R, typename HT>
+__device__ void eval_hinge(const ElemLaunch& L, const SceneDev& S, const ElemBlock& B,
+                           int64_t e, ThreadOut& o)
+{
+    const int4 t = B.conn[e];
+    const int nid[4] = {t.x, t.y, t.z, t.w};
+    // s = sum_a q_a x_a, formed relative to node 0 (exact for any q once the
+    // q-sum term is added back; for a translation-free hinge it vanishes)
+    double x0[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x0[i] = S.x[3 * (int64_t)nid[0] + i];
+    double qd[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) qd[a] = B.q[(int64_t)a * B.n + e];
+    const double qs = qd[0] + qd[1] + qd[2] + qd[3];
+    double sd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sd[i] = qs * x0[i];
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) sd[i] += qd[a] * (S.x[3 * (int64_t)nid[a] + i] - x0[i]);
+    const double kcd = B.kb * B.c[e];
+    o.E = 0.5 * kcd * (sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
+    if (!isfinite(o.E)) o.nonfinite = 1;
+    const R kc = (R)kcd;
+    const R s[3] = {(R)sd[0], (R)sd[1], (R)sd[2]};
+    R q[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) q[a] = (R)qd[a];
+    const int64_t gid = B.base + e;
+    if (L.level >= 1) {
+        double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) gout[3 * a + i] = (double)(kc * q[a] * s[i]);
+    }
+    if (L.level >= 2) {
+        auto blockfn = [&](int a, int b, R* out) {
+            R h = kc * q[a] * q[b];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) out[k] = (k % 4 == 0) ? h : R(0);
+        };
+        HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
+        double* full = L.out_H ? L.out_H + 144 * e : nullptr;
+        write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
+    }
+}
+
+template <typename R, typename HT>
+__device__ void eval_barrier(const ElemLaunch& L, int scene, int blk, const SceneDev& S,
+                             const ElemBlock& B, int64_t e, ThreadOut& o)
+{
+    const int4 t = B.conn[e];
+    const int nid[4] = {t.x, t.y, t.z, t.w};
+    // coordinates relative to the point, formed in double
+    double xr[12];
+    double p0[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) p0[i] = S.x[3 * (int64_t)nid[0] + i];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xr[3 * a + i] = S.x[3 * (int64_t)nid[a] + i] - p0[i];
+    BarrierOut<R> bo;
+    int st = barrier_eval<R>(xr, (R)B.dhat, (R)B.kappa, L.level, bo);
+    double Ed = (double)bo.E;
+    if (sizeof(R) != sizeof(double)) {
+        // the energy (the line-search quantity) is always evaluated in double
+        BarrierOut<double> bd;
+        const int sd = barrier_eval<double>(xr, B.dhat, B.kappa, 0, bd);
+        Ed = (sd == 1) ? bd.E : 0.0;
+        if (sd != 1) st = sd;
+    }
+    const int64_t gid = B.base + e;
+    if (st < 0) o.bad = 1;
+    o.E = (st == 1) ? Ed : 0.0;
+    if (!isfinite(o.E)) o.nonfinite = 1;
+    if (L.level >= 1) {
+        double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) gout[k] = (st == 1) ? (double)bo.g[k] : 0.0;
+    }
+    if (L.level >= 2) {
+        auto blockfn = [&](int a, int b, R* out) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    out[i * 3 + k] = (st == 1) ? bo.H[(3 * a + i) * 12 + 3 * b + k] : R(0);
+        };
+        HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
+        double* full = L.out_H ? L.out_H + 144 * e : nullptr;
+        write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
+        if (st == 1 && L.project) {
+            // M = (Hd kron I3) H (Hd kron I3) restricted to the modes c, d = 1..3
+            double M[45];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    double Tm[4][3];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        double h[4];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            h[b] = 0.5 * ((double)bo.H[(3 * a + i) * 12 + 3 * b + k] +
+                                          (double)bo.H[(3 * b + k) * 12 + 3 * a + i]);
+                        had_fwd(h[0], h[1], h[2], h[3], Tm[a][0], Tm[a][1], Tm[a][2]);
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        double y[3];
+                        had_fwd(Tm[0][d], Tm[1][d], Tm[2][d], Tm[3][d], y[0], y[1], y[2]);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            if (3 * c + i >= 3 * d + k) M[pk(3 * c + i, 3 * d + k)] = y[c];
+                    }
+                }
+            o.clamped = queue_if_indefinite(L, scene, blk, e, M);
+        }
+    }
+}
+
+// KINDS: bit mask of the stencil kinds compiled in (1 SNH, 2 hinge, 4
+// barrier), 8 for the F-space projection of the SNH tets (project mode
+// 2) and 16 for tets of the other densities. A batch with SNH tets only
+// runs an SNH-only instantiation, which needs fewer registers than the one
+// that can take every kind.
+template <typename R, typename HT, int KINDS>
+__global__ void __launch_bounds__(kElemThreads)
+k_elements(ElemLaunch L)
+{
+    __shared__ double sE[kElemThreads];
+    __shared__ int sI[3][kElemThreads];
+    __shared__ int tile_id;
+    for (;;) {
+        if (threadIdx.x == 0) tile_id = atomicAdd(L.queue, 1);
+        __syncthreads();
+        const int ti = tile_id;
+        __syncthreads();
+        if (ti >= L.ntiles) return;
+        const Tile T = L.tiles[ti];
+        const SceneDev& S = L.scenes[T.scene];
+        ThreadOut o{0.0, 0, 0, 0};
+        if (S.sc == nullptr || S.sc->active) {
+            const ElemBlock& B = S.blk[T.blk];
+            if ((int)threadIdx.x < T.count) {
+                const int64_t e = T.start + threadIdx.x;
+                if ((KINDS & 16) && B.kind == SX_KIND_SNH_TET4 && B.model != SX_MODEL_SNH)
+                    eval_model<R, HT>(L, T.scene, T.blk, S, B, e, o);
+                else if ((KINDS & 1) && B.kind == SX_KIND_SNH_TET4)
+                    eval_snh<R, HT, (KINDS & 8) != 0>(L, T.scene, T.blk, S, B, e, o);
+                else if ((KINDS & 2) && B.kind == SX_KIND_HINGE4)
+                    eval_hinge<R, HT>(L, S, B, e, o);
+                else if ((KINDS & 4) && B.kind == SX_KIND_PT_BARRIER)
+                    eval_barrier<R, HT>(L, T.scene, T.blk, S, B, e, o);
+                if (L.out_E) L.out_E[e] = o.E;
+                else S.Ee[B.base + e] = o.E;
+            }
+        }
+        // fixed-order tile reductions
+        sE[threadIdx.x] = o.E;
+        sI[0][threadIdx.x] = o.bad;
+        sI[1][threadIdx.x] = o.nonfinite;
+        sI[2][threadIdx.x] = o.clamped;
+        __syncthreads();
+        for (int w = kElemThreads / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) {
+                sE[threadIdx.x] += sE[threadIdx.x + w];
+                sI[0][threadIdx.x] += sI[0][threadIdx.x + w];
+                sI[1][threadIdx.x] += sI[1][threadIdx.x + w];
+                sI[2][threadIdx.x] += sI[2][threadIdx.x + w];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (L.tile_E) L.tile_E[ti] = sE[0];
+            if (L.tile_bad) L.tile_bad[ti] = sI[0][0];
+            if (L.tile_nonfinite) L.tile_nonfinite[ti] = sI[1][0];
+            if (L.tile_clamped) L.tile_clamped[ti] = sI[2][0];
+        }
+        __syncthreads();
+    }
+}
+
+// host-side access to the instantiations of one translation unit
+template <int K>
+const void* elements_kernel_ptr(bool f32)
+{
+    return f32 ? (const void*)k_elements<float, float, K> : (const void*)k_elements<double, double, K>;
+}
+
+template <int K>
+void elements_launch(bool f32, const ElemLaunch& L, int grid, cudaStream_t s)
+{
+    if (f32) k_elements<float, float, K><<<grid, kElemThreads, 0, s>>>(L);
+    else k_elements<double, double, K><<<grid, kElemThreads, 0, s>>>(L);
+}
+
+}  // namespace sx

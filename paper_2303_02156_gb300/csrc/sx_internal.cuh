@@ -41,6 +41,7 @@ __host__ __device__ constexpr int up_index(int a, int b)
 
 struct ElemBlock {
     int kind;            // SX_KIND_*
+    int model;           // SX_MODEL_* of a tet4 block
     int64_t n;           // stencils in this block
     int64_t base;        // first scene-global stencil id of this block
     const int4* conn;
@@ -49,6 +50,7 @@ struct ElemBlock {
     const double* V;
     const double* mu;
     const double* lam;
+    const double* R;      // [9][n] lagged rotations (COROT, ARAP)
     // hinge
     const double* q;      // [4][n]
     const double* c;
@@ -190,6 +192,19 @@ int clamp_block_threads();
 // the element kernel instantiations: variant 0 every kind, 1 SNH only, 2
 // every kind with the F-space projection, 3 SNH only with it
 const void* elements_kernel(int precision, int variant);
+constexpr int kElemVariants = 6;
+// the element-kernel instantiations of each translation unit (KINDS values)
+const void* elements_kernel_snh(int kinds, bool f32);      // 1, 7
+const void* elements_kernel_fproj(int kinds, bool f32);    // 9, 15
+const void* elements_kernel_models(int kinds, bool f32);   // 25, 31
+cudaError_t launch_elements_snh(int kinds, bool f32, const ElemLaunch& L, int grid,
+                                cudaStream_t s);
+cudaError_t launch_elements_fproj(int kinds, bool f32, const ElemLaunch& L, int grid,
+                                  cudaStream_t s);
+cudaError_t launch_elements_models(int kinds, bool f32, const ElemLaunch& L, int grid,
+                                   cudaStream_t s);
+cudaError_t launch_tet_rotations(const int4* conn, const double* x, const double* Dminv,
+                                 int64_t n, double* R, cudaStream_t s);
 int elements_variant(int kinds, int project);
 
 // point-triangle pair activation and order-preserving compaction

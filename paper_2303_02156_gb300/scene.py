@@ -104,6 +104,33 @@ class Scene:
                                 float(density), int(literal), self.stream, C.byref(eid))
         return self._id(rc, eid, sx.SX_KIND_SNH_TET4, n)
 
+    def add_tet(self, model, tets, young, poisson, density=1000.0):
+        """Linear tets of density ``model`` (sx.SX_MODEL_*)."""
+        tets = _i32(tets); n = tets.shape[0]
+        E = _f64(np.broadcast_to(young, (n,))); nu = _f64(np.broadcast_to(poisson, (n,)))
+        eid = C.c_int()
+        rc = sx.sx_add_tet4(self.h, int(model), tets.ctypes.data, n, E.ctypes.data,
+                            nu.ctypes.data, float(density), self.stream, C.byref(eid))
+        return self._id(rc, eid, sx.SX_KIND_TET4, n)
+
+    def update_rotations(self):
+        """Lagged rotations of the COROT / ARAP blocks := polar rotations of
+        F at the current state."""
+        self.ctx.check(sx.sx_update_rotations(self.h, self.stream))
+
+    def rotations(self, energy_id):
+        """Lagged rotations of a COROT / ARAP block, n x 3 x 3."""
+        n = self.blocks[energy_id][1]
+        R = np.empty((n, 9))
+        self.ctx.check(sx.sx_get_rotations(self.h, energy_id, R.ctypes.data if n else None,
+                                           self.stream))
+        return R.reshape(n, 3, 3)
+
+    def set_rotations(self, energy_id, R):
+        R = _f64(R).reshape(-1, 9)
+        self.ctx.check(sx.sx_set_rotations(self.h, energy_id,
+                                           R.ctypes.data if R.shape[0] else None, self.stream))
+
     def add_hinge(self, stencils, q, c, kb):
         st = _i32(stencils); n = st.shape[0]
         q = _f64(q); c = _f64(c)

@@ -23,6 +23,8 @@ SX_FP64, SX_FP32 = 0, 1
 SX_KIND_SNH_TET4, SX_KIND_HINGE4, SX_KIND_PT_BARRIER = 0, 1, 2
 SX_SERVER_MAX_LANES = 8
 SX_PROJECT_NONE, SX_PROJECT_ELEMENT, SX_PROJECT_MATERIAL = 0, 1, 2
+SX_KIND_TET4 = SX_KIND_SNH_TET4
+SX_MODEL_SNH, SX_MODEL_NH, SX_MODEL_STVK, SX_MODEL_COROT, SX_MODEL_ARAP = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "SX_OK", -1: "SX_EINVAL", -2: "SX_ENOMEM", -3: "SX_ECUDA", -4: "SX_ENAN",
                 -5: "SX_ENOTCONV", -6: "SX_ESTATE", -7: "SX_EDEGENERATE", -8: "SX_EBUDGET",
@@ -39,7 +41,8 @@ EXPORTS = [
     "sx_copy_bsr", "sx_copy_grad", "sx_scene_info", "sx_block_info", "sx_eval_stats",
     "sx_profile", "sx_profile_read", "sx_eval_elements_noalloc",
     "sx_autotune", "sx_set_launch_shape", "sx_get_launch_shape", "sx_set_pairs",
-    "sx_compact_pairs",
+    "sx_compact_pairs", "sx_add_tet4", "sx_update_rotations", "sx_get_rotations",
+    "sx_set_rotations",
     "sx_server_create", "sx_server_set_lanes", "sx_server_submit", "sx_server_poll", "sx_server_result",
     "sx_server_drain", "sx_server_stats", "sx_server_destroy",
 ]
@@ -143,6 +146,10 @@ _SIGS = {
     "sx_server_create": (_I, [_P, _I64, C.POINTER(sx_newton_opts), _PP]),
     "sx_autotune": (_I, [_P, C.POINTER(_P), _I, _I, C.POINTER(sx_tune_report), _P]),
     "sx_set_pairs": (_I, [_P, _I, _P, _I64, _P]),
+    "sx_add_tet4": (_I, [_P, _I, _P, _I64, _P, _P, _D, _P, C.POINTER(_I)]),
+    "sx_update_rotations": (_I, [_P, _P]),
+    "sx_get_rotations": (_I, [_P, _I, _P, _P]),
+    "sx_set_rotations": (_I, [_P, _I, _P, _P]),
     "sx_compact_pairs": (_I, [_P, _I, C.POINTER(_I64), _P]),
     "sx_set_launch_shape": (_I, [_P, _I, _I, _I]),
     "sx_get_launch_shape": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I)]),
