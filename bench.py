@@ -198,7 +198,7 @@ def clamp_profile_figures():
     if not os.path.exists(path):
         return None, None, False
     h = hashlib.sha256()
-    for f in ["sx_elements.cu", "sx_clamp.cuh"]:
+    for f in ["sx_clamp.cu", "sx_clamp.cuh"]:
         h.update(open(os.path.join(ROOT, "paper_2303_02156_gb300", "csrc", f), "rb").read())
     vals = {}
     for line in open(path):
@@ -220,7 +220,7 @@ def clamp_traffic_per_element():
     if not os.path.exists(path):
         return None
     h = hashlib.sha256()
-    for f in ["sx_elements.cu", "sx_clamp.cuh"]:
+    for f in ["sx_clamp.cu", "sx_clamp.cuh"]:
         h.update(open(os.path.join(ROOT, "paper_2303_02156_gb300", "csrc", f), "rb").read())
     want = h.hexdigest()[:16]
     vals = {}
