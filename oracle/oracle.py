@@ -68,6 +68,13 @@ def lib():
     L.orc_tet_batch.argtypes = [C.c_int, C.c_int, _dp, _ip, _dp, _dp, _dp, _dp, C.c_void_p,
                                 C.c_int, C.c_int, _dp, C.c_void_p, C.c_void_p]
     L.orc_tet_batch.restype = C.c_int
+    L.orc_friction_lag_batch.argtypes = [C.c_int, _dp, _ip, C.c_double, C.c_double, _dp, _dp,
+                                         _dp, _dp]
+    L.orc_friction_element.argtypes = [_dp, _dp, _dp, C.c_double, _dp, C.c_double, C.c_double,
+                                       C.c_double, _dp, _dp, _dp]
+    L.orc_friction_batch.argtypes = [C.c_int, _dp, _ip, _dp, _dp, _dp, _dp, C.c_double,
+                                     C.c_double, C.c_double, C.c_int, _dp, C.c_void_p,
+                                     C.c_void_p]
     L.orc_hinge_element.argtypes = [_dp, _dp, C.c_double, C.c_double, _dp, _dp, _dp]
     L.orc_hinge_batch.argtypes = [C.c_int, _dp, _ip, _dp, _dp, C.c_double, C.c_int,
                                   _dp, C.c_void_p, C.c_void_p]
@@ -231,6 +238,36 @@ def lagged_rotations(x, tets, Dminv):
     return (U @ Vt).reshape(-1, 9)
 
 
+# ---------------------------------------------------------------- friction
+def friction_lag(x, pairs, dhat, kappa):
+    """Lagged contact data per pair at state x: closest-point weights beta
+    (P x 3), tangent basis T (P x 2 x 3), contact force fn (P), separation
+    dxt = p - c (P x 3)."""
+    pairs = _i32(pairs).reshape(-1, 4); P = pairs.shape[0]
+    beta = np.zeros((P, 3)); T = np.zeros((P, 6)); fn = np.zeros(P); dxt = np.zeros((P, 3))
+    lib().orc_friction_lag_batch(P, _f64(x).ravel(), pairs, float(dhat), float(kappa), beta, T,
+                                 fn, dxt)
+    return {"beta": beta, "T": T.reshape(P, 2, 3), "fn": fn, "dxt": dxt}
+
+
+def friction_element(xe, beta, T, fn, dxt, mu, yhat, dt):
+    E = np.zeros(1); g = np.zeros(12); H = np.zeros(144)
+    lib().orc_friction_element(_f64(xe).ravel(), _f64(beta), _f64(T).ravel(), float(fn),
+                               _f64(dxt), float(mu), float(yhat), float(dt), E, g, H)
+    return E[0], g, H.reshape(12, 12)
+
+
+def friction_batch(x, pairs, lag, mu, yhat, dt, level=LEVEL_EGH):
+    pairs = _i32(pairs).reshape(-1, 4); P = pairs.shape[0]
+    E = np.empty(P)
+    g = np.empty((P, 12)) if level >= 1 else None
+    H = np.empty((P, 12, 12)) if level >= 2 else None
+    lib().orc_friction_batch(P, _f64(x).ravel(), pairs, _f64(lag["beta"]),
+                             _f64(lag["T"]).reshape(P, 6), _f64(lag["fn"]), _f64(lag["dxt"]),
+                             float(mu), float(yhat), float(dt), level, E, _ptr(g), _ptr(H))
+    return E, g, H
+
+
 # ---------------------------------------------------------------- hinge
 def hinge_element(xe, q, c, kb):
     E = np.zeros(1); g = np.zeros(12); H = np.zeros(144)
@@ -351,6 +388,10 @@ class _OrcScene(C.Structure):
         ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("slots", C.c_void_p),
         ("diag_slot", C.c_void_p), ("nnzb", C.c_longlong),
         ("snh_model", C.c_int), ("snh_R", C.c_void_p),
+        ("n_fr", C.c_int), ("fr", C.c_void_p), ("fr_mu", C.c_double),
+        ("fr_yhat", C.c_double), ("fr_dhat", C.c_double), ("fr_kappa", C.c_double),
+        ("fr_beta", C.c_void_p), ("fr_T", C.c_void_p), ("fr_fn", C.c_void_p),
+        ("fr_dxt", C.c_void_p),
     ]
 
 
@@ -372,7 +413,7 @@ class Scene:
     registration order (SNH tets, hinges, point-triangle pairs), pinned
     nodes; the pattern and slot maps are built at construction."""
 
-    def __init__(self, N, mass=None, snh=None, hinge=None, pt=None, pinned=None):
+    def __init__(self, N, mass=None, snh=None, hinge=None, pt=None, pinned=None, fr=None):
         self.N = int(N)
         self._keep = []
         self.R = None
@@ -413,6 +454,19 @@ class Scene:
             s.pt = _ptr(pr)
             s.dhat, s.kappa = float(pt["dhat"]), float(pt["kappa"])
             conns.append(pr)
+        self.fr = None
+        if fr is not None:
+            pr = _i32(fr["pairs"]).reshape(-1, 4)
+            P = pr.shape[0]
+            self.fr = {"pairs": pr, "beta": np.zeros((P, 3)), "T": np.zeros((P, 6)),
+                       "fn": np.zeros(P), "dxt": np.zeros((P, 3))}
+            s.n_fr = P
+            s.fr = _ptr(pr)
+            s.fr_mu, s.fr_yhat = float(fr["mu"]), float(fr["yhat"])
+            s.fr_dhat, s.fr_kappa = float(fr["dhat"]), float(fr["kappa"])
+            s.fr_beta, s.fr_T = _ptr(self.fr["beta"]), _ptr(self.fr["T"])
+            s.fr_fn, s.fr_dxt = _ptr(self.fr["fn"]), _ptr(self.fr["dxt"])
+            conns.append(pr)
         self.pinned_mask = np.zeros(self.N, dtype=np.uint8)
         if pinned is not None and len(pinned):
             self.pinned_mask[np.asarray(pinned)] = 1
@@ -439,6 +493,14 @@ class Scene:
         bad = lib().orc_scene_eval(C.byref(self._s), x, _ptr(xt_), float(dt), level,
                                    int(project), C.byref(E), _ptr(grad), _ptr(vals))
         return E.value, grad, vals, bad
+
+    def friction_lag(self, x):
+        """Lag the friction block's contact data at the state x (what a
+        Newton step does at its start)."""
+        f = self.fr
+        lib().orc_friction_lag_batch(f["pairs"].shape[0], _f64(x).ravel(), f["pairs"],
+                                     self._s.fr_dhat, self._s.fr_kappa, f["beta"], f["T"],
+                                     f["fn"], f["dxt"])
 
     def set_rotations(self, R):
         """Lagged rotations of the tet block (COROT / ARAP), 9 per tet."""

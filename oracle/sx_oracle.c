@@ -22,6 +22,9 @@
  *   - IPC log barrier E = -k (d - dhat)^2 ln(d/dhat) on the unsigned
  *     point-triangle distance [§6.4, Eq. 15], active only for d < dhat
  *     [§5.2 "Conditional evaluations", Eq. 9].
+ *   - Lagged IPC friction on point-triangle pairs [§6.4, friction
+ *     potential] with its lag data (closest point, tangent basis, contact
+ *     force) taken at the start of a step.
  *   - Per-element projection to positive semi-definiteness [§5.2
  *     "Projection to positive semi-definiteness", Algorithm 1 ProjectToPD]
  *     by cyclic Jacobi eigen-decomposition and eigenvalue clamping.
@@ -968,6 +971,195 @@ int orc_tet_batch(int model, int T, const double* x, const int* tets, const doub
 }
 
 /* ------------------------------------------------------------------ */
+/* Lagged IPC friction on point-triangle pairs (§6.4, friction          */
+/* potential)                                                           */
+/* ------------------------------------------------------------------ */
+
+/* Closest point of triangle (a, b, c) to p as barycentric weights, from
+ * the Voronoi region of orc_pt_region: a vertex gets weight 1, an edge
+ * (u, v) the clamped projection parameter t (weights 1 - t, t), the face
+ * the barycentrics of the plane projection. */
+static void pt_closest_weights(const double* xe, double beta[3])
+{
+    const double *p = xe, *t[3] = {xe + 3, xe + 6, xe + 9};
+    int reg = orc_pt_region(xe);
+    beta[0] = beta[1] = beta[2] = 0.0;
+    if (reg <= 2) {
+        beta[reg] = 1.0;
+        return;
+    }
+    if (reg <= 5) {
+        int u = reg - 3, v = (reg - 3 + 1) % 3;
+        double num = 0.0, den = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double e = t[v][k] - t[u][k];
+            num += (p[k] - t[u][k]) * e;
+            den += e * e;
+        }
+        double tt = den > 0.0 ? num / den : 0.0;
+        if (tt < 0.0) tt = 0.0;
+        if (tt > 1.0) tt = 1.0;
+        beta[u] = 1.0 - tt;
+        beta[v] = tt;
+        return;
+    }
+    double ab[3], ac[3], ap[3];
+    for (int k = 0; k < 3; ++k) {
+        ab[k] = t[1][k] - t[0][k];
+        ac[k] = t[2][k] - t[0][k];
+        ap[k] = p[k] - t[0][k];
+    }
+    double d00 = 0, d01 = 0, d11 = 0, d20 = 0, d21 = 0;
+    for (int k = 0; k < 3; ++k) {
+        d00 += ab[k] * ab[k]; d01 += ab[k] * ac[k]; d11 += ac[k] * ac[k];
+        d20 += ap[k] * ab[k]; d21 += ap[k] * ac[k];
+    }
+    double den = d00 * d11 - d01 * d01;
+    double v = (d11 * d20 - d01 * d21) / den, w = (d00 * d21 - d01 * d20) / den;
+    beta[0] = 1.0 - v - w;
+    beta[1] = v;
+    beta[2] = w;
+}
+
+/* Lagged contact data of one pair at the state xe (p, t0, t1, t2), held
+ * for a time step like IPC's lagged friction. READINGS (the paper gives
+ * the potential, not its lagged inputs): the contact point is the closest
+ * point c of the triangle; f_n = -b'(d) is the magnitude of the barrier's
+ * contact force at d = |p - c| (zero outside 0 < d < dhat); T (2x3, rows)
+ * is an orthonormal basis of the plane normal to p - c (any basis gives
+ * the same potential). out: beta[3], T[6], fn, dxt[3] = p - c. */
+void orc_friction_lag(const double* xe, double dhat, double kappa, double* beta, double* T,
+                      double* fn, double* dxt)
+{
+    pt_closest_weights(xe, beta);
+    double r[3], d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double c = beta[0] * xe[3 + k] + beta[1] * xe[6 + k] + beta[2] * xe[9 + k];
+        r[k] = xe[k] - c;
+        dxt[k] = r[k];
+        d2 += r[k] * r[k];
+    }
+    double d = sqrt(d2);
+    *fn = 0.0;
+    if (d > 0.0 && d < dhat) {
+        double b, b1, b2;
+        orc_barrier_1d(d, dhat, kappa, &b, &b1, &b2);
+        *fn = -b1;
+    }
+    double n[3] = {0.0, 0.0, 1.0};
+    if (d > 0.0)
+        for (int k = 0; k < 3; ++k) n[k] = r[k] / d;
+    /* first tangent: n x (the axis least aligned with n), normalized */
+    int ax = 0;
+    for (int k = 1; k < 3; ++k)
+        if (fabs(n[k]) < fabs(n[ax])) ax = k;
+    double e[3] = {0.0, 0.0, 0.0};
+    e[ax] = 1.0;
+    double t1[3] = {n[1] * e[2] - n[2] * e[1], n[2] * e[0] - n[0] * e[2], n[0] * e[1] - n[1] * e[0]};
+    double l = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+    for (int k = 0; k < 3; ++k) t1[k] /= l;
+    double t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2], n[0] * t1[1] - n[1] * t1[0]};
+    for (int k = 0; k < 3; ++k) {
+        T[k] = t1[k];
+        T[3 + k] = t2[k];
+    }
+}
+
+/* f0(s) = dt f(s/dt) with the friction profile of §6.4:
+ * f(y) = -y^3/(3 yh^2) + y^2/yh + yh/3 for y <= yh, y otherwise; and its
+ * first two derivatives in s. */
+static void friction_f0(double s, double yh, double dt, double* f, double* f1, double* f2)
+{
+    double y = s / dt;
+    if (y <= yh) {
+        *f = dt * (-y * y * y / (3.0 * yh * yh) + y * y / yh + yh / 3.0);
+        *f1 = -y * y / (yh * yh) + 2.0 * y / yh;
+        *f2 = (-2.0 * y / (yh * yh) + 2.0 / yh) / dt;
+    } else {
+        *f = dt * y;
+        *f1 = 1.0;
+        *f2 = 0.0;
+    }
+}
+
+/* One friction stencil: E = mu fn f0(s), s = |T (dx - dxt)|, with
+ * dx = p - sum_i beta_i t_i the current separation at the lagged contact
+ * point, so T (dx - dxt) / dt is the tangential relative velocity y of
+ * §6.4 over the step. READING: the potential is taken as dt mu fn f(y)
+ * (= mu fn f0(s)), the incremental potential of the friction force, whose
+ * sliding force is mu fn (IPC's lagged friction potential with threshold
+ * yh dt). At s = 0 the derivatives are the limits (g = 0,
+ * H = mu fn 2/(yh dt) J^T J). */
+void orc_friction_element(const double* xe, const double* beta, const double* T, double fn,
+                          const double* dxt, double mu, double yhat, double dt,
+                          double* E, double* g, double* H)
+{
+    q2 u[2];
+    for (int j = 0; j < 2; ++j) {
+        q2_const(&u[j], 0.0);
+        for (int k = 0; k < 3; ++k) {
+            double w = xe[k] - beta[0] * xe[3 + k] - beta[1] * xe[6 + k] - beta[2] * xe[9 + k]
+                     - dxt[k];
+            u[j].v += T[3 * j + k] * w;
+            u[j].g[k] += T[3 * j + k];
+            for (int i = 0; i < 3; ++i) u[j].g[3 * (i + 1) + k] -= T[3 * j + k] * beta[i];
+        }
+    }
+    q2 s2, t;
+    q2_mul(&s2, &u[0], &u[0]);
+    q2_mul(&t, &u[1], &u[1]);
+    q2_add(&s2, &s2, &t, 1.0);
+    const double k = mu * fn;
+    if (s2.v > 0.0) {
+        double sv = sqrt(s2.v), f, f1, f2;
+        q2 s;
+        q2_apply(&s, &s2, sv, 0.5 / sv, -0.25 / (sv * sv * sv));
+        friction_f0(sv, yhat, dt, &f, &f1, &f2);
+        q2_apply(&t, &s, f, f1, f2);
+        *E = k * t.v;
+        if (g) for (int c = 0; c < 12; ++c) g[c] = k * t.g[c];
+        if (H) for (int c = 0; c < 144; ++c) H[c] = k * t.H[c];
+        return;
+    }
+    *E = k * dt * yhat / 3.0;
+    if (g) memset(g, 0, 12 * sizeof(double));
+    if (H) {
+        /* J^T J with J the (constant) gradients of u */
+        for (int a = 0; a < 12; ++a)
+            for (int b = 0; b < 12; ++b)
+                H[a * 12 + b] = k * 2.0 / (yhat * dt) *
+                                (u[0].g[a] * u[0].g[b] + u[1].g[a] * u[1].g[b]);
+    }
+}
+
+void orc_friction_lag_batch(int P, const double* x, const int* pairs, double dhat, double kappa,
+                            double* beta, double* T, double* fn, double* dxt)
+{
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < P; ++e) {
+        double xe[12];
+        gather4(x, pairs + 4 * e, xe);
+        orc_friction_lag(xe, dhat, kappa, beta + 3 * (size_t)e, T + 6 * (size_t)e, fn + e,
+                         dxt + 3 * (size_t)e);
+    }
+}
+
+void orc_friction_batch(int P, const double* x, const int* pairs, const double* beta,
+                        const double* T, const double* fn, const double* dxt, double mu,
+                        double yhat, double dt, int level, double* E_e, double* g_e, double* H_e)
+{
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < P; ++e) {
+        double xe[12];
+        gather4(x, pairs + 4 * e, xe);
+        orc_friction_element(xe, beta + 3 * (size_t)e, T + 6 * (size_t)e, fn[e],
+                             dxt + 3 * (size_t)e, mu, yhat, dt, E_e + e,
+                             level >= 1 ? g_e + 12 * (size_t)e : NULL,
+                             level >= 2 ? H_e + 144 * (size_t)e : NULL);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* 3x3 block CRS pattern and slot maps (§5.3)                           */
 /* ------------------------------------------------------------------ */
 
@@ -1221,6 +1413,15 @@ typedef struct {
      * (9 per tet, COROT / ARAP) */
     int snh_model;
     const double* snh_R;
+    /* lagged friction block on point-triangle pairs: its lag data is taken
+     * at the start of every Newton step (orc_newton_step writes it) */
+    int n_fr;
+    const int* fr;
+    double fr_mu, fr_yhat, fr_dhat, fr_kappa;
+    double* fr_beta;
+    double* fr_T;
+    double* fr_fn;
+    double* fr_dxt;
 } orc_scene;
 
 /* Full evaluation of E_BE = inertia + sum of element energies at x
@@ -1237,8 +1438,8 @@ static int scene_eval_impl(const orc_scene* s, const double* x, const double* x0
     if (level >= 2) memset(vals, 0, 9 * (size_t)s->nnzb * sizeof(double));
     double E = 0.0;
     size_t base = 0;
-    int counts[3] = {s->n_snh, s->n_hinge, s->n_pt};
-    for (int kind = 0; kind < 3; ++kind) {
+    int counts[4] = {s->n_snh, s->n_hinge, s->n_pt, s->n_fr};
+    for (int kind = 0; kind < 4; ++kind) {
         int n = counts[kind];
         if (n == 0) continue;
         double* Ee = (double*)malloc((size_t)n * sizeof(double));
@@ -1252,10 +1453,15 @@ static int scene_eval_impl(const orc_scene* s, const double* x, const double* x0
         } else if (kind == 1) {
             conn = s->hinge;
             orc_hinge_batch(n, x, conn, s->hinge_q, s->hinge_c, s->kb, level, Ee, ge, He);
-        } else {
+        } else if (kind == 2) {
             conn = s->pt;
             bad += orc_barrier_batch(n, x, conn, s->dhat, s->kappa, level, project,
                                      Ee, ge, He, NULL);
+        } else {
+            /* friction: PSD by construction, never projected */
+            conn = s->fr;
+            orc_friction_batch(n, x, conn, s->fr_beta, s->fr_T, s->fr_fn, s->fr_dxt, s->fr_mu,
+                               s->fr_yhat, dt, level, Ee, ge, He);
         }
         for (int e = 0; e < n; ++e) E += Ee[e];
         if (level >= 1)
@@ -1328,6 +1534,10 @@ int orc_newton_step(const orc_scene* s, double dt, const double gravity[3],
             /* increment xt - x0 = dt v + dt^2 g (Eq. 2) */
             xt[3 * n + i] = dt * v[3 * n + i] + dt * dt * gravity[i];
         }
+    /* lagged friction data at the start-of-step state */
+    if (s->n_fr)
+        orc_friction_lag_batch(s->n_fr, x0, s->fr, s->fr_dhat, s->fr_kappa, s->fr_beta, s->fr_T,
+                               s->fr_fn, s->fr_dxt);
     int status = ORC_ENOTCONV, it = 0, pcg_total = 0;
     double E, gn0 = 0.0, gn = 0.0;
     double fext = 0.0;   /* || M g_ext || over the free DOFs */
