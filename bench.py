@@ -341,6 +341,36 @@ def run_mixed(ctx, stream, flush, reps=5):
     out["note"] = ("one particle per pair (no vertex sharing among contact points), so the "
                    "barrier gathers reuse less than a real contact scene would")
     s.close()
+    # lagged friction on the same pairs (mu 0.3, yhat 1e-3 m/s, lag at the
+    # state with dt = 0.01): the same workload plus one friction stencil per pair
+    s = Scene(ctx, w["X"], stream=sh)
+    s.add_snh(w["tets"], w["E"], w["nu"], 1000.0)
+    s.add_hinge(w["hinges"], w["q"], w["c"], w["kb"])
+    s.add_barrier(w["pairs"], w["dhat"], w["kappa"])
+    s.add_friction(w["pairs"], 0.3, 1e-3, w["dhat"], w["kappa"])
+    s.add_node_mass(w["extra_mass"])
+    s.set_pinned(w["pinned"])
+    s.finalize()
+    s.set_state(x=w["x"])
+    s.update_friction(0.01)
+    fr = {"stencils": int(s.info()["n_stencils"])}
+    for name, prec in (("fp32", sx.SX_FP32), ("fp64", sx.SX_FP64)):
+        for _ in range(2):
+            ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(3):
+            flush.zero_()
+            e0.record(stream)
+            ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        fr[name] = {"ms_per_step": med, "stencils_per_s": fr["stencils"] / (med / 1e3)}
+    out["with_friction"] = fr
+    s.close()
     # changing contact pairs: the same scene with pair distances up to 2 dhat
     # (about half the pairs inactive), activation compaction + pattern
     # rebuild, and the FP32 pass before and after

@@ -78,6 +78,7 @@ extern "C" {
 #define SX_KIND_TET4 SX_KIND_SNH_TET4
 #define SX_KIND_HINGE4 1
 #define SX_KIND_PT_BARRIER 2
+#define SX_KIND_PT_FRICTION 3
 
 /* ---- tet4 densities (§7.1 "Non-linear material models", App. B) -------
  * SNH    Stable Neo-Hookean (§3.1 Eq. 7), parameters mu', lambda' as in
@@ -184,6 +185,30 @@ int sx_add_hinge4(sx_scene* scene, const int32_t* stencils, int64_t n,
  * d <= 0 makes sx_eval return SX_ESTATE. Synchronous. */
 int sx_add_pt_barrier(sx_scene* scene, const int32_t* pairs, int64_t n,
                       double dhat, double kappa, void* stream, int* energy_id);
+
+/* Lagged IPC friction on point-triangle pairs (§6.4, friction potential).
+ * Per pair (p, t0, t1, t2): E = mu fn f0(|T (dx - dx_lag)|), where
+ * dx = p - sum_i beta_i t_i is the separation at the lagged contact point,
+ * f0(s) = dt f(s / dt) and f(y) = -y^3/(3 yh^2) + y^2/yh + yh/3 for
+ * y <= yh, y otherwise (yh = yhat: the stick/slide velocity threshold), so
+ * that a sliding pair feels the Coulomb force mu fn. Lagged per pair by
+ * sx_update_friction and at the start of every Newton step (with the
+ * step's dt): the closest point's barycentric weights beta, an orthonormal
+ * basis T (2 x 3) of the plane normal to p - c, the contact force
+ * fn = -b'(d) of the barrier b(d) = -kappa (d - dhat)^2 ln(d / dhat) at
+ * d = |p - c| (0 outside 0 < d < dhat) and dx_lag = p - c. Until the first
+ * lag fn = 0 (no friction). The Hessian is PSD by construction and never
+ * projected. mu >= 0, yhat > 0, dhat > 0, kappa >= 0. Synchronous. */
+int sx_add_pt_friction(sx_scene* scene, const int32_t* pairs, int64_t n, double mu,
+                       double yhat, double dhat, double kappa, void* stream, int* energy_id);
+/* Lag every friction block of the scene at its current state with time
+ * step dt > 0 (stream-ordered). */
+int sx_update_friction(sx_scene* scene, double dt, void* stream);
+/* The lag of friction block `energy_id` (host or device arrays, any may be
+ * NULL): beta n x 3, T n x 6 (two rows), fn n, dx_lag n x 3. Synchronizes
+ * `stream`. */
+int sx_get_friction_lag(sx_scene* scene, int energy_id, double* beta, double* T, double* fn,
+                        double* dx_lag, void* stream);
 
 /* Add per-node mass (n_nodes doubles) to the lumped mass, e.g. for shell
  * vertices or free points that belong to no tet. Synchronous. */

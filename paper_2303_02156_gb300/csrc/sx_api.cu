@@ -38,6 +38,9 @@ struct BlockHost {
     double* c = nullptr;
     double kb = 0.0;
     double dhat = 0.0, kappa = 0.0;
+    // friction: lag [13][n] (beta, T, fn, dx_lag), mu, yhat, dt of the lag
+    double* flag = nullptr;
+    double mu_f = 0.0, yhat = 0.0, dt_f = 1.0;
 };
 
 constexpr int kNodeTile = 256;
@@ -221,6 +224,7 @@ int elem_grid(const sx_ctx* ctx, int precision, int kinds, int project, int ntil
 int kind_bit(const BlockHost& b)
 {
     if (b.kind == SX_KIND_SNH_TET4) return b.model == SX_MODEL_SNH ? 1 : 1 | 16;
+    if (b.kind == SX_KIND_PT_FRICTION) return 32;
     return b.kind == SX_KIND_HINGE4 ? 2 : 4;
 }
 
@@ -360,6 +364,10 @@ SceneDev make_desc(const sx_scene* s, bool trial)
         e.kb = h.kb;
         e.dhat = h.dhat;
         e.kappa = h.kappa;
+        e.flag = h.flag;
+        e.mu_f = h.mu_f;
+        e.yhat = h.yhat;
+        e.dt_f = h.dt_f;
     }
     d.x = trial ? s->x_trial : s->x;
     d.v = s->v;
@@ -471,7 +479,8 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         B->kinds = 0;
         for (sx_scene* s : B->scenes)
             for (auto& b : s->blocks) {
-                if (b.kind != SX_KIND_HINGE4) cap += b.n;
+                // hinges and friction are PSD by construction: never queued
+                if (b.kind != SX_KIND_HINGE4 && b.kind != SX_KIND_PT_FRICTION) cap += b.n;
                 if (b.n) B->kinds |= kind_bit(b);
             }
         if (!B->kinds) B->kinds = 1;
@@ -950,6 +959,16 @@ __global__ void k_identity_rotations(int64_t n, double* R)
     for (int k = 0; k < 9; ++k) R[(int64_t)k * n + e] = (k % 4 == 0) ? 1.0 : 0.0;
 }
 
+// [rows][n] layout -> n records of `rows` values
+__global__ void k_rows_to_records(const double* __restrict__ in, int64_t n, int rows,
+                                  double* __restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rows * n) return;
+    const int64_t e = i / rows, k = i % rows;
+    out[i] = in[k * n + e];
+}
+
 // row-major 3x3 per tet (n x 9) <-> the block's [9][n] layout
 __global__ void k_rot_transpose(const double* __restrict__ in, int64_t n, int to_soa,
                                 double* __restrict__ out)
@@ -1025,6 +1044,22 @@ BlockHost* lagged_block(sx_scene* s, int energy_id)
     return lagged_model(b) ? &b : nullptr;
 }
 
+// friction lag of every friction block at the current state with step dt
+// (a changed dt changes the block descriptors: new scene version)
+cudaError_t update_friction(sx_scene* s, double dt, cudaStream_t st)
+{
+    for (auto& b : s->blocks)
+        if (b.kind == SX_KIND_PT_FRICTION) {
+            if (b.dt_f != dt) {
+                b.dt_f = dt;
+                s->version++;
+            }
+            cudaError_t e = launch_friction_lag(s->x, b.conn, b.n, b.dhat, b.kappa, b.flag, st);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
 // R of every lagged block of the scene at its current state
 cudaError_t update_rotations(sx_scene* s, cudaStream_t st)
 {
@@ -1060,6 +1095,52 @@ int sx_update_rotations(sx_scene* s, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     s->stream = st;
     CK(update_rotations(s, st));
+    return SX_OK;
+}
+
+int sx_update_friction(sx_scene* s, double dt, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    if (!(dt > 0.0)) return fail(ctx, SX_EINVAL, "update_friction: dt must be > 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
+    CK(update_friction(s, dt, st));
+    return SX_OK;
+}
+
+int sx_get_friction_lag(sx_scene* s, int energy_id, double* beta, double* T, double* fn,
+                        double* dx_lag, void* stream)
+{
+    if (!s) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    if (energy_id < 0 || energy_id >= (int)s->blocks.size() ||
+        s->blocks[energy_id].kind != SX_KIND_PT_FRICTION)
+        return fail(ctx, SX_EINVAL, "get_friction_lag: not a friction block");
+    const BlockHost& b = s->blocks[energy_id];
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!b.n) return SX_OK;
+    double* tmp = nullptr;
+    CK(cudaMallocAsync((void**)&tmp, 13 * b.n * sizeof(double), st));
+    k_rows_to_records<<<(unsigned)((13 * b.n + 255) / 256), 256, 0, st>>>(b.flag, b.n, 13, tmp);
+    CK(cudaGetLastError());
+    std::vector<double> h(13 * (size_t)b.n);
+    CK(cudaMemcpyAsync(h.data(), tmp, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(tmp, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<double> ob(3 * (size_t)b.n), oT(6 * (size_t)b.n), of((size_t)b.n),
+        od(3 * (size_t)b.n);
+    for (int64_t e = 0; e < b.n; ++e) {
+        const double* r = h.data() + 13 * e;
+        for (int k = 0; k < 3; ++k) ob[3 * e + k] = r[k];
+        for (int k = 0; k < 6; ++k) oT[6 * e + k] = r[3 + k];
+        of[e] = r[9];
+        for (int k = 0; k < 3; ++k) od[3 * e + k] = r[10 + k];
+    }
+    if (beta) CK(cudaMemcpy(beta, ob.data(), ob.size() * sizeof(double), cudaMemcpyDefault));
+    if (T) CK(cudaMemcpy(T, oT.data(), oT.size() * sizeof(double), cudaMemcpyDefault));
+    if (fn) CK(cudaMemcpy(fn, of.data(), of.size() * sizeof(double), cudaMemcpyDefault));
+    if (dx_lag) CK(cudaMemcpy(dx_lag, od.data(), od.size() * sizeof(double), cudaMemcpyDefault));
     return SX_OK;
 }
 
@@ -1144,6 +1225,33 @@ int sx_add_pt_barrier(sx_scene* s, const int32_t* pairs, int64_t n, double dhat,
     b.dhat = dhat;
     b.kappa = kappa;
     if ((rc = copy_conn(ctx, s, pairs, n, &b.conn, st)) != SX_OK) return rc;
+    CK(cudaStreamSynchronize(st));
+    register_block(s, std::move(b), energy_id);
+    return SX_OK;
+}
+
+int sx_add_pt_friction(sx_scene* s, const int32_t* pairs, int64_t n, double mu, double yhat,
+                       double dhat, double kappa, void* stream, int* energy_id)
+{
+    int rc = add_block_common(s, "add_pt_friction");
+    if (rc != SX_OK) return rc;
+    sx_ctx* ctx = s->ctx;
+    if (n < 0 || (n > 0 && !pairs) || !(mu >= 0.0) || !(yhat > 0.0) || !(dhat > 0.0) ||
+        !(kappa >= 0.0))
+        return fail(ctx, SX_EINVAL, "add_pt_friction: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
+    BlockHost b;
+    b.kind = SX_KIND_PT_FRICTION;
+    b.n = n;
+    b.dhat = dhat;
+    b.kappa = kappa;
+    b.mu_f = mu;
+    b.yhat = yhat;
+    if ((rc = copy_conn(ctx, s, pairs, n, &b.conn, st)) != SX_OK) return rc;
+    if (dalloc(s, &b.flag, 13 * (size_t)std::max<int64_t>(n, 1)))
+        return fail(ctx, SX_ENOMEM, "add_pt_friction: allocation failed");
+    CK(cudaMemsetAsync(b.flag, 0, 13 * std::max<int64_t>(n, 1) * sizeof(double), st));
     CK(cudaStreamSynchronize(st));
     register_block(s, std::move(b), energy_id);
     return SX_OK;
@@ -1289,6 +1397,16 @@ void release_finalized(sx_scene* s)
 int replace_pairs(sx_scene* s, int b, int4* conn, int64_t n, cudaStream_t st)
 {
     BlockHost& blk = s->blocks[b];
+    if (blk.kind == SX_KIND_PT_FRICTION) {
+        // a new lag array, zero (no friction until the next lag)
+        double* nl = nullptr;
+        if (dalloc(s, &nl, 13 * (size_t)std::max<int64_t>(n, 1))) return SX_ENOMEM;
+        cudaError_t e = cudaMemsetAsync(nl, 0, 13 * std::max<int64_t>(n, 1) * sizeof(double), st);
+        if (e != cudaSuccess) return SX_ECUDA;
+        if (blk.flag)
+            free_scene_alloc(s, blk.flag, 13 * std::max<int64_t>(blk.n, 1) * (int64_t)sizeof(double));
+        blk.flag = nl;
+    }
     if (blk.conn) free_scene_alloc(s, blk.conn, std::max<int64_t>(blk.n, 1) * (int64_t)sizeof(int4));
     blk.conn = conn;
     blk.n = n;
@@ -1313,7 +1431,9 @@ int sx_set_pairs(sx_scene* s, int energy_id, const int32_t* pairs, int64_t n, vo
     if (!s) return SX_EINVAL;
     sx_ctx* ctx = s->ctx;
     if (energy_id < 0 || energy_id >= (int)s->blocks.size() ||
-        s->blocks[energy_id].kind != SX_KIND_PT_BARRIER || n < 0 || (n > 0 && !pairs))
+        (s->blocks[energy_id].kind != SX_KIND_PT_BARRIER &&
+         s->blocks[energy_id].kind != SX_KIND_PT_FRICTION) ||
+        n < 0 || (n > 0 && !pairs))
         return fail(ctx, SX_EINVAL, "set_pairs: needs a point-triangle block and n >= 0 pairs");
     cudaStream_t st = (cudaStream_t)stream;
     s->stream = st;
@@ -1736,6 +1856,9 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
         s->inertia_on = true;
         s->inertia_mode = 1;
         s->dt = dt;
+        // friction lag at the start-of-step state with this step's dt (before
+        // the batch's descriptors are prepared: dt is part of them)
+        CK(update_friction(s, dt, st));
     }
     Batch* B = get_batch(ctx, scenes, n);
     int rc = prepare_batch(ctx, B, st);

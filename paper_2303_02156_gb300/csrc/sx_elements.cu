@@ -76,6 +76,119 @@ cudaError_t launch_gather_pairs(const int4* conn, const int* keep, const int* of
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ friction lag
+// Lag of point-triangle pairs at the state x: the closest point of the
+// triangle (the barrier's classification: the plane projection when its
+// barycentrics are all >= 0, else the nearest clamped segment projection),
+// its weights beta, d = |p - c|, fn = -b'(d) = kappa (2 (d - dhat) ln(d/dhat)
+// + (d - dhat)^2 / d) for 0 < d < dhat (else 0), the unit normal (p - c)/d
+// and a tangent basis: the coordinate axis least aligned with the normal,
+// orthogonalized and normalized, then normal x that. Written as [13][n]:
+// beta, T (two rows), fn, dx_lag = p - c.
+__global__ void k_friction_lag(const double* __restrict__ x, const int4* __restrict__ conn,
+                               int64_t n, double dhat, double kappa, double* __restrict__ lag)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int4 q = conn[e];
+    const int nid[4] = {q.x, q.y, q.z, q.w};
+    double t[3][3];   // triangle vertices relative to p
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            t[a][i] = x[3 * (int64_t)nid[a + 1] + i] - x[3 * (int64_t)nid[0] + i];
+    double beta[3] = {0.0, 0.0, 0.0};
+    bool face = false;
+    {
+        double E1[3], E2[3], ev[3], N[3], c1[3], c2[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            E1[i] = t[1][i] - t[0][i];
+            E2[i] = t[2][i] - t[0][i];
+            ev[i] = -t[0][i];
+        }
+        cross3(E1, E2, N);
+        const double w = N[0] * N[0] + N[1] * N[1] + N[2] * N[2];
+        if (w > 0.0) {
+            cross3(ev, E2, c1);
+            cross3(E1, ev, c2);
+            const double b1 = (c1[0] * N[0] + c1[1] * N[1] + c1[2] * N[2]) / w;
+            const double b2 = (c2[0] * N[0] + c2[1] * N[1] + c2[2] * N[2]) / w;
+            const double b0 = 1.0 - b1 - b2;
+            if (b0 >= 0.0 && b1 >= 0.0 && b2 >= 0.0) {
+                face = true;
+                beta[0] = b0;
+                beta[1] = b1;
+                beta[2] = b2;
+            }
+        }
+    }
+    if (!face) {
+        double best = 0.0, bt = 0.0;
+        int bi = -1;
+        for (int sgm = 0; sgm < 3; ++sgm) {
+            const int iu = sgm, iw = (sgm + 1) % 3;
+            double ee[3], EE[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                ee[i] = -t[iu][i];
+                EE[i] = t[iw][i] - t[iu][i];
+            }
+            const double bb = EE[0] * EE[0] + EE[1] * EE[1] + EE[2] * EE[2];
+            double tt = bb > 0.0 ? (ee[0] * EE[0] + ee[1] * EE[1] + ee[2] * EE[2]) / bb : 0.0;
+            tt = tt < 0.0 ? 0.0 : (tt > 1.0 ? 1.0 : tt);
+            double dd = 0.0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double r = ee[i] - tt * EE[i];
+                dd += r * r;
+            }
+            if (bi < 0 || dd < best) {
+                best = dd;
+                bt = tt;
+                bi = sgm;
+            }
+        }
+        beta[bi] = 1.0 - bt;
+        beta[(bi + 1) % 3] = bt;
+    }
+    double r[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r[i] = -(beta[0] * t[0][i] + beta[1] * t[1][i] + beta[2] * t[2][i]);
+    const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double fn = 0.0;
+    if (d > 0.0 && d < dhat) {
+        const double dd = d - dhat;
+        fn = kappa * (2.0 * dd * log(d / dhat) + dd * dd / d);
+    }
+    double nv[3] = {0.0, 0.0, 1.0};
+    if (d > 0.0)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) nv[i] = r[i] / d;
+    const double a0 = fabs(nv[0]), a1 = fabs(nv[1]), a2 = fabs(nv[2]);
+    const int ax = (a0 <= a1 && a0 <= a2) ? 0 : (a1 <= a2 ? 1 : 2);
+    double t1[3], t2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t1[i] = (i == ax ? 1.0 : 0.0) - nv[ax] * nv[i];
+    const double l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t1[i] /= l1;
+    cross3(nv, t1, t2);
+    double out[13] = {beta[0], beta[1], beta[2], t1[0], t1[1], t1[2], t2[0], t2[1], t2[2],
+                      fn, r[0], r[1], r[2]};
+#pragma unroll
+    for (int k = 0; k < 13; ++k) lag[(int64_t)k * n + e] = out[k];
+}
+
+cudaError_t launch_friction_lag(const double* x, const int4* conn, int64_t n, double dhat,
+                                double kappa, double* lag, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_friction_lag<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(x, conn, n, dhat, kappa, lag);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ lagged rotations
 // R = U V^T of F = U diag(s) V^T (s descending) for every tet of a block:
 // V from Jacobi on F^T F (made a rotation: v2 = v0 x v1), u0 = F v0 / |F v0|,
@@ -177,16 +290,16 @@ const void* elements_kernel(int precision, int variant)
     case 2: return elements_kernel_fproj(15, f);
     case 3: return elements_kernel_fproj(9, f);
     case 4: return elements_kernel_models(25, f);
-    case 5: return elements_kernel_models(31, f);
+    case 5: return elements_kernel_models(63, f);
     default: return elements_kernel_snh(7, f);
     }
 }
 
 int elements_variant(int kinds, int project)
 {
-    // tets of the other densities: one instantiation with the material
-    // projection compiled in, with or without hinges and barriers
-    if (kinds & 16) return (kinds & 6) ? 5 : 4;
+    // tets of the other densities or friction: one instantiation with the
+    // material projection compiled in, for tets alone or every kind
+    if (kinds & (16 | 32)) return (kinds & (2 | 4 | 32)) ? 5 : 4;
     const bool snh_only = kinds == 1;
     return project == 2 ? (snh_only ? 3 : 2) : (snh_only ? 1 : 0);
 }
@@ -208,7 +321,7 @@ cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s)
     case 2: return launch_elements_fproj(15, f, L, grid, s);
     case 3: return launch_elements_fproj(9, f, L, grid, s);
     case 4: return launch_elements_models(25, f, L, grid, s);
-    case 5: return launch_elements_models(31, f, L, grid, s);
+    case 5: return launch_elements_models(63, f, L, grid, s);
     default: return launch_elements_snh(7, f, L, grid, s);
     }
 }

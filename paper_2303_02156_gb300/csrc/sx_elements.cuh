@@ -33,7 +33,7 @@
 //
 // The element kernel k_elements<R, HT, KINDS> is instantiated in three
 // translation units (sx_elements.cu: KINDS 1, 7; sx_elements_fproj.cu: 9,
-// 15; sx_elements_models.cu: 25, 31) so that they compile in parallel.
+// 15; sx_elements_models.cu: 25, 63) so that they compile in parallel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -899,6 +899,97 @@ __device__ __noinline__ void eval_model(const ElemLaunch& L, int scene, int blk,
     }
 }
 
+// ------------------------------------------------------------------ friction
+// Lagged IPC friction (§6.4 friction potential). The lag of a pair holds
+// beta (closest-point weights), T (tangent basis, 2 rows), fn and dx_lag.
+// With w = dx - dx_lag (dx = p - sum beta_i t_i, formed relative to p),
+// u = T w, s = |u|, y = s / dt and k = mu fn:
+//   E = k f0(s), f0(s) = dt f(y);  g_u = k (f0'/s) u;
+//   H_u = k [ (f0'/s) I2 + ((f0'' - f0'/s) / s^2) u u^T ] with
+//   stick (y <= yh): f0'/s = (2/yh - y/yh^2)/dt, (f0'' - f0'/s)/s^2 = -1/(s yh^2 dt^2)
+//                    (a term that vanishes with s: 0 at s = 0)
+//   slide:           f0'/s = 1/s,               (f0'' - f0'/s)/s^2 = -1/s^3.
+// With c = (1, -beta0, -beta1, -beta2): g_a = c_a T^T g_u and
+// H_ab = c_a c_b T^T H_u T. H_u is PSD in both regimes: never projected.
+template <typename R, typename HT>
+__device__ __noinline__ void eval_friction(const ElemLaunch& L, const SceneDev& S,
+                                           const ElemBlock& B, int64_t e, ThreadOut& o)
+{
+    const int4 t = B.conn[e];
+    const int nid[4] = {t.x, t.y, t.z, t.w};
+    const int64_t n = B.n;
+    double lag[13];
+#pragma unroll
+    for (int k = 0; k < 13; ++k) lag[k] = B.flag[(int64_t)k * n + e];
+    const double kf = B.mu_f * lag[9];
+    double p0[3], w[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p0[i] = S.x[3 * (int64_t)nid[0] + i];
+        w[i] = -lag[10 + i];
+    }
+#pragma unroll
+    for (int a = 1; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w[i] -= lag[a - 1] * (S.x[3 * (int64_t)nid[a] + i] - p0[i]);
+    const double u0 = lag[3] * w[0] + lag[4] * w[1] + lag[5] * w[2];
+    const double u1 = lag[6] * w[0] + lag[7] * w[1] + lag[8] * w[2];
+    const double s = sqrt(u0 * u0 + u1 * u1);
+    const double dt = B.dt_f, yh = B.yhat, y = s / dt;
+    double f0, a1, a2;
+    if (y <= yh) {
+        f0 = dt * (y * y * (1.0 / yh - y / (3.0 * yh * yh)) + yh / 3.0);
+        a1 = (2.0 / yh - y / (yh * yh)) / dt;
+        a2 = s > 0.0 ? -1.0 / (s * yh * yh * dt * dt) : 0.0;
+    } else {
+        f0 = s;
+        a1 = 1.0 / s;
+        a2 = -1.0 / (s * s * s);
+    }
+    o.E = kf * f0;
+    if (!isfinite(o.E)) o.nonfinite = 1;
+    const int64_t gid = B.base + e;
+    const R c[4] = {R(1), (R)(-lag[0]), (R)(-lag[1]), (R)(-lag[2])};
+    R T[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) T[r][i] = (R)lag[3 + 3 * r + i];
+    if (L.level >= 1) {
+        const R gu0 = (R)(kf * a1 * u0), gu1 = (R)(kf * a1 * u1);
+        R G3[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) G3[i] = T[0][i] * gu0 + T[1][i] * gu1;
+        double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                gout[3 * a + i] = (double)(c[a] * G3[i]);
+                if (!isfinite(gout[3 * a + i])) o.nonfinite = 1;
+            }
+    }
+    if (L.level >= 2) {
+        const R h00 = (R)(kf * (a1 + a2 * u0 * u0)), h11 = (R)(kf * (a1 + a2 * u1 * u1));
+        const R h01 = (R)(kf * a2 * u0 * u1);
+        R M3[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                M3[i * 3 + j] = T[0][i] * (h00 * T[0][j] + h01 * T[1][j]) +
+                                T[1][i] * (h01 * T[0][j] + h11 * T[1][j]);
+        auto blockfn = [&](int a, int b, R* out) {
+            const R cc = c[a] * c[b];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) out[k] = cc * M3[k];
+        };
+        HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
+        double* full = L.out_H ? L.out_H + 144 * e : nullptr;
+        write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
+    }
+}
+
 template <typename R, typename HT>
 __device__ void eval_hinge(const ElemLaunch& L, const SceneDev& S, const ElemBlock& B,
                            int64_t e, ThreadOut& o)
@@ -1027,7 +1118,7 @@ __device__ void eval_barrier(const ElemLaunch& L, int scene, int blk, const Scen
 
 // KINDS: bit mask of the stencil kinds compiled in (1 SNH, 2 hinge, 4
 // barrier), 8 for the F-space projection of the SNH tets (project mode
-// 2) and 16 for tets of the other densities. A batch with SNH tets only
+// 2), 16 for tets of the other densities and 32 for friction. A batch with SNH tets only
 // runs an SNH-only instantiation, which needs fewer registers than the one
 // that can take every kind.
 template <typename R, typename HT, int KINDS>
@@ -1056,6 +1147,8 @@ k_elements(ElemLaunch L)
                     eval_snh<R, HT, (KINDS & 8) != 0>(L, T.scene, T.blk, S, B, e, o);
                 else if ((KINDS & 2) && B.kind == SX_KIND_HINGE4)
                     eval_hinge<R, HT>(L, S, B, e, o);
+                else if ((KINDS & 32) && B.kind == SX_KIND_PT_FRICTION)
+                    eval_friction<R, HT>(L, S, B, e, o);
                 else if ((KINDS & 4) && B.kind == SX_KIND_PT_BARRIER)
                     eval_barrier<R, HT>(L, T.scene, T.blk, S, B, e, o);
                 if (L.out_E) L.out_E[e] = o.E;

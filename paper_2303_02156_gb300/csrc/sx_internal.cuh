@@ -55,8 +55,11 @@ struct ElemBlock {
     const double* q;      // [4][n]
     const double* c;
     double kb;
-    // barrier
+    // barrier, friction (the friction's fn comes from this barrier)
     double dhat, kappa;
+    // friction: lag [13][n] = beta (3), T (6), fn, dx_lag (3); mu, yhat, dt
+    const double* flag;
+    double mu_f, yhat, dt_f;
 };
 
 // per-scene scalars the device loops read and write
@@ -196,13 +199,15 @@ constexpr int kElemVariants = 6;
 // the element-kernel instantiations of each translation unit (KINDS values)
 const void* elements_kernel_snh(int kinds, bool f32);      // 1, 7
 const void* elements_kernel_fproj(int kinds, bool f32);    // 9, 15
-const void* elements_kernel_models(int kinds, bool f32);   // 25, 31
+const void* elements_kernel_models(int kinds, bool f32);   // 25, 63
 cudaError_t launch_elements_snh(int kinds, bool f32, const ElemLaunch& L, int grid,
                                 cudaStream_t s);
 cudaError_t launch_elements_fproj(int kinds, bool f32, const ElemLaunch& L, int grid,
                                   cudaStream_t s);
 cudaError_t launch_elements_models(int kinds, bool f32, const ElemLaunch& L, int grid,
                                    cudaStream_t s);
+cudaError_t launch_friction_lag(const double* x, const int4* conn, int64_t n, double dhat,
+                                double kappa, double* lag, cudaStream_t s);
 cudaError_t launch_tet_rotations(const int4* conn, const double* x, const double* Dminv,
                                  int64_t n, double* R, cudaStream_t s);
 int elements_variant(int kinds, int project);

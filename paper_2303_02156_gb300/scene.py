@@ -113,6 +113,28 @@ class Scene:
                             nu.ctypes.data, float(density), self.stream, C.byref(eid))
         return self._id(rc, eid, sx.SX_KIND_TET4, n)
 
+    def add_friction(self, pairs, mu, yhat, dhat, kappa):
+        """Lagged IPC friction on point-triangle pairs (no friction until
+        the first lag: update_friction or a Newton step)."""
+        pr = _i32(pairs); n = pr.shape[0]
+        eid = C.c_int()
+        rc = sx.sx_add_pt_friction(self.h, pr.ctypes.data if n else None, n, float(mu),
+                                   float(yhat), float(dhat), float(kappa), self.stream,
+                                   C.byref(eid))
+        return self._id(rc, eid, sx.SX_KIND_PT_FRICTION, n)
+
+    def update_friction(self, dt):
+        """Lag the friction blocks at the current state with step dt."""
+        self.ctx.check(sx.sx_update_friction(self.h, float(dt), self.stream))
+
+    def friction_lag(self, energy_id):
+        n = self.blocks[energy_id][1]
+        beta = np.empty((n, 3)); T = np.empty((n, 6)); fn = np.empty(n); dxl = np.empty((n, 3))
+        self.ctx.check(sx.sx_get_friction_lag(self.h, energy_id, beta.ctypes.data,
+                                              T.ctypes.data, fn.ctypes.data, dxl.ctypes.data,
+                                              self.stream))
+        return {"beta": beta, "T": T.reshape(n, 2, 3), "fn": fn, "dxt": dxl}
+
     def update_rotations(self):
         """Lagged rotations of the COROT / ARAP blocks := polar rotations of
         F at the current state."""
