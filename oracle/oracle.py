@@ -68,6 +68,13 @@ def lib():
     L.orc_tet_batch.argtypes = [C.c_int, C.c_int, _dp, _ip, _dp, _dp, _dp, _dp, C.c_void_p,
                                 C.c_int, C.c_int, _dp, C.c_void_p, C.c_void_p]
     L.orc_tet_batch.restype = C.c_int
+    L.orc_tetho_shape.argtypes = [C.c_int, _dp, _dp, _dp]
+    L.orc_tetho_element.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, C.c_double, C.c_double,
+                                    C.c_int, _dp, _dp, _dp]
+    L.orc_tetho_element.restype = C.c_int
+    L.orc_tetho_batch.argtypes = [C.c_int, C.c_int, _dp, _dp, _ip, C.c_int, _dp, _dp, _dp,
+                                  C.c_int, C.c_int, _dp, C.c_void_p, C.c_void_p]
+    L.orc_tetho_batch.restype = C.c_int
     L.orc_friction_lag_batch.argtypes = [C.c_int, _dp, _ip, C.c_double, C.c_double, _dp, _dp,
                                          _dp, _dp]
     L.orc_friction_element.argtypes = [_dp, _dp, _dp, C.c_double, _dp, C.c_double, C.c_double,
@@ -236,6 +243,49 @@ def lagged_rotations(x, tets, Dminv):
     neg = np.linalg.det(U @ Vt) < 0
     U[neg, :, 2] *= -1
     return (U @ Vt).reshape(-1, 9)
+
+
+# ---------------------------------------------------------------- high-order tets
+def tetho_shape(K, xi):
+    N = np.zeros(K); dN = np.zeros(3 * K)
+    lib().orc_tetho_shape(int(K), _f64(xi), N, dN)
+    return N, dN.reshape(K, 3)
+
+
+def tetho_element(K, rule, Xe, xe, mu, lam, project=False):
+    rule = _f64(rule).reshape(-1, 4)
+    n3 = 3 * K
+    E = np.zeros(1); g = np.zeros(n3); H = np.zeros(n3 * n3)
+    bad = lib().orc_tetho_element(int(K), rule.shape[0], rule, _f64(Xe).ravel(),
+                                  _f64(xe).ravel(), float(mu), float(lam), int(project), E, g, H)
+    return bad, E[0], g, H.reshape(n3, n3)
+
+
+def tetho_batch(K, X, x, tets, rule, mu, lam, level=LEVEL_EGH, project=False):
+    tets = _i32(tets).reshape(-1, K); T = tets.shape[0]
+    rule = _f64(rule).reshape(-1, 4)
+    n3 = 3 * K
+    E = np.empty(T)
+    g = np.empty((T, n3)) if level >= 1 else None
+    H = np.empty((T, n3, n3)) if level >= 2 else None
+    bad = lib().orc_tetho_batch(int(K), T, _f64(X), _f64(x), tets, rule.shape[0], rule,
+                                _f64(mu), _f64(lam), level, int(project), E, _ptr(g), _ptr(H))
+    return E, g, H, bad
+
+
+def tetho_assemble(N, tets, g_e, H_e):
+    """Dense assembly (small scenes): sum over elements of their K-node
+    gradients and Hessians into the 3N vector and the 3N x 3N matrix."""
+    tets = np.asarray(tets)
+    K = tets.shape[1]
+    g = np.zeros(3 * N)
+    H = np.zeros((3 * N, 3 * N)) if H_e is not None else None
+    for e in range(tets.shape[0]):
+        idx = (3 * tets[e][:, None] + np.arange(3)[None, :]).ravel()
+        g[idx] += g_e[e]
+        if H is not None:
+            H[np.ix_(idx, idx)] += H_e[e]
+    return g, H
 
 
 # ---------------------------------------------------------------- friction

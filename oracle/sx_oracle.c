@@ -22,6 +22,8 @@
  *   - IPC log barrier E = -k (d - dhat)^2 ln(d/dhat) on the unsigned
  *     point-triangle distance [§6.4, Eq. 15], active only for d < dhat
  *     [§5.2 "Conditional evaluations", Eq. 9].
+ *   - High-order (10- and 20-node) Lagrange tets with a quadrature sum
+ *     [§7.2 Eq. fem_final, App. A shape functions].
  *   - Lagged IPC friction on point-triangle pairs [§6.4, friction
  *     potential] with its lag data (closest point, tangent basis, contact
  *     force) taken at the start of a step.
@@ -1157,6 +1159,166 @@ void orc_friction_batch(int P, const double* x, const int* pairs, const double* 
                              level >= 1 ? g_e + 12 * (size_t)e : NULL,
                              level >= 2 ? H_e + 144 * (size_t)e : NULL);
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* High-order Lagrange tets with a quadrature sum (§7.2 "High-order      */
+/* Lagrangian finite elements", Eq. fem_final; App. A shape functions;   */
+/* §5 fixed-value summation)                                            */
+/* ------------------------------------------------------------------ */
+
+/* Local node order. Barycentric L = (1 - xi0 - xi1 - xi2, xi0, xi1, xi2).
+ * tet4: the vertices. tet10 (App. A): the vertices, then one node per edge
+ * in the order 01, 12, 20, 03, 13, 23. tet20 (READING: the paper shows no
+ * cubic listing; the standard cubic Lagrange tet): the vertices; two nodes
+ * per edge in the same edge order, first the one nearer the edge's first
+ * vertex; one node per face in the order 012, 013, 123, 023. */
+static const int ORC_EDGES[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+static const int ORC_FACES[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+
+/* Shape functions N (K) and their reference gradients dN (K x 3) at xi. */
+void orc_tetho_shape(int K, const double* xi, double* N, double* dN)
+{
+    double L[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
+    static const double dL[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    /* each N as a function of L with its partials dN/dL, then the chain rule */
+    double dNL[20][4];
+    memset(dNL, 0, sizeof(dNL));
+    int a = 0;
+    if (K == 4) {
+        for (int v = 0; v < 4; ++v, ++a) { N[a] = L[v]; dNL[a][v] = 1.0; }
+    } else if (K == 10) {
+        for (int v = 0; v < 4; ++v, ++a) {
+            N[a] = L[v] * (2.0 * L[v] - 1.0);
+            dNL[a][v] = 4.0 * L[v] - 1.0;
+        }
+        for (int e = 0; e < 6; ++e, ++a) {
+            int i = ORC_EDGES[e][0], j = ORC_EDGES[e][1];
+            N[a] = 4.0 * L[i] * L[j];
+            dNL[a][i] = 4.0 * L[j];
+            dNL[a][j] = 4.0 * L[i];
+        }
+    } else {
+        for (int v = 0; v < 4; ++v, ++a) {
+            double l = L[v];
+            N[a] = 0.5 * l * (3.0 * l - 1.0) * (3.0 * l - 2.0);
+            dNL[a][v] = 0.5 * (27.0 * l * l - 18.0 * l + 2.0);
+        }
+        for (int e = 0; e < 6; ++e)
+            for (int side = 0; side < 2; ++side, ++a) {
+                int i = ORC_EDGES[e][side], j = ORC_EDGES[e][1 - side];
+                /* node nearer i: 9/2 L_i L_j (3 L_i - 1) */
+                N[a] = 4.5 * L[i] * L[j] * (3.0 * L[i] - 1.0);
+                dNL[a][i] = 4.5 * L[j] * (6.0 * L[i] - 1.0);
+                dNL[a][j] = 4.5 * L[i] * (3.0 * L[i] - 1.0);
+            }
+        for (int f = 0; f < 4; ++f, ++a) {
+            int i = ORC_FACES[f][0], j = ORC_FACES[f][1], k = ORC_FACES[f][2];
+            N[a] = 27.0 * L[i] * L[j] * L[k];
+            dNL[a][i] = 27.0 * L[j] * L[k];
+            dNL[a][j] = 27.0 * L[i] * L[k];
+            dNL[a][k] = 27.0 * L[i] * L[j];
+        }
+    }
+    for (int b = 0; b < K; ++b)
+        for (int m = 0; m < 3; ++m) {
+            double sdn = 0.0;
+            for (int v = 0; v < 4; ++v) sdn += dNL[b][v] * dL[v][m];
+            dN[3 * b + m] = sdn;
+        }
+}
+
+/* One SNH element of K nodes: E = sum_q w_q det(J0_q) psi(F_q) with
+ * J0 = sum_a X_a dN_a^T, F = (sum_a x_a dN_a^T) J0^-1 at the quadrature
+ * point xi_q (Eq. fem_final); g and H by the chain rule through the 9 x 3K
+ * map of each point. rule: nq x (w, xi0, xi1, xi2). project != 0 clamps
+ * d2psi/dF2 at every point (READING: the PSD projection of high-order
+ * elements is taken per quadrature point in F-space; the sum of PSD terms
+ * is PSD). Returns 1 if some det(J0_q) <= 0. */
+int orc_tetho_element(int K, int nq, const double* rule, const double* Xe, const double* xe,
+                      double mu, double lam, int project, double* E, double* g, double* H)
+{
+    int n3 = 3 * K, bad = 0;
+    double N[20], dN[60], B[9 * 60];
+    *E = 0.0;
+    if (g) memset(g, 0, n3 * sizeof(double));
+    if (H) memset(H, 0, (size_t)n3 * n3 * sizeof(double));
+    for (int q = 0; q < nq; ++q) {
+        const double w = rule[4 * q];
+        orc_tetho_shape(K, rule + 4 * q + 1, N, dN);
+        double J0[9] = {0}, Ds[9] = {0}, J0i[9], det;
+        for (int a = 0; a < K; ++a)
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    J0[3 * i + j] += Xe[3 * a + i] * dN[3 * a + j];
+                    Ds[3 * i + j] += xe[3 * a + i] * dN[3 * a + j];
+                }
+        inv3(J0, J0i, &det);
+        if (!(det > 0.0)) bad = 1;
+        double F[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double sf = 0.0;
+                for (int m = 0; m < 3; ++m) sf += Ds[3 * i + m] * J0i[3 * m + j];
+                F[3 * i + j] = sf;
+            }
+        /* B[(3i+j), (3a+k)] = delta_ik G_aj, G_a = J0^-T dN_a */
+        memset(B, 0, sizeof(double) * 9 * n3);
+        for (int a = 0; a < K; ++a)
+            for (int j = 0; j < 3; ++j) {
+                double G = 0.0;
+                for (int m = 0; m < 3; ++m) G += dN[3 * a + m] * J0i[3 * m + j];
+                for (int i = 0; i < 3; ++i) B[(3 * i + j) * n3 + 3 * a + i] = G;
+            }
+        double psi, P[9], A[81];
+        snh_density(F, mu, lam, &psi, P, A);
+        const double wd = w * det;
+        *E += wd * psi;
+        if (g)
+            for (int c = 0; c < n3; ++c) {
+                double sg = 0.0;
+                for (int r = 0; r < 9; ++r) sg += B[r * n3 + c] * P[r];
+                g[c] += wd * sg;
+            }
+        if (H) {
+            if (project) orc_clamp_psd(9, A);
+            for (int r = 0; r < n3; ++r)
+                for (int c = 0; c < n3; ++c) {
+                    double sh = 0.0;
+                    for (int k = 0; k < 9; ++k) {
+                        if (B[k * n3 + r] == 0.0) continue;
+                        double ab = 0.0;
+                        for (int l = 0; l < 9; ++l) ab += A[k * 9 + l] * B[l * n3 + c];
+                        sh += B[k * n3 + r] * ab;
+                    }
+                    H[(size_t)r * n3 + c] += wd * sh;
+                }
+        }
+    }
+    return bad;
+}
+
+/* A batch of T elements (tets: T x K node ids; X rest, x current: node
+ * arrays). E_e (T), g_e (T x 3K), H_e (T x 3K x 3K). Returns the number of
+ * elements with a non-positive det(J0) at some point. */
+int orc_tetho_batch(int K, int T, const double* X, const double* x, const int* tets, int nq,
+                    const double* rule, const double* mu, const double* lam, int level,
+                    int project, double* E_e, double* g_e, double* H_e)
+{
+    int bad = 0, n3 = 3 * K;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : bad)
+    for (int e = 0; e < T; ++e) {
+        double Xe[60], xe[60];
+        for (int a = 0; a < K; ++a)
+            for (int i = 0; i < 3; ++i) {
+                Xe[3 * a + i] = X[3 * (size_t)tets[K * (size_t)e + a] + i];
+                xe[3 * a + i] = x[3 * (size_t)tets[K * (size_t)e + a] + i];
+            }
+        bad += orc_tetho_element(K, nq, rule, Xe, xe, mu[e], lam[e], project, E_e + e,
+                                 level >= 1 ? g_e + (size_t)n3 * e : NULL,
+                                 level >= 2 ? H_e + (size_t)n3 * n3 * e : NULL);
+    }
+    return bad;
 }
 
 /* ------------------------------------------------------------------ */

@@ -316,3 +316,108 @@ def batch_boxes(n_scenes: int = 512, t_min: float = 1e3, t_max: float = 2e5, see
         m["nu"] = float(rng.uniform(0.2, 0.45))
         out.append(m)
     return out
+
+
+# ------------------------------------------------------------------ high-order tets
+_HO_EDGES = ((0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3))
+_HO_FACES = ((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3))
+
+
+def kuhn_box_ho(nx: int, ny: int, nz: int, order: int, h=1.0, jitter: float = 0.1,
+                seed: int = 1):
+    """The Kuhn box of ``kuhn_box`` with quadratic (order 2: 10 nodes) or
+    cubic (order 3: 20 nodes) tets: straight-sided elements whose extra
+    nodes are shared between neighbours (edge nodes by edge, face nodes by
+    face) and placed at the Lagrange positions between the vertices.
+
+    Local node order: the four vertices; order 2: one node per edge in the
+    order 01, 12, 20, 03, 13, 23; order 3: two per edge in that order (first
+    the one nearer the edge's first vertex), then one per face in the order
+    012, 013, 123, 023. Returns dict with ``X`` (N,3), ``tets`` (T,K),
+    ``pinned`` (nodes on the k = 0 layer) and ``n_vertices``.
+    """
+    m = kuhn_box(nx, ny, nz, h=h, jitter=jitter, seed=seed)
+    X0, t4 = m["X"], m["tets"].astype(np.int64)
+    nv = X0.shape[0]
+    pts = [X0]
+    count = nv
+    K = 10 if order == 2 else 20
+    tets = np.empty((t4.shape[0], K), dtype=np.int64)
+    tets[:, :4] = t4
+    # edges: a sorted vertex pair -> its node id(s) along (lo -> hi)
+    keys = np.sort(np.stack([t4[:, list(e)] for e in _HO_EDGES], axis=1), axis=2)   # T x 6 x 2
+    flat = keys.reshape(-1, 2)
+    uniq, inv = np.unique(flat, axis=0, return_inverse=True)
+    inv = inv.reshape(t4.shape[0], 6)
+    A, B = X0[uniq[:, 0]], X0[uniq[:, 1]]
+    if order == 2:
+        pts.append(0.5 * (A + B))
+        tets[:, 4:10] = count + inv
+        count += uniq.shape[0]
+    else:
+        pts.append((2.0 * A + B) / 3.0)        # node nearer lo
+        pts.append((A + 2.0 * B) / 3.0)        # node nearer hi
+        near_lo = count + inv
+        near_hi = count + uniq.shape[0] + inv
+        count += 2 * uniq.shape[0]
+        for e, (i, j) in enumerate(_HO_EDGES):
+            first_is_lo = t4[:, i] < t4[:, j]
+            tets[:, 4 + 2 * e] = np.where(first_is_lo, near_lo[:, e], near_hi[:, e])
+            tets[:, 5 + 2 * e] = np.where(first_is_lo, near_hi[:, e], near_lo[:, e])
+        fkeys = np.sort(np.stack([t4[:, list(f)] for f in _HO_FACES], axis=1), axis=2)
+        funiq, finv = np.unique(fkeys.reshape(-1, 3), axis=0, return_inverse=True)
+        pts.append(X0[funiq].mean(axis=1))
+        tets[:, 16:20] = count + finv.reshape(t4.shape[0], 4)
+        count += funiq.shape[0]
+    X = np.vstack(pts)
+    z0 = X0[m["pinned"], 2].max()
+    pinned = np.flatnonzero(X[:, 2] <= z0 + 1e-12 * max(abs(z0), 1.0)).astype(np.int32)
+    if jitter > 0.0:
+        pinned = np.unique(np.concatenate([m["pinned"], pinned[pinned >= nv]]))
+        # extra nodes of bottom-face elements: those whose defining vertices are all pinned
+        bot = np.zeros(count, dtype=bool)
+        bot[m["pinned"]] = True
+        for e in range(6):
+            i, j = _HO_EDGES[e]
+            both = bot[t4[:, i]] & bot[t4[:, j]]
+            cols = [4 + e] if order == 2 else [4 + 2 * e, 5 + 2 * e]
+            for c in cols:
+                bot[tets[both, c]] = True
+        if order == 3:
+            for f, (i, j, k) in enumerate(_HO_FACES):
+                allp = bot[t4[:, i]] & bot[t4[:, j]] & bot[t4[:, k]]
+                bot[tets[allp, 16 + f]] = True
+        pinned = np.flatnonzero(bot).astype(np.int32)
+    return {"X": X, "tets": tets.astype(np.int32), "pinned": pinned, "n_vertices": nv}
+
+
+def tet_rule_4point():
+    """The symmetric 4-point tet rule of degree 2 (reference tet volume 1/6):
+    the points are the permutations of the barycentric (a, b, b, b) with
+    a = (5 + 3 sqrt 5)/20, b = (5 - sqrt 5)/20, weights 1/24. Rows (w, xi)."""
+    a = (5.0 + 3.0 * math.sqrt(5.0)) / 20.0
+    b = (5.0 - math.sqrt(5.0)) / 20.0
+    rows = []
+    for k in range(4):
+        L = [b, b, b, b]
+        L[k] = a
+        rows.append([1.0 / 24.0, L[1], L[2], L[3]])
+    return np.array(rows)
+
+
+def tet_rule_conical(n: int):
+    """Conical-product (Duffy) rule with n^3 points on the reference tet:
+    Gauss-Legendre points on [0, 1] per direction (numpy's leggauss), the
+    map xi0 = u, xi1 = v (1 - u), xi2 = w (1 - u)(1 - v) and its Jacobian
+    (1 - u)^2 (1 - v) in the weights. Exact for polynomials of degree
+    <= 2n - 3 on the tet. Rows (w, xi)."""
+    t, wt = np.polynomial.legendre.leggauss(n)
+    t = 0.5 * (t + 1.0); wt = 0.5 * wt
+    rows = []
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                u, v, w = t[i], t[j], t[k]
+                rows.append([wt[i] * wt[j] * wt[k] * (1 - u) ** 2 * (1 - v),
+                             u, v * (1 - u), w * (1 - u) * (1 - v)])
+    return np.array(rows)
