@@ -114,7 +114,9 @@ def test_model_elements_parity(ctx, model, precision, project):
 @pytest.mark.parametrize("model", MODELS)
 def test_model_strong_deformation_projection(ctx, model):
     """Large jitter (many indefinite element Hessians) with projection."""
-    m, E, nu, inp, mass, x, xt = _case(model, dims=(5, 4, 4), seed=5, jitter=0.3)
+    # NH is undefined at J <= 0: its case stays uninverted (min J ~ 0.06)
+    jitter = 0.25 if model == sx.SX_MODEL_NH else 0.3
+    m, E, nu, inp, mass, x, xt = _case(model, dims=(5, 4, 4), seed=5, jitter=jitter)
     F = orc.deformation_gradients(x, m["tets"], inp["Dminv"])
     if model == sx.SX_MODEL_NH:
         assert (np.linalg.det(F) > 0).all()
