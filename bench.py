@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batch-scenes", type=int, default=512)
     p.add_argument("--no-models", action="store_true")
+    p.add_argument("--no-high-order", action="store_true")
     return p.parse_args()
 
 
@@ -463,6 +464,68 @@ def run_models(ctx, stream, flush, m, E, nu, x, reps=5):
     return out
 
 
+# ------------------------------------------------------------------ high-order tets
+def run_high_order(ctx, stream, flush, reps=5):
+    """Linear, quadratic and cubic SNH tets on Kuhn cubes of about the same
+    DoF count as the paper's simulation benchmark (137K DoF): one E + g + H
+    + assembly evaluation without projection (the paper's timed quantity,
+    per Newton iteration), the same with the per-point projection, FP64 and
+    FP32, and one backward-Euler step (FP64, dt = 0.005, gravity)."""
+    import numpy as np
+    import torch
+    from paper_2303_02156_gb300 import scenes, sx
+    from paper_2303_02156_gb300.scene import Scene
+    sh = stream.cuda_stream
+    out = {}
+    for order, n in ((1, 35), (2, 17), (3, 12)):
+        if order == 1:
+            m = scenes.kuhn_box(n, n, n, h=1.0 / n, seed=2)
+        else:
+            m = scenes.kuhn_box_ho(n, n, n, order, h=1.0 / n, seed=2)
+        T = m["tets"].shape[0]
+        E, nu = scenes.material_random(T, seed=2)
+        s = Scene(ctx, m["X"], stream=sh)
+        if order == 1:
+            s.add_snh(m["tets"], E, nu, 1000.0)
+        else:
+            rule = scenes.tet_rule_4point() if order == 2 else scenes.tet_rule_conical(3)
+            s.add_tet_ho(order, m["tets"], E, nu, 1000.0, rule)
+        s.set_pinned(m["pinned"])
+        s.set_gravity((0.0, 0.0, -9.81))
+        s.finalize()
+        s.set_state(x=scenes.jitter_state(m["X"], 0.02 / n / order, seed=5))
+        r = {"elements": int(T), "dof": int(3 * m["X"].shape[0]),
+             "nodes_per_element": int(m["tets"].shape[1]),
+             "quadrature_points": 1 if order == 1 else (4 if order == 2 else 27),
+             "nnzb": int(s.info()["nnzb"])}
+        for pname, prec, proj in (("fp64", sx.SX_FP64, 0), ("fp32", sx.SX_FP32, 0),
+                                  ("fp64_projected", sx.SX_FP64, 1)):
+            for _ in range(2):
+                ctx.check(sx.sx_eval(s.h, sx.SX_EGH, proj, prec, None, sh))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                e0.record(stream)
+                ctx.check(sx.sx_eval(s.h, sx.SX_EGH, proj, prec, None, sh))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            med = statistics.median(ms)
+            r[pname] = {"ms_per_eval": med, "elements_per_s": T / (med / 1e3)}
+        s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+        rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-8, pcg_tol=1e-10)
+        r["newton_step"] = {"status": sx.STATUS_NAMES.get(rc, rc), "ms": rep["ms"],
+                            "newton_iters": rep["newton_iters"], "pcg_iters": rep["pcg_iters"]}
+        out[{1: "linear", 2: "quadratic", 3: "cubic"}[order]] = r
+        s.close()
+    out["paper_cpu_ms_per_iteration"] = {"linear": 14.8, "quadratic": 24.3, "cubic": 52.9,
+                                         "note": "E+g+H+assembly per Newton iteration at 137K "
+                                                 "DoF, no projection, the paper's CPU system"}
+    return out
+
+
 # ------------------------------------------------------------------ batched scenes
 def run_batched(ctx, stream, n_scenes, dt=0.01):
     """``n_scenes`` independent Kuhn boxes (tet counts log-uniform in
@@ -801,6 +864,7 @@ def main():
 
     # ---- the other tet4 densities on the same cube
     models = None if args.no_models else run_models(ctx, stream, flush, m, E, nu, x)
+    high_order = None if args.no_high_order else run_high_order(ctx, stream, flush)
 
     # ---- serving: Poisson stream of scene requests (bounded sample)
     serving = None
@@ -834,7 +898,7 @@ def main():
             "phase_ms_per_step": {k: round(v, 4) for k, v in phases.items()},
             "projected_fraction": clamped / T, "fp32": fp32, "newton_step": newton,
             "serving": serving, "mixed": mixed, "batched": batched, "autotune": tune,
-            "material_projection": matproj, "models": models,
+            "material_projection": matproj, "models": models, "high_order": high_order,
             "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
                         "max": max(step_ms)},
         }

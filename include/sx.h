@@ -79,6 +79,8 @@ extern "C" {
 #define SX_KIND_HINGE4 1
 #define SX_KIND_PT_BARRIER 2
 #define SX_KIND_PT_FRICTION 3
+#define SX_KIND_TET_HO 4       /* 10- or 20-node tets (sx_add_tet_ho) */
+#define SX_HO_MAX_QP 64        /* quadrature points per high-order rule */
 
 /* ---- tet4 densities (§7.1 "Non-linear material models", App. B) -------
  * SNH    Stable Neo-Hookean (§3.1 Eq. 7), parameters mu', lambda' as in
@@ -153,6 +155,29 @@ int sx_add_snh_tet4(sx_scene* scene, const int32_t* tets, int64_t n,
 int sx_add_tet4(sx_scene* scene, int model, const int32_t* tets, int64_t n,
                 const double* young, const double* poisson, double density, void* stream,
                 int* energy_id);
+
+/* High-order Lagrange tets (§7.2 Eq. fem_final; App. A shape functions)
+ * with the Stable Neo-Hookean density (mu', lambda' as in sx_add_snh_tet4):
+ * E_e = sum_q w_q det J0(xi_q) psi(F(xi_q)) over a quadrature rule given by
+ * the caller (the fixed-value summation of §5), J0 = sum_a X_a dN_a^T,
+ * F = (sum_a x_a dN_a^T) J0^-1. order 2: 10 nodes per tet (the vertices,
+ * then one node per edge in the order 01, 12, 20, 03, 13, 23: App. A);
+ * order 3: 20 nodes (the vertices; two per edge in that order, first the
+ * one nearer the edge's first vertex; one per face in the order 012, 013,
+ * 123, 023). tets: n x K node ids; rule: nq x 4 doubles (w, xi0, xi1, xi2)
+ * on the reference tet of volume 1/6, 1 <= nq <= SX_HO_MAX_QP; host
+ * arrays. Lumped mass rho V_e / K per node (V_e = sum_q w_q det J0);
+ * det J0 <= 0 at a point: SX_EDEGENERATE. With projection (sx_eval
+ * project != 0) the material Hessian is clamped at every point in closed
+ * form (as SX_PROJECT_MATERIAL does for linear SNH tets), so the element
+ * Hessian is PSD. For the fixed pattern an element is S four-node
+ * sub-stencils that together cover its node pairs (S = 10 for order 2, 38
+ * for order 3): sx_block_info and sx_eval_elements count n S stencils, and
+ * an element's E, g and H are the sums over its S sub-stencils (each pair
+ * block and node gradient is held by exactly one of them). Synchronous. */
+int sx_add_tet_ho(sx_scene* scene, int order, const int32_t* tets, int64_t n,
+                  const double* young, const double* poisson, double density,
+                  const double* rule, int nq, void* stream, int* energy_id);
 
 /* Lagged rotations of the COROT / ARAP blocks of a scene (§7.1).
  * sx_update_rotations: R of every tet of those blocks := the rotation of

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsx.so")
-SOURCES = ["sx_elements.cu", "sx_elements_fproj.cu", "sx_elements_models.cu", "sx_clamp.cu",
+SOURCES = ["sx_elements.cu", "sx_elements_fproj.cu", "sx_elements_models.cu", "sx_elements_ho.cu",
+           "sx_clamp.cu", "sx_tetho.cu",
            "sx_graph.cu", "sx_assemble.cu", "sx_solve.cu", "sx_api.cu", "sx_server.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -41,6 +41,15 @@ struct BlockHost {
     // friction: lag [13][n] (beta, T, fn, dx_lag), mu, yhat, dt of the lag
     double* flag = nullptr;
     double mu_f = 0.0, yhat = 0.0, dt_f = 1.0;
+    // high-order tets (n = ho_n ho_S sub-stencils)
+    int ho_K = 0, ho_S = 0, ho_nq = 0;
+    int64_t ho_n = 0;
+    int* ho_conn = nullptr;
+    double* ho_Jinv = nullptr;
+    double* ho_wdet = nullptr;
+    double* ho_dN = nullptr;
+    int* ho_sub = nullptr;
+    int* ho_own = nullptr;
 };
 
 constexpr int kNodeTile = 256;
@@ -221,10 +230,15 @@ int elem_grid(const sx_ctx* ctx, int precision, int kinds, int project, int ntil
 }
 
 // instantiation bits of a block (tets of a density other than SNH add 16)
+// units the element kernel's tiles count: elements for high-order tets
+// (one thread evaluates all sub-stencils of an element), stencils otherwise
+int64_t tile_units(const BlockHost& b) { return b.kind == SX_KIND_TET_HO ? b.ho_n : b.n; }
+
 int kind_bit(const BlockHost& b)
 {
     if (b.kind == SX_KIND_SNH_TET4) return b.model == SX_MODEL_SNH ? 1 : 1 | 16;
     if (b.kind == SX_KIND_PT_FRICTION) return 32;
+    if (b.kind == SX_KIND_TET_HO) return 64;
     return b.kind == SX_KIND_HINGE4 ? 2 : 4;
 }
 
@@ -368,6 +382,16 @@ SceneDev make_desc(const sx_scene* s, bool trial)
         e.mu_f = h.mu_f;
         e.yhat = h.yhat;
         e.dt_f = h.dt_f;
+        e.ho_K = h.ho_K;
+        e.ho_S = h.ho_S;
+        e.ho_nq = h.ho_nq;
+        e.ho_n = h.ho_n;
+        e.ho_conn = h.ho_conn;
+        e.ho_Jinv = h.ho_Jinv;
+        e.ho_wdet = h.ho_wdet;
+        e.ho_dN = h.ho_dN;
+        e.ho_sub = h.ho_sub;
+        e.ho_own = h.ho_own;
     }
     d.x = trial ? s->x_trial : s->x;
     d.v = s->v;
@@ -430,10 +454,11 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
             sx_scene* s = B->scenes[i];
             eb[i] = (int)B->elem_tiles.size();
             const int et = sx::elements_block_threads();
-            for (size_t b = 0; b < s->blocks.size(); ++b)
-                for (int64_t k = 0; k < s->blocks[b].n; k += et)
-                    B->elem_tiles.push_back(
-                        Tile{i, (int)b, k, (int)std::min<int64_t>(et, s->blocks[b].n - k), 0});
+            for (size_t b = 0; b < s->blocks.size(); ++b) {
+                const int64_t nu = tile_units(s->blocks[b]);
+                for (int64_t k = 0; k < nu; k += et)
+                    B->elem_tiles.push_back(Tile{i, (int)b, k, (int)std::min<int64_t>(et, nu - k), 0});
+            }
             ee[i] = (int)B->elem_tiles.size();
             nb[i] = (int)B->node_tiles.size();
             for (int64_t k = 0; k < s->N; k += kNodeTile)
@@ -480,7 +505,10 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
         for (sx_scene* s : B->scenes)
             for (auto& b : s->blocks) {
                 // hinges and friction are PSD by construction: never queued
-                if (b.kind != SX_KIND_HINGE4 && b.kind != SX_KIND_PT_FRICTION) cap += b.n;
+                // (high-order tets project per quadrature point in the element kernel)
+                if (b.kind != SX_KIND_HINGE4 && b.kind != SX_KIND_PT_FRICTION &&
+                    b.kind != SX_KIND_TET_HO)
+                    cap += b.n;
                 if (b.n) B->kinds |= kind_bit(b);
             }
         if (!B->kinds) B->kinds = 1;
@@ -1230,6 +1258,119 @@ int sx_add_pt_barrier(sx_scene* s, const int32_t* pairs, int64_t n, double dhat,
     return SX_OK;
 }
 
+int sx_add_tet_ho(sx_scene* s, int order, const int32_t* tets, int64_t n, const double* young,
+                  const double* poisson, double density, const double* rule, int nq,
+                  void* stream, int* energy_id)
+{
+    int rc = add_block_common(s, "add_tet_ho");
+    if (rc != SX_OK) return rc;
+    sx_ctx* ctx = s->ctx;
+    if ((order != 2 && order != 3) || n < 0 || (n > 0 && (!tets || !young || !poisson)) ||
+        !rule || nq < 1 || nq > SX_HO_MAX_QP || !(density >= 0.0))
+        return fail(ctx, SX_EINVAL, "add_tet_ho: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    s->stream = st;
+    const int K = order == 2 ? 10 : 20;
+    std::vector<int> sub, own;
+    const int S = tetho_cover(K, sub, own);
+    // host copies of the element arrays (host or device input)
+    std::vector<int32_t> ht((size_t)n * K);
+    std::vector<double> hy((size_t)n), hp((size_t)n);
+    if (n) {
+        CK(cudaMemcpy(ht.data(), tets, ht.size() * sizeof(int32_t), cudaMemcpyDefault));
+        CK(cudaMemcpy(hy.data(), young, n * sizeof(double), cudaMemcpyDefault));
+        CK(cudaMemcpy(hp.data(), poisson, n * sizeof(double), cudaMemcpyDefault));
+    }
+    for (int32_t id : ht)
+        if (id < 0 || id >= s->N) return fail(ctx, SX_EINVAL, "add_tet_ho: node id out of range");
+    BlockHost b;
+    b.kind = SX_KIND_TET_HO;
+    b.n = n * S;
+    b.rho = density;
+    b.ho_K = K;
+    b.ho_S = S;
+    b.ho_nq = nq;
+    b.ho_n = n;
+    // the sub-stencils as 4-node stencils for the pattern and the assembly
+    {
+        std::vector<int32_t> c4((size_t)n * S * 4);
+        for (int64_t e = 0; e < n; ++e)
+            for (int j = 0; j < S; ++j)
+                for (int a = 0; a < 4; ++a)
+                    c4[((size_t)e * S + j) * 4 + a] = ht[(size_t)e * K + sub[4 * j + a]];
+        if ((rc = copy_conn(ctx, s, c4.data(), n * S, &b.conn, st)) != SX_OK) return rc;
+        CK(cudaStreamSynchronize(st));
+    }
+    std::vector<int32_t> soa((size_t)n * K);
+    for (int64_t e = 0; e < n; ++e)
+        for (int a = 0; a < K; ++a) soa[(size_t)a * n + e] = ht[(size_t)e * K + a];
+    std::vector<double> hdN((size_t)nq * K * 3), hw(nq);
+    for (int q = 0; q < nq; ++q) {
+        hw[q] = rule[4 * q];
+        tetho_ref_grads(K, rule + 4 * q + 1, hdN.data() + (size_t)q * K * 3);
+    }
+    // Lame parameters of the SNH density (mu' = 4 mu / 3, lambda' = lambda + 5 mu / 6)
+    std::vector<double> hmu((size_t)n), hlam((size_t)n);
+    for (int64_t e = 0; e < n; ++e) {
+        const double m = hy[e] / (2.0 * (1.0 + hp[e]));
+        const double l = hy[e] * hp[e] / ((1.0 + hp[e]) * (1.0 - 2.0 * hp[e]));
+        hmu[e] = m * (4.0 / 3.0);
+        hlam[e] = l + m * (5.0 / 6.0);
+    }
+    if (dalloc(s, &b.ho_conn, (size_t)n * K) || dalloc(s, &b.ho_Jinv, (size_t)nq * 9 * n) ||
+        dalloc(s, &b.ho_wdet, (size_t)nq * n) || dalloc(s, &b.ho_dN, hdN.size()) ||
+        dalloc(s, &b.ho_sub, sub.size()) || dalloc(s, &b.ho_own, own.size()) ||
+        dalloc(s, &b.mu, (size_t)n) || dalloc(s, &b.lam, (size_t)n))
+        return fail(ctx, SX_ENOMEM, "add_tet_ho: allocation failed");
+    if (n) {
+        CK(cudaMemcpyAsync(b.ho_conn, soa.data(), soa.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b.mu, hmu.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b.lam, hlam.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemcpyAsync(b.ho_dN, hdN.data(), hdN.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b.ho_sub, sub.data(), sub.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b.ho_own, own.data(), own.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    double *dw = nullptr, *vol = nullptr;
+    int* bad = nullptr;
+    CK(cudaMallocAsync((void**)&dw, nq * sizeof(double), st));
+    CK(cudaMallocAsync((void**)&vol, std::max<int64_t>(n, 1) * sizeof(double), st));
+    CK(cudaMallocAsync((void**)&bad, 2 * sizeof(int), st));
+    CK(cudaMemsetAsync(bad, 0, 2 * sizeof(int), st));
+    CK(cudaMemcpyAsync(dw, hw.data(), nq * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(launch_tetho_rest(s->X, s->N, b.ho_conn, n, K, nq, dw, b.ho_dN, b.ho_Jinv, b.ho_wdet, vol,
+                         bad, st));
+    int hbad[2] = {0, 0};
+    std::vector<double> hv((size_t)n);
+    CK(cudaMemcpyAsync(hbad, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (n) CK(cudaMemcpyAsync(hv.data(), vol, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(dw, st));
+    CK(cudaFreeAsync(vol, st));
+    CK(cudaFreeAsync(bad, st));
+    CK(cudaStreamSynchronize(st));
+    if (hbad[1]) return fail(ctx, SX_EINVAL, "add_tet_ho: node id out of range");
+    if (hbad[0])
+        return fail(ctx, SX_EDEGENERATE, "add_tet_ho: " + std::to_string(hbad[0]) +
+                                              " elements with det J0 <= 0 at a point");
+    // lumped mass rho V_e / K per node, in element order, into the extra mass
+    if (n && density > 0.0) {
+        std::vector<double> m((size_t)s->N, 0.0);
+        for (int64_t e = 0; e < n; ++e)
+            for (int a = 0; a < K; ++a) m[ht[(size_t)e * K + a]] += density * hv[e] / K;
+        double* tmp = nullptr;
+        CK(cudaMallocAsync((void**)&tmp, s->N * sizeof(double), st));
+        CK(cudaMemcpyAsync(tmp, m.data(), s->N * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_add_vec<<<(unsigned)((s->N + 255) / 256), 256, 0, st>>>(s->extra_mass, tmp, s->N);
+        if (s->finalized)
+            k_add_vec<<<(unsigned)((s->N + 255) / 256), 256, 0, st>>>(s->mass, tmp, s->N);
+        CK(cudaGetLastError());
+        CK(cudaFreeAsync(tmp, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    register_block(s, std::move(b), energy_id);
+    return SX_OK;
+}
+
 int sx_add_pt_friction(sx_scene* s, const int32_t* pairs, int64_t n, double mu, double yhat,
                        double dhat, double kappa, void* stream, int* energy_id)
 {
@@ -1691,8 +1832,9 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
     std::vector<Tile> tiles;
     const int et = elements_block_threads();
-    for (int64_t k = 0; k < b.n; k += et)
-        tiles.push_back(Tile{0, energy_id, k, (int)std::min<int64_t>(et, b.n - k), 0});
+    const int64_t nu = tile_units(b);
+    for (int64_t k = 0; k < nu; k += et)
+        tiles.push_back(Tile{0, energy_id, k, (int)std::min<int64_t>(et, nu - k), 0});
     Tile* d_tiles = nullptr;
     if ((rc = upload(ctx, &d_tiles, tiles, st)) != SX_OK) return rc;
     double* tmpE = nullptr;
@@ -2290,8 +2432,9 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
     Tile tiles[kNaMaxTiles];
     const int et = elements_block_threads();
     int nt = 0;
-    for (int64_t k = 0; k < b.n; k += et)
-        tiles[nt++] = Tile{0, energy_id, k, (int)std::min<int64_t>(et, b.n - k), 0};
+    const int64_t nu = tile_units(b);
+    for (int64_t k = 0; k < nu; k += et)
+        tiles[nt++] = Tile{0, energy_id, k, (int)std::min<int64_t>(et, nu - k), 0};
     CK(cudaMemcpyAsync(P->tiles, tiles, nt * sizeof(Tile), cudaMemcpyHostToDevice, st));
     static const int one = 1;
     CK(cudaMemcpyAsync((char*)s->sc + offsetof(SceneScal, active), &one, sizeof(int),

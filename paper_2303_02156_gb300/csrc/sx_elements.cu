@@ -291,12 +291,16 @@ const void* elements_kernel(int precision, int variant)
     case 3: return elements_kernel_fproj(9, f);
     case 4: return elements_kernel_models(25, f);
     case 5: return elements_kernel_models(63, f);
+    case 6: return elements_kernel_ho(64, f);
+    case 7: return elements_kernel_ho(127, f);
     default: return elements_kernel_snh(7, f);
     }
 }
 
 int elements_variant(int kinds, int project)
 {
+    // high-order tets: alone, or with every other kind
+    if (kinds & 64) return (kinds & ~64) ? 7 : 6;
     // tets of the other densities or friction: one instantiation with the
     // material projection compiled in, for tets alone or every kind
     if (kinds & (16 | 32)) return (kinds & (2 | 4 | 32)) ? 5 : 4;
@@ -322,6 +326,8 @@ cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s)
     case 3: return launch_elements_fproj(9, f, L, grid, s);
     case 4: return launch_elements_models(25, f, L, grid, s);
     case 5: return launch_elements_models(63, f, L, grid, s);
+    case 6: return launch_elements_ho(64, f, L, grid, s);
+    case 7: return launch_elements_ho(127, f, L, grid, s);
     default: return launch_elements_snh(7, f, L, grid, s);
     }
 }

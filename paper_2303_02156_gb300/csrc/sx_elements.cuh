@@ -33,7 +33,8 @@
 //
 // The element kernel k_elements<R, HT, KINDS> is instantiated in three
 // translation units (sx_elements.cu: KINDS 1, 7; sx_elements_fproj.cu: 9,
-// 15; sx_elements_models.cu: 25, 63) so that they compile in parallel.
+// 15; sx_elements_models.cu: 25, 63; sx_elements_ho.cu: 64, 127) so that
+// they compile in parallel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -357,28 +358,20 @@ __device__ __forceinline__ void jacobi3(double (&A)[6], double (&Q)[9])
     }
 }
 
-// project mode 2 for one SNH tet: removes from its Hessian blocks the
-// negative modes of d2psi/dF2 (H = V B^T proj(d2psi/dF2) B). In the frame
+// Negative modes of the SNH material Hessian d2psi/dF2 at F. In the frame
 // of the signed SVD F = U diag(s) V^T (U, V rotations) the material Hessian
 // a I + gam F F^T + lam' C C^T + b dC/dF splits into three twist/flip pairs,
 // eigenvalue a - b s_k on (u_i v_j^T + u_j v_i^T)/sqrt2 and a + b s_k on
 // (u_i v_j^T - u_j v_i^T)/sqrt2 ({i, j, k} = {0, 1, 2}), and the stretch
 // block a I + gam s s^T + lam' p p^T + b K on U diag(q) V^T, with
 // p = (s1 s2, s0 s2, s0 s1) and K the symmetric 3x3 with zero diagonal and
-// K01 = s2, K02 = s1, K12 = s0. A negative mode (lambda, E) changes block
-// (a, b) by -V lambda (E G_a)(E G_b)^T. Returns the number of modes removed.
-template <typename HT>
-__device__ int snh_fproj(const double* xg, const double* Dinv, double Vd, double mud,
-                         double lamd, HT* staged, double* full)
+// K01 = s2, K02 = s1, K12 = s0. Writes each negative eigenvalue and its unit
+// F-space eigenvector as a 3x3 matrix M (row-major); returns their count.
+// A mode changes the Hessian block (a, b) of an element by
+// -V lambda (M G_a)(M G_b)^T.
+__device__ __forceinline__ int snh_neg_modes(const double (&F)[9], double mud, double lamd,
+                                             double (&lam)[9], double (&M)[9][9])
 {
-    double F[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const double d1 = xg[3 + i] - xg[i], d2 = xg[6 + i] - xg[i], d3 = xg[9 + i] - xg[i];
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            F[3 * i + j] = d1 * Dinv[j] + d2 * Dinv[3 + j] + d3 * Dinv[6 + j];
-    }
     double Ic = 0.0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) Ic = fma(F[k], F[k], Ic);
@@ -447,7 +440,70 @@ __device__ int snh_fproj(const double* xg, const double* Dinv, double Vd, double
             sg[k] = (k == i0) ? si : (k == j0) ? sj : sm;
         }
     }
-    // g[a][k] = v_k . G_a
+    int cnt = 0;
+    const double h = 0.70710678118654752440;   // 1/sqrt(2)
+    // twist / flip pairs: M = (u_i v_j^T +- u_j v_i^T)/sqrt2
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+#pragma unroll
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            const double lambda = a + sgn * b * sg[k];   // sgn -1: symmetric, +1: antisymmetric
+            if (!(lambda < 0.0)) continue;
+            const double sym = (sgn < 0) ? 1.0 : -1.0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    M[cnt][3 * r + c] = h * (U[i][r] * Vm[3 * c + j] + sym * U[j][r] * Vm[3 * c + i]);
+            lam[cnt++] = lambda;
+        }
+    }
+    // stretch block: M = sum_k Q3[k][e] u_k v_k^T
+    const double pv[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};
+    double A3[6];
+    A3[pk(0, 0)] = a + gam * sg[0] * sg[0] + lamd * pv[0] * pv[0];
+    A3[pk(1, 1)] = a + gam * sg[1] * sg[1] + lamd * pv[1] * pv[1];
+    A3[pk(2, 2)] = a + gam * sg[2] * sg[2] + lamd * pv[2] * pv[2];
+    A3[pk(1, 0)] = gam * sg[1] * sg[0] + lamd * pv[1] * pv[0] + b * sg[2];
+    A3[pk(2, 0)] = gam * sg[2] * sg[0] + lamd * pv[2] * pv[0] + b * sg[1];
+    A3[pk(2, 1)] = gam * sg[2] * sg[1] + lamd * pv[2] * pv[1] + b * sg[0];
+    double Q3[9];
+    jacobi3(A3, Q3);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const double lambda = A3[pk(e, e)];
+        if (!(lambda < 0.0)) continue;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                M[cnt][3 * r + c] = Q3[0 + e] * U[0][r] * Vm[3 * c + 0] +
+                                    Q3[3 + e] * U[1][r] * Vm[3 * c + 1] +
+                                    Q3[6 + e] * U[2][r] * Vm[3 * c + 2];
+        lam[cnt++] = lambda;
+    }
+    return cnt;
+}
+
+// project mode 2 for one SNH tet: removes from its Hessian blocks the
+// negative modes of d2psi/dF2 (H = V B^T proj(d2psi/dF2) B). Returns the
+// number of modes removed.
+template <typename HT>
+__device__ int snh_fproj(const double* xg, const double* Dinv, double Vd, double mud,
+                         double lamd, HT* staged, double* full)
+{
+    double F[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double d1 = xg[3 + i] - xg[i], d2 = xg[6 + i] - xg[i], d3 = xg[9 + i] - xg[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            F[3 * i + j] = d1 * Dinv[j] + d2 * Dinv[3 + j] + d3 * Dinv[6 + j];
+    }
+    double lam[9], M[9][9];
+    const int cnt = snh_neg_modes(F, mud, lamd, lam, M);
+    if (!cnt) return 0;
     double G[4][3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -456,15 +512,15 @@ __device__ int snh_fproj(const double* xg, const double* Dinv, double Vd, double
         G[3][j] = Dinv[6 + j];
         G[0][j] = -(Dinv[j] + Dinv[3 + j] + Dinv[6 + j]);
     }
-    double g[4][3];
+    for (int md = 0; md < cnt; ++md) {
+        double w[12];
 #pragma unroll
-    for (int n = 0; n < 4; ++n)
+        for (int n = 0; n < 4; ++n)
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-            g[n][k] = G[n][0] * Vm[k] + G[n][1] * Vm[3 + k] + G[n][2] * Vm[6 + k];
-    int removed = 0;
-    auto remove = [&](double lambda, const double (&w)[12]) {
-        const double sc = Vd * lambda;
+            for (int r = 0; r < 3; ++r)
+                w[3 * n + r] = M[md][3 * r] * G[n][0] + M[md][3 * r + 1] * G[n][1] +
+                               M[md][3 * r + 2] * G[n][2];
+        const double sc = Vd * lam[md];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -486,52 +542,8 @@ __device__ int snh_fproj(const double* xg, const double* Dinv, double Vd, double
                             }
                         }
                     }
-        ++removed;
-    };
-    const double h = 0.70710678118654752440;   // 1/sqrt(2)
-    // twist / flip pairs
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int i = (k + 1) % 3, j = (k + 2) % 3;
-#pragma unroll
-        for (int sgn = -1; sgn <= 1; sgn += 2) {
-            const double lambda = a + sgn * b * sg[k];   // sgn -1: symmetric, +1: antisymmetric
-            if (!(lambda < 0.0)) continue;
-            const double sym = (sgn < 0) ? 1.0 : -1.0;
-            double w[12];
-#pragma unroll
-            for (int n = 0; n < 4; ++n)
-#pragma unroll
-                for (int r = 0; r < 3; ++r)
-                    w[3 * n + r] = h * (U[i][r] * g[n][j] + sym * U[j][r] * g[n][i]);
-            remove(lambda, w);
-        }
     }
-    // stretch block
-    const double pv[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};
-    double A3[6];
-    A3[pk(0, 0)] = a + gam * sg[0] * sg[0] + lamd * pv[0] * pv[0];
-    A3[pk(1, 1)] = a + gam * sg[1] * sg[1] + lamd * pv[1] * pv[1];
-    A3[pk(2, 2)] = a + gam * sg[2] * sg[2] + lamd * pv[2] * pv[2];
-    A3[pk(1, 0)] = gam * sg[1] * sg[0] + lamd * pv[1] * pv[0] + b * sg[2];
-    A3[pk(2, 0)] = gam * sg[2] * sg[0] + lamd * pv[2] * pv[0] + b * sg[1];
-    A3[pk(2, 1)] = gam * sg[2] * sg[1] + lamd * pv[2] * pv[1] + b * sg[0];
-    double Q3[9];
-    jacobi3(A3, Q3);
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        const double lambda = A3[pk(e, e)];
-        if (!(lambda < 0.0)) continue;
-        double w[12];
-#pragma unroll
-        for (int n = 0; n < 4; ++n)
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-                w[3 * n + r] = Q3[0 + e] * g[n][0] * U[0][r] + Q3[3 + e] * g[n][1] * U[1][r] +
-                               Q3[6 + e] * g[n][2] * U[2][r];
-        remove(lambda, w);
-    }
-    return removed;
+    return cnt;
 }
 
 template <typename R, typename HT, bool FPROJ>
@@ -990,6 +1002,243 @@ __device__ __noinline__ void eval_friction(const ElemLaunch& L, const SceneDev& 
     }
 }
 
+// ------------------------------------------------------------------ high-order tets
+// psi(F) (double, rest-relative, cancellation-free as for the linear tet)
+// and, at level >= 1, P and the Hessian coefficients of SNH at one point
+// with unit volume (the caller scales by w det J0).
+template <typename R>
+__device__ __forceinline__ double snh_point(const double (&Fd)[9], double mud, double lamd,
+                                            int level, SnhCore<R>& S, R (&P)[9])
+{
+    double D[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) D[k] = Fd[k] - ((k % 4 == 0) ? 1.0 : 0.0);
+    const double trD = D[0] + D[4] + D[8];
+    double Ic3 = 2.0 * trD;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ic3 = fma(D[k], D[k], Ic3);
+    const double c2 = (D[0] * D[4] - D[1] * D[3]) + (D[0] * D[8] - D[2] * D[6]) +
+                      (D[4] * D[8] - D[5] * D[7]);
+    const double detD = D[0] * (D[4] * D[8] - D[5] * D[7]) - D[1] * (D[3] * D[8] - D[5] * D[6]) +
+                        D[2] * (D[3] * D[7] - D[4] * D[6]);
+    const double Jm1 = trD + c2 + detD;
+    double psi = 0.5 * mud * Ic3 - 0.5 * mud * log1p(0.25 * Ic3);
+    if (lamd != 0.0) psi += 0.5 * lamd * Jm1 * Jm1 - 0.75 * mud * Jm1;
+    if (level < 1) return psi;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S.F[k] = (R)Fd[k];
+    {
+        const R* F = S.F;
+        R f0[3] = {F[0], F[3], F[6]}, f1[3] = {F[1], F[4], F[7]}, f2[3] = {F[2], F[5], F[8]};
+        R c0[3], c1[3], cc2[3];
+        cross3(f1, f2, c0);
+        cross3(f2, f0, c1);
+        cross3(f0, f1, cc2);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            S.C[i * 3 + 0] = c0[i];
+            S.C[i * 3 + 1] = c1[i];
+            S.C[i * 3 + 2] = cc2[i];
+        }
+    }
+    const double Icd = 3.0 + Ic3;
+    const R inv1 = (R)(1.0 / (Icd + 1.0));
+    const R a = (R)(mud * Icd / (Icd + 1.0));
+    const R b = (lamd != 0.0) ? (R)(lamd * Jm1 - 0.75 * mud) : R(0);
+    const R s0 = (lamd != 0.0) ? (R)(mud * Ic3 / (4.0 * (Icd + 1.0)) + lamd * Jm1)
+                               : (R)(mud * Icd / (Icd + 1.0));
+    R Dr[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Dr[k] = (R)D[k];
+    const R trr = (R)trD;
+    R cofD[9];
+    cofD[0] = Dr[4] * Dr[8] - Dr[5] * Dr[7];
+    cofD[1] = Dr[5] * Dr[6] - Dr[3] * Dr[8];
+    cofD[2] = Dr[3] * Dr[7] - Dr[4] * Dr[6];
+    cofD[3] = Dr[2] * Dr[7] - Dr[1] * Dr[8];
+    cofD[4] = Dr[0] * Dr[8] - Dr[2] * Dr[6];
+    cofD[5] = Dr[1] * Dr[6] - Dr[0] * Dr[7];
+    cofD[6] = Dr[1] * Dr[5] - Dr[2] * Dr[4];
+    cofD[7] = Dr[2] * Dr[3] - Dr[0] * Dr[5];
+    cofD[8] = Dr[0] * Dr[4] - Dr[1] * Dr[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            P[i * 3 + j] = ((i == j) ? s0 + b * trr : R(0)) + a * Dr[i * 3 + j] +
+                           b * (cofD[i * 3 + j] - Dr[j * 3 + i]);
+    S.cI = a;
+    S.cF = R(2) * (R)mud * inv1 * inv1;
+    S.cC = (R)lamd;
+    S.cS = b;
+    return psi;
+}
+
+// 10- and 20-node tets (§7.2 Eq. fem_final): E = sum_q wd_q psi(F_q) with
+// wd_q = w_q det J0_q, F_q = sum_a x_a G_qa^T and G_qa = J0_q^-T dN_a(xi_q).
+// Each point adds SNH blocks of the linear tet's form with V -> wd_q and
+// G_a -> G_qa; with projection the negative modes of d2psi/dF2 at F_q are
+// removed from them (the per-point F-space projection). For the fixed
+// pattern an element is S four-node sub-stencils covering its node pairs:
+// each Hessian block (a, b) goes to the sub-stencil that owns the pair,
+// each node gradient to the one that owns the node, the energy to the
+// first; the other slots hold zeros. The blocks are accumulated over the
+// points in the element's staged slots (one thread per element).
+template <typename R, typename HT>
+__device__ __noinline__ void eval_tetho(const ElemLaunch& L, const SceneDev& S,
+                                        const ElemBlock& B, int64_t e, ThreadOut& o)
+{
+    const int K = B.ho_K, NS = B.ho_S, nq = B.ho_nq;
+    const int64_t ne = B.ho_n;
+    const double mud = B.mu[e], lamd = B.lam[e];
+    double xr[kHoMaxK][3];
+    const double* x0 = S.x + 3 * (int64_t)B.ho_conn[e];
+    for (int a = 0; a < K; ++a) {
+        const double* p = S.x + 3 * (int64_t)B.ho_conn[(int64_t)a * ne + e];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) xr[a][i] = p[i] - x0[i];
+    }
+    R gacc[kHoMaxK][3];
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gacc[a][i] = R(0);
+    double E = 0.0;
+    const int64_t s0 = e * NS;   // first sub-stencil of the element in the block
+    const bool proj = L.level >= 2 && L.project;
+    for (int q = 0; q < nq; ++q) {
+        double Ji[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ji[k] = B.ho_Jinv[((int64_t)q * 9 + k) * ne + e];
+        const double wd = B.ho_wdet[(int64_t)q * ne + e];
+        double G[kHoMaxK][3];
+        double Fd[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int a = 0; a < K; ++a) {
+            const double* dn = B.ho_dN + (q * K + a) * 3;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                G[a][j] = dn[0] * Ji[0 * 3 + j] + dn[1] * Ji[1 * 3 + j] + dn[2] * Ji[2 * 3 + j];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) Fd[3 * i + j] = fma(xr[a][i], G[a][j], Fd[3 * i + j]);
+        }
+        SnhCore<R> C;
+        R P[9];
+        E += wd * snh_point<R>(Fd, mud, lamd, L.level, C, P);
+        if (L.level < 1) continue;
+        const R w = (R)wd;
+        R Gr[kHoMaxK][3];
+        for (int a = 0; a < K; ++a)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Gr[a][j] = (R)G[a][j];
+        for (int a = 0; a < K; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                gacc[a][i] += w * (P[i * 3 + 0] * Gr[a][0] + P[i * 3 + 1] * Gr[a][1] +
+                                   P[i * 3 + 2] * Gr[a][2]);
+        if (L.level < 2) continue;
+        C.cI *= w;
+        C.cF *= w;
+        C.cC *= w;
+        C.cS *= w;
+        R u[kHoMaxK][3], v[kHoMaxK][3];
+        for (int a = 0; a < K; ++a) {
+            matvec3(C.F, Gr[a], u[a]);
+            matvec3(C.C, Gr[a], v[a]);
+        }
+        double mlam[9], M[9][9];
+        const int nm = proj ? snh_neg_modes(Fd, mud, lamd, mlam, M) : 0;
+        for (int j = 0; j < NS; ++j) {
+            const int* l = B.ho_sub + 4 * j;
+            const int own = B.ho_own[j];
+            const int64_t sid = s0 + j;
+            HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (B.base + sid);
+            double* full = L.out_H ? L.out_H + 144 * sid : nullptr;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = a; b < 4; ++b) {
+                    const int ab = up_index(a, b);
+                    R blk[9];
+                    if ((own >> ab) & 1) {
+                        const int la = l[a], lb = l[b];
+                        snh_block(C, Gr[la], Gr[lb], u[la], u[lb], v[la], v[lb], a == b, blk);
+                        for (int md = 0; md < nm; ++md) {
+                            double wa[3], wb[3];
+#pragma unroll
+                            for (int r = 0; r < 3; ++r) {
+                                wa[r] = M[md][3 * r] * G[la][0] + M[md][3 * r + 1] * G[la][1] +
+                                        M[md][3 * r + 2] * G[la][2];
+                                wb[r] = M[md][3 * r] * G[lb][0] + M[md][3 * r + 1] * G[lb][1] +
+                                        M[md][3 * r + 2] * G[lb][2];
+                            }
+                            const double sc = wd * mlam[md];
+#pragma unroll
+                            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) blk[3 * r + c] -= (R)(sc * wa[r] * wb[c]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) blk[k] = R(0);
+                    }
+                    if (staged) {
+                        HT* dst = staged + 9 * ab;
+#pragma unroll
+                        for (int k = 0; k < 9; ++k)
+                            dst[k] = q == 0 ? (HT)blk[k] : (HT)((R)dst[k] + blk[k]);
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < 3; ++r)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                double* p1 = full + (3 * a + r) * 12 + 3 * b + c;
+                                *p1 = (q == 0 ? 0.0 : *p1) + (double)blk[3 * r + c];
+                                if (a != b) {
+                                    double* p2 = full + (3 * b + c) * 12 + 3 * a + r;
+                                    *p2 = (q == 0 ? 0.0 : *p2) + (double)blk[3 * r + c];
+                                }
+                            }
+                    }
+                }
+        }
+    }
+    if (L.level >= 2) {
+        // non-finite check over the element's written blocks
+        for (int j = 0; j < NS; ++j) {
+            const int64_t sid = s0 + j;
+            if (L.out_H) {
+                for (int k = 0; k < 144; ++k)
+                    if (!isfinite(L.out_H[144 * sid + k])) o.nonfinite = 1;
+            } else {
+                const HT* h = (const HT*)S.He + 90 * (B.base + sid);
+                for (int k = 0; k < 90; ++k)
+                    if (!isfinite((double)h[k])) o.nonfinite = 1;
+            }
+        }
+    }
+    o.E = E;
+    if (!isfinite(E)) o.nonfinite = 1;
+    for (int j = 0; j < NS; ++j) {
+        const int64_t sid = s0 + j;
+        if (L.out_E) L.out_E[sid] = j == 0 ? E : 0.0;
+        else S.Ee[B.base + sid] = j == 0 ? E : 0.0;
+        if (L.level >= 1) {
+            const int* l = B.ho_sub + 4 * j;
+            const int own = B.ho_own[j];
+            double* gout = L.out_g ? L.out_g + 12 * sid : S.ge + 12 * (B.base + sid);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double gv = ((own >> (10 + a)) & 1) ? (double)gacc[l[a]][i] : 0.0;
+                    gout[3 * a + i] = gv;
+                    if (!isfinite(gv)) o.nonfinite = 1;
+                }
+        }
+    }
+}
+
 template <typename R, typename HT>
 __device__ void eval_hinge(const ElemLaunch& L, const SceneDev& S, const ElemBlock& B,
                            int64_t e, ThreadOut& o)
@@ -1118,7 +1367,8 @@ __device__ void eval_barrier(const ElemLaunch& L, int scene, int blk, const Scen
 
 // KINDS: bit mask of the stencil kinds compiled in (1 SNH, 2 hinge, 4
 // barrier), 8 for the F-space projection of the SNH tets (project mode
-// 2), 16 for tets of the other densities and 32 for friction. A batch with SNH tets only
+// 2), 16 for tets of the other densities, 32 for friction and 64 for
+// high-order tets. A batch with SNH tets only
 // runs an SNH-only instantiation, which needs fewer registers than the one
 // that can take every kind.
 template <typename R, typename HT, int KINDS>
@@ -1141,7 +1391,9 @@ k_elements(ElemLaunch L)
             const ElemBlock& B = S.blk[T.blk];
             if ((int)threadIdx.x < T.count) {
                 const int64_t e = T.start + threadIdx.x;
-                if ((KINDS & 16) && B.kind == SX_KIND_SNH_TET4 && B.model != SX_MODEL_SNH)
+                if ((KINDS & 64) && B.kind == SX_KIND_TET_HO)
+                    eval_tetho<R, HT>(L, S, B, e, o);
+                else if ((KINDS & 16) && B.kind == SX_KIND_SNH_TET4 && B.model != SX_MODEL_SNH)
                     eval_model<R, HT>(L, T.scene, T.blk, S, B, e, o);
                 else if ((KINDS & 1) && B.kind == SX_KIND_SNH_TET4)
                     eval_snh<R, HT, (KINDS & 8) != 0>(L, T.scene, T.blk, S, B, e, o);
@@ -1151,8 +1403,11 @@ k_elements(ElemLaunch L)
                     eval_friction<R, HT>(L, S, B, e, o);
                 else if ((KINDS & 4) && B.kind == SX_KIND_PT_BARRIER)
                     eval_barrier<R, HT>(L, T.scene, T.blk, S, B, e, o);
-                if (L.out_E) L.out_E[e] = o.E;
-                else S.Ee[B.base + e] = o.E;
+                // (high-order elements write the energies of their sub-stencils)
+                if (!(KINDS & 64) || B.kind != SX_KIND_TET_HO) {
+                    if (L.out_E) L.out_E[e] = o.E;
+                    else S.Ee[B.base + e] = o.E;
+                }
             }
         }
         // fixed-order tile reductions

@@ -60,6 +60,16 @@ struct ElemBlock {
     // friction: lag [13][n] = beta (3), T (6), fn, dx_lag (3); mu, yhat, dt
     const double* flag;
     double mu_f, yhat, dt_f;
+    // high-order tets: ho_n elements of ho_K nodes, ho_S sub-stencils each
+    // (n = ho_n ho_S), ho_nq quadrature points
+    int ho_K, ho_S, ho_nq;
+    int64_t ho_n;
+    const int* ho_conn;      // [K][ho_n] node ids
+    const double* ho_Jinv;   // [nq][9][ho_n] J0^-1 at the points
+    const double* ho_wdet;   // [nq][ho_n] w_q det J0
+    const double* ho_dN;     // [nq][K][3] reference gradients
+    const int* ho_sub;       // [S][4] local nodes of the sub-stencils
+    const int* ho_own;       // [S] bits 0-9: owned upper blocks, 10-13: owned nodes
 };
 
 // per-scene scalars the device loops read and write
@@ -195,7 +205,7 @@ int clamp_block_threads();
 // the element kernel instantiations: variant 0 every kind, 1 SNH only, 2
 // every kind with the F-space projection, 3 SNH only with it
 const void* elements_kernel(int precision, int variant);
-constexpr int kElemVariants = 6;
+constexpr int kElemVariants = 8;
 // the element-kernel instantiations of each translation unit (KINDS values)
 const void* elements_kernel_snh(int kinds, bool f32);      // 1, 7
 const void* elements_kernel_fproj(int kinds, bool f32);    // 9, 15
@@ -206,6 +216,16 @@ cudaError_t launch_elements_fproj(int kinds, bool f32, const ElemLaunch& L, int 
                                   cudaStream_t s);
 cudaError_t launch_elements_models(int kinds, bool f32, const ElemLaunch& L, int grid,
                                    cudaStream_t s);
+// high-order tets (sx_tetho.cu)
+constexpr int kHoMaxK = 20;
+int tetho_cover(int K, std::vector<int>& sub, std::vector<int>& own);
+void tetho_ref_grads(int K, const double* xi, double* dN);
+cudaError_t launch_tetho_rest(const double* X, int64_t N, const int* conn, int64_t n, int K,
+                              int nq, const double* rule_w, const double* dN, double* Jinv,
+                              double* wdet, double* vol, int* bad, cudaStream_t s);
+const void* elements_kernel_ho(int kinds, bool f32);       // 64, 127
+cudaError_t launch_elements_ho(int kinds, bool f32, const ElemLaunch& L, int grid,
+                               cudaStream_t s);
 cudaError_t launch_friction_lag(const double* x, const int4* conn, int64_t n, double dhat,
                                 double kappa, double* lag, cudaStream_t s);
 cudaError_t launch_tet_rotations(const int4* conn, const double* x, const double* Dminv,

@@ -113,6 +113,23 @@ class Scene:
                             nu.ctypes.data, float(density), self.stream, C.byref(eid))
         return self._id(rc, eid, sx.SX_KIND_TET4, n)
 
+    def add_tet_ho(self, order, tets, young, poisson, density, rule):
+        """High-order (order 2: 10-node, 3: 20-node) SNH tets with the
+        quadrature rule ``rule`` (nq x (w, xi0, xi1, xi2))."""
+        K = 10 if order == 2 else 20
+        tets = _i32(tets).reshape(-1, K); n = tets.shape[0]
+        E = _f64(np.broadcast_to(young, (n,))); nu = _f64(np.broadcast_to(poisson, (n,)))
+        rule = _f64(rule).reshape(-1, 4)
+        eid = C.c_int()
+        rc = sx.sx_add_tet_ho(self.h, int(order), tets.ctypes.data, n, E.ctypes.data,
+                              nu.ctypes.data, float(density), rule.ctypes.data, rule.shape[0],
+                              self.stream, C.byref(eid))
+        self.ctx.check(rc)
+        kind, ns = C.c_int(), C.c_int64()
+        self.ctx.check(sx.sx_block_info(self.h, eid.value, C.byref(kind), C.byref(ns)))
+        self.blocks.append((kind.value, ns.value))
+        return eid.value
+
     def add_friction(self, pairs, mu, yhat, dhat, kappa):
         """Lagged IPC friction on point-triangle pairs (no friction until
         the first lag: update_friction or a Newton step)."""

@@ -25,6 +25,8 @@ SX_SERVER_MAX_LANES = 8
 SX_PROJECT_NONE, SX_PROJECT_ELEMENT, SX_PROJECT_MATERIAL = 0, 1, 2
 SX_KIND_TET4 = SX_KIND_SNH_TET4
 SX_KIND_PT_FRICTION = 3
+SX_KIND_TET_HO = 4
+SX_HO_MAX_QP = 64
 SX_MODEL_SNH, SX_MODEL_NH, SX_MODEL_STVK, SX_MODEL_COROT, SX_MODEL_ARAP = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "SX_OK", -1: "SX_EINVAL", -2: "SX_ENOMEM", -3: "SX_ECUDA", -4: "SX_ENAN",
@@ -44,6 +46,7 @@ EXPORTS = [
     "sx_autotune", "sx_set_launch_shape", "sx_get_launch_shape", "sx_set_pairs",
     "sx_compact_pairs", "sx_add_tet4", "sx_update_rotations", "sx_get_rotations",
     "sx_set_rotations", "sx_add_pt_friction", "sx_update_friction", "sx_get_friction_lag",
+    "sx_add_tet_ho",
     "sx_server_create", "sx_server_set_lanes", "sx_server_submit", "sx_server_poll", "sx_server_result",
     "sx_server_drain", "sx_server_stats", "sx_server_destroy",
 ]
@@ -152,6 +155,7 @@ _SIGS = {
     "sx_get_rotations": (_I, [_P, _I, _P, _P]),
     "sx_set_rotations": (_I, [_P, _I, _P, _P]),
     "sx_add_pt_friction": (_I, [_P, _P, _I64, _D, _D, _D, _D, _P, C.POINTER(_I)]),
+    "sx_add_tet_ho": (_I, [_P, _I, _P, _I64, _P, _P, _D, _P, _I, _P, C.POINTER(_I)]),
     "sx_update_friction": (_I, [_P, _D, _P]),
     "sx_get_friction_lag": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "sx_compact_pairs": (_I, [_P, _I, C.POINTER(_I64), _P]),
