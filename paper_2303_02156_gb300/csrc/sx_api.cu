@@ -230,9 +230,9 @@ int elem_grid(const sx_ctx* ctx, int precision, int kinds, int project, int ntil
 }
 
 // instantiation bits of a block (tets of a density other than SNH add 16)
-// units the element kernel's tiles count: elements for high-order tets
-// (one thread evaluates all sub-stencils of an element), stencils otherwise
-int64_t tile_units(const BlockHost& b) { return b.kind == SX_KIND_TET_HO ? b.ho_n : b.n; }
+// units the element kernel's tiles count: stencils (for high-order tets,
+// one thread per sub-stencil)
+int64_t tile_units(const BlockHost& b) { return b.n; }
 
 int kind_bit(const BlockHost& b)
 {

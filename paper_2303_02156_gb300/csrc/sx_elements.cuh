@@ -486,6 +486,13 @@ __device__ __forceinline__ int snh_neg_modes(const double (&F)[9], double mud, d
     return cnt;
 }
 
+// the same as an out-of-line call, for callers with many live registers
+__device__ __noinline__ int snh_neg_modes_call(const double (&F)[9], double mud, double lamd,
+                                               double (&lam)[9], double (&M)[9][9])
+{
+    return snh_neg_modes(F, mud, lamd, lam, M);
+}
+
 // project mode 2 for one SNH tet: removes from its Hessian blocks the
 // negative modes of d2psi/dF2 (H = V B^T proj(d2psi/dF2) B). Returns the
 // number of modes removed.
@@ -1080,16 +1087,21 @@ __device__ __forceinline__ double snh_point(const double (&Fd)[9], double mud, d
 // G_a -> G_qa; with projection the negative modes of d2psi/dF2 at F_q are
 // removed from them (the per-point F-space projection). For the fixed
 // pattern an element is S four-node sub-stencils covering its node pairs:
-// each Hessian block (a, b) goes to the sub-stencil that owns the pair,
+// each Hessian block (a, b) belongs to the sub-stencil that owns the pair,
 // each node gradient to the one that owns the node, the energy to the
-// first; the other slots hold zeros. The blocks are accumulated over the
-// points in the element's staged slots (one thread per element).
+// first. One thread per sub-stencil (an element alone would leave the GPU
+// idle: a 137K-DoF cubic mesh has 10K elements): it forms F at every point
+// from all K nodes and accumulates only its own blocks in registers.
 template <typename R, typename HT>
 __device__ __noinline__ void eval_tetho(const ElemLaunch& L, const SceneDev& S,
-                                        const ElemBlock& B, int64_t e, ThreadOut& o)
+                                        const ElemBlock& B, int64_t sid, ThreadOut& o)
 {
     const int K = B.ho_K, NS = B.ho_S, nq = B.ho_nq;
     const int64_t ne = B.ho_n;
+    const int64_t e = sid / NS;
+    const int j = (int)(sid - e * NS);
+    const int* l = B.ho_sub + 4 * j;
+    const int own = B.ho_own[j];
     const double mud = B.mu[e], lamd = B.lam[e];
     double xr[kHoMaxK][3];
     const double* x0 = S.x + 3 * (int64_t)B.ho_conn[e];
@@ -1098,144 +1110,131 @@ __device__ __noinline__ void eval_tetho(const ElemLaunch& L, const SceneDev& S,
 #pragma unroll
         for (int i = 0; i < 3; ++i) xr[a][i] = p[i] - x0[i];
     }
-    R gacc[kHoMaxK][3];
-    for (int a = 0; a < K; ++a)
+    R acc[10][9];
+    R gl[4][3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) gacc[a][i] = R(0);
+    for (int ab = 0; ab < 10; ++ab)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[ab][k] = R(0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gl[a][i] = R(0);
     double E = 0.0;
-    const int64_t s0 = e * NS;   // first sub-stencil of the element in the block
     const bool proj = L.level >= 2 && L.project;
     for (int q = 0; q < nq; ++q) {
         double Ji[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Ji[k] = B.ho_Jinv[((int64_t)q * 9 + k) * ne + e];
         const double wd = B.ho_wdet[(int64_t)q * ne + e];
-        double G[kHoMaxK][3];
+        const double* dq = B.ho_dN + q * K * 3;
         double Fd[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int a = 0; a < K; ++a) {
-            const double* dn = B.ho_dN + (q * K + a) * 3;
+            const double* dn = dq + 3 * a;
+            double G[3];
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
-                G[a][j] = dn[0] * Ji[0 * 3 + j] + dn[1] * Ji[1 * 3 + j] + dn[2] * Ji[2 * 3 + j];
+            for (int c = 0; c < 3; ++c)
+                G[c] = dn[0] * Ji[0 * 3 + c] + dn[1] * Ji[1 * 3 + c] + dn[2] * Ji[2 * 3 + c];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) Fd[3 * i + j] = fma(xr[a][i], G[a][j], Fd[3 * i + j]);
+                for (int c = 0; c < 3; ++c) Fd[3 * i + c] = fma(xr[a][i], G[c], Fd[3 * i + c]);
         }
         SnhCore<R> C;
         R P[9];
         E += wd * snh_point<R>(Fd, mud, lamd, L.level, C, P);
         if (L.level < 1) continue;
+        // the sub-stencil's four nodes: G (double and R), u = F G, v = C G
+        double Gd[4][3];
+        R Gr[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const double* dn = dq + 3 * l[a];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Gd[a][c] = dn[0] * Ji[0 * 3 + c] + dn[1] * Ji[1 * 3 + c] + dn[2] * Ji[2 * 3 + c];
+                Gr[a][c] = (R)Gd[a][c];
+            }
+        }
         const R w = (R)wd;
-        R Gr[kHoMaxK][3];
-        for (int a = 0; a < K; ++a)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) Gr[a][j] = (R)G[a][j];
-        for (int a = 0; a < K; ++a)
+        for (int a = 0; a < 4; ++a)
+            if ((own >> (10 + a)) & 1)
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-                gacc[a][i] += w * (P[i * 3 + 0] * Gr[a][0] + P[i * 3 + 1] * Gr[a][1] +
-                                   P[i * 3 + 2] * Gr[a][2]);
+                for (int i = 0; i < 3; ++i)
+                    gl[a][i] += w * (P[i * 3 + 0] * Gr[a][0] + P[i * 3 + 1] * Gr[a][1] +
+                                     P[i * 3 + 2] * Gr[a][2]);
         if (L.level < 2) continue;
         C.cI *= w;
         C.cF *= w;
         C.cC *= w;
         C.cS *= w;
-        R u[kHoMaxK][3], v[kHoMaxK][3];
-        for (int a = 0; a < K; ++a) {
+        R u[4][3], v[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
             matvec3(C.F, Gr[a], u[a]);
             matvec3(C.C, Gr[a], v[a]);
         }
-        double mlam[9], M[9][9];
-        const int nm = proj ? snh_neg_modes(Fd, mud, lamd, mlam, M) : 0;
-        for (int j = 0; j < NS; ++j) {
-            const int* l = B.ho_sub + 4 * j;
-            const int own = B.ho_own[j];
-            const int64_t sid = s0 + j;
-            HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (B.base + sid);
-            double* full = L.out_H ? L.out_H + 144 * sid : nullptr;
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = a; b < 4; ++b) {
-                    const int ab = up_index(a, b);
-                    R blk[9];
-                    if ((own >> ab) & 1) {
-                        const int la = l[a], lb = l[b];
-                        snh_block(C, Gr[la], Gr[lb], u[la], u[lb], v[la], v[lb], a == b, blk);
-                        for (int md = 0; md < nm; ++md) {
-                            double wa[3], wb[3];
+            for (int b = a; b < 4; ++b) {
+                const int ab = up_index(a, b);
+                if (!((own >> ab) & 1)) continue;
+                R blk[9];
+                snh_block(C, Gr[a], Gr[b], u[a], u[b], v[a], v[b], a == b, blk);
 #pragma unroll
-                            for (int r = 0; r < 3; ++r) {
-                                wa[r] = M[md][3 * r] * G[la][0] + M[md][3 * r + 1] * G[la][1] +
-                                        M[md][3 * r + 2] * G[la][2];
-                                wb[r] = M[md][3 * r] * G[lb][0] + M[md][3 * r + 1] * G[lb][1] +
-                                        M[md][3 * r + 2] * G[lb][2];
-                            }
-                            const double sc = wd * mlam[md];
+                for (int k = 0; k < 9; ++k) acc[ab][k] += blk[k];
+            }
+        if (proj) {
+            double mlam[9], M[9][9];
+            const int nm = snh_neg_modes_call(Fd, mud, lamd, mlam, M);
+#pragma unroll 1
+            for (int md = 0; md < nm; ++md) {
+                double wv[4][3];
 #pragma unroll
-                            for (int r = 0; r < 3; ++r)
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                                for (int c = 0; c < 3; ++c) blk[3 * r + c] -= (R)(sc * wa[r] * wb[c]);
-                        }
-                    } else {
+                    for (int r = 0; r < 3; ++r)
+                        wv[a][r] = M[md][3 * r] * Gd[a][0] + M[md][3 * r + 1] * Gd[a][1] +
+                                   M[md][3 * r + 2] * Gd[a][2];
+                const double sc = wd * mlam[md];
 #pragma unroll
-                        for (int k = 0; k < 9; ++k) blk[k] = R(0);
-                    }
-                    if (staged) {
-                        HT* dst = staged + 9 * ab;
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                        for (int k = 0; k < 9; ++k)
-                            dst[k] = q == 0 ? (HT)blk[k] : (HT)((R)dst[k] + blk[k]);
-                    } else {
+                    for (int b = a; b < 4; ++b) {
+                        const int ab = up_index(a, b);
+                        if (!((own >> ab) & 1)) continue;
 #pragma unroll
                         for (int r = 0; r < 3; ++r)
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                double* p1 = full + (3 * a + r) * 12 + 3 * b + c;
-                                *p1 = (q == 0 ? 0.0 : *p1) + (double)blk[3 * r + c];
-                                if (a != b) {
-                                    double* p2 = full + (3 * b + c) * 12 + 3 * a + r;
-                                    *p2 = (q == 0 ? 0.0 : *p2) + (double)blk[3 * r + c];
-                                }
-                            }
+                            for (int c = 0; c < 3; ++c)
+                                acc[ab][3 * r + c] -= (R)(sc * wv[a][r] * wv[b][c]);
                     }
-                }
-        }
-    }
-    if (L.level >= 2) {
-        // non-finite check over the element's written blocks
-        for (int j = 0; j < NS; ++j) {
-            const int64_t sid = s0 + j;
-            if (L.out_H) {
-                for (int k = 0; k < 144; ++k)
-                    if (!isfinite(L.out_H[144 * sid + k])) o.nonfinite = 1;
-            } else {
-                const HT* h = (const HT*)S.He + 90 * (B.base + sid);
-                for (int k = 0; k < 90; ++k)
-                    if (!isfinite((double)h[k])) o.nonfinite = 1;
             }
         }
     }
-    o.E = E;
-    if (!isfinite(E)) o.nonfinite = 1;
-    for (int j = 0; j < NS; ++j) {
-        const int64_t sid = s0 + j;
-        if (L.out_E) L.out_E[sid] = j == 0 ? E : 0.0;
-        else S.Ee[B.base + sid] = j == 0 ? E : 0.0;
-        if (L.level >= 1) {
-            const int* l = B.ho_sub + 4 * j;
-            const int own = B.ho_own[j];
-            double* gout = L.out_g ? L.out_g + 12 * sid : S.ge + 12 * (B.base + sid);
+    o.E = j == 0 ? E : 0.0;
+    if (!isfinite(o.E)) o.nonfinite = 1;
+    if (L.level >= 1) {
+        double* gout = L.out_g ? L.out_g + 12 * sid : S.ge + 12 * (B.base + sid);
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const double gv = ((own >> (10 + a)) & 1) ? (double)gacc[l[a]][i] : 0.0;
-                    gout[3 * a + i] = gv;
-                    if (!isfinite(gv)) o.nonfinite = 1;
-                }
-        }
+            for (int i = 0; i < 3; ++i) {
+                gout[3 * a + i] = (double)gl[a][i];
+                if (!isfinite((double)gl[a][i])) o.nonfinite = 1;
+            }
+    }
+    if (L.level >= 2) {
+        auto blockfn = [&](int a, int b, R* out) {
+            const int ab = up_index(a, b);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) out[k] = acc[ab][k];
+        };
+        HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (B.base + sid);
+        double* full = L.out_H ? L.out_H + 144 * sid : nullptr;
+        write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
     }
 }
 
@@ -1403,11 +1402,8 @@ k_elements(ElemLaunch L)
                     eval_friction<R, HT>(L, S, B, e, o);
                 else if ((KINDS & 4) && B.kind == SX_KIND_PT_BARRIER)
                     eval_barrier<R, HT>(L, T.scene, T.blk, S, B, e, o);
-                // (high-order elements write the energies of their sub-stencils)
-                if (!(KINDS & 64) || B.kind != SX_KIND_TET_HO) {
-                    if (L.out_E) L.out_E[e] = o.E;
-                    else S.Ee[B.base + e] = o.E;
-                }
+                if (L.out_E) L.out_E[e] = o.E;
+                else S.Ee[B.base + e] = o.E;
             }
         }
         // fixed-order tile reductions
