@@ -487,7 +487,7 @@ __device__ __forceinline__ int snh_neg_modes(const double (&F)[9], double mud, d
 }
 
 // the same as an out-of-line call, for callers with many live registers
-__device__ __noinline__ int snh_neg_modes_call(const double (&F)[9], double mud, double lamd,
+static __device__ __noinline__ int snh_neg_modes_call(const double (&F)[9], double mud, double lamd,
                                                double (&lam)[9], double (&M)[9][9])
 {
     return snh_neg_modes(F, mud, lamd, lam, M);
