@@ -50,6 +50,8 @@ struct BlockHost {
     double* ho_dN = nullptr;
     int* ho_sub = nullptr;
     int* ho_own = nullptr;
+    double* ho_modes = nullptr;
+    int ho_ept = 1;   // whole elements per element-kernel tile
 };
 
 constexpr int kNodeTile = 256;
@@ -230,9 +232,13 @@ int elem_grid(const sx_ctx* ctx, int precision, int kinds, int project, int ntil
 }
 
 // instantiation bits of a block (tets of a density other than SNH add 16)
-// units the element kernel's tiles count: stencils (for high-order tets,
-// one thread per sub-stencil)
+// units the element kernel's tiles count (stencils) and the tile length:
+// a high-order tile holds whole elements (one thread per sub-stencil)
 int64_t tile_units(const BlockHost& b) { return b.n; }
+int64_t tile_step(const BlockHost& b, int et)
+{
+    return b.kind == SX_KIND_TET_HO ? (int64_t)b.ho_ept * b.ho_S : et;
+}
 
 int kind_bit(const BlockHost& b)
 {
@@ -392,6 +398,7 @@ SceneDev make_desc(const sx_scene* s, bool trial)
         e.ho_dN = h.ho_dN;
         e.ho_sub = h.ho_sub;
         e.ho_own = h.ho_own;
+        e.ho_modes = h.ho_modes;
     }
     d.x = trial ? s->x_trial : s->x;
     d.v = s->v;
@@ -455,9 +462,9 @@ int prepare_batch(sx_ctx* ctx, Batch* B, cudaStream_t st)
             eb[i] = (int)B->elem_tiles.size();
             const int et = sx::elements_block_threads();
             for (size_t b = 0; b < s->blocks.size(); ++b) {
-                const int64_t nu = tile_units(s->blocks[b]);
-                for (int64_t k = 0; k < nu; k += et)
-                    B->elem_tiles.push_back(Tile{i, (int)b, k, (int)std::min<int64_t>(et, nu - k), 0});
+                const int64_t nu = tile_units(s->blocks[b]), st = tile_step(s->blocks[b], et);
+                for (int64_t k = 0; k < nu; k += st)
+                    B->elem_tiles.push_back(Tile{i, (int)b, k, (int)std::min<int64_t>(st, nu - k), 0});
             }
             ee[i] = (int)B->elem_tiles.size();
             nb[i] = (int)B->node_tiles.size();
@@ -1291,6 +1298,9 @@ int sx_add_tet_ho(sx_scene* s, int order, const int32_t* tets, int64_t n, const 
     b.ho_S = S;
     b.ho_nq = nq;
     b.ho_n = n;
+    // a tile of whole elements: at most one thread per sub-stencil and one
+    // per (element, point)
+    b.ho_ept = std::max(1, std::min(elements_block_threads() / S, elements_block_threads() / nq));
     // the sub-stencils as 4-node stencils for the pattern and the assembly
     {
         std::vector<int32_t> c4((size_t)n * S * 4);
@@ -1320,7 +1330,8 @@ int sx_add_tet_ho(sx_scene* s, int order, const int32_t* tets, int64_t n, const 
     if (dalloc(s, &b.ho_conn, (size_t)n * K) || dalloc(s, &b.ho_Jinv, (size_t)nq * 9 * n) ||
         dalloc(s, &b.ho_wdet, (size_t)nq * n) || dalloc(s, &b.ho_dN, hdN.size()) ||
         dalloc(s, &b.ho_sub, sub.size()) || dalloc(s, &b.ho_own, own.size()) ||
-        dalloc(s, &b.mu, (size_t)n) || dalloc(s, &b.lam, (size_t)n))
+        dalloc(s, &b.mu, (size_t)n) || dalloc(s, &b.lam, (size_t)n) ||
+        dalloc(s, &b.ho_modes, (size_t)n * nq * 91))
         return fail(ctx, SX_ENOMEM, "add_tet_ho: allocation failed");
     if (n) {
         CK(cudaMemcpyAsync(b.ho_conn, soa.data(), soa.size() * sizeof(int32_t),
@@ -1832,9 +1843,9 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
     std::vector<Tile> tiles;
     const int et = elements_block_threads();
-    const int64_t nu = tile_units(b);
-    for (int64_t k = 0; k < nu; k += et)
-        tiles.push_back(Tile{0, energy_id, k, (int)std::min<int64_t>(et, nu - k), 0});
+    const int64_t nu = tile_units(b), ts = tile_step(b, et);
+    for (int64_t k = 0; k < nu; k += ts)
+        tiles.push_back(Tile{0, energy_id, k, (int)std::min<int64_t>(ts, nu - k), 0});
     Tile* d_tiles = nullptr;
     if ((rc = upload(ctx, &d_tiles, tiles, st)) != SX_OK) return rc;
     double* tmpE = nullptr;
@@ -2421,6 +2432,14 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
                         " elements, more than the static scratch holds (" +
                         std::to_string(SX_NOALLOC_MAX_ELEMENTS) + ")");
     if (b.n == 0) return SX_OK;
+    {
+        // the static tile table holds kNaMaxTiles tiles (shorter high-order
+        // tiles may need more than the 128-stencil ones it is sized for)
+        const int64_t ts = tile_step(b, elements_block_threads());
+        if ((b.n + ts - 1) / ts > kNaMaxTiles)
+            return fail(ctx, SX_EINVAL, "eval_elements_noalloc: block needs more tiles than the "
+                                        "static scratch holds");
+    }
     NaPtrs* P = nullptr;
     if ((rc = na_setup(ctx, &P)) != SX_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -2432,9 +2451,9 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
     Tile tiles[kNaMaxTiles];
     const int et = elements_block_threads();
     int nt = 0;
-    const int64_t nu = tile_units(b);
-    for (int64_t k = 0; k < nu; k += et)
-        tiles[nt++] = Tile{0, energy_id, k, (int)std::min<int64_t>(et, nu - k), 0};
+    const int64_t nu = tile_units(b), ts = tile_step(b, et);
+    for (int64_t k = 0; k < nu; k += ts)
+        tiles[nt++] = Tile{0, energy_id, k, (int)std::min<int64_t>(ts, nu - k), 0};
     CK(cudaMemcpyAsync(P->tiles, tiles, nt * sizeof(Tile), cudaMemcpyHostToDevice, st));
     static const int one = 1;
     CK(cudaMemcpyAsync((char*)s->sc + offsetof(SceneScal, active), &one, sizeof(int),

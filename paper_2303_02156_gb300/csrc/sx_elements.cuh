@@ -1089,153 +1089,215 @@ __device__ __forceinline__ double snh_point(const double (&Fd)[9], double mud, d
 // pattern an element is S four-node sub-stencils covering its node pairs:
 // each Hessian block (a, b) belongs to the sub-stencil that owns the pair,
 // each node gradient to the one that owns the node, the energy to the
-// first. One thread per sub-stencil (an element alone would leave the GPU
-// idle: a 137K-DoF cubic mesh has 10K elements): it forms F at every point
-// from all K nodes and accumulates only its own blocks in registers.
+// first. A tile holds whole elements (ho_ept of them, ho_ept nq <= 128).
+// Phase 1, one thread per (element, point): F_q from all K nodes, psi, P
+// and the Hessian coefficients into a shared record, the negative modes
+// (with projection) into the block's scratch. Phase 2, one thread per
+// sub-stencil: its own blocks and node gradients, accumulated over the
+// points in registers. All threads of the CTA call this (it synchronizes).
+constexpr int kHoRec = 42;   // wd, psi, Ji (9), F (9), C (9), P (9), cI cF cC cS
+
 template <typename R, typename HT>
-__device__ __noinline__ void eval_tetho(const ElemLaunch& L, const SceneDev& S,
-                                        const ElemBlock& B, int64_t sid, ThreadOut& o)
+__device__ void tetho_tile(const ElemLaunch& L, const SceneDev& S, const ElemBlock& B,
+                           const Tile& T, ThreadOut& o)
 {
+    __shared__ double rec[kElemThreads][kHoRec];
     const int K = B.ho_K, NS = B.ho_S, nq = B.ho_nq;
     const int64_t ne = B.ho_n;
-    const int64_t e = sid / NS;
-    const int j = (int)(sid - e * NS);
-    const int* l = B.ho_sub + 4 * j;
-    const int own = B.ho_own[j];
-    const double mud = B.mu[e], lamd = B.lam[e];
-    double xr[kHoMaxK][3];
-    const double* x0 = S.x + 3 * (int64_t)B.ho_conn[e];
-    for (int a = 0; a < K; ++a) {
-        const double* p = S.x + 3 * (int64_t)B.ho_conn[(int64_t)a * ne + e];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) xr[a][i] = p[i] - x0[i];
-    }
-    R acc[10][9];
-    R gl[4][3];
-#pragma unroll
-    for (int ab = 0; ab < 10; ++ab)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) acc[ab][k] = R(0);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) gl[a][i] = R(0);
-    double E = 0.0;
+    const int64_t e0 = T.start / NS;
+    const int nel = T.count / NS;
     const bool proj = L.level >= 2 && L.project;
-    for (int q = 0; q < nq; ++q) {
+    // ---- phase 1: one (element, point) per thread
+    if ((int)threadIdx.x < nel * nq) {
+        const int el = threadIdx.x / nq, q = threadIdx.x - el * nq;
+        const int64_t e = e0 + el;
+        const double mud = B.mu[e], lamd = B.lam[e];
+        double* r = rec[threadIdx.x];
         double Ji[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Ji[k] = B.ho_Jinv[((int64_t)q * 9 + k) * ne + e];
         const double wd = B.ho_wdet[(int64_t)q * ne + e];
+        // Ds = sum_a (x_a - x_0) dN_a^T, F = Ds J0^-1
+        const double* x0 = S.x + 3 * (int64_t)B.ho_conn[e];
         const double* dq = B.ho_dN + q * K * 3;
-        double Fd[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int a = 0; a < K; ++a) {
+        double Ds[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int a = 1; a < K; ++a) {
+            const double* p = S.x + 3 * (int64_t)B.ho_conn[(int64_t)a * ne + e];
             const double* dn = dq + 3 * a;
-            double G[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double xi = p[i] - x0[i];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Ds[3 * i + c] = fma(xi, dn[c], Ds[3 * i + c]);
+            }
+        }
+        double Fd[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                G[c] = dn[0] * Ji[0 * 3 + c] + dn[1] * Ji[1 * 3 + c] + dn[2] * Ji[2 * 3 + c];
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) Fd[3 * i + c] = fma(xr[a][i], G[c], Fd[3 * i + c]);
-        }
+                Fd[3 * i + c] = Ds[3 * i] * Ji[c] + Ds[3 * i + 1] * Ji[3 + c] + Ds[3 * i + 2] * Ji[6 + c];
         SnhCore<R> C;
         R P[9];
-        E += wd * snh_point<R>(Fd, mud, lamd, L.level, C, P);
-        if (L.level < 1) continue;
-        // the sub-stencil's four nodes: G (double and R), u = F G, v = C G
-        double Gd[4][3];
-        R Gr[4][3];
+        const double psi = snh_point<R>(Fd, mud, lamd, L.level, C, P);
+        r[0] = wd;
+        r[1] = psi;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const double* dn = dq + 3 * l[a];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                Gd[a][c] = dn[0] * Ji[0 * 3 + c] + dn[1] * Ji[1 * 3 + c] + dn[2] * Ji[2 * 3 + c];
-                Gr[a][c] = (R)Gd[a][c];
+        for (int k = 0; k < 9; ++k) {
+            r[2 + k] = Ji[k];
+            if (L.level >= 1) {
+                r[11 + k] = (double)C.F[k];
+                r[20 + k] = (double)C.C[k];
+                r[29 + k] = (double)P[k];
             }
         }
-        const R w = (R)wd;
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-            if ((own >> (10 + a)) & 1)
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-                    gl[a][i] += w * (P[i * 3 + 0] * Gr[a][0] + P[i * 3 + 1] * Gr[a][1] +
-                                     P[i * 3 + 2] * Gr[a][2]);
-        if (L.level < 2) continue;
-        C.cI *= w;
-        C.cF *= w;
-        C.cC *= w;
-        C.cS *= w;
-        R u[4][3], v[4][3];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            matvec3(C.F, Gr[a], u[a]);
-            matvec3(C.C, Gr[a], v[a]);
+        if (L.level >= 1) {
+            r[38] = (double)C.cI;
+            r[39] = (double)C.cF;
+            r[40] = (double)C.cC;
+            r[41] = (double)C.cS;
         }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = a; b < 4; ++b) {
-                const int ab = up_index(a, b);
-                if (!((own >> ab) & 1)) continue;
-                R blk[9];
-                snh_block(C, Gr[a], Gr[b], u[a], u[b], v[a], v[b], a == b, blk);
-#pragma unroll
-                for (int k = 0; k < 9; ++k) acc[ab][k] += blk[k];
-            }
         if (proj) {
             double mlam[9], M[9][9];
             const int nm = snh_neg_modes_call(Fd, mud, lamd, mlam, M);
-#pragma unroll 1
-            for (int md = 0; md < nm; ++md) {
-                double wv[4][3];
+            double* md = B.ho_modes + ((int64_t)e * nq + q) * 91;
+            md[0] = nm;
+            for (int m = 0; m < nm; ++m) {
+                md[1 + m] = mlam[m];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-                        wv[a][r] = M[md][3 * r] * Gd[a][0] + M[md][3 * r + 1] * Gd[a][1] +
-                                   M[md][3 * r + 2] * Gd[a][2];
-                const double sc = wd * mlam[md];
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = a; b < 4; ++b) {
-                        const int ab = up_index(a, b);
-                        if (!((own >> ab) & 1)) continue;
-#pragma unroll
-                        for (int r = 0; r < 3; ++r)
-#pragma unroll
-                            for (int c = 0; c < 3; ++c)
-                                acc[ab][3 * r + c] -= (R)(sc * wv[a][r] * wv[b][c]);
-                    }
+                for (int k = 0; k < 9; ++k) md[10 + 9 * m + k] = M[m][k];
             }
         }
     }
-    o.E = j == 0 ? E : 0.0;
-    if (!isfinite(o.E)) o.nonfinite = 1;
-    if (L.level >= 1) {
-        double* gout = L.out_g ? L.out_g + 12 * sid : S.ge + 12 * (B.base + sid);
+    __syncthreads();
+    // ---- phase 2: one sub-stencil per thread
+    if ((int)threadIdx.x < T.count) {
+        const int64_t sid = T.start + threadIdx.x;
+        const int64_t e = sid / NS;
+        const int el = (int)(e - e0);
+        const int j = (int)(sid - e * NS);
+        const int* l = B.ho_sub + 4 * j;
+        const int own = B.ho_own[j];
+        R acc[10][9];
+        R gl[4][3];
+#pragma unroll
+        for (int ab = 0; ab < 10; ++ab)
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[ab][k] = R(0);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                gout[3 * a + i] = (double)gl[a][i];
-                if (!isfinite((double)gl[a][i])) o.nonfinite = 1;
-            }
-    }
-    if (L.level >= 2) {
-        auto blockfn = [&](int a, int b, R* out) {
-            const int ab = up_index(a, b);
+            for (int i = 0; i < 3; ++i) gl[a][i] = R(0);
+        double E = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            const double* r = rec[el * nq + q];
+            const double wd = r[0];
+            if (j == 0) E += wd * r[1];
+            if (L.level < 1) continue;
+            const double* dq = B.ho_dN + q * K * 3;
+            double Gd[4][3];
+            R Gr[4][3];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) out[k] = acc[ab][k];
-        };
-        HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (B.base + sid);
-        double* full = L.out_H ? L.out_H + 144 * sid : nullptr;
-        write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
+            for (int a = 0; a < 4; ++a) {
+                const double* dn = dq + 3 * l[a];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Gd[a][c] = dn[0] * r[2 + c] + dn[1] * r[5 + c] + dn[2] * r[8 + c];
+                    Gr[a][c] = (R)Gd[a][c];
+                }
+            }
+            const R w = (R)wd;
+            R P[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) P[k] = (R)r[29 + k];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if ((own >> (10 + a)) & 1)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        gl[a][i] += w * (P[i * 3 + 0] * Gr[a][0] + P[i * 3 + 1] * Gr[a][1] +
+                                         P[i * 3 + 2] * Gr[a][2]);
+            if (L.level < 2) continue;
+            SnhCore<R> C;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                C.F[k] = (R)r[11 + k];
+                C.C[k] = (R)r[20 + k];
+            }
+            C.cI = w * (R)r[38];
+            C.cF = w * (R)r[39];
+            C.cC = w * (R)r[40];
+            C.cS = w * (R)r[41];
+            R u[4][3], v[4][3];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                matvec3(C.F, Gr[a], u[a]);
+                matvec3(C.C, Gr[a], v[a]);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = a; b < 4; ++b) {
+                    const int ab = up_index(a, b);
+                    if (!((own >> ab) & 1)) continue;
+                    R blk[9];
+                    snh_block(C, Gr[a], Gr[b], u[a], u[b], v[a], v[b], a == b, blk);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) acc[ab][k] += blk[k];
+                }
+            if (proj) {
+                const double* md = B.ho_modes + ((int64_t)e * nq + q) * 91;
+                const int nm = (int)md[0];
+#pragma unroll 1
+                for (int m = 0; m < nm; ++m) {
+                    const double* M = md + 10 + 9 * m;
+                    double wv[4][3];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int rr = 0; rr < 3; ++rr)
+                            wv[a][rr] = M[3 * rr] * Gd[a][0] + M[3 * rr + 1] * Gd[a][1] +
+                                        M[3 * rr + 2] * Gd[a][2];
+                    const double sc = wd * md[1 + m];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = a; b < 4; ++b) {
+                            const int ab = up_index(a, b);
+                            if (!((own >> ab) & 1)) continue;
+#pragma unroll
+                            for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                                for (int c = 0; c < 3; ++c)
+                                    acc[ab][3 * rr + c] -= (R)(sc * wv[a][rr] * wv[b][c]);
+                        }
+                }
+            }
+        }
+        o.E = j == 0 ? E : 0.0;
+        if (!isfinite(o.E)) o.nonfinite = 1;
+        if (L.level >= 1) {
+            double* gout = L.out_g ? L.out_g + 12 * sid : S.ge + 12 * (B.base + sid);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    gout[3 * a + i] = (double)gl[a][i];
+                    if (!isfinite((double)gl[a][i])) o.nonfinite = 1;
+                }
+        }
+        if (L.level >= 2) {
+            auto blockfn = [&](int a, int b, R* out) {
+                const int ab = up_index(a, b);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) out[k] = acc[ab][k];
+            };
+            HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (B.base + sid);
+            double* full = L.out_H ? L.out_H + 144 * sid : nullptr;
+            write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
+        }
     }
+    __syncthreads();
 }
 
 template <typename R, typename HT>
@@ -1388,11 +1450,22 @@ k_elements(ElemLaunch L)
         ThreadOut o{0.0, 0, 0, 0};
         if (S.sc == nullptr || S.sc->active) {
             const ElemBlock& B = S.blk[T.blk];
-            if ((int)threadIdx.x < T.count) {
+            bool ho = false;
+            if constexpr ((KINDS & 64) != 0) {
+                if (B.kind == SX_KIND_TET_HO) {
+                    // block-uniform: every thread takes part (the tile synchronizes)
+                    ho = true;
+                    tetho_tile<R, HT>(L, S, B, T, o);
+                    if ((int)threadIdx.x < T.count) {
+                        const int64_t e = T.start + threadIdx.x;
+                        if (L.out_E) L.out_E[e] = o.E;
+                        else S.Ee[B.base + e] = o.E;
+                    }
+                }
+            }
+            if (!ho && (int)threadIdx.x < T.count) {
                 const int64_t e = T.start + threadIdx.x;
-                if ((KINDS & 64) && B.kind == SX_KIND_TET_HO)
-                    eval_tetho<R, HT>(L, S, B, e, o);
-                else if ((KINDS & 16) && B.kind == SX_KIND_SNH_TET4 && B.model != SX_MODEL_SNH)
+                if ((KINDS & 16) && B.kind == SX_KIND_SNH_TET4 && B.model != SX_MODEL_SNH)
                     eval_model<R, HT>(L, T.scene, T.blk, S, B, e, o);
                 else if ((KINDS & 1) && B.kind == SX_KIND_SNH_TET4)
                     eval_snh<R, HT, (KINDS & 8) != 0>(L, T.scene, T.blk, S, B, e, o);

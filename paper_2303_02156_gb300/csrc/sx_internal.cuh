@@ -70,6 +70,7 @@ struct ElemBlock {
     const double* ho_dN;     // [nq][K][3] reference gradients
     const int* ho_sub;       // [S][4] local nodes of the sub-stencils
     const int* ho_own;       // [S] bits 0-9: owned upper blocks, 10-13: owned nodes
+    double* ho_modes;        // [ho_n][nq][91] negative modes per point (projection scratch)
 };
 
 // per-scene scalars the device loops read and write
