@@ -179,3 +179,84 @@ def test_high_order_rejects_bad_input(ctx):
                           1000.0, rule.ctypes.data, 0, None, C.byref(eid))
     assert rc == sx.SX_EINVAL
     s.close()
+
+
+@pytest.mark.gpu
+def test_every_kind_in_one_scene_composes(ctx):
+    """One scene holding a quadratic-tet box, a co-rotational linear box and
+    a sheet with barrier + friction pairs (the every-kind instantiation):
+    its assembled energy, gradient and BSR values equal the sum of the three
+    parts evaluated as separate scenes (each part is checked against the
+    oracle elsewhere); and a batched Newton step of it equals its single
+    step bit for bit."""
+    from paper_2303_02156_gb300.scene import Scene
+    ho = scenes.kuhn_box_ho(2, 2, 2, 2, h=0.05, seed=11)
+    lin = scenes.kuhn_box(2, 2, 2, h=0.05, seed=12, origin=(0.3, 0.0, 0.0))
+    sh = scenes.shell_sheet(6, length=0.1, z0=0.3, noise=0.05, seed=13)
+    n1, n2, n3 = ho["X"].shape[0], lin["X"].shape[0], sh["X"].shape[0]
+    bp = scenes.barrier_pairs(sh["x"], sh["tris"], 40, 1e-4, 9e-4, seed=14,
+                              tri_node_offset=n1 + n2, point_node_offset=n1 + n2 + n3)
+    X = np.vstack([ho["X"], lin["X"], sh["X"], bp["points"]])
+    N = X.shape[0]
+    x = scenes.jitter_state(X, 2e-4, seed=15)
+    x[n1 + n2:n1 + n2 + n3] = sh["x"]
+    x[n1 + n2 + n3:] = bp["points"]
+    T1, T2 = ho["tets"].shape[0], lin["tets"].shape[0]
+    hinge = sh["hinges"] + n1 + n2
+
+    def build(parts):
+        s = Scene(ctx, X)
+        if "ho" in parts:
+            s.add_tet_ho(2, ho["tets"], np.full(T1, 2e5), np.full(T1, 0.35), 1000.0,
+                         scenes.tet_rule_4point())
+        if "lin" in parts:
+            s.add_tet(sx.SX_MODEL_COROT, lin["tets"] + n1, np.full(T2, 1e5), np.full(T2, 0.3),
+                      1000.0)
+        if "sheet" in parts:
+            s.add_hinge(hinge, sh["q"], sh["c"], 1e-3)
+            s.add_barrier(bp["pairs"], 1e-3, 1e4)
+            s.add_friction(bp["pairs"], 0.3, 1e-3, 1e-3, 1e4)
+            s.add_node_mass(np.concatenate([np.zeros(n1 + n2), np.full(N - n1 - n2, 1e-4)]))
+        s.finalize()
+        s.set_state(x=x)
+        s.update_friction(0.01)
+        return s
+
+    full = build(("ho", "lin", "sheet"))
+    Ef = full.eval(sx.SX_EGH, True, sx.SX_FP64)
+    rp, col, vf = full.bsr()
+    gf = full.grad()
+    Es, gs = 0.0, np.zeros(3 * N)
+    Hs = np.zeros((3 * N, 3 * N))
+    for part in ("ho", "lin", "sheet"):
+        s = build((part,))
+        Es += s.eval(sx.SX_EGH, True, sx.SX_FP64)
+        gs += s.grad()
+        r2, c2, v2 = s.bsr()
+        Hs += _dense_bsr(r2, c2, v2, N)
+        s.close()
+    Hf = _dense_bsr(rp, col, vf, N)
+    assert abs(Ef - Es) <= 1e-12 * abs(Es)
+    assert np.linalg.norm(gf - gs) <= 1e-12 * np.linalg.norm(gs)
+    assert np.linalg.norm(Hf - Hs) <= 1e-12 * np.linalg.norm(Hs)
+    # batched Newton step (with a second scene) equals the single step
+    full.set_pinned(np.concatenate([ho["pinned"], lin["pinned"] + n1,
+                                    np.arange(n1 + n2, n1 + n2 + n3)]).astype(np.int32))
+    full.set_gravity((0.0, 0.0, -9.81))
+    other = build(("lin",))
+    other.set_gravity((0.0, 0.0, -9.81))
+    v0 = np.zeros_like(x)
+    v0[n1 + n2 + n3:, 0] = 0.05
+    full.set_state(x=x, v=v0)
+    other.set_state(x=x, v=np.zeros_like(x))
+    arr = (C.c_void_p * 2)(full.h.value, other.h.value)
+    reps = (sx.sx_step_report * 2)()
+    o = sx.newton_opts(newton_tol=1e-8, pcg_tol=1e-10)
+    assert sx.sx_newton_step_batch(ctx.h, arr, 2, 0.01, C.byref(o), reps, None) == sx.SX_OK, \
+        [reps[i].status for i in range(2)]
+    xb = full.get_state()[0]
+    full.set_state(x=x, v=v0)
+    rc, r = full.newton_step(0.01, newton_tol=1e-8, pcg_tol=1e-10)
+    assert rc == sx.SX_OK, r
+    assert np.array_equal(full.get_state()[0], xb)
+    full.close(); other.close()
