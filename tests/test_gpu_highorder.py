@@ -244,6 +244,8 @@ def test_every_kind_in_one_scene_composes(ctx):
                                     np.arange(n1 + n2, n1 + n2 + n3)]).astype(np.int32))
     full.set_gravity((0.0, 0.0, -9.81))
     other = build(("lin",))
+    # its other nodes have neither mass nor elements: pinned
+    other.set_pinned(np.concatenate([np.arange(n1), np.arange(n1 + n2, N)]).astype(np.int32))
     other.set_gravity((0.0, 0.0, -9.81))
     v0 = np.zeros_like(x)
     v0[n1 + n2 + n3:, 0] = 0.05
