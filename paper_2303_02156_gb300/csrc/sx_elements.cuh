@@ -278,7 +278,7 @@ __device__ __forceinline__ void write_blocks(BlockFn blockfn, HT* staged, double
             blockfn(a, b, blk);
             bool bad = false;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) bad |= !isfinite((double)blk[k]);
+            for (int k = 0; k < 9; ++k) bad |= nonfinite_bits(blk[k]);
             if (bad) *nonfinite = 1;
             if (staged) {
                 HT* dst = staged + 9 * up_index(a, b);
@@ -573,14 +573,14 @@ __device__ void eval_snh(const ElemLaunch& L, int scene, int blk, const SceneDev
     SnhCore<R> C;
     R g[12];
     o.E = snh_core<R>(xg, Dinv, B.V[e], B.mu[e], B.lam[e], L.level, C, g);
-    if (!isfinite(o.E)) o.nonfinite = 1;
+    if (nonfinite_bits(o.E)) o.nonfinite = 1;
     const int64_t gid = B.base + e;
     if (L.level >= 1) {
         double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             gout[k] = (double)g[k];
-            if (!isfinite((double)g[k])) o.nonfinite = 1;
+            if (nonfinite_bits(g[k])) o.nonfinite = 1;
         }
     }
     if (L.level >= 2) {
@@ -855,14 +855,14 @@ __device__ __noinline__ void eval_model(const ElemLaunch& L, int scene, int blk,
     int bad = 0;
     o.E = model_core<R>(model, xg, Dinv, Rl, B.V[e], B.mu[e], B.lam[e], L.level, C, T, g, bad);
     if (bad) o.bad = 1;
-    if (!isfinite(o.E)) o.nonfinite = 1;
+    if (nonfinite_bits(o.E)) o.nonfinite = 1;
     const int64_t gid = B.base + e;
     if (L.level >= 1) {
         double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             gout[k] = bad ? 0.0 : (double)g[k];
-            if (!bad && !isfinite((double)g[k])) o.nonfinite = 1;
+            if (!bad && nonfinite_bits(g[k])) o.nonfinite = 1;
         }
     }
     if (L.level >= 2) {
@@ -966,7 +966,7 @@ __device__ __noinline__ void eval_friction(const ElemLaunch& L, const SceneDev& 
         a2 = -1.0 / (s * s * s);
     }
     o.E = kf * f0;
-    if (!isfinite(o.E)) o.nonfinite = 1;
+    if (nonfinite_bits(o.E)) o.nonfinite = 1;
     const int64_t gid = B.base + e;
     const R c[4] = {R(1), (R)(-lag[0]), (R)(-lag[1]), (R)(-lag[2])};
     R T[2][3];
@@ -985,7 +985,7 @@ __device__ __noinline__ void eval_friction(const ElemLaunch& L, const SceneDev& 
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 gout[3 * a + i] = (double)(c[a] * G3[i]);
-                if (!isfinite(gout[3 * a + i])) o.nonfinite = 1;
+                if (nonfinite_bits(gout[3 * a + i])) o.nonfinite = 1;
             }
     }
     if (L.level >= 2) {
@@ -1275,7 +1275,7 @@ __device__ void tetho_tile(const ElemLaunch& L, const SceneDev& S, const ElemBlo
             }
         }
         o.E = j == 0 ? E : 0.0;
-        if (!isfinite(o.E)) o.nonfinite = 1;
+        if (nonfinite_bits(o.E)) o.nonfinite = 1;
         if (L.level >= 1) {
             double* gout = L.out_g ? L.out_g + 12 * sid : S.ge + 12 * (B.base + sid);
 #pragma unroll
@@ -1283,7 +1283,7 @@ __device__ void tetho_tile(const ElemLaunch& L, const SceneDev& S, const ElemBlo
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     gout[3 * a + i] = (double)gl[a][i];
-                    if (!isfinite((double)gl[a][i])) o.nonfinite = 1;
+                    if (nonfinite_bits(gl[a][i])) o.nonfinite = 1;
                 }
         }
         if (L.level >= 2) {
@@ -1324,7 +1324,7 @@ __device__ void eval_hinge(const ElemLaunch& L, const SceneDev& S, const ElemBlo
         for (int i = 0; i < 3; ++i) sd[i] += qd[a] * (S.x[3 * (int64_t)nid[a] + i] - x0[i]);
     const double kcd = B.kb * B.c[e];
     o.E = 0.5 * kcd * (sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
-    if (!isfinite(o.E)) o.nonfinite = 1;
+    if (nonfinite_bits(o.E)) o.nonfinite = 1;
     const R kc = (R)kcd;
     const R s[3] = {(R)sd[0], (R)sd[1], (R)sd[2]};
     R q[4];
@@ -1378,7 +1378,7 @@ __device__ void eval_barrier(const ElemLaunch& L, int scene, int blk, const Scen
     const int64_t gid = B.base + e;
     if (st < 0) o.bad = 1;
     o.E = (st == 1) ? Ed : 0.0;
-    if (!isfinite(o.E)) o.nonfinite = 1;
+    if (nonfinite_bits(o.E)) o.nonfinite = 1;
     if (L.level >= 1) {
         double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
 #pragma unroll

@@ -33,6 +33,18 @@
 namespace sx {
 
 // upper 3x3 blocks of a 4-node stencil Hessian, in staging order
+// non-finite test on the exponent bits: an integer-pipe operation (a
+// floating compare would take an issue slot of the FP64 pipe, and a float
+// value would first be converted there)
+__device__ __forceinline__ bool nonfinite_bits(double x)
+{
+    return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000;
+}
+__device__ __forceinline__ bool nonfinite_bits(float x)
+{
+    return (__float_as_int(x) & 0x7f800000) == 0x7f800000;
+}
+
 __host__ __device__ constexpr int up_index(int a, int b)
 {
     // (0,0)=0 (0,1)=1 (0,2)=2 (0,3)=3 (1,1)=4 (1,2)=5 (1,3)=6 (2,2)=7 (2,3)=8 (3,3)=9
