@@ -885,6 +885,20 @@ def main():
                "sample": "first %d tets (two bottom layers) of the cube, %d passes in %.1f s: "
                          "E+g+H, 12x12 cyclic-Jacobi clamp, ordered BSR assembly; host %s"
                          % (n_tets, reps, dt, cpu_model())}
+        # the same on one core (beside the paper's single-element timings),
+        # on the first layer only
+        from oracle import oracle as orc
+        nth = orc.num_threads()
+        orc.set_num_threads(1)
+        try:
+            n1 = n_tets // 2
+            sc1, x1 = oracle_sample(m, E, nu, x, n1)
+            v1, reps1, dt1, _ = time_oracle(sc1, x1, n1, min(2.0, args.cpu_seconds))
+        finally:
+            orc.set_num_threads(nth)
+        cpu["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
+                                "us_per_element": 1e6 / v1,
+                                "sample": "first %d tets, %d passes in %.1f s" % (n1, reps1, dt1)}
 
     if rank == 0:
         line = {
