@@ -71,7 +71,6 @@ def test_lagged_rotations_parity(ctx, model):
     m, E, nu, inp, mass, x, xt = _case(model)
     s, eid = _gpu(ctx, model, m, E, nu, x, xt)
     if model not in LAGGED:
-        n = C.c_int64()
         buf = np.empty(9)
         assert sx.sx_get_rotations(s.h, eid, buf.ctypes.data, None) == sx.SX_EINVAL
         s.close()
@@ -125,8 +124,10 @@ def test_model_strong_deformation_projection(ctx, model):
     out = s.eval_elements(eid, project=True, precision=sx.SX_FP64)
     Ee, ge, He, bad = orc.tet_batch(model, x, m["tets"], inp["Dminv"], inp["V"], inp["mu"],
                                     inp["lam"], R, 2, True)
+    assert bad == 0
     scale = inp["V"] * inp["mu"]
-    worst = max(_relerr(out["H"][e], He[e], scale[e]) for e in range(Ee.size))
+    worst = max(max(_relerr(out["H"][e], He[e], scale[e]), _relerr(out["g"][e], ge[e], scale[e]))
+                for e in range(Ee.size))
     assert worst <= 1e-10, worst
     s.close()
 
