@@ -308,14 +308,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
 #ifndef SX_SPMV_STAGE
 #define SX_SPMV_STAGE 1
 #endif
-static constexpr int kSpmvRows = 48;                 // block rows per tile
+#ifndef SX_SPMV_ROWS
+#define SX_SPMV_ROWS 48
+#endif
+static constexpr int kSpmvRows = SX_SPMV_ROWS;        // block rows per tile
 static constexpr int kSpmvThreads = 3 * kSpmvRows;    // one thread per output component
-static constexpr int kSpmvSmemCols = 4 * 1024;        // bytes of staged column ids
-// bytes of staged values: 48 rows of up to ~20 blocks, in the value type
+// bytes of staged column ids and values: up to ~20 blocks per row (values in
+// the value type), 1 KB granules; rows with more fall back to direct loads
+static constexpr int kSpmvSmemCols = ((kSpmvRows * 4 * 1024 / 48) + 1023) / 1024 * 1024;
 template <typename VT>
 __host__ __device__ constexpr int spmv_smem_vals()
 {
-    return sizeof(VT) == 8 ? 56 * 1024 : 28 * 1024;
+    return ((kSpmvRows * (sizeof(VT) == 8 ? 56 : 28) * 1024 / 48) + 1023) / 1024 * 1024;
 }
 __device__ __forceinline__ double fma_vt(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_vt(float a, float b, float c) { return fmaf(a, b, c); }
