@@ -308,8 +308,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
 #ifndef SX_SPMV_STAGE
 #define SX_SPMV_STAGE 1
 #endif
+// 32 rows: 96 threads, three full warps (48 rows left half a warp idle);
+// measured on the 64^3 cube, FP64 SpMV per call 134 us at 32 rows against
+// 146 (48), 154 (64) and 165 (16); FP32 within 2% across 32-64
 #ifndef SX_SPMV_ROWS
-#define SX_SPMV_ROWS 48
+#define SX_SPMV_ROWS 32
 #endif
 static constexpr int kSpmvRows = SX_SPMV_ROWS;        // block rows per tile
 static constexpr int kSpmvThreads = 3 * kSpmvRows;    // one thread per output component
