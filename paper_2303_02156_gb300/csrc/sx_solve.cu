@@ -310,7 +310,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
 #endif
 // 32 rows: 96 threads, three full warps (48 rows left half a warp idle);
 // measured on the 64^3 cube, FP64 SpMV per call 134 us at 32 rows against
-// 146 (48), 154 (64) and 165 (16); FP32 within 2% across 32-64
+// 146 (48), 154 (64) and 165 (16); FP32 within 2% across 32-64. A form
+// without staging (a half-warp per block row reading its blocks straight
+// from global memory) measured 268 us: each lane's nine loads are 72 B apart
+// from its neighbours', many sectors per load instruction.
 #ifndef SX_SPMV_ROWS
 #define SX_SPMV_ROWS 32
 #endif
@@ -448,84 +451,7 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
     }
 }
 
-// ------------------------------------------------------------------ SpMV, vector form
-// One half-warp per block row: lane l takes the row's blocks l, l + 16, ...
-// (a row's blocks are contiguous, so the half-warp reads its values
-// coalesced straight from global memory; no staging, no shared-memory
-// limit on the resident blocks), three chains of fused multiply-adds per
-// lane, then a fixed-order shuffle tree over the 16 lanes: deterministic.
-#ifndef SX_SPMV_VEC
-#define SX_SPMV_VEC 0
-#endif
-static constexpr int kVecLanes = 16;         // lanes per block row
-static constexpr int kVecRowsPerTile = 16;   // 256 threads per tile
-
-template <typename VT>
-__global__ void __launch_bounds__(kVecLanes * kVecRowsPerTile)
-k_spmv_vec(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part,
-           const int* tbeg, const int* tend)
-{
-    constexpr int NT = kVecLanes * kVecRowsPerTile;
-    __shared__ double sh[1][NT];
-    const int ti = blockIdx.x;
-    const Tile T = tiles[ti];
-    const SceneDev& S = scenes[T.scene];
-    if (!(scene_live(S) && !S.sc->pcg_done)) return;   // the same for every tile of the scene
-    const int lr = threadIdx.x / kVecLanes, lane = threadIdx.x % kVecLanes;
-    const bool row_ok = lr < T.count;
-    const int64_t r = T.start + lr;
-    const double* pn = par ? S.p0 : S.p1;
-    const bool pin = row_ok && S.pinned[r];
-    VT a0 = VT(0), a1 = VT(0), a2 = VT(0);
-    if (row_ok && !pin) {
-        const VT* vals = (sizeof(VT) == 8) ? (const VT*)S.vals64 : (const VT*)S.vals32;
-        // the gathered direction: p itself (FP64) or its float copy (FP32);
-        // p is zero on pinned DOFs, so their columns need no test
-        const VT* pg = (sizeof(VT) == 8) ? (const VT*)pn : (const VT*)S.p32;
-        const int b = S.row_ptr[r], e = S.row_ptr[r + 1];
-        for (int k = b + lane; k < e; k += kVecLanes) {
-            const int64_t c = S.col[k];
-            const VT* B = vals + 9 * (int64_t)k;
-            const VT p0 = pg[3 * c], p1 = pg[3 * c + 1], p2 = pg[3 * c + 2];
-            a0 = fma_vt(B[2], p2, fma_vt(B[1], p1, fma_vt(B[0], p0, a0)));
-            a1 = fma_vt(B[5], p2, fma_vt(B[4], p1, fma_vt(B[3], p0, a1)));
-            a2 = fma_vt(B[8], p2, fma_vt(B[7], p1, fma_vt(B[6], p0, a2)));
-        }
-    }
-#pragma unroll
-    for (int off = kVecLanes / 2; off > 0; off >>= 1) {
-        a0 += __shfl_down_sync(0xffffffffu, a0, off, kVecLanes);
-        a1 += __shfl_down_sync(0xffffffffu, a1, off, kVecLanes);
-        a2 += __shfl_down_sync(0xffffffffu, a2, off, kVecLanes);
-    }
-    double v = 0.0;
-    if (row_ok && lane == 0) {
-        const double q[3] = {pin ? pn[3 * r] : (double)a0, pin ? pn[3 * r + 1] : (double)a1,
-                             pin ? pn[3 * r + 2] : (double)a2};
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            S.q[3 * r + i] = q[i];
-            v = fma(pn[3 * r + i], q[i], v);
-        }
-    }
-    const double vv[1] = {v};
-    double pq[1];
-    if (last_tile_sums<1, NT>(vv, sh, part, ti, &S.sc->cnt_spmv, tbeg[T.scene], tend[T.scene],
-                              pq) &&
-        threadIdx.x == 0) {
-        SceneScal* sc = S.sc;
-        sc->pq = pq[0];
-        if (!(pq[0] > 0.0) || !isfinite(pq[0])) {   // not a descent system: stop
-            sc->pcg_done = 1;
-            sc->pcg_status = 1;
-            sc->pcg_alpha = 0.0;
-        } else {
-            sc->pcg_alpha = sc->rz / pq[0];
-        }
-    }
-}
-
-int spmv_rows_per_tile() { return SX_SPMV_VEC ? kVecRowsPerTile : kSpmvRows; }
+int spmv_rows_per_tile() { return kSpmvRows; }
 
 void prepare_spmv()
 {
@@ -551,16 +477,6 @@ cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int nt
     if (!ntiles) return cudaSuccess;
     const int smem64 = spmv_smem_vals<double>() + kSpmvSmemCols;
     const int smem32 = spmv_smem_vals<float>() + kSpmvSmemCols;
-    if (SX_SPMV_VEC) {
-        constexpr int NT = kVecLanes * kVecRowsPerTile;
-        if (precision == SX_FP32)
-            k_spmv_vec<float><<<ntiles, NT, 0, s>>>(scenes, row_tiles, ntiles, parity, part, tbeg,
-                                                    tend);
-        else
-            k_spmv_vec<double><<<ntiles, NT, 0, s>>>(scenes, row_tiles, ntiles, parity, part, tbeg,
-                                                     tend);
-        return cudaGetLastError();
-    }
     prepare_spmv();
     if (precision == SX_FP32)
         k_spmv<float><<<ntiles, kSpmvThreads, smem32, s>>>(scenes, row_tiles, ntiles, parity, part,
@@ -743,13 +659,10 @@ cudaError_t add_pcg_chunk_nodes(cudaGraph_t graph, const PcgChunkArgs& a)
     NodeChain c{graph};
     const bool f32 = a.precision == SX_FP32;
     const void* pdir = f32 ? (const void*)k_pcg_pdir<true> : (const void*)k_pcg_pdir<false>;
-    const void* spmv = SX_SPMV_VEC
-                           ? (f32 ? (const void*)k_spmv_vec<float> : (const void*)k_spmv_vec<double>)
-                           : (f32 ? (const void*)k_spmv<float> : (const void*)k_spmv<double>);
-    const unsigned smem = SX_SPMV_VEC ? 0u
-                                      : (unsigned)(kSpmvSmemCols + (f32 ? spmv_smem_vals<float>()
-                                                                        : spmv_smem_vals<double>()));
-    const unsigned spmv_threads = SX_SPMV_VEC ? kVecLanes * kVecRowsPerTile : kSpmvThreads;
+    const void* spmv = f32 ? (const void*)k_spmv<float> : (const void*)k_spmv<double>;
+    const unsigned smem = (unsigned)(kSpmvSmemCols + (f32 ? spmv_smem_vals<float>()
+                                                          : spmv_smem_vals<double>()));
+    const unsigned spmv_threads = kSpmvThreads;
     // argument values must outlive each cudaGraphAddKernelNode call only
     const SceneDev* scenes = a.scenes;
     const Tile* nt = a.node_tiles;
