@@ -786,7 +786,7 @@ def main():
     fpe = fpe or 6946.0
     achieved = fpe * clamped / t_clamp / 1e12 if t_clamp > 0 else None
     scope = CLAMP_FLOPS_PER_ELEMENT * clamped / t_clamp / 1e12 if t_clamp > 0 else None
-    roofline = {"bound": "alu", "kernel": "k_clamp (FP64 9x9 eigen-clamp)",
+    roofline = {"bound": "alu", "kernel": "k_clamp_float + k_clamp_double (FP64 9x9 eigen-clamp of the queued stencils)",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                 "traffic": (tpe * clamped) if (tpe and fresh) else None,
