@@ -317,16 +317,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
 #ifndef SX_SPMV_ROWS
 #define SX_SPMV_ROWS 32
 #endif
-// threads per output component: each takes every SX_SPMV_SPLIT-th block of
-// the row, the partial sums are added in a fixed order (more warps resident
-// for the same staged tile)
-#ifndef SX_SPMV_SPLIT
-#define SX_SPMV_SPLIT 1
-#endif
 static constexpr int kSpmvRows = SX_SPMV_ROWS;        // block rows per tile
-static constexpr int kSpmvSplit = SX_SPMV_SPLIT;
-static constexpr int kSpmvThreads = 3 * kSpmvSplit * kSpmvRows;
-static_assert(kSpmvThreads <= 256, "the tile reductions take at most 256 threads");
+static constexpr int kSpmvThreads = 3 * kSpmvRows;    // one thread per output component
 // bytes of staged column ids and values: up to ~20 blocks per row (values in
 // the value type), 1 KB granules; rows with more fall back to direct loads
 static constexpr int kSpmvSmemCols = ((kSpmvRows * 4 * 1024 / 48) + 1023) / 1024 * 1024;
@@ -405,15 +397,12 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
         }
     }
     double v = 0.0;
-    constexpr int TPR = 3 * kSpmvSplit;   // threads per block row
-    const int lr = threadIdx.x / TPR, w = threadIdx.x - TPR * lr;
-    const int ci = w % 3, hs = w / 3;     // component, and which interleaved share of blocks
-    const double* pn = par ? S.p0 : S.p1;
-    double q = 0.0;
-    const bool pin = live && lr < T.count && S.pinned[r0 + lr];
+    const int lr = threadIdx.x / 3, ci = threadIdx.x - 3 * lr;
     if (live && lr < T.count) {
         const int64_t r = r0 + lr;
-        if (pin) {
+        const double* pn = par ? S.p0 : S.p1;
+        double q;
+        if (S.pinned[r]) {
             q = pn[3 * r + ci];
         } else {
             VT acc = VT(0);
@@ -427,7 +416,7 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
             // p is exactly zero on pinned DOFs (their r, z and p stay 0), so
             // pinned columns drop out without a test in the loop
 #pragma unroll 4
-            for (int k = hs; k < e - b; k += kSpmvSplit) {
+            for (int k = 0; k < e - b; ++k) {
                 const int c = cs[k];
                 const VT* B = vs + 9 * k + 3 * ci;
                 // a chain of three fused multiply-adds: the minimum FP64
@@ -438,17 +427,6 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
             }
             q = (double)acc;
         }
-    }
-    if (kSpmvSplit > 1) {
-        // the shares of a component, added in share order by its first thread
-        __shared__ double sp[kSpmvThreads];
-        sp[threadIdx.x] = q;
-        __syncthreads();
-        if (hs == 0 && !pin)
-            for (int h = 1; h < kSpmvSplit; ++h) q += sp[threadIdx.x + 3 * h];
-    }
-    if (live && lr < T.count && hs == 0) {
-        const int64_t r = r0 + lr;
         S.q[3 * r + ci] = q;
         v = pn[3 * r + ci] * q;
     }
