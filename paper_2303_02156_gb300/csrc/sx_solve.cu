@@ -313,7 +313,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
 // 146 (48), 154 (64) and 165 (16); FP32 within 2% across 32-64. A form
 // without staging (a half-warp per block row reading its blocks straight
 // from global memory) measured 268 us: each lane's nine loads are 72 B apart
-// from its neighbours', many sectors per load instruction.
+// from its neighbours', many sectors per load instruction. Splitting each
+// output component over two threads (interleaved blocks, more warps for the
+// same staged tile) made the 64^3 Newton step slower (224 vs 206 ms).
 #ifndef SX_SPMV_ROWS
 #define SX_SPMV_ROWS 32
 #endif
