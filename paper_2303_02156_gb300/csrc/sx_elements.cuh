@@ -1170,12 +1170,14 @@ __device__ void tetho_tile(const ElemLaunch& L, const SceneDev& S, const ElemBlo
         }
     }
     __syncthreads();
-    // ---- phase 2: one sub-stencil per thread
+    // ---- phase 2: one sub-stencil per thread; consecutive threads take the
+    // same sub-stencil index j of different elements, so the lanes of a warp
+    // share j's ownership mask and local nodes (few divergent paths)
     if ((int)threadIdx.x < T.count) {
-        const int64_t sid = T.start + threadIdx.x;
-        const int64_t e = sid / NS;
-        const int el = (int)(e - e0);
-        const int j = (int)(sid - e * NS);
+        const int el = (int)threadIdx.x % nel;
+        const int j = (int)threadIdx.x / nel;
+        const int64_t e = e0 + el;
+        const int64_t sid = e * NS + j;
         const int* l = B.ho_sub + 4 * j;
         const int own = B.ho_own[j];
         R acc[10][9];
@@ -1276,6 +1278,8 @@ __device__ void tetho_tile(const ElemLaunch& L, const SceneDev& S, const ElemBlo
         }
         o.E = j == 0 ? E : 0.0;
         if (nonfinite_bits(o.E)) o.nonfinite = 1;
+        if (L.out_E) L.out_E[sid] = o.E;
+        else S.Ee[B.base + sid] = o.E;
         if (L.level >= 1) {
             double* gout = L.out_g ? L.out_g + 12 * sid : S.ge + 12 * (B.base + sid);
 #pragma unroll
@@ -1455,12 +1459,7 @@ k_elements(ElemLaunch L)
                 if (B.kind == SX_KIND_TET_HO) {
                     // block-uniform: every thread takes part (the tile synchronizes)
                     ho = true;
-                    tetho_tile<R, HT>(L, S, B, T, o);
-                    if ((int)threadIdx.x < T.count) {
-                        const int64_t e = T.start + threadIdx.x;
-                        if (L.out_E) L.out_E[e] = o.E;
-                        else S.Ee[B.base + e] = o.E;
-                    }
+                    tetho_tile<R, HT>(L, S, B, T, o);   // writes its sub-stencils' energies
                 }
             }
             if (!ho && (int)threadIdx.x < T.count) {
