@@ -354,8 +354,10 @@ int sx_eval_elements(sx_scene* scene, int energy_id, int project, int precision,
  * library, about 25 MB that every GPU which loads the library holds until
  * the process exits. It makes no cudaMalloc/cudaFree call and calls no
  * allocating routine.
- *  - Blocks with more than SX_NOALLOC_MAX_ELEMENTS elements are rejected
- *    with SX_EINVAL.
+ *  - Blocks with more than SX_NOALLOC_MAX_ELEMENTS elements (stencils;
+ *    sub-stencils for high-order tets) are rejected with SX_EINVAL, and so
+ *    are high-order blocks whose element-kernel tiles (whole elements, up
+ *    to 128 threads each) would exceed the static tile table of 512.
  *  - E, g, H: device outputs as in sx_eval_elements (n, n x 12,
  *    n x 144); a NULL E or g sends that output to the scene's own staging
  *    buffers instead. The call synchronizes `stream`.
