@@ -264,3 +264,68 @@ def test_every_kind_in_one_scene_composes(ctx):
     assert rc == sx.SX_OK, r
     assert np.array_equal(full.get_state()[0], xb)
     full.close(); other.close()
+
+
+@pytest.mark.gpu
+def test_empty_blocks_of_the_newer_kinds(ctx):
+    """Blocks with no element of every newer kind (another density, lagged
+    friction, high-order tets) next to a small linear block: the scene
+    evaluates and steps as if they were absent."""
+    from paper_2303_02156_gb300.scene import Scene
+    m = scenes.kuhn_box(2, 2, 2, h=0.1, seed=21)
+    T = m["tets"].shape[0]
+    E, nu = np.full(T, 1e5), np.full(T, 0.3)
+
+    def build(with_empty):
+        s = Scene(ctx, m["X"])
+        s.add_snh(m["tets"], E, nu, 1000.0)
+        if with_empty:
+            s.add_tet(sx.SX_MODEL_STVK, np.zeros((0, 4), np.int32), np.zeros(0), np.zeros(0))
+            s.add_friction(np.zeros((0, 4), np.int32), 0.3, 1e-3, 1e-3, 1e4)
+            s.add_tet_ho(2, np.zeros((0, 10), np.int32), np.zeros(0), np.zeros(0), 1000.0,
+                         scenes.tet_rule_4point())
+        s.set_pinned(m["pinned"])
+        s.set_gravity((0.0, 0.0, -9.81))
+        s.finalize()
+        s.set_state(x=scenes.jitter_state(m["X"], 0.003, seed=3))
+        return s
+
+    a, b = build(False), build(True)
+    Ea = a.eval(sx.SX_EGH, True, sx.SX_FP64)
+    Eb = b.eval(sx.SX_EGH, True, sx.SX_FP64)
+    assert Ea == Eb and np.array_equal(a.grad(), b.grad())
+    assert np.array_equal(a.bsr()[2], b.bsr()[2])
+    for s in (a, b):
+        s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+        rc, _ = s.newton_step(0.01, newton_tol=1e-8, pcg_tol=1e-10)
+        assert rc == sx.SX_OK
+    assert np.array_equal(a.get_state()[0], b.get_state()[0])
+    a.close(); b.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("order", [2, 3])
+def test_single_high_order_element(ctx, order):
+    """One element alone (a tile shorter than the others, no neighbour)."""
+    m, X, E, nu, mu, lam = _mesh(order, dims=(1, 1, 1), seed=8)
+    t = m["tets"][:1]
+    used = np.unique(t)
+    remap = -np.ones(X.shape[0], np.int64); remap[used] = np.arange(used.size)
+    t1 = remap[t].astype(np.int32)
+    X1 = X[used]
+    x1 = scenes.jitter_state(X1, 0.01, seed=2)
+    from paper_2303_02156_gb300.scene import Scene
+    s = Scene(ctx, X1)
+    s.add_tet_ho(order, t1, E[:1], nu[:1], 1000.0, _rule(order))
+    s.finalize()
+    s.set_state(x=x1)
+    Eg = s.eval(sx.SX_EGH, False, sx.SX_FP64)
+    K = t1.shape[1]
+    Ee, ge, He, bad = orc.tetho_batch(K, X1, x1, t1, _rule(order), mu[:1], lam[:1], 2, False)
+    assert bad == 0
+    go, Ho = orc.tetho_assemble(X1.shape[0], t1, ge, He)
+    rp, col, vals = s.bsr()
+    assert abs(Eg - Ee[0]) <= 1e-10 * abs(Ee[0])
+    assert np.linalg.norm(s.grad() - go) <= 1e-10 * np.linalg.norm(go)
+    assert np.linalg.norm(_dense_bsr(rp, col, vals, X1.shape[0]) - Ho) <= 1e-10 * np.linalg.norm(Ho)
+    s.close()
