@@ -1,8 +1,9 @@
 // sx_elements.cu -- launches of the element kernel (instantiations for
-// SNH tets alone and for every stencil kind; the material-projection and
-// other-density instantiations live in sx_elements_fproj.cu and
-// sx_elements_models.cu), the contact-pair activity kernels and the
-// lagged rotations of the co-rotational densities.
+// SNH tets alone and for SNH tets with hinges and barriers; the
+// material-projection, other-density and high-order instantiations live in
+// sx_elements_fproj.cu, sx_elements_models.cu and sx_elements_ho.cu), the
+// contact-pair activity kernels, the friction lag and the lagged rotations
+// of the co-rotational densities.
 #include <cuda_runtime.h>
 
 #include <algorithm>

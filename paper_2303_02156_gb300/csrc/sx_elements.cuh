@@ -25,13 +25,15 @@
 // have the same Hessian form with gam = 0 and their own coefficients; St.
 // Venant-Kirchhoff has its own blocks (see model_core).
 //
-// Point-triangle barrier (§6.4 Eq. 15) lives in sx_barrier.cuh.
+// Point-triangle barrier (§6.4 Eq. 15) lives in sx_barrier.cuh; the
+// lagged IPC friction (§6.4, KINDS bit 32) is eval_friction and the 10- and
+// 20-node tets (§7.2 Eq. fem_final, KINDS bit 64) are tetho_tile.
 //
 // Precision: SX_FP64 computes everything in double. SX_FP32 forms the
 // gathered edge vectors (x_a - x_0) in double, then does the element math
 // in float; the projection always runs in double.
 //
-// The element kernel k_elements<R, HT, KINDS> is instantiated in three
+// The element kernel k_elements<R, HT, KINDS> is instantiated in four
 // translation units (sx_elements.cu: KINDS 1, 7; sx_elements_fproj.cu: 9,
 // 15; sx_elements_models.cu: 25, 63; sx_elements_ho.cu: 64, 127) so that
 // they compile in parallel.
