@@ -1172,10 +1172,13 @@ int sx_get_friction_lag(sx_scene* s, int energy_id, double* beta, double* T, dou
         of[e] = r[9];
         for (int k = 0; k < 3; ++k) od[3 * e + k] = r[10 + k];
     }
-    if (beta) CK(cudaMemcpy(beta, ob.data(), ob.size() * sizeof(double), cudaMemcpyDefault));
-    if (T) CK(cudaMemcpy(T, oT.data(), oT.size() * sizeof(double), cudaMemcpyDefault));
-    if (fn) CK(cudaMemcpy(fn, of.data(), of.size() * sizeof(double), cudaMemcpyDefault));
-    if (dx_lag) CK(cudaMemcpy(dx_lag, od.data(), od.size() * sizeof(double), cudaMemcpyDefault));
+    // stream-ordered copies (no synchronization with other streams)
+    if (beta) CK(cudaMemcpyAsync(beta, ob.data(), ob.size() * sizeof(double), cudaMemcpyDefault, st));
+    if (T) CK(cudaMemcpyAsync(T, oT.data(), oT.size() * sizeof(double), cudaMemcpyDefault, st));
+    if (fn) CK(cudaMemcpyAsync(fn, of.data(), of.size() * sizeof(double), cudaMemcpyDefault, st));
+    if (dx_lag)
+        CK(cudaMemcpyAsync(dx_lag, od.data(), od.size() * sizeof(double), cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
     return SX_OK;
 }
 
@@ -1284,9 +1287,10 @@ int sx_add_tet_ho(sx_scene* s, int order, const int32_t* tets, int64_t n, const 
     std::vector<int32_t> ht((size_t)n * K);
     std::vector<double> hy((size_t)n), hp((size_t)n);
     if (n) {
-        CK(cudaMemcpy(ht.data(), tets, ht.size() * sizeof(int32_t), cudaMemcpyDefault));
-        CK(cudaMemcpy(hy.data(), young, n * sizeof(double), cudaMemcpyDefault));
-        CK(cudaMemcpy(hp.data(), poisson, n * sizeof(double), cudaMemcpyDefault));
+        CK(cudaMemcpyAsync(ht.data(), tets, ht.size() * sizeof(int32_t), cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(hy.data(), young, n * sizeof(double), cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(hp.data(), poisson, n * sizeof(double), cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
     }
     for (int32_t id : ht)
         if (id < 0 || id >= s->N) return fail(ctx, SX_EINVAL, "add_tet_ho: node id out of range");
