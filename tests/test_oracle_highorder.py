@@ -10,8 +10,10 @@ a! b! c! / (a+b+c+3)!); the affine patch test (under an affine map a
 straight-sided element has F = A at every point, so E equals the linear
 tet's V psi(A), the virtual work of an affine variation is V P:dA, and so is
 the Hessian form); E = g = 0 at rest also for a curved element; central
-differences of E -> g and g -> H at curved states; rotation invariance; and
-the per-point F-space projection giving a PSD Hessian.
+differences of E -> g and g -> H at curved states; rotation invariance;
+the per-point F-space projection giving a PSD Hessian; and the rest Hessian
+against the linear-elastic energy of quadratic / cubic displacement fields
+integrated from their analytic strain.
 """
 import math
 
@@ -194,3 +196,54 @@ def test_mesh_generator_shares_nodes():
         # for order 2; order 3 adds face nodes (not on a grid)
         if order == 2:
             assert m["X"].shape[0] == 5 ** 3
+
+
+@pytest.mark.parametrize("K,deg", [(10, 2), (20, 3)])
+def test_rest_hessian_is_linear_elasticity_for_polynomial_fields(K, deg):
+    """At rest the SNH Hessian (mu' = 4mu/3, lambda' = lambda + 5mu/6) is the
+    linear-elastic stiffness with (mu, lambda). For a displacement field u(X)
+    that is a polynomial of the element's order (reproduced exactly by a
+    straight-sided element), u^T H u equals the integral of
+    2 mu |eps(u)|^2 + lambda tr(eps(u))^2, computed here from the analytic
+    strain of u on a conical rule exact for the integrand's degree."""
+    Xe, X4 = _element(K, 11)
+    rng = np.random.default_rng(K)
+    young, nu = 1e5, 0.3
+    mu = young / (2 * (1 + nu)); lam = young * nu / ((1 + nu) * (1 - 2 * nu))
+    mus, lams = orc.snh_lame(young, nu)
+    mons = [(a, b, c) for a in range(deg + 1) for b in range(deg + 1) for c in range(deg + 1)
+            if 1 <= a + b + c <= deg]
+    coef = rng.normal(size=(3, len(mons))) * 0.1
+
+    def u_of(X):
+        return np.array([sum(coef[i, k] * X[0] ** a * X[1] ** b * X[2] ** c
+                             for k, (a, b, c) in enumerate(mons)) for i in range(3)])
+
+    def grad_u(X):
+        G = np.zeros((3, 3))
+        for i in range(3):
+            for k, (a, b, c) in enumerate(mons):
+                e = (a, b, c)
+                for j in range(3):
+                    if e[j] == 0:
+                        continue
+                    p = list(e); p[j] -= 1
+                    G[i, j] += coef[i, k] * e[j] * X[0] ** p[0] * X[1] ** p[1] * X[2] ** p[2]
+        return G
+
+    # the oracle's rest Hessian with a rule exact for the integrand
+    # (products of two gradients: degree 2 (deg - 1))
+    rule = scenes.tet_rule_conical(4)
+    bad, E, g, H = orc.tetho_element(K, rule, Xe, Xe, mus[0], lams[0])
+    assert bad == 0
+    uvec = np.concatenate([u_of(x) for x in Xe])
+    # the reference integral over the physical tet: X(xi) = X0 + Dm xi
+    Dm = (X4[1:] - X4[0]).T
+    det = np.linalg.det(Dm)
+    ref = 0.0
+    for w, *xi in rule:
+        X = X4[0] + Dm @ np.array(xi)
+        Gu = grad_u(X)
+        eps = 0.5 * (Gu + Gu.T)
+        ref += w * det * (2 * mu * np.sum(eps * eps) + lam * np.trace(eps) ** 2)
+    assert uvec @ H @ uvec == pytest.approx(ref, rel=1e-10)
