@@ -198,3 +198,38 @@ def test_friction_pairs_can_be_replaced(ctx):
     o = orc.friction_lag(x, bp["pairs"][::2], DHAT, KAPPA)
     assert np.allclose(s.friction_lag(eid)["fn"], o["fn"], rtol=1e-12, atol=0)
     s.close()
+
+
+@pytest.mark.gpu
+def test_friction_lag_and_elements_in_edge_and_vertex_regions(ctx):
+    """Points moved beyond triangle edges and vertices (the closest point on
+    an edge or at a vertex) and a few beyond dhat: the lag and the element
+    values against the oracle's Voronoi-region classification."""
+    from test_gpu_parity import _barrier_scene
+    X, x, pairs = _barrier_scene(n_pairs=300, seed=7, regions=True)
+    ns = X.shape[0] - pairs.shape[0]
+    s, eid = _gpu_scene(ctx, X, x, pairs)
+    s.update_friction(DT)
+    g = s.friction_lag(eid)
+    o = orc.friction_lag(x, pairs, DHAT, KAPPA)
+    # the three region kinds are present
+    nz = (o["beta"] > 1e-12).sum(1)
+    assert (nz == 1).any() and (nz == 2).any() and (nz == 3).any()
+    assert np.abs(g["beta"] - o["beta"]).max() <= 1e-12
+    assert np.allclose(g["fn"], o["fn"], rtol=1e-12, atol=0)
+    d = np.linalg.norm(o["dxt"], axis=1)
+    assert (np.linalg.norm(g["dxt"] - o["dxt"], axis=1) <= 1e-12 * d + 1e-18).all()
+    Pg = np.einsum("pri,prj->pij", g["T"], g["T"])
+    Po = np.einsum("pri,prj->pij", o["T"], o["T"])
+    assert np.abs(Pg - Po).max() <= 1e-9
+    y = _slid(x, ns, 12, YH * DT)
+    s.set_state(x=y)
+    out = s.eval_elements(eid, project=False, precision=sx.SX_FP64)
+    Ee, ge, He = orc.friction_batch(y, pairs, o, MU, YH, DT)
+    k = MU * o["fn"]
+    for e in np.flatnonzero(k > 0):
+        sE, sg, sH = k[e] * YH * DT, k[e], k[e] / (YH * DT)
+        assert abs(out["E"][e] - Ee[e]) <= 1e-10 * max(abs(Ee[e]), sE)
+        assert np.linalg.norm(out["g"][e] - ge[e]) <= 1e-10 * max(np.linalg.norm(ge[e]), sg)
+        assert np.linalg.norm(out["H"][e] - He[e]) <= 1e-10 * max(np.linalg.norm(He[e]), 1e-6 * sH)
+    s.close()
