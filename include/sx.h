@@ -412,6 +412,23 @@ typedef struct {
 int sx_newton_step(sx_scene* scene, double dt, const sx_newton_opts* opts,
                    sx_step_report* report, void* stream);
 
+/* Advance a scene by dt with the time-step halving restart of a failed
+ * step (§7 experiments: a step whose Newton iteration or line search fails
+ * is redone as two steps of half the size): substeps are taken in time
+ * order; when one fails to converge (SX_ENOTCONV, SX_ELINESEARCH, SX_ENAN or
+ * SX_ESTATE) the scene's x and v are restored to that substep's start and
+ * its interval is covered by two substeps of half its size, at most
+ * max_dt_halvings levels deep. Other errors return at once. On failure the
+ * state is that of the start of the failed substep (the whole call's start
+ * when nothing succeeded). report (may be NULL): status, Newton / PCG /
+ * line-search counts summed over the successful substeps, g0_norm of the
+ * first, g_norm and energy of the last, ms of the whole call; substeps (may
+ * be NULL) receives their number. A checkpoint of a scene is its x and v
+ * (sx_get_state / sx_set_state): lagged rotations and friction data are
+ * retaken at every step, the rest is fixed at registration. Synchronous. */
+int sx_advance(sx_scene* scene, double dt, const sx_newton_opts* opts, int max_dt_halvings,
+               sx_step_report* report, int* substeps, void* stream);
+
 /* One step for each of n scenes, batched: every kernel of the Newton and
  * PCG loops covers all still-active scenes in one launch, with per-scene
  * scalars (step sizes, convergence) kept on the device. reports: host

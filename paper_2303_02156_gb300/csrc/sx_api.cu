@@ -2235,6 +2235,73 @@ int sx_newton_step(sx_scene* s, double dt, const sx_newton_opts* opts, sx_step_r
     return sx_newton_step_batch(s->ctx, arr, 1, dt, opts, report, stream);
 }
 
+int sx_advance(sx_scene* s, double dt, const sx_newton_opts* opts, int max_dt_halvings,
+               sx_step_report* report, int* substeps, void* stream)
+{
+    if (!s || !(dt > 0.0) || max_dt_halvings < 0 || max_dt_halvings > 30) return SX_EINVAL;
+    sx_ctx* ctx = s->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t n3 = 3 * (size_t)s->N;
+    double *xs = nullptr, *vs = nullptr;
+    CK(cudaMallocAsync((void**)&xs, n3 * sizeof(double), st));
+    CK(cudaMallocAsync((void**)&vs, n3 * sizeof(double), st));
+    sx_step_report agg{};
+    int taken = 0, rc_final = SX_OK;
+    // intervals still to cover, the next one at the back: (size, depth)
+    std::vector<std::pair<double, int>> todo{{dt, 0}};
+    while (!todo.empty()) {
+        const std::pair<double, int> cur = todo.back();
+        todo.pop_back();
+        cudaError_t e = cudaMemcpyAsync(xs, s->x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(vs, s->v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) {
+            rc_final = cuda_fail(ctx, e, "advance: state copy");
+            break;
+        }
+        sx_step_report r{};
+        const int rc = sx_newton_step(s, cur.first, opts, &r, stream);
+        if (rc == SX_OK) {
+            if (taken == 0) agg.g0_norm = r.g0_norm;
+            agg.newton_iters += r.newton_iters;
+            agg.pcg_iters += r.pcg_iters;
+            agg.ls_halvings += r.ls_halvings;
+            agg.g_norm = r.g_norm;
+            agg.energy = r.energy;
+            ++taken;
+            continue;
+        }
+        const bool retry = rc == SX_ENOTCONV || rc == SX_ELINESEARCH || rc == SX_ENAN ||
+                           rc == SX_ESTATE;
+        if (retry) {
+            // back to the start of this substep
+            e = cudaMemcpyAsync(s->x, xs, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s->v, vs, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) {
+                rc_final = cuda_fail(ctx, e, "advance: state restore");
+                break;
+            }
+        }
+        if (!retry || cur.second >= max_dt_halvings) {
+            rc_final = rc;
+            break;
+        }
+        // two halves, the first one next
+        todo.push_back({0.5 * cur.first, cur.second + 1});
+        todo.push_back({0.5 * cur.first, cur.second + 1});
+    }
+    cudaFreeAsync(xs, st);
+    cudaFreeAsync(vs, st);
+    CK(cudaStreamSynchronize(st));
+    agg.status = rc_final;
+    agg.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (report) *report = agg;
+    if (substeps) *substeps = taken;
+    return rc_final;
+}
+
 int sx_scene_footprint(const sx_scene_desc* d, int64_t* bytes)
 {
     if (!d || !bytes) return SX_EINVAL;

@@ -300,6 +300,18 @@ class Scene:
             self.ctx.check(rc)
         return rc, _rep(r)
 
+    def advance(self, dt, max_dt_halvings=4, raise_on_error=True, **opts):
+        """Advance by dt; failed Newton steps are redone as two half steps
+        (sx_advance). Returns (status, report, substeps)."""
+        o = sx.newton_opts(**opts)
+        r = sx.sx_step_report()
+        n = C.c_int()
+        rc = sx.sx_advance(self.h, float(dt), C.byref(o), int(max_dt_halvings), C.byref(r),
+                           C.byref(n), self.stream)
+        if raise_on_error:
+            self.ctx.check(rc)
+        return rc, _rep(r), n.value
+
     def nbytes(self):
         b = C.c_int64()
         self.ctx.check(sx.sx_scene_bytes(self.h, C.byref(b)))

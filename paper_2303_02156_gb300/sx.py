@@ -46,7 +46,7 @@ EXPORTS = [
     "sx_autotune", "sx_set_launch_shape", "sx_get_launch_shape", "sx_set_pairs",
     "sx_compact_pairs", "sx_add_tet4", "sx_update_rotations", "sx_get_rotations",
     "sx_set_rotations", "sx_add_pt_friction", "sx_update_friction", "sx_get_friction_lag",
-    "sx_add_tet_ho",
+    "sx_add_tet_ho", "sx_advance",
     "sx_server_create", "sx_server_set_lanes", "sx_server_submit", "sx_server_poll", "sx_server_result",
     "sx_server_drain", "sx_server_stats", "sx_server_destroy",
 ]
@@ -156,6 +156,7 @@ _SIGS = {
     "sx_set_rotations": (_I, [_P, _I, _P, _P]),
     "sx_add_pt_friction": (_I, [_P, _P, _I64, _D, _D, _D, _D, _P, C.POINTER(_I)]),
     "sx_add_tet_ho": (_I, [_P, _I, _P, _I64, _P, _P, _D, _P, _I, _P, C.POINTER(_I)]),
+    "sx_advance": (_I, [_P, _D, _P, _I, _P, C.POINTER(_I), _P]),
     "sx_update_friction": (_I, [_P, _D, _P]),
     "sx_get_friction_lag": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "sx_compact_pairs": (_I, [_P, _I, C.POINTER(_I64), _P]),

@@ -665,3 +665,56 @@ def test_material_projection_assembly_and_newton(ctx):
     ref = np.abs(xo - m["X"]).max()
     assert np.abs(xg - xo).max() <= 1e-8 * ref + 1e-12
     s.close()
+
+
+@pytest.mark.gpu
+def test_advance_halves_failed_steps_and_restores_state(ctx):
+    """sx_advance: (a) a tolerance no step reaches: every substep fails and
+    the state comes back unchanged; (b) with a one-iteration Newton budget
+    the call equals the same policy run as single steps with snapshots
+    (sx_get_state / sx_set_state), bit for bit."""
+    from paper_2303_02156_gb300.scene import Scene
+    m, E, nu = _c1()
+
+    def scene():
+        s = Scene(ctx, m["X"])
+        s.add_snh(m["tets"], E, nu, 1000.0)
+        s.set_pinned(m["pinned"])
+        s.set_gravity((0.0, 0.0, -9.81))
+        s.finalize()
+        return s
+
+    x0 = scenes.jitter_state(m["X"], 1e-3, seed=4)
+    x0[m["pinned"]] = m["X"][m["pinned"]]
+    v0 = np.zeros_like(x0)
+    v0[:, 0] = 0.1
+    v0[m["pinned"]] = 0.0
+    s = scene()
+    s.set_state(x=x0, v=v0)
+    rc, rep, n = s.advance(0.01, max_dt_halvings=2, raise_on_error=False, newton_tol=1e-300,
+                           max_newton=2)
+    assert rc == sx.SX_ENOTCONV and n == 0 and rep["status"] == rc
+    x, v = s.get_state()
+    assert np.array_equal(x, x0) and np.array_equal(v, v0)
+    opts = dict(newton_tol=1e-6, max_newton=1, pcg_tol=1e-10)
+    s.set_state(x=x0, v=v0)
+    rc, rep, n = s.advance(0.2, max_dt_halvings=10, raise_on_error=False, **opts)
+    xa = s.get_state()[0]
+    s2 = scene()
+    s2.set_state(x=x0, v=v0)
+    todo, taken, rc2 = [(0.2, 0)], 0, sx.SX_OK
+    while todo:
+        h, depth = todo.pop()
+        xs, vs = s2.get_state()
+        r2, _ = s2.newton_step(h, raise_on_error=False, **opts)
+        if r2 == sx.SX_OK:
+            taken += 1
+            continue
+        s2.set_state(x=xs, v=vs)
+        if depth >= 10:
+            rc2 = r2
+            break
+        todo += [(h / 2, depth + 1), (h / 2, depth + 1)]
+    assert rc == rc2 and n == taken and n >= 1
+    assert np.array_equal(xa, s2.get_state()[0])
+    s.close(); s2.close()
