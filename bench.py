@@ -419,7 +419,7 @@ def run_mixed(ctx, stream, flush, reps=5):
 
 # ------------------------------------------------------------------ other densities
 def run_models(ctx, stream, flush, m, E, nu, x, reps=5):
-    """The bench cube with each of the other tet4 densities (§7.1): one
+    """The bench cube with each of the other tet4 densities (§6.1): one
     E + g + projected H + assembly pass at the jittered state (FP64, FP32)
     and one backward-Euler Newton step from rest (FP64, dt = 0.005)."""
     import numpy as np

@@ -82,7 +82,7 @@ extern "C" {
 #define SX_KIND_TET_HO 4       /* 10- or 20-node tets (sx_add_tet_ho) */
 #define SX_HO_MAX_QP 64        /* quadrature points per high-order rule */
 
-/* ---- tet4 densities (§7.1 "Non-linear material models", App. B) -------
+/* ---- tet4 densities (§6.1 "Non-Linear Material Models", App. B) -------
  * SNH    Stable Neo-Hookean (§3.1 Eq. 7), parameters mu', lambda' as in
  *        sx_add_snh_tet4;
  * NH     Neo-Hookean mu/2 (Ic - 3) - mu ln J + lambda/2 ln^2 J (the text
@@ -94,7 +94,7 @@ extern "C" {
  * ARAP   as-rigid-as-possible with a volume term
  *        mu/2 |F - R|^2 + lambda/2 (J - 1)^2.
  * COROT and ARAP use a lagged rotation R per tet (constant within a time
- * step, §7.1; not differentiated): the rotation of the polar decomposition
+ * step, §6.1; not differentiated): the rotation of the polar decomposition
  * of F, taken at the start of every Newton step and by
  * sx_update_rotations; the identity when the block is added. */
 #define SX_MODEL_SNH 0
@@ -156,7 +156,7 @@ int sx_add_tet4(sx_scene* scene, int model, const int32_t* tets, int64_t n,
                 const double* young, const double* poisson, double density, void* stream,
                 int* energy_id);
 
-/* High-order Lagrange tets (§7.2 Eq. fem_final; App. A shape functions)
+/* High-order Lagrange tets (§6.2 Eq. 12; App. A shape functions)
  * with the Stable Neo-Hookean density (mu', lambda' as in sx_add_snh_tet4):
  * E_e = sum_q w_q det J0(xi_q) psi(F(xi_q)) over a quadrature rule given by
  * the caller (the fixed-value summation of §5), J0 = sum_a X_a dN_a^T,
@@ -179,7 +179,7 @@ int sx_add_tet_ho(sx_scene* scene, int order, const int32_t* tets, int64_t n,
                   const double* young, const double* poisson, double density,
                   const double* rule, int nq, void* stream, int* energy_id);
 
-/* Lagged rotations of the COROT / ARAP blocks of a scene (§7.1).
+/* Lagged rotations of the COROT / ARAP blocks of a scene (§6.1).
  * sx_update_rotations: R of every tet of those blocks := the rotation of
  * the polar decomposition of F at the current state (F = U S V^T with
  * singular values in descending order, R = U V^T, the column of U of the
@@ -408,7 +408,10 @@ typedef struct {
 } sx_step_report;
 
 /* One step: x_tilde = x + dt v + dt^2 g_ext; x0 = x; Newton with PCG and
- * Armijo backtracking; v = (x - x_t)/dt. Synchronous. */
+ * Armijo backtracking; v = (x - x_t)/dt. A step that fails (any status but
+ * SX_OK: non-finite values, an invalid state, an iteration cap, a line search
+ * without decrease) is not taken: the scene keeps the x and v it had at the
+ * call. Synchronous. */
 int sx_newton_step(sx_scene* scene, double dt, const sx_newton_opts* opts,
                    sx_step_report* report, void* stream);
 
@@ -418,9 +421,11 @@ int sx_newton_step(sx_scene* scene, double dt, const sx_newton_opts* opts,
  * order; when one fails to converge (SX_ENOTCONV, SX_ELINESEARCH, SX_ENAN or
  * SX_ESTATE) the scene's x and v are restored to that substep's start and
  * its interval is covered by two substeps of half its size, at most
- * max_dt_halvings levels deep. Other errors return at once. On failure the
- * state is that of the start of the failed substep (the whole call's start
- * when nothing succeeded). report (may be NULL): status, Newton / PCG /
+ * max_dt_halvings levels deep. Other errors return at once. On any failure
+ * the state is that of the start of the failed substep (the whole call's
+ * start when nothing succeeded), restored from a device snapshot taken
+ * before each substep. A successful call clears sx_last_error's text, also
+ * when substeps failed on the way. report (may be NULL): status, Newton / PCG /
  * line-search counts summed over the successful substeps, g0_norm of the
  * first, g_norm and energy of the last, ms of the whole call; substeps (may
  * be NULL) receives their number. A checkpoint of a scene is its x and v
@@ -432,7 +437,8 @@ int sx_advance(sx_scene* scene, double dt, const sx_newton_opts* opts, int max_d
 /* One step for each of n scenes, batched: every kernel of the Newton and
  * PCG loops covers all still-active scenes in one launch, with per-scene
  * scalars (step sizes, convergence) kept on the device. reports: host
- * array of n. */
+ * array of n. A scene whose step fails keeps its state (as sx_newton_step);
+ * the others are stepped. */
 int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
                          const sx_newton_opts* opts, sx_step_report* reports,
                          void* stream);

@@ -449,7 +449,7 @@ class _OrcOpts(C.Structure):
     _fields_ = [("newton_tol", C.c_double), ("pcg_tol", C.c_double),
                 ("max_newton", C.c_int), ("max_pcg", C.c_int),
                 ("max_halvings", C.c_int), ("armijo_c", C.c_double),
-                ("project", C.c_int)]
+                ("project", C.c_int), ("forcing", C.c_int)]
 
 
 class _OrcReport(C.Structure):
@@ -558,15 +558,17 @@ class Scene:
 
     def newton_step(self, x, v, dt, gravity=(0.0, 0.0, -9.81), newton_tol=1e-8,
                     pcg_tol=1e-10, max_newton=100, max_pcg=10000, max_halvings=30,
-                    armijo_c=1e-4, project=True):
+                    armijo_c=1e-4, project=True, forcing=False):
         """One backward-Euler step. The lagged rotations of a COROT / ARAP
         block are taken at the start-of-step state and held for the step
-        (§7.1: rotations constant per time step)."""
+        (§6.1: rotations constant per time step). forcing: PCG tolerance
+        max(pcg_tol, min(1/2, sqrt(|g_k| / |g_0|))) per Newton iteration (the
+        §7.2 solver's forcing sequence, as read here)."""
         x = _f64(x).ravel().copy(); v = _f64(v).ravel().copy()
         if self.R is not None:
             self.set_rotations(lagged_rotations(x.reshape(-1, 3), self.tets, self.Dminv))
         o = _OrcOpts(newton_tol, pcg_tol, max_newton, max_pcg, max_halvings, armijo_c,
-                     int(project))
+                     int(project), int(forcing))
         r = _OrcReport()
         st = lib().orc_newton_step(C.byref(self._s), float(dt), _f64(gravity),
                                    C.byref(o), x, v, C.byref(r))

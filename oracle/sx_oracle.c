@@ -14,7 +14,7 @@
  *     [App. B, "Eq. 14 from Smith et al."]; derivatives by the chain rule
  *     through P = dpsi/dF and d2psi/dF2 and the constant 9x12 map vec(F) =
  *     B xhat built from Dm^-1 [App. A, tet4 shape functions].
- *   - The other tet4 densities of §7.1 / App. B (Neo-Hookean, St.
+ *   - The other tet4 densities of §6.1 / App. B (Neo-Hookean, St.
  *     Venant-Kirchhoff, fixed co-rotational and ARAP with lagged rotations)
  *     written as plain expressions of F and differentiated by second-order
  *     forward-mode arithmetic in the 12 stencil coordinates.
@@ -23,7 +23,7 @@
  *     point-triangle distance [§6.4, Eq. 15], active only for d < dhat
  *     [§5.2 "Conditional evaluations", Eq. 9].
  *   - High-order (10- and 20-node) Lagrange tets with a quadrature sum
- *     [§7.2 Eq. fem_final, App. A shape functions].
+ *     [§6.2 Eq. 12, App. A shape functions].
  *   - Lagged IPC friction on point-triangle pairs [§6.4, friction
  *     potential] with its lag data (closest point, tangent basis, contact
  *     force) taken at the start of a step.
@@ -757,7 +757,7 @@ int orc_barrier_batch(int P, const double* x, const int* pairs, double dhat,
 }
 
 /* ------------------------------------------------------------------ */
-/* Other tet4 densities (§7.1 "Non-linear material models", App. B):    */
+/* Other tet4 densities (§6.1 "Non-Linear Material Models", App. B):    */
 /* Neo-Hookean, St. Venant-Kirchhoff, fixed co-rotational and ARAP with */
 /* a volume term, the two co-rotational ones with a lagged rotation R   */
 /* ------------------------------------------------------------------ */
@@ -1162,8 +1162,8 @@ void orc_friction_batch(int P, const double* x, const int* pairs, const double* 
 }
 
 /* ------------------------------------------------------------------ */
-/* High-order Lagrange tets with a quadrature sum (§7.2 "High-order      */
-/* Lagrangian finite elements", Eq. fem_final; App. A shape functions;   */
+/* High-order Lagrange tets with a quadrature sum (§6.2 "High-order      */
+/* Lagrangian finite elements", Eq. 12; App. A shape functions;       */
 /* §5 fixed-value summation)                                            */
 /* ------------------------------------------------------------------ */
 
@@ -1230,7 +1230,7 @@ void orc_tetho_shape(int K, const double* xi, double* N, double* dN)
 
 /* One SNH element of K nodes: E = sum_q w_q det(J0_q) psi(F_q) with
  * J0 = sum_a X_a dN_a^T, F = (sum_a x_a dN_a^T) J0^-1 at the quadrature
- * point xi_q (Eq. fem_final); g and H by the chain rule through the 9 x 3K
+ * point xi_q (Eq. 12); g and H by the chain rule through the 9 x 3K
  * map of each point. rule: nq x (w, xi0, xi1, xi2). project != 0 clamps
  * d2psi/dF2 at every point (READING: the PSD projection of high-order
  * elements is taken per quadrature point in F-space; the sum of PSD terms
@@ -1653,6 +1653,10 @@ typedef struct {
     int max_halvings;
     double armijo_c;
     int project;
+    /* 1: the PCG tolerance of Newton iteration k is the forcing term
+     * max(pcg_tol, min(1/2, sqrt(||g_k|| / ||g_0||))) (READING of the §7.2
+     * solver paragraph, which names a forcing sequence without a formula) */
+    int forcing;
 } orc_newton_opts;
 
 typedef struct {
@@ -1724,9 +1728,15 @@ int orc_newton_step(const orc_scene* s, double dt, const double gravity[3],
         for (int n = 0; n < N; ++n)
             for (int i = 0; i < 3; ++i)
                 b[3 * n + i] = (s->pinned && s->pinned[n]) ? 0.0 : -g[3 * n + i];
+        double ptol = o->pcg_tol;
+        if (o->forcing) {
+            double eta = sqrt(gn / (gn0 > 1e-300 ? gn0 : 1e-300));
+            if (eta > 0.5) eta = 0.5;
+            if (eta > ptol) ptol = eta;
+        }
         int pit = 0;
         int pst = orc_pcg(N, s->row_ptr, s->col, vals, s->diag_slot, s->pinned, b,
-                          o->pcg_tol, o->max_pcg, dx, &pit, NULL);
+                          ptol, o->max_pcg, dx, &pit, NULL);
         pcg_total += pit;
         if (pst != 0) { status = ORC_ENOTCONV; break; }
         double gdx = dotv(n3, g, dx);

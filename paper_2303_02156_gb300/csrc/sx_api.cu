@@ -129,6 +129,12 @@ struct sx_scene {
     double* He = nullptr;   // 90 doubles per stencil; float staging reuses it
     double* vals64 = nullptr;
     float* vals32 = nullptr;
+    // the PCG's sliced-ELLPACK copy of the values (32-row slices)
+    int* sell_ptr = nullptr;   // [nslices + 1] steps before each slice
+    int* sell_col = nullptr;   // [32 steps]
+    double* sell_v64 = nullptr;   // [9 x 32 steps]
+    float* sell_v32 = nullptr;
+    int64_t sell_steps = 0;
     float* p32 = nullptr;
     double* grad = nullptr;
     double *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
@@ -423,6 +429,10 @@ SceneDev make_desc(const sx_scene* s, bool trial)
     d.node_src = s->pat.node_src;
     d.vals64 = s->vals64;
     d.vals32 = s->vals32;
+    d.sell_ptr = s->sell_ptr;
+    d.sell_col = s->sell_col;
+    d.sell_v64 = s->sell_v64;
+    d.sell_v32 = s->sell_v32;
     d.r = s->r;
     d.z = s->z;
     d.p0 = s->p0;
@@ -697,12 +707,43 @@ int read_scal(sx_ctx* ctx, Batch* B, cudaStream_t st)
     return SX_OK;
 }
 
+// The SpMV's sliced copy of the pattern: slice widths, their prefix sum,
+// the padded column array and the (zeroed) FP64 value array.
+int build_sell(sx_scene* s, cudaStream_t st)
+{
+    sx_ctx* ctx = s->ctx;
+    const int64_t nsl = (s->N + 31) / 32;
+    int* w = nullptr;
+    if (dalloc_fin(s, &s->sell_ptr, (size_t)nsl + 1) != SX_OK)
+        return fail(ctx, SX_ENOMEM, "finalize: device allocation failed (SpMV layout)");
+    CK(cudaMallocAsync((void**)&w, std::max<int64_t>(nsl, 1) * sizeof(int), st));
+    CK(launch_sell_widths(s->pat.row_ptr, s->N, w, st));
+    std::string err;
+    const int rc = scan_counts(w, nsl, s->sell_ptr, st, &err);
+    cudaFreeAsync(w, st);
+    if (rc != SX_OK) return fail(ctx, rc, err);
+    int steps = 0;
+    CK(cudaMemcpyAsync(&steps, s->sell_ptr + nsl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    s->sell_steps = steps;
+    if (dalloc_fin(s, &s->sell_col, 32 * (size_t)steps + 32) != SX_OK ||
+        dalloc_fin(s, &s->sell_v64, 288 * (size_t)steps + 32) != SX_OK)
+        return fail(ctx, SX_ENOMEM, "finalize: device allocation failed (SpMV layout)");
+    CK(launch_sell_cols(s->pat.row_ptr, s->pat.col, s->N, s->sell_ptr, s->sell_col, st));
+    CK(cudaMemsetAsync(s->sell_v64, 0, (288 * (size_t)steps + 32) * sizeof(double), st));
+    return SX_OK;
+}
+
 int ensure_vals32(sx_ctx* ctx, sx_scene* s)
 {
     if (s->vals32) return SX_OK;
     if (dalloc_fin(s, &s->vals32, 9 * (size_t)s->pat.nnzb + 16) != SX_OK ||
-        dalloc_fin(s, &s->p32, 3 * (size_t)s->N + 4) != SX_OK)
+        dalloc_fin(s, &s->p32, 3 * (size_t)s->N + 4) != SX_OK ||
+        dalloc_fin(s, &s->sell_v32, 288 * (size_t)s->sell_steps + 64) != SX_OK)
         return fail(ctx, SX_ENOMEM, "eval: device allocation failed (FP32 values)");
+    // pad entries (and the lanes past the last row) stay zero
+    CK(cudaMemsetAsync(s->sell_v32, 0, (288 * (size_t)s->sell_steps + 64) * sizeof(float),
+                       s->stream));
     s->version++;
     return SX_OK;
 }
@@ -1512,6 +1553,7 @@ int sx_finalize(sx_scene* s, void* stream)
         return fail(ctx, SX_ENOMEM, "finalize: device allocation failed");
     CK(cudaMemsetAsync(s->grad, 0, n3 * sizeof(double), st));
     CK(cudaMemsetAsync(s->vals64, 0, 9 * (size_t)s->pat.nnzb * sizeof(double), st));
+    if ((rc = build_sell(s, st)) != SX_OK) return rc;
     CK(cudaStreamSynchronize(st));
     s->finalized = true;
     s->version++;
@@ -1543,6 +1585,10 @@ void release_finalized(sx_scene* s)
     s->r = s->z = s->p0 = s->p1 = s->q = s->Minv = nullptr;
     s->vals32 = nullptr;
     s->p32 = nullptr;
+    s->sell_ptr = s->sell_col = nullptr;
+    s->sell_v64 = nullptr;
+    s->sell_v32 = nullptr;
+    s->sell_steps = 0;
     s->finalized = false;
     s->last_level = -1;
     s->version++;
@@ -2027,7 +2073,7 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
     std::vector<int> act(n, 1);
     if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
     // lagged rotations (COROT, ARAP): taken at the start-of-step state and
-    // held for the step (§7.1)
+    // held for the step (§6.1)
     for (int i = 0; i < n; ++i) CK(update_rotations(scenes[i], st));
     PL(SX_PH_NEWTON, 1, launch_predict(B->d_desc, B->d_node, nnt, B->d_part_node, st));
     PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_node, 1, 0, B->d_node_beg, B->d_node_end,
@@ -2148,11 +2194,10 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
             pcg_it[i] += B->h_scal[i].pcg_iters;
             if (B->h_scal[i].pcg_status != 0) {
                 const int ps = B->h_scal[i].pcg_status;
-                status[i] = ps == 3 ? SX_ECUDA : SX_ENOTCONV;
+                status[i] = SX_ENOTCONV;
                 if (why.empty())
-                    why = ps == 3 ? "PCG: a staged SpMV tile copy did not complete in time"
-                          : ps == 1 ? "PCG: p.q <= 0 (the system is not positive definite)"
-                                    : "PCG: iteration cap reached";
+                    why = ps == 1 ? "PCG: p.q <= 0 (the system is not positive definite)"
+                                  : "PCG: iteration cap reached";
                 done[i] = 1;
                 act[i] = 0;
             }
@@ -2202,8 +2247,21 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
                 if (why.empty()) why = "line search: no sufficient decrease";
             }
     }
-    std::vector<int> all(n, 1);
-    if ((rc = set_active(ctx, B, all, st)) != SX_OK) return rc;
+    // a scene whose step failed keeps the state it had at the call (x back
+    // to the start of the step, v untouched); the others take
+    // v = (x - x_t) / dt
+    std::vector<int> okv(n), badv(n);
+    bool any_bad = false;
+    for (int i = 0; i < n; ++i) {
+        okv[i] = status[i] == SX_OK;
+        badv[i] = !okv[i];
+        any_bad = any_bad || badv[i];
+    }
+    if (any_bad) {
+        if ((rc = set_active(ctx, B, badv, st)) != SX_OK) return rc;
+        PL(SX_PH_NEWTON, 1, launch_restore(B->d_desc, B->d_node, nnt, st));
+    }
+    if ((rc = set_active(ctx, B, okv, st)) != SX_OK) return rc;
     PL(SX_PH_NEWTON, 1, launch_velocity(B->d_desc, B->d_node, nnt, st));
     CK(cudaStreamSynchronize(st));
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -2244,8 +2302,17 @@ int sx_advance(sx_scene* s, double dt, const sx_newton_opts* opts, int max_dt_ha
     const auto t0 = std::chrono::steady_clock::now();
     const size_t n3 = 3 * (size_t)s->N;
     double *xs = nullptr, *vs = nullptr;
-    CK(cudaMallocAsync((void**)&xs, n3 * sizeof(double), st));
-    CK(cudaMallocAsync((void**)&vs, n3 * sizeof(double), st));
+    {
+        // both snapshots or neither (no buffer left behind on failure)
+        const cudaError_t ex = cudaMallocAsync((void**)&xs, n3 * sizeof(double), st);
+        const cudaError_t ev = ex == cudaSuccess
+                                   ? cudaMallocAsync((void**)&vs, n3 * sizeof(double), st)
+                                   : cudaSuccess;
+        if (ex != cudaSuccess || ev != cudaSuccess) {
+            if (xs) cudaFreeAsync(xs, st);
+            return cuda_fail(ctx, ex != cudaSuccess ? ex : ev, "advance: state snapshot");
+        }
+    }
     sx_step_report agg{};
     int taken = 0, rc_final = SX_OK;
     // intervals still to cover, the next one at the back: (size, depth)
@@ -2274,15 +2341,14 @@ int sx_advance(sx_scene* s, double dt, const sx_newton_opts* opts, int max_dt_ha
         }
         const bool retry = rc == SX_ENOTCONV || rc == SX_ELINESEARCH || rc == SX_ENAN ||
                            rc == SX_ESTATE;
-        if (retry) {
-            // back to the start of this substep
-            e = cudaMemcpyAsync(s->x, xs, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(s->v, vs, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) {
-                rc_final = cuda_fail(ctx, e, "advance: state restore");
-                break;
-            }
+        // back to the start of this substep, whatever the failure (a retried
+        // substep starts there; any other failure returns with that state)
+        e = cudaMemcpyAsync(s->x, xs, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->v, vs, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) {
+            rc_final = cuda_fail(ctx, e, "advance: state restore after a failed substep");
+            break;
         }
         if (!retry || cur.second >= max_dt_halvings) {
             rc_final = rc;
@@ -2295,6 +2361,9 @@ int sx_advance(sx_scene* s, double dt, const sx_newton_opts* opts, int max_dt_ha
     cudaFreeAsync(xs, st);
     cudaFreeAsync(vs, st);
     CK(cudaStreamSynchronize(st));
+    // substeps that failed and were covered by halves left their reason in
+    // the context's error text; a successful call clears it
+    if (rc_final == SX_OK) ctx->err.clear();
     agg.status = rc_final;
     agg.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (report) *report = agg;
@@ -2317,6 +2386,7 @@ int sx_scene_footprint(const sx_scene_desc* d, int64_t* bytes)
     // (tets and pairs): 9x9 matrix, reference, float eigenvectors, norm, bins
     b += (d->n_tets + d->n_pairs) * (45 * 8 + 16 + 81 * 4 + 8 + 10 * 4);
     b += nnzb * (4 + 4 + 4 + 9 * 8);                        // col, slot_ptr, order, values
+    b += (nnzb + nnzb / 4 + 64) * (4 + 9 * 8) + N / 8;      // SpMV sliced copy (padded)
     b += 1 << 20;
     *bytes = b;
     return SX_OK;
@@ -2449,11 +2519,6 @@ struct NaPtrs {
     int* counters = nullptr;
     double* clampM = nullptr;
     ClampRef* clampRef = nullptr;
-    // two-launch projection scratch (same capacity as the queue)
-    float* clampX = nullptr;
-    double* clampFro = nullptr;
-    int* clampBucket = nullptr;
-    int* clampBucketCount = nullptr;
 };
 
 constexpr int kNaMaxDevices = 64;

@@ -20,14 +20,14 @@
 // E = k_b c |sum_a q_a x_a|^2 / 2, g_a = k_b c q_a s, H_ab = k_b c q_a q_b I3
 // with s = sum_a q_a x_a; Q is PSD and never projected.
 //
-// Other tet4 densities (§7.1, App. B; compiled into separate
+// Other tet4 densities (§6.1, App. B; compiled into separate
 // instantiations, KINDS bit 16): Neo-Hookean, fixed co-rotational and ARAP
 // have the same Hessian form with gam = 0 and their own coefficients; St.
 // Venant-Kirchhoff has its own blocks (see model_core).
 //
 // Point-triangle barrier (§6.4 Eq. 15) lives in sx_barrier.cuh; the
 // lagged IPC friction (§6.4, KINDS bit 32) is eval_friction and the 10- and
-// 20-node tets (§7.2 Eq. fem_final, KINDS bit 64) are tetho_tile.
+// 20-node tets (§6.2 Eq. 12, KINDS bit 64) are tetho_tile.
 //
 // Precision: SX_FP64 computes everything in double. SX_FP32 forms the
 // gathered edge vectors (x_a - x_0) in double, then does the element math
@@ -1083,7 +1083,7 @@ __device__ __forceinline__ double snh_point(const double (&Fd)[9], double mud, d
     return psi;
 }
 
-// 10- and 20-node tets (§7.2 Eq. fem_final): E = sum_q wd_q psi(F_q) with
+// 10- and 20-node tets (§6.2 Eq. 12): E = sum_q wd_q psi(F_q) with
 // wd_q = w_q det J0_q, F_q = sum_a x_a G_qa^T and G_qa = J0_q^-T dN_a(xi_q).
 // Each point adds SNH blocks of the linear tet's form with V -> wd_q and
 // G_a -> G_qa; with projection the negative modes of d2psi/dF2 at F_q are

@@ -13,6 +13,9 @@
 //            slot_src int[nst*16] (code 16*stencil + 4a + b),
 //            node_ptr int[N+1], node_src int[nst*4] (code 4*stencil + a)
 //   BSR values: double[nnzb][9] (FP64) and float[nnzb][9] (FP32 form)
+//   SpMV copy of the values, sliced ELLPACK (32-row slices padded to their
+//   longest row): sell_ptr int[N/32+1], sell_col int[32 steps],
+//   sell_v64 double[9 x 32 steps] (+ sell_v32 float in the FP32 form)
 //
 // Kernels are written over "tiles" (scene, block, start, count) so that a
 // single scene, a batch of scenes and the server's mixes all run through
@@ -103,7 +106,7 @@ struct SceneScal {
     double grav[3];    // external acceleration (M^-1 f_ext)
     int pcg_done;      // 1 once converged or stopped (kernels skip the scene)
     int pcg_iters;
-    int pcg_status;    // 0 ok, 1 breakdown (p.Ap <= 0), 2 iteration cap, 3 copy timeout
+    int pcg_status;    // 0 ok, 1 breakdown (p.Ap <= 0), 2 iteration cap
     int active;        // scene takes part in the current batched phase
     int bad_state;     // barrier pairs with d <= 0 in the last evaluation
     int nonfinite;     // non-finite values seen in the last evaluation
@@ -147,6 +150,13 @@ struct SceneDev {
     const int* node_src;
     double* vals64;
     float* vals32;
+    // the PCG's sliced-ELLPACK copy of the values: 32-row slices, slice s
+    // spans steps sell_ptr[s] .. sell_ptr[s+1]; columns [step][lane],
+    // values [step][9][lane] (pad entries: value 0, the row's own column)
+    const int* sell_ptr;
+    const int* sell_col;
+    double* sell_v64;
+    float* sell_v32;
     double* r;
     double* z;
     double* p0;
@@ -319,8 +329,12 @@ cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int nt
 cudaError_t launch_pcg_pdir(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
                             int precision, int parity, cudaStream_t s);
 int spmv_rows_per_tile();
-// sets the SpMV kernels' shared-memory opt-in on the current device (once)
-void prepare_spmv();
+// the SpMV's sliced copy of a pattern: per 32-row slice its longest row
+// (widths[(N + 31) / 32]), then, from their exclusive prefix sum sell_ptr,
+// the padded column array
+cudaError_t launch_sell_widths(const int* row_ptr, int64_t N, int* widths, cudaStream_t s);
+cudaError_t launch_sell_cols(const int* row_ptr, const int* col, int64_t N, const int* sell_ptr,
+                             int* sell_col, cudaStream_t s);
 // eight PCG iterations as a chain of kernel nodes appended to `graph`
 struct PcgChunkArgs {   // (the fused kernels take the scenes' tile ranges)
     const SceneDev* scenes;
@@ -356,5 +370,8 @@ cudaError_t launch_accept(const SceneDev* scenes, const Tile* node_tiles, int nt
                           cudaStream_t s);
 cudaError_t launch_velocity(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
                             cudaStream_t s);
+// x = x_start (the state at the start of the step) for the active scenes
+cudaError_t launch_restore(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                           cudaStream_t s);
 
 }  // namespace sx

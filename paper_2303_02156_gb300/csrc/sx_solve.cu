@@ -2,7 +2,9 @@
 // Eqs. 2-3) and the 3x3 block-Jacobi preconditioned CG of §7.2, batched
 // over scenes with per-scene scalars on the device.
 //
-// PCG iteration (per scene, x0 = 0, b = -g on free DOFs, 0 on pinned):
+// The setup also copies the assembled values into the SpMV's sliced
+// layout (below). PCG iteration (per scene, x0 = 0, b = -g on free DOFs, 0
+// on pinned):
 //   p_new = z + beta p_old;  q = A p_new;  alpha = (r.z) / (p_new.q)
 //   dx += alpha p_new;  r -= alpha q;  z = Minv r
 //   stop when ||r|| <= tol ||b||;  beta = r.z_new / r.z
@@ -135,6 +137,21 @@ k_pcg_setup(const SceneDev* scenes, const Tile* tiles, int ntiles, double* part)
         }
 #pragma unroll
         for (int k = 0; k < 9; ++k) S.Minv[9 * n + k] = Mi[k];
+        // this row into the SpMV's sliced copy (node tiles start at multiples
+        // of 256, so the 32 lanes of a warp fill one slice: coalesced stores)
+        {
+            const VT* vals = (sizeof(VT) == 8) ? (const VT*)S.vals64 : (const VT*)S.vals32;
+            VT* sv = (sizeof(VT) == 8) ? (VT*)S.sell_v64 : (VT*)S.sell_v32;
+            const int64_t sl = n >> 5;
+            const int k0 = S.sell_ptr[sl], w = S.sell_ptr[sl + 1] - k0;
+            const int b = S.row_ptr[n], len = S.pinned[n] ? 0 : S.row_ptr[n + 1] - b;
+            VT* dst = sv + (int64_t)k0 * 288 + (n & 31);
+            const VT* src = vals + 9 * (int64_t)b;
+            for (int k = 0; k < w; ++k)
+#pragma unroll
+                for (int e = 0; e < 9; ++e)
+                    __stcs(dst + (int64_t)288 * k + 32 * e, k < len ? src[9 * k + e] : VT(0));
+        }
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             double z = Mi[3 * i] * b[0] + Mi[3 * i + 1] * b[1] + Mi[3 * i + 2] * b[2];
@@ -265,174 +282,121 @@ cudaError_t launch_pcg_pdir(const SceneDev* scenes, const Tile* node_tiles, int 
     return cudaGetLastError();
 }
 
-// --- TMA bulk copy (non-tensor form) helpers: global -> shared, completion
-// tracked by an mbarrier transaction count
-__device__ __forceinline__ unsigned smem_u32(const void* p)
+// ------------------------------------------------------------------ SpMV layout
+// The PCG multiplies with a copy of the BSR values in sliced-ELLPACK form.
+// A slice is 32 consecutive block rows (one warp, one lane per block row),
+// padded to its longest row; entry (slice s, step k, lane l) is the k-th
+// block of row 32 s + l. The blocks are stored [step][9 entries][32 lanes],
+// so each of a warp's value loads is one contiguous segment (256 bytes in
+// FP64, 128 in FP32) and the matrix streams from HBM with no staging and no
+// idle lanes. sell_ptr[s] counts the steps of the slices before s. Pad
+// entries hold zeros and a valid column (the row's own). The columns are
+// laid out once per pattern; the values are copied from the BSR in the PCG
+// setup, with pinned rows as zeros (their q = A p is then 0, which equals p
+// there: p stays zero on pinned DOFs).
+__global__ void k_sell_widths(const int* __restrict__ row_ptr, int64_t N, int* __restrict__ w)
 {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= (N + 31) / 32) return;
+    int m = 0;
+    const int64_t r1 = min(N, 32 * s + 32);
+    for (int64_t r = 32 * s; r < r1; ++r) m = max(m, row_ptr[r + 1] - row_ptr[r]);
+    w[s] = m;
 }
 
-#ifndef SX_SPMV_STAGE
-#define SX_SPMV_STAGE 1
-#endif
-// 32 rows: 96 threads, three full warps (48 rows left half a warp idle);
-// measured on the 64^3 cube, FP64 SpMV per call 134 us at 32 rows against
-// 146 (48), 154 (64) and 165 (16); FP32 within 2% across 32-64. A form
-// without staging (a half-warp per block row reading its blocks straight
-// from global memory) measured 268 us: each lane's nine loads are 72 B apart
-// from its neighbours', many sectors per load instruction. Splitting each
-// output component over two threads (interleaved blocks, more warps for the
-// same staged tile) made the 64^3 Newton step slower (224 vs 206 ms).
-#ifndef SX_SPMV_ROWS
-#define SX_SPMV_ROWS 32
-#endif
-static constexpr int kSpmvRows = SX_SPMV_ROWS;        // block rows per tile
-static constexpr int kSpmvThreads = 3 * kSpmvRows;    // one thread per output component
-// bytes of staged column ids and values: up to ~20 blocks per row (values in
-// the value type), 1 KB granules; rows with more fall back to direct loads
-static constexpr int kSpmvSmemCols = ((kSpmvRows * 4 * 1024 / 48) + 1023) / 1024 * 1024;
-template <typename VT>
-__host__ __device__ constexpr int spmv_smem_vals()
+__global__ void k_sell_cols(const int* __restrict__ row_ptr, const int* __restrict__ col,
+                            int64_t N, const int* __restrict__ sell_ptr, int* __restrict__ sell_col)
 {
-    return ((kSpmvRows * (sizeof(VT) == 8 ? 56 : 28) * 1024 / 48) + 1023) / 1024 * 1024;
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // 32 s + lane
+    if (r >= 32 * ((N + 31) / 32)) return;
+    const int64_t s = r >> 5;
+    const int lane = (int)(r & 31);
+    const int k0 = sell_ptr[s], w = sell_ptr[s + 1] - k0;
+    const bool real = r < N;
+    const int b = real ? row_ptr[r] : 0, len = real ? row_ptr[r + 1] - b : 0;
+    const int own = real ? (int)r : (int)(32 * s);
+    for (int k = 0; k < w; ++k)
+        sell_col[((int64_t)(k0 + k) << 5) + lane] = k < len ? col[b + k] : own;
 }
+
+cudaError_t launch_sell_widths(const int* row_ptr, int64_t N, int* widths, cudaStream_t s)
+{
+    const int64_t nsl = (N + 31) / 32;
+    if (!nsl) return cudaSuccess;
+    k_sell_widths<<<(unsigned)((nsl + 255) / 256), 256, 0, s>>>(row_ptr, N, widths);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sell_cols(const int* row_ptr, const int* col, int64_t N, const int* sell_ptr,
+                             int* sell_col, cudaStream_t s)
+{
+    const int64_t nr = 32 * ((N + 31) / 32);
+    if (!nr) return cudaSuccess;
+    k_sell_cols<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(row_ptr, col, N, sell_ptr, sell_col);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ SpMV
+// q = A p_new over the sliced copy of A, with the p.q partials. A tile is
+// four slices (128 block rows, four warps); lane l of warp w takes block
+// row start + 32 w + l and its three output components, as three chains of
+// fused multiply-adds over the row's blocks in column order (on GB300 the
+// FP64 SpMV is bound by the FP64 pipe before HBM: 9 FMA per 76-byte block,
+// the minimum). The matrix is read once, with evict-first loads so that the
+// gathered direction (L2-resident, ~7 MB per million rows) stays cached.
+static constexpr int kSpmvSlices = 4;
+static constexpr int kSpmvRows = 32 * kSpmvSlices;   // block rows per tile
+static constexpr int kSpmvThreads = kSpmvRows;       // one thread per block row
 __device__ __forceinline__ double fma_vt(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_vt(float a, float b, float c) { return fmaf(a, b, c); }
-static constexpr long kWaitLimit = 1L << 24;          // bounded mbarrier wait
 
 template <typename VT>
 __global__ void __launch_bounds__(kSpmvThreads)
 k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part,
        const int* tbeg, const int* tend)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar;
     __shared__ double sh[1][kSpmvThreads];
-    __shared__ int s_mode;   // 1: staged in shared memory, 0: direct loads
-    __shared__ long s_vofs, s_cofs;
     const int ti = blockIdx.x;
     const Tile T = tiles[ti];
     const SceneDev& S = scenes[T.scene];
-    const bool live = scene_live(S) && !S.sc->pcg_done;
-    const VT* vals = (sizeof(VT) == 8) ? (const VT*)S.vals64 : (const VT*)S.vals32;
-    const int64_t r0 = T.start, r1 = T.start + T.count;
-    if (threadIdx.x == 0) {
-        s_mode = 0;
-        if (live) {
-            const int64_t k0 = S.row_ptr[r0], k1 = S.row_ptr[r1];
-            // 16-byte aligned windows containing the tile's value and column
-            // segments (the allocations are padded for the rounded-up end)
-            const long vb0 = (long)(k0 * 9 * (int64_t)sizeof(VT)) & ~15L;
-            const long vb1 = ((long)(k1 * 9 * (int64_t)sizeof(VT)) + 15L) & ~15L;
-            const long cb0 = (long)(k0 * 4) & ~15L;
-            const long cb1 = ((long)(k1 * 4) + 15L) & ~15L;
-            if (SX_SPMV_STAGE && vb1 - vb0 <= spmv_smem_vals<VT>() && cb1 - cb0 <= kSpmvSmemCols &&
-                k1 > k0) {
-                s_mode = 1;
-                s_vofs = vb0;
-                s_cofs = cb0;
-                mbar_init(&bar, 1);
-                mbar_expect_tx(&bar, (unsigned)((vb1 - vb0) + (cb1 - cb0)));
-                bulk_g2s(smem, (const unsigned char*)vals + vb0, (unsigned)(vb1 - vb0), &bar);
-                bulk_g2s(smem + spmv_smem_vals<VT>(), (const unsigned char*)S.col + cb0,
-                         (unsigned)(cb1 - cb0), &bar);
-            }
-        }
-    }
-    __syncthreads();
-    const int mode = s_mode;
-    if (mode == 1) {
-        long it = 0;
-        while (!mbar_try_wait(&bar, 0) && ++it < kWaitLimit) {
-        }
-        if (it >= kWaitLimit) {
-            // the copy did not complete in time: report it through the
-            // scene's PCG status (the scene's last tile then stops its PCG),
-            // wait (bounded) once more so that no write lands after exit, and
-            // count the tile with a zero partial
-            if (threadIdx.x == 0) S.sc->pcg_status = 3;
-            long it2 = 0;
-            while (!mbar_try_wait(&bar, 0) && ++it2 < kWaitLimit) {
-            }
-            const double z[1] = {0.0};
-            double tot[1];
-            if (last_tile_sums<1, kSpmvThreads>(z, sh, part, ti, &S.sc->cnt_spmv, tbeg[T.scene],
-                                                tend[T.scene], tot) &&
-                threadIdx.x == 0) {
-                S.sc->pcg_done = 1;
-                S.sc->pcg_alpha = 0.0;
-            }
-            return;
-        }
-    }
+    if (!scene_live(S) || S.sc->pcg_done) return;   // the same for every tile of the scene
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double* pn = par ? S.p0 : S.p1;
     double v = 0.0;
-    const int lr = threadIdx.x / 3, ci = threadIdx.x - 3 * lr;
-    if (live && lr < T.count) {
-        const int64_t r = r0 + lr;
-        const double* pn = par ? S.p0 : S.p1;
-        double q;
-        if (S.pinned[r]) {
-            q = pn[3 * r + ci];
-        } else {
-            VT acc = VT(0);
-            const int b = S.row_ptr[r], e = S.row_ptr[r + 1];
-            // the gathered direction: p itself (FP64) or its float copy (FP32)
-            const VT* pg = (sizeof(VT) == 8) ? (const VT*)pn : (const VT*)S.p32;
-            const VT* vs = mode ? (const VT*)(smem + ((long)b * 9 * (long)sizeof(VT) - s_vofs))
-                                : vals + 9 * (int64_t)b;
-            const int* cs = mode ? (const int*)(smem + spmv_smem_vals<VT>() + ((long)b * 4 - s_cofs))
-                                 : S.col + b;
-            // p is exactly zero on pinned DOFs (their r, z and p stay 0), so
-            // pinned columns drop out without a test in the loop
-#pragma unroll 4
-            for (int k = 0; k < e - b; ++k) {
-                const int c = cs[k];
-                const VT* B = vs + 9 * k + 3 * ci;
-                // a chain of three fused multiply-adds: the minimum FP64
-                // instruction count per block row
-                acc = fma_vt(B[0], pg[3 * (int64_t)c], acc);
-                acc = fma_vt(B[1], pg[3 * (int64_t)c + 1], acc);
-                acc = fma_vt(B[2], pg[3 * (int64_t)c + 2], acc);
-            }
-            q = (double)acc;
+    if (32 * warp < T.count) {
+        // tiles start at multiples of 128 rows: warp w owns slice start/32 + w
+        const int64_t sl = (T.start >> 5) + warp;
+        const int k0 = S.sell_ptr[sl], w = S.sell_ptr[sl + 1] - k0;
+        const VT* vs = (sizeof(VT) == 8 ? (const VT*)S.sell_v64 : (const VT*)S.sell_v32) +
+                       (int64_t)k0 * 288 + lane;
+        const int* cs = S.sell_col + ((int64_t)k0 << 5) + lane;
+        // the gathered direction: p itself (FP64) or its float copy (FP32)
+        const VT* pg = (sizeof(VT) == 8) ? (const VT*)pn : (const VT*)S.p32;
+        VT a0 = VT(0), a1 = VT(0), a2 = VT(0);
+#pragma unroll 2
+        for (int k = 0; k < w; ++k) {
+            const int64_t c = 3 * (int64_t)__ldcs(cs + 32 * k);
+            const VT x0 = __ldg(pg + c), x1 = __ldg(pg + c + 1), x2 = __ldg(pg + c + 2);
+            const VT* B = vs + (int64_t)288 * k;
+            a0 = fma_vt(__ldcs(B), x0, a0);
+            a0 = fma_vt(__ldcs(B + 32), x1, a0);
+            a0 = fma_vt(__ldcs(B + 64), x2, a0);
+            a1 = fma_vt(__ldcs(B + 96), x0, a1);
+            a1 = fma_vt(__ldcs(B + 128), x1, a1);
+            a1 = fma_vt(__ldcs(B + 160), x2, a1);
+            a2 = fma_vt(__ldcs(B + 192), x0, a2);
+            a2 = fma_vt(__ldcs(B + 224), x1, a2);
+            a2 = fma_vt(__ldcs(B + 256), x2, a2);
         }
-        S.q[3 * r + ci] = q;
-        v = pn[3 * r + ci] * q;
+        if ((int)threadIdx.x < T.count) {
+            const int64_t r = T.start + threadIdx.x;
+            const double q0 = (double)a0, q1 = (double)a1, q2 = (double)a2;
+            S.q[3 * r] = q0;
+            S.q[3 * r + 1] = q1;
+            S.q[3 * r + 2] = q2;
+            v = pn[3 * r] * q0 + pn[3 * r + 1] * q1 + pn[3 * r + 2] * q2;
+        }
     }
-    if (!live) return;   // every tile of the scene sees the same state
     const double vv[1] = {v};
     double pq[1];
     if (last_tile_sums<1, kSpmvThreads>(vv, sh, part, ti, &S.sc->cnt_spmv, tbeg[T.scene],
@@ -440,10 +404,7 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
         threadIdx.x == 0) {
         SceneScal* sc = S.sc;
         sc->pq = pq[0];
-        if (sc->pcg_status == 3) {
-            sc->pcg_done = 1;
-            sc->pcg_alpha = 0.0;
-        } else if (!(pq[0] > 0.0) || !isfinite(pq[0])) {   // not a descent system: stop
+        if (!(pq[0] > 0.0) || !isfinite(pq[0])) {   // not a descent system: stop
             sc->pcg_done = 1;
             sc->pcg_status = 1;
             sc->pcg_alpha = 0.0;
@@ -455,37 +416,17 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
 
 int spmv_rows_per_tile() { return kSpmvRows; }
 
-void prepare_spmv()
-{
-    // the shared-memory opt-in is per device; contexts on several host
-    // threads may reach this concurrently (setting it twice is harmless)
-    static std::atomic<unsigned long long> attr_done{0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
-    if (!bit || !(attr_done.load(std::memory_order_acquire) & bit)) {
-        cudaFuncSetAttribute(k_spmv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             spmv_smem_vals<float>() + kSpmvSmemCols);
-        cudaFuncSetAttribute(k_spmv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             spmv_smem_vals<double>() + kSpmvSmemCols);
-        attr_done.fetch_or(bit, std::memory_order_release);
-    }
-}
-
 cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int ntiles,
                            int precision, int parity, double* part, const int* tbeg,
                            const int* tend, cudaStream_t s)
 {
     if (!ntiles) return cudaSuccess;
-    const int smem64 = spmv_smem_vals<double>() + kSpmvSmemCols;
-    const int smem32 = spmv_smem_vals<float>() + kSpmvSmemCols;
-    prepare_spmv();
     if (precision == SX_FP32)
-        k_spmv<float><<<ntiles, kSpmvThreads, smem32, s>>>(scenes, row_tiles, ntiles, parity, part,
-                                                           tbeg, tend);
+        k_spmv<float><<<ntiles, kSpmvThreads, 0, s>>>(scenes, row_tiles, ntiles, parity, part,
+                                                      tbeg, tend);
     else
-        k_spmv<double><<<ntiles, kSpmvThreads, smem64, s>>>(scenes, row_tiles, ntiles, parity,
-                                                            part, tbeg, tend);
+        k_spmv<double><<<ntiles, kSpmvThreads, 0, s>>>(scenes, row_tiles, ntiles, parity, part,
+                                                       tbeg, tend);
     return cudaGetLastError();
 }
 
@@ -657,13 +598,11 @@ struct NodeChain {
 
 cudaError_t add_pcg_chunk_nodes(cudaGraph_t graph, const PcgChunkArgs& a)
 {
-    prepare_spmv();
     NodeChain c{graph};
     const bool f32 = a.precision == SX_FP32;
     const void* pdir = f32 ? (const void*)k_pcg_pdir<true> : (const void*)k_pcg_pdir<false>;
     const void* spmv = f32 ? (const void*)k_spmv<float> : (const void*)k_spmv<double>;
-    const unsigned smem = (unsigned)(kSpmvSmemCols + (f32 ? spmv_smem_vals<float>()
-                                                          : spmv_smem_vals<double>()));
+    const unsigned smem = 0;
     const unsigned spmv_threads = kSpmvThreads;
     // argument values must outlive each cudaGraphAddKernelNode call only
     const SceneDev* scenes = a.scenes;
@@ -747,6 +686,25 @@ cudaError_t launch_accept(const SceneDev* scenes, const Tile* node_tiles, int nt
 {
     if (!ntiles) return cudaSuccess;
     k_accept<<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles);
+    return cudaGetLastError();
+}
+
+// a failed step is not taken: x back to the start of the step
+__global__ void k_restore(const SceneDev* scenes, const Tile* tiles, int ntiles)
+{
+    const Tile T = tiles[blockIdx.x];
+    const SceneDev& S = scenes[T.scene];
+    if (!scene_live(S) || (int)threadIdx.x >= T.count) return;
+    const int64_t n = T.start + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) S.x[3 * n + i] = S.x_start[3 * n + i];
+}
+
+cudaError_t launch_restore(const SceneDev* scenes, const Tile* node_tiles, int ntiles,
+                           cudaStream_t s)
+{
+    if (!ntiles) return cudaSuccess;
+    k_restore<<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles);
     return cudaGetLastError();
 }
 

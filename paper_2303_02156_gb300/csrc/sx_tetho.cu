@@ -1,5 +1,5 @@
 // sx_tetho.cu -- rest precompute and host tables of the high-order Lagrange
-// tets (§7.2 Eq. fem_final; App. A shape functions): reference shape
+// tets (§6.2 Eq. 12; App. A shape functions): reference shape
 // gradients at the quadrature points, J0^-1 and w det J0 per element and
 // point, and the cover of an element's node pairs by 4-node sub-stencils
 // through which the fixed-pattern assembly takes its blocks.

@@ -157,8 +157,8 @@ def test_mixed_full_size_sampled_rows(ctx, mixed, precision):
                 pt={"pairs": w["pairs"], "dhat": w["dhat"], "kappa": w["kappa"]})
 
 
-@pytest.mark.gpu
-def test_batched_512_newton_step(ctx):
+@pytest.fixture(scope="module")
+def batch512(ctx):
     from paper_2303_02156_gb300.scene import Scene
     boxes = scenes.batch_boxes(512)
     sc = []
@@ -169,6 +169,26 @@ def test_batched_512_newton_step(ctx):
         s.set_gravity((0.0, 0.0, -9.81))
         s.finalize()
         sc.append(s)
+    yield boxes, sc
+    for s in sc:
+        s.close()
+
+
+def _oracle_step(b, dt):
+    T = b["tets"].shape[0]
+    snh, mass, _ = orc.snh_scene_inputs(b["X"], b["tets"], np.full(T, b["E"]),
+                                        np.full(T, b["nu"]), 1000.0)
+    osc = orc.Scene(b["X"].shape[0], mass=mass, snh=snh, pinned=b["pinned"])
+    xo, _, st, _ = osc.newton_step(b["X"], np.zeros_like(b["X"]), dt)
+    assert st == 0
+    return xo
+
+
+@pytest.mark.gpu
+def test_batched_512_newton_step(ctx, batch512):
+    boxes, sc = batch512
+    for s, b in zip(sc, boxes):
+        s.set_state(x=b["X"], v=np.zeros_like(b["X"]))
     dt = 0.01
     arr = (C.c_void_p * len(sc))(*[s.h.value for s in sc])
     reps = (sx.sx_step_report * len(sc))()
@@ -180,12 +200,7 @@ def test_batched_512_newton_step(ctx):
     # small scenes: the oracle's Newton step (item-10 tolerance of a step)
     for k in np.argsort(sizes)[:3]:
         b = boxes[k]
-        T = b["tets"].shape[0]
-        snh, mass, _ = orc.snh_scene_inputs(b["X"], b["tets"], np.full(T, b["E"]),
-                                            np.full(T, b["nu"]), 1000.0)
-        osc = orc.Scene(b["X"].shape[0], mass=mass, snh=snh, pinned=b["pinned"])
-        xo, _, st, _ = osc.newton_step(b["X"], np.zeros_like(b["X"]), dt)
-        assert st == 0
+        xo = _oracle_step(b, dt)
         ref = np.abs(xo - b["X"]).max()
         assert np.abs(xb[k] - xo).max() <= 1e-8 * ref + 1e-12, k
     # sampled scenes alone (the largest, the median, a small one): bitwise
@@ -197,5 +212,32 @@ def test_batched_512_newton_step(ctx):
         rc, r = sc[k].newton_step(dt, newton_tol=1e-8, pcg_tol=1e-10)
         assert rc == sx.SX_OK
         assert np.array_equal(sc[k].get_state()[0], xb[k]), k
-    for s in sc:
-        s.close()
+
+
+@pytest.mark.gpu
+def test_batched_512_newton_step_fp32(ctx, batch512):
+    """The FP32 form of the batched step (FP32 element math, BSR values and
+    SpMV; FP64 projection, norms, dots and energy sums) at its Newton and PCG
+    tolerance 1e-6, against the FP64 oracle's step: displacement error within
+    1e-5 of the displacement, on the three smallest scenes and one of median
+    size."""
+    boxes, sc = batch512
+    for s, b in zip(sc, boxes):
+        s.set_state(x=b["X"], v=np.zeros_like(b["X"]))
+    dt = 0.01
+    arr = (C.c_void_p * len(sc))(*[s.h.value for s in sc])
+    reps = (sx.sx_step_report * len(sc))()
+    o = sx.newton_opts(newton_tol=1e-6, pcg_tol=1e-6, precision=sx.SX_FP32)
+    rc = sx.sx_newton_step_batch(ctx.h, arr, len(sc), dt, C.byref(o), reps, None)
+    assert rc == sx.SX_OK, [r.status for r in reps if r.status != 0][:5]
+    sizes = np.array([b["tets"].shape[0] for b in boxes])
+    order = np.argsort(sizes)
+    worst = 0.0
+    for k in list(order[:3]) + [order[len(order) // 2]]:
+        b = boxes[k]
+        xo = _oracle_step(b, dt)
+        ref = np.abs(xo - b["X"]).max()
+        err = np.abs(sc[k].get_state()[0] - xo).max()
+        worst = max(worst, err / ref)
+        assert err <= 1e-5 * ref, (k, err, ref)
+    print(f"FP32 batched step vs FP64 oracle: worst relative displacement error {worst:.2e}")

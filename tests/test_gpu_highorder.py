@@ -1,4 +1,4 @@
-"""High-order Lagrange tets (§7.2 Eq. fem_final; 10- and 20-node SNH
+"""High-order Lagrange tets (§6.2 Eq. 12; 10- and 20-node SNH
 elements with a quadrature sum) through the C ABI against the FP64 oracle:
 the assembled energy, gradient and BSR Hessian (the oracle's element
 matrices assembled densely), with and without the per-point projection, in

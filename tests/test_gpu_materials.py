@@ -1,4 +1,4 @@
-"""The other tet4 densities (§7.1 "Non-linear material models", App. B:
+"""The other tet4 densities (§6.1 "Non-Linear Material Models", App. B:
 Neo-Hookean, St. Venant-Kirchhoff, fixed co-rotational, ARAP with a volume
 term; lagged rotations for the last two) through the C ABI against the
 FP64 oracle, which differentiates each density by forward-mode arithmetic.

@@ -121,3 +121,65 @@ def test_lanes_fixed_after_first_submit(ctx):
     assert sx.sx_server_set_lanes(srv.h, 2, b) == sx.SX_EORDER
     assert srv.drain(60000.0) == sx.SX_OK
     srv.close()
+
+
+def _oracle_trajectory(m, E, nu, steps, dt, g, forcing):
+    """The oracle's backward-Euler steps (§3 Eqs. 2-3) of one request's
+    scene, with the same Newton and PCG options as the server."""
+    from oracle import oracle as orc
+    T = m["tets"].shape[0]
+    Ev = np.full(T, E); nuv = np.full(T, nu)
+    snh, mass, bad = orc.snh_scene_inputs(m["X"], m["tets"], Ev, nuv, 1000.0)
+    assert bad == 0
+    sc = orc.Scene(m["X"].shape[0], mass=mass, snh=snh, pinned=m["pinned"])
+    x = m["X"].copy(); v = np.zeros_like(x)
+    for _ in range(steps):
+        x, v, st, _ = sc.newton_step(x, v, dt, gravity=g, forcing=forcing)
+        assert st == 0
+    return x, v
+
+
+@pytest.mark.gpu
+def test_served_results_match_oracle_with_forcing_sequence(ctx):
+    """Every served request of a staggered mix, run with the forcing-sequence
+    PCG tolerance the serving bench uses (§7.2 solver paragraph, as read),
+    equals its own alone run bit for bit and the oracle's three steps within
+    the Newton-step tolerance: |x - x*| <= 1e-8 max|x* - X| + 1e-12 and the
+    same for v scaled by 1/dt (v = (x - x_t)/dt)."""
+    from paper_2303_02156_gb300.scene import Scene, Server
+    reqs = _requests(6, seed=7)
+    steps, dt, g = 3, 0.01, (0.0, 0.0, -9.81)
+    alone = []
+    for m, E, nu in reqs:
+        s = Scene(ctx, m["X"])
+        s.add_snh(m["tets"], E, nu, 1000.0)
+        s.set_pinned(m["pinned"])
+        s.set_gravity(g)
+        s.finalize()
+        for _ in range(steps):
+            s.newton_step(dt, forcing=1)
+        alone.append(s.get_state())
+        s.close()
+    srv = Server(ctx, 8 << 30, forcing=1)
+    ids = []
+    for k, (m, E, nu) in enumerate(reqs):
+        ids.append(srv.submit(m["X"], m["tets"], E, nu, 1000.0, pinned=m["pinned"], gravity=g,
+                              n_steps=steps, dt=dt))
+        if k == 2:
+            time.sleep(0.05)
+    assert srv.drain(120000.0) == sx.SX_OK
+    done = {c["req_id"]: c for c in srv.poll()}
+    worst = 0.0
+    for rid, (xa, va), (m, E, nu) in zip(ids, alone, reqs):
+        assert done[rid]["status"] == sx.SX_OK and done[rid]["steps"] == steps, done[rid]["error"]
+        x, v = srv.result(rid)
+        assert np.array_equal(x, xa) and np.array_equal(v, va)
+        xo, vo = _oracle_trajectory(m, E, nu, steps, dt, g, True)
+        ref = np.abs(xo - m["X"]).max()
+        tol = 1e-8 * ref + 1e-12
+        dxo = np.abs(x - xo).max()
+        worst = max(worst, dxo / ref)
+        assert dxo <= tol, (rid, dxo, ref)
+        assert np.abs(v - vo).max() <= tol / dt
+    srv.close()
+    print(f"served vs oracle: worst max|x - x*| / max|x* - X| = {worst:.2e}")

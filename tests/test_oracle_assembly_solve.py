@@ -167,3 +167,32 @@ def test_newton_c1_converges_monotone_and_keeps_pins():
     assert all(b <= a for a, b in zip(energies, energies[1:]))
     # the cube sags: free nodes move down on average
     assert (x[:, 2] - X[:, 2])[sc.pinned_mask == 0].mean() < 0
+
+
+def test_newton_forcing_sequence_solves_inexactly_and_converges():
+    # forcing option (§7.2 solver paragraph, as read: PCG tolerance
+    # max(pcg_tol, min(1/2, sqrt(|g_k|/|g_0|)))): the first Newton direction
+    # is an inexact solve (relative residual of the dense system at x0 at most
+    # 1/2, far above the fixed 1e-10), and the step still ends at a point whose
+    # free gradient meets the Newton tolerance, with fewer PCG iterations.
+    m = scenes.kuhn_box(4, 4, 4, h=0.25, seed=1)
+    sc, snh = _snh_scene(m, young=3e5)
+    X = m["X"]; N = X.shape[0]; dt = 0.01; g = np.array([0, 0, -9.81])
+    v0 = np.zeros_like(X); v0[:, 0] = 0.5; v0[m["pinned"]] = 0.0
+    xt = X + dt * v0 + dt * dt * g
+    free = np.repeat(sc.pinned_mask == 0, 3)
+    E0, g0, vals0, _ = sc.eval(X, xt=xt, dt=dt, level=2, project=True)
+    H0 = _dense_from_bsr(sc.row_ptr, sc.col, vals0.reshape(-1, 3, 3), N)
+    Hf = H0[np.ix_(free, free)]
+    x1, *_ = sc.newton_step(X, v0, dt, gravity=g, max_newton=1, forcing=True)
+    d = (x1 - X).ravel()[free]
+    rel = np.linalg.norm(Hf @ d + g0[free]) / np.linalg.norm(g0[free])
+    assert 1e-6 < rel <= 0.5 * (1 + 1e-9)
+    xf, vf, st, rf = sc.newton_step(X, v0, dt, gravity=g, forcing=True)
+    xe, ve, st2, re_ = sc.newton_step(X, v0, dt, gravity=g)
+    assert st == 0 and st2 == 0
+    _, gf, _, _ = sc.eval(xf, xt=xt, dt=dt, level=1)
+    assert np.linalg.norm(gf[free]) <= 1e-8 * rf["g0_norm"] * (1 + 1e-7)
+    assert rf["pcg_iters_total"] < re_["pcg_iters_total"]
+    # both end within the Newton tolerance of the same solution
+    assert np.abs(xf - xe).max() <= 1e-6 * np.abs(xe - X).max()

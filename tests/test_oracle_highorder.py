@@ -1,4 +1,4 @@
-"""Pins of the oracle's high-order Lagrange tets (§7.2 Eq. fem_final; App. A
+"""Pins of the oracle's high-order Lagrange tets (§6.2 Eq. 12; App. A
 shape functions): 10-node quadratic and 20-node cubic SNH elements with a
 quadrature sum.
 

@@ -1,5 +1,5 @@
-"""Pins of the oracle's other tet4 densities (§7.1 "Non-linear material
-models", App. B): Neo-Hookean, St. Venant-Kirchhoff, fixed co-rotational
+"""Pins of the oracle's other tet4 densities (§6.1 "Non-Linear Material
+Models", App. B): Neo-Hookean, St. Venant-Kirchhoff, fixed co-rotational
 and ARAP with a volume term, the last two with a lagged rotation R.
 
 Fixed by: the small-strain limit of linear elasticity (textbook stiffness,

@@ -201,3 +201,40 @@ def test_generator_tets_positive_and_mass_sums_to_total():
     # the jittered cube keeps the volume of the unit cube (only boundary
     # nodes change it, and only slightly)
     assert V.sum() == pytest.approx(1.0, rel=0.05)
+
+
+def _snh_psi_plain(F, mu, lam):
+    """App. B's Stable Neo-Hookean density written as printed (with the
+    re-parameterized mu', lambda' passed in): psi = mu/2 (Ic - 3)
+    + lambda/2 (J - alpha)^2 - mu/2 ln(Ic + 1), alpha = 1 + mu/lambda
+    - mu/(4 lambda). Plain numpy, no cancellation-free rewriting."""
+    Ic = np.sum(F * F)
+    J = np.linalg.det(F)
+    alpha = 1.0 + mu / lam - mu / (4.0 * lam)
+    return 0.5 * mu * (Ic - 3.0) + 0.5 * lam * (J - alpha) ** 2 - 0.5 * mu * np.log(Ic + 1.0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("inverted", [False, True])
+def test_energy_equals_plain_definition_at_large_strain(seed, inverted):
+    # E = V (psi(F) - psi(I)) at strains of order one, including inverted
+    # tets (J < 0). At large strain the plain form of App. B has no
+    # cancellation, so it checks the value of the oracle's rewritten energy
+    # independently of that rewriting.
+    rng = np.random.default_rng(100 + seed)
+    X = _tet(seed)
+    F = np.eye(3) + rng.uniform(-0.6, 0.6, (3, 3))
+    if (np.linalg.det(F) < 0) != inverted:
+        F[:, 0] *= -1.0
+    assert (np.linalg.det(F) < 0) == inverted
+    assert abs(np.linalg.det(F)) > 0.05
+    young = 10 ** rng.uniform(4, 6); nu = rng.uniform(0.2, 0.45)
+    mus, lams = orc.snh_lame(young, nu)
+    mu, lam = mus[0], lams[0]
+    x = X @ F.T   # x_a = F X_a, so the deformation gradient is F
+    Dminv, V = _elem(X, mu, lam)
+    E, _, _ = orc.snh_element(x, Dminv, V, mu, lam)
+    Eplain = V * (_snh_psi_plain(F, mu, lam) - _snh_psi_plain(np.eye(3), mu, lam))
+    assert abs(E - Eplain) <= 1e-12 * V * mu
+    # and it is not trivially small: a dropped term would show
+    assert abs(Eplain) > 1e-2 * V * mu
