@@ -59,7 +59,8 @@ def parse():
     p.add_argument("--no-newton", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=6.0)
-    p.add_argument("--serve-requests", type=int, default=48)
+    p.add_argument("--serve-requests", type=int, default=2000)
+    p.add_argument("--serve-lane-cap", type=int, default=32)
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batch-scenes", type=int, default=512)
@@ -96,6 +97,17 @@ def max_over_ranks(x, dist=None):
     dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
     t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, dist=None):
+    """The sum of every rank's ``x``; ``x`` itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -238,13 +250,18 @@ def clamp_traffic_per_element():
 
 
 # ------------------------------------------------------------------ serving
-def run_serving(ctx, n_req, seed, rate=200.0, steps=10, dt=0.01, budget=150e9):
-    """Poisson arrivals (mean `rate` req/s) of `n_req` scene requests, tet
-    count log-uniform in [1e3, 5e5] (grid-split boxes, aspect <= 8:1, h = 2 cm,
-    per-scene E ~ logU[1e4, 1e6] Pa, nu ~ U[0.2, 0.45]), each asking for
-    `steps` backward-Euler steps; admission by memory into `budget` bytes."""
+def run_serving(ctx, n_req, seed, rate=200.0, steps=10, dt=0.01, budget=150e9, lane_cap=0,
+                rank=0, world=1, dist=None, total=2000):
+    """Poisson arrivals (mean `rate` req/s) of the first `n_req` of a
+    `total`-request stream of scene requests, tet count log-uniform in
+    [1e3, 5e5] (grid-split boxes, aspect <= 8:1, h = 2 cm, per-scene
+    E ~ logU[1e4, 1e6] Pa, nu ~ U[0.2, 0.45]), each asking for `steps`
+    backward-Euler steps; admission by memory into `budget` bytes per GPU;
+    `lane_cap`: most scenes resident per lane (0: no limit). On N ranks each
+    request goes, in arrival order, to the rank with the least footprint
+    routed so far; each rank serves its own requests."""
     import numpy as np
-    from paper_2303_02156_gb300 import scenes
+    from paper_2303_02156_gb300 import placement, scenes
     from paper_2303_02156_gb300.scene import Server
     rng = scenes.rng_for(seed)
     reqs, t = [], 0.0
@@ -256,11 +273,18 @@ def run_serving(ctx, n_req, seed, rate=200.0, steps=10, dt=0.01, budget=150e9):
         E = float(np.exp(rng.uniform(np.log(1e4), np.log(1e6))))
         nu = float(rng.uniform(0.2, 0.45))
         reqs.append((t, m, E, nu))
+    where = placement.route_stream([scene_footprint(m) for _, m, _, _ in reqs], world)
+    mine = placement.mine(where, rank)
     # Newton tolerance 1e-8 relative; PCG with the forcing-sequence tolerance
     # the paper's solver uses (§7.2)
     srv = Server(ctx, int(budget), forcing=1)
+    if lane_cap:
+        srv.set_lane_cap(lane_cap)
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
-    for (ta, m, E, nu) in reqs:
+    for i in mine:
+        ta, m, E, nu = reqs[i]
         wait = ta - (time.perf_counter() - t0)
         if wait > 0:
             time.sleep(wait)
@@ -268,20 +292,35 @@ def run_serving(ctx, n_req, seed, rate=200.0, steps=10, dt=0.01, budget=150e9):
     srv.drain(3.6e6)
     wall = time.perf_counter() - t0
     st = srv.stats()
-    comp = srv.poll(n_req + 8)
+    comp = srv.poll(len(mine) + 8)
     ok = sum(1 for c in comp if c["status"] == 0)
     for c in comp:
         srv.result(c["req_id"])
     srv.close()
     tets = [m["tets"].shape[0] for _, m, _, _ in reqs]
-    return {"requests": n_req, "completed_ok": ok, "steps_per_request": steps, "dt": dt,
-            "arrival_rate_per_s": rate, "tets_total": int(sum(tets)), "tets_max": int(max(tets)),
-            "step_p50_ms": st["step_p50_ms"], "step_p99_ms": st["step_p99_ms"],
-            "request_p50_ms": st["request_p50_ms"], "request_p99_ms": st["request_p99_ms"],
-            "elements_per_s": st["element_steps"] / wall, "ticks": st["ticks"],
-            "peak_bytes": st["peak_bytes"], "budget_bytes": int(budget),
-            "newton_tol": 1e-8, "pcg": "forcing sequence min(1/2, sqrt(|g|/|g0|))",
-            "sample": "first %d requests of the 2,000-request stream" % n_req}
+    offered = sum(tets) * steps / reqs[-1][0]   # element-steps/s the stream asks for
+    job_wall = max_over_ranks(wall, dist)
+    job_es = sum_over_ranks(st["element_steps"], dist)
+    out = {"requests": n_req, "completed_ok": int(sum_over_ranks(ok, dist)),
+           "steps_per_request": steps, "dt": dt,
+           "arrival_rate_per_s": rate, "tets_total": int(sum(tets)), "tets_max": int(max(tets)),
+           "step_p50_ms": st["step_p50_ms"], "step_p99_ms": st["step_p99_ms"],
+           "request_p50_ms": st["request_p50_ms"], "request_p99_ms": st["request_p99_ms"],
+           "elements_per_s": job_es / job_wall, "wall_s": job_wall, "ticks": st["ticks"],
+           "offered_element_steps_per_s": offered,
+           "offered_load_ratio": offered / (job_es / job_wall) if job_es else None,
+           "peak_bytes": st["peak_bytes"], "budget_bytes": int(budget),
+           "lane_cap": lane_cap or None,
+           "newton_tol": 1e-8, "pcg": "forcing sequence min(1/2, sqrt(|g|/|g0|))",
+           "sample": ("the whole %d-request stream" % total) if n_req >= total else
+                     ("first %d requests of the %d-request stream" % (n_req, total))}
+    if world > 1:
+        out["placement"] = {"ranks": world, "rule": "each request, in arrival order, to the "
+                            "rank with the least footprint routed so far",
+                            "requests_on_rank0": len(mine),
+                            "step_p99_ms_max_over_ranks": max_over_ranks(st["step_p99_ms"], dist),
+                            "latencies": "step and request percentiles are rank 0's"}
+    return out
 
 
 # ------------------------------------------------------------------ mixed stencils
@@ -527,17 +566,37 @@ def run_high_order(ctx, stream, flush, reps=5):
 
 
 # ------------------------------------------------------------------ batched scenes
-def run_batched(ctx, stream, n_scenes, dt=0.01):
+def scene_footprint(m):
+    from paper_2303_02156_gb300 import sx
+    d = sx.sx_scene_desc()
+    d.n_nodes = m["X"].shape[0]
+    d.n_tets = m["tets"].shape[0]
+    d.n_hinges = 0
+    d.n_pairs = 0
+    d.nnzb_hint = 0
+    b = C.c_int64()
+    sx.sx_scene_footprint(C.byref(d), C.byref(b))
+    return b.value
+
+
+def run_batched(ctx, stream, n_scenes, dt=0.01, rank=0, world=1, dist=None):
     """``n_scenes`` independent Kuhn boxes (tet counts log-uniform in
     [1e3, 2e5], aspect up to 8:1, per-scene materials, bottom layer pinned,
     gravity): one batched E + g + projected H + assembly pass, the same
     scenes evaluated one call each, and one backward-Euler Newton step of all
-    scenes in one batched call, FP64 and FP32."""
+    scenes in one batched call, FP64 and FP32. On N ranks the scenes are
+    placed whole on the ranks (largest footprint first to the least-loaded
+    rank); each rank steps its own, and the job's time is the slowest
+    rank's."""
     import numpy as np
     import torch
-    from paper_2303_02156_gb300 import scenes, sx
+    from paper_2303_02156_gb300 import placement, scenes, sx
     from paper_2303_02156_gb300.scene import Scene
-    boxes = scenes.batch_boxes(n_scenes)
+    boxes_all = scenes.batch_boxes(n_scenes)
+    T_all = int(sum(b["tets"].shape[0] for b in boxes_all))
+    where = placement.place_by_footprint([scene_footprint(b) for b in boxes_all], world)
+    boxes = [boxes_all[i] for i in placement.mine(where, rank)]
+    n_scenes = len(boxes)
     sh = stream.cuda_stream
     sc = []
     for b in boxes:
@@ -548,10 +607,14 @@ def run_batched(ctx, stream, n_scenes, dt=0.01):
         s.finalize()
         sc.append(s)
     T = int(sum(b["tets"].shape[0] for b in boxes))
-    out = {"workload": "%d Kuhn boxes, tets logU[1e3, 2e5], aspect <= 8:1" % n_scenes,
-           "scenes": n_scenes, "tets": T,
-           "tets_min": int(min(b["tets"].shape[0] for b in boxes)),
-           "tets_max": int(max(b["tets"].shape[0] for b in boxes))}
+    out = {"workload": "%d Kuhn boxes, tets logU[1e3, 2e5], aspect <= 8:1" % len(boxes_all),
+           "scenes": len(boxes_all), "tets": T_all,
+           "tets_min": int(min(b["tets"].shape[0] for b in boxes_all)),
+           "tets_max": int(max(b["tets"].shape[0] for b in boxes_all))}
+    if world > 1:
+        out["placement"] = {"ranks": world, "rule": "whole scenes, largest footprint first to "
+                            "the least-loaded rank; no exchange on the data path",
+                            "scenes_on_rank0": n_scenes, "tets_on_rank0": T}
     arr = (C.c_void_p * n_scenes)(*[s.h.value for s in sc])
     for b, s in zip(boxes, sc):
         s.set_state(x=scenes.jitter_state(b["X"], 0.002 * 0.02, seed=7))
@@ -561,33 +624,37 @@ def run_batched(ctx, stream, n_scenes, dt=0.01):
         for _ in range(2):
             ctx.check(sx.sx_eval_batch(ctx.h, arr, n_scenes, sx.SX_EGH, 1, prec, None, sh))
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
         ctx.check(sx.sx_eval_batch(ctx.h, arr, n_scenes, sx.SX_EGH, 1, prec, None, sh))
         torch.cuda.synchronize()
-        tb = time.perf_counter() - t0
+        tb = max_over_ranks(time.perf_counter() - t0, dist)
         t0 = time.perf_counter()
         for s in sc:
             ctx.check(sx.sx_eval(s.h, sx.SX_EGH, 1, prec, None, sh))
         torch.cuda.synchronize()
-        t1 = time.perf_counter() - t0
-        out["eval_" + name] = {"batched_ms": tb * 1e3, "batched_elements_per_s": T / tb,
+        t1 = max_over_ranks(time.perf_counter() - t0, dist)
+        out["eval_" + name] = {"batched_ms": tb * 1e3, "batched_elements_per_s": T_all / tb,
                                "one_call_per_scene_ms": t1 * 1e3,
-                               "one_call_per_scene_elements_per_s": T / t1}
+                               "one_call_per_scene_elements_per_s": T_all / t1}
     xs = {}
     for prec, name, tol in ((sx.SX_FP64, "fp64", 1e-8), (sx.SX_FP32, "fp32", 1e-6)):
         for b, s in zip(boxes, sc):
             s.set_state(x=b["X"], v=np.zeros_like(b["X"]))
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
         reps = (sx.sx_step_report * n_scenes)()
         o = sx.newton_opts(precision=prec, newton_tol=tol, pcg_tol=1e-10 if prec == 0 else 1e-6)
         rc = sx.sx_newton_step_batch(ctx.h, arr, n_scenes, float(dt), C.byref(o), reps, sh)
         torch.cuda.synchronize()
-        t = time.perf_counter() - t0
+        t = max_over_ranks(time.perf_counter() - t0, dist)
         xs[name] = [s.get_state()[0] for s in sc]
         st = [r.status for r in reps]
         out["newton_" + name] = {
-            "status": sx.STATUS_NAMES.get(rc, rc), "ms": t * 1e3, "element_steps_per_s": T / t,
+            "status": sx.STATUS_NAMES.get(rc, rc), "ms": t * 1e3, "element_steps_per_s": T_all / t,
             "scenes_ok": int(sum(1 for v in st if v == 0)),
             "newton_iters_max": int(max(r.newton_iters for r in reps)),
             "pcg_iters_max": int(max(r.pcg_iters for r in reps)), "newton_tol": tol, "dt": dt}
@@ -869,11 +936,24 @@ def main():
     # ---- serving: Poisson stream of scene requests (bounded sample)
     serving = None
     if args.serve_requests > 0:
-        serving = run_serving(ctx, args.serve_requests, seed=5)
+        # the whole stream (its latencies are those of a queue: the stream
+        # asks for more than one GPU serves), the same with a per-lane cap on
+        # resident scenes (shorter ticks: the step-latency lever), and the
+        # first 48 requests alone (the unloaded latencies)
+        serving = run_serving(ctx, args.serve_requests, seed=5, rank=rank, world=world,
+                              dist=dist)
+        if args.serve_lane_cap > 0:
+            serving["lane_cap_run"] = run_serving(ctx, args.serve_requests, seed=5,
+                                                  lane_cap=args.serve_lane_cap, rank=rank,
+                                                  world=world, dist=dist)
+        if args.serve_requests > 48:
+            serving["unloaded_sample"] = run_serving(ctx, 48, seed=5, rank=rank, world=world,
+                                                     dist=dist)
 
     # ---- mixed stencils in one scene, and batched independent scenes
     mixed = None if args.no_mixed else run_mixed(ctx, stream, flush)
-    batched = None if args.no_batched else run_batched(ctx, stream, args.batch_scenes)
+    batched = None if args.no_batched else run_batched(ctx, stream, args.batch_scenes,
+                                                       rank=rank, world=world, dist=dist)
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None

@@ -122,6 +122,15 @@ typedef struct {
 int sx_create(sx_ctx** ctx, const sx_options* opt);
 int sx_destroy(sx_ctx* ctx);
 const char* sx_last_error(sx_ctx* ctx);
+
+/* Fault injection for tests of the failure paths (the paper has no
+ * counterpart): the n-th device allocation that a scene of this context
+ * makes from now on fails as if the device were out of memory (n = 0
+ * disarms). The call that meets it returns SX_ENOMEM and leaves the context
+ * and its other scenes usable; a finalize that fails this way leaves its
+ * scene unfinalized, so it can be retried. Host-side only: no GPU fault is
+ * involved. */
+int sx_inject_alloc_failure(sx_ctx* ctx, int n);
 /* Library build string (arch, version); never NULL. */
 const char* sx_version(void);
 
@@ -574,6 +583,13 @@ int sx_server_create(sx_ctx* ctx, int64_t hbm_budget_bytes, const sx_newton_opts
  * the last lane the rest; NULL if n_lanes == 1). Only before the first
  * submit (else SX_EORDER). Synchronous. */
 int sx_server_set_lanes(sx_server* srv, int n_lanes, const int64_t* bounds);
+/* At most max_resident scenes resident in one lane (0, the default: no
+ * limit other than the memory budget). A lane then admits a waiting request
+ * only when one of its scenes retires: its ticks stay short (lower step
+ * latency for the admitted scenes) at the price of longer queueing (higher
+ * request latency) and smaller batches. May be changed at any time; takes
+ * effect at the lanes' next admissions. */
+int sx_server_set_lane_cap(sx_server* srv, int max_resident);
 /* Copies the spec (the caller's arrays may be freed on return) and queues
  * the request; SX_EBUDGET if its footprint alone exceeds the budget. */
 int sx_server_submit(sx_server* srv, const sx_snh_scene_spec* spec, int n_steps, double dt,

@@ -82,6 +82,9 @@ struct sx_ctx {
     int clamp_threads[2] = {128, 128};
     int elem_bps[2] = {-1, -1};   // -1: as many as fit; 0: one tile per block
     std::string err;
+    // fault injection (sx_inject_alloc_failure): scene allocations left
+    // until one fails; 0 = off
+    int fail_alloc_in = 0;
     int* queue = nullptr;
     // pinned host staging of per-scene scalars and controls, shared by the
     // batches of this context (a context runs one call at a time); grown on
@@ -328,6 +331,10 @@ template <typename T>
 int dalloc(sx_scene* s, T** p, size_t count)
 {
     size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (s->ctx && s->ctx->fail_alloc_in > 0 && --s->ctx->fail_alloc_in == 0) {
+        *p = nullptr;   // an injected failure: as if the pool were exhausted
+        return SX_ENOMEM;
+    }
     if (cudaMallocAsync((void**)p, bytes, s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -736,14 +743,19 @@ int build_sell(sx_scene* s, cudaStream_t st)
 
 int ensure_vals32(sx_ctx* ctx, sx_scene* s)
 {
-    if (s->vals32) return SX_OK;
-    if (dalloc_fin(s, &s->vals32, 9 * (size_t)s->pat.nnzb + 16) != SX_OK ||
-        dalloc_fin(s, &s->p32, 3 * (size_t)s->N + 4) != SX_OK ||
-        dalloc_fin(s, &s->sell_v32, 288 * (size_t)s->sell_steps + 64) != SX_OK)
+    if (s->vals32 && s->p32 && s->sell_v32) return SX_OK;
+    // each array once (a call that failed part-way leaves the others for the
+    // next one)
+    if ((!s->vals32 && dalloc_fin(s, &s->vals32, 9 * (size_t)s->pat.nnzb + 16) != SX_OK) ||
+        (!s->p32 && dalloc_fin(s, &s->p32, 3 * (size_t)s->N + 4) != SX_OK))
         return fail(ctx, SX_ENOMEM, "eval: device allocation failed (FP32 values)");
-    // pad entries (and the lanes past the last row) stay zero
-    CK(cudaMemsetAsync(s->sell_v32, 0, (288 * (size_t)s->sell_steps + 64) * sizeof(float),
-                       s->stream));
+    if (!s->sell_v32) {
+        if (dalloc_fin(s, &s->sell_v32, 288 * (size_t)s->sell_steps + 64) != SX_OK)
+            return fail(ctx, SX_ENOMEM, "eval: device allocation failed (FP32 values)");
+        // pad entries (and the lanes past the last row) stay zero
+        CK(cudaMemsetAsync(s->sell_v32, 0, (288 * (size_t)s->sell_steps + 64) * sizeof(float),
+                           s->stream));
+    }
     s->version++;
     return SX_OK;
 }
@@ -959,6 +971,13 @@ int sx_destroy(sx_ctx* ctx)
 }
 
 const char* sx_last_error(sx_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int sx_inject_alloc_failure(sx_ctx* ctx, int n)
+{
+    if (!ctx || n < 0) return SX_EINVAL;
+    ctx->fail_alloc_in = n;
+    return SX_OK;
+}
 
 int sx_scene_create(sx_ctx* ctx, int64_t n_nodes, const double* X_rest, int64_t stride,
                     void* stream, sx_scene** out)
@@ -1509,6 +1528,14 @@ int sx_set_gravity(sx_scene* s, const double g[3])
     return SX_OK;
 }
 
+}  // extern "C"
+
+namespace {
+void release_finalized(sx_scene* s);
+}  // namespace
+
+extern "C" {
+
 int sx_finalize(sx_scene* s, void* stream)
 {
     if (!s) return SX_EINVAL;
@@ -1549,11 +1576,18 @@ int sx_finalize(sx_scene* s, void* stream)
         dalloc_fin(s, &s->vals64, 9 * (size_t)s->pat.nnzb + 8) || dalloc_fin(s, &s->grad, n3) ||
         dalloc_fin(s, &s->r, n3) || dalloc_fin(s, &s->z, n3) || dalloc_fin(s, &s->p0, n3) ||
         dalloc_fin(s, &s->p1, n3) || dalloc_fin(s, &s->q, n3) ||
-        dalloc_fin(s, &s->Minv, 9 * (size_t)s->N))
+        dalloc_fin(s, &s->Minv, 9 * (size_t)s->N)) {
+        // back to the registered, unfinalized form: finalize can be retried
+        release_finalized(s);
         return fail(ctx, SX_ENOMEM, "finalize: device allocation failed");
+    }
     CK(cudaMemsetAsync(s->grad, 0, n3 * sizeof(double), st));
     CK(cudaMemsetAsync(s->vals64, 0, 9 * (size_t)s->pat.nnzb * sizeof(double), st));
-    if ((rc = build_sell(s, st)) != SX_OK) return rc;
+    if ((rc = build_sell(s, st)) != SX_OK) {
+        const std::string why = ctx->err;
+        release_finalized(s);
+        return fail(ctx, rc, why);
+    }
     CK(cudaStreamSynchronize(st));
     s->finalized = true;
     s->version++;
@@ -1916,12 +1950,25 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     double* qM = nullptr;
     ClampRef* qR = nullptr;
     int* qC = nullptr;
+    // the same two-launch projection as an assembled evaluation: float
+    // eigenvectors, norms and the bins by N-block size
+    float* qX = nullptr;
+    double* qF = nullptr;
+    int* qB = nullptr;
     if (H && project) {
-        CK(cudaMallocAsync((void**)&qM, std::max<int64_t>(b.n, 1) * 45 * sizeof(double), st));
-        CK(cudaMallocAsync((void**)&qR, std::max<int64_t>(b.n, 1) * sizeof(ClampRef), st));
-        CK(cudaMallocAsync((void**)&qC, 2 * sizeof(int), st));
-        CK(cudaMemsetAsync(qC, 0, 2 * sizeof(int), st));
+        const size_t cap = (size_t)std::max<int64_t>(b.n, 1);
+        CK(cudaMallocAsync((void**)&qM, cap * 45 * sizeof(double), st));
+        CK(cudaMallocAsync((void**)&qR, cap * sizeof(ClampRef), st));
+        CK(cudaMallocAsync((void**)&qC, 12 * sizeof(int), st));
+        CK(cudaMemsetAsync(qC, 0, 12 * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&qX, cap * 81 * sizeof(float), st));
+        CK(cudaMallocAsync((void**)&qF, cap * sizeof(double), st));
+        CK(cudaMallocAsync((void**)&qB, cap * 10 * sizeof(int), st));
     }
+    L.clamp_X = qX;
+    L.clamp_fro = qF;
+    L.clamp_bucket = qB;
+    L.clamp_bucket_count = qC ? qC + 2 : nullptr;
     L.clamp_M = qM;
     L.clamp_ref = qR;
     L.clamp_count = qC;
@@ -1941,6 +1988,9 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
         cudaFreeAsync(qM, st);
         cudaFreeAsync(qR, st);
         cudaFreeAsync(qC, st);
+        cudaFreeAsync(qX, st);
+        cudaFreeAsync(qF, st);
+        cudaFreeAsync(qB, st);
     }
     cudaFreeAsync(d_tiles, st);
     if (tmpE) cudaFreeAsync(tmpE, st);

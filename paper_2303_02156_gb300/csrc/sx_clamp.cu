@@ -168,8 +168,13 @@ k_clamp_float(ElemLaunch L)
     L.clamp_bucket[(int64_t)k * cap + pos] = (int)idx;
 }
 
+// resident threads per SM the double part is compiled for (a register cap:
+// 65536 / this); 256 (two blocks of 128) measured best
+#ifndef SX_CLAMP_MINB_THREADS
+#define SX_CLAMP_MINB_THREADS 256
+#endif
 template <typename HT, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, (SX_CLAMP_MINB_THREADS / NT) > 0 ? SX_CLAMP_MINB_THREADS / NT : 1)
 k_clamp_double(ElemLaunch L)
 {
     extern __shared__ __align__(16) double Xs[];   // [81][NT]

@@ -57,6 +57,25 @@ namespace sx {
 #define SX_CLAMP_THETA32 1e-9
 #endif
 
+// The float Jacobi angle only decides how far a rotation goes (every
+// rotation is exactly orthogonal in the precision it is applied in, and the
+// double sweeps correct what the float ones leave), so it is computed with
+// the approximate float division and square root (about 2 ulp) instead of
+// the correctly rounded ones, which are long instruction sequences on the
+// serial chain of a Jacobi sweep.
+#ifndef SX_CLAMP_FAST_F32
+#define SX_CLAMP_FAST_F32 1
+#endif
+__device__ __forceinline__ float jac_div(float a, float b)
+{
+    return SX_CLAMP_FAST_F32 ? __fdividef(a, b) : a / b;
+}
+// sqrt of x >= 1
+__device__ __forceinline__ float jac_sqrt1(float x)
+{
+    return SX_CLAMP_FAST_F32 ? x * rsqrtf(x) : sqrtf(x);
+}
+
 // packed lower-triangle index of (i, j), any order
 __host__ __device__ constexpr int pk(int i, int j)
 {
@@ -188,8 +207,9 @@ __device__ __forceinline__ void jacobi_sweep_f32(float (&A)[45], float (&X)[81])
         for (int q = p + 1; q < 9; ++q) {
             const float apq = A[pk(p, q)], app = A[pk(p, p)], aqq = A[pk(q, q)];
             const bool nz = apq != 0.0f;
-            const float tau = (aqq - app) / (nz ? 2.0f * apq : 1.0f);
-            const float tt = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+            const float tau = jac_div(aqq - app, nz ? 2.0f * apq : 1.0f);
+            const float tt = jac_div(copysignf(1.0f, tau),
+                                     fabsf(tau) + jac_sqrt1(fmaf(tau, tau, 1.0f)));
             const float t = nz ? tt : 0.0f;
             const float c = rsqrtf(fmaf(t, t, 1.0f)), s = t * c;
             A[pk(p, p)] = app - t * apq;
@@ -240,8 +260,9 @@ __device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat&
             if (!__any_sync(live, need)) continue;
             const float fpq = (float)apq;
             const bool nz = fpq != 0.0f;
-            const float tau = (float)(aqq - app) / (nz ? 2.0f * fpq : 1.0f);
-            const float tt = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+            const float tau = jac_div((float)(aqq - app), nz ? 2.0f * fpq : 1.0f);
+            const float tt = jac_div(copysignf(1.0f, tau),
+                                     fabsf(tau) + jac_sqrt1(fmaf(tau, tau, 1.0f)));
             const double t = nz ? (double)tt : 0.0;
             const double c = rsqrt(fma(t, t, 1.0)), s = t * c;
             const double cc = c * c, ss = s * s, cs = c * s;

@@ -80,6 +80,7 @@ struct sx_server {
     std::deque<Request*> pending;
     std::vector<Lane*> lanes;
     std::vector<int64_t> bounds;   // lane i takes n_tets < bounds[i]; the last lane the rest
+    int lane_cap = 0;              // most scenes resident in one lane (0: no limit)
     std::deque<sx_completion> completions;
     std::unordered_map<int64_t, Request*> finished;
     bool stop = false;
@@ -200,6 +201,9 @@ void lane_loop(sx_server* S, Lane* L)
                     ++it;
                     continue;
                 }
+                if (S->lane_cap > 0 &&
+                    (int)(L->active.size() + to_admit.size()) >= S->lane_cap)
+                    break;
                 if (S->in_use + r->footprint > S->budget) break;
                 S->in_use += r->footprint;
                 S->peak = std::max(S->peak, S->in_use);
@@ -344,6 +348,15 @@ int sx_server_create(sx_ctx* ctx, int64_t budget, const sx_newton_opts* opts, sx
         return rc;
     }
     *out = S;
+    return SX_OK;
+}
+
+int sx_server_set_lane_cap(sx_server* S, int max_resident)
+{
+    if (!S || max_resident < 0) return SX_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->lane_cap = max_resident;
+    S->cv.notify_all();
     return SX_OK;
 }
 

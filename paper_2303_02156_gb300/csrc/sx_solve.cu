@@ -246,28 +246,97 @@ __device__ __forceinline__ bool last_tile_sums(const double (&v)[NV], double (*s
     return true;
 }
 
+// The pieces of last_tile_sums for blocks that handle several tiles: the
+// sum of a scene's NV-value tile partials over its tile range [tb, te) in a
+// fixed order (every thread of the block takes part; the result on all).
+template <int NV, int NT>
+__device__ __forceinline__ void scene_tile_sums(double (*sh)[NT], const double* part, int tb,
+                                                int te, double (&out)[NV])
+{
+    double a[4][NV];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) a[j][k] = 0.0;
+    int t = tb + threadIdx.x;
+    for (; t + 3 * NT < te; t += 4 * NT)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) a[j][k] += __ldcg(part + (int64_t)NV * (t + j * NT) + k);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)   // fewer than 4 strides left
+        if (t < te) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) a[j][k] += __ldcg(part + (int64_t)NV * t + k);
+            t += NT;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = (a[0][k] + a[1][k]) + (a[2][k] + a[3][k]);
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w && (int)threadIdx.x + w < NT)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = sh[k][0];
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------ SpMV
 // p_new = z + beta p_old (own rows), then q = A p_new. The direction update
 // runs as its own vector pass so that the SpMV gathers a single vector and
 // spends exactly 9 multiply-adds per 3x3 block (on GB300 the FP64 SpMV is
 // bound by the FP64 pipe before HBM: 9 FMA per 76-byte block).
+#ifndef SX_UPD_TILES
+#define SX_UPD_TILES 1
+#endif
+static constexpr int kUpdTiles = SX_UPD_TILES;
+int pcg_update_blocks(int n_node_tiles) { return (n_node_tiles + kUpdTiles - 1) / kUpdTiles; }
+
 template <bool F32>
 __global__ void __launch_bounds__(kVecThreads)
 k_pcg_pdir(const SceneDev* scenes, const Tile* tiles, int ntiles, int par)
 {
-    const Tile T = tiles[blockIdx.x];
-    const SceneDev& S = scenes[T.scene];
-    if (!scene_live(S) || S.sc->pcg_done || (int)threadIdx.x >= T.count) return;
-    const int64_t n = T.start + threadIdx.x;
-    const double beta = S.sc->pcg_beta;
-    const double* po = par ? S.p1 : S.p0;
-    double* pn = par ? S.p0 : S.p1;
+    // kUpdTiles node tiles per block, loads first (as in the update)
+    double zv[kUpdTiles][3], ov[kUpdTiles][3], beta[kUpdTiles];
+    bool on[kUpdTiles];
+    int64_t nd[kUpdTiles];
+    const int t0 = blockIdx.x * kUpdTiles;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const double p = fma(beta, po[3 * n + i], S.z[3 * n + i]);
-        pn[3 * n + i] = p;
-        // the FP32 SpMV gathers this rounded copy (no conversion per block)
-        if (F32) S.p32[3 * n + i] = (float)p;
+    for (int j = 0; j < kUpdTiles; ++j) {
+        on[j] = false;
+        if (t0 + j >= ntiles) continue;
+        const Tile T = tiles[t0 + j];
+        const SceneDev& S = scenes[T.scene];
+        on[j] = scene_live(S) && !S.sc->pcg_done && (int)threadIdx.x < T.count;
+        if (!on[j]) continue;
+        const int64_t n = T.start + threadIdx.x;
+        nd[j] = n;
+        beta[j] = S.sc->pcg_beta;
+        const double* po = par ? S.p1 : S.p0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            ov[j][i] = po[3 * n + i];
+            zv[j][i] = S.z[3 * n + i];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kUpdTiles; ++j) {
+        if (!on[j]) continue;
+        const SceneDev& S = scenes[tiles[t0 + j].scene];
+        const int64_t n = nd[j];
+        double* pn = par ? S.p0 : S.p1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double p = fma(beta[j], ov[j][i], zv[j][i]);
+            pn[3 * n + i] = p;
+            // the FP32 SpMV gathers this rounded copy (no conversion per block)
+            if (F32) S.p32[3 * n + i] = (float)p;
+        }
     }
 }
 
@@ -275,10 +344,11 @@ cudaError_t launch_pcg_pdir(const SceneDev* scenes, const Tile* node_tiles, int 
                             int precision, int parity, cudaStream_t s)
 {
     if (!ntiles) return cudaSuccess;
+    const int g = pcg_update_blocks(ntiles);
     if (precision == SX_FP32)
-        k_pcg_pdir<true><<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity);
+        k_pcg_pdir<true><<<g, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity);
     else
-        k_pcg_pdir<false><<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity);
+        k_pcg_pdir<false><<<g, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity);
     return cudaGetLastError();
 }
 
@@ -344,7 +414,14 @@ cudaError_t launch_sell_cols(const int* row_ptr, const int* col, int64_t N, cons
 // FP64 SpMV is bound by the FP64 pipe before HBM: 9 FMA per 76-byte block,
 // the minimum). The matrix is read once, with evict-first loads so that the
 // gathered direction (L2-resident, ~7 MB per million rows) stays cached.
-static constexpr int kSpmvSlices = 4;
+#ifndef SX_SPMV_SLICES
+#define SX_SPMV_SLICES 4
+#endif
+#ifndef SX_SPMV_UNROLL
+#define SX_SPMV_UNROLL 2
+#endif
+static constexpr int kSpmvSlices = SX_SPMV_SLICES;
+static constexpr int kSpmvUnroll = SX_SPMV_UNROLL;
 static constexpr int kSpmvRows = 32 * kSpmvSlices;   // block rows per tile
 static constexpr int kSpmvThreads = kSpmvRows;       // one thread per block row
 __device__ __forceinline__ double fma_vt(double a, double b, double c) { return fma(a, b, c); }
@@ -373,7 +450,7 @@ k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* p
         // the gathered direction: p itself (FP64) or its float copy (FP32)
         const VT* pg = (sizeof(VT) == 8) ? (const VT*)pn : (const VT*)S.p32;
         VT a0 = VT(0), a1 = VT(0), a2 = VT(0);
-#pragma unroll 2
+#pragma unroll kSpmvUnroll
         for (int k = 0; k < w; ++k) {
             const int64_t c = 3 * (int64_t)__ldcs(cs + 32 * k);
             const VT x0 = __ldg(pg + c), x1 = __ldg(pg + c + 1), x2 = __ldg(pg + c + 2);
@@ -431,54 +508,130 @@ cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int nt
 }
 
 // ------------------------------------------------------------------ update
+// dx += alpha p, r -= alpha q, z = Minv r with the r.z and r.r partials per
+// node tile; the last tile of each scene forms its convergence test and
+// beta. A block takes kUpdTiles consecutive node tiles (a build parameter:
+// their loads issued together, one block prologue for several tiles); each
+// tile's partials are reduced by the same 256-thread tree as a block of its
+// own, so the sums do not depend on how tiles are grouped. Measured on the
+// 64^3 cube's Newton step: 1 and 2 tiles per block alike (153 ms), 4 slower
+// (160 ms: the registers of four tiles halve the resident blocks).
 __global__ void __launch_bounds__(kVecThreads)
 k_pcg_update(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part,
              const int* tbeg, const int* tend, double tol, int max_iter)
 {
-    __shared__ double sh[2][kVecThreads];
-    const int ti = blockIdx.x;
-    const Tile T = tiles[ti];
-    const SceneDev& S = scenes[T.scene];
-    if (!scene_live(S) || S.sc->pcg_done) return;   // the same for every tile of the scene
-    double v[2] = {0.0, 0.0};
-    if ((int)threadIdx.x < T.count) {
+    __shared__ double sh[2 * kUpdTiles][kVecThreads];
+    __shared__ int s_last[kUpdTiles];
+    const int t0 = blockIdx.x * kUpdTiles;
+    double rr_[kUpdTiles], rz_[kUpdTiles];
+    bool live[kUpdTiles];
+    double pv[kUpdTiles][3], dxv[kUpdTiles][3], rv[kUpdTiles][3], qv[kUpdTiles][3],
+        Mi[kUpdTiles][9], alpha[kUpdTiles];
+    int64_t nd[kUpdTiles];
+    bool on[kUpdTiles];
+    // loads of every tile first
+#pragma unroll
+    for (int j = 0; j < kUpdTiles; ++j) {
+        live[j] = false;
+        on[j] = false;
+        const int ti = t0 + j;
+        if (ti >= ntiles) continue;
+        const Tile T = tiles[ti];
+        const SceneDev& S = scenes[T.scene];
+        live[j] = scene_live(S) && !S.sc->pcg_done;   // the same for all tiles of a scene
+        on[j] = live[j] && (int)threadIdx.x < T.count;
+        if (!on[j]) continue;
         const int64_t n = T.start + threadIdx.x;
-        const double alpha = S.sc->pcg_alpha;
+        nd[j] = n;
+        alpha[j] = S.sc->pcg_alpha;
         const double* pn = par ? S.p0 : S.p1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            pv[j][i] = pn[3 * n + i];
+            dxv[j][i] = S.dx[3 * n + i];
+            rv[j][i] = S.r[3 * n + i];
+            qv[j][i] = S.q[3 * n + i];
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Mi[j][k] = S.Minv[9 * n + k];
+    }
+    // arithmetic and stores
+#pragma unroll
+    for (int j = 0; j < kUpdTiles; ++j) {
+        rz_[j] = 0.0;
+        rr_[j] = 0.0;
+        if (!on[j]) continue;
+        const SceneDev& S = scenes[tiles[t0 + j].scene];
+        const int64_t n = nd[j];
         double r[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            S.dx[3 * n + i] += alpha * pn[3 * n + i];
-            r[i] = S.r[3 * n + i] - alpha * S.q[3 * n + i];
+            S.dx[3 * n + i] = dxv[j][i] + alpha[j] * pv[j][i];
+            r[i] = rv[j][i] - alpha[j] * qv[j][i];
             S.r[3 * n + i] = r[i];
         }
-        const double* Mi = S.Minv + 9 * n;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            double z = Mi[3 * i] * r[0] + Mi[3 * i + 1] * r[1] + Mi[3 * i + 2] * r[2];
+            const double z = Mi[j][3 * i] * r[0] + Mi[j][3 * i + 1] * r[1] + Mi[j][3 * i + 2] * r[2];
             S.z[3 * n + i] = z;
-            v[0] += r[i] * z;
-            v[1] += r[i] * r[i];
+            rz_[j] += r[i] * z;
+            rr_[j] += r[i] * r[i];
         }
     }
-    double rzr[2];
-    if (last_tile_sums<2, kVecThreads>(v, sh, part, ti, &S.sc->cnt_update, tbeg[T.scene],
-                                       tend[T.scene], rzr) &&
-        threadIdx.x == 0) {
-        // convergence test and beta (the update of the chunk's p.q stage)
-        SceneScal* sc = S.sc;
-        sc->rz_new = rzr[0];
-        sc->rr = rzr[1];
-        sc->pcg_iters += 1;
-        const double t = sc->pcg_tol > 0.0 ? sc->pcg_tol : tol;
-        if (rzr[1] <= t * t * sc->bnorm2) {
-            sc->pcg_done = 1;
-        } else if (sc->pcg_iters >= max_iter || !isfinite(rzr[1])) {
-            sc->pcg_done = 1;
-            sc->pcg_status = 2;
-        } else {
-            sc->pcg_beta = rzr[0] / sc->rz;
-            sc->rz = rzr[0];
+    // per tile: the 256-thread tree, the partials, the count
+#pragma unroll
+    for (int j = 0; j < kUpdTiles; ++j) {
+        sh[2 * j][threadIdx.x] = rz_[j];
+        sh[2 * j + 1][threadIdx.x] = rr_[j];
+    }
+    __syncthreads();
+    for (int w = kVecThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < 2 * kUpdTiles; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < kUpdTiles; ++j) {
+            s_last[j] = 0;
+            if (!live[j]) continue;
+            const int ti = t0 + j;
+            const Tile T = tiles[ti];
+            const SceneDev& S = scenes[T.scene];
+            part[2 * (int64_t)ti] = sh[2 * j][0];
+            part[2 * (int64_t)ti + 1] = sh[2 * j + 1][0];
+            // release: this tile's partials are visible to whoever counts
+            // last; acquire: the last one sees every partial released before it
+            cuda::atomic_ref<int, cuda::thread_scope_device> cnt(S.sc->cnt_update);
+            s_last[j] = cnt.fetch_add(1, cuda::memory_order_acq_rel) ==
+                        tend[T.scene] - tbeg[T.scene] - 1;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kUpdTiles; ++j) {
+        if (!s_last[j]) continue;
+        const int sc_i = tiles[t0 + j].scene;
+        double rzr[2];
+        scene_tile_sums<2, kVecThreads>(sh, part, tbeg[sc_i], tend[sc_i], rzr);
+        if (threadIdx.x == 0) {
+            // convergence test and beta
+            SceneScal* sc = scenes[sc_i].sc;
+            sc->cnt_update = 0;
+            sc->rz_new = rzr[0];
+            sc->rr = rzr[1];
+            sc->pcg_iters += 1;
+            const double t = sc->pcg_tol > 0.0 ? sc->pcg_tol : tol;
+            if (rzr[1] <= t * t * sc->bnorm2) {
+                sc->pcg_done = 1;
+            } else if (sc->pcg_iters >= max_iter || !isfinite(rzr[1])) {
+                sc->pcg_done = 1;
+                sc->pcg_status = 2;
+            } else {
+                sc->pcg_beta = rzr[0] / sc->rz;
+                sc->rz = rzr[0];
+            }
         }
     }
 }
@@ -488,8 +641,9 @@ cudaError_t launch_pcg_update(const SceneDev* scenes, const Tile* node_tiles, in
                               double tol, int max_iter, cudaStream_t s)
 {
     if (!ntiles) return cudaSuccess;
-    k_pcg_update<<<ntiles, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity, part, tbeg,
-                                                tend, tol, max_iter);
+    k_pcg_update<<<pcg_update_blocks(ntiles), kVecThreads, 0, s>>>(scenes, node_tiles, ntiles,
+                                                                   parity, part, tbeg, tend, tol,
+                                                                   max_iter);
     return cudaGetLastError();
 }
 
@@ -620,9 +774,12 @@ cudaError_t add_pcg_chunk_nodes(cudaGraph_t graph, const PcgChunkArgs& a)
         void* a_pdir[] = {&scenes, &nt, &nnt, &par};
         void* a_spmv[] = {&scenes, &rt, &nrt, &par, &prow, &rb, &re};
         void* a_upd[] = {&scenes, &nt, &nnt, &par, &pnode, &nb, &ne, &tol, &maxit};
-        if (e == cudaSuccess) e = c.add(pdir, (unsigned)nnt, kVecThreads, 0, a_pdir);
+        if (e == cudaSuccess)
+            e = c.add(pdir, (unsigned)pcg_update_blocks(nnt), kVecThreads, 0, a_pdir);
         if (e == cudaSuccess) e = c.add(spmv, (unsigned)nrt, spmv_threads, smem, a_spmv);
-        if (e == cudaSuccess) e = c.add((const void*)k_pcg_update, (unsigned)nnt, kVecThreads, 0, a_upd);
+        if (e == cudaSuccess)
+            e = c.add((const void*)k_pcg_update, (unsigned)pcg_update_blocks(nnt), kVecThreads,
+                      0, a_upd);
     }
     return e;
 }

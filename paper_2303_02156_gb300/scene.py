@@ -336,6 +336,12 @@ class Server:
             if rc != sx.SX_OK:
                 raise sx.SxError(rc, "server lanes")
 
+    def set_lane_cap(self, max_resident):
+        """At most max_resident scenes resident per lane (0: no limit)."""
+        rc = sx.sx_server_set_lane_cap(self.h, int(max_resident))
+        if rc != sx.SX_OK:
+            raise sx.SxError(rc, "server lane cap")
+
     def submit(self, X, tets, young, poisson, density=1000.0, pinned=None,
                gravity=(0.0, 0.0, -9.81), n_steps=10, dt=0.01):
         X = _f64(X).reshape(-1, 3); tets = _i32(tets)

@@ -35,7 +35,8 @@ STATUS_NAMES = {0: "SX_OK", -1: "SX_EINVAL", -2: "SX_ENOMEM", -3: "SX_ECUDA", -4
 
 # every symbol include/sx.h declares
 EXPORTS = [
-    "sx_create", "sx_destroy", "sx_last_error", "sx_version", "sx_scene_create",
+    "sx_create", "sx_destroy", "sx_last_error", "sx_inject_alloc_failure", "sx_version",
+    "sx_scene_create",
     "sx_scene_destroy", "sx_add_snh_tet4", "sx_add_hinge4", "sx_add_pt_barrier",
     "sx_add_node_mass", "sx_set_pinned", "sx_set_gravity", "sx_finalize", "sx_set_state",
     "sx_get_state", "sx_set_inertia", "sx_eval", "sx_eval_batch", "sx_get_bsr",
@@ -47,7 +48,8 @@ EXPORTS = [
     "sx_compact_pairs", "sx_add_tet4", "sx_update_rotations", "sx_get_rotations",
     "sx_set_rotations", "sx_add_pt_friction", "sx_update_friction", "sx_get_friction_lag",
     "sx_add_tet_ho", "sx_advance",
-    "sx_server_create", "sx_server_set_lanes", "sx_server_submit", "sx_server_poll", "sx_server_result",
+    "sx_server_create", "sx_server_set_lanes", "sx_server_set_lane_cap", "sx_server_submit",
+    "sx_server_poll", "sx_server_result",
     "sx_server_drain", "sx_server_stats", "sx_server_destroy",
 ]
 SX_NOALLOC_MAX_ELEMENTS = 65536
@@ -114,6 +116,7 @@ _SIGS = {
     "sx_create": (_I, [_PP, _P]),
     "sx_destroy": (_I, [_P]),
     "sx_last_error": (C.c_char_p, [_P]),
+    "sx_inject_alloc_failure": (C.c_int, [_P, C.c_int]),
     "sx_version": (C.c_char_p, []),
     "sx_scene_create": (_I, [_P, _I64, _P, _I64, _P, _PP]),
     "sx_scene_destroy": (_I, [_P]),
@@ -163,6 +166,7 @@ _SIGS = {
     "sx_set_launch_shape": (_I, [_P, _I, _I, _I]),
     "sx_get_launch_shape": (_I, [_P, _I, C.POINTER(_I), C.POINTER(_I)]),
     "sx_server_set_lanes": (_I, [_P, _I, C.POINTER(_I64)]),
+    "sx_server_set_lane_cap": (C.c_int, [_P, C.c_int]),
     "sx_server_submit": (_I, [_P, C.POINTER(sx_snh_scene_spec), _I, _D, C.POINTER(_I64)]),
     "sx_server_poll": (_I, [_P, C.POINTER(sx_completion), _I, C.POINTER(_I)]),
     "sx_server_result": (_I, [_P, _I64, _P, _P]),

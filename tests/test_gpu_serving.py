@@ -183,3 +183,37 @@ def test_served_results_match_oracle_with_forcing_sequence(ctx):
         assert np.abs(v - vo).max() <= tol / dt
     srv.close()
     print(f"served vs oracle: worst max|x - x*| / max|x* - X| = {worst:.2e}")
+
+
+@pytest.mark.gpu
+def test_lane_cap_keeps_results_and_serves_everything(ctx):
+    """With at most two scenes resident per lane, all requests of a single
+    lane are still served, each equal to its alone run bit for bit."""
+    from paper_2303_02156_gb300.scene import Scene, Server
+    reqs = _requests(5, seed=9)
+    steps, dt, g = 2, 0.01, (0.0, 0.0, -9.81)
+    alone = []
+    for m, E, nu in reqs:
+        s = Scene(ctx, m["X"])
+        s.add_snh(m["tets"], E, nu, 1000.0)
+        s.set_pinned(m["pinned"])
+        s.set_gravity(g)
+        s.finalize()
+        for _ in range(steps):
+            s.newton_step(dt)
+        alone.append(s.get_state())
+        s.close()
+    srv = Server(ctx, 8 << 30, lanes=[])
+    srv.set_lane_cap(2)
+    ids = [srv.submit(m["X"], m["tets"], E, nu, 1000.0, pinned=m["pinned"], gravity=g,
+                      n_steps=steps, dt=dt) for m, E, nu in reqs]
+    assert srv.drain(120000.0) == sx.SX_OK
+    done = {c["req_id"]: c for c in srv.poll()}
+    assert srv.stats()["completed"] == 5
+    for rid, (xa, va) in zip(ids, alone):
+        assert done[rid]["status"] == sx.SX_OK, done[rid]["error"]
+        x, v = srv.result(rid)
+        assert np.array_equal(x, xa) and np.array_equal(v, va)
+    with pytest.raises(sx.SxError):
+        srv.set_lane_cap(-1)
+    srv.close()
