@@ -70,10 +70,11 @@ __device__ __forceinline__ float jac_div(float a, float b)
 {
     return SX_CLAMP_FAST_F32 ? __fdividef(a, b) : a / b;
 }
-// sqrt of x >= 1
+// sqrt of x >= 1 (x may be +inf: tau^2 + 1 overflows when a_pq is tiny;
+// x rsqrt(x) would give inf * 0 there)
 __device__ __forceinline__ float jac_sqrt1(float x)
 {
-    return SX_CLAMP_FAST_F32 ? x * rsqrtf(x) : sqrtf(x);
+    return (SX_CLAMP_FAST_F32 && x <= 1e36f) ? x * rsqrtf(x) : sqrtf(x);
 }
 
 // packed lower-triangle index of (i, j), any order
