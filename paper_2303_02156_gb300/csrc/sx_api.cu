@@ -51,6 +51,10 @@ struct BlockHost {
     int* ho_sub = nullptr;
     int* ho_own = nullptr;
     double* ho_modes = nullptr;
+    double* ho_rec = nullptr;
+    int* ho_flag = nullptr;
+    int* ho_pair = nullptr;
+    int* ho_gown = nullptr;
     int ho_ept = 1;   // whole elements per element-kernel tile
 };
 
@@ -412,6 +416,10 @@ SceneDev make_desc(const sx_scene* s, bool trial)
         e.ho_sub = h.ho_sub;
         e.ho_own = h.ho_own;
         e.ho_modes = h.ho_modes;
+        e.ho_rec = h.ho_rec;
+        e.ho_flag = h.ho_flag;
+        e.ho_pair = h.ho_pair;
+        e.ho_gown = h.ho_gown;
     }
     d.x = trial ? s->x_trial : s->x;
     d.v = s->v;
@@ -760,6 +768,22 @@ int ensure_vals32(sx_ctx* ctx, sx_scene* s)
     return SX_OK;
 }
 
+// phase 1 of every high-order block of the batch's scenes (before the
+// element kernel, which reads its records)
+int launch_ho_points(sx_ctx* ctx, const std::vector<sx_scene*>& scenes, const ElemLaunch& L,
+                     cudaStream_t st)
+{
+    if (!(L.kinds & 64)) return SX_OK;
+    for (size_t i = 0; i < scenes.size(); ++i)
+        for (size_t b = 0; b < scenes[i]->blocks.size(); ++b) {
+            const BlockHost& h = scenes[i]->blocks[b];
+            if (h.kind != SX_KIND_TET_HO || h.ho_n == 0) continue;
+            PL(SX_PH_ELEMENTS, 1, launch_tetho_points(L, (int)i, (int)b, h.ho_n, h.ho_nq, st));
+            PL(SX_PH_ELEMENTS, 1, launch_tetho_blocks(L, (int)i, (int)b, h.ho_n, h.ho_K, h.ho_nq, st));
+        }
+    return SX_OK;
+}
+
 // E / E+g / E+g+H over every active scene of the batch
 int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool trial,
              cudaStream_t st)
@@ -799,6 +823,8 @@ int run_eval(sx_ctx* ctx, Batch* B, int level, int project, int precision, bool 
     L.share_sms = ctx->share_sms;
     L.kinds = B->kinds;
     const int grid = elem_grid(ctx, precision, L.kinds, level >= 2 ? project : 0, L.ntiles);
+    int rc = launch_ho_points(ctx, B->scenes, L, st);
+    if (rc != SX_OK) return rc;
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (level >= 2 && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     PL(SX_PH_REDUCE, 1, launch_scene_reduce(B->d_part_elem, 1, 0, B->d_elem_beg, B->d_elem_end,
@@ -1364,7 +1390,7 @@ int sx_add_tet_ho(sx_scene* s, int order, const int32_t* tets, int64_t n, const 
     b.ho_n = n;
     // a tile of whole elements: at most one thread per sub-stencil and one
     // per (element, point)
-    b.ho_ept = std::max(1, std::min(elements_block_threads() / S, elements_block_threads() / nq));
+    b.ho_ept = kHoTileElems;
     // the sub-stencils as 4-node stencils for the pattern and the assembly
     {
         std::vector<int32_t> c4((size_t)n * S * 4);
@@ -1395,8 +1421,33 @@ int sx_add_tet_ho(sx_scene* s, int order, const int32_t* tets, int64_t n, const 
         dalloc(s, &b.ho_wdet, (size_t)nq * n) || dalloc(s, &b.ho_dN, hdN.size()) ||
         dalloc(s, &b.ho_sub, sub.size()) || dalloc(s, &b.ho_own, own.size()) ||
         dalloc(s, &b.mu, (size_t)n) || dalloc(s, &b.lam, (size_t)n) ||
-        dalloc(s, &b.ho_modes, (size_t)n * nq * 91))
+        dalloc(s, &b.ho_modes, (size_t)n * nq * 91) ||
+        dalloc(s, &b.ho_rec, (size_t)n * nq * kHoRec) || dalloc(s, &b.ho_flag, (size_t)n) ||
+        dalloc(s, &b.ho_pair, (size_t)3 * K * (K + 1) / 2) || dalloc(s, &b.ho_gown, (size_t)K))
         return fail(ctx, SX_ENOMEM, "add_tet_ho: allocation failed");
+    {
+        // owned blocks (owner-local node pair, slot j * 10 + ab) and the
+        // owner of each node's gradient (j * 4 + local node)
+        std::vector<int> pr, gown(K, -1);
+        for (int j = 0; j < S; ++j)
+            for (int a = 0; a < 4; ++a) {
+                if ((own[j] >> (10 + a)) & 1) gown[sub[4 * j + a]] = j * 4 + a;
+                for (int c = a; c < 4; ++c) {
+                    const int ab = a == 0 ? c : (a == 1 ? 3 + c : (a == 2 ? 5 + c : 9));
+                    if ((own[j] >> ab) & 1) {
+                        pr.push_back(sub[4 * j + a]);
+                        pr.push_back(sub[4 * j + c]);
+                        pr.push_back(j * 10 + ab);
+                    }
+                }
+            }
+        if ((int)pr.size() != 3 * K * (K + 1) / 2)
+            return fail(ctx, SX_EINVAL, "add_tet_ho: sub-stencil cover does not own every pair once");
+        CK(cudaMemcpyAsync(b.ho_pair, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(b.ho_gown, gown.data(), K * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(b.ho_flag, 0, std::max<int64_t>(n, 1) * sizeof(int), st));
+        CK(cudaStreamSynchronize(st));
+    }
     if (n) {
         CK(cudaMemcpyAsync(b.ho_conn, soa.data(), soa.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, st));
@@ -1978,6 +2029,10 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
     L.clamp_grid = clamp_grid_for(L.clamp_cap, L.clamp_threads);
     L.share_sms = ctx->share_sms;
     L.kinds = kind_bit(b);
+    if (b.kind == SX_KIND_TET_HO && b.ho_n) {
+        PL(SX_PH_ELEMENTS, 1, launch_tetho_points(L, 0, energy_id, b.ho_n, b.ho_nq, st));
+        PL(SX_PH_ELEMENTS, 1, launch_tetho_blocks(L, 0, energy_id, b.ho_n, b.ho_K, b.ho_nq, st));
+    }
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, elem_grid(ctx, precision, L.kinds, H ? project : 0,
                                                          L.ntiles), st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
@@ -2666,6 +2721,10 @@ extern "C" int sx_eval_elements_noalloc(sx_scene* s, int energy_id, int project,
     L.share_sms = ctx->share_sms;
     L.kinds = kind_bit(b);
     const int grid = elem_grid(ctx, precision, L.kinds, H ? project : 0, nt);
+    if (b.kind == SX_KIND_TET_HO && b.ho_n) {
+        PL(SX_PH_ELEMENTS, 1, launch_tetho_points(L, 0, energy_id, b.ho_n, b.ho_nq, st));
+        PL(SX_PH_ELEMENTS, 1, launch_tetho_blocks(L, 0, energy_id, b.ho_n, b.ho_K, b.ho_nq, st));
+    }
     PL(SX_PH_ELEMENTS, 1, launch_elements(L, grid, st));
     if (H && project) PL(SX_PH_CLAMP, 1, launch_clamp(L, st));
     int failed = 0;

@@ -1091,219 +1091,328 @@ __device__ __forceinline__ double snh_point(const double (&Fd)[9], double mud, d
 // pattern an element is S four-node sub-stencils covering its node pairs:
 // each Hessian block (a, b) belongs to the sub-stencil that owns the pair,
 // each node gradient to the one that owns the node, the energy to the
-// first. A tile holds whole elements (ho_ept of them, ho_ept nq <= 128).
-// Phase 1, one thread per (element, point): F_q from all K nodes, psi, P
-// and the Hessian coefficients into a shared record, the negative modes
-// (with projection) into the block's scratch. Phase 2, one thread per
-// sub-stencil: its own blocks and node gradients, accumulated over the
-// points in registers. All threads of the CTA call this (it synchronizes).
-constexpr int kHoRec = 42;   // wd, psi, Ji (9), F (9), C (9), P (9), cI cF cC cS
+// first; the other slots of the sub-stencils hold zeros. Two launches
+// before the element kernel:
+//   k_tetho_points, one thread per (element, point): F_q from all K
+//     nodes, psi, P and the Hessian coefficients into the element's record
+//     (ho_rec, [element][point][kHoRec]), the negative modes (with
+//     projection) into ho_modes;
+//   k_tetho_blocks, one element per group of threads: the element's records
+//     and modes into shared memory, then G_qa, F G_qa and cof(F) G_qa for
+//     every (point, node), then one thread per owned block (a, b) summing
+//     its SNH block over the points (nine accumulators, no thread handles
+//     more than one block, nothing is recomputed per sub-stencil), one per
+//     node gradient, and the zeros of the unowned slots.
+// The element kernel's tiles of these blocks then only sum the staged
+// energies and the non-finite flags (tetho_tile).
+template <typename R>
+__device__ __forceinline__ void tetho_point(const ElemLaunch& L, const SceneDev& S,
+                                            const ElemBlock& B, int64_t e, int q)
+{
+    const int K = B.ho_K, nq = B.ho_nq;
+    const int64_t ne = B.ho_n;
+    const bool proj = L.level >= 2 && L.project;
+    const double mud = B.mu[e], lamd = B.lam[e];
+    double* r = B.ho_rec + (e * nq + q) * kHoRec;
+    double Ji[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ji[k] = B.ho_Jinv[((int64_t)q * 9 + k) * ne + e];
+    const double wd = B.ho_wdet[(int64_t)q * ne + e];
+    // Ds = sum_a (x_a - x_0) dN_a^T, F = Ds J0^-1
+    const double* x0 = S.x + 3 * (int64_t)B.ho_conn[e];
+    const double* dq = B.ho_dN + q * K * 3;
+    double Ds[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int a = 1; a < K; ++a) {
+        const double* p = S.x + 3 * (int64_t)B.ho_conn[(int64_t)a * ne + e];
+        const double* dn = dq + 3 * a;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double xi = p[i] - x0[i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Ds[3 * i + c] = fma(xi, dn[c], Ds[3 * i + c]);
+        }
+    }
+    double Fd[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            Fd[3 * i + c] = Ds[3 * i] * Ji[c] + Ds[3 * i + 1] * Ji[3 + c] + Ds[3 * i + 2] * Ji[6 + c];
+    SnhCore<R> C;
+    R P[9];
+    const double psi = snh_point<R>(Fd, mud, lamd, L.level, C, P);
+    r[0] = wd;
+    r[1] = psi;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        r[2 + k] = Ji[k];
+        r[11 + k] = L.level >= 1 ? (double)C.F[k] : 0.0;
+        r[20 + k] = L.level >= 1 ? (double)C.C[k] : 0.0;
+        r[29 + k] = L.level >= 1 ? (double)P[k] : 0.0;
+    }
+    r[38] = L.level >= 1 ? (double)C.cI : 0.0;
+    r[39] = L.level >= 1 ? (double)C.cF : 0.0;
+    r[40] = L.level >= 1 ? (double)C.cC : 0.0;
+    r[41] = L.level >= 1 ? (double)C.cS : 0.0;
+    if (proj) {
+        double mlam[9], M[9][9];
+        const int nm = snh_neg_modes_call(Fd, mud, lamd, mlam, M);
+        double* md = B.ho_modes + ((int64_t)e * nq + q) * 91;
+        md[0] = nm;
+        for (int m = 0; m < nm; ++m) {
+            md[1 + m] = mlam[m];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) md[10 + 9 * m + k] = M[m][k];
+        }
+    }
+}
 
+template <typename R>
+__global__ void __launch_bounds__(128)
+k_tetho_points(ElemLaunch L, int scene, int blk)
+{
+    const SceneDev& S = L.scenes[scene];
+    if (!(S.sc == nullptr || S.sc->active)) return;
+    const ElemBlock& B = S.blk[blk];
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int nq = B.ho_nq;
+    if (idx >= B.ho_n * nq) return;
+    // consecutive threads: consecutive points of one element (the
+    // element's records are contiguous)
+    const int64_t e = idx / nq;
+    tetho_point<R>(L, S, B, e, (int)(idx - e * nq));
+}
+
+// shared bytes of one element in k_tetho_blocks: with projection its
+// modes (double), then its records and (G, F G, cof(F) G) per (point,
+// node) in the element precision (rs = sizeof(R)); 16-byte multiples
+__host__ __device__ constexpr int tetho_smem_bytes(int K, int nq, bool proj, int rs)
+{
+    return ((proj ? nq * 91 * 8 : 0) + (nq * kHoRec + nq * K * 9) * rs + 15) / 16 * 16;
+}
+constexpr int kHoBlockThreads = 256;
+
+template <typename R, typename HT>
+__global__ void __launch_bounds__(kHoBlockThreads)
+k_tetho_blocks(ElemLaunch L, int scene, int blk, int epc)
+{
+    extern __shared__ __align__(16) unsigned char hsm_raw[];
+    const SceneDev& S = L.scenes[scene];
+    if (!(S.sc == nullptr || S.sc->active)) return;
+    const ElemBlock& B = S.blk[blk];
+    const int K = B.ho_K, NS = B.ho_S, nq = B.ho_nq;
+    const int64_t ne = B.ho_n;
+    const bool proj = L.level >= 2 && L.project;
+    const int per = tetho_smem_bytes(K, nq, proj, (int)sizeof(R));
+    const int tpe = kHoBlockThreads / epc;   // threads per element
+    const int g = threadIdx.x / tpe, t = threadIdx.x - g * tpe;
+    const int64_t e = (int64_t)blockIdx.x * epc + g;
+    const bool live = g < epc && e < ne;
+    double* mds = (double*)(hsm_raw + (size_t)g * per);   // [q][91] (with projection)
+    R* rec = (R*)(mds + (proj ? nq * 91 : 0));             // [q][kHoRec]
+    R* gv = rec + nq * kHoRec;   // [q][node][9]: G (3), F G (3), C G (3)
+    // ---- the element's records (in R) and modes
+    if (live) {
+        const double* src = B.ho_rec + e * nq * kHoRec;
+        for (int i = t; i < nq * kHoRec; i += tpe) rec[i] = (R)__ldg(src + i);
+        if (proj) {
+            const double* ms = B.ho_modes + e * nq * 91;
+            for (int i = t; i < nq * 91; i += tpe) mds[i] = __ldg(ms + i);
+        }
+    }
+    __syncthreads();
+    // ---- G_qa, F G_qa, cof(F) G_qa (in the element precision R; G from
+    // the double records)
+    if (live && L.level >= 1) {
+        for (int i = t; i < nq * K; i += tpe) {
+            const int q = i / K, a = i - q * K;
+            const double* rd = B.ho_rec + (e * nq + q) * kHoRec;
+            const R* r = rec + q * kHoRec;
+            const double* dn = B.ho_dN + (q * K + a) * 3;
+            R Gr[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Gr[c] = (R)(dn[0] * __ldg(rd + 2 + c) + dn[1] * __ldg(rd + 5 + c) +
+                            dn[2] * __ldg(rd + 8 + c));
+            R u[3], v[3];
+            matvec3(r + 11, Gr, u);
+            matvec3(r + 20, Gr, v);
+            R* o = gv + (q * K + a) * 9;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o[c] = Gr[c];
+                o[3 + c] = u[c];
+                o[6 + c] = v[c];
+            }
+        }
+    }
+    __syncthreads();
+    if (!live) return;
+    int bad = 0;
+    const int P = K * (K + 1) / 2;
+    const int64_t sid0 = e * NS;
+    // ---- owned blocks (one per thread), node gradients, energy
+    for (int it = t; it < P + K + 1; it += tpe) {
+        if (it < P && L.level >= 2) {
+            const int* pr = B.ho_pair + 3 * it;   // nodes (in the owner's local order), slot
+            const int na = pr[0], nb = pr[1], slot = pr[2];
+            const bool diag = na == nb;
+            R acc[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[k] = R(0);
+            for (int q = 0; q < nq; ++q) {
+                const R* r = rec + q * kHoRec;
+                const R* ga = gv + (q * K + na) * 9;
+                const R* gb = gv + (q * K + nb) * 9;
+                SnhCore<R> C;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) C.F[k] = r[11 + k];
+                const R w = r[0];
+                C.cI = w * r[38];
+                C.cF = w * r[39];
+                C.cC = w * r[40];
+                C.cS = w * r[41];
+                R blkv[9];
+                snh_block(C, ga, gb, ga + 3, gb + 3, ga + 6, gb + 6, diag, blkv);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) acc[k] += blkv[k];
+                if (proj) {
+                    const double* md = mds + q * 91;
+                    const int nm = (int)md[0];
+                    for (int m = 0; m < nm; ++m) {
+                        const double* M = md + 10 + 9 * m;
+                        double wa[3], wb[3];
+#pragma unroll
+                        for (int rr = 0; rr < 3; ++rr) {
+                            wa[rr] = M[3 * rr] * (double)ga[0] + M[3 * rr + 1] * (double)ga[1] +
+                                     M[3 * rr + 2] * (double)ga[2];
+                            wb[rr] = M[3 * rr] * (double)gb[0] + M[3 * rr + 1] * (double)gb[1] +
+                                     M[3 * rr + 2] * (double)gb[2];
+                        }
+                        const double sc = __ldg(B.ho_rec + (e * nq + q) * kHoRec) * md[1 + m];
+#pragma unroll
+                        for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) acc[3 * rr + c] -= (R)(sc * wa[rr] * wb[c]);
+                    }
+                }
+            }
+            const int j = slot / 10, ab = slot - 10 * (slot / 10);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) bad |= nonfinite_bits(acc[k]) ? 1 : 0;
+            if (L.out_H) {
+                // the sub-stencil's full 12x12: block (a, b) and its transpose
+                int la = 0, lb = 0;
+                for (int x = 0; x < 4; ++x)
+                    for (int y = x; y < 4; ++y)
+                        if (up_index(x, y) == ab) {
+                            la = x;
+                            lb = y;
+                        }
+                double* full = L.out_H + 144 * (sid0 + j);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        full[(3 * la + i) * 12 + 3 * lb + k] = (double)acc[3 * i + k];
+                        full[(3 * lb + k) * 12 + 3 * la + i] = (double)acc[3 * i + k];
+                    }
+            } else {
+                HT* dst = (HT*)S.He + 90 * (B.base + sid0 + j) + 9 * ab;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) dst[k] = (HT)acc[k];
+            }
+        } else if (it >= P && it < P + K && L.level >= 1) {
+            const int a = it - P;
+            const int gs = B.ho_gown[a];   // owner sub-stencil * 4 + local node
+            R gl[3] = {R(0), R(0), R(0)};
+            for (int q = 0; q < nq; ++q) {
+                const R* r = rec + q * kHoRec;
+                const R* Gr = gv + (q * K + a) * 9;
+                const R w = r[0];
+                const R* Pq = r + 29;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    gl[i] += w * (Pq[i * 3 + 0] * Gr[0] + Pq[i * 3 + 1] * Gr[1] + Pq[i * 3 + 2] * Gr[2]);
+            }
+            double* gout = L.out_g ? L.out_g + 12 * (sid0 + gs / 4)
+                                   : S.ge + 12 * (B.base + sid0 + gs / 4);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                gout[3 * (gs % 4) + i] = (double)gl[i];
+                bad |= nonfinite_bits(gl[i]) ? 1 : 0;
+            }
+        } else if (it == P + K) {
+            // the energy in double from the double records
+            const double* rd = B.ho_rec + e * nq * kHoRec;
+            double E = 0.0;
+            for (int q = 0; q < nq; ++q) E += __ldg(rd + q * kHoRec) * __ldg(rd + q * kHoRec + 1);
+            bad |= nonfinite_bits(E) ? 1 : 0;
+            if (L.out_E) L.out_E[sid0] = E;
+            else S.Ee[B.base + sid0] = E;
+        }
+    }
+    // ---- zeros in every slot no block owns (and the energies of j > 0)
+    for (int i = t; i < NS * 10; i += tpe) {
+        const int j = i / 10, ab = i - 10 * j;
+        if ((B.ho_own[j] >> ab) & 1) continue;
+        if (L.level < 2) break;
+        if (L.out_H) {
+            int la = 0, lb = 0;
+            for (int x = 0; x < 4; ++x)
+                for (int y = x; y < 4; ++y)
+                    if (up_index(x, y) == ab) {
+                        la = x;
+                        lb = y;
+                    }
+            double* full = L.out_H + 144 * (sid0 + j);
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    full[(3 * la + ii) * 12 + 3 * lb + k] = 0.0;
+                    full[(3 * lb + k) * 12 + 3 * la + ii] = 0.0;
+                }
+        } else {
+            HT* dst = (HT*)S.He + 90 * (B.base + sid0 + j) + 9 * ab;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) dst[k] = HT(0);
+        }
+    }
+    for (int i = t; i < NS * 4; i += tpe) {
+        const int j = i / 4, a = i - 4 * j;
+        if (L.level >= 1 && !((B.ho_own[j] >> (10 + a)) & 1)) {
+            double* gout = L.out_g ? L.out_g + 12 * (sid0 + j) : S.ge + 12 * (B.base + sid0 + j);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gout[3 * a + k] = 0.0;
+        }
+        if (a == 0 && j > 0) {
+            if (L.out_E) L.out_E[sid0 + j] = 0.0;
+            else S.Ee[B.base + sid0 + j] = 0.0;
+        }
+    }
+    if (bad) B.ho_flag[e] = 1;
+}
+
+// The element kernel's share of a high-order tile (kHoTileElems whole
+// elements): the energies and non-finite flags the two launches before it
+// left, summed in element order.
 template <typename R, typename HT>
 __device__ void tetho_tile(const ElemLaunch& L, const SceneDev& S, const ElemBlock& B,
                            const Tile& T, ThreadOut& o)
 {
-    __shared__ double rec[kElemThreads][kHoRec];
-    const int K = B.ho_K, NS = B.ho_S, nq = B.ho_nq;
-    const int64_t ne = B.ho_n;
+    const int NS = B.ho_S;
     const int64_t e0 = T.start / NS;
     const int nel = T.count / NS;
-    const bool proj = L.level >= 2 && L.project;
-    // ---- phase 1: one (element, point) per thread
-    if ((int)threadIdx.x < nel * nq) {
-        const int el = threadIdx.x / nq, q = threadIdx.x - el * nq;
-        const int64_t e = e0 + el;
-        const double mud = B.mu[e], lamd = B.lam[e];
-        double* r = rec[threadIdx.x];
-        double Ji[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Ji[k] = B.ho_Jinv[((int64_t)q * 9 + k) * ne + e];
-        const double wd = B.ho_wdet[(int64_t)q * ne + e];
-        // Ds = sum_a (x_a - x_0) dN_a^T, F = Ds J0^-1
-        const double* x0 = S.x + 3 * (int64_t)B.ho_conn[e];
-        const double* dq = B.ho_dN + q * K * 3;
-        double Ds[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int a = 1; a < K; ++a) {
-            const double* p = S.x + 3 * (int64_t)B.ho_conn[(int64_t)a * ne + e];
-            const double* dn = dq + 3 * a;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const double xi = p[i] - x0[i];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) Ds[3 * i + c] = fma(xi, dn[c], Ds[3 * i + c]);
-            }
-        }
-        double Fd[9];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                Fd[3 * i + c] = Ds[3 * i] * Ji[c] + Ds[3 * i + 1] * Ji[3 + c] + Ds[3 * i + 2] * Ji[6 + c];
-        SnhCore<R> C;
-        R P[9];
-        const double psi = snh_point<R>(Fd, mud, lamd, L.level, C, P);
-        r[0] = wd;
-        r[1] = psi;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            r[2 + k] = Ji[k];
-            if (L.level >= 1) {
-                r[11 + k] = (double)C.F[k];
-                r[20 + k] = (double)C.C[k];
-                r[29 + k] = (double)P[k];
-            }
-        }
-        if (L.level >= 1) {
-            r[38] = (double)C.cI;
-            r[39] = (double)C.cF;
-            r[40] = (double)C.cC;
-            r[41] = (double)C.cS;
-        }
-        if (proj) {
-            double mlam[9], M[9][9];
-            const int nm = snh_neg_modes_call(Fd, mud, lamd, mlam, M);
-            double* md = B.ho_modes + ((int64_t)e * nq + q) * 91;
-            md[0] = nm;
-            for (int m = 0; m < nm; ++m) {
-                md[1 + m] = mlam[m];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) md[10 + 9 * m + k] = M[m][k];
-            }
+    o.E = 0.0;
+    if ((int)threadIdx.x < nel) {
+        const int64_t e = e0 + threadIdx.x;
+        o.E = L.out_E ? L.out_E[e * NS] : S.Ee[B.base + e * NS];
+        if (B.ho_flag[e]) {
+            o.nonfinite = 1;
+            B.ho_flag[e] = 0;
         }
     }
-    __syncthreads();
-    // ---- phase 2: one sub-stencil per thread; consecutive threads take the
-    // same sub-stencil index j of different elements, so the lanes of a warp
-    // share j's ownership mask and local nodes (few divergent paths)
-    if ((int)threadIdx.x < T.count) {
-        const int el = (int)threadIdx.x % nel;
-        const int j = (int)threadIdx.x / nel;
-        const int64_t e = e0 + el;
-        const int64_t sid = e * NS + j;
-        const int* l = B.ho_sub + 4 * j;
-        const int own = B.ho_own[j];
-        R acc[10][9];
-        R gl[4][3];
-#pragma unroll
-        for (int ab = 0; ab < 10; ++ab)
-#pragma unroll
-            for (int k = 0; k < 9; ++k) acc[ab][k] = R(0);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) gl[a][i] = R(0);
-        double E = 0.0;
-        for (int q = 0; q < nq; ++q) {
-            const double* r = rec[el * nq + q];
-            const double wd = r[0];
-            if (j == 0) E += wd * r[1];
-            if (L.level < 1) continue;
-            const double* dq = B.ho_dN + q * K * 3;
-            double Gd[4][3];
-            R Gr[4][3];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const double* dn = dq + 3 * l[a];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    Gd[a][c] = dn[0] * r[2 + c] + dn[1] * r[5 + c] + dn[2] * r[8 + c];
-                    Gr[a][c] = (R)Gd[a][c];
-                }
-            }
-            const R w = (R)wd;
-            R P[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) P[k] = (R)r[29 + k];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                if ((own >> (10 + a)) & 1)
-#pragma unroll
-                    for (int i = 0; i < 3; ++i)
-                        gl[a][i] += w * (P[i * 3 + 0] * Gr[a][0] + P[i * 3 + 1] * Gr[a][1] +
-                                         P[i * 3 + 2] * Gr[a][2]);
-            if (L.level < 2) continue;
-            SnhCore<R> C;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                C.F[k] = (R)r[11 + k];
-                C.C[k] = (R)r[20 + k];
-            }
-            C.cI = w * (R)r[38];
-            C.cF = w * (R)r[39];
-            C.cC = w * (R)r[40];
-            C.cS = w * (R)r[41];
-            R u[4][3], v[4][3];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                matvec3(C.F, Gr[a], u[a]);
-                matvec3(C.C, Gr[a], v[a]);
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = a; b < 4; ++b) {
-                    const int ab = up_index(a, b);
-                    if (!((own >> ab) & 1)) continue;
-                    R blk[9];
-                    snh_block(C, Gr[a], Gr[b], u[a], u[b], v[a], v[b], a == b, blk);
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) acc[ab][k] += blk[k];
-                }
-            if (proj) {
-                const double* md = B.ho_modes + ((int64_t)e * nq + q) * 91;
-                const int nm = (int)md[0];
-#pragma unroll 1
-                for (int m = 0; m < nm; ++m) {
-                    const double* M = md + 10 + 9 * m;
-                    double wv[4][3];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int rr = 0; rr < 3; ++rr)
-                            wv[a][rr] = M[3 * rr] * Gd[a][0] + M[3 * rr + 1] * Gd[a][1] +
-                                        M[3 * rr + 2] * Gd[a][2];
-                    const double sc = wd * md[1 + m];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int b = a; b < 4; ++b) {
-                            const int ab = up_index(a, b);
-                            if (!((own >> ab) & 1)) continue;
-#pragma unroll
-                            for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-                                for (int c = 0; c < 3; ++c)
-                                    acc[ab][3 * rr + c] -= (R)(sc * wv[a][rr] * wv[b][c]);
-                        }
-                }
-            }
-        }
-        o.E = j == 0 ? E : 0.0;
-        if (nonfinite_bits(o.E)) o.nonfinite = 1;
-        if (L.out_E) L.out_E[sid] = o.E;
-        else S.Ee[B.base + sid] = o.E;
-        if (L.level >= 1) {
-            double* gout = L.out_g ? L.out_g + 12 * sid : S.ge + 12 * (B.base + sid);
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    gout[3 * a + i] = (double)gl[a][i];
-                    if (nonfinite_bits(gl[a][i])) o.nonfinite = 1;
-                }
-        }
-        if (L.level >= 2) {
-            auto blockfn = [&](int a, int b, R* out) {
-                const int ab = up_index(a, b);
-#pragma unroll
-                for (int k = 0; k < 9; ++k) out[k] = acc[ab][k];
-            };
-            HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (B.base + sid);
-            double* full = L.out_H ? L.out_H + 144 * sid : nullptr;
-            write_blocks<R, HT>(blockfn, staged, full, &o.nonfinite);
-        }
-    }
-    __syncthreads();
 }
 
 template <typename R, typename HT>

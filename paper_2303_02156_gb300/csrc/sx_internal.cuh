@@ -86,6 +86,10 @@ struct ElemBlock {
     const int* ho_sub;       // [S][4] local nodes of the sub-stencils
     const int* ho_own;       // [S] bits 0-9: owned upper blocks, 10-13: owned nodes
     double* ho_modes;        // [ho_n][nq][91] negative modes per point (projection scratch)
+    double* ho_rec;          // [ho_n][nq][kHoRec] per-point records (scratch)
+    int* ho_flag;            // [ho_n] non-finite output seen (scratch)
+    const int* ho_pair;      // [K(K+1)/2][3] owned blocks: owner-local node pair, slot j*10+ab
+    const int* ho_gown;      // [K] owner of each node's gradient: j*4 + local node
 };
 
 // per-scene scalars the device loops read and write
@@ -247,6 +251,19 @@ cudaError_t launch_tetho_rest(const double* X, int64_t N, const int* conn, int64
                               int nq, const double* rule_w, const double* dN, double* Jinv,
                               double* wdet, double* vol, int* bad, cudaStream_t s);
 const void* elements_kernel_ho(int kinds, bool f32);       // 64, 127
+// phase 1 of the high-order tets: one thread per (element, point) of block
+// `blk` of scene `scene` (F, psi, P, the Hessian coefficients -> ho_rec;
+// with projection the negative modes -> ho_modes), before the element kernel
+cudaError_t launch_tetho_points(const ElemLaunch& L, int scene, int blk, int64_t n_el, int nq,
+                                cudaStream_t s);
+// then the blocks, gradients and energies of the block's sub-stencils
+// (one element per group of threads; K, nq as registered)
+cudaError_t launch_tetho_blocks(const ElemLaunch& L, int scene, int blk, int64_t n_el, int K,
+                                int nq, cudaStream_t s);
+// shared memory one element of k_tetho_blocks needs (bytes), with projection
+int tetho_block_smem(int K, int nq);
+constexpr int kHoRec = 42;   // wd, psi, Ji (9), F (9), C (9), P (9), cI cF cC cS
+constexpr int kHoTileElems = 32;   // whole elements per element-kernel tile
 cudaError_t launch_elements_ho(int kinds, bool f32, const ElemLaunch& L, int grid,
                                cudaStream_t s);
 cudaError_t launch_friction_lag(const double* x, const int4* conn, int64_t n, double dhat,

@@ -32,6 +32,21 @@ __device__ __forceinline__ bool scene_live(const SceneDev& S)
     return S.sc == nullptr || S.sc->active;
 }
 
+// In the PCG chunk graph each iteration kernel may be launched before the
+// one it depends on has finished (a programmatic edge from that kernel's
+// launch completion); it waits here, before reading anything the previous
+// kernel writes, until that kernel has completed and its writes are
+// visible. Without such an edge (plain launches) this returns at once.
+#ifndef SX_PCG_PDL
+#define SX_PCG_PDL 1
+#endif
+__device__ __forceinline__ void wait_prior_grid()
+{
+#if SX_PCG_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
 // ------------------------------------------------------------------ predictor
 // x_start = x, x~ = x + dt v + dt^2 g; tile partial: sum over free nodes of
 // m^2 |g|^2 (the external-force scale of the Newton residual test)
@@ -301,6 +316,7 @@ template <bool F32>
 __global__ void __launch_bounds__(kVecThreads)
 k_pcg_pdir(const SceneDev* scenes, const Tile* tiles, int ntiles, int par)
 {
+    wait_prior_grid();
     // kUpdTiles node tiles per block, loads first (as in the update)
     double zv[kUpdTiles][3], ov[kUpdTiles][3], beta[kUpdTiles];
     bool on[kUpdTiles];
@@ -432,6 +448,7 @@ __global__ void __launch_bounds__(kSpmvThreads)
 k_spmv(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part,
        const int* tbeg, const int* tend)
 {
+    wait_prior_grid();
     __shared__ double sh[1][kSpmvThreads];
     const int ti = blockIdx.x;
     const Tile T = tiles[ti];
@@ -515,11 +532,14 @@ cudaError_t launch_spmv_pq(const SceneDev* scenes, const Tile* row_tiles, int nt
 // tile's partials are reduced by the same 256-thread tree as a block of its
 // own, so the sums do not depend on how tiles are grouped. Measured on the
 // 64^3 cube's Newton step: 1 and 2 tiles per block alike (153 ms), 4 slower
-// (160 ms: the registers of four tiles halve the resident blocks).
+// (160 ms: the registers of four tiles halve the resident blocks); capping
+// the registers for 7 or 8 resident blocks (one wave of the cube's 1,073
+// tiles) changed nothing (154 ms).
 __global__ void __launch_bounds__(kVecThreads)
 k_pcg_update(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part,
              const int* tbeg, const int* tend, double tol, int max_iter)
 {
+    wait_prior_grid();
     __shared__ double sh[2 * kUpdTiles][kVecThreads];
     __shared__ int s_last[kUpdTiles];
     const int t0 = blockIdx.x * kUpdTiles;
@@ -743,7 +763,20 @@ struct NodeChain {
         p.kernelParams = args;
         p.extra = nullptr;
         cudaGraphNode_t n = nullptr;
+#if SX_PCG_PDL
+        cudaError_t e = cudaGraphAddKernelNode(&n, g, nullptr, 0, &p);
+        if (e == cudaSuccess && last) {
+            // programmatic edge: the node may launch once every block of
+            // `last` has started; it waits (wait_prior_grid) for its completion
+            cudaGraphEdgeData ed{};
+            ed.from_port = cudaGraphKernelNodePortLaunchCompletion;
+            ed.to_port = 0;
+            ed.type = cudaGraphDependencyTypeProgrammatic;
+            e = cudaGraphAddDependencies(g, &last, &n, &ed, 1);
+        }
+#else
         cudaError_t e = cudaGraphAddKernelNode(&n, g, last ? &last : nullptr, last ? 1 : 0, &p);
+#endif
         if (e == cudaSuccess) last = n;
         return e;
     }
