@@ -226,29 +226,6 @@ def clamp_profile_figures():
     return tpe, fpe, vals.get("source_sha256_16") == h.hexdigest()[:16]
 
 
-def clamp_traffic_per_element():
-    """DRAM bytes per projected stencil of the clamp kernel from the
-    committed ncu summary, if it was taken on the current sources."""
-    path = os.path.join(ROOT, "profiles", "k_clamp_snh_cube_40.md")
-    if not os.path.exists(path):
-        return None
-    h = hashlib.sha256()
-    for f in ["sx_clamp.cu", "sx_clamp.cuh"]:
-        h.update(open(os.path.join(ROOT, "paper_2303_02156_gb300", "csrc", f), "rb").read())
-    want = h.hexdigest()[:16]
-    vals = {}
-    for line in open(path):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("source_sha256_16") != want:
-        return None
-    try:
-        return float(vals["dram_bytes_per_projected_stencil"])
-    except (KeyError, ValueError):
-        return None
-
-
 # ------------------------------------------------------------------ serving
 def run_serving(ctx, n_req, seed, rate=200.0, steps=10, dt=0.01, budget=150e9, lane_cap=0,
                 rank=0, world=1, dist=None, total=2000):

@@ -199,8 +199,26 @@ __device__ __forceinline__ int psd_class_f32(const double (&M)[45])
 // every loop is unrolled and there is no data-dependent control flow, so a
 // warp runs its 32 stencils in lockstep.
 
+// The float eigenvector matrix, row-major (column c = eigenvector c): in
+// registers (a per-thread array) or in shared memory laid out [81][threads]
+// (fewer registers, more resident warps for the float Jacobi's serial
+// chains).
+struct RegXf {
+    float (&a)[81];
+    __device__ __forceinline__ float& operator()(int r, int c) const { return a[r * 9 + c]; }
+};
+struct SmemXf {
+    float* base;
+    int stride;
+    __device__ __forceinline__ float& operator()(int r, int c) const
+    {
+        return base[(r * 9 + c) * stride];
+    }
+};
+
 // float sweep: exact float angle, a_pq set to zero
-__device__ __forceinline__ void jacobi_sweep_f32(float (&A)[45], float (&X)[81])
+template <typename XF>
+__device__ __forceinline__ void jacobi_sweep_f32(float (&A)[45], const XF& X)
 {
 #pragma unroll
     for (int p = 0; p < 8; ++p)
@@ -225,9 +243,9 @@ __device__ __forceinline__ void jacobi_sweep_f32(float (&A)[45], float (&X)[81])
             }
 #pragma unroll
             for (int r = 0; r < 9; ++r) {
-                const float xp = X[r * 9 + p], xq = X[r * 9 + q];
-                X[r * 9 + p] = c * xp - s * xq;
-                X[r * 9 + q] = s * xp + c * xq;
+                const float xp = X(r, p), xq = X(r, q);
+                X(r, p) = c * xp - s * xq;
+                X(r, q) = s * xp + c * xq;
             }
         }
 }
@@ -298,15 +316,16 @@ __device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat&
 // entry r of the column that lands in `slot`. Returns k, the number of
 // eigenvalues below delta = 1e-5 ||M||_F (9 when a Gershgorin test on the
 // float matrix cannot confirm that the rest is a positive definite block).
-template <typename Put>
-__device__ __forceinline__ int eig9_float(const double* __restrict__ Mg, double fro, Put put)
+template <typename XF, typename Put>
+__device__ __forceinline__ int eig9_float_x(const double* __restrict__ Mg, double fro, const XF& Xf,
+                                            Put put)
 {
     int k = 0;
-    float A[45], Xf[81];
+    float A[45];
 #pragma unroll
     for (int i = 0; i < 45; ++i) A[i] = (float)Mg[i];
 #pragma unroll
-    for (int i = 0; i < 81; ++i) Xf[i] = (i % 10 == 0) ? 1.0f : 0.0f;
+    for (int i = 0; i < 81; ++i) Xf(i / 9, i % 9) = (i % 10 == 0) ? 1.0f : 0.0f;
 #pragma unroll 1
     for (int sw = 0; sw < 5; ++sw) jacobi_sweep_f32(A, Xf);
     const float delta = 1e-5f * (float)fro;
@@ -327,9 +346,17 @@ __device__ __forceinline__ int eig9_float(const double* __restrict__ Mg, double 
         // Gershgorin disc of the P block, with half of delta to spare
         if (lc >= delta) pblock_ok = pblock_ok && (lc - rad > 0.5f * delta);
 #pragma unroll
-        for (int r = 0; r < 9; ++r) put(r, rank, Xf[r * 9 + c]);
+        for (int r = 0; r < 9; ++r) put(r, rank, Xf(r, c));
     }
     return pblock_ok ? k : 9;
+}
+
+// the same with the float eigenvectors in registers
+template <typename Put>
+__device__ __forceinline__ int eig9_float(const double* __restrict__ Mg, double fro, Put put)
+{
+    float a[81];
+    return eig9_float_x(Mg, fro, RegXf{a}, put);
 }
 
 // Phase 2, double part: X (shared memory, columns ordered as above) is
