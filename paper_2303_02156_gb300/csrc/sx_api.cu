@@ -638,12 +638,12 @@ int ensure_clamp_queue(sx_ctx* ctx, int64_t need, cudaStream_t st)
     ctx->clampBucket = nullptr;
     if (!ctx->clampCount) CK(cudaMallocAsync((void**)&ctx->clampCount, 2 * sizeof(int), st));
     if (!ctx->clampBucketCount)
-        CK(cudaMallocAsync((void**)&ctx->clampBucketCount, 10 * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&ctx->clampBucketCount, kClampBins * sizeof(int), st));
     if (cudaMallocAsync((void**)&ctx->clampM, (size_t)need * 45 * sizeof(double), st) != cudaSuccess ||
         cudaMallocAsync((void**)&ctx->clampRef, (size_t)need * sizeof(ClampRef), st) != cudaSuccess ||
-        cudaMallocAsync((void**)&ctx->clampX, (size_t)need * 81 * sizeof(float), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&ctx->clampX, (size_t)need * kClampRec * sizeof(float), st) != cudaSuccess ||
         cudaMallocAsync((void**)&ctx->clampFro, (size_t)need * sizeof(double), st) != cudaSuccess ||
-        cudaMallocAsync((void**)&ctx->clampBucket, (size_t)need * 10 * sizeof(int), st) != cudaSuccess) {
+        cudaMallocAsync((void**)&ctx->clampBucket, (size_t)need * kClampBins * sizeof(int), st) != cudaSuccess) {
         cudaGetLastError();
         for (void* p : {(void*)ctx->clampM, (void*)ctx->clampRef, (void*)ctx->clampX,
                         (void*)ctx->clampFro, (void*)ctx->clampBucket})
@@ -2010,11 +2010,11 @@ int sx_eval_elements(sx_scene* s, int energy_id, int project, int precision, dou
         const size_t cap = (size_t)std::max<int64_t>(b.n, 1);
         CK(cudaMallocAsync((void**)&qM, cap * 45 * sizeof(double), st));
         CK(cudaMallocAsync((void**)&qR, cap * sizeof(ClampRef), st));
-        CK(cudaMallocAsync((void**)&qC, 12 * sizeof(int), st));
-        CK(cudaMemsetAsync(qC, 0, 12 * sizeof(int), st));
-        CK(cudaMallocAsync((void**)&qX, cap * 81 * sizeof(float), st));
+        CK(cudaMallocAsync((void**)&qC, (2 + kClampBins) * sizeof(int), st));
+        CK(cudaMemsetAsync(qC, 0, (2 + kClampBins) * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&qX, cap * kClampRec * sizeof(float), st));
         CK(cudaMallocAsync((void**)&qF, cap * sizeof(double), st));
-        CK(cudaMallocAsync((void**)&qB, cap * 10 * sizeof(int), st));
+        CK(cudaMallocAsync((void**)&qB, cap * kClampBins * sizeof(int), st));
     }
     L.clamp_X = qX;
     L.clamp_fro = qF;
@@ -2489,7 +2489,7 @@ int sx_scene_footprint(const sx_scene_desc* d, int64_t* bytes)
     b += nst * (8 + 12 * 8 + 90 * 8 + 16 * 4 * 2 + 4 * 4); // staging, slots, lists
     // the context's projection scratch for the scene's projectable stencils
     // (tets and pairs): 9x9 matrix, reference, float eigenvectors, norm, bins
-    b += (d->n_tets + d->n_pairs) * (45 * 8 + 16 + 81 * 4 + 8 + 10 * 4);
+    b += (d->n_tets + d->n_pairs) * (45 * 8 + 16 + kClampRec * 4 + 8 + kClampBins * 4);
     b += nnzb * (4 + 4 + 4 + 9 * 8);                        // col, slot_ptr, order, values
     b += (nnzb + nnzb / 4 + 64) * (4 + 9 * 8) + N / 8;      // SpMV sliced copy (padded)
     b += 1 << 20;

@@ -1,9 +1,10 @@
 // sx_clamp.cu -- phase 2 of the per-element projection to positive
 // semi-definiteness (§5.2 "Projection to positive semi-definiteness",
 // Algorithm 1): the queued 9x9 translation-free Hessians are
-// eigen-decomposed (float Jacobi, then double Gram-Schmidt and
-// block-restricted double sweeps, sx_clamp.cuh), their negative eigenvalues
-// clamped and the stencils' Hessian blocks rewritten.
+// eigen-decomposed (float Jacobi; then, in double, a certified refinement of
+// the subspace of the k <= 3 lowest eigenvalues, or Gram-Schmidt and
+// block-restricted Jacobi sweeps for the other k: sx_clamp.cuh), their
+// negative eigenvalues clamped and the stencils' Hessian blocks rewritten.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +19,11 @@ namespace sx {
 // per projection)
 #ifndef SX_CLAMP_XF_SMEM
 #define SX_CLAMP_XF_SMEM 1
+#endif
+// stencils with an N block of 1..3 columns: subspace refinement (1) or the
+// block-restricted double Jacobi of every other k (0)
+#ifndef SX_CLAMP_REFINE
+#define SX_CLAMP_REFINE 1
 #endif
 
 // After the eigen-decomposition: flags a non-finite result, else clamps
@@ -136,11 +142,13 @@ k_clamp(ElemLaunch L)
     }
 }
 
-// The projection of a batched evaluation in two launches. The float part
-// runs per queued stencil and bins the stencil by k (the size of its N
-// block, 0..9); the double part then takes the stencils bucket by bucket,
-// so the 32 stencils of a warp share k and the warp runs only the rotations
-// they all need. Every stencil's arithmetic is the same as in k_clamp.
+// The projection of a batched evaluation in split launches. The float part
+// runs per queued stencil, writes its record and bins the stencil by k (the
+// size of its N block, 0..9); the double parts then take the stencils bin by
+// bin, so the 32 stencils of a warp share k: the refinement (k_clamp_refine,
+// k = 1..3) and the block-restricted Jacobi (k_clamp_double, k >= 4 and what
+// the refinement hands over), whose arithmetic is that of k_clamp. k = 0
+// needs nothing (M positive definite by the float Gershgorin test).
 template <int NT>
 __global__ void __launch_bounds__(NT)
 k_clamp_float(ElemLaunch L)
@@ -159,7 +167,7 @@ k_clamp_float(ElemLaunch L)
         }
     const double fro = sqrt(s);
     const int64_t cap = L.clamp_cap;
-    float* Xg = L.clamp_X;   // [81][cap], entry r*9 + slot of stencil idx
+    float* rec = L.clamp_X + idx * kClampRec;   // the stencil's record
 #if SX_CLAMP_XF_SMEM
     extern __shared__ __align__(16) float Xfs[];   // [81][NT]
     const SmemXf Xf{Xfs + threadIdx.x, NT};
@@ -167,9 +175,11 @@ k_clamp_float(ElemLaunch L)
     float xa[81];
     const RegXf Xf{xa};
 #endif
-    const int k = eig9_float_x(Mg, fro, Xf, [&](int r, int slot, float v) {
-        Xg[(int64_t)(r * 9 + slot) * cap + idx] = v;
-    });
+    int k = eig9_float_x(
+        Mg, fro, Xf, [&](int r, int slot, float v) { rec[9 * slot + r] = v; },
+        [&](int slot, float l) { rec[81 + slot] = l; });
+    // a non-finite matrix goes to the full double Jacobi, which reports it
+    if (!isfinite(fro)) k = 9;
     L.clamp_fro[idx] = fro;
     // bucket slot: one atomic per (warp, k) for the lanes that share k
     const unsigned peers = __match_any_sync(__activemask(), k);
@@ -195,11 +205,13 @@ k_clamp_double(ElemLaunch L)
     const SmemMat X{Xs + threadIdx.x, NT};
     __shared__ int s_k, s_off;
     if (threadIdx.x == 0) {
-        // block -> (bucket, offset): buckets in order, ceil(count / NT) blocks each
+        // block -> (bucket, offset): buckets in order, ceil(count / NT) blocks
+        // each (with the N-block refinement, k = 1..3 are done before and k =
+        // 0 needs nothing: M is positive definite)
         int b = blockIdx.x;
         s_k = -1;
         s_off = 0;
-        for (int kk = 0; kk < 10; ++kk) {
+        for (int kk = SX_CLAMP_REFINE ? 4 : 0; kk < 10; ++kk) {
             const int nb = (L.clamp_bucket_count[kk] + NT - 1) / NT;
             if (b < nb) {
                 s_k = kk;
@@ -218,9 +230,9 @@ k_clamp_double(ElemLaunch L)
     if (jj >= cntk) return;
     const int64_t cap = L.clamp_cap;
     const int64_t idx = L.clamp_bucket[(int64_t)k * cap + jj];
-    const float* Xg = L.clamp_X;
+    const float* rec = L.clamp_X + idx * kClampRec;
 #pragma unroll
-    for (int q = 0; q < 81; ++q) X(q / 9, q % 9) = (double)Xg[(int64_t)q * cap + idx];
+    for (int q = 0; q < 81; ++q) X(q % 9, q / 9) = (double)__ldg(rec + q);
     const ClampRef ref = L.clamp_ref[idx];
     const double* Mg = L.clamp_M + 45 * idx;
     const double fro = L.clamp_fro[idx];
@@ -229,6 +241,164 @@ k_clamp_double(ElemLaunch L)
     eig9_double(Mg, X, lam, fro, sizeof(HT) == 4 ? SX_CLAMP_THETA32 : 1e-13, k, live);
     clamp_finish<HT>(L, ref, Mg, X, lam, k, tau, live);
 }
+// N-block refinement of the stencils with k = 1..3 (sx_clamp.cuh). Pass 1
+// takes bins 1..3 and allows one correction; a stencil not certified by
+// then goes to bin kClampPass2 + k, which pass 2 takes with up to three
+// corrections from the same start (so a stencil's result depends only on
+// its own data); one not certified there goes to bin 9, the full double
+// Jacobi. Block -> (bin, offset) as in k_clamp_double.
+template <typename HT, int K, int PASS>
+__device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t idx)
+{
+    const int64_t cap = L.clamp_cap;
+    const float* rec = L.clamp_X + idx * kClampRec;
+    const double* Mg = L.clamp_M + 45 * idx;
+    const double fro = L.clamp_fro[idx];
+    const double tau = 1e-13 * fro;
+    const double thr = (sizeof(HT) == 4 ? SX_CLAMP_THETA32 : 1e-13) * fro;
+    const double thr2 = thr * thr * (9 - K);
+    float mu[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i] = __ldg(rec + 81 + i);
+    double V[9][K], R[9][K], B[K][K];
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int p = 0; p < K; ++p) V[r][p] = (double)__ldg(rec + 9 * p + r);
+    // the float vectors are orthonormal only to float precision: correct
+    // once before the first certified residual
+    refine_residual<K>(Mg, V, R, B);
+    refine_correct<K>(rec, mu, R, V);
+    refine_residual<K>(Mg, V, R, B);
+    constexpr int kMore = PASS == 1 ? 0 : 2;
+    bool conv = false;
+#pragma unroll 1
+    for (int it = 0;; ++it) {
+        bool c = true;
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            double rn = 0.0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) rn = fma(R[r][p], R[r][p], rn);
+            c = c && (rn <= thr2);
+        }
+        conv = c;
+        if (conv || it >= kMore) break;
+        refine_correct<K>(rec, mu, R, V);
+        refine_residual<K>(Mg, V, R, B);
+    }
+    if (!conv) {
+        const int bin = PASS == 1 ? kClampPass2 + K : 9;
+        const int pos = atomicAdd(L.clamp_bucket_count + bin, 1);
+        L.clamp_bucket[(int64_t)bin * cap + pos] = (int)idx;
+        return;
+    }
+    const ClampRef ref = L.clamp_ref[idx];
+    bool ok = true;
+#pragma unroll
+    for (int p = 0; p < K; ++p)
+#pragma unroll
+        for (int j = 0; j < K; ++j) ok = ok && isfinite(B[p][j]);
+    if (!ok) {
+        atomicAdd(L.clamp_failed, 1);
+        atomicExch(&L.scenes[ref.scene].sc->clamp_fail, 1);
+        return;
+    }
+    // B_-: the part of B below -tau
+    if (!refine_negdef<K>(B, tau)) {
+        refine_negpart<K>(B, tau, thr);
+        bool any = false;
+#pragma unroll
+        for (int p = 0; p < K; ++p) any = any || B[p][p] != 0.0;
+        if (!any) return;   // nothing below -tau: the blocks stay as they are
+    }
+    // U = 2 Ut: rows 3 a + r, the Hadamard inverse of V's mode rows (the
+    // 1/2 of Hd is folded into B / 4)
+    double U[12][K];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            const double y1 = V[r][p], y2 = V[3 + r][p], y3 = V[6 + r][p];
+            const double a = y1 + y3, b = y1 - y3;
+            U[r][p] = y2 + a;
+            U[3 + r][p] = y2 - a;
+            U[6 + r][p] = b - y2;
+            U[9 + r][p] = -(b + y2);
+        }
+#pragma unroll
+    for (int p = 0; p < K; ++p)
+#pragma unroll
+        for (int j = 0; j < K; ++j) B[p][j] *= 0.25;
+    const SceneDev& S = L.scenes[ref.scene];
+    const ElemBlock& Bk = S.blk[ref.blk];
+    HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (Bk.base + ref.e);
+    double* full = L.out_H ? L.out_H + 144 * ref.e : nullptr;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        double UB[3][K];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                double t = 0.0;
+#pragma unroll
+                for (int p = 0; p < K; ++p) t = fma(U[3 * a + r][p], B[p][j], t);
+                UB[r][j] = t;
+            }
+#pragma unroll
+        for (int b = a; b < 4; ++b)
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double d = 0.0;
+#pragma unroll
+                    for (int j = 0; j < K; ++j) d = fma(UB[r][j], U[3 * b + c][j], d);
+                    if (staged) {
+                        HT* h = staged + 9 * up_index(a, b) + 3 * r + c;
+                        *h = (HT)((double)*h - d);
+                    } else {
+                        const double h = full[(3 * a + r) * 12 + 3 * b + c] - d;
+                        full[(3 * a + r) * 12 + 3 * b + c] = h;
+                        if (a != b) full[(3 * b + c) * 12 + 3 * a + r] = h;
+                    }
+                }
+    }
+}
+
+template <typename HT, int PASS, int NT>
+__global__ void __launch_bounds__(NT)
+k_clamp_refine(ElemLaunch L)
+{
+    __shared__ int s_k, s_off;
+    constexpr int kb = PASS == 1 ? 1 : kClampPass2 + 1;
+    if (threadIdx.x == 0) {
+        int b = blockIdx.x;
+        s_k = -1;
+        s_off = 0;
+        for (int kk = 0; kk < 3; ++kk) {
+            const int nb = (L.clamp_bucket_count[kb + kk] + NT - 1) / NT;
+            if (b < nb) {
+                s_k = kk + 1;
+                s_off = b * NT;
+                break;
+            }
+            b -= nb;
+        }
+    }
+    __syncthreads();
+    const int k = s_k;
+    if (k < 0) return;
+    const int bin = kb + k - 1;
+    const int jj = s_off + threadIdx.x;
+    if (jj >= L.clamp_bucket_count[bin]) return;
+    const int64_t idx = L.clamp_bucket[(int64_t)bin * L.clamp_cap + jj];
+    if (k == 1) clamp_refine_one<HT, 1, PASS>(L, idx);
+    else if (k == 2) clamp_refine_one<HT, 2, PASS>(L, idx);
+    else clamp_refine_one<HT, 3, PASS>(L, idx);
+}
+
 cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
 {
     if (L.ntiles == 0 || !(L.level >= 2 && L.project)) return cudaSuccess;
@@ -268,6 +438,16 @@ cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
         const int64_t cap = L.clamp_cap;
         const int ga = (int)std::max<int64_t>(1, (cap + 127) / 128);
         k_clamp_float<128><<<ga, 128, SX_CLAMP_XF_SMEM ? 81 * 4 * 128 : 0, s>>>(L);
+        if (SX_CLAMP_REFINE) {
+            const int gr = (int)std::max<int64_t>(1, (cap + 127) / 128 + 3);
+            if (f32) {
+                k_clamp_refine<float, 1, 128><<<gr, 128, 0, s>>>(L);
+                k_clamp_refine<float, 2, 128><<<gr, 128, 0, s>>>(L);
+            } else {
+                k_clamp_refine<double, 1, 128><<<gr, 128, 0, s>>>(L);
+                k_clamp_refine<double, 2, 128><<<gr, 128, 0, s>>>(L);
+            }
+        }
         const int gb = (int)std::max<int64_t>(1, (cap + nt - 1) / nt + 10);
         if (nt == 32) {
             if (f32) k_clamp_double<float, 32><<<gb, 32, smem, s>>>(L);

@@ -28,6 +28,11 @@
 //      are clamped: M' = M - sum of lambda v v^T over them, and the
 //      stencil's Hessian is rewritten as (Hd kron I3) diag(0, M')
 //      (Hd kron I3)^T.
+//   For k = 1..3 (nearly every queued SNH tet: its negative modes are
+//   the rotational ones) the double part instead refines the k-column
+//   subspace alone, with a certified residual (see "N-block refinement"
+//   below); the Jacobi described above is the path of every other k and of
+//   a stencil the refinement does not certify.
 //   Accuracy: clamping at zero is 1-Lipschitz in the Frobenius norm on
 //   symmetric matrices, so the projection is off by at most about twice the
 //   Frobenius norm of the N-N and N-P off-diagonal entries left in At
@@ -316,9 +321,13 @@ __device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat&
 // entry r of the column that lands in `slot`. Returns k, the number of
 // eigenvalues below delta = 1e-5 ||M||_F (9 when a Gershgorin test on the
 // float matrix cannot confirm that the rest is a positive definite block).
-template <typename XF, typename Put>
+// putl(slot, value) receives the float eigenvalue that lands in `slot`.
+struct NoPutL {
+    __device__ __forceinline__ void operator()(int, float) const {}
+};
+template <typename XF, typename Put, typename PutL = NoPutL>
 __device__ __forceinline__ int eig9_float_x(const double* __restrict__ Mg, double fro, const XF& Xf,
-                                            Put put)
+                                            Put put, PutL putl = PutL())
 {
     int k = 0;
     float A[45];
@@ -347,6 +356,7 @@ __device__ __forceinline__ int eig9_float_x(const double* __restrict__ Mg, doubl
         if (lc >= delta) pblock_ok = pblock_ok && (lc - rad > 0.5f * delta);
 #pragma unroll
         for (int r = 0; r < 9; ++r) put(r, rank, Xf(r, c));
+        putl(rank, lc);
     }
     return pblock_ok ? k : 9;
 }
@@ -422,6 +432,213 @@ __device__ __forceinline__ int eig9(const double* __restrict__ Mg, const SmemMat
     const int k = eig9_float(Mg, fro, [&](int r, int slot, float v) { X(r, slot) = (double)v; });
     eig9_double(Mg, X, lam, fro, theta, k, live);
     return k;
+}
+
+// ------------------------------------------------- N-block refinement (k <= 3)
+// For a small N block the double part need not re-orthonormalize and
+// rotate the whole 9x9: only the invariant subspace of the k lowest
+// eigenvalues enters the clamp. It is refined as a subspace (Rayleigh-Ritz
+// with a first-order correction, Golub & Van Loan 8.1, 8.2):
+//   V = the k float eigenvectors of N (double), W = M V, B = V^T W (k x k),
+//   R = W - V B, the part of M V outside span(V). With V orthonormal, V
+//   spans an invariant subspace of M to within ||R||. The correction
+//   v_p -= sum_{q in P} x_q (x_q . r_p) / (mu_q - mu_p), over the float
+//   eigenpairs (mu_q, x_q) of the P block, removes R to first order; it only
+//   has to be as accurate as float (it moves V by ~1e-7), so it runs in
+//   float arithmetic. V is then re-orthonormalized (modified Gram-Schmidt)
+//   and R recomputed in double, which certifies the result: a stencil is
+//   done once ||r_p|| <= theta ||M||_F sqrt(9 - k) for every column p (the
+//   same bound as k (9 - k) couplings of at most theta ||M||_F each).
+// Then M' = M - V B_- V^T, with B_- the part of B below -tau (B itself when
+// -B - tau I is positive definite, else from a small Jacobi on B), and the
+// stencil's blocks become H - Ut B_- Ut^T with Ut = (Hd kron I3)(0; V).
+// A stencil that is not certified after its allowed corrections is handed
+// to the full double Jacobi (k = 9). Every step is per lane, so a stencil's
+// result does not depend on the other stencils of its warp.
+
+template <int K>
+__device__ __forceinline__ void refine_mgs(double (&V)[9][K])
+{
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+#pragma unroll
+        for (int j = 0; j < p; ++j) {
+            double d = 0.0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) d = fma(V[r][j], V[r][p], d);
+#pragma unroll
+            for (int r = 0; r < 9; ++r) V[r][p] = fma(-d, V[r][j], V[r][p]);
+        }
+        double nn = 0.0;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) nn = fma(V[r][p], V[r][p], nn);
+        const double inv = rsqrt(nn);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) V[r][p] *= inv;
+    }
+}
+
+// W = M V, B = V^T W (symmetric: the lower triangle, mirrored), R = W - V B
+// (R returned in place of W)
+template <int K>
+__device__ __forceinline__ void refine_residual(const double* __restrict__ Mg,
+                                                const double (&V)[9][K], double (&R)[9][K],
+                                                double (&B)[K][K])
+{
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        double mr[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) mr[c] = __ldg(Mg + pk(r, c));
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) s = fma(mr[c], V[c][p], s);
+            R[r][p] = s;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < K; ++p)
+#pragma unroll
+        for (int j = 0; j <= p; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) s = fma(V[r][p], R[r][j], s);
+            B[p][j] = s;
+            B[j][p] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            double s = R[r][p];
+#pragma unroll
+            for (int j = 0; j < K; ++j) s = fma(-V[r][j], B[j][p], s);
+            R[r][p] = s;
+        }
+}
+
+// first-order correction of V from the float eigenpairs of the P block
+// (rec: the stencil's record, eigenvector q at rec[9 q]; mu: eigenvalues)
+template <int K>
+__device__ __forceinline__ void refine_correct(const float* __restrict__ rec, const float (&mu)[9],
+                                               const double (&R)[9][K], double (&V)[9][K])
+{
+    float rf[9][K], dv[9][K];
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            rf[r][p] = (float)R[r][p];
+            dv[r][p] = 0.0f;
+        }
+#pragma unroll
+    for (int q = K; q < 9; ++q) {
+        float xq[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) xq[r] = __ldg(rec + 9 * q + r);
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            float c = 0.0f;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) c = fmaf(xq[r], rf[r][p], c);
+            const float z = __fdividef(c, mu[q] - mu[p]);
+#pragma unroll
+            for (int r = 0; r < 9; ++r) dv[r][p] = fmaf(xq[r], z, dv[r][p]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int p = 0; p < K; ++p) V[r][p] -= (double)dv[r][p];
+    refine_mgs<K>(V);
+}
+
+// true when -B - tau I is positive definite (every eigenvalue of B below
+// -tau): LDL^T without pivoting
+template <int K>
+__device__ __forceinline__ bool refine_negdef(const double (&B)[K][K], double tau)
+{
+    double L[K][K], dg[K];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        double s = -B[j][j] - tau;
+#pragma unroll
+        for (int m = 0; m < j; ++m) s -= L[j][m] * L[j][m] * dg[m];
+        ok = ok && (s > 0.0);
+        dg[j] = s;
+#pragma unroll
+        for (int i = j + 1; i < K; ++i) {
+            double t = -B[i][j];
+#pragma unroll
+            for (int m = 0; m < j; ++m) t -= L[i][m] * L[j][m] * dg[m];
+            L[i][j] = t / s;
+        }
+    }
+    return ok;
+}
+
+// B <- its part below -tau, sum over eigenvalues l < -tau of l g g^T
+// (cyclic Jacobi on the k x k B, rotations skipped at |b_pq| <= thr)
+template <int K>
+__device__ __forceinline__ void refine_negpart(double (&B)[K][K], double tau, double thr)
+{
+    double A[K][K], G[K][K];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            A[i][j] = B[i][j];
+            G[i][j] = i == j ? 1.0 : 0.0;
+        }
+#pragma unroll 1
+    for (int sw = 0; sw < 10; ++sw) {
+        bool any = false;
+#pragma unroll
+        for (int p = 0; p < K; ++p)
+#pragma unroll
+            for (int q = p + 1; q < K; ++q) {
+                const double apq = A[p][q];
+                if (!(fabs(apq) > thr)) continue;
+                any = true;
+                const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
+                const double t = copysign(1.0, th) / (fabs(th) + sqrt(fma(th, th, 1.0)));
+                const double c = rsqrt(fma(t, t, 1.0)), s = t * c;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const double arp = A[r][p], arq = A[r][q];
+                    A[r][p] = fma(c, arp, -s * arq);
+                    A[r][q] = fma(s, arp, c * arq);
+                }
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const double apr = A[p][r], aqr = A[q][r];
+                    A[p][r] = fma(c, apr, -s * aqr);
+                    A[q][r] = fma(s, apr, c * aqr);
+                }
+                A[p][q] = 0.0;
+                A[q][p] = 0.0;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const double gp = G[r][p], gq = G[r][q];
+                    G[r][p] = fma(c, gp, -s * gq);
+                    G[r][q] = fma(s, gp, c * gq);
+                }
+            }
+        if (!any) break;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int l = 0; l < K; ++l)
+                s = A[l][l] < -tau ? fma(A[l][l] * G[i][l], G[j][l], s) : s;
+            B[i][j] = s;
+        }
 }
 
 }  // namespace sx

@@ -317,7 +317,7 @@ cudaError_t launch_elements(const ElemLaunch& L, int grid, cudaStream_t s)
     if (L.level >= 2 && L.project) {
         err = cudaMemsetAsync(L.clamp_count, 0, sizeof(int), s);
         if (err == cudaSuccess && L.clamp_bucket_count)
-            err = cudaMemsetAsync(L.clamp_bucket_count, 0, 10 * sizeof(int), s);
+            err = cudaMemsetAsync(L.clamp_bucket_count, 0, kClampBins * sizeof(int), s);
         if (err != cudaSuccess) return err;
     }
     const bool f = L.precision == SX_FP32;

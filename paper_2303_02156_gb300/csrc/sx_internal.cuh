@@ -187,6 +187,12 @@ struct ClampRef {
     int64_t e;   // element index inside its energy block
 };
 
+// per queued stencil record of the split projection (floats): 81 for the
+// ordered float eigenvectors (column c at 9 c), 9 for the eigenvalues, pad
+constexpr int kClampRec = 96;
+constexpr int kClampBins = 16;
+constexpr int kClampPass2 = 10;
+
 struct ElemLaunch {
     const SceneDev* scenes;
     const Tile* tiles;
@@ -214,9 +220,12 @@ struct ElemLaunch {
     int* clamp_failed;
     int clamp_cap;
     int clamp_grid;
-    // two-launch projection (batched evaluations; null: one fused launch):
-    // float eigenvectors [81][clamp_cap], ||M||_F per queued stencil, and
-    // the queue positions binned by N-block size k (10 bins of clamp_cap)
+    // split projection (batched evaluations; null: one fused launch): a
+    // record of kClampRec floats per queued stencil (its float eigenvectors
+    // by ascending eigenvalue, column after column, then the 9 eigenvalues),
+    // ||M||_F per queued stencil, and the queue positions binned
+    // (kClampBins bins of clamp_cap: 0..9 by N-block size k, kClampPass2 + k
+    // for the second refinement pass of k = 1..3)
     float* clamp_X;
     double* clamp_fro;
     int* clamp_bucket;
