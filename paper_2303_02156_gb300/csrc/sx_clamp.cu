@@ -14,12 +14,6 @@
 
 namespace sx {
 
-// float part: its eigenvector matrix in shared memory (1) or registers (0);
-// shared memory measured 1% faster on the 64^3 SNH cube (9.67 vs 9.75 ms
-// per projection)
-#ifndef SX_CLAMP_XF_SMEM
-#define SX_CLAMP_XF_SMEM 1
-#endif
 // stencils with an N block of 1..3 columns: subspace refinement (1) or the
 // block-restricted double Jacobi of every other k (0)
 #ifndef SX_CLAMP_REFINE
@@ -149,47 +143,82 @@ k_clamp(ElemLaunch L)
 // k = 1..3) and the block-restricted Jacobi (k_clamp_double, k >= 4 and what
 // the refinement hands over), whose arithmetic is that of k_clamp. k = 0
 // needs nothing (M positive definite by the float Gershgorin test).
+// float part: one thread per queued stencil; its eigenvector matrix lives in
+// shared memory ([81][NT + 1]: the odd stride keeps the copy-out free of
+// bank conflicts), next to [NT][17] words of eigenvalues and slot order.
+// The block's records are contiguous (record = queue position), so they are
+// copied out by the whole block with coalesced stores.
+constexpr int kClampFloatThreads = 128;
+constexpr int clamp_float_smem(int nt) { return (81 * (nt + 1) + 17 * nt) * 4; }
+
 template <int NT>
 __global__ void __launch_bounds__(NT)
 k_clamp_float(ElemLaunch L)
 {
+    extern __shared__ __align__(16) float Xfs[];
+    constexpr int XS = NT + 1;
+    float* Ms = Xfs + 81 * XS;
     const int count = min(*L.clamp_count, L.clamp_cap);
-    const int64_t idx = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (idx >= count) return;
-    const double* Mg = L.clamp_M + 45 * idx;
-    double s = 0.0;
+    const int64_t base = (int64_t)blockIdx.x * NT;
+    if (base >= count) return;   // the whole block
+    const int64_t idx = base + threadIdx.x;
+    if (idx < count) {
+        const double* Mg = L.clamp_M + 45 * idx;
+        double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < 9; ++i)
 #pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            const double v = Mg[pk(i, j)];
-            s = fma((i == j ? 1.0 : 2.0) * v, v, s);
-        }
-    const double fro = sqrt(s);
-    const int64_t cap = L.clamp_cap;
-    float* rec = L.clamp_X + idx * kClampRec;   // the stencil's record
-#if SX_CLAMP_XF_SMEM
-    extern __shared__ __align__(16) float Xfs[];   // [81][NT]
-    const SmemXf Xf{Xfs + threadIdx.x, NT};
-#else
-    float xa[81];
-    const RegXf Xf{xa};
-#endif
-    int k = eig9_float_x(
-        Mg, fro, Xf, [&](int r, int slot, float v) { rec[9 * slot + r] = v; },
-        [&](int slot, float l) { rec[81 + slot] = l; });
-    // a non-finite matrix goes to the full double Jacobi, which reports it
-    if (!isfinite(fro)) k = 9;
-    L.clamp_fro[idx] = fro;
-    // bucket slot: one atomic per (warp, k) for the lanes that share k
-    const unsigned peers = __match_any_sync(__activemask(), k);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(L.clamp_bucket_count + k, __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    const int pos = base + __popc(peers & ((1u << lane) - 1u));
-    L.clamp_bucket[(int64_t)k * cap + pos] = (int)idx;
+            for (int j = 0; j <= i; ++j) {
+                const double v = Mg[pk(i, j)];
+                s = fma((i == j ? 1.0 : 2.0) * v, v, s);
+            }
+        const double fro = sqrt(s);
+        const int64_t cap = L.clamp_cap;
+        const SmemXf Xf{Xfs + threadIdx.x, XS};
+        float* ms = Ms + 17 * threadIdx.x;
+        unsigned long long order = 0ull;
+        int k = eig9_float_x(
+            Mg, fro, Xf, [](int, int, float) {},
+            [&](int slot, int c, float l) {
+                ms[c] = l;
+                order |= (unsigned long long)c << (4 * slot);
+            });
+        ms[9] = __uint_as_float((unsigned)order);
+        ms[10] = __uint_as_float((unsigned)(order >> 32));
+        // a non-finite matrix goes to the full double Jacobi, which reports it
+        if (!isfinite(fro)) k = 9;
+        L.clamp_fro[idx] = fro;
+        // bucket slot: one atomic per (warp, k) for the lanes that share k
+        const unsigned peers = __match_any_sync(__activemask(), k);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        int b0 = 0;
+        if (lane == leader) b0 = atomicAdd(L.clamp_bucket_count + k, __popc(peers));
+        b0 = __shfl_sync(peers, b0, leader);
+        const int pos = b0 + __popc(peers & ((1u << lane) - 1u));
+        L.clamp_bucket[(int64_t)k * cap + pos] = (int)idx;
+    }
+    __syncthreads();
+    const int nrec = (int)(count - base < NT ? count - base : NT);
+    float* dst = L.clamp_X + base * kClampRec;
+    for (int g = threadIdx.x; g < nrec * kClampRec; g += NT) {
+        const int t = g / kClampRec, j = g - t * kClampRec;
+        float v = 0.0f;
+        if (j < 81) v = Xfs[((j % 9) * 9 + j / 9) * XS + t];
+        else if (j < 92) v = Ms[17 * t + (j - 81)];
+        dst[g] = v;
+    }
+}
+
+// the column of ascending-eigenvalue slot `slot` in a stencil's record
+__device__ __forceinline__ unsigned long long rec_order(const float* rec)
+{
+    return (unsigned long long)__float_as_uint(__ldg(rec + 90)) |
+           ((unsigned long long)__float_as_uint(__ldg(rec + 91)) << 32);
+}
+__device__ __forceinline__ int rec_col(unsigned long long order, int slot)
+{
+    return (int)((order >> (4 * slot)) & 15ull);
 }
 
 // resident threads per SM the double part is compiled for (a register cap:
@@ -197,42 +226,22 @@ k_clamp_float(ElemLaunch L)
 #ifndef SX_CLAMP_MINB_THREADS
 #define SX_CLAMP_MINB_THREADS 256
 #endif
-template <typename HT, int NT>
-__global__ void __launch_bounds__(NT, (SX_CLAMP_MINB_THREADS / NT) > 0 ? SX_CLAMP_MINB_THREADS / NT : 1)
-k_clamp_double(ElemLaunch L)
+// one stencil of bin k (position jj) through the block-restricted double
+// Jacobi
+template <typename HT>
+__device__ __forceinline__ void clamp_double_one(const ElemLaunch& L, const SmemMat& X, int k,
+                                                 int jj, unsigned live)
 {
-    extern __shared__ __align__(16) double Xs[];   // [81][NT]
-    const SmemMat X{Xs + threadIdx.x, NT};
-    __shared__ int s_k, s_off;
-    if (threadIdx.x == 0) {
-        // block -> (bucket, offset): buckets in order, ceil(count / NT) blocks
-        // each (with the N-block refinement, k = 1..3 are done before and k =
-        // 0 needs nothing: M is positive definite)
-        int b = blockIdx.x;
-        s_k = -1;
-        s_off = 0;
-        for (int kk = SX_CLAMP_REFINE ? 4 : 0; kk < 10; ++kk) {
-            const int nb = (L.clamp_bucket_count[kk] + NT - 1) / NT;
-            if (b < nb) {
-                s_k = kk;
-                s_off = b * NT;
-                break;
-            }
-            b -= nb;
-        }
-    }
-    __syncthreads();
-    const int k = s_k;
-    if (k < 0) return;
-    const int cntk = L.clamp_bucket_count[k];
-    const int jj = s_off + threadIdx.x;
-    const unsigned live = __ballot_sync(0xffffffffu, jj < cntk);
-    if (jj >= cntk) return;
     const int64_t cap = L.clamp_cap;
     const int64_t idx = L.clamp_bucket[(int64_t)k * cap + jj];
     const float* rec = L.clamp_X + idx * kClampRec;
+    const unsigned long long order = rec_order(rec);
 #pragma unroll
-    for (int q = 0; q < 81; ++q) X(q % 9, q / 9) = (double)__ldg(rec + q);
+    for (int c = 0; c < 9; ++c) {
+        const int col = rec_col(order, c);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) X(r, c) = (double)__ldg(rec + 9 * col + r);
+    }
     const ClampRef ref = L.clamp_ref[idx];
     const double* Mg = L.clamp_M + 45 * idx;
     const double fro = L.clamp_fro[idx];
@@ -241,14 +250,55 @@ k_clamp_double(ElemLaunch L)
     eig9_double(Mg, X, lam, fro, sizeof(HT) == 4 ? SX_CLAMP_THETA32 : 1e-13, k, live);
     clamp_finish<HT>(L, ref, Mg, X, lam, k, tau, live);
 }
+
+template <typename HT, int NT>
+__global__ void __launch_bounds__(NT, (SX_CLAMP_MINB_THREADS / NT) > 0 ? SX_CLAMP_MINB_THREADS / NT : 1)
+k_clamp_double(ElemLaunch L)
+{
+    extern __shared__ __align__(16) double Xs[];   // [81][NT]
+    const SmemMat X{Xs + threadIdx.x, NT};
+    __shared__ int s_k, s_off;
+    // work unit b -> (bucket, offset): buckets in order, ceil(count / NT)
+    // units each; the grid loops over the units (with the N-block
+    // refinement, k = 1..3 are done before and k = 0 needs nothing: M is
+    // positive definite, so few stencils are left here)
+    for (int b0 = blockIdx.x;; b0 += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int b = b0;
+            s_k = -1;
+            s_off = 0;
+            for (int kk = SX_CLAMP_REFINE ? 4 : 0; kk < 10; ++kk) {
+                const int nb = (L.clamp_bucket_count[kk] + NT - 1) / NT;
+                if (b < nb) {
+                    s_k = kk;
+                    s_off = b * NT;
+                    break;
+                }
+                b -= nb;
+            }
+        }
+        __syncthreads();
+        const int k = s_k;
+        const int jj = s_off + threadIdx.x;
+        __syncthreads();   // s_k, s_off read by all before thread 0 rewrites them
+        if (k < 0) return;
+        const int cntk = L.clamp_bucket_count[k];
+        const unsigned live = __ballot_sync(0xffffffffu, jj < cntk);
+        if (jj >= cntk) continue;
+        clamp_double_one<HT>(L, X, k, jj, live);
+    }
+}
+
 // N-block refinement of the stencils with k = 1..3 (sx_clamp.cuh). Pass 1
-// takes bins 1..3 and allows one correction; a stencil not certified by
-// then goes to bin kClampPass2 + k, which pass 2 takes with up to three
-// corrections from the same start (so a stencil's result depends only on
-// its own data); one not certified there goes to bin 9, the full double
-// Jacobi. Block -> (bin, offset) as in k_clamp_double.
+// takes bins 1..3, refines the k-column subspace and allows one
+// correction; a stencil not certified by then goes to bin kClampPass2 + k.
+// Pass 2 starts again from the float vectors and allows up to three
+// corrections; a stencil not certified there goes to bin 9, the full double
+// Jacobi. A stencil's result depends only on its own data. (A wider
+// subspace in pass 2, max(k + 1, 3) columns, certified every stencil of a
+// sample but measured slower on the 40^3 cube: 0.39 against 0.23 ms.)
 template <typename HT, int K, int PASS>
-__device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t idx)
+__device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t idx, int k)
 {
     const int64_t cap = L.clamp_cap;
     const float* rec = L.clamp_X + idx * kClampRec;
@@ -257,18 +307,24 @@ __device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t id
     const double tau = 1e-13 * fro;
     const double thr = (sizeof(HT) == 4 ? SX_CLAMP_THETA32 : 1e-13) * fro;
     const double thr2 = thr * thr * (9 - K);
+    // the record's eigenpairs in ascending order: slot q is column cq[q]
+    const unsigned long long order = rec_order(rec);
     float mu[9];
+    int cq[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) mu[i] = __ldg(rec + 81 + i);
+    for (int q = 0; q < 9; ++q) {
+        cq[q] = rec_col(order, q);
+        mu[q] = __ldg(rec + 81 + cq[q]);
+    }
     double V[9][K], R[9][K], B[K][K];
 #pragma unroll
-    for (int r = 0; r < 9; ++r)
+    for (int p = 0; p < K; ++p)
 #pragma unroll
-        for (int p = 0; p < K; ++p) V[r][p] = (double)__ldg(rec + 9 * p + r);
+        for (int r = 0; r < 9; ++r) V[r][p] = (double)__ldg(rec + 9 * cq[p] + r);
     // the float vectors are orthonormal only to float precision: correct
     // once before the first certified residual
     refine_residual<K>(Mg, V, R, B);
-    refine_correct<K>(rec, mu, R, V);
+    refine_correct<K>(rec, cq, mu, R, V);
     refine_residual<K>(Mg, V, R, B);
     constexpr int kMore = PASS == 1 ? 0 : 2;
     bool conv = false;
@@ -284,11 +340,11 @@ __device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t id
         }
         conv = c;
         if (conv || it >= kMore) break;
-        refine_correct<K>(rec, mu, R, V);
+        refine_correct<K>(rec, cq, mu, R, V);
         refine_residual<K>(Mg, V, R, B);
     }
     if (!conv) {
-        const int bin = PASS == 1 ? kClampPass2 + K : 9;
+        const int bin = PASS == 1 ? kClampPass2 + k : 9;
         const int pos = atomicAdd(L.clamp_bucket_count + bin, 1);
         L.clamp_bucket[(int64_t)bin * cap + pos] = (int)idx;
         return;
@@ -373,30 +429,52 @@ k_clamp_refine(ElemLaunch L)
 {
     __shared__ int s_k, s_off;
     constexpr int kb = PASS == 1 ? 1 : kClampPass2 + 1;
-    if (threadIdx.x == 0) {
-        int b = blockIdx.x;
-        s_k = -1;
-        s_off = 0;
-        for (int kk = 0; kk < 3; ++kk) {
-            const int nb = (L.clamp_bucket_count[kb + kk] + NT - 1) / NT;
-            if (b < nb) {
-                s_k = kk + 1;
-                s_off = b * NT;
-                break;
+    // work unit b -> (bin, offset) over the three bins; the grid loops
+    for (int b0 = blockIdx.x;; b0 += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int b = b0;
+            s_k = -1;
+            s_off = 0;
+            for (int kk = 0; kk < 3; ++kk) {
+                const int nb = (L.clamp_bucket_count[kb + kk] + NT - 1) / NT;
+                if (b < nb) {
+                    s_k = kk + 1;
+                    s_off = b * NT;
+                    break;
+                }
+                b -= nb;
             }
-            b -= nb;
         }
+        __syncthreads();
+        const int k = s_k;
+        const int jj = s_off + threadIdx.x;
+        __syncthreads();   // s_k, s_off read by all before thread 0 rewrites them
+        if (k < 0) return;
+        const int bin = kb + k - 1;
+        if (jj >= L.clamp_bucket_count[bin]) continue;
+        const int64_t idx = L.clamp_bucket[(int64_t)bin * L.clamp_cap + jj];
+        if (k == 1) clamp_refine_one<HT, 1, PASS>(L, idx, k);
+        else if (k == 2) clamp_refine_one<HT, 2, PASS>(L, idx, k);
+        else clamp_refine_one<HT, 3, PASS>(L, idx, k);
     }
-    __syncthreads();
-    const int k = s_k;
-    if (k < 0) return;
-    const int bin = kb + k - 1;
-    const int jj = s_off + threadIdx.x;
-    if (jj >= L.clamp_bucket_count[bin]) return;
-    const int64_t idx = L.clamp_bucket[(int64_t)bin * L.clamp_cap + jj];
-    if (k == 1) clamp_refine_one<HT, 1, PASS>(L, idx);
-    else if (k == 2) clamp_refine_one<HT, 2, PASS>(L, idx);
-    else clamp_refine_one<HT, 3, PASS>(L, idx);
+}
+
+// SM count of the current device (cached per device): the looping grids of
+// the refinement's second pass and of the double part are sized by it
+static int device_sms()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 152;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        v = 152;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
 }
 
 cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
@@ -430,25 +508,38 @@ cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
                              (const void*)k_clamp_double<double, 256>};
         for (const void* f : fns)
             cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kClampMaxSmem);
+        cudaFuncSetAttribute((const void*)k_clamp_float<kClampFloatThreads>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             clamp_float_smem(kClampFloatThreads));
         attr_done.fetch_or(bit, std::memory_order_release);
     }
     const bool f32 = L.precision == SX_FP32;
     if (L.clamp_X) {
         // two launches: float part binned by k, then the double part per bucket
         const int64_t cap = L.clamp_cap;
-        const int ga = (int)std::max<int64_t>(1, (cap + 127) / 128);
-        k_clamp_float<128><<<ga, 128, SX_CLAMP_XF_SMEM ? 81 * 4 * 128 : 0, s>>>(L);
+        const int ga = (int)std::max<int64_t>(1, (cap + kClampFloatThreads - 1) / kClampFloatThreads);
+        k_clamp_float<kClampFloatThreads>
+            <<<ga, kClampFloatThreads, clamp_float_smem(kClampFloatThreads), s>>>(L);
+        const int sms = device_sms();
         if (SX_CLAMP_REFINE) {
+            // pass 1 covers its largest possible work in one trip; pass 2
+            // (a few percent of the stencils) loops over a grid of 8 blocks
+            // per SM
             const int gr = (int)std::max<int64_t>(1, (cap + 127) / 128 + 3);
+            const int gr2 = std::min(gr, 8 * sms);
             if (f32) {
                 k_clamp_refine<float, 1, 128><<<gr, 128, 0, s>>>(L);
-                k_clamp_refine<float, 2, 128><<<gr, 128, 0, s>>>(L);
+                k_clamp_refine<float, 2, 128><<<gr2, 128, 0, s>>>(L);
             } else {
                 k_clamp_refine<double, 1, 128><<<gr, 128, 0, s>>>(L);
-                k_clamp_refine<double, 2, 128><<<gr, 128, 0, s>>>(L);
+                k_clamp_refine<double, 2, 128><<<gr2, 128, 0, s>>>(L);
             }
         }
-        const int gb = (int)std::max<int64_t>(1, (cap + nt - 1) / nt + 10);
+        // the double part loops over its units with at most 4 blocks per SM
+        // (256 / nt more for smaller blocks); every stencil when the
+        // refinement is off
+        const int gfull = (int)std::max<int64_t>(1, (cap + nt - 1) / nt + 10);
+        const int gb = SX_CLAMP_REFINE ? std::min(gfull, 4 * (256 / nt) * sms) : gfull;
         if (nt == 32) {
             if (f32) k_clamp_double<float, 32><<<gb, 32, smem, s>>>(L);
             else k_clamp_double<double, 32><<<gb, 32, smem, s>>>(L);

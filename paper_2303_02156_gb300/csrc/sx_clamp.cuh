@@ -321,9 +321,10 @@ __device__ __forceinline__ void jacobi_sweep_f64(double (&A)[45], const SmemMat&
 // entry r of the column that lands in `slot`. Returns k, the number of
 // eigenvalues below delta = 1e-5 ||M||_F (9 when a Gershgorin test on the
 // float matrix cannot confirm that the rest is a positive definite block).
-// putl(slot, value) receives the float eigenvalue that lands in `slot`.
+// putl(slot, c, value) receives the float eigenvalue of column c, which
+// lands in `slot`.
 struct NoPutL {
-    __device__ __forceinline__ void operator()(int, float) const {}
+    __device__ __forceinline__ void operator()(int, int, float) const {}
 };
 template <typename XF, typename Put, typename PutL = NoPutL>
 __device__ __forceinline__ int eig9_float_x(const double* __restrict__ Mg, double fro, const XF& Xf,
@@ -356,7 +357,7 @@ __device__ __forceinline__ int eig9_float_x(const double* __restrict__ Mg, doubl
         if (lc >= delta) pblock_ok = pblock_ok && (lc - rad > 0.5f * delta);
 #pragma unroll
         for (int r = 0; r < 9; ++r) put(r, rank, Xf(r, c));
-        putl(rank, lc);
+        putl(rank, c, lc);
     }
     return pblock_ok ? k : 9;
 }
@@ -520,10 +521,12 @@ __device__ __forceinline__ void refine_residual(const double* __restrict__ Mg,
 }
 
 // first-order correction of V from the float eigenpairs of the P block
-// (rec: the stencil's record, eigenvector q at rec[9 q]; mu: eigenvalues)
+// (rec: the stencil's record, the eigenvector of ascending slot q at
+// rec[9 cq[q]]; mu: the eigenvalues by slot)
 template <int K>
-__device__ __forceinline__ void refine_correct(const float* __restrict__ rec, const float (&mu)[9],
-                                               const double (&R)[9][K], double (&V)[9][K])
+__device__ __forceinline__ void refine_correct(const float* __restrict__ rec, const int (&cq)[9],
+                                               const float (&mu)[9], const double (&R)[9][K],
+                                               double (&V)[9][K])
 {
     float rf[9][K], dv[9][K];
 #pragma unroll
@@ -537,7 +540,7 @@ __device__ __forceinline__ void refine_correct(const float* __restrict__ rec, co
     for (int q = K; q < 9; ++q) {
         float xq[9];
 #pragma unroll
-        for (int r = 0; r < 9; ++r) xq[r] = __ldg(rec + 9 * q + r);
+        for (int r = 0; r < 9; ++r) xq[r] = __ldg(rec + 9 * cq[q] + r);
 #pragma unroll
         for (int p = 0; p < K; ++p) {
             float c = 0.0f;

@@ -187,8 +187,10 @@ struct ClampRef {
     int64_t e;   // element index inside its energy block
 };
 
-// per queued stencil record of the split projection (floats): 81 for the
-// ordered float eigenvectors (column c at 9 c), 9 for the eigenvalues, pad
+// per queued stencil record of the split projection (floats): the float
+// eigenvectors as the Jacobi left them (column c at 9 c), their 9
+// eigenvalues (81 + c), and the column of each ascending-eigenvalue slot
+// (4 bits per slot in the two words at 90), pad
 constexpr int kClampRec = 96;
 constexpr int kClampBins = 16;
 constexpr int kClampPass2 = 10;
@@ -221,8 +223,8 @@ struct ElemLaunch {
     int clamp_cap;
     int clamp_grid;
     // split projection (batched evaluations; null: one fused launch): a
-    // record of kClampRec floats per queued stencil (its float eigenvectors
-    // by ascending eigenvalue, column after column, then the 9 eigenvalues),
+    // record of kClampRec floats per queued stencil (its float eigenvectors,
+    // their eigenvalues and their order),
     // ||M||_F per queued stencil, and the queue positions binned
     // (kClampBins bins of clamp_cap: 0..9 by N-block size k, kClampPass2 + k
     // for the second refinement pass of k = 1..3)
