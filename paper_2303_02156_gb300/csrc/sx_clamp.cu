@@ -260,14 +260,15 @@ k_clamp_double(ElemLaunch L)
     __shared__ int s_k, s_off;
     // work unit b -> (bucket, offset): buckets in order, ceil(count / NT)
     // units each; the grid loops over the units (with the N-block
-    // refinement, k = 1..3 are done before and k = 0 needs nothing: M is
-    // positive definite, so few stencils are left here)
+    // refinement, k = 1..3 are done before, k = 0 needs nothing (M is
+    // positive definite) and bin 9 goes to k_clamp_warp, so few stencils are
+    // left here)
     for (int b0 = blockIdx.x;; b0 += gridDim.x) {
         if (threadIdx.x == 0) {
             int b = b0;
             s_k = -1;
             s_off = 0;
-            for (int kk = SX_CLAMP_REFINE ? 4 : 0; kk < 10; ++kk) {
+            for (int kk = SX_CLAMP_REFINE ? 4 : 0; kk < (SX_CLAMP_REFINE ? 9 : 10); ++kk) {
                 const int nb = (L.clamp_bucket_count[kk] + NT - 1) / NT;
                 if (b < nb) {
                     s_k = kk;
@@ -459,6 +460,189 @@ k_clamp_refine(ElemLaunch L)
     }
 }
 
+// Bin 9 (no certified small N block: the float Gershgorin test failed, or
+// the refinement did not certify the stencil) holds few stencils, and one
+// warp running a full double Jacobi for a thread's stencil takes a long
+// time on this GPU (a warp's FP64 instruction occupies its SM quarter for
+// 64 cycles). Here a warp takes one stencil and spreads the work over its
+// lanes: the same algorithm as the k = 9 path of k_clamp_double (modified
+// Gram-Schmidt of the float vectors, At = X^T M X, up to SX_F64_SWEEPS
+// cyclic sweeps skipping |a_pq| <= theta ||M||_F, clamp below -tau,
+// rewrite), with the sums in another order.
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int kClampWarpThreads = 128;
+
+template <typename HT>
+__global__ void __launch_bounds__(kClampWarpThreads)
+k_clamp_warp(ElemLaunch L)
+{
+    constexpr int NW = kClampWarpThreads / 32;
+    __shared__ double sX[NW][81], sY[NW][81], sA[NW][81];   // row-major r * 9 + c
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* X = sX[w];
+    double* Y = sY[w];
+    double* A = sA[w];
+    const int64_t cap = L.clamp_cap;
+    const int cnt = L.clamp_bucket_count[9];
+    for (int j = blockIdx.x * NW + w; j < cnt; j += gridDim.x * NW) {
+        const int64_t idx = L.clamp_bucket[9 * cap + j];
+        const float* rec = L.clamp_X + idx * kClampRec;
+        const unsigned long long order = rec_order(rec);
+        const double* Mg = L.clamp_M + 45 * idx;
+        const double fro = L.clamp_fro[idx];
+        const double tau = 1e-13 * fro;
+        const double thr = (sizeof(HT) == 4 ? SX_CLAMP_THETA32 : 1e-13) * fro;
+        for (int e = lane; e < 81; e += 32) {
+            const int r = e / 9, c = e - 9 * (e / 9);
+            X[e] = (double)__ldg(rec + 9 * rec_col(order, c) + r);
+        }
+        __syncwarp();
+        // modified Gram-Schmidt, column after column (lanes 0..8: the rows)
+        for (int jc = 0; jc < 9; ++jc) {
+            for (int ic = 0; ic < jc; ++ic) {
+                const double d = warp_sum(lane < 9 ? X[lane * 9 + ic] * X[lane * 9 + jc] : 0.0);
+                if (lane < 9) X[lane * 9 + jc] = fma(-d, X[lane * 9 + ic], X[lane * 9 + jc]);
+                __syncwarp();
+            }
+            const double nn = warp_sum(lane < 9 ? X[lane * 9 + jc] * X[lane * 9 + jc] : 0.0);
+            if (lane < 9) X[lane * 9 + jc] *= rsqrt(nn);
+            __syncwarp();
+        }
+        // Y = M X, then At = X^T Y (the lower triangle, mirrored)
+        for (int e = lane; e < 81; e += 32) {
+            const int r = e / 9, c = e - 9 * (e / 9);
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) t = fma(__ldg(Mg + pk(r, q)), X[q * 9 + c], t);
+            Y[e] = t;
+        }
+        __syncwarp();
+        for (int q = lane; q < 45; q += 32) {
+            int i = 0;
+            while ((i + 1) * (i + 2) / 2 <= q) ++i;
+            const int c = q - i * (i + 1) / 2;
+            double t = 0.0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) t = fma(X[r * 9 + i], Y[r * 9 + c], t);
+            A[i * 9 + c] = t;
+            A[c * 9 + i] = t;
+        }
+        __syncwarp();
+        // cyclic sweeps (the whole warp on one pair at a time: lane r < 9
+        // updates row r of A and of X)
+        for (int sw = 0; sw < SX_F64_SWEEPS; ++sw)
+            for (int p = 0; p < 8; ++p)
+                for (int q = p + 1; q < 9; ++q) {
+                    const double apq = A[p * 9 + q], app = A[p * 9 + p], aqq = A[q * 9 + q];
+                    if (!(fabs(apq) > thr)) continue;   // the same on every lane
+                    const float fpq = (float)apq;
+                    const bool nz = fpq != 0.0f;
+                    const float ft = jac_div((float)(aqq - app), nz ? 2.0f * fpq : 1.0f);
+                    const float tt = jac_div(copysignf(1.0f, ft),
+                                             fabsf(ft) + jac_sqrt1(fmaf(ft, ft, 1.0f)));
+                    const double t = nz ? (double)tt : 0.0;
+                    const double c = rsqrt(fma(t, t, 1.0)), s = t * c;
+                    double arp = 0.0, arq = 0.0, xp = 0.0, xq = 0.0;
+                    if (lane < 9) {
+                        arp = A[lane * 9 + p];
+                        arq = A[lane * 9 + q];
+                        xp = X[lane * 9 + p];
+                        xq = X[lane * 9 + q];
+                    }
+                    __syncwarp();
+                    if (lane < 9) {
+                        if (lane != p && lane != q) {
+                            const double nrp = fma(c, arp, -s * arq), nrq = fma(s, arp, c * arq);
+                            A[lane * 9 + p] = nrp;
+                            A[p * 9 + lane] = nrp;
+                            A[lane * 9 + q] = nrq;
+                            A[q * 9 + lane] = nrq;
+                        }
+                        X[lane * 9 + p] = fma(c, xp, -s * xq);
+                        X[lane * 9 + q] = fma(s, xp, c * xq);
+                    } else if (lane == 9) {
+                        const double cc = c * c, ss = s * s, cs = c * s;
+                        A[p * 9 + p] = fma(cc, app, fma(-2.0 * cs, apq, ss * aqq));
+                        A[q * 9 + q] = fma(ss, app, fma(2.0 * cs, apq, cc * aqq));
+                        const double npq = fma(cc - ss, apq, cs * (app - aqq));
+                        A[p * 9 + q] = npq;
+                        A[q * 9 + p] = npq;
+                    }
+                    __syncwarp();
+                }
+        double lam[9];
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            lam[i] = A[i * 9 + i];
+            ok = ok && isfinite(lam[i]);
+        }
+        const ClampRef ref = L.clamp_ref[idx];
+        if (!ok) {
+            if (lane == 0) {
+                atomicAdd(L.clamp_failed, 1);
+                atomicExch(&L.scenes[ref.scene].sc->clamp_fail, 1);
+            }
+            continue;
+        }
+        bool any_neg = false;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) any_neg = any_neg || lam[i] < -tau;
+        if (!any_neg) continue;
+        // M' = M - sum lambda v v^T (packed entries over the lanes, into Y)
+        for (int q = lane; q < 45; q += 32) {
+            int i = 0;
+            while ((i + 1) * (i + 2) / 2 <= q) ++i;
+            const int c = q - i * (i + 1) / 2;
+            double m = __ldg(Mg + q);
+#pragma unroll
+            for (int l = 0; l < 9; ++l)
+                if (lam[l] < -tau) m = fma(-lam[l] * X[i * 9 + l], X[c * 9 + l], m);
+            Y[i * 9 + c] = m;
+            Y[c * 9 + i] = m;
+        }
+        __syncwarp();
+        // H' = (Hd kron I3) diag(0, M') (Hd kron I3)^T, the 10 upper blocks
+        const SceneDev& S = L.scenes[ref.scene];
+        const ElemBlock& Bk = S.blk[ref.blk];
+        HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * (Bk.base + ref.e);
+        double* full = L.out_H ? L.out_H + 144 * ref.e : nullptr;
+        constexpr int SG[4][3] = {{1, 1, 1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, 1}};
+        for (int e = lane; e < 90; e += 32) {
+            const int ab = e / 9, rc = e - 9 * (e / 9), r = rc / 3, c = rc - 3 * (rc / 3);
+            int a = 0, b = 0;
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = x; y < 4; ++y)
+                    if (up_index(x, y) == ab) {
+                        a = x;
+                        b = y;
+                    }
+            double h = 0.0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int n = 0; n < 3; ++n)
+                    h += (double)(SG[a][m] * SG[b][n]) * Y[(3 * m + r) * 9 + 3 * n + c];
+            h *= 0.25;
+            if (staged) {
+                staged[9 * ab + rc] = (HT)h;
+            } else {
+                full[(3 * a + r) * 12 + 3 * b + c] = h;
+                if (a != b) full[(3 * b + c) * 12 + 3 * a + r] = h;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // SM count of the current device (cached per device): the looping grids of
 // the refinement's second pass and of the double part are sized by it
 static int device_sms()
@@ -534,6 +718,12 @@ cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
                 k_clamp_refine<double, 1, 128><<<gr, 128, 0, s>>>(L);
                 k_clamp_refine<double, 2, 128><<<gr2, 128, 0, s>>>(L);
             }
+        }
+        if (SX_CLAMP_REFINE) {
+            // bin 9, a warp per stencil (grid-stride over the bin)
+            const int gw = (int)std::min<int64_t>((cap + 3) / 4 + 1, 4 * sms);
+            if (f32) k_clamp_warp<float><<<gw, kClampWarpThreads, 0, s>>>(L);
+            else k_clamp_warp<double><<<gw, kClampWarpThreads, 0, s>>>(L);
         }
         // the double part loops over its units with at most 4 blocks per SM
         // (256 / nt more for smaller blocks); every stencil when the

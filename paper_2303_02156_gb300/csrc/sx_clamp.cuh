@@ -178,6 +178,36 @@ __device__ __forceinline__ bool ldlt_f32_pd(const float (&A)[45], float shift)
     return pd;
 }
 
+// double -> float with the mantissa truncated (toward zero), built from the
+// bit fields on the integer pipe: on this GPU a hardware conversion issues
+// on the FP64 pipe, which the element kernels saturate. Magnitudes below
+// the normal float range give a signed zero; above it (and inf, NaN) a NaN,
+// which leaves the pre-test undecided. The truncation (at most 2^-23
+// relative) is far inside the pre-test's margin.
+__device__ __forceinline__ float f64_to_f32_trunc(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned ex = (hi >> 20) & 0x7FFu;
+    unsigned f;
+    if (ex <= 896u) f = 0u;
+    else if (ex >= 1151u) f = 0x7FC00000u;
+    else f = ((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    return __uint_as_float((hi & 0x80000000u) | f);
+}
+
+// float -> double (exact) from the bit fields on the integer pipe; a
+// subnormal float takes the hardware conversion
+__device__ __forceinline__ double f32_to_f64_bits(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned ex = (u >> 23) & 0xFFu, mt = u & 0x7FFFFFu, sg = u & 0x80000000u;
+    if (ex == 0u && mt != 0u) return (double)x;
+    const unsigned e64 = ex == 0u ? 0u : (ex == 255u ? 2047u : ex + 896u);
+    return __hiloint2double((int)(sg | (e64 << 20) | (mt >> 3)), (int)(mt << 29));
+}
+__device__ __forceinline__ double to_f64_bits(float x) { return f32_to_f64_bits(x); }
+__device__ __forceinline__ double to_f64_bits(double x) { return x; }
+
 __device__ __forceinline__ int psd_class_f32(const double (&M)[45])
 {
     float A[45];
@@ -186,7 +216,7 @@ __device__ __forceinline__ int psd_class_f32(const double (&M)[45])
     for (int i = 0; i < 9; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j) {
-            const float v = (float)M[pk(i, j)];
+            const float v = f64_to_f32_trunc(M[pk(i, j)]);
             A[pk(i, j)] = v;
             f2 = fmaf((i == j ? 1.0f : 2.0f) * v, v, f2);
         }

@@ -261,7 +261,7 @@ __device__ __forceinline__ void snh_M(const SnhCore<R>& S, double (&M)[45])
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
                     if (3 * d + k <= 3 * c + i || c != d)
-                        M[pk(3 * d + k, 3 * c + i)] = (double)blk[i * 3 + k];
+                        M[pk(3 * d + k, 3 * c + i)] = to_f64_bits(blk[i * 3 + k]);
         }
 }
 
@@ -581,7 +581,7 @@ __device__ void eval_snh(const ElemLaunch& L, int scene, int blk, const SceneDev
         double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            gout[k] = (double)g[k];
+            gout[k] = to_f64_bits(g[k]);
             if (nonfinite_bits(g[k])) o.nonfinite = 1;
         }
     }
@@ -913,7 +913,7 @@ __device__ __noinline__ void eval_model(const ElemLaunch& L, int scene, int blk,
 #pragma unroll
                         for (int k = 0; k < 3; ++k)
                             if (3 * d + k <= 3 * c + i || c != d)
-                                M[pk(3 * d + k, 3 * c + i)] = (double)bl[i * 3 + k];
+                                M[pk(3 * d + k, 3 * c + i)] = to_f64_bits(bl[i * 3 + k]);
                 }
             o.clamped = queue_if_indefinite(L, scene, blk, e, M);
         }
@@ -1497,7 +1497,7 @@ __device__ void eval_barrier(const ElemLaunch& L, int scene, int blk, const Scen
     if (L.level >= 1) {
         double* gout = L.out_g ? L.out_g + 12 * e : S.ge + 12 * gid;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) gout[k] = (st == 1) ? (double)bo.g[k] : 0.0;
+        for (int k = 0; k < 12; ++k) gout[k] = (st == 1) ? to_f64_bits(bo.g[k]) : 0.0;
     }
     if (L.level >= 2) {
         auto blockfn = [&](int a, int b, R* out) {
@@ -1523,8 +1523,8 @@ __device__ void eval_barrier(const ElemLaunch& L, int scene, int blk, const Scen
                         double h[4];
 #pragma unroll
                         for (int b = 0; b < 4; ++b)
-                            h[b] = 0.5 * ((double)bo.H[(3 * a + i) * 12 + 3 * b + k] +
-                                          (double)bo.H[(3 * b + k) * 12 + 3 * a + i]);
+                            h[b] = 0.5 * (to_f64_bits(bo.H[(3 * a + i) * 12 + 3 * b + k]) +
+                                          to_f64_bits(bo.H[(3 * b + k) * 12 + 3 * a + i]));
                         had_fwd(h[0], h[1], h[2], h[3], Tm[a][0], Tm[a][1], Tm[a][2]);
                     }
 #pragma unroll
