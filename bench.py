@@ -203,27 +203,61 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ roofline traffic
-def clamp_profile_figures():
-    """(DRAM bytes, executed FP64 flops) per projected stencil of the clamp
-    kernel from the committed ncu summary, and whether that capture was
-    taken on the current sources."""
-    path = os.path.join(ROOT, "profiles", "k_clamp_snh_cube_40.md")
+def profile_figures(name, sources):
+    """The '- key: value' figures of the committed ncu summary
+    profiles/<name>.md, and whether its capture was taken on the current
+    sources (its source_sha256_16 against the listed csrc files)."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
     if not os.path.exists(path):
-        return None, None, False
+        return {}, False
     h = hashlib.sha256()
-    for f in ["sx_clamp.cu", "sx_clamp.cuh"]:
+    for f in sources:
         h.update(open(os.path.join(ROOT, "paper_2303_02156_gb300", "csrc", f), "rb").read())
     vals = {}
     for line in open(path):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
+    return vals, vals.get("source_sha256_16") == h.hexdigest()[:16]
+
+
+# the sources each profiled kernel is compiled from
+ELEMENT_SOURCES = ["sx_elements.cu", "sx_elements.cuh", "sx_clamp.cuh", "sx_barrier.cuh",
+                   "sx_internal.cuh"]
+CLAMP_SOURCES = ["sx_clamp.cu", "sx_clamp.cuh", "sx_internal.cuh"]
+
+
+def roofline_entry(kernel, units, t_ms, name, sources, flops_key, bytes_key, unit_name):
+    """FP64-ALU roofline of a kernel (or kernel group) from its live time and
+    the executed FP64 flops (2 DFMA + DMUL + DADD) and DRAM bytes per unit
+    of its committed ncu summary."""
+    vals, fresh = profile_figures(name, sources)
     try:
-        tpe = float(vals["dram_bytes_per_projected_stencil"])
-        fpe = float(vals["executed_fp64_flops_per_projected_stencil"])
+        fpu = float(vals[flops_key])
     except (KeyError, ValueError):
-        return None, None, False
-    return tpe, fpe, vals.get("source_sha256_16") == h.hexdigest()[:16]
+        fpu = None
+    try:
+        bpu = float(vals[bytes_key])
+    except (KeyError, ValueError):
+        bpu = None
+    t = t_ms / 1e3
+    achieved = fpu * units / t / 1e12 if (fpu and t > 0) else None
+    out = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+           "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+           "traffic": (bpu * units) if (bpu and fresh) else None,
+           "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                          "(nominal 1.25 TFLOP/s); probe-measured 1.198 TFLOP/s",
+           "units_per_launch": units, "unit_counted": unit_name, "flops_per_unit": fpu,
+           "flops_per_unit_source": "executed FP64 flops per %s, ncu (profiles/%s.md)%s"
+                                    % (unit_name, name, "" if fresh else "; capture on earlier sources"),
+           "avg_launch_ms": t_ms}
+    for k in ("fp64_pipe_active_pct", "max_frac_for_instruction_mix"):
+        if k in vals:
+            try:
+                out[k] = float(vals[k])
+            except ValueError:
+                pass
+    return out
 
 
 # ------------------------------------------------------------------ serving
@@ -820,48 +854,54 @@ def main():
     _, _, vm = s.bsr()
     matproj["bsr_rel_diff_vs_element_clamp"] = float(np.linalg.norm(vm - v64) / np.linalg.norm(v64))
 
-    # ---- roofline of the dominant kernel (the FP64 eigen-clamp). The work
-    # per projected stencil is the FP64 flops this algorithm executes (ncu
-    # count of DFMA x 2 + DMUL + DADD, profiles/k_clamp_snh_cube_40.md);
-    # the hot-path scope table's 1.5e4 estimate (for other eigen-solvers)
-    # is reported beside it.
+    # ---- roofline of the dominant kernel: the element kernel (one launch per
+    # pass: E, g, H of every tet, the PSD pre-test and the projection queue),
+    # and beside it the projection (float eigen-solver, the refinement's two
+    # passes, the warp-per-stencil and block-restricted double Jacobi; FP64
+    # ALU), with the hot-path scope table's 1.5e4 flops per projected
+    # stencil (written for QL or cyclic-Jacobi solvers) next to the executed count
+    roofline = roofline_entry("k_elements<double, double, 1> (SNH E+g+H, PSD pre-test, queue)", T,
+                              phases["elements"], "k_elements_snh_cube_40", ELEMENT_SOURCES,
+                              "executed_fp64_flops_per_tet", "dram_bytes_per_tet", "tet")
+    rp = roofline_entry("projection: k_clamp_float, k_clamp_refine (2 passes), k_clamp_warp, "
+                        "k_clamp_double", clamped, phases["clamp"], "k_clamp_snh_cube_40",
+                        CLAMP_SOURCES, "executed_fp64_flops_per_projected_stencil",
+                        "dram_bytes_per_projected_stencil", "projected stencil")
     t_clamp = phases["clamp"] / 1e3
-    tpe, fpe, fresh = clamp_profile_figures()
-    fpe = fpe or 6946.0
-    achieved = fpe * clamped / t_clamp / 1e12 if t_clamp > 0 else None
     scope = CLAMP_FLOPS_PER_ELEMENT * clamped / t_clamp / 1e12 if t_clamp > 0 else None
-    roofline = {"bound": "alu", "kernel": "k_clamp_float + k_clamp_double (FP64 9x9 eigen-clamp of the queued stencils)",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                "traffic": (tpe * clamped) if (tpe and fresh) else None,
-                "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s); "
-                               "probe-measured 1.198 TFLOP/s",
-                "units_per_launch": clamped, "flops_per_unit": fpe,
-                "flops_per_unit_source": "executed FP64 flops per projected stencil, ncu"
-                                         + ("" if fresh else " (capture on earlier sources)"),
-                "scope_table_flops_per_unit": CLAMP_FLOPS_PER_ELEMENT,
-                "frac_at_scope_table_figure": (scope / FP64_PEAK_TFLOPS) if scope else None,
-                "avg_launch_ms": phases["clamp"]}
+    rp["scope_table_flops_per_unit"] = CLAMP_FLOPS_PER_ELEMENT
+    rp["frac_at_scope_table_figure"] = (scope / FP64_PEAK_TFLOPS) if scope else None
+    roofline["projection"] = rp
 
-    # ---- backward-Euler Newton step from rest under gravity
+    # ---- backward-Euler Newton step from rest under gravity: one untimed
+    # step (PCG chunk graphs built), the step as a user runs it (phase tracer
+    # off: its per-phase synchronization adds ~15 ms), then the same step with
+    # the tracer for its phase split
     newton = None
     if not args.no_newton:
         s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+        s.newton_step(0.005, raise_on_error=False, newton_tol=1e-8, pcg_tol=1e-10)
+        s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+        rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-8, pcg_tol=1e-10)
+        x64 = s.get_state()[0]
+        s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
         sx.sx_profile(ctx.h, 1)
         sx.sx_profile_read(ctx.h, None, None, 1)
-        rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-8, pcg_tol=1e-10)
+        _, rep_t = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-8, pcg_tol=1e-10)
         sx.sx_profile_read(ctx.h, ms_arr, ln_arr, 1)
         sx.sx_profile(ctx.h, 0)
-        x64 = s.get_state()[0]
         newton = {"status": sx.STATUS_NAMES.get(rc, rc), "ms": rep["ms"],
                   "newton_iters": rep["newton_iters"], "pcg_iters": rep["pcg_iters"],
+                  "ms_traced": rep_t["ms"],
                   "phase_ms": {sx.PHASES[i]: round(ms_arr[i], 3) for i in range(9)},
                   "dt": 0.005, "newton_tol": 1e-8, "pcg_tol": 1e-10}
         # the FP32 form of the same step (FP64 clamp, residual norms and
-        # line-search energies), and its deviation from the FP64 step
-        s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
-        rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-6, pcg_tol=1e-6,
-                                precision=sx.SX_FP32)
+        # line-search energies; after one untimed step), and its deviation
+        # from the FP64 step
+        for _ in range(2):
+            s.set_state(x=m["X"], v=np.zeros_like(m["X"]))
+            rc, rep = s.newton_step(0.005, raise_on_error=False, newton_tol=1e-6, pcg_tol=1e-6,
+                                    precision=sx.SX_FP32)
         x32 = s.get_state()[0]
         newton["fp32"] = {"status": sx.STATUS_NAMES.get(rc, rc), "ms": rep["ms"],
                           "newton_iters": rep["newton_iters"], "pcg_iters": rep["pcg_iters"],

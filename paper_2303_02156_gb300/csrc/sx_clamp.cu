@@ -150,9 +150,15 @@ k_clamp(ElemLaunch L)
 // copied out by the whole block with coalesced stores.
 constexpr int kClampFloatThreads = 128;
 constexpr int clamp_float_smem(int nt) { return (81 * (nt + 1) + 17 * nt) * 4; }
+// resident blocks per SM the float part is compiled for (a register cap;
+// 4, i.e. 128 registers, measured slower on the 64^3 cube: projection 4.50
+// -> 4.85 ms)
+#ifndef SX_CLAMP_FLOAT_MINB
+#define SX_CLAMP_FLOAT_MINB 1
+#endif
 
 template <int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, SX_CLAMP_FLOAT_MINB)
 k_clamp_float(ElemLaunch L)
 {
     extern __shared__ __align__(16) float Xfs[];
@@ -321,7 +327,7 @@ __device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t id
 #pragma unroll
     for (int p = 0; p < K; ++p)
 #pragma unroll
-        for (int r = 0; r < 9; ++r) V[r][p] = (double)__ldg(rec + 9 * cq[p] + r);
+        for (int r = 0; r < 9; ++r) V[r][p] = f32_to_f64_bits(__ldg(rec + 9 * cq[p] + r));
     // the float vectors are orthonormal only to float precision: correct
     // once before the first certified residual
     refine_residual<K>(Mg, V, R, B);
@@ -414,7 +420,7 @@ __device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t id
                     for (int j = 0; j < K; ++j) d = fma(UB[r][j], U[3 * b + c][j], d);
                     if (staged) {
                         HT* h = staged + 9 * up_index(a, b) + 3 * r + c;
-                        *h = (HT)((double)*h - d);
+                        *h = from_f64_bits<HT>(to_f64_bits(*h) - d);
                     } else {
                         const double h = full[(3 * a + r) * 12 + 3 * b + c] - d;
                         full[(3 * a + r) * 12 + 3 * b + c] = h;

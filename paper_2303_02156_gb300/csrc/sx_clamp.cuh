@@ -195,6 +195,26 @@ __device__ __forceinline__ float f64_to_f32_trunc(double d)
     return __uint_as_float((hi & 0x80000000u) | f);
 }
 
+// double -> float rounded to nearest (ties to even) from the bit fields on
+// the integer pipe: the 29 dropped mantissa bits are rounded into the kept
+// ones (a carry runs on into the exponent, as it should); results outside
+// the normal float range as in f64_to_f32_trunc
+__device__ __forceinline__ float f64_to_f32_rn(double d)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned sg = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned ex0 = (unsigned)(b >> 52) & 0x7FFu;
+    if (ex0 == 0x7FFu) return __uint_as_float(sg | 0x7FC00000u);
+    b += 0x0FFFFFFFull + ((b >> 29) & 1ull);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned ex = (hi >> 20) & 0x7FFu;
+    unsigned f;
+    if (ex <= 896u) f = 0u;
+    else if (ex >= 1151u) f = 0x7FC00000u;
+    else f = ((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    return __uint_as_float(sg | f);
+}
+
 // float -> double (exact) from the bit fields on the integer pipe; a
 // subnormal float takes the hardware conversion
 __device__ __forceinline__ double f32_to_f64_bits(float x)
@@ -207,6 +227,13 @@ __device__ __forceinline__ double f32_to_f64_bits(float x)
 }
 __device__ __forceinline__ double to_f64_bits(float x) { return f32_to_f64_bits(x); }
 __device__ __forceinline__ double to_f64_bits(double x) { return x; }
+// a double result stored as HT (float: rounded to nearest on the integer pipe)
+template <typename HT>
+__device__ __forceinline__ HT from_f64_bits(double x);
+template <>
+__device__ __forceinline__ double from_f64_bits<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_f64_bits<float>(double x) { return f64_to_f32_rn(x); }
 
 __device__ __forceinline__ int psd_class_f32(const double (&M)[45])
 {
@@ -563,7 +590,7 @@ __device__ __forceinline__ void refine_correct(const float* __restrict__ rec, co
     for (int r = 0; r < 9; ++r)
 #pragma unroll
         for (int p = 0; p < K; ++p) {
-            rf[r][p] = (float)R[r][p];
+            rf[r][p] = f64_to_f32_trunc(R[r][p]);
             dv[r][p] = 0.0f;
         }
 #pragma unroll
@@ -584,7 +611,7 @@ __device__ __forceinline__ void refine_correct(const float* __restrict__ rec, co
 #pragma unroll
     for (int r = 0; r < 9; ++r)
 #pragma unroll
-        for (int p = 0; p < K; ++p) V[r][p] -= (double)dv[r][p];
+        for (int p = 0; p < K; ++p) V[r][p] -= f32_to_f64_bits(dv[r][p]);
     refine_mgs<K>(V);
 }
 

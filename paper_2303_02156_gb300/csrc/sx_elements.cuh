@@ -71,7 +71,8 @@ template <typename R>
 struct SnhCore {
     R G[4][3];   // shape-function gradients (row a)
     R F[9];      // row-major
-    R C[9];      // cofactor
+    R C[9];      // cofactor (the models' and quadrature cores; the SNH tet4 path
+                 // takes cof(F) G_a from the deformed edges instead)
     R cI, cF, cC, cS;   // V*a, V*gam, V*lam', V*b
 };
 
@@ -135,23 +136,10 @@ __device__ __forceinline__ double snh_core(const double* xg, const double* Dinv,
         }
 #pragma unroll
         for (int k = 0; k < 9; ++k) S.F[k] = (R)Fd[k];
-        const R* F = S.F;
-        // cofactor columns: dJ/dF columns are f1 x f2, f2 x f0, f0 x f1
-        {
-            R f0[3] = {F[0], F[3], F[6]}, f1[3] = {F[1], F[4], F[7]}, f2[3] = {F[2], F[5], F[8]};
-            R c0[3], c1[3], cc2[3];
-            cross3(f1, f2, c0);
-            cross3(f2, f0, c1);
-            cross3(f0, f1, cc2);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                S.C[i * 3 + 0] = c0[i];
-                S.C[i * 3 + 1] = c1[i];
-                S.C[i * 3 + 2] = cc2[i];
-            }
-        }
         const R Ic = (R)(3.0 + Ic3);
-        const R inv1 = R(1) / (Ic + R(1));
+        const double Icd = 3.0 + Ic3;
+        const double invd = 1.0 / (Icd + 1.0);   // the one division: 1 / (Ic + 1)
+        const R inv1 = (R)invd;
         const R a = mu * Ic * inv1;
         // lam'(J - alpha) = lam'(J - 1) - 3/4 mu'
         const R b = (lamd != 0.0) ? (R)(lamd * Jm1 - 0.75 * mud) : R(0);
@@ -162,9 +150,8 @@ __device__ __forceinline__ double snh_core(const double* xg, const double* Dinv,
         // is taken in double; the rest is O(mu' |D|) and keeps R's relative
         // precision (in FP32 this is what lets the assembled forces resolve
         // below float epsilon times mu')
-        const double Icd = 3.0 + Ic3;
-        const R s0 = (lamd != 0.0) ? (R)(mud * Ic3 / (4.0 * (Icd + 1.0)) + lamd * Jm1)
-                                   : (R)(mud * Icd / (Icd + 1.0));
+        const R s0 = (lamd != 0.0) ? (R)(0.25 * mud * Ic3 * invd + lamd * Jm1)
+                                   : (R)(mud * Icd * invd);
         R Dr[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Dr[k] = (R)D[k];
@@ -236,26 +223,140 @@ __device__ __forceinline__ void matvec3(const R* M, const R* v, R* o)
     for (int i = 0; i < 3; ++i) o[i] = M[i * 3 + 0] * v[0] + M[i * 3 + 1] * v[1] + M[i * 3 + 2] * v[2];
 }
 
-// 9x9 translation-free Hessian M (double, packed lower) of an SNH tet.
+// ---- SNH tet4 Hessian blocks from the deformed edges
+// With Dm = [X1 - X0, X2 - X0, X3 - X0], G_1..G_3 the rows of Dm^-1 and
+// G_0 = -(G_1 + G_2 + G_3), adj(Dm^-1) = Dm^-1^-1 det(Dm^-1) gives
+// G_2 x G_3 = (X1 - X0)/det(Dm), G_3 x G_1 = (X2 - X0)/det(Dm),
+// G_1 x G_2 = (X3 - X0)/det(Dm); since F (X_k - X0) = x_k - x0 = ds_{k-1},
+// the skew vectors of the blocks are scaled deformed edges:
+//   F(G_2 x G_3) = ds0 / det(Dm), F(G_1 x G_3) = -ds1 / det(Dm),
+//   F(G_1 x G_2) = ds2 / det(Dm), F(G_0 x G_1) = (ds2 - ds1) / det(Dm),
+//   F(G_0 x G_2) = (ds0 - ds2) / det(Dm), F(G_0 x G_3) = (ds1 - ds0) / det(Dm),
+// and cof(F) G_a = J F^-T G_a (the deformed area vectors over det(Dm)):
+//   cof(F) G_1 = ds1 x ds2 / det(Dm), cof(F) G_2 = ds2 x ds0 / det(Dm),
+//   cof(F) G_3 = ds0 x ds1 / det(Dm), cof(F) G_0 = -(sum of the three).
+// For the Hadamard combinations K_c of the G_a (c = 1..3), F (K_c x K_d) is
+// again an edge combination: (ds2 - ds1 - ds0), (ds1 + ds2 - ds0),
+// (ds1 - ds2 - ds0) over det(Dm) for (c, d) = (1, 2), (1, 3), (2, 3). This
+// takes no cofactor matrix, no F (G_a x G_b) products and no cof(F) G_a
+// matvecs; a diagonal block (a = b: no skew part) is formed once per pair
+// of its symmetric entries.
+
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+
+// block uSa ub^T + vSa vb^T + cIgg I (+ the skew matrix of ws off the
+// diagonal); uSa = V gam u_a, vSa = V lam' v_a, ws = V b w_ab
 template <typename R>
-__device__ __forceinline__ void snh_M(const SnhCore<R>& S, double (&M)[45])
+__device__ __forceinline__ void snh_block_e(const R* uSa, const R* ub, const R* vSa, const R* vb,
+                                            R cIgg, const R* ws, bool diag, R* out)
 {
-    R K[3][3];   // K_c, c = 1..3 stored at [c-1]
+    if (diag) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-        had_fwd(S.G[0][j], S.G[1][j], S.G[2][j], S.G[3][j], K[0][j], K[1][j], K[2][j]);
-    R u[3][3], v[3][3];
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        matvec3(S.F, K[c], u[c]);
-        matvec3(S.C, K[c], v[c]);
+            for (int k = i; k < 3; ++k) {
+                const R t = fma_r(vSa[i], vb[k], uSa[i] * ub[k]) + (i == k ? cIgg : R(0));
+                out[i * 3 + k] = t;
+                out[k * 3 + i] = t;
+            }
+        return;
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            out[i * 3 + k] = fma_r(vSa[i], vb[k], uSa[i] * ub[k]) + (i == k ? cIgg : R(0));
+    // S(w) = [[0, w2, -w1], [-w2, 0, w0], [w1, -w0, 0]]
+    out[1] += ws[2];
+    out[2] -= ws[1];
+    out[3] -= ws[2];
+    out[5] += ws[0];
+    out[6] += ws[1];
+    out[7] -= ws[0];
+}
+
+// V b F (G_a x G_b) for node pair a < b, from the deformed edges ds
+// (sw = V b / det(Dm))
+template <typename R>
+__device__ __forceinline__ void snh_node_skew(int a, int b, const R (&ds)[3][3], R sw, R* ws)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R t;
+        if (a == 2) t = ds[0][i];                       // (2, 3)
+        else if (a == 1) t = b == 2 ? ds[2][i] : -ds[1][i];   // (1, 2), (1, 3)
+        else if (b == 1) t = ds[2][i] - ds[1][i];       // (0, 1)
+        else if (b == 2) t = ds[0][i] - ds[2][i];       // (0, 2)
+        else t = ds[1][i] - ds[0][i];                   // (0, 3)
+        ws[i] = sw * t;
+    }
+}
+
+// the same for Hadamard mode pair c < d (0-based c, d: modes c + 1, d + 1)
+template <typename R>
+__device__ __forceinline__ void snh_mode_skew(int c, int d, const R (&ds)[3][3], R sw, R* ws)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R t;
+        if (c == 1) t = ds[1][i] - ds[2][i] - ds[0][i];        // (2, 3)
+        else if (d == 1) t = ds[2][i] - ds[1][i] - ds[0][i];   // (1, 2)
+        else t = ds[1][i] + ds[2][i] - ds[0][i];               // (1, 3)
+        ws[i] = sw * t;
+    }
+}
+
+// u_a = F G_a and v_a = cof(F) G_a (node a = 0..3) from the core and the
+// deformed edges (dD = 1 / det(Dm))
+template <typename R>
+__device__ __forceinline__ void snh_uv(const SnhCore<R>& S, const R (&ds)[3][3], R dD,
+                                       R (&u)[4][3], R (&v)[4][3])
+{
+#pragma unroll
+    for (int a = 0; a < 4; ++a) matvec3(S.F, S.G[a], u[a]);
+    cross3(ds[1], ds[2], v[1]);
+    cross3(ds[2], ds[0], v[2]);
+    cross3(ds[0], ds[1], v[3]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        v[1][i] *= dD;
+        v[2][i] *= dD;
+        v[3][i] *= dD;
+        v[0][i] = -(v[1][i] + v[2][i] + v[3][i]);
+    }
+}
+
+// 9x9 translation-free Hessian M (double, packed lower) of an SNH tet from
+// the node vectors: u, v of the modes are Hadamard combinations of the node
+// ones, the K_c those of the G_a
+template <typename R>
+__device__ __forceinline__ void snh_M_e(const SnhCore<R>& S, const R (&u)[4][3],
+                                        const R (&v)[4][3], const R (&ds)[3][3], R sw,
+                                        double (&M)[45])
+{
+    R K[3][3], um[3][3], vm[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        had_fwd(S.G[0][j], S.G[1][j], S.G[2][j], S.G[3][j], K[0][j], K[1][j], K[2][j]);
+        had_fwd(u[0][j], u[1][j], u[2][j], u[3][j], um[0][j], um[1][j], um[2][j]);
+        had_fwd(v[0][j], v[1][j], v[2][j], v[3][j], vm[0][j], vm[1][j], vm[2][j]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        R uS[3], vS[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            uS[i] = S.cF * um[c][i];
+            vS[i] = S.cC * vm[c][i];
+        }
 #pragma unroll
         for (int d = c; d < 3; ++d) {
+            const R gg = K[c][0] * K[d][0] + K[c][1] * K[d][1] + K[c][2] * K[d][2];
+            R ws[3] = {R(0), R(0), R(0)};
+            if (c != d) snh_mode_skew(c, d, ds, sw, ws);
             R blk[9];
-            snh_block(S, K[c], K[d], u[c], u[d], v[c], v[d], c == d, blk);
+            snh_block_e(uS, um[d], vS, vm[d], S.cI * gg, ws, c == d, blk);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -263,6 +364,7 @@ __device__ __forceinline__ void snh_M(const SnhCore<R>& S, double (&M)[45])
                     if (3 * d + k <= 3 * c + i || c != d)
                         M[pk(3 * d + k, 3 * c + i)] = to_f64_bits(blk[i * 3 + k]);
         }
+    }
 }
 
 // ------------------------------------------------------------------ output
@@ -586,15 +688,29 @@ __device__ void eval_snh(const ElemLaunch& L, int scene, int blk, const SceneDev
         }
     }
     if (L.level >= 2) {
-        {
-            R u[4][3], v[4][3];
+        // deformed edges and 1 / det(Dm) (the edge identities above snh_block_e)
+        R ds[3][3];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                matvec3(C.F, C.G[a], u[a]);
-                matvec3(C.C, C.G[a], v[a]);
-            }
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ds[k][i] = (R)(xg[3 * (k + 1) + i] - xg[i]);
+        const R dD = (R)(Dinv[0] * (Dinv[4] * Dinv[8] - Dinv[5] * Dinv[7]) -
+                         Dinv[1] * (Dinv[3] * Dinv[8] - Dinv[5] * Dinv[6]) +
+                         Dinv[2] * (Dinv[3] * Dinv[7] - Dinv[4] * Dinv[6]));
+        const R sw = C.cS * dD;
+        R u[4][3], v[4][3];
+        snh_uv(C, ds, dD, u, v);
+        {
             auto blockfn = [&](int a, int b, R* out) {
-                snh_block(C, C.G[a], C.G[b], u[a], u[b], v[a], v[b], a == b, out);
+                R uS[3], vS[3], ws[3] = {R(0), R(0), R(0)};
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    uS[i] = C.cF * u[a][i];
+                    vS[i] = C.cC * v[a][i];
+                }
+                if (a != b) snh_node_skew(a, b, ds, sw, ws);
+                const R gg = C.G[a][0] * C.G[b][0] + C.G[a][1] * C.G[b][1] + C.G[a][2] * C.G[b][2];
+                snh_block_e(uS, u[b], vS, v[b], C.cI * gg, ws, a == b, out);
             };
             HT* staged = L.out_H ? nullptr : (HT*)S.He + 90 * gid;
             double* full = L.out_H ? L.out_H + 144 * e : nullptr;
@@ -606,7 +722,7 @@ __device__ void eval_snh(const ElemLaunch& L, int scene, int blk, const SceneDev
             o.clamped = snh_fproj<HT>(xg, Dinv, B.V[e], B.mu[e], B.lam[e], staged, full) > 0;
         } else if (L.project) {
             double M[45];
-            snh_M<R>(C, M);
+            snh_M_e<R>(C, u, v, ds, sw, M);
             o.clamped = queue_if_indefinite(L, scene, blk, e, M);
         }
     }

@@ -312,6 +312,162 @@ __device__ __forceinline__ void scene_tile_sums(double (*sh)[NT], const double* 
 static constexpr int kUpdTiles = SX_UPD_TILES;
 int pcg_update_blocks(int n_node_tiles) { return (n_node_tiles + kUpdTiles - 1) / kUpdTiles; }
 
+// The update (below) with half the threads: a 128-thread block per 256-node
+// tile, thread t taking nodes t and t + 128 (loads of both first). Each
+// thread adds its two nodes' r.z and r.r in node order; lane l of warp 0
+// then adds the partials of threads l, l + 32, l + 64, l + 96 in that order
+// and the warp finishes with a fixed shuffle tree, so a tile's partial (and
+// the scene sums, folded by the last tile as above) depends only on the
+// tile's data. On this GPU the update is bound by the FP64 pipe, which a
+// 256-thread shared-memory tree with nine barriers per tile kept waiting.
+#ifndef SX_UPD_SPLIT
+#define SX_UPD_SPLIT 1
+#endif
+constexpr int kUpd2Threads = 128;
+
+__device__ __forceinline__ double warp_sum_xor(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kUpd2Threads)
+k_pcg_update2(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part,
+              const int* tbeg, const int* tend, double tol, int max_iter)
+{
+    wait_prior_grid();
+    __shared__ double sh[2][kUpd2Threads];
+    __shared__ int s_last;
+    const int ti = blockIdx.x;
+    if (ti >= ntiles) return;
+    const Tile T = tiles[ti];
+    const SceneDev& S = scenes[T.scene];
+    if (!scene_live(S) || S.sc->pcg_done) return;   // the same for all tiles of a scene
+    const double alpha = S.sc->pcg_alpha;
+    const double* pn = par ? S.p0 : S.p1;
+    double pv[2][3], dxv[2][3], rv[2][3], qv[2][3], Mi[2][9];
+    bool on[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int l = (int)threadIdx.x + kUpd2Threads * h;
+        on[h] = l < T.count;
+        if (!on[h]) continue;
+        const int64_t n = T.start + l;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            pv[h][i] = pn[3 * n + i];
+            dxv[h][i] = S.dx[3 * n + i];
+            rv[h][i] = S.r[3 * n + i];
+            qv[h][i] = S.q[3 * n + i];
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Mi[h][k] = S.Minv[9 * n + k];
+    }
+    double rz = 0.0, rr = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!on[h]) continue;
+        const int64_t n = T.start + (int)threadIdx.x + kUpd2Threads * h;
+        double r[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            S.dx[3 * n + i] = dxv[h][i] + alpha * pv[h][i];
+            r[i] = rv[h][i] - alpha * qv[h][i];
+            S.r[3 * n + i] = r[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double z = Mi[h][3 * i] * r[0] + Mi[h][3 * i + 1] * r[1] + Mi[h][3 * i + 2] * r[2];
+            S.z[3 * n + i] = z;
+            rz += r[i] * z;
+            rr += r[i] * r[i];
+        }
+    }
+    sh[0][threadIdx.x] = rz;
+    sh[1][threadIdx.x] = rr;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        double a = ((sh[0][l] + sh[0][l + 32]) + sh[0][l + 64]) + sh[0][l + 96];
+        double b = ((sh[1][l] + sh[1][l + 32]) + sh[1][l + 64]) + sh[1][l + 96];
+        a = warp_sum_xor(a);
+        b = warp_sum_xor(b);
+        if (l == 0) {
+            part[2 * (int64_t)ti] = a;
+            part[2 * (int64_t)ti + 1] = b;
+            // release: this tile's partials are visible to whoever counts
+            // last; acquire: the last one sees every partial released before it
+            cuda::atomic_ref<int, cuda::thread_scope_device> cnt(S.sc->cnt_update);
+            s_last = cnt.fetch_add(1, cuda::memory_order_acq_rel) == tend[T.scene] - tbeg[T.scene] - 1;
+        }
+    }
+    __syncthreads();
+    if (!s_last) return;
+    double rzr[2];
+    scene_tile_sums<2, kUpd2Threads>(sh, part, tbeg[T.scene], tend[T.scene], rzr);
+    if (threadIdx.x == 0) {
+        // convergence test and beta
+        SceneScal* sc = S.sc;
+        sc->cnt_update = 0;
+        sc->rz_new = rzr[0];
+        sc->rr = rzr[1];
+        sc->pcg_iters += 1;
+        const double t = sc->pcg_tol > 0.0 ? sc->pcg_tol : tol;
+        if (rzr[1] <= t * t * sc->bnorm2) {
+            sc->pcg_done = 1;
+        } else if (sc->pcg_iters >= max_iter || !isfinite(rzr[1])) {
+            sc->pcg_done = 1;
+            sc->pcg_status = 2;
+        } else {
+            sc->pcg_beta = rzr[0] / sc->rz;
+            sc->rz = rzr[0];
+        }
+    }
+}
+
+// the direction pass with the same thread layout (two nodes per thread)
+template <bool F32>
+__global__ void __launch_bounds__(kUpd2Threads)
+k_pcg_pdir2(const SceneDev* scenes, const Tile* tiles, int ntiles, int par)
+{
+    wait_prior_grid();
+    const int ti = blockIdx.x;
+    if (ti >= ntiles) return;
+    const Tile T = tiles[ti];
+    const SceneDev& S = scenes[T.scene];
+    if (!scene_live(S) || S.sc->pcg_done) return;
+    const double beta = S.sc->pcg_beta;
+    const double* po = par ? S.p1 : S.p0;
+    double* pw = par ? S.p0 : S.p1;
+    double zv[2][3], ov[2][3];
+    bool on[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int l = (int)threadIdx.x + kUpd2Threads * h;
+        on[h] = l < T.count;
+        if (!on[h]) continue;
+        const int64_t n = T.start + l;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            ov[h][i] = po[3 * n + i];
+            zv[h][i] = S.z[3 * n + i];
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!on[h]) continue;
+        const int64_t n = T.start + (int)threadIdx.x + kUpd2Threads * h;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double p = fma(beta, ov[h][i], zv[h][i]);
+            pw[3 * n + i] = p;
+            // the FP32 SpMV gathers this rounded copy (no conversion per block)
+            if (F32) S.p32[3 * n + i] = (float)p;
+        }
+    }
+}
+
 template <bool F32>
 __global__ void __launch_bounds__(kVecThreads)
 k_pcg_pdir(const SceneDev* scenes, const Tile* tiles, int ntiles, int par)
@@ -361,10 +517,16 @@ cudaError_t launch_pcg_pdir(const SceneDev* scenes, const Tile* node_tiles, int 
 {
     if (!ntiles) return cudaSuccess;
     const int g = pcg_update_blocks(ntiles);
-    if (precision == SX_FP32)
+    if (SX_UPD_SPLIT) {
+        if (precision == SX_FP32)
+            k_pcg_pdir2<true><<<ntiles, kUpd2Threads, 0, s>>>(scenes, node_tiles, ntiles, parity);
+        else
+            k_pcg_pdir2<false><<<ntiles, kUpd2Threads, 0, s>>>(scenes, node_tiles, ntiles, parity);
+    } else if (precision == SX_FP32) {
         k_pcg_pdir<true><<<g, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity);
-    else
+    } else {
         k_pcg_pdir<false><<<g, kVecThreads, 0, s>>>(scenes, node_tiles, ntiles, parity);
+    }
     return cudaGetLastError();
 }
 
@@ -661,9 +823,12 @@ cudaError_t launch_pcg_update(const SceneDev* scenes, const Tile* node_tiles, in
                               double tol, int max_iter, cudaStream_t s)
 {
     if (!ntiles) return cudaSuccess;
-    k_pcg_update<<<pcg_update_blocks(ntiles), kVecThreads, 0, s>>>(scenes, node_tiles, ntiles,
-                                                                   parity, part, tbeg, tend, tol,
-                                                                   max_iter);
+    if (SX_UPD_SPLIT)
+        k_pcg_update2<<<ntiles, kUpd2Threads, 0, s>>>(scenes, node_tiles, ntiles, parity, part,
+                                                      tbeg, tend, tol, max_iter);
+    else
+        k_pcg_update<<<pcg_update_blocks(ntiles), kVecThreads, 0, s>>>(
+            scenes, node_tiles, ntiles, parity, part, tbeg, tend, tol, max_iter);
     return cudaGetLastError();
 }
 
@@ -787,7 +952,13 @@ cudaError_t add_pcg_chunk_nodes(cudaGraph_t graph, const PcgChunkArgs& a)
 {
     NodeChain c{graph};
     const bool f32 = a.precision == SX_FP32;
-    const void* pdir = f32 ? (const void*)k_pcg_pdir<true> : (const void*)k_pcg_pdir<false>;
+    const void* pdir = SX_UPD_SPLIT
+                           ? (f32 ? (const void*)k_pcg_pdir2<true> : (const void*)k_pcg_pdir2<false>)
+                           : (f32 ? (const void*)k_pcg_pdir<true> : (const void*)k_pcg_pdir<false>);
+    const void* upd = SX_UPD_SPLIT ? (const void*)k_pcg_update2 : (const void*)k_pcg_update;
+    const unsigned upd_grid = SX_UPD_SPLIT ? (unsigned)a.n_node_tiles
+                                           : (unsigned)pcg_update_blocks(a.n_node_tiles);
+    const unsigned upd_threads = SX_UPD_SPLIT ? kUpd2Threads : kVecThreads;
     const void* spmv = f32 ? (const void*)k_spmv<float> : (const void*)k_spmv<double>;
     const unsigned smem = 0;
     const unsigned spmv_threads = kSpmvThreads;
@@ -807,12 +978,9 @@ cudaError_t add_pcg_chunk_nodes(cudaGraph_t graph, const PcgChunkArgs& a)
         void* a_pdir[] = {&scenes, &nt, &nnt, &par};
         void* a_spmv[] = {&scenes, &rt, &nrt, &par, &prow, &rb, &re};
         void* a_upd[] = {&scenes, &nt, &nnt, &par, &pnode, &nb, &ne, &tol, &maxit};
-        if (e == cudaSuccess)
-            e = c.add(pdir, (unsigned)pcg_update_blocks(nnt), kVecThreads, 0, a_pdir);
+        if (e == cudaSuccess) e = c.add(pdir, upd_grid, upd_threads, 0, a_pdir);
         if (e == cudaSuccess) e = c.add(spmv, (unsigned)nrt, spmv_threads, smem, a_spmv);
-        if (e == cudaSuccess)
-            e = c.add((const void*)k_pcg_update, (unsigned)pcg_update_blocks(nnt), kVecThreads,
-                      0, a_upd);
+        if (e == cudaSuccess) e = c.add(upd, upd_grid, upd_threads, 0, a_upd);
     }
     return e;
 }
