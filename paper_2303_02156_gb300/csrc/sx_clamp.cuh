@@ -393,6 +393,9 @@ __device__ __forceinline__ int eig9_float_x(const double* __restrict__ Mg, doubl
     for (int i = 0; i < 45; ++i) A[i] = (float)Mg[i];
 #pragma unroll
     for (int i = 0; i < 81; ++i) Xf(i / 9, i % 9) = (i % 10 == 0) ? 1.0f : 0.0f;
+    // (a round-robin pair order, four independent rotations at a time,
+    // measured the same on the 64^3 cube: 4.475 against 4.492 ms per
+    // projection; the cyclic order stays)
 #pragma unroll 1
     for (int sw = 0; sw < 5; ++sw) jacobi_sweep_f32(A, Xf);
     const float delta = 1e-5f * (float)fro;
