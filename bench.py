@@ -167,19 +167,26 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi takes a moment to start: wait for its first sample so
+        # that the timed region is sampled from its start
+        t_end = time.perf_counter() + 5.0
+        while not self.samples and time.perf_counter() < t_end:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.samples.append([v.strip() for v in line.split(",")])
+            self.samples.append((time.perf_counter(), [v.strip() for v in line.split(",")]))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples taken in [t0, t1 + one period] (all of
+        them without bounds)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -188,6 +195,9 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        if t0 is not None and t1 is not None:
+            self.samples = [x for x in self.samples if t0 <= x[0] <= t1 + 0.05]
+        self.samples = [x[1] for x in self.samples]
         sm = [float(s[1]) for s in self.samples if len(s) >= 9 and s[1].replace(".", "").isdigit()]
         mx = [float(s[2]) for s in self.samples if len(s) >= 9 and s[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -770,15 +780,17 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    t_clk0 = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
         eval_async()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    t_clk1 = time.perf_counter()
     if dist:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_clk0, t_clk1)
     ms_arr = (C.c_double * 9)()
     ln_arr = (C.c_int64 * 9)()
     sx.sx_profile_read(ctx.h, ms_arr, ln_arr, 1)
