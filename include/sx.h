@@ -473,6 +473,17 @@ int sx_profile(sx_ctx* ctx, int enable);
  * launches since the last reset (launches[SX_PH_COUNT], may be NULL; counted
  * whether or not timing is enabled). reset != 0 clears both. */
 int sx_profile_read(sx_ctx* ctx, double* ms, int64_t* launches, int reset);
+/* Diagnostics of the projection of the context's last batched evaluation
+ * (sx_eval, sx_eval_batch, a Newton step's evaluations; the paper has no
+ * counterpart: it shows which paths of phase 2 ran). counts must hold
+ * SX_PROJ_BINS ints: counts[k], k = 0..9, the queued stencils whose float
+ * eigen-solve left an N block of k columns (9 also when its Gershgorin test
+ * failed; bin 9 further receives the stencils the refinement did not
+ * certify), counts[10 + k], k = 1..3, the stencils of k that the
+ * refinement's first pass did not certify; the other entries are 0.
+ * Before any projection all counts are 0. Synchronizes `stream`. */
+#define SX_PROJ_BINS 16
+int sx_projection_bins(sx_ctx* ctx, int* counts, void* stream);
 
 /* ---- launch shapes and the autotuner -----------------------------------
  * (No counterpart in the paper: these pick GPU launch configurations.)

@@ -2078,6 +2078,19 @@ int sx_profile_read(sx_ctx* ctx, double* ms, int64_t* launches, int reset)
     return SX_OK;
 }
 
+int sx_projection_bins(sx_ctx* ctx, int* counts, void* stream)
+{
+    if (!ctx || !counts) return SX_EINVAL;
+    static_assert(SX_PROJ_BINS == kClampBins, "projection bins");
+    for (int i = 0; i < SX_PROJ_BINS; ++i) counts[i] = 0;
+    if (!ctx->clampBucketCount) return SX_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(counts, ctx->clampBucketCount, SX_PROJ_BINS * sizeof(int),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SX_OK;
+}
+
 void sx_newton_opts_default(sx_newton_opts* o)
 {
     if (!o) return;

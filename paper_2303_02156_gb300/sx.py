@@ -43,7 +43,7 @@ EXPORTS = [
     "sx_get_grad", "sx_get_diag_slots", "sx_eval_elements", "sx_newton_opts_default",
     "sx_newton_step", "sx_newton_step_batch", "sx_scene_footprint", "sx_scene_bytes",
     "sx_copy_bsr", "sx_copy_grad", "sx_scene_info", "sx_block_info", "sx_eval_stats",
-    "sx_profile", "sx_profile_read", "sx_eval_elements_noalloc",
+    "sx_profile", "sx_profile_read", "sx_projection_bins", "sx_eval_elements_noalloc",
     "sx_autotune", "sx_set_launch_shape", "sx_get_launch_shape", "sx_set_pairs",
     "sx_compact_pairs", "sx_add_tet4", "sx_update_rotations", "sx_get_rotations",
     "sx_set_rotations", "sx_add_pt_friction", "sx_update_friction", "sx_get_friction_lag",
@@ -149,6 +149,7 @@ _SIGS = {
     "sx_eval_stats": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), _P]),
     "sx_profile": (_I, [_P, _I]),
     "sx_profile_read": (_I, [_P, C.POINTER(_D), C.POINTER(_I64), _I]),
+    "sx_projection_bins": (_I, [_P, C.POINTER(_I), _P]),
     "sx_eval_elements_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
     "sx_server_create": (_I, [_P, _I64, C.POINTER(sx_newton_opts), _PP]),
     "sx_autotune": (_I, [_P, C.POINTER(_P), _I, _I, C.POINTER(sx_tune_report), _P]),
