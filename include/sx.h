@@ -478,11 +478,14 @@ int sx_profile_read(sx_ctx* ctx, double* ms, int64_t* launches, int reset);
  * counterpart: it shows which paths of phase 2 ran). counts must hold
  * SX_PROJ_BINS ints: counts[k], k = 0..9, the queued stencils whose float
  * eigen-solve left an N block of k columns (9 also when its Gershgorin test
- * failed; bin 9 further receives the stencils the refinement did not
- * certify), counts[10 + k], k = 1..3, the stencils of k that the
- * refinement's first pass did not certify; the other entries are 0.
- * Before any projection all counts are 0. Synchronizes `stream`. */
-#define SX_PROJ_BINS 16
+ * failed), except those of k >= 4 with 1..3 clearly negative modes, which
+ * are counted in counts[16 + k'] (k' = 1..3, the deflation of those modes);
+ * counts[10 + k], k = 1..3, the stencils of k that the refinement's first
+ * pass did not certify. A stencil that a later pass hands on is counted
+ * again where it goes (bin 9, or its own k for a deflation not certified).
+ * The other entries are 0; before any projection all counts are 0.
+ * Synchronizes `stream`. */
+#define SX_PROJ_BINS 20
 int sx_projection_bins(sx_ctx* ctx, int* counts, void* stream);
 
 /* ---- launch shapes and the autotuner -----------------------------------

@@ -19,6 +19,11 @@ namespace sx {
 #ifndef SX_CLAMP_REFINE
 #define SX_CLAMP_REFINE 1
 #endif
+// stencils of k >= 4 with 1..3 clearly negative modes: deflation of those
+// (1) or the block-restricted double Jacobi (0)
+#ifndef SX_CLAMP_DEFL
+#define SX_CLAMP_DEFL 1
+#endif
 
 // After the eigen-decomposition: flags a non-finite result, else clamps
 // the N-block eigenvalues below -tau in the Hadamard basis and rewrites the
@@ -183,26 +188,37 @@ k_clamp_float(ElemLaunch L)
         const SmemXf Xf{Xfs + threadIdx.x, XS};
         float* ms = Ms + 17 * threadIdx.x;
         unsigned long long order = 0ull;
+        const float delta = 1e-5f * (float)fro;
+        int kneg = 0;   // eigenvalues below -delta
         int k = eig9_float_x(
             Mg, fro, Xf, [](int, int, float) {},
             [&](int slot, int c, float l) {
                 ms[c] = l;
                 order |= (unsigned long long)c << (4 * slot);
+                kneg += (l < -delta) ? 1 : 0;
             });
         ms[9] = __uint_as_float((unsigned)order);
         ms[10] = __uint_as_float((unsigned)(order >> 32));
         // a non-finite matrix goes to the full double Jacobi, which reports it
         if (!isfinite(fro)) k = 9;
+        ms[11] = __int_as_float(k);
         L.clamp_fro[idx] = fro;
-        // bucket slot: one atomic per (warp, k) for the lanes that share k
-        const unsigned peers = __match_any_sync(__activemask(), k);
+        // bin: k, or for k >= 4 with 1..3 clearly negative modes the deflation
+        // of those (a null space, as the barrier stencils' 4 structural
+        // zeros, then needs no rotation; the rest is certified in double)
+        const int bin = (SX_CLAMP_REFINE && SX_CLAMP_DEFL && k >= 4 && kneg >= 1 && kneg <= 3 &&
+                         isfinite(fro))
+                            ? kClampDefl + kneg
+                            : k;
+        // bucket slot: one atomic per (warp, bin) for the lanes that share it
+        const unsigned peers = __match_any_sync(__activemask(), bin);
         const int lane = threadIdx.x & 31;
         const int leader = __ffs(peers) - 1;
         int b0 = 0;
-        if (lane == leader) b0 = atomicAdd(L.clamp_bucket_count + k, __popc(peers));
+        if (lane == leader) b0 = atomicAdd(L.clamp_bucket_count + bin, __popc(peers));
         b0 = __shfl_sync(peers, b0, leader);
         const int pos = b0 + __popc(peers & ((1u << lane) - 1u));
-        L.clamp_bucket[(int64_t)k * cap + pos] = (int)idx;
+        L.clamp_bucket[(int64_t)bin * cap + pos] = (int)idx;
     }
     __syncthreads();
     const int nrec = (int)(count - base < NT ? count - base : NT);
@@ -211,7 +227,7 @@ k_clamp_float(ElemLaunch L)
         const int t = g / kClampRec, j = g - t * kClampRec;
         float v = 0.0f;
         if (j < 81) v = Xfs[((j % 9) * 9 + j / 9) * XS + t];
-        else if (j < 92) v = Ms[17 * t + (j - 81)];
+        else if (j < 93) v = Ms[17 * t + (j - 81)];
         dst[g] = v;
     }
 }
@@ -301,9 +317,13 @@ k_clamp_double(ElemLaunch L)
 // correction; a stencil not certified by then goes to bin kClampPass2 + k.
 // Pass 2 starts again from the float vectors and allows up to three
 // corrections; a stencil not certified there goes to bin 9, the full double
-// Jacobi. A stencil's result depends only on its own data. (A wider
-// subspace in pass 2, max(k + 1, 3) columns, certified every stencil of a
-// sample but measured slower on the 40^3 cube: 0.39 against 0.23 ms.)
+// Jacobi. Pass 3 (the deflation) takes a stencil of k >= 4 whose float
+// spectrum has k' = 1..3 eigenvalues below -delta: the k'-column subspace of
+// those is refined the same way (up to three corrections) and the rest of
+// M certified by a double LDL^T instead of rotated; a stencil not certified
+// goes back to bin k. A stencil's result depends only on its own data. (A
+// wider subspace in pass 2, max(k + 1, 3) columns, certified every stencil
+// of a sample but measured slower on the 40^3 cube: 0.39 against 0.23 ms.)
 template <typename HT, int K, int PASS>
 __device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t idx, int k)
 {
@@ -333,7 +353,7 @@ __device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t id
     refine_residual<K>(Mg, V, R, B);
     refine_correct<K>(rec, cq, mu, R, V);
     refine_residual<K>(Mg, V, R, B);
-    constexpr int kMore = PASS == 1 ? 0 : 2;
+    constexpr int kMore = PASS == 1 ? 0 : 2;   // passes 2 and 3: up to three corrections
     bool conv = false;
 #pragma unroll 1
     for (int it = 0;; ++it) {
@@ -350,10 +370,12 @@ __device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t id
         refine_correct<K>(rec, cq, mu, R, V);
         refine_residual<K>(Mg, V, R, B);
     }
+    // where a stencil goes that this pass does not finish: pass 1 -> its
+    // second pass, pass 2 -> bin 9, pass 3 -> the bin of its N-block size
+    const int bin_next = PASS == 1 ? kClampPass2 + k : PASS == 2 ? 9 : __float_as_int(__ldg(rec + 92));
     if (!conv) {
-        const int bin = PASS == 1 ? kClampPass2 + k : 9;
-        const int pos = atomicAdd(L.clamp_bucket_count + bin, 1);
-        L.clamp_bucket[(int64_t)bin * cap + pos] = (int)idx;
+        const int pos = atomicAdd(L.clamp_bucket_count + bin_next, 1);
+        L.clamp_bucket[(int64_t)bin_next * cap + pos] = (int)idx;
         return;
     }
     const ClampRef ref = L.clamp_ref[idx];
@@ -365,6 +387,19 @@ __device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t id
     if (!ok) {
         atomicAdd(L.clamp_failed, 1);
         atomicExch(&L.scenes[ref.scene].sc->clamp_fail, 1);
+        return;
+    }
+    // pass 3 (deflation): V holds the clearly negative modes only, the rest
+    // of M (its near-null space and positive part) is certified instead of
+    // rotated: M - V B V^T + s I positive definite (double LDL^T) means no
+    // eigenvalue of the rest lies below -s. s = tau for an FP64 Hessian; for
+    // an FP32 one 1e-6 ||M||_F: its exact zeros are spread over ~1e-7
+    // ||M||_F by the float element math, and what lies above -1e-6 ||M||_F
+    // is left unclamped (a change far inside that form's tolerance)
+    const double rest_shift = sizeof(HT) == 4 ? 1e-6 * fro : tau;
+    if (PASS == 3 && !refine_rest_pd<K>(Mg, V, B, rest_shift)) {
+        const int pos = atomicAdd(L.clamp_bucket_count + bin_next, 1);
+        L.clamp_bucket[(int64_t)bin_next * cap + pos] = (int)idx;
         return;
     }
     // B_-: the part of B below -tau
@@ -433,22 +468,28 @@ __device__ __forceinline__ void clamp_refine_one(const ElemLaunch& L, int64_t id
     }
 }
 
-template <typename HT, int PASS, int NT>
+// Launch 1 takes bins 1..3 (pass 1); launch 2 takes the second-pass bins
+// kClampPass2 + 1..3 and, in the same launch, the deflation bins
+// kClampDefl + 1..3 (pass 3): a launch of its own over an empty bin cost
+// 0.13 ms on the 64^3 cube. Work unit b -> (bin, offset) over the launch's
+// bins in order; the grid loops.
+template <typename HT, int LAUNCH, int NT>
 __global__ void __launch_bounds__(NT)
 k_clamp_refine(ElemLaunch L)
 {
-    __shared__ int s_k, s_off;
-    constexpr int kb = PASS == 1 ? 1 : kClampPass2 + 1;
-    // work unit b -> (bin, offset) over the three bins; the grid loops
+    __shared__ int s_bin, s_off;
+    constexpr int nbins = LAUNCH == 1 ? 3 : (SX_CLAMP_DEFL ? 6 : 3);
     for (int b0 = blockIdx.x;; b0 += gridDim.x) {
         if (threadIdx.x == 0) {
             int b = b0;
-            s_k = -1;
+            s_bin = -1;
             s_off = 0;
-            for (int kk = 0; kk < 3; ++kk) {
-                const int nb = (L.clamp_bucket_count[kb + kk] + NT - 1) / NT;
+            for (int kk = 0; kk < nbins; ++kk) {
+                const int bin = LAUNCH == 1 ? 1 + kk
+                                            : (kk < 3 ? kClampPass2 + 1 + kk : kClampDefl + kk - 2);
+                const int nb = (L.clamp_bucket_count[bin] + NT - 1) / NT;
                 if (b < nb) {
-                    s_k = kk + 1;
+                    s_bin = bin;
                     s_off = b * NT;
                     break;
                 }
@@ -456,16 +497,28 @@ k_clamp_refine(ElemLaunch L)
             }
         }
         __syncthreads();
-        const int k = s_k;
+        const int bin = s_bin;
         const int jj = s_off + threadIdx.x;
-        __syncthreads();   // s_k, s_off read by all before thread 0 rewrites them
-        if (k < 0) return;
-        const int bin = kb + k - 1;
+        __syncthreads();   // s_bin, s_off read by all before thread 0 rewrites them
+        if (bin < 0) return;
         if (jj >= L.clamp_bucket_count[bin]) continue;
         const int64_t idx = L.clamp_bucket[(int64_t)bin * L.clamp_cap + jj];
-        if (k == 1) clamp_refine_one<HT, 1, PASS>(L, idx, k);
-        else if (k == 2) clamp_refine_one<HT, 2, PASS>(L, idx, k);
-        else clamp_refine_one<HT, 3, PASS>(L, idx, k);
+        if (LAUNCH == 1) {
+            const int k = bin;
+            if (k == 1) clamp_refine_one<HT, 1, 1>(L, idx, k);
+            else if (k == 2) clamp_refine_one<HT, 2, 1>(L, idx, k);
+            else clamp_refine_one<HT, 3, 1>(L, idx, k);
+        } else if (bin < kClampDefl) {
+            const int k = bin - kClampPass2;
+            if (k == 1) clamp_refine_one<HT, 1, 2>(L, idx, k);
+            else if (k == 2) clamp_refine_one<HT, 2, 2>(L, idx, k);
+            else clamp_refine_one<HT, 3, 2>(L, idx, k);
+        } else {
+            const int k = bin - kClampDefl;   // k', the negative modes
+            if (k == 1) clamp_refine_one<HT, 1, 3>(L, idx, k);
+            else if (k == 2) clamp_refine_one<HT, 2, 3>(L, idx, k);
+            else clamp_refine_one<HT, 3, 3>(L, idx, k);
+        }
     }
 }
 
@@ -715,9 +768,10 @@ cudaError_t launch_clamp(const ElemLaunch& L, cudaStream_t s)
             <<<ga, kClampFloatThreads, clamp_float_smem(kClampFloatThreads), s>>>(L);
         const int sms = device_sms();
         if (SX_CLAMP_REFINE) {
-            // pass 1 covers its largest possible work in one trip; pass 2
-            // (a few percent of the stencils) loops over a grid of 8 blocks
-            // per SM
+            // pass 1 covers its largest possible work in one trip; the
+            // launch of pass 2 (a few percent of the stencils) and the
+            // deflation (none on a tet mesh, most of a contact scene's
+            // barrier stencils) loops over a grid of 8 blocks per SM
             const int gr = (int)std::max<int64_t>(1, (cap + 127) / 128 + 3);
             const int gr2 = std::min(gr, 8 * sms);
             if (f32) {

@@ -643,6 +643,56 @@ __device__ __forceinline__ bool refine_negdef(const double (&B)[K][K], double ta
     return ok;
 }
 
+// true when M - V B V^T + shift I is positive definite (LDL^T without
+// pivoting, in double): the part of M outside span(V) has no eigenvalue
+// below -shift (up to the coupling ||M V - V B||, which the caller certified)
+template <int K>
+__device__ __forceinline__ bool refine_rest_pd(const double* __restrict__ Mg,
+                                               const double (&V)[9][K], const double (&B)[K][K],
+                                               double shift)
+{
+    double U[9][K];
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            double t = 0.0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) t = fma(V[r][j], B[j][p], t);
+            U[r][p] = t;
+        }
+    double A[45];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            double t = __ldg(Mg + pk(i, j));
+#pragma unroll
+            for (int p = 0; p < K; ++p) t = fma(-U[i][p], V[j][p], t);
+            A[pk(i, j)] = t;
+        }
+    double Lm[45];
+    double dg[9];
+    bool pd = true;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        double s = A[pk(j, j)] + shift;
+#pragma unroll
+        for (int m = 0; m < j; ++m) s -= Lm[pk(j, m)] * Lm[pk(j, m)] * dg[m];
+        pd = pd && (s > 0.0);
+        dg[j] = s;
+        const double inv = 1.0 / s;
+#pragma unroll
+        for (int i = j + 1; i < 9; ++i) {
+            double t = A[pk(i, j)];
+#pragma unroll
+            for (int m = 0; m < j; ++m) t -= Lm[pk(i, m)] * Lm[pk(j, m)] * dg[m];
+            Lm[pk(i, j)] = t * inv;
+        }
+    }
+    return pd;
+}
+
 // B <- its part below -tau, sum over eigenvalues l < -tau of l g g^T
 // (cyclic Jacobi on the k x k B, rotations skipped at |b_pq| <= thr)
 template <int K>

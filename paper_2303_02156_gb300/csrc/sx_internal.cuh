@@ -189,11 +189,13 @@ struct ClampRef {
 
 // per queued stencil record of the split projection (floats): the float
 // eigenvectors as the Jacobi left them (column c at 9 c), their 9
-// eigenvalues (81 + c), and the column of each ascending-eigenvalue slot
-// (4 bits per slot in the two words at 90), pad
+// eigenvalues (81 + c), the column of each ascending-eigenvalue slot
+// (4 bits per slot in the two words at 90), the N-block size k (an int in
+// word 92), pad
 constexpr int kClampRec = 96;
-constexpr int kClampBins = 16;
-constexpr int kClampPass2 = 10;
+constexpr int kClampBins = 20;
+constexpr int kClampPass2 = 10;   // bins 11..13: second refinement pass, k = 1..3
+constexpr int kClampDefl = 16;    // bins 17..19: deflation of k' = 1..3 negative modes
 
 struct ElemLaunch {
     const SceneDev* scenes;
@@ -227,7 +229,8 @@ struct ElemLaunch {
     // their eigenvalues and their order),
     // ||M||_F per queued stencil, and the queue positions binned
     // (kClampBins bins of clamp_cap: 0..9 by N-block size k, kClampPass2 + k
-    // for the second refinement pass of k = 1..3)
+    // for the second refinement pass of k = 1..3, kClampDefl + k' for the
+    // deflation of the k' negative modes of a stencil with k >= 4)
     float* clamp_X;
     double* clamp_fro;
     int* clamp_bucket;

@@ -1,7 +1,9 @@
 """Phase 2 of the projection (§5.2 "Projection to positive semi-definiteness")
 runs different paths by the size k of a stencil's N block: the certified
-subspace refinement (k = 1..3, two passes), the block-restricted double Jacobi
-(k = 4..8) and the warp-per-stencil Jacobi (bin 9). These tests assemble
+subspace refinement (k = 1..3, two passes), the deflation of 1..3 clearly
+negative modes of a stencil with k >= 4 (the rest certified by a double
+LDL^T), the block-restricted double Jacobi (other k = 4..8) and the
+warp-per-stencil Jacobi (bin 9). These tests assemble
 scenes whose stencils take each path, read the bin counts of the evaluation
 (sx_projection_bins) to show that the path ran, and compare the assembled
 system with the FP64 oracle's (FP64 1e-10, FP32 1e-4, normwise over the BSR
@@ -16,7 +18,7 @@ from oracle import oracle as orc
 from paper_2303_02156_gb300 import scenes, sx
 
 TOL64, TOL32 = 1e-10, 1e-4
-NBINS = 16
+NBINS = 20
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +50,8 @@ def _bins(ctx, s):
 def test_refinement_passes_match_oracle(ctx, precision):
     """A strongly deformed SNH box (inverted tets, jitter 0.45 h): stencils of
     k = 1..3 go through the refinement, some of them (an N block close to
-    the next eigenvalue) through its second pass."""
+    the next eigenvalue) through its second pass; tets with 4 or 5 negative
+    modes through the block-restricted Jacobi."""
     from paper_2303_02156_gb300.scene import Scene
     m = scenes.kuhn_box(10, 9, 8, h=0.25, seed=31)
     T = m["tets"].shape[0]
@@ -70,10 +73,11 @@ def test_refinement_passes_match_oracle(ctx, precision):
     assert np.array_equal(rp, sc.row_ptr) and np.array_equal(col, sc.col)
     tol = TOL64 if precision == sx.SX_FP64 else TOL32
     err = _relerr(vals, vo)
-    # every queued stencil sits in one bin of the float part's; bin 9 also
-    # takes what the second pass did not certify
-    assert sum(bins[:10]) >= clamped > 0, bins
+    # every queued stencil sits in one bin of the float part's (0..9 or a
+    # deflation bin); bin 9 also takes what the second pass did not certify
+    assert sum(bins[:10]) + sum(bins[17:20]) >= clamped > 0, bins
     assert sum(bins[1:4]) > 0 and sum(bins[11:14]) > 0, bins
+    assert sum(bins[4:9]) > 0, bins
     assert err <= tol, (err, bins)
     s.close()
 
@@ -90,10 +94,11 @@ def _barrier_case(n_pairs=600, seed=41):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", [sx.SX_FP64, sx.SX_FP32])
-def test_block_restricted_jacobi_matches_oracle(ctx, precision):
-    """Point-triangle barrier stencils: their Hessians have a large null
-    space and negative modes from the distance's curvature, so their N
-    blocks have k >= 4 and go to the block-restricted double Jacobi."""
+def test_deflation_matches_oracle(ctx, precision):
+    """Point-triangle barrier stencils: their Hessians have a null space
+    (four exact zeros in the translation-free 9x9) and two negative modes
+    from the distance's curvature, so k = 6 with k' = 2 clearly negative
+    modes: the deflation refines those two and certifies the rest."""
     from paper_2303_02156_gb300.scene import Scene
     X, x, pairs = _barrier_case()
     s = Scene(ctx, X)
@@ -109,7 +114,7 @@ def test_block_restricted_jacobi_matches_oracle(ctx, precision):
     assert np.array_equal(rp, sc.row_ptr) and np.array_equal(col, sc.col)
     tol = TOL64 if precision == sx.SX_FP64 else TOL32
     err = _relerr(vals, vo)
-    assert sum(bins[4:9]) > 0, bins
+    assert sum(bins[17:20]) > 0, bins
     assert err <= tol, (err, bins)
     s.close()
 
