@@ -2,8 +2,7 @@
 // semi-definiteness (§5.2 "Projection to positive semi-definiteness",
 // Algorithm 1): the queued 9x9 translation-free Hessians are
 // eigen-decomposed (float Jacobi; then, in double, a certified refinement of
-// the subspace of the k <= 3 lowest eigenvalues, a deflation of 1..3 clearly
-// negative modes with the rest certified by an LDL^T, or Gram-Schmidt and
+// the subspace of the k <= 3 lowest eigenvalues, or Gram-Schmidt and
 // block-restricted Jacobi sweeps for the other k: sx_clamp.cuh), their
 // negative eigenvalues clamped and the stencils' Hessian blocks rewritten.
 #include <cuda_runtime.h>
