@@ -2198,7 +2198,44 @@ int sx_newton_step_batch(sx_ctx* ctx, sx_scene* const* scenes, int n, double dt,
                                             n, B->d_desc, F_FEXT2, 0, st));
     std::vector<double> fext(n, 0.0);
     for (int it = 0; it <= o.max_newton; ++it) {
+        // The convergence test needs E and g only. A scene whose previous
+        // residual was within 10 sqrt(tol) of its reference will likely pass
+        // it now (Newton converges quadratically): it is evaluated to E + g
+        // first, and only a scene that does not pass takes the E + g + H
+        // evaluation below, at the same state (the same E and g: level 1 runs
+        // the same kernels without the Hessian). This saves the last
+        // iteration's Hessian, projection and assembly.
+        if (it > 0) {
+            std::vector<int> likely(n, 0);
+            int nl = 0;
+            for (int i = 0; i < n; ++i) {
+                const double ref = std::max(std::max(g0[i], fext[i]), 1e-30);
+                likely[i] = !done[i] && gl[i] <= 10.0 * std::sqrt(o.newton_tol) * ref;
+                nl += likely[i];
+            }
+            if (nl > 0) {
+                if ((rc = set_active(ctx, B, likely, st)) != SX_OK) return rc;
+                if ((rc = run_eval(ctx, B, SX_EG, 0, o.precision, false, st)) != SX_OK) return rc;
+                if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
+                for (int i = 0; i < n; ++i) {
+                    if (!likely[i]) continue;
+                    const SceneScal& sc = B->h_scal[i];
+                    if (sc.nonfinite || !std::isfinite(sc.E) || sc.bad_state) continue;
+                    const double gn = std::sqrt(sc.gnorm2);
+                    if (gn <= o.newton_tol * std::max(std::max(g0[i], fext[i]), 1e-30)) {
+                        E[i] = sc.E;
+                        gl[i] = gn;
+                        done[i] = 1;
+                    }
+                }
+            }
+        }
         for (int i = 0; i < n; ++i) act[i] = !done[i];
+        {
+            bool any = false;
+            for (int i = 0; i < n; ++i) any = any || act[i];
+            if (!any) break;
+        }
         if ((rc = set_active(ctx, B, act, st)) != SX_OK) return rc;
         if ((rc = run_eval(ctx, B, SX_EGH, o.project, o.precision, false, st)) != SX_OK) return rc;
         if ((rc = read_scal(ctx, B, st)) != SX_OK) return rc;
