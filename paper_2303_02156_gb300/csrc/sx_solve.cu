@@ -324,6 +324,13 @@ int pcg_update_blocks(int n_node_tiles) { return (n_node_tiles + kUpdTiles - 1) 
 #define SX_UPD_SPLIT 1
 #endif
 constexpr int kUpd2Threads = 128;
+// resident blocks per SM the two-node update is compiled for (a register
+// cap; 0: none, 106 registers, four blocks). Caps for 5, 6 and 8 blocks (96,
+// 80, 64 registers, with spills) measured no faster on the 64^3 cube's
+// Newton step: 113.0, 112.5, 111.3 against 111.1 ms
+#ifndef SX_UPD2_MINB
+#define SX_UPD2_MINB 0
+#endif
 
 __device__ __forceinline__ double warp_sum_xor(double v)
 {
@@ -332,7 +339,7 @@ __device__ __forceinline__ double warp_sum_xor(double v)
     return v;
 }
 
-__global__ void __launch_bounds__(kUpd2Threads)
+__global__ void __launch_bounds__(kUpd2Threads, SX_UPD2_MINB > 0 ? SX_UPD2_MINB : 1)
 k_pcg_update2(const SceneDev* scenes, const Tile* tiles, int ntiles, int par, double* part,
               const int* tbeg, const int* tend, double tol, int max_iter)
 {
